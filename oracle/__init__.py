@@ -1,0 +1,244 @@
+"""CPU FP64 oracle for the many-body MD hot path (test infrastructure only).
+
+A ctypes wrapper around ``md_oracle.c``. Only the tests, the smoke check and
+the benchmark's CPU-baseline leg may import this package; the CUDA library
+and its Python binding never do, and share no code with it.
+
+Every function here takes numpy float64 arrays in the caller's atom order:
+positions ``x`` [N, 3] (wrapped into [0, L)), box lengths ``box`` [3].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import pathlib
+import subprocess
+
+import numpy as np
+
+_HERE = pathlib.Path(__file__).resolve().parent
+_LIBDIR = _HERE / "_lib"
+_SO = _LIBDIR / "libmd_oracle.so"
+
+KIND = {"rgl": 0, "sc": 1, "spline": 2}
+RGL_ORDER = ("A", "xi", "p", "q", "r0")
+SC_ORDER = ("eps", "c", "a", "n", "m")
+
+
+def build(force: bool = False) -> pathlib.Path:
+    """Compiles the oracle with gcc: -O2, no fast-math, no FMA contraction
+    (the neighbour-list distance test must round after every operation)."""
+    src = _HERE / "md_oracle.c"
+    if not force and _SO.exists() and _SO.stat().st_mtime >= src.stat().st_mtime:
+        return _SO
+    _LIBDIR.mkdir(exist_ok=True)
+    tmp = _SO.with_suffix(f".{os.getpid()}.tmp")
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           str(src), "-o", str(tmp), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(str(build()))
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
+    lib.orc_pot_new.restype = vp
+    lib.orc_pot_new.argtypes = [i32, _D, dbl, dbl, i32, i32, i32, _D, dbl, dbl, dbl, dbl]
+    lib.orc_pot_free.argtypes = [vp]
+    lib.orc_pot_eval.argtypes = [vp, i32, _D, _D, _D, _D, _D]
+    lib.orc_embed_eval.argtypes = [vp, i32, _D, _D, _D, _D]
+    lib.orc_wrap.argtypes = [i32, _D, _D]
+    lib.orc_pairs_brute.restype = i64
+    lib.orc_pairs_brute.argtypes = [i32, _D, _D, dbl, _I, _I, i64]
+    lib.orc_pairs_cells.restype = i64
+    lib.orc_pairs_cells.argtypes = [i32, _D, _D, dbl, _I, _I, i64]
+    lib.orc_forces_brute.restype = dbl
+    lib.orc_forces_brute.argtypes = [vp, i32, _D, _D, _D, _D, _D]
+    lib.orc_forces_pairs.restype = dbl
+    lib.orc_forces_pairs.argtypes = [vp, i32, _D, _D, i64, _I, _I, _D, _D, _D, _D]
+    lib.orc_md_run.restype = i64
+    lib.orc_md_run.argtypes = [vp, i32, _D, _D, _D, dbl, dbl, dbl, i32, _D]
+    lib.orc_param_deriv.restype = dbl
+    lib.orc_param_deriv.argtypes = [vp, i32, i32, _D, _D, i64, _I, _I, _D]
+    lib.orc_param_grad.argtypes = [vp, i32, i32, _D, _D, i64, _I, _I, _D, dbl, _D]
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Potential:
+    """Oracle-side potential. ``spec`` is a dict like
+    ``{"kind": "rgl", "A":..., "xi":..., "p":..., "q":..., "r0":..., "r_taper":..., "r_cut":...}``,
+    ``{"kind": "sc", "eps", "c", "a", "n", "m", "r_taper", "r_cut"}`` or
+    ``{"kind": "spline", "phi": knots, "f": knots, "F": knots, "r_lo", "r_hi", "rho_lo", "rho_hi"}``."""
+
+    def __init__(self, spec: dict):
+        lib = _load()
+        self.spec = dict(spec)
+        kind = spec["kind"]
+        prm = np.zeros(8)
+        knots = np.zeros(1)
+        n_phi = n_f = n_F = 0
+        r_lo = r_hi = rho_lo = rho_hi = 0.0
+        r_taper = float(spec.get("r_taper", 0.0))
+        r_cut = float(spec.get("r_cut", 0.0))
+        if kind == "rgl":
+            prm[:5] = [spec[k] for k in RGL_ORDER]
+            self.n_param = 5
+        elif kind == "sc":
+            prm[:5] = [spec[k] for k in SC_ORDER]
+            self.n_param = 5
+        elif kind == "spline":
+            phi, f, F = (_f64(spec[k]) for k in ("phi", "f", "F"))
+            n_phi, n_f, n_F = len(phi), len(f), len(F)
+            knots = np.concatenate([phi, f, F])
+            r_lo, r_hi = float(spec["r_lo"]), float(spec["r_hi"])
+            rho_lo, rho_hi = float(spec["rho_lo"]), float(spec["rho_hi"])
+            r_taper = r_cut = r_hi
+            self.n_param = n_phi + n_f + n_F
+        else:
+            raise ValueError(kind)
+        self.r_cut = r_cut
+        self._prm, self._knots = prm, knots
+        self._h = lib.orc_pot_new(KIND[kind], _dp(prm), r_taper, r_cut, n_phi, n_f, n_F, _dp(knots),
+                                  r_lo, r_hi, rho_lo, rho_hi)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.orc_pot_free(self._h)
+            self._h = None
+
+    def pair(self, r) -> tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:
+        """(V, V', rho, rho') at distances r."""
+        r = _f64(np.atleast_1d(r))
+        out = [np.empty_like(r) for _ in range(4)]
+        _load().orc_pot_eval(self._h, r.size, _dp(r), *(_dp(o) for o in out))
+        return tuple(out)
+
+    def embed(self, rho) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """(F, F', F'') at densities rho."""
+        rho = _f64(np.atleast_1d(rho))
+        out = [np.empty_like(rho) for _ in range(3)]
+        _load().orc_embed_eval(self._h, rho.size, _dp(rho), *(_dp(o) for o in out))
+        return tuple(out)
+
+
+def wrap(x, box) -> np.ndarray:
+    x = _f64(x).copy()
+    box = _f64(box)
+    _load().orc_wrap(x.shape[0], _dp(x), _dp(box))
+    return x
+
+
+def pairs(x, box, rl: float, method: str = "cells") -> tuple[np.ndarray, np.ndarray]:
+    """Half list (i < j) of pairs with minimum-image r^2 < rl^2."""
+    lib = _load()
+    x, box = _f64(x), _f64(box)
+    n = x.shape[0]
+    fn = lib.orc_pairs_cells if method == "cells" else lib.orc_pairs_brute
+    cap = max(64, n * 80)
+    while True:
+        pi = np.empty(cap, dtype=np.int32)
+        pj = np.empty(cap, dtype=np.int32)
+        np_ = fn(n, _dp(x), _dp(box), float(rl), _ip(pi), _ip(pj), cap)
+        if np_ <= cap:
+            return pi[:np_].copy(), pj[:np_].copy()
+        cap = int(np_)
+
+
+def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs") -> dict:
+    """Energies and forces of Eq. (1)-(3). method "pairs" uses the half list
+    within r_cut + skin and Newton's third law; "brute" the O(N^2) double sums."""
+    lib = _load()
+    x, box = _f64(x), _f64(box)
+    n = x.shape[0]
+    rho = np.zeros(n)
+    e = np.zeros(n)
+    f = np.zeros((n, 3))
+    if method == "brute":
+        E = lib.orc_forces_brute(pot._h, n, _dp(x), _dp(box), _dp(rho), _dp(e), _dp(f))
+        Fp = pot.embed(rho)[1] if n else np.zeros(0)
+        return dict(E=E, rho=rho, Fp=Fp, e_atom=e, f=f)
+    pi, pj = pairs(x, box, pot.r_cut + skin)
+    Fp = np.zeros(n)
+    E = lib.orc_forces_pairs(pot._h, n, _dp(x), _dp(box), pi.size, _ip(pi), _ip(pj), _dp(rho), _dp(Fp),
+                             _dp(e), _dp(f))
+    return dict(E=E, rho=rho, Fp=Fp, e_atom=e, f=f)
+
+
+def md_run(pot: Potential, x, v, box, mass: float, dt: float, skin: float, n_steps: int) -> dict:
+    """Velocity-Verlet trajectory; returns final x, v, per-step thermo rows
+    (KE, PE, E_tot, T) and the number of list rebuilds."""
+    lib = _load()
+    x, v, box = _f64(x).copy(), _f64(v).copy(), _f64(box)
+    thermo = np.zeros((n_steps + 1, 4))
+    nreb = lib.orc_md_run(pot._h, x.shape[0], _dp(x), _dp(v), _dp(box), float(mass), float(dt), float(skin),
+                          int(n_steps), _dp(thermo))
+    return dict(x=x, v=v, thermo=thermo, n_rebuild=int(nreb))
+
+
+def param_deriv(pot: Potential, which: int, x, box) -> tuple[float, np.ndarray]:
+    """(dE/dtheta, dF/dtheta [N,3]) for parameter index ``which``."""
+    lib = _load()
+    x, box = _f64(x), _f64(box)
+    pi, pj = pairs(x, box, pot.r_cut)
+    dF = np.zeros((x.shape[0], 3))
+    dE = lib.orc_param_deriv(pot._h, int(which), x.shape[0], _dp(x), _dp(box), pi.size, _ip(pi), _ip(pj),
+                             _dp(dF))
+    return dE, dF
+
+
+def param_grad(pot: Potential, x, box, gF, gE: float, grad: np.ndarray | None = None) -> np.ndarray:
+    """Accumulates sum_i gF_i . dF_i/dtheta + gE dE/dtheta into ``grad``."""
+    lib = _load()
+    x, box, gF = _f64(x), _f64(box), _f64(gF)
+    if grad is None:
+        grad = np.zeros(pot.n_param)
+    pi, pj = pairs(x, box, pot.r_cut)
+    lib.orc_param_grad(pot._h, pot.n_param, x.shape[0], _dp(x), _dp(box), pi.size, _ip(pi), _ip(pj), _dp(gF),
+                       float(gE), _dp(grad))
+    return grad
+
+
+def full_neighbor_lists(n: int, pi: np.ndarray, pj: np.ndarray) -> list[np.ndarray]:
+    """Per-atom sorted neighbour sets (both directions) from a half list."""
+    a = np.concatenate([pi, pj])
+    b = np.concatenate([pj, pi])
+    order = np.lexsort((b, a))
+    a, b = a[order], b[order]
+    starts = np.searchsorted(a, np.arange(n + 1))
+    return [b[starts[i]:starts[i + 1]] for i in range(n)]
+
+
+def tabulate_spline(spec: dict, n_knots: int = 200, r_lo: float = 1.5, r_hi: float = 5.0,
+                    rho_hi: float | None = None) -> dict:
+    """Knot values of a spline model tabulated from an analytic potential:
+    V and rho on ``n_knots`` uniform knots over [r_lo, r_hi], F on
+    ``n_knots`` uniform knots over [0, rho_hi] (default twice the perfect
+    fcc density is supplied by the caller)."""
+    pot = Potential(spec)
+    r = np.linspace(r_lo, r_hi, n_knots)
+    V, _, rho, _ = pot.pair(r)
+    rg = np.linspace(0.0, rho_hi, n_knots)
+    F = pot.embed(rg)[0]
+    return dict(kind="spline", phi=V, f=rho, F=F, r_lo=r_lo, r_hi=r_hi, rho_lo=0.0, rho_hi=rho_hi)

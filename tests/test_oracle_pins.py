@@ -1,0 +1,382 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks the oracle against a closed form, a literature value, an
+independent library routine (scipy), brute force, a physical invariant, or
+a finite difference, chosen so that a dropped term, a wrong sign or index,
+or a wrong convention in the oracle fails at least one of them.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1212_6332_gb300 import inputs as I
+
+
+def fcc_shells(a, rmax):
+    """Distances of all fcc lattice sites within rmax of the origin, by
+    enumerating conventional cells (independent of any neighbour search)."""
+    n = int(rmax / a) + 2
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    out = []
+    for i, j, k in itertools.product(range(-n, n + 1), repeat=3):
+        p = (np.array([i, j, k]) + basis) * a
+        r = np.linalg.norm(p, axis=1)
+        out.append(r[(r > 0) & (r < rmax)])
+    return np.concatenate(out)
+
+
+def smoothstep(r, rs, rc):
+    x = np.clip((r - rs) / (rc - rs), 0.0, 1.0)
+    return np.where(r < rc, 1 - 10 * x ** 3 + 15 * x ** 4 - 6 * x ** 5, 0.0)
+
+
+def rgl_lattice_energy(spec, a):
+    """Cohesive energy per atom of the perfect fcc lattice as a shell sum:
+    E = -sqrt(sum_s rho(r_s)) + 1/2 sum_s V(r_s)."""
+    r = fcc_shells(a, spec["r_cut"])
+    S = smoothstep(r, spec["r_taper"], spec["r_cut"])
+    V = 2 * spec["A"] * np.exp(-spec["p"] * (r / spec["r0"] - 1)) * S
+    rho = spec["xi"] ** 2 * np.exp(-2 * spec["q"] * (r / spec["r0"] - 1)) * S
+    return -np.sqrt(rho.sum()) + 0.5 * V.sum(), rho.sum()
+
+
+def sc_lattice_energy(spec, a):
+    r = fcc_shells(a, spec["r_cut"])
+    S = smoothstep(r, spec["r_taper"], spec["r_cut"])
+    V = spec["eps"] * (spec["a"] / r) ** spec["n"] * S
+    rho = (spec["a"] / r) ** spec["m"] * S
+    return -spec["c"] * spec["eps"] * np.sqrt(rho.sum()) + 0.5 * V.sum(), rho.sum()
+
+
+# ---------------------------------------------------------------- lists
+
+@pytest.mark.parametrize("n,spec,skin", [(3, I.RGL_CU, 0.3), (4, I.RGL_CU, 0.3), (5, I.RGL_CU, 0.3),
+                                         (6, I.RGL_CU, 0.3), (7, I.SC_CU, 0.3)])
+def test_linked_cells_equal_brute_force(n, spec, skin):
+    bx = I.perturbed_fcc(n, I.A_CU, 300.0, I.MASS_CU, seed=7 + n)
+    rl = spec["r_cut"] + skin
+    a = O.pairs(bx.x, bx.box, rl, "cells")
+    b = O.pairs(bx.x, bx.box, rl, "brute")
+    sa = set(zip(a[0].tolist(), a[1].tolist()))
+    sb = set(zip(b[0].tolist(), b[1].tolist()))
+    assert sa == sb and len(sa) == len(a[0])
+    assert all(i < j for i, j in sa)
+
+
+def test_pairs_match_scipy_periodic_kdtree():
+    spatial = pytest.importorskip("scipy.spatial")
+    bx = I.perturbed_fcc(6, I.A_CU, 300.0, I.MASS_CU, seed=99)
+    rl = 5.3
+    pi, pj = O.pairs(bx.x, bx.box, rl)
+    tree = spatial.cKDTree(bx.x, boxsize=bx.box)
+    ref = tree.query_pairs(rl, output_type="ndarray")
+    ref = set(map(tuple, np.sort(ref, axis=1).tolist()))
+    assert set(zip(pi.tolist(), pj.tolist())) == ref
+
+
+@pytest.mark.parametrize("spec,a,rc_count,rl_count", [(I.RGL_CU, I.A_CU, 42, 54), (I.SC_CU, I.A_CU, 134, 140),
+                                                      (I.RGL_NI, I.A_NI, 42, 54)])
+def test_neighbour_counts_on_perfect_lattice(spec, a, rc_count, rl_count):
+    n = 6 if spec is not I.SC_CU else 7
+    x, box = I.fcc_lattice(n, a)
+    lists = O.full_neighbor_lists(len(x), *O.pairs(x, box, spec["r_cut"] + 0.3))
+    counts = np.array([len(l) for l in lists])
+    assert (counts == rl_count).all()
+    inner = O.full_neighbor_lists(len(x), *O.pairs(x, box, spec["r_cut"]))
+    assert all(len(l) == rc_count for l in inner)
+    assert rc_count == len(fcc_shells(a, spec["r_cut"]))
+
+
+# ---------------------------------------------------------------- energies
+
+@pytest.mark.parametrize("scale", [1.0, 0.98, 1.02])
+def test_rgl_cu_lattice_shell_sum(scale):
+    a = I.A_CU * scale
+    x, box = I.fcc_lattice(6, a)
+    r = O.forces(O.Potential(I.RGL_CU), x, box, skin=0.3)
+    e_ref, rho_ref = rgl_lattice_energy(I.RGL_CU, a)
+    assert r["E"] / len(x) == pytest.approx(e_ref, rel=1e-13)
+    assert np.allclose(r["rho"], rho_ref, rtol=1e-13)
+    assert np.allclose(r["e_atom"], e_ref, rtol=1e-13)
+
+
+def test_rgl_ni_lattice_shell_sum():
+    x, box = I.fcc_lattice(6, I.A_NI)
+    r = O.forces(O.Potential(I.RGL_NI), x, box, skin=0.3)
+    assert r["E"] / len(x) == pytest.approx(rgl_lattice_energy(I.RGL_NI, I.A_NI)[0], rel=1e-13)
+
+
+def test_sutton_chen_lattice_shell_sum():
+    x, box = I.fcc_lattice(7, I.A_CU)
+    r = O.forces(O.Potential(I.SC_CU), x, box, skin=0.3)
+    assert r["E"] / len(x) == pytest.approx(sc_lattice_energy(I.SC_CU, I.A_CU)[0], rel=1e-13)
+
+
+def test_rgl_cu_literature_cohesive_energy():
+    """Cleri and Rosato (Phys. Rev. B 48, 22 (1993)) fitted these Cu
+    parameters with interactions out to the fifth neighbour shell to the
+    cohesive energy 3.544 eV/atom. A hard cut between the 5th (5.72 A) and
+    6th (6.26 A) shells reproduces it; the taper is switched off by
+    r_taper = r_cut."""
+    spec = dict(I.RGL_CU, r_taper=6.0, r_cut=6.0)
+    x, box = I.fcc_lattice(8, I.A_CU)
+    r = O.forces(O.Potential(spec), x, box, skin=0.0)
+    assert r["E"] / len(x) == pytest.approx(-3.544, abs=2e-3)
+
+
+def test_dimer_closed_form():
+    """Two atoms: rho_1 = rho_2 = rho(r), E = V(r) + 2 F(rho(r)),
+    |F| = dE/dr (by a central difference of the closed form)."""
+    pot = O.Potential(I.RGL_CU)
+    box = np.array([40.0, 40.0, 40.0])
+    for r in (2.2, 3.0, 4.7):
+        x = np.array([[10.0, 10.0, 10.0], [10.0 + r, 10.0, 10.0]])
+        out = O.forces(pot, x, box, method="brute")
+        e = lambda s: 2 * I.RGL_CU["A"] * np.exp(-I.RGL_CU["p"] * (s / I.RGL_CU["r0"] - 1)) * smoothstep(s, 4.5, 5.0) \
+            - 2 * np.sqrt(I.RGL_CU["xi"] ** 2 * np.exp(-2 * I.RGL_CU["q"] * (s / I.RGL_CU["r0"] - 1))
+                          * smoothstep(s, 4.5, 5.0))
+        assert out["E"] == pytest.approx(float(e(r)), rel=1e-13)
+        h = 1e-6
+        dEdr = (e(r + h) - e(r - h)) / (2 * h)
+        # atom 1 sits at larger x: F_1x = -dE/dr, F_0x = +dE/dr
+        assert out["f"][1, 0] == pytest.approx(-dEdr, rel=1e-7, abs=1e-10)
+        assert out["f"][0, 0] == pytest.approx(dEdr, rel=1e-7, abs=1e-10)
+        assert np.abs(out["f"][:, 1:]).max() == 0.0
+    far = np.array([[1.0, 1.0, 1.0], [20.0, 1.0, 1.0]])
+    out = O.forces(pot, far, box, method="brute")
+    assert out["E"] == 0.0 and np.abs(out["f"]).max() == 0.0
+
+
+# ---------------------------------------------------------------- forces
+
+@pytest.mark.parametrize("spec,a,n", [(I.RGL_CU, I.A_CU, 5), (I.SC_CU, I.A_CU, 7), (I.RGL_NI, I.A_NI, 5)])
+def test_perfect_lattice_has_zero_force(spec, a, n):
+    x, box = I.fcc_lattice(n, a)
+    r = O.forces(O.Potential(spec), x, box, skin=0.3)
+    assert np.abs(r["f"]).max() < 1e-12
+
+
+@pytest.mark.parametrize("spec", [I.RGL_CU, I.SC_CU])
+def test_half_list_equals_double_sums(spec):
+    bx = I.perturbed_fcc(5 if spec is I.RGL_CU else 7, I.A_CU, 300.0, I.MASS_CU, seed=3)
+    pot = O.Potential(spec)
+    a = O.forces(pot, bx.x, bx.box, skin=0.3)
+    b = O.forces(pot, bx.x, bx.box, method="brute")
+    assert a["E"] == pytest.approx(b["E"], rel=1e-13)
+    assert np.allclose(a["rho"], b["rho"], rtol=1e-13)
+    assert np.allclose(a["e_atom"], b["e_atom"], rtol=1e-12, atol=1e-13)
+    assert np.abs(a["f"] - b["f"]).max() <= 1e-12 * np.abs(b["f"]).max()
+
+
+def test_net_force_vanishes():
+    bx = I.perturbed_fcc(5, I.A_CU, 300.0, I.MASS_CU, seed=11)
+    r = O.forces(O.Potential(I.RGL_CU), bx.x, bx.box, skin=0.3, method="brute")
+    assert np.abs(r["f"].sum(axis=0)).max() < 1e-12
+
+
+def test_translation_and_permutation_invariance():
+    bx = I.perturbed_fcc(5, I.A_CU, 300.0, I.MASS_CU, seed=5)
+    pot = O.Potential(I.RGL_CU)
+    a = O.forces(pot, bx.x, bx.box, skin=0.3)
+    shifted = I.wrap(bx.x + np.array([1.234, -0.77, 5.5]), bx.box)
+    b = O.forces(pot, shifted, bx.box, skin=0.3)
+    assert b["E"] == pytest.approx(a["E"], rel=1e-12)
+    assert np.abs(a["f"] - b["f"]).max() < 1e-11
+    perm = np.random.default_rng(0).permutation(len(bx.x))
+    c = O.forces(pot, bx.x[perm], bx.box, skin=0.3)
+    assert c["E"] == pytest.approx(a["E"], rel=1e-13)
+    assert np.abs(c["f"] - a["f"][perm]).max() < 1e-12
+
+
+@pytest.mark.parametrize("spec", [I.RGL_CU, I.SC_CU])
+def test_forces_are_minus_energy_gradient(spec):
+    """Central differences of E_T against the force of Eq. (3)."""
+    bx = I.perturbed_fcc(5 if spec is I.RGL_CU else 7, I.A_CU, 300.0, I.MASS_CU, seed=21)
+    pot = O.Potential(spec)
+    f = O.forces(pot, bx.x, bx.box, skin=0.3)["f"]
+    h = 1e-5
+    rng = np.random.default_rng(1)
+    for i in rng.choice(len(bx.x), 6, replace=False):
+        for a in range(3):
+            xp, xm = bx.x.copy(), bx.x.copy()
+            xp[i, a] += h
+            xm[i, a] -= h
+            ep = O.forces(pot, xp, bx.box, skin=0.3)["E"]
+            em = O.forces(pot, xm, bx.box, skin=0.3)["E"]
+            assert -(ep - em) / (2 * h) == pytest.approx(f[i, a], abs=2e-7 * max(1.0, abs(f[i, a])))
+
+
+# ---------------------------------------------------------------- functions
+
+def test_taper_and_pair_derivatives():
+    pot = O.Potential(I.RGL_CU)
+    r = np.linspace(2.0, 4.999, 301)
+    V, dV, rho, drho = pot.pair(r)
+    h = 1e-6
+    Vp, _, rp, _ = pot.pair(r + h)
+    Vm, _, rm, _ = pot.pair(r - h)
+    assert np.allclose(dV, (Vp - Vm) / (2 * h), rtol=1e-7, atol=1e-9)
+    assert np.allclose(drho, (rp - rm) / (2 * h), rtol=1e-7, atol=1e-9)
+    # taper: value and slope continuous at r_taper, zero at and beyond r_cut
+    lo = pot.pair(np.array([4.5 - 1e-9, 4.5 + 1e-9]))
+    assert abs(lo[0][0] - lo[0][1]) < 1e-9 and abs(lo[1][0] - lo[1][1]) < 1e-8
+    hi = pot.pair(np.array([5.0 - 1e-4, 5.0, 5.2]))
+    assert abs(hi[0][0]) < 1e-10 and abs(hi[1][0]) < 1e-6
+    assert (hi[0][1:] == 0).all() and (hi[1][1:] == 0).all() and (hi[2][1:] == 0).all()
+    F, Fp, Fpp = pot.embed(np.array([0.0, 4.0, 20.0]))
+    assert F[0] == 0 and Fp[0] == 0
+    assert F[1] == pytest.approx(-2.0) and Fp[1] == pytest.approx(-0.25) and Fpp[1] == pytest.approx(1 / 32)
+
+
+def test_natural_spline_matches_scipy():
+    interp = pytest.importorskip("scipy.interpolate")
+    rng = np.random.default_rng(3)
+    n = 23
+    spec = dict(kind="spline", phi=rng.normal(size=n), f=rng.normal(size=n), F=rng.normal(size=n),
+                r_lo=1.5, r_hi=5.0, rho_lo=0.0, rho_hi=40.0)
+    pot = O.Potential(spec)
+    t = np.linspace(1.5, 5.0, n)
+    cs = interp.CubicSpline(t, spec["phi"], bc_type="natural")
+    r = np.linspace(1.5, 4.999, 777)
+    V, dV, rho, drho = pot.pair(r)
+    assert np.allclose(V, cs(r), atol=1e-12) and np.allclose(dV, cs(r, 1), atol=1e-11)
+    cf = interp.CubicSpline(t, spec["f"], bc_type="natural")
+    assert np.allclose(rho, cf(r), atol=1e-12)
+    tF = np.linspace(0.0, 40.0, n)
+    cF = interp.CubicSpline(tF, spec["F"], bc_type="natural")
+    g = np.linspace(0.0, 40.0, 501)
+    F, Fp, Fpp = pot.embed(g)
+    assert np.allclose(F, cF(g), atol=1e-12) and np.allclose(Fp, cF(g, 1), atol=1e-11)
+    assert np.allclose(Fpp, cF(g, 2), atol=1e-10)
+    # linear extrapolation beyond the F range, zero beyond r_hi
+    Fo, Fpo, _ = pot.embed(np.array([45.0]))
+    assert Fo[0] == pytest.approx(cF(40.0) + 5.0 * cF(40.0, 1)) and Fpo[0] == pytest.approx(cF(40.0, 1))
+    assert pot.pair(np.array([5.0, 6.0]))[0].tolist() == [0.0, 0.0]
+
+
+# ---------------------------------------------------------------- dynamics
+
+def test_nve_energy_drift_bounded():
+    bx = I.perturbed_fcc(4, I.A_CU, 300.0, I.MASS_CU, seed=12345)
+    out = O.md_run(O.Potential(I.RGL_CU), bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 200)
+    et = out["thermo"][:, 2]
+    n = len(bx.x)
+    assert np.abs(et - et[0]).max() / n < 2e-5
+    slope = np.polyfit(np.arange(len(et)), et / n, 1)[0]
+    assert abs(slope) < 2e-8  # eV/atom per fs
+    assert out["n_rebuild"] >= 1
+    # the initial temperature is the fixture's exact 300 K
+    assert out["thermo"][0, 3] == pytest.approx(300.0, rel=1e-12)
+
+
+def test_time_reversibility():
+    bx = I.perturbed_fcc(4, I.A_CU, 600.0, I.MASS_CU, seed=4)
+    pot = O.Potential(I.RGL_CU)
+    fwd = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 50)
+    back = O.md_run(pot, fwd["x"], -fwd["v"], bx.box, I.MASS_CU, 1.0, 0.3, 50)
+    d = back["x"] - bx.x
+    d -= bx.box * np.round(d / bx.box)
+    assert np.abs(d).max() < 1e-9
+    assert np.abs(back["v"] + bx.v).max() < 1e-10
+
+
+def test_dimer_small_oscillation_period():
+    """A dimer near its bond length oscillates at omega = sqrt(k/mu), with
+    k = E''(r_eq) of the closed-form dimer energy and mu = m/2."""
+    pot = O.Potential(I.RGL_CU)
+    box = np.array([40.0, 40.0, 40.0])
+
+    def energy(r):
+        x = np.array([[10.0, 10.0, 10.0], [10.0 + r, 10.0, 10.0]])
+        return O.forces(pot, x, box, method="brute")["E"]
+
+    rs = np.linspace(2.0, 2.6, 6001)
+    req = rs[np.argmin([energy(r) for r in rs])]
+    h = 1e-4
+    k = (energy(req + h) - 2 * energy(req) + energy(req - h)) / h ** 2
+    mu = I.MASS_CU / 2 * I.MVV_EV
+    period = 2 * np.pi / np.sqrt(k / mu)
+    x0 = np.array([[10.0, 10.0, 10.0], [10.0 + req + 0.002, 10.0, 10.0]])
+    n_steps = int(3 * period)
+    out = O.md_run(pot, x0, np.zeros((2, 3)), box, I.MASS_CU, 0.5, 0.3, 2 * n_steps)
+    # sample the bond length by re-running step by step
+    xs = [x0]
+    x, v = x0, np.zeros((2, 3))
+    for _ in range(2 * n_steps):
+        o = O.md_run(pot, x, v, box, I.MASS_CU, 0.5, 0.3, 1)
+        x, v = o["x"], o["v"]
+        xs.append(x)
+    b = np.array([xx[1, 0] - xx[0, 0] for xx in xs]) - req
+    crossings = np.where(np.diff(np.sign(b)) != 0)[0]
+    measured = 2 * 0.5 * np.mean(np.diff(crossings))
+    assert measured == pytest.approx(period, rel=0.02)
+    assert out["thermo"][:, 2].std() < 1e-6
+
+
+# ---------------------------------------------------------------- gradients
+
+def loss_of(pot, configs, targets):
+    L = 0.0
+    for (x, box), (ft, et) in zip(configs, targets):
+        r = O.forces(pot, x, box)
+        n = len(x)
+        L += np.mean((r["f"] - ft) ** 2) + 0.1 * (r["E"] / n - et / n) ** 2
+    return L / len(configs)
+
+
+def test_rgl_param_derivatives_match_finite_differences():
+    bx = I.strained_fcc(3, I.A_CU, seed=8)
+    pot = O.Potential(I.RGL_CU)
+    for k, name in enumerate(O.RGL_ORDER):
+        dE, dF = O.param_deriv(pot, k, bx.x, bx.box)
+        h = 1e-6 * abs(I.RGL_CU[name])
+        rp = O.forces(O.Potential(dict(I.RGL_CU, **{name: I.RGL_CU[name] + h})), bx.x, bx.box)
+        rm = O.forces(O.Potential(dict(I.RGL_CU, **{name: I.RGL_CU[name] - h})), bx.x, bx.box)
+        assert dE == pytest.approx((rp["E"] - rm["E"]) / (2 * h), rel=1e-6)
+        fd = (rp["f"] - rm["f"]) / (2 * h)
+        assert np.abs(dF - fd).max() <= 1e-6 * np.abs(fd).max()
+
+
+def test_loss_gradient_matches_finite_differences():
+    """d/dtheta of the force-matching loss, RGL and spline models."""
+    configs = [(b.x, b.box) for b in (I.strained_fcc(3, I.A_CU, seed=s) for s in (1, 2))]
+    ref = O.Potential(I.RGL_CU)
+    targets = [(O.forces(ref, x, box)["f"], O.forces(ref, x, box)["E"]) for x, box in configs]
+    model = dict(I.RGL_CU, A=0.0855 * 1.05, xi=1.224 * 0.95, p=10.96 * 1.05, q=2.278 * 0.95, r0=2.5562 * 1.05)
+    pot = O.Potential(model)
+    grad = np.zeros(5)
+    for (x, box), (ft, et) in zip(configs, targets):
+        r = O.forces(pot, x, box)
+        n = len(x)
+        gF = 2 * (r["f"] - ft) / (3 * n) / len(configs)
+        gE = 0.2 * (r["E"] / n - et / n) / n / len(configs)
+        O.param_grad(pot, x, box, gF, gE, grad)
+    for k, name in enumerate(O.RGL_ORDER):
+        h = 1e-6 * abs(model[name])
+        lp = loss_of(O.Potential(dict(model, **{name: model[name] + h})), configs, targets)
+        lm = loss_of(O.Potential(dict(model, **{name: model[name] - h})), configs, targets)
+        assert grad[k] == pytest.approx((lp - lm) / (2 * h), rel=1e-6)
+    # spline model tabulated from the perturbed RGL, gradient on a few knots
+    sp = O.tabulate_spline(model, n_knots=40, rho_hi=2 * 20.620605425592796)
+    spot = O.Potential(sp)
+    grad = np.zeros(spot.n_param)
+    for (x, box), (ft, et) in zip(configs, targets):
+        r = O.forces(spot, x, box)
+        n = len(x)
+        gF = 2 * (r["f"] - ft) / (3 * n) / len(configs)
+        gE = 0.2 * (r["E"] / n - et / n) / n / len(configs)
+        O.param_grad(spot, x, box, gF, gE, grad)
+    keys = [("phi", 8), ("phi", 20), ("f", 15), ("f", 30), ("F", 19), ("F", 21)]
+    offs = {"phi": 0, "f": 40, "F": 80}
+    for key, idx in keys:
+        h = 1e-6 * max(abs(sp[key][idx]), 1e-3)
+        up, dn = dict(sp), dict(sp)
+        up[key] = sp[key].copy()
+        dn[key] = sp[key].copy()
+        up[key][idx] += h
+        dn[key][idx] -= h
+        fd = (loss_of(O.Potential(up), configs, targets) - loss_of(O.Potential(dn), configs, targets)) / (2 * h)
+        g = grad[offs[key] + idx]
+        assert g == pytest.approx(fd, rel=1e-5, abs=1e-9 * max(1.0, abs(grad).max()))
