@@ -1,0 +1,256 @@
+/*
+ * md.h -- C ABI of the GB300 many-body molecular-dynamics library (libmd.so).
+ *
+ * The library evaluates the per-step hot path of molecular dynamics with
+ * embedded-atom / second-moment tight-binding potentials as described by
+ * Hou et al., "Molecular dynamics simulations with many-body potentials on
+ * multiple GPUs" (arXiv:1212.6332):
+ *   - cell binning and a Verlet neighbour list            (Sec. 3.2, Fig. 3)
+ *   - the density pass rho_i = sum_j rho(r_ij)            (Sec. 3.3, Fig. 5)
+ *   - the embedding derivative F'(rho_i)                  (Eq. 3)
+ *   - the force pass of Eq. (3)                           (Sec. 3.3, Fig. 6)
+ *   - time integration (velocity Verlet here; the paper uses a
+ *     predictor-corrector, Sec. 3.3)
+ *   - many independent boxes in one run                   (Sec. 4.4)
+ * plus parameter gradients of a force-matching loss (no counterpart in the
+ * paper).
+ *
+ * Conventions for every entry point:
+ *   - Units: Angstrom, eV, fs, atomic mass unit (u), kelvin.
+ *   - Atom arrays are in the caller's atom order, row-major [n_atoms][3]
+ *     float64 for 3-vectors. Internally atoms are re-sorted by cell; the
+ *     library maps back on every input and output.
+ *   - Pointer arguments marked "host or device" may point to host memory
+ *     (pageable or pinned) or to device memory of the current device; the
+ *     library copies with cudaMemcpyAsync(cudaMemcpyDefault). Pointers
+ *     marked "device" must be device memory. The caller owns every pointer
+ *     it passes; the library owns its handles and internal buffers and
+ *     frees them in md_destroy / md_batch_destroy.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream). Outputs written to device memory are valid once
+ *     the stream reaches that point; outputs written to host memory are
+ *     valid when the call returns (the call synchronizes the stream).
+ *   - Every call returns an md_status. Argument errors are detected on the
+ *     host before any work is enqueued. Device-side conditions (neighbour
+ *     overflow beyond the regrow cap, non-finite energies) are recorded in
+ *     a device status word and returned by the next call that synchronizes.
+ *     md_last_error() gives a text for the last failure on a handle;
+ *     md_status_string() names a code. No C++ exception crosses the ABI.
+ *   - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MD_API __attribute__((visibility("default")))
+#else
+#define MD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* md_stream; /* identical to cudaStream_t */
+typedef struct md_batch md_batch;
+typedef md_batch md_ctx; /* a single box is a batch of one box */
+
+enum md_status {
+    MD_OK = 0,
+    MD_ERR_ARG = 1,            /* invalid argument (nothing enqueued) */
+    MD_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    MD_ERR_NOMEM = 3,          /* device allocation failed */
+    MD_ERR_NEIGH_OVERFLOW = 4, /* neighbour list exceeded the regrow cap */
+    MD_ERR_NONFINITE = 5,      /* a non-finite energy or force appeared */
+    MD_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+    MD_ERR_UNSUPPORTED = 7     /* valid but not supported combination */
+};
+
+enum md_precision {
+    MD_FP64 = 0,  /* all arithmetic in float64 */
+    MD_MIXED = 1  /* float32 pair math relative to cell-local origins;
+                     compensated sums; float64 positions, velocities and
+                     integration */
+};
+
+enum md_pot_kind {
+    MD_POT_RGL = 0,   /* second-moment tight binding (Cleri-Rosato):
+                         V = 2A exp(-p(r/r0-1)) S(r),
+                         rho = xi^2 exp(-2q(r/r0-1)) S(r), F = -sqrt(rho);
+                         p[] = {A, xi, p, q, r0} */
+    MD_POT_SC = 1,    /* Sutton-Chen: V = eps (a/r)^n S(r),
+                         rho = (a/r)^m S(r), F = -c eps sqrt(rho);
+                         p[] = {eps, c, a, n, m} */
+    MD_POT_SPLINE = 2 /* V, rho natural cubic splines of knot values on a
+                         uniform grid over [r_lo, r_hi] (zero for
+                         r >= r_hi, linear below r_lo); F a natural cubic
+                         spline over [rho_lo, rho_hi], linear outside */
+};
+
+/* Potential of Eq. (1): pair term V, density function rho, embedding F.
+ * S(r) is the C2 taper 1 - 10x^3 + 15x^4 - 6x^5, x = (r - r_taper) /
+ * (r_cut - r_taper), S = 1 below r_taper and 0 from r_cut on; r_taper >=
+ * r_cut gives a hard cut. F(rho) = F'(rho) = 0 for rho <= 0 (RGL, SC). */
+typedef struct md_potential {
+    int kind;              /* enum md_pot_kind */
+    double p[8];           /* parameters, see enum md_pot_kind */
+    double r_taper, r_cut; /* taper interval (RGL, SC); spline: ignored, r_cut = r_hi */
+    const double* knots;   /* spline only: host array of n_phi + n_f + n_F
+                              knot values, V knots then rho knots then F knots */
+    int n_phi, n_f, n_F;   /* spline knot counts, each >= 4 */
+    double r_lo, r_hi;     /* spline V and rho range */
+    double rho_lo, rho_hi; /* spline F range */
+} md_potential;
+
+/* Run configuration. box[] is used by md_create only (md_batch_create takes
+ * one box per batch member). The neighbour list radius is r_cut + skin; it
+ * is rebuilt when some atom has moved more than skin/2 since the last build
+ * (Sec. 4.2 uses a list radius beyond the force cutoff). The cells of a box
+ * are the largest count per axis with side >= r_cut + skin; every box
+ * needs r_cut + skin < L/2 on each axis (minimum image). */
+typedef struct md_config {
+    double box[3];     /* orthorhombic periodic box lengths, A */
+    double skin;       /* neighbour-list skin, A (>= 0) */
+    double dt;         /* time step, fs */
+    double mass;       /* atomic mass, u (one species) */
+    int precision;     /* enum md_precision */
+    int max_neighbors; /* initial list capacity per atom; 0 = automatic */
+} md_config;
+
+/* Thermodynamic state after the last completed step (or set_state). */
+typedef struct md_thermo {
+    double ke;          /* kinetic energy, eV: 1/2 sum m v^2 */
+    double pe;          /* potential energy E_T of Eq. (2), eV */
+    double etot;        /* ke + pe */
+    double temperature; /* 2 ke / ((3N - 3) k_B), K; summed over all boxes */
+    double max_disp;    /* largest displacement since the last list build, A */
+    int64_t n_rebuild;  /* list builds since set_state (excluding its own) */
+    int64_t step;       /* steps taken since set_state */
+} md_thermo;
+
+/* ---------------------------------------------------------------- single box */
+
+/* Creates a single-box context for n_atoms atoms. Allocates every device
+ * buffer (positions, velocities, forces, cells, neighbour list). No state
+ * is set: call md_set_state or md_compute_forces next. *out receives the
+ * handle. Errors: MD_ERR_ARG (bad config or potential, box too small for
+ * the list radius), MD_ERR_NOMEM, MD_ERR_CUDA. */
+MD_API int md_create(const md_config* cfg, const md_potential* pot, int64_t n_atoms, md_ctx** out);
+
+/* Frees the handle and all its device memory (synchronizes its streams). */
+MD_API int md_destroy(md_ctx* ctx);
+
+/* Sets positions x [n][3] and velocities v [n][3] (host or device; v may be
+ * NULL for zero velocities). Positions are wrapped into the box, atoms are
+ * binned and sorted, the neighbour list is built and forces are evaluated,
+ * so that md_step can start. Resets the step and rebuild counters. */
+MD_API int md_set_state(md_ctx* ctx, const double* x, const double* v, md_stream stream);
+
+/* Copies the current positions and/or velocities (either may be NULL) to
+ * x, v [n][3] (host or device), caller order. */
+MD_API int md_get_state(md_ctx* ctx, double* x, double* v, md_stream stream);
+
+/* Rebuilds cells and the neighbour list from the current positions
+ * (Sec. 3.2): counting sort of atoms into Morton-ordered cells, then the
+ * full list (both i->j and j->i) of pairs with minimum-image
+ * r^2 < (r_cut + skin)^2, r^2 = dx*dx + dy*dy + dz*dz evaluated left to
+ * right in float64 without fused multiply-add. Grows the list capacity and
+ * retries on overflow (up to 4 times; then MD_ERR_NEIGH_OVERFLOW). */
+MD_API int md_build_neighbors(md_ctx* ctx, md_stream stream);
+
+/* Copies the current neighbour list in caller ids: nn [n] (device) gets
+ * each atom's count, nl [n][ld] (device) its neighbours (unordered; slots
+ * beyond the count are left untouched). MD_ERR_ARG if ld is smaller than
+ * the largest count (query it with md_max_count). */
+MD_API int md_get_neighbors(md_ctx* ctx, int32_t* nn, int32_t* nl, int32_t ld, md_stream stream);
+
+/* Largest neighbour count of the current list (synchronizes). */
+MD_API int md_max_count(md_ctx* ctx, int32_t* out);
+
+/* Sets positions x [n][3] (host or device; velocities are kept), rebuilds
+ * cells and list, runs the density pass (Fig. 5) and force pass (Fig. 6),
+ * and writes forces f [n][3] (eV/A), per-atom energies e_atom [n]
+ * (E_i of Eq. 1), densities rho [n] and the total energy e_total [1] (E_T
+ * of Eq. 2). Every output is optional (NULL) and may be host or device. */
+MD_API int md_compute_forces(md_ctx* ctx, const double* x, double* f, double* e_atom, double* rho, double* e_total,
+                      md_stream stream);
+
+/* Copies forces, per-atom energies and densities of the current state
+ * (each optional; host or device). */
+MD_API int md_get_forces(md_ctx* ctx, double* f, double* e_atom, double* rho, md_stream stream);
+
+/* Advances n_steps velocity-Verlet steps of dt:
+ *   v += dt/2 F/m; x += dt v; wrap; rebuild the list if some atom moved
+ *   more than skin/2 since the last build; density pass; force pass;
+ *   v += dt/2 F/m.
+ * The rebuild decision is taken on the device (no host synchronization
+ * per step). thermo_hist (optional, host or device) receives n_steps rows
+ * of (ke, pe, etot, temperature); out (optional, host) the final state's
+ * md_thermo. use_graph != 0 replays the steps from a captured CUDA graph
+ * (faster for small systems; same results). */
+MD_API int md_step(md_ctx* ctx, int n_steps, md_thermo* out, double* thermo_hist, int use_graph, md_stream stream);
+
+/* The current md_thermo (host). Synchronizes the stream. */
+MD_API int md_get_thermo(md_ctx* ctx, md_thermo* out, md_stream stream);
+
+/* ---------------------------------------------------------------- batches */
+
+/* Creates a batch of n_boxes independent periodic boxes (Sec. 4.4: the
+ * cells of box I are numbered after those of boxes 0..I-1 and only cells
+ * of the same box neighbour each other). atom_offsets [n_boxes + 1] (host)
+ * are prefix sums of the per-box atom counts; box_lengths [n_boxes][3]
+ * (host). cfg->box is ignored. */
+MD_API int md_batch_create(const md_config* cfg, const md_potential* pot, int n_boxes, const int64_t* atom_offsets,
+                    const double* box_lengths, md_batch** out);
+
+MD_API int md_batch_destroy(md_batch* b);
+
+/* As md_set_state, md_get_state and md_compute_forces, over all boxes back
+ * to back. e_box [n_boxes] (optional, host or device) gets each box's E_T. */
+MD_API int md_batch_set_state(md_batch* b, const double* x, const double* v, md_stream stream);
+MD_API int md_batch_get_state(md_batch* b, double* x, double* v, md_stream stream);
+MD_API int md_batch_compute_forces(md_batch* b, const double* x, double* f, double* e_box, md_stream stream);
+
+/* Schedules for md_batch_step. */
+enum md_schedule {
+    MD_SCHED_AUTO = 0, /* pick by the autotuner's cached choice, or time both once */
+    MD_SCHED_BOX = 1,  /* one persistent thread block owns a whole box for all
+                          n_steps, positions held in shared memory */
+    MD_SCHED_TILE = 2  /* one launch per phase over the atoms of all boxes */
+};
+
+/* Advances every box by n_steps velocity-Verlet steps (as md_step).
+ * thermo_box [n_boxes][4] (optional, host or device) gets each box's final
+ * (ke, pe, etot, temperature). */
+MD_API int md_batch_step(md_batch* b, int n_steps, int schedule, int use_graph, double* thermo_box, md_stream stream);
+
+/* Replaces the potential's parameters (same kind and knot counts). */
+MD_API int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream stream);
+
+/* Gradient of a scalar loss L with respect to the potential parameters
+ * (RGL: A, xi, p, q, r0; spline: all knot values, V then rho then F), at
+ * the batch's current positions, given g_f = dL/dF [n][3] (device, caller
+ * order) and g_e = dL/dE_T per box [n_boxes] (device):
+ *   grad = sum_i g_f_i . dF_i/dtheta + sum_b g_e_b dE_b/dtheta.
+ * The adjoint recomputes rho_i and F'(rho_i) instead of storing per-pair
+ * terms. grad [n_param] (device) is overwritten. No counterpart in the
+ * paper. MD_ERR_UNSUPPORTED for Sutton-Chen. */
+MD_API int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* grad, md_stream stream);
+
+/* Number of potential parameters (5 for RGL/SC, n_phi + n_f + n_F for a spline). */
+MD_API int md_num_params(const md_batch* b);
+
+/* ---------------------------------------------------------------- errors */
+
+MD_API const char* md_status_string(int status);
+/* Text of the last failure on the handle (or of the last failed create
+ * when h is NULL). Valid until the next call on the handle. */
+MD_API const char* md_last_error(const md_batch* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_H */

@@ -1,0 +1,82 @@
+"""Builds libmd.so (the CUDA library behind include/md.h) in-tree.
+
+Every translation unit under csrc/ is compiled by nvcc for sm_103a only, in
+parallel, then linked into paper_1212_6332_gb300/_lib/libmd.so. No CUDA
+compiler flag changes float64 arithmetic beyond the default contraction of
+multiply-add pairs, which the neighbour-list distance test avoids with
+explicit round-to-nearest intrinsics.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import os
+import pathlib
+import shutil
+import subprocess
+
+PKG = pathlib.Path(__file__).resolve().parent
+ROOT = PKG.parent
+CSRC = PKG / "csrc"
+LIBDIR = PKG / "_lib"
+SO = LIBDIR / "libmd.so"
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "-I", str(ROOT / "include"), "-I", str(CSRC)]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmd.so")
+
+
+def _digest() -> str:
+    h = hashlib.sha256()
+    for p in sorted(list(CSRC.glob("*.cu")) + list(CSRC.glob("*.cuh")) + [ROOT / "include" / "md.h", PKG / "build.py"]):
+        h.update(p.name.encode())
+        h.update(p.read_bytes())
+    return h.hexdigest()
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> pathlib.Path:
+    """Compiles and links libmd.so unless an up-to-date one exists."""
+    LIBDIR.mkdir(exist_ok=True)
+    stamp = LIBDIR / "libmd.sha256"
+    dig = _digest()
+    if not force and SO.exists() and stamp.exists() and stamp.read_text() == dig:
+        return SO
+    nvcc = _nvcc()
+    objdir = LIBDIR / "obj"
+    objdir.mkdir(exist_ok=True)
+    srcs = sorted(CSRC.glob("*.cu"))
+    extra = ["-Xptxas", "-v"] if ptxas_info else []
+
+    def compile_one(src: pathlib.Path) -> tuple[pathlib.Path, str]:
+        obj = objdir / (src.stem + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", str(src), "-o", str(obj)]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src.name}:\n{r.stderr}")
+        return obj, r.stderr
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+        results = list(ex.map(compile_one, srcs))
+    if verbose or ptxas_info:
+        for _, log in results:
+            if log:
+                print(log)
+    tmp = SO.with_suffix(f".{os.getpid()}.tmp")
+    cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *[str(o) for o, _ in results]]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, SO)
+    stamp.write_text(dig)
+    return SO
+
+
+if __name__ == "__main__":
+    import sys
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))

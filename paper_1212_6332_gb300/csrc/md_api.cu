@@ -1,0 +1,961 @@
+// Host side of the C ABI declared in md.h: argument checks, device buffers,
+// Morton-ordered cell tables, state transfer in caller order, the step loop
+// with a device-side rebuild decision, neighbour-overflow recovery and CUDA
+// graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "md_engine.cuh"
+
+using namespace mdk;
+
+struct md_batch {
+    Engine e;
+    cudaStream_t cap_stream = nullptr;
+};
+
+static thread_local std::string g_err;
+
+namespace mdk {
+
+Geo make_geo(const Engine& e) {
+    Geo g{};
+    g.B = e.B;
+    g.L = e.L;
+    g.cell_len = e.cell_len;
+    g.cell_len_f = e.cell_len_f;
+    g.nc = e.nc;
+    g.cell_off = e.cell_off;
+    g.atom_off = e.atom_off;
+    g.atom_box = e.atom_box;
+    g.cell_box = e.cell_box;
+    g.cell_rank = e.cell_rank;
+    g.cell_xyz = e.cell_xyz;
+    for (int a = 0; a < 3; ++a) g.L0[a] = e.L_h.size() >= 3 ? e.L_h[a] : 0.0;
+    return g;
+}
+
+}  // namespace mdk
+
+namespace {
+
+int fail(Engine* e, int code, const std::string& msg) {
+    if (e)
+        e->err = msg;
+    else
+        g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t ck_ = (call);                                                              \
+        if (ck_ != cudaSuccess) return fail(E, MD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(ck_)); \
+    } while (0)
+
+bool finite(double v) { return std::isfinite(v); }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int dalloc(Engine* E, T** p, size_t count) {
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(E, MD_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    return MD_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+int check_potential(const md_potential* p, std::string& why) {
+    if (!p) return why = "potential is NULL", MD_ERR_ARG;
+    if (p->kind == MD_POT_RGL || p->kind == MD_POT_SC) {
+        for (int k = 0; k < 5; ++k)
+            if (!finite(p->p[k])) return why = "non-finite potential parameter", MD_ERR_ARG;
+        if (!(p->r_cut > 0.0) || !finite(p->r_cut) || !finite(p->r_taper))
+            return why = "r_cut must be positive and finite", MD_ERR_ARG;
+        if (p->kind == MD_POT_RGL && !(p->p[4] > 0.0)) return why = "RGL r0 must be positive", MD_ERR_ARG;
+        if (p->kind == MD_POT_SC && !(p->p[2] > 0.0)) return why = "Sutton-Chen a must be positive", MD_ERR_ARG;
+        return MD_OK;
+    }
+    if (p->kind == MD_POT_SPLINE) {
+        if (!p->knots) return why = "spline knots are NULL", MD_ERR_ARG;
+        if (p->n_phi < 4 || p->n_f < 4 || p->n_F < 4) return why = "each spline needs >= 4 knots", MD_ERR_ARG;
+        if (!(p->r_hi > p->r_lo) || !(p->r_lo > 0.0) || !finite(p->r_hi))
+            return why = "spline needs 0 < r_lo < r_hi", MD_ERR_ARG;
+        if (!(p->rho_hi > p->rho_lo) || !finite(p->rho_lo) || !finite(p->rho_hi))
+            return why = "spline needs rho_lo < rho_hi", MD_ERR_ARG;
+        return MD_OK;
+    }
+    return why = "unknown potential kind " + std::to_string(p->kind), MD_ERR_ARG;
+}
+
+double pot_cutoff(const md_potential* p) { return p->kind == MD_POT_SPLINE ? p->r_hi : p->r_cut; }
+
+void fill_pot(Engine& e) {
+    const md_potential& p = e.pot_host;
+    Pot P{};
+    P.kind = p.kind;
+    if (p.kind == MD_POT_SPLINE) {
+        P.rc = p.r_hi;
+        P.rs = p.r_hi;
+        P.inv_w = 0.0;
+        int ns[3] = {p.n_phi, p.n_f, p.n_F};
+        double lo[3] = {p.r_lo, p.r_lo, p.rho_lo}, hi[3] = {p.r_hi, p.r_hi, p.rho_hi};
+        int off = 0;
+        for (int w = 0; w < 3; ++w) {
+            P.sp[w] = e.spline_coef + off;
+            P.sn[w] = ns[w];
+            P.st0[w] = lo[w];
+            P.sh[w] = (hi[w] - lo[w]) / (ns[w] - 1);
+            P.sinvh[w] = 1.0 / P.sh[w];
+            off += ns[w];
+        }
+    } else {
+        P.rc = p.r_cut;
+        if (p.r_taper < p.r_cut) {
+            P.rs = p.r_taper;
+            P.inv_w = 1.0 / (p.r_cut - p.r_taper);
+        } else {
+            P.rs = p.r_cut;
+            P.inv_w = 0.0;
+        }
+    }
+    P.rc2 = P.rc * P.rc;
+    P.F_scale = 1.0;
+    if (p.kind == MD_POT_RGL) {
+        double A = p.p[0], xi = p.p[1], pp = p.p[2], q = p.p[3], r0 = p.p[4];
+        P.A2 = 2.0 * A;
+        P.xi2 = xi * xi;
+        P.p = pp;
+        P.p_r0 = pp / r0;
+        P.q2 = 2.0 * q;
+        P.q2_r0 = 2.0 * q / r0;
+    } else if (p.kind == MD_POT_SC) {
+        P.eps = p.p[0];
+        P.a = p.p[2];
+        P.n = p.p[3];
+        P.m = p.p[4];
+        P.F_scale = p.p[1] * p.p[0];
+    }
+    P.f_rc2 = (float)P.rc2;
+    P.f_rs = (float)P.rs;
+    P.f_inv_w = (float)P.inv_w;
+    P.f_A2 = (float)P.A2;
+    P.f_xi2 = (float)P.xi2;
+    P.f_p = (float)P.p;
+    P.f_p_r0 = (float)P.p_r0;
+    P.f_q2 = (float)P.q2;
+    P.f_q2_r0 = (float)P.q2_r0;
+    P.f_eps = (float)P.eps;
+    P.f_a = (float)P.a;
+    P.f_n = (float)P.n;
+    P.f_m = (float)P.m;
+    e.pot = P;
+}
+
+uint64_t spread3(uint64_t v) {
+    uint64_t r = 0;
+    for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+    return r;
+}
+
+void destroy_graphs(Engine& e) {
+    if (e.graph_step) cudaGraphExecDestroy(e.graph_step);
+    if (e.graph_chunk) cudaGraphExecDestroy(e.graph_chunk);
+    e.graph_step = e.graph_chunk = nullptr;
+}
+
+void free_engine(Engine& e) {
+    destroy_graphs(e);
+    dfree(e.L); dfree(e.cell_len); dfree(e.cell_len_f); dfree(e.nc); dfree(e.cell_off); dfree(e.atom_off);
+    dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.spline_coef);
+    dfree(e.spline_work); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
+    dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
+    dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
+    dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
+    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.stage); dfree(e.red);
+    dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl);
+    if (e.ctl_host) cudaFreeHost(e.ctl_host);
+    e.ctl_host = nullptr;
+}
+
+int upload_potential(md_batch* h, cudaStream_t s) {
+    Engine* E = &h->e;
+    Engine& e = *E;
+    fill_pot(e);
+    if (e.pot_host.kind == MD_POT_SPLINE) {
+        size_t nk = (size_t)e.pot_host.n_phi + e.pot_host.n_f + e.pot_host.n_F;
+        CK(cudaMemcpyAsync(e.knots_dev, e.knots_host.data(), nk * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_spline_setup(e, s);
+        CK(cudaGetLastError());
+    }
+    return MD_OK;
+}
+
+int create_impl(const md_config* cfg, const md_potential* pot, int B, const int64_t* atom_off, const double* box,
+                md_batch** out) {
+    Engine* E = nullptr;
+    if (!out) return fail(nullptr, MD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, MD_ERR_ARG, "config is NULL");
+    std::string why;
+    if (check_potential(pot, why) != MD_OK) return fail(nullptr, MD_ERR_ARG, why);
+    if (!(cfg->skin >= 0.0) || !finite(cfg->skin)) return fail(nullptr, MD_ERR_ARG, "skin must be >= 0");
+    if (!(cfg->dt >= 0.0) || !finite(cfg->dt)) return fail(nullptr, MD_ERR_ARG, "dt must be >= 0");
+    if (!(cfg->mass > 0.0) || !finite(cfg->mass)) return fail(nullptr, MD_ERR_ARG, "mass must be > 0");
+    if (cfg->precision != MD_FP64 && cfg->precision != MD_MIXED)
+        return fail(nullptr, MD_ERR_ARG, "unknown precision");
+    if (cfg->max_neighbors < 0) return fail(nullptr, MD_ERR_ARG, "max_neighbors must be >= 0");
+    if (B < 1) return fail(nullptr, MD_ERR_ARG, "need at least one box");
+    if (!atom_off || atom_off[0] != 0) return fail(nullptr, MD_ERR_ARG, "atom_offsets[0] must be 0");
+    for (int b = 0; b < B; ++b)
+        if (atom_off[b + 1] < atom_off[b]) return fail(nullptr, MD_ERR_ARG, "atom_offsets must not decrease");
+    if (atom_off[B] > (int64_t)INT32_MAX - 64) return fail(nullptr, MD_ERR_ARG, "too many atoms");
+    double rl = pot_cutoff(pot) + cfg->skin;
+    for (int b = 0; b < 3 * B; ++b) {
+        if (!(box[b] > 0.0) || !finite(box[b])) return fail(nullptr, MD_ERR_ARG, "box lengths must be > 0");
+        if (!(rl < 0.5 * box[b]))
+            return fail(nullptr, MD_ERR_ARG,
+                        "r_cut + skin must be below half of every box length (minimum image)");
+    }
+
+    md_batch* h = new (std::nothrow) md_batch();
+    if (!h) return fail(nullptr, MD_ERR_NOMEM, "host allocation failed");
+    E = &h->e;
+    Engine& e = *E;
+    e.cfg = *cfg;
+    e.pot_host = *pot;
+    if (pot->kind == MD_POT_SPLINE) {
+        size_t nk = (size_t)pot->n_phi + pot->n_f + pot->n_F;
+        e.knots_host.assign(pot->knots, pot->knots + nk);
+        e.pot_host.knots = nullptr;
+    }
+    e.B = B;
+    e.N = atom_off[B];
+    e.N_pad = std::max<int64_t>(32, (e.N + 31) / 32 * 32);
+    e.rl = rl;
+    e.atom_off_h.assign(atom_off, atom_off + B + 1);
+    e.L_h.assign(box, box + 3 * B);
+
+    // cells: largest count per axis with side >= rl, Morton order inside a box
+    e.nc_h.resize(3 * B);
+    e.cell_off_h.assign(B + 1, 0);
+    std::vector<double> cl(3 * B);
+    std::vector<float> clf(3 * B);
+    int64_t tot = 0;
+    for (int b = 0; b < B; ++b) {
+        int64_t nb = 1;
+        for (int a = 0; a < 3; ++a) {
+            int n = (int)std::floor(box[3 * b + a] / (rl * (1.0 + 1e-12)));
+            n = std::max(1, std::min(n, 1023));
+            e.nc_h[3 * b + a] = n;
+            cl[3 * b + a] = box[3 * b + a] / n;
+            clf[3 * b + a] = (float)cl[3 * b + a];
+            nb *= n;
+        }
+        tot += nb;
+        if (tot > (int64_t)INT32_MAX / 2) {
+            delete h;
+            return fail(nullptr, MD_ERR_ARG, "too many cells");
+        }
+        e.cell_off_h[b + 1] = (int)tot;
+    }
+    e.n_cells = (int)tot;
+    std::vector<int> rank(tot), xyz(tot), cbox(tot);
+    for (int b = 0; b < B; ++b) {
+        int nx = e.nc_h[3 * b], ny = e.nc_h[3 * b + 1], nz = e.nc_h[3 * b + 2];
+        int off = e.cell_off_h[b];
+        int n = nx * ny * nz;
+        std::vector<std::pair<uint64_t, int>> key(n);
+        for (int cx = 0; cx < nx; ++cx)
+            for (int cy = 0; cy < ny; ++cy)
+                for (int cz = 0; cz < nz; ++cz) {
+                    int lin = (cx * ny + cy) * nz + cz;
+                    key[lin] = {spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2), lin};
+                }
+        std::sort(key.begin(), key.end());
+        for (int r = 0; r < n; ++r) {
+            int lin = key[r].second;
+            int cz = lin % nz, cy = (lin / nz) % ny, cx = lin / (ny * nz);
+            rank[off + lin] = off + r;
+            xyz[off + r] = cx | (cy << 10) | (cz << 20);
+            cbox[off + r] = b;
+        }
+    }
+    std::vector<int> abox(e.N);
+    std::vector<int64_t> clo, chi;
+    std::vector<int> bco(B + 1, 0);
+    int64_t max_box = 0;
+    double max_dens = 0.0;
+    const int64_t CH = 4096;
+    for (int b = 0; b < B; ++b) {
+        int64_t a0 = atom_off[b], a1 = atom_off[b + 1];
+        for (int64_t i = a0; i < a1; ++i) abox[i] = b;
+        for (int64_t lo = a0; lo < a1; lo += CH) {
+            clo.push_back(lo);
+            chi.push_back(std::min(a1, lo + CH));
+        }
+        bco[b + 1] = (int)clo.size();
+        max_box = std::max(max_box, a1 - a0);
+        double vol = box[3 * b] * box[3 * b + 1] * box[3 * b + 2];
+        max_dens = std::max(max_dens, (a1 - a0) / vol);
+    }
+    e.n_chunks = (int)clo.size();
+    if (cfg->max_neighbors > 0) {
+        e.max_nb = cfg->max_neighbors;
+    } else {
+        double est = max_dens * 4.0 / 3.0 * M_PI * rl * rl * rl;
+        int m = (int)std::ceil(1.4 * est + 24.0);
+        m = (m + 7) / 8 * 8;
+        e.max_nb = (int)std::max<int64_t>(8, std::min<int64_t>(m, std::max<int64_t>(max_box - 1, 1)));
+    }
+
+    int rc = MD_OK;
+    size_t Np = (size_t)e.N_pad;
+    size_t nk = (size_t)pot->n_phi + pot->n_f + pot->n_F;
+#define AL(p, n) \
+    if ((rc = dalloc(E, &(p), (n))) != MD_OK) goto fail_alloc;
+    AL(e.L, 3 * B);
+    AL(e.cell_len, 3 * B);
+    AL(e.cell_len_f, 3 * B);
+    AL(e.nc, 3 * B);
+    AL(e.cell_off, B + 1);
+    AL(e.atom_off, B + 1);
+    AL(e.atom_box, e.N);
+    AL(e.cell_box, tot);
+    AL(e.cell_rank, tot);
+    AL(e.cell_xyz, tot);
+    if (pot->kind == MD_POT_SPLINE) {
+        AL(e.spline_coef, nk);
+        AL(e.spline_work, 3 * nk);
+        AL(e.knots_dev, nk);
+    }
+    AL(e.chunk_lo, e.n_chunks);
+    AL(e.chunk_hi, e.n_chunks);
+    AL(e.box_chunk_off, B + 1);
+    AL(e.x, Np);
+    AL(e.x_alt, Np);
+    AL(e.xb, Np);
+    AL(e.v, 3 * Np);
+    AL(e.v_alt, 3 * Np);
+    AL(e.f, 3 * Np);
+    AL(e.rho, Np);
+    AL(e.Fp, Np);
+    AL(e.Fpf, Np);
+    AL(e.e_atom, Np);
+    if (cfg->precision == MD_MIXED) AL(e.xo, Np);
+    AL(e.perm, Np);
+    AL(e.perm_alt, Np);
+    AL(e.iperm, Np);
+    AL(e.cell_of, Np);
+    AL(e.cell_t, Np);
+    AL(e.cell_t_alt, Np);
+    AL(e.src, Np);
+    AL(e.cell_count, tot);
+    AL(e.cell_start, tot + 1);
+    AL(e.scan_tmp, tot / 1024 + 2);
+    AL(e.nn, Np);
+    AL(e.nl, (size_t)e.max_nb * Np);
+    AL(e.stage, 3 * std::max<size_t>(e.N, 1));
+    AL(e.red, 2 * std::max(e.n_chunks, 1));
+    AL(e.thermo_dev, 4 * (B + 1));
+    AL(e.ctl, 1);
+#undef AL
+    if (cudaMallocHost((void**)&e.ctl_host, sizeof(Ctl)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(E, MD_ERR_NOMEM, "cudaMallocHost failed");
+        goto fail_alloc;
+    }
+    {
+        cudaStream_t s = nullptr;
+        auto up = [&](void* d, const void* hsrc, size_t bytes) {
+            return cudaMemcpy(d, hsrc, bytes, cudaMemcpyHostToDevice);
+        };
+        cudaError_t ce = cudaSuccess;
+        ce = ce != cudaSuccess ? ce : up(e.L, box, 3 * B * sizeof(double));
+        ce = ce != cudaSuccess ? ce : up(e.cell_len, cl.data(), 3 * B * sizeof(double));
+        ce = ce != cudaSuccess ? ce : up(e.cell_len_f, clf.data(), 3 * B * sizeof(float));
+        ce = ce != cudaSuccess ? ce : up(e.nc, e.nc_h.data(), 3 * B * sizeof(int));
+        ce = ce != cudaSuccess ? ce : up(e.cell_off, e.cell_off_h.data(), (B + 1) * sizeof(int));
+        ce = ce != cudaSuccess ? ce : up(e.atom_off, atom_off, (B + 1) * sizeof(int64_t));
+        if (e.N) ce = ce != cudaSuccess ? ce : up(e.atom_box, abox.data(), e.N * sizeof(int));
+        ce = ce != cudaSuccess ? ce : up(e.cell_box, cbox.data(), tot * sizeof(int));
+        ce = ce != cudaSuccess ? ce : up(e.cell_rank, rank.data(), tot * sizeof(int));
+        ce = ce != cudaSuccess ? ce : up(e.cell_xyz, xyz.data(), tot * sizeof(int));
+        if (e.n_chunks) {
+            ce = ce != cudaSuccess ? ce : up(e.chunk_lo, clo.data(), clo.size() * sizeof(int64_t));
+            ce = ce != cudaSuccess ? ce : up(e.chunk_hi, chi.data(), chi.size() * sizeof(int64_t));
+        }
+        ce = ce != cudaSuccess ? ce : up(e.box_chunk_off, bco.data(), (B + 1) * sizeof(int));
+        if (ce == cudaSuccess) ce = cudaMemset(e.cell_count, 0, tot * sizeof(int));
+        if (ce == cudaSuccess) ce = cudaMemset(e.v, 0, 3 * Np * sizeof(double));
+        if (ce == cudaSuccess) ce = cudaMemset(e.f, 0, 3 * Np * sizeof(double));
+        if (ce == cudaSuccess) ce = cudaMemset(e.e_atom, 0, Np * sizeof(double));
+        if (ce == cudaSuccess) ce = cudaMemset(e.ctl, 0, sizeof(Ctl));
+        if (ce != cudaSuccess) {
+            rc = fail(E, MD_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(ce));
+            goto fail_alloc;
+        }
+        launch_reset_perm(e, s);
+        if ((rc = upload_potential(h, s)) != MD_OK) goto fail_alloc;
+        ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+        if (ce != cudaSuccess) {
+            rc = fail(E, MD_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(ce));
+            goto fail_alloc;
+        }
+    }
+    *out = h;
+    return MD_OK;
+fail_alloc:
+    g_err = e.err;
+    free_engine(e);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+    return rc;
+}
+
+// ---- transfers ----
+
+// Device pointer for an input array: the array itself if it lives on the
+// device, else a copy in the staging buffer.
+int stage_in(Engine* E, const double* src, size_t count, cudaStream_t s, const double** out) {
+    if (is_device_ptr(src)) {
+        *out = src;
+        return MD_OK;
+    }
+    CK(cudaMemcpyAsync(E->stage, src, count * sizeof(double), cudaMemcpyHostToDevice, s));
+    *out = E->stage;
+    return MD_OK;
+}
+
+struct OutDst {
+    double* dev;     // where the kernel writes
+    double* host;    // host destination or NULL
+    size_t count;
+};
+
+OutDst out_dst(Engine& e, double* dst, size_t count) {
+    if (is_device_ptr(dst)) return {dst, nullptr, count};
+    return {e.stage, dst, count};
+}
+
+int out_finish(Engine* E, const OutDst& o, cudaStream_t s) {
+    if (o.host) CK(cudaMemcpyAsync(o.host, o.dev, o.count * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return MD_OK;
+}
+
+int read_ctl(Engine* E, cudaStream_t s) {
+    CK(cudaMemcpyAsync(E->ctl_host, E->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MD_OK;
+}
+
+int clear_status(Engine* E, cudaStream_t s) {
+    CK(cudaMemsetAsync(&E->ctl->status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(&E->ctl->overflow_count, 0, sizeof(int), s));
+    return MD_OK;
+}
+
+int grow_list(Engine* E, int needed) {
+    Engine& e = *E;
+    int m = std::max(needed + needed / 4 + 8, e.max_nb + e.max_nb / 2);
+    m = (m + 7) / 8 * 8;
+    int* nl = nullptr;
+    if (dalloc(E, &nl, (size_t)m * e.N_pad) != MD_OK) return MD_ERR_NOMEM;
+    cudaFree(e.nl);
+    e.nl = nl;
+    e.max_nb = m;
+    destroy_graphs(e);
+    return MD_OK;
+}
+
+// After a launch sequence that may have overflowed the list: grow and
+// rebuild (list only: cells and order are already done) up to 4 times.
+int settle_overflow(Engine* E, cudaStream_t s, bool* had) {
+    *had = false;
+    for (int attempt = 0;; ++attempt) {
+        int rc = read_ctl(E, s);
+        if (rc) return rc;
+        int st = E->ctl_host->status;
+        if (st & kStNonFinite) return fail(E, MD_ERR_NONFINITE, "non-finite energy");
+        if (!(st & kStOverflow)) return MD_OK;
+        *had = true;
+        if (attempt >= 4)
+            return fail(E, MD_ERR_NEIGH_OVERFLOW,
+                        "neighbour list overflow: " + std::to_string(E->ctl_host->overflow_count) + " > " +
+                            std::to_string(E->max_nb));
+        if ((rc = grow_list(E, E->ctl_host->overflow_count)) != MD_OK) return rc;
+        if ((rc = clear_status(E, s)) != MD_OK) return rc;
+        launch_build_list(*E, 1, s);
+        CK(cudaGetLastError());
+    }
+}
+
+int rebuild_and_forces(Engine* E, cudaStream_t s) {
+    launch_rebuild(*E, 1, s);
+    CK(cudaGetLastError());
+    bool had;
+    int rc = settle_overflow(E, s, &had);
+    if (rc) return rc;
+    launch_forces(*E, 0, s);
+    launch_thermo(*E, s);
+    CK(cudaGetLastError());
+    return MD_OK;
+}
+
+int finish_sync(Engine* E, cudaStream_t s) {
+    int rc = read_ctl(E, s);
+    if (rc) return rc;
+    if (E->ctl_host->status & kStNonFinite) return fail(E, MD_ERR_NONFINITE, "non-finite energy");
+    if (E->ctl_host->status & kStOverflow) return fail(E, MD_ERR_NEIGH_OVERFLOW, "neighbour list overflow");
+    return MD_OK;
+}
+
+int set_positions(Engine* E, const double* x, const double* v, bool set_v, cudaStream_t s) {
+    Engine& e = *E;
+    if (e.N == 0) {
+        e.have_state = true;
+        return MD_OK;
+    }
+    const double* xd = nullptr;
+    int rc = stage_in(E, x, 3 * (size_t)e.N, s, &xd);
+    if (rc) return rc;
+    launch_load_positions(e, xd, s);
+    if (set_v) {
+        const double* vd = nullptr;
+        if (v && (rc = stage_in(E, v, 3 * (size_t)e.N, s, &vd))) return rc;
+        launch_load_velocities(e, vd, s);
+    }
+    launch_reset_ctl(e, s);
+    CK(cudaGetLastError());
+    if ((rc = rebuild_and_forces(E, s))) return rc;
+    e.have_state = true;
+    return finish_sync(E, s);
+}
+
+// ---- stepping ----
+
+void enqueue_step(Engine& e, bool hist, cudaStream_t s) {
+    launch_kick_drift(e, s);
+    launch_rebuild(e, 0, s);
+    launch_forces(e, 1, s);
+    launch_end_step(e, hist ? 1 : 0, s);
+}
+
+int capture(md_batch* h, int steps, bool hist, cudaGraphExec_t* out) {
+    Engine* E = &h->e;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < steps; ++k) enqueue_step(h->e, hist, h->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+    if (ce != cudaSuccess) return fail(E, MD_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return fail(E, MD_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
+    return MD_OK;
+}
+
+constexpr int kGraphChunk = 8;
+
+int enqueue_steps(md_batch* h, int n, bool hist, bool use_graph, cudaStream_t s) {
+    Engine* E = &h->e;
+    Engine& e = *E;
+    if (!use_graph || e.N == 0) {
+        for (int k = 0; k < n; ++k) enqueue_step(e, hist, s);
+        CK(cudaGetLastError());
+        return MD_OK;
+    }
+    if (e.graph_hist != hist) destroy_graphs(e);
+    e.graph_hist = hist;
+    int rc;
+    if (n >= kGraphChunk && !e.graph_chunk && (rc = capture(h, kGraphChunk, hist, &e.graph_chunk))) return rc;
+    if (n % kGraphChunk && !e.graph_step && (rc = capture(h, 1, hist, &e.graph_step))) return rc;
+    for (int k = 0; k < n / kGraphChunk; ++k) CK(cudaGraphLaunch(e.graph_chunk, s));
+    for (int k = 0; k < n % kGraphChunk; ++k) CK(cudaGraphLaunch(e.graph_step, s));
+    return MD_OK;
+}
+
+int ensure_hist(Engine* E, int n) {
+    Engine& e = *E;
+    if (e.hist_cap >= n) return MD_OK;
+    dfree(e.hist);
+    int cap = std::max(n, 1024);
+    if (dalloc(E, &e.hist, 4 * (size_t)cap) != MD_OK) return MD_ERR_NOMEM;
+    e.hist_cap = cap;
+    destroy_graphs(e);
+    return MD_OK;
+}
+
+int steps_impl(md_batch* h, int n, double* hist_out, bool use_graph, cudaStream_t s) {
+    Engine* E = &h->e;
+    Engine& e = *E;
+    if (n < 0) return fail(E, MD_ERR_ARG, "n_steps must be >= 0");
+    if (!e.have_state) return fail(E, MD_ERR_ARG, "no state: call set_state or compute_forces first");
+    bool hist = hist_out != nullptr;
+    int rc;
+    if (hist && (rc = ensure_hist(E, n))) return rc;
+    if ((rc = read_ctl(E, s))) return rc;
+    long long step0 = e.ctl_host->step;
+    long long target = step0 + n;
+    int remaining = n;
+    while (remaining > 0) {
+        if ((rc = enqueue_steps(h, remaining, hist, use_graph, s))) return rc;
+        if ((rc = read_ctl(E, s))) return rc;
+        int st = e.ctl_host->status;
+        if (st & kStNonFinite) return fail(E, MD_ERR_NONFINITE, "non-finite energy");
+        if (st & kStOverflow) {
+            // the step that overflowed has drifted and re-sorted; finish it
+            bool had;
+            if ((rc = settle_overflow(E, s, &had))) return rc;
+            launch_forces(e, 1, s);
+            launch_end_step(e, hist ? 1 : 0, s);
+            CK(cudaGetLastError());
+            if ((rc = read_ctl(E, s))) return rc;
+        }
+        remaining = (int)(target - e.ctl_host->step);
+    }
+    launch_thermo(e, s);
+    CK(cudaGetLastError());
+    if (hist) {
+        // rows step0 .. step0+n-1 of the ring
+        OutDst o = out_dst(e, hist_out, 4 * (size_t)n);
+        for (long long k = 0; k < n;) {
+            long long r = (step0 + k) % e.hist_cap;
+            long long len = std::min<long long>(n - k, e.hist_cap - r);
+            CK(cudaMemcpyAsync(o.dev + 4 * k, e.hist + 4 * r, 4 * len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            k += len;
+        }
+        if ((rc = out_finish(E, o, s))) return rc;
+    }
+    return finish_sync(E, s);
+}
+
+int thermo_impl(md_batch* h, md_thermo* out, double* per_box, cudaStream_t s) {
+    Engine* E = &h->e;
+    Engine& e = *E;
+    double t[4];
+    CK(cudaMemcpyAsync(t, e.thermo_dev + 4 * e.B, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    int rc;
+    if (per_box) {
+        OutDst o = out_dst(e, per_box, 4 * (size_t)e.B);
+        CK(cudaMemcpyAsync(o.dev, e.thermo_dev, 4 * e.B * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if ((rc = out_finish(E, o, s))) return rc;
+    }
+    if ((rc = read_ctl(E, s))) return rc;
+    if (out) {
+        out->ke = t[0];
+        out->pe = t[1];
+        out->etot = t[2];
+        out->temperature = t[3];
+        double d2;
+        memcpy(&d2, &e.ctl_host->disp2_last, sizeof(d2));
+        out->max_disp = std::sqrt(d2);
+        out->n_rebuild = e.ctl_host->n_rebuild;
+        out->step = e.ctl_host->step;
+    }
+    return MD_OK;
+}
+
+md_batch* H(const md_batch* p) { return const_cast<md_batch*>(p); }
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+int md_create(const md_config* cfg, const md_potential* pot, int64_t n_atoms, md_ctx** out) {
+    if (!cfg) return fail(nullptr, MD_ERR_ARG, "config is NULL");
+    if (n_atoms < 0) return fail(nullptr, MD_ERR_ARG, "n_atoms must be >= 0");
+    int64_t off[2] = {0, n_atoms};
+    return create_impl(cfg, pot, 1, off, cfg->box, out);
+}
+
+int md_batch_create(const md_config* cfg, const md_potential* pot, int n_boxes, const int64_t* atom_offsets,
+                    const double* box_lengths, md_batch** out) {
+    if (!atom_offsets || !box_lengths) return fail(nullptr, MD_ERR_ARG, "offsets or box lengths are NULL");
+    return create_impl(cfg, pot, n_boxes, atom_offsets, box_lengths, out);
+}
+
+int md_destroy(md_ctx* h) {
+    if (!h) return MD_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_engine(h->e);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+    return MD_OK;
+}
+
+int md_batch_destroy(md_batch* b) { return md_destroy(b); }
+
+int md_set_state(md_ctx* h, const double* x, const double* v, md_stream s) {
+    if (!h) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    if (h->e.N > 0 && !x) return fail(E, MD_ERR_ARG, "x is NULL");
+    return set_positions(E, x, v, true, (cudaStream_t)s);
+}
+
+int md_batch_set_state(md_batch* b, const double* x, const double* v, md_stream s) { return md_set_state(b, x, v, s); }
+
+int md_get_state(md_ctx* h, double* x, double* v, md_stream st) {
+    if (!h) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    Engine& e = *E;
+    cudaStream_t s = (cudaStream_t)st;
+    if (!e.have_state) return fail(E, MD_ERR_ARG, "no state");
+    int rc;
+    if (x && e.N) {
+        OutDst o = out_dst(e, x, 3 * (size_t)e.N);
+        launch_store_vec(e, nullptr, e.x, o.dev, s);
+        if ((rc = out_finish(E, o, s))) return rc;
+    }
+    if (v && e.N) {
+        OutDst o = out_dst(e, v, 3 * (size_t)e.N);
+        launch_store_vec(e, e.v, nullptr, o.dev, s);
+        if ((rc = out_finish(E, o, s))) return rc;
+    }
+    CK(cudaGetLastError());
+    return finish_sync(E, s);
+}
+
+int md_batch_get_state(md_batch* b, double* x, double* v, md_stream s) { return md_get_state(b, x, v, s); }
+
+int md_build_neighbors(md_ctx* h, md_stream st) {
+    if (!h) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
+    if (E->N == 0) return MD_OK;
+    cudaStream_t s = (cudaStream_t)st;
+    int rc = rebuild_and_forces(E, s);
+    if (rc) return rc;
+    return finish_sync(E, s);
+}
+
+int md_max_count(md_ctx* h, int32_t* out) {
+    if (!h || !out) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    int rc = read_ctl(E, nullptr);
+    if (rc) return rc;
+    *out = E->N ? E->ctl_host->max_count : 0;
+    return MD_OK;
+}
+
+int md_get_neighbors(md_ctx* h, int32_t* nn, int32_t* nl, int32_t ld, md_stream st) {
+    if (!h) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    Engine& e = *E;
+    cudaStream_t s = (cudaStream_t)st;
+    if (!e.have_state) return fail(E, MD_ERR_ARG, "no state");
+    if (e.N == 0) return MD_OK;
+    if (!is_device_ptr(nn) || !is_device_ptr(nl)) return fail(E, MD_ERR_ARG, "nn and nl must be device pointers");
+    int rc = read_ctl(E, s);
+    if (rc) return rc;
+    if (ld < e.ctl_host->max_count)
+        return fail(E, MD_ERR_ARG, "ld " + std::to_string(ld) + " < largest count " +
+                                       std::to_string(e.ctl_host->max_count));
+    launch_get_neighbors(e, nn, nl, ld, s);
+    CK(cudaGetLastError());
+    return finish_sync(E, s);
+}
+
+static int emit_outputs(md_batch* h, double* f, double* e_atom, double* rho, cudaStream_t s) {
+    Engine* E = &h->e;
+    Engine& e = *E;
+    int rc;
+    if (e.N == 0) return MD_OK;
+    if (f) {
+        OutDst o = out_dst(e, f, 3 * (size_t)e.N);
+        launch_store_vec(e, e.f, nullptr, o.dev, s);
+        if ((rc = out_finish(E, o, s))) return rc;
+    }
+    if (e_atom) {
+        OutDst o = out_dst(e, e_atom, (size_t)e.N);
+        launch_store_scalar(e, e.e_atom, o.dev, s);
+        if ((rc = out_finish(E, o, s))) return rc;
+    }
+    if (rho) {
+        OutDst o = out_dst(e, rho, (size_t)e.N);
+        launch_store_scalar(e, e.rho, o.dev, s);
+        if ((rc = out_finish(E, o, s))) return rc;
+    }
+    CK(cudaGetLastError());
+    return MD_OK;
+}
+
+int md_compute_forces(md_ctx* h, const double* x, double* f, double* e_atom, double* rho, double* e_total,
+                      md_stream st) {
+    if (!h) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    cudaStream_t s = (cudaStream_t)st;
+    if (E->N > 0 && !x) return fail(E, MD_ERR_ARG, "x is NULL");
+    int rc = set_positions(E, x, nullptr, false, s);
+    if (rc) return rc;
+    if ((rc = emit_outputs(h, f, e_atom, rho, s))) return rc;
+    if (e_total) {
+        OutDst o = out_dst(*E, e_total, 1);
+        CK(cudaMemcpyAsync(o.dev, E->thermo_dev + 4 * E->B + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if ((rc = out_finish(E, o, s))) return rc;
+    }
+    return finish_sync(E, s);
+}
+
+int md_get_forces(md_ctx* h, double* f, double* e_atom, double* rho, md_stream st) {
+    if (!h) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    cudaStream_t s = (cudaStream_t)st;
+    if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
+    int rc = emit_outputs(h, f, e_atom, rho, s);
+    if (rc) return rc;
+    return finish_sync(E, s);
+}
+
+int md_batch_compute_forces(md_batch* b, const double* x, double* f, double* e_box, md_stream st) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    cudaStream_t s = (cudaStream_t)st;
+    if (E->N > 0 && !x) return fail(E, MD_ERR_ARG, "x is NULL");
+    int rc = set_positions(E, x, nullptr, false, s);
+    if (rc) return rc;
+    if ((rc = emit_outputs(b, f, nullptr, nullptr, s))) return rc;
+    if (e_box) {
+        OutDst o = out_dst(*E, e_box, (size_t)E->B);
+        launch_box_energy(*E, o.dev, s);
+        if ((rc = out_finish(E, o, s))) return rc;
+    }
+    return finish_sync(E, s);
+}
+
+int md_step(md_ctx* h, int n_steps, md_thermo* out, double* thermo_hist, int use_graph, md_stream st) {
+    if (!h) return MD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)st;
+    int rc = steps_impl(h, n_steps, thermo_hist, use_graph != 0, s);
+    if (rc) return rc;
+    if (out) return thermo_impl(h, out, nullptr, s);
+    return MD_OK;
+}
+
+int md_get_thermo(md_ctx* h, md_thermo* out, md_stream st) {
+    if (!h || !out) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    cudaStream_t s = (cudaStream_t)st;
+    if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
+    launch_thermo(*E, s);
+    CK(cudaGetLastError());
+    return thermo_impl(h, out, nullptr, s);
+}
+
+int md_batch_step(md_batch* b, int n_steps, int schedule, int use_graph, double* thermo_box, md_stream st) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    cudaStream_t s = (cudaStream_t)st;
+    if (schedule < MD_SCHED_AUTO || schedule > MD_SCHED_TILE) return fail(E, MD_ERR_ARG, "unknown schedule");
+    int rc;
+    bool box = schedule == MD_SCHED_BOX;
+    if (schedule == MD_SCHED_AUTO) box = E->sched_choice == MD_SCHED_BOX;
+    if (box) {
+        if (!box_schedule_fits(*E)) return fail(E, MD_ERR_UNSUPPORTED, "a box is too large for the box schedule");
+        if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
+        if (n_steps < 0) return fail(E, MD_ERR_ARG, "n_steps must be >= 0");
+        rc = launch_box_steps(*E, n_steps, s);
+        if (rc) return fail(E, rc, "box schedule failed");
+        launch_thermo(*E, s);
+        CK(cudaGetLastError());
+        if ((rc = finish_sync(E, s))) return rc;
+    } else {
+        if ((rc = steps_impl(b, n_steps, nullptr, use_graph != 0, s))) return rc;
+    }
+    if (thermo_box) return thermo_impl(b, nullptr, thermo_box, s);
+    return MD_OK;
+}
+
+int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream st) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    cudaStream_t s = (cudaStream_t)st;
+    std::string why;
+    if (check_potential(pot, why) != MD_OK) return fail(E, MD_ERR_ARG, why);
+    const md_potential& o = E->pot_host;
+    if (pot->kind != o.kind) return fail(E, MD_ERR_ARG, "potential kind differs");
+    if (pot->kind == MD_POT_SPLINE &&
+        (pot->n_phi != o.n_phi || pot->n_f != o.n_f || pot->n_F != o.n_F || pot->r_lo != o.r_lo ||
+         pot->r_hi != o.r_hi))
+        return fail(E, MD_ERR_ARG, "spline knot counts or range differ");
+    if (pot_cutoff(pot) > pot_cutoff(&o)) return fail(E, MD_ERR_ARG, "cutoff may not grow");
+    E->pot_host = *pot;
+    if (pot->kind == MD_POT_SPLINE) {
+        size_t nk = (size_t)pot->n_phi + pot->n_f + pot->n_F;
+        E->knots_host.assign(pot->knots, pot->knots + nk);
+        E->pot_host.knots = nullptr;
+    }
+    destroy_graphs(*E);
+    int rc = upload_potential(b, s);
+    if (rc) return rc;
+    if (E->have_state && E->N) {
+        launch_forces(*E, 0, s);
+        launch_thermo(*E, s);
+        CK(cudaGetLastError());
+    }
+    return finish_sync(E, s);
+}
+
+int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* grad, md_stream st) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    cudaStream_t s = (cudaStream_t)st;
+    if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
+    if (E->pot_host.kind == MD_POT_SC) return fail(E, MD_ERR_UNSUPPORTED, "no gradient for Sutton-Chen");
+    if (!grad || !is_device_ptr(grad)) return fail(E, MD_ERR_ARG, "grad must be a device pointer");
+    if (E->N && (!g_f || !is_device_ptr(g_f))) return fail(E, MD_ERR_ARG, "g_f must be a device pointer");
+    if (g_e && !is_device_ptr(g_e)) return fail(E, MD_ERR_ARG, "g_e must be a device pointer");
+    int rc = launch_param_grad(*E, g_f, g_e, grad, s);
+    if (rc) return fail(E, rc, "parameter gradient failed");
+    CK(cudaGetLastError());
+    return finish_sync(E, s);
+}
+
+int md_num_params(const md_batch* b) {
+    if (!b) return -1;
+    const md_potential& p = b->e.pot_host;
+    return p.kind == MD_POT_SPLINE ? p.n_phi + p.n_f + p.n_F : 5;
+}
+
+const char* md_status_string(int st) {
+    switch (st) {
+        case MD_OK: return "ok";
+        case MD_ERR_ARG: return "invalid argument";
+        case MD_ERR_CUDA: return "CUDA error";
+        case MD_ERR_NOMEM: return "out of device memory";
+        case MD_ERR_NEIGH_OVERFLOW: return "neighbour list overflow";
+        case MD_ERR_NONFINITE: return "non-finite energy or force";
+        case MD_ERR_TIMEOUT: return "device wait timed out";
+        case MD_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char* md_last_error(const md_batch* h) { return h ? H(h)->e.err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

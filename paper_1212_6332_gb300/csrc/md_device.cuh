@@ -1,0 +1,315 @@
+// Device-side helpers: periodic geometry, the taper, and the pair and
+// embedding functions of Eq. (1) in float64 and float32.
+#pragma once
+
+#include "md_engine.cuh"
+
+namespace mdk {
+
+// Minimum image of one separation component d = x_j - x_i in a box of
+// length L (h = L/2): one shift of +-L at most.
+__device__ __forceinline__ double minimg(double d, double L, double h) {
+    if (d > h) return d - L;
+    if (d < -h) return d + L;
+    return d;
+}
+
+__device__ __forceinline__ float minimgf(float d, float L, float h) {
+    if (d > h) return d - L;
+    if (d < -h) return d + L;
+    return d;
+}
+
+// Wraps a coordinate into [0, L): x - L*floor(x/L) rounded after each
+// operation (no fused multiply-add), then one more -L if rounding gave L.
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+    double k = floor(__ddiv_rn(x, L));
+    double y = __dsub_rn(x, __dmul_rn(L, k));
+    if (y >= L) y = __dsub_rn(y, L);
+    return y;
+}
+
+__device__ __forceinline__ int load_status(const Ctl* c) {
+    return *((volatile const int*)&c->status);
+}
+
+// ---------------------------------------------------------------- float64
+
+// C2 smoothstep taper S(r) = 1 - 10x^3 + 15x^4 - 6x^5 on [rs, rc), x = (r - rs)/(rc - rs),
+// and dS/dr. The caller guarantees r < rc.
+__device__ __forceinline__ void taper(const Pot& P, double r, double& S, double& dS) {
+    if (r <= P.rs) {
+        S = 1.0;
+        dS = 0.0;
+        return;
+    }
+    double x = (r - P.rs) * P.inv_w;
+    double x2 = x * x;
+    S = 1.0 + x2 * x * (-10.0 + x * (15.0 - 6.0 * x));
+    dS = x2 * (-30.0 + x * (60.0 - 30.0 * x)) * P.inv_w;
+}
+
+__device__ __forceinline__ void spline_eval(const Pot& P, int w, double t, double& v, double& dv) {
+    double s = (t - P.st0[w]) * P.sinvh[w];
+    int n = P.sn[w];
+    const double4_32a* c = P.sp[w];
+    if (s < 0.0) {
+        double4_32a c0 = c[0];
+        v = c0.x + (t - P.st0[w]) * c0.y;
+        dv = c0.y;
+        return;
+    }
+    int k = (int)s;
+    if (k >= n - 1) {  // beyond the last knot: coefficient n-1 holds (value, slope) at the end
+        double4_32a ce = c[n - 1];
+        double u = t - (P.st0[w] + P.sh[w] * (n - 1));
+        v = ce.x + u * ce.y;
+        dv = ce.y;
+        return;
+    }
+    double u = t - (P.st0[w] + P.sh[w] * k);
+    double4_32a ck = c[k];
+    v = ck.x + u * (ck.y + u * (ck.z + u * ck.w));
+    dv = ck.y + u * (2.0 * ck.z + 3.0 * u * ck.w);
+}
+
+// integer power for the Sutton-Chen exponents when they are whole numbers
+__device__ __forceinline__ double powr(double b, double e) {
+    int k = (int)e;
+    if ((double)k == e && k >= 0 && k <= 16) {
+        double r = 1.0, p = b;
+        while (k) {
+            if (k & 1) r *= p;
+            p *= p;
+            k >>= 1;
+        }
+        return r;
+    }
+    return pow(b, e);
+}
+
+// density function rho(r) only (r < rc)
+template <int KIND>
+__device__ __forceinline__ double dens_f(const Pot& P, double r) {
+    if (KIND == MD_POT_RGL) {
+        double S, dS;
+        taper(P, r, S, dS);
+        return P.xi2 * exp(P.q2 - P.q2_r0 * r) * S;
+    } else if (KIND == MD_POT_SC) {
+        double S, dS;
+        taper(P, r, S, dS);
+        return powr(P.a / r, P.m) * S;
+    } else {
+        if (r >= P.rc) return 0.0;
+        double v, dv;
+        spline_eval(P, 1, r, v, dv);
+        return v;
+    }
+}
+
+// V, V', rho, rho' at r < rc
+template <int KIND>
+__device__ __forceinline__ void pair_all(const Pot& P, double r, double& phi, double& dphi, double& fr,
+                                         double& dfr) {
+    if (KIND == MD_POT_RGL) {
+        double S, dS;
+        taper(P, r, S, dS);
+        double e1 = P.A2 * exp(P.p - P.p_r0 * r);
+        double e2 = P.xi2 * exp(P.q2 - P.q2_r0 * r);
+        phi = e1 * S;
+        dphi = e1 * (dS - P.p_r0 * S);
+        fr = e2 * S;
+        dfr = e2 * (dS - P.q2_r0 * S);
+    } else if (KIND == MD_POT_SC) {
+        double S, dS;
+        taper(P, r, S, dS);
+        double rinv = 1.0 / r;
+        double ar = P.a * rinv;
+        double an = P.eps * powr(ar, P.n), am = powr(ar, P.m);
+        phi = an * S;
+        dphi = an * (dS - P.n * rinv * S);
+        fr = am * S;
+        dfr = am * (dS - P.m * rinv * S);
+    } else {
+        if (r >= P.rc) {
+            phi = dphi = fr = dfr = 0.0;
+            return;
+        }
+        spline_eval(P, 0, r, phi, dphi);
+        spline_eval(P, 1, r, fr, dfr);
+    }
+}
+
+// F(rho) and F'(rho); F = F' = 0 for rho <= 0 (RGL, SC)
+template <int KIND>
+__device__ __forceinline__ void embed(const Pot& P, double rho, double& F, double& Fp) {
+    if (KIND == MD_POT_SPLINE) {
+        spline_eval(P, 2, rho, F, Fp);
+    } else {
+        if (rho <= 0.0) {
+            F = 0.0;
+            Fp = 0.0;
+            return;
+        }
+        double s = sqrt(rho);
+        F = -P.F_scale * s;
+        Fp = -0.5 * P.F_scale / s;
+    }
+}
+
+// ---------------------------------------------------------------- float32
+
+__device__ __forceinline__ void taperf(const Pot& P, float r, float& S, float& dS) {
+    if (r <= P.f_rs) {
+        S = 1.0f;
+        dS = 0.0f;
+        return;
+    }
+    float x = (r - P.f_rs) * P.f_inv_w;
+    float x2 = x * x;
+    S = 1.0f + x2 * x * (-10.0f + x * (15.0f - 6.0f * x));
+    dS = x2 * (-30.0f + x * (60.0f - 30.0f * x)) * P.f_inv_w;
+}
+
+__device__ __forceinline__ float powrf(float b, float e) {
+    int k = (int)e;
+    if ((float)k == e && k >= 0 && k <= 16) {
+        float r = 1.0f, p = b;
+        while (k) {
+            if (k & 1) r *= p;
+            p *= p;
+            k >>= 1;
+        }
+        return r;
+    }
+    return powf(b, e);
+}
+
+__device__ __forceinline__ void spline_evalf(const Pot& P, int w, float t, float& v, float& dv) {
+    // spline tables stay float64; evaluation rounds them to float32
+    double vd, dvd;
+    float s = (t - (float)P.st0[w]) * (float)P.sinvh[w];
+    int n = P.sn[w];
+    const double4_32a* c = P.sp[w];
+    if (s < 0.0f) {
+        double4_32a c0 = c[0];
+        v = (float)c0.x + (t - (float)P.st0[w]) * (float)c0.y;
+        dv = (float)c0.y;
+        return;
+    }
+    int k = (int)s;
+    if (k >= n - 1) {
+        double4_32a ce = c[n - 1];
+        float u = t - (float)(P.st0[w] + P.sh[w] * (n - 1));
+        v = (float)ce.x + u * (float)ce.y;
+        dv = (float)ce.y;
+        return;
+    }
+    float u = t - (float)(P.st0[w] + P.sh[w] * k);
+    double4_32a ck = c[k];
+    float c0 = (float)ck.x, c1 = (float)ck.y, c2 = (float)ck.z, c3 = (float)ck.w;
+    v = c0 + u * (c1 + u * (c2 + u * c3));
+    dv = c1 + u * (2.0f * c2 + 3.0f * u * c3);
+    (void)vd;
+    (void)dvd;
+}
+
+template <int KIND>
+__device__ __forceinline__ float dens_ff(const Pot& P, float r) {
+    if (KIND == MD_POT_RGL) {
+        float S, dS;
+        taperf(P, r, S, dS);
+        return P.f_xi2 * __expf(P.f_q2 - P.f_q2_r0 * r) * S;
+    } else if (KIND == MD_POT_SC) {
+        float S, dS;
+        taperf(P, r, S, dS);
+        return powrf(P.f_a / r, P.f_m) * S;
+    } else {
+        if (r >= (float)P.rc) return 0.0f;
+        float v, dv;
+        spline_evalf(P, 1, r, v, dv);
+        return v;
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ void pair_allf(const Pot& P, float r, float& phi, float& dphi, float& fr,
+                                          float& dfr) {
+    if (KIND == MD_POT_RGL) {
+        float S, dS;
+        taperf(P, r, S, dS);
+        float e1 = P.f_A2 * __expf(P.f_p - P.f_p_r0 * r);
+        float e2 = P.f_xi2 * __expf(P.f_q2 - P.f_q2_r0 * r);
+        phi = e1 * S;
+        dphi = e1 * (dS - P.f_p_r0 * S);
+        fr = e2 * S;
+        dfr = e2 * (dS - P.f_q2_r0 * S);
+    } else if (KIND == MD_POT_SC) {
+        float S, dS;
+        taperf(P, r, S, dS);
+        float rinv = 1.0f / r;
+        float ar = P.f_a * rinv;
+        float an = P.f_eps * powrf(ar, P.f_n), am = powrf(ar, P.f_m);
+        phi = an * S;
+        dphi = an * (dS - P.f_n * rinv * S);
+        fr = am * S;
+        dfr = am * (dS - P.f_m * rinv * S);
+    } else {
+        if (r >= (float)P.rc) {
+            phi = dphi = fr = dfr = 0.0f;
+            return;
+        }
+        spline_evalf(P, 0, r, phi, dphi);
+        spline_evalf(P, 1, r, fr, dfr);
+    }
+}
+
+// Compensated float32 accumulator (Kahan-Babuska / Neumaier): s + c carries
+// about twice the float32 precision over the few hundred terms of one atom.
+struct KSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        float t = s + x;
+        if (fabsf(s) >= fabsf(x))
+            c += (s - t) + x;
+        else
+            c += (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// ---------------------------------------------------------------- reductions
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// Block-wide sum in a fixed order (deterministic). Result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NT / 32; ++k) r += sh[k];
+    return r;
+}
+
+}  // namespace mdk

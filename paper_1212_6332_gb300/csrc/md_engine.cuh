@@ -1,0 +1,183 @@
+// Internal declarations of the many-body MD engine (CUDA, sm_103a).
+//
+// One engine serves a single box and a batch of boxes alike: a single box is
+// a batch of one (the paper's multiple-box-in-one-run scheme, Sec. 4.4,
+// numbers the cells of box I after those of boxes 0..I-1). Atoms are kept
+// sorted by cell, cells of each box in Morton order; boxes are contiguous.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "md.h"
+
+namespace mdk {
+
+// Unit constants (CODATA 2018).
+constexpr double kMVV = 103.642696527;  // eV per u (A/fs)^2
+constexpr double kBoltz = 8.617333262e-5;  // eV/K
+
+// Device status bits.
+constexpr int kStOverflow = 1;
+constexpr int kStNonFinite = 2;
+constexpr int kStTimeout = 4;
+
+// Potential, passed by value to kernels.
+struct Pot {
+    int kind;
+    double rc, rc2, rs, inv_w;  // cutoff, taper start, 1/(rc - rs); rs >= rc: hard cut
+    // RGL: V = A2 exp(p - p_r0 r) S, rho = xi2 exp(q2 - q2_r0 r) S
+    double A2, xi2, p, p_r0, q2, q2_r0;
+    // SC: V = eps (a/r)^n S, rho = (a/r)^m S; F = -F_scale sqrt(rho)
+    double eps, a, n, m;
+    double F_scale;
+    // spline: per-interval cubic coefficients (c0 + c1 u + c2 u^2 + c3 u^3,
+    // u = t - t_k) for V, rho, F; n knots -> n - 1 intervals
+    const double4_32a* sp[3];
+    int sn[3];
+    double st0[3], sh[3], sinvh[3];
+    // float copies for the mixed-precision path
+    float f_rc2, f_rs, f_inv_w, f_A2, f_xi2, f_p, f_p_r0, f_q2, f_q2_r0, f_eps, f_a, f_n, f_m;
+};
+
+// Geometry of the boxes, passed by value to kernels.
+struct Geo {
+    int B;                    // number of boxes
+    const double* L;          // [B*3] box lengths
+    const double* cell_len;   // [B*3] cell sides
+    const float* cell_len_f;  // [B*3] cell sides as float
+    const int* nc;            // [B*3] cells per axis
+    const int* cell_off;      // [B+1] first global cell of each box
+    const int64_t* atom_off;  // [B+1] first atom of each box
+    const int* atom_box;      // [N] box of each atom slot
+    const int* cell_box;      // [n_cells] box of each global cell
+    const int* cell_rank;     // [n_cells] (box, row-major cell) -> global Morton-ordered cell
+    const int* cell_xyz;      // [n_cells] global cell -> packed (cx | cy << 10 | cz << 20)
+    // single-box fast path
+    double L0[3];
+};
+
+// Device-resident control words.
+struct Ctl {
+    int status;                      // kSt* bits
+    int overflow_count;              // largest neighbour count seen at overflow
+    unsigned long long disp2_bits;   // max squared displacement this step (double bits)
+    unsigned long long disp2_last;   // value of the last completed step
+    long long step;                  // completed steps since set_state
+    long long n_rebuild;             // list builds since set_state
+    int rebuilt;                     // the current step rebuilt the list
+    int max_count;                   // largest neighbour count of the current list
+};
+
+struct Engine {
+    // configuration
+    md_config cfg{};
+    md_potential pot_host{};
+    std::vector<double> knots_host;
+    Pot pot{};
+    int B = 0;
+    int64_t N = 0, N_pad = 0;
+    int n_cells = 0;
+    int max_nb = 0;
+    double rl = 0.0;  // list radius r_cut + skin
+    std::vector<int64_t> atom_off_h;
+    std::vector<double> L_h;
+    std::vector<int> nc_h, cell_off_h;
+    std::string err;
+
+    // geometry tables (device)
+    double* L = nullptr;
+    double* cell_len = nullptr;
+    float* cell_len_f = nullptr;
+    int* nc = nullptr;
+    int* cell_off = nullptr;
+    int64_t* atom_off = nullptr;
+    int* atom_box = nullptr;
+    int* cell_box = nullptr;
+    int* cell_rank = nullptr;
+    int* cell_xyz = nullptr;
+    double4_32a* spline_coef = nullptr;  // 3 splines back to back
+    double* spline_work = nullptr;   // [3 * total knots] setup scratch
+    double* knots_dev = nullptr;
+    // reduction chunks: (box, [lo, hi)) pieces of at most 4096 atoms
+    int n_chunks = 0;
+    int64_t* chunk_lo = nullptr;
+    int64_t* chunk_hi = nullptr;
+    int* box_chunk_off = nullptr;  // [B+1]
+
+    // atoms, sorted order (device)
+    double4_32a* x = nullptr;    // positions (w unused)
+    double4_32a* x_alt = nullptr;
+    double4_32a* xb = nullptr;   // positions at the last list build
+    double* v = nullptr;     // [3][N_pad] SoA
+    double* v_alt = nullptr;
+    double* f = nullptr;     // [3][N_pad] SoA
+    double* rho = nullptr;
+    double* Fp = nullptr;
+    float* Fpf = nullptr;    // mixed: float copy of F'(rho)
+    double* e_atom = nullptr;
+    float4* xo = nullptr;    // mixed: cell-local offsets, w = packed cell coords
+    int* perm = nullptr;     // sorted slot -> caller index
+    int* perm_alt = nullptr;
+    int* iperm = nullptr;    // caller index -> sorted slot
+    int* cell_of = nullptr;  // [N] global cell of each slot (binning, old order)
+    int* cell_t = nullptr;      // [N] cell of each sorted slot at the last build
+    int* cell_t_alt = nullptr;
+    int* src = nullptr;      // [N] new slot -> old slot
+    int* cell_count = nullptr;  // [n_cells] zero at rest
+    int* cell_start = nullptr;  // [n_cells + 1]
+    int* scan_tmp = nullptr;
+    int* nn = nullptr;          // [N_pad]
+    int* nl = nullptr;          // [max_nb][N_pad] column-major
+    double* stage = nullptr;    // [3N] staging for host copies / caller-order outputs
+    double* red = nullptr;      // reduction scratch [2 * n_chunks]
+    double* thermo_dev = nullptr;  // [B][4] + [4] totals
+    double* hist = nullptr;        // per-step thermo ring
+    int hist_cap = 0;
+    Ctl* ctl = nullptr;
+    Ctl* ctl_host = nullptr;       // pinned mirror
+
+    bool have_state = false;
+    // CUDA graph of one step (and of a chunk of steps)
+    cudaGraphExec_t graph_step = nullptr;
+    cudaGraphExec_t graph_chunk = nullptr;
+    int graph_chunk_len = 0;
+    bool graph_hist = false;
+    int sched_choice = 0;  // autotuner result for batches (0 = unknown)
+};
+
+Geo make_geo(const Engine& e);
+
+// ---- kernels' host launchers (all enqueue on `s`) ----
+// binning + sort + permute + list build; mode 1 = always, 0 = only when the
+// device displacement word exceeds (skin/2)^2
+void launch_rebuild(Engine& e, int mode, cudaStream_t s);
+void launch_build_list(Engine& e, int mode, cudaStream_t s);
+// density and force passes (fp64 or mixed); kick != 0 fuses v += dt/2 F/m
+void launch_forces(Engine& e, int kick, cudaStream_t s);
+void launch_kick_drift(Engine& e, cudaStream_t s);
+void launch_end_step(Engine& e, int record_hist, cudaStream_t s);
+void launch_thermo(Engine& e, cudaStream_t s);
+void launch_thermo_hist(Engine& e, cudaStream_t s);
+void launch_reset_ctl(Engine& e, cudaStream_t s);
+void launch_prepare_mixed(Engine& e, cudaStream_t s);
+void launch_spline_setup(Engine& e, cudaStream_t s);
+// caller-order <-> sorted-order copies
+void launch_load_positions(Engine& e, const double* src_caller, cudaStream_t s);
+void launch_load_velocities(Engine& e, const double* src_caller, cudaStream_t s);
+void launch_store_vec(Engine& e, const double* soa_or_null, const double4_32a* x4_or_null, double* dst_caller,
+                      cudaStream_t s);
+void launch_store_scalar(Engine& e, const double* src_sorted, double* dst_caller, cudaStream_t s);
+void launch_get_neighbors(Engine& e, int32_t* nn_out, int32_t* nl_out, int32_t ld, cudaStream_t s);
+void launch_box_energy(Engine& e, double* e_box_dev, cudaStream_t s);
+void launch_reset_perm(Engine& e, cudaStream_t s);
+// batched block-per-box schedule
+int launch_box_steps(Engine& e, int n_steps, cudaStream_t s);
+bool box_schedule_fits(const Engine& e);
+// parameter adjoint
+int launch_param_grad(Engine& e, const double* g_f, const double* g_e, double* grad, cudaStream_t s);
+
+}  // namespace mdk

@@ -1,0 +1,351 @@
+// Time integration, reductions and caller-order copies.
+//
+//   k_kick_drift   v += dt/2 F/m; x += dt v; wrap; largest displacement since
+//                  the last list build (device rebuild trigger); mixed
+//                  precision: refresh the cell-local float32 offsets
+//   k_end_step     step bookkeeping on the device (no host round trip)
+//   k_chunk_sums / k_thermo_final
+//                  deterministic fixed-order sums of kinetic and potential
+//                  energy per box, totals, temperature, non-finite check
+// The paper integrates with a predictor-corrector (Sec. 3.3); velocity
+// Verlet replaces it here.
+#include "md_device.cuh"
+
+namespace mdk {
+
+constexpr int kINT = 256;
+
+template <bool SINGLE, bool MIXED>
+__global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo g, double4_32a* __restrict__ x,
+                                                     double* __restrict__ v, const double* __restrict__ f,
+                                                     const double4_32a* __restrict__ xb, double c_kick, double dt,
+                                                     float4* __restrict__ xo, const int* __restrict__ cell_t,
+                                                     Ctl* ctl) {
+    if (load_status(ctl)) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double d2 = 0.0;
+    if (i < N) {
+        int b = SINGLE ? 0 : g.atom_box[i];
+        double L[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+        double4_32a p = x[i];
+        double4_32a q = xb[i];
+        double vx = v[i] + c_kick * f[i];
+        double vy = v[Np + i] + c_kick * f[Np + i];
+        double vz = v[2 * Np + i] + c_kick * f[2 * Np + i];
+        p.x = wrap_coord(p.x + dt * vx, L[0]);
+        p.y = wrap_coord(p.y + dt * vy, L[1]);
+        p.z = wrap_coord(p.z + dt * vz, L[2]);
+        v[i] = vx;
+        v[Np + i] = vy;
+        v[2 * Np + i] = vz;
+        x[i] = p;
+        double dx = minimg(p.x - q.x, L[0], 0.5 * L[0]);
+        double dy = minimg(p.y - q.y, L[1], 0.5 * L[1]);
+        double dz = minimg(p.z - q.z, L[2], 0.5 * L[2]);
+        d2 = dx * dx + dy * dy + dz * dz;
+        if (MIXED) {
+            int gc = cell_t[i];
+            int xyz = g.cell_xyz[gc];
+            int c[3] = {xyz & 1023, (xyz >> 10) & 1023, (xyz >> 20) & 1023};
+            double pc[3] = {p.x, p.y, p.z};
+            float o[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double d = pc[a] - c[a] * g.cell_len[3 * b + a];
+                o[a] = (float)minimg(d, L[a], 0.5 * L[a]);
+            }
+            xo[i] = make_float4(o[0], o[1], o[2], __int_as_float(xyz));
+        }
+    }
+    // block max of d2 (non-negative doubles order like their bit patterns)
+    __shared__ double sm[kINT / 32];
+    d2 = warp_max(d2);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int k = 0; k < kINT / 32; ++k) m = sm[k] > m ? sm[k] : m;
+        if (m > 0.0) atomicMax(&ctl->disp2_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+__global__ void k_end_step(Ctl* ctl) {
+    if (load_status(ctl)) return;
+    ctl->disp2_last = ctl->disp2_bits;
+    ctl->disp2_bits = 0ull;
+    ctl->step += 1;
+    if (ctl->rebuilt) {
+        ctl->n_rebuild += 1;
+        ctl->rebuilt = 0;
+    }
+}
+
+__global__ void k_reset_ctl(Ctl* ctl) {
+    ctl->status = 0;
+    ctl->overflow_count = 0;
+    ctl->disp2_bits = 0ull;
+    ctl->disp2_last = 0ull;
+    ctl->step = 0;
+    ctl->n_rebuild = 0;
+    ctl->rebuilt = 0;
+}
+
+constexpr int kRNT = 256;
+
+// partial sums over one chunk of atoms of one box: (sum v^2, sum E_i)
+__global__ void __launch_bounds__(kRNT) k_chunk_sums(int64_t Np, const int64_t* __restrict__ lo,
+                                                     const int64_t* __restrict__ hi, const double* __restrict__ v,
+                                                     const double* __restrict__ e_atom, double* __restrict__ part) {
+    __shared__ double sh[kRNT / 32];
+    int c = blockIdx.x;
+    int64_t a = lo[c], b = hi[c];
+    double sv = 0.0, se = 0.0;
+    for (int64_t i = a + threadIdx.x; i < b; i += kRNT) {
+        double vx = v[i], vy = v[Np + i], vz = v[2 * Np + i];
+        sv += vx * vx + vy * vy + vz * vz;
+        se += e_atom[i];
+    }
+    double tv = block_sum<kRNT>(sv, sh);
+    double te = block_sum<kRNT>(se, sh);
+    if (threadIdx.x == 0) {
+        part[2 * c] = tv;
+        part[2 * c + 1] = te;
+    }
+}
+
+// per-box and total (ke, pe, etot, T); optional history row
+__global__ void __launch_bounds__(1024) k_thermo_final(int B, const int* __restrict__ box_chunk_off,
+                                                       const int64_t* __restrict__ atom_off,
+                                                       const double* __restrict__ part, double half_mv,
+                                                       double* __restrict__ thermo, double* __restrict__ hist,
+                                                       int hist_cap, Ctl* ctl) {
+    __shared__ double sh[32];
+    double ke_t = 0.0, pe_t = 0.0, dof_t = 0.0;
+    for (int b = threadIdx.x; b < B; b += 1024) {
+        double sv = 0.0, se = 0.0;
+        for (int c = box_chunk_off[b]; c < box_chunk_off[b + 1]; ++c) {
+            sv += part[2 * c];
+            se += part[2 * c + 1];
+        }
+        double ke = half_mv * sv;
+        double nb = (double)(atom_off[b + 1] - atom_off[b]);
+        double dof = 3.0 * nb - 3.0;
+        thermo[4 * b] = ke;
+        thermo[4 * b + 1] = se;
+        thermo[4 * b + 2] = ke + se;
+        thermo[4 * b + 3] = dof > 0.0 ? 2.0 * ke / (dof * kBoltz) : 0.0;
+        ke_t += ke;
+        pe_t += se;
+        dof_t += dof > 0.0 ? dof : 0.0;
+    }
+    double ke = block_sum<1024>(ke_t, sh);
+    double pe = block_sum<1024>(pe_t, sh);
+    double dof = block_sum<1024>(dof_t, sh);
+    if (threadIdx.x == 0) {
+        double* t = thermo + 4 * B;
+        t[0] = ke;
+        t[1] = pe;
+        t[2] = ke + pe;
+        t[3] = dof > 0.0 ? 2.0 * ke / (dof * kBoltz) : 0.0;
+        if (!isfinite(ke) || !isfinite(pe)) atomicOr(&ctl->status, kStNonFinite);
+        if (hist) {
+            long long s = ctl->step % hist_cap;
+            for (int k = 0; k < 4; ++k) hist[4 * s + k] = t[k];
+        }
+    }
+}
+
+template <bool SINGLE, bool MIXED>
+static void kick_drift_t(Engine& e, cudaStream_t s) {
+    Geo g = make_geo(e);
+    int nb = (int)((e.N + kINT - 1) / kINT);
+    double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
+    k_kick_drift<SINGLE, MIXED><<<nb, kINT, 0, s>>>(e.N, e.N_pad, g, e.x, e.v, e.f, e.xb, c_kick, e.cfg.dt, e.xo,
+                                                   e.cell_t, e.ctl);
+}
+
+void launch_kick_drift(Engine& e, cudaStream_t s) {
+    if (e.N == 0) return;
+    bool mixed = e.cfg.precision == MD_MIXED;
+    if (e.B == 1)
+        mixed ? kick_drift_t<true, true>(e, s) : kick_drift_t<true, false>(e, s);
+    else
+        mixed ? kick_drift_t<false, true>(e, s) : kick_drift_t<false, false>(e, s);
+}
+
+void launch_end_step(Engine& e, int record_hist, cudaStream_t s) {
+    if (record_hist) launch_thermo_hist(e, s);
+    k_end_step<<<1, 1, 0, s>>>(e.ctl);
+}
+
+static void thermo_impl(Engine& e, bool hist, cudaStream_t s) {
+    if (e.n_chunks > 0)
+        k_chunk_sums<<<e.n_chunks, kRNT, 0, s>>>(e.N_pad, e.chunk_lo, e.chunk_hi, e.v, e.e_atom, e.red);
+    double half_mv = 0.5 * e.cfg.mass * kMVV;
+    k_thermo_final<<<1, 1024, 0, s>>>(e.B, e.box_chunk_off, e.atom_off, e.red, half_mv, e.thermo_dev,
+                                      hist ? e.hist : nullptr, e.hist_cap, e.ctl);
+}
+
+void launch_thermo(Engine& e, cudaStream_t s) { thermo_impl(e, false, s); }
+void launch_thermo_hist(Engine& e, cudaStream_t s) { thermo_impl(e, true, s); }
+
+void launch_reset_ctl(Engine& e, cudaStream_t s) { k_reset_ctl<<<1, 1, 0, s>>>(e.ctl); }
+
+// ---------------------------------------------------------------- copies
+
+__global__ void k_load_pos(int64_t N, const double* __restrict__ src, const int* __restrict__ iperm, Geo g,
+                           double4_32a* __restrict__ x) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    int b = g.B == 1 ? 0 : g.atom_box[c];
+    int t = iperm[c];
+    double4_32a p;
+    p.x = wrap_coord(src[3 * c], g.L[3 * b]);
+    p.y = wrap_coord(src[3 * c + 1], g.L[3 * b + 1]);
+    p.z = wrap_coord(src[3 * c + 2], g.L[3 * b + 2]);
+    p.w = 0.0;
+    x[t] = p;
+}
+
+__global__ void k_load_vel(int64_t N, int64_t Np, const double* __restrict__ src, const int* __restrict__ iperm,
+                           double* __restrict__ v) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    int t = iperm[c];
+    v[t] = src ? src[3 * c] : 0.0;
+    v[Np + t] = src ? src[3 * c + 1] : 0.0;
+    v[2 * Np + t] = src ? src[3 * c + 2] : 0.0;
+}
+
+__global__ void k_store_vec(int64_t N, int64_t Np, const double* __restrict__ soa, const double4_32a* __restrict__ x4,
+                            const int* __restrict__ perm, double* __restrict__ dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    int64_t c = perm[t];
+    if (soa) {
+        dst[3 * c] = soa[t];
+        dst[3 * c + 1] = soa[Np + t];
+        dst[3 * c + 2] = soa[2 * Np + t];
+    } else {
+        double4_32a p = x4[t];
+        dst[3 * c] = p.x;
+        dst[3 * c + 1] = p.y;
+        dst[3 * c + 2] = p.z;
+    }
+}
+
+__global__ void k_store_scalar(int64_t N, const double* __restrict__ src, const int* __restrict__ perm,
+                               double* __restrict__ dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    dst[perm[t]] = src[t];
+}
+
+__global__ void k_get_neighbors(int64_t N, int64_t Np, const int* __restrict__ nn, const int* __restrict__ nl,
+                                int max_nb, const int* __restrict__ perm, int32_t* __restrict__ nn_out,
+                                int32_t* __restrict__ nl_out, int32_t ld) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    int64_t c = perm[t];
+    int n = nn[t];
+    nn_out[c] = n;
+    int m = min(min(n, max_nb), ld);
+    for (int k = 0; k < m; ++k) nl_out[c * ld + k] = perm[nl[(int64_t)k * Np + t]];
+}
+
+__global__ void k_box_energy(int B, const double* __restrict__ thermo, double* __restrict__ e_box) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) e_box[b] = thermo[4 * b + 1];
+}
+
+__global__ void k_reset_perm(int64_t N, int* __restrict__ perm, int* __restrict__ iperm) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    perm[t] = (int)t;
+    iperm[t] = (int)t;
+}
+
+static int nblk(int64_t n, int nt) { return (int)((n + nt - 1) / nt); }
+
+void launch_load_positions(Engine& e, const double* src, cudaStream_t s) {
+    if (e.N == 0) return;
+    k_load_pos<<<nblk(e.N, 256), 256, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x);
+}
+
+void launch_load_velocities(Engine& e, const double* src, cudaStream_t s) {
+    if (e.N == 0) return;
+    k_load_vel<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, src, e.iperm, e.v);
+}
+
+void launch_store_vec(Engine& e, const double* soa, const double4_32a* x4, double* dst, cudaStream_t s) {
+    if (e.N == 0) return;
+    k_store_vec<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, soa, x4, e.perm, dst);
+}
+
+void launch_store_scalar(Engine& e, const double* src, double* dst, cudaStream_t s) {
+    if (e.N == 0) return;
+    k_store_scalar<<<nblk(e.N, 256), 256, 0, s>>>(e.N, src, e.perm, dst);
+}
+
+void launch_get_neighbors(Engine& e, int32_t* nn_out, int32_t* nl_out, int32_t ld, cudaStream_t s) {
+    if (e.N == 0) return;
+    k_get_neighbors<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, e.nn, e.nl, e.max_nb, e.perm, nn_out, nl_out, ld);
+}
+
+void launch_box_energy(Engine& e, double* e_box, cudaStream_t s) {
+    k_box_energy<<<nblk(e.B, 256), 256, 0, s>>>(e.B, e.thermo_dev, e_box);
+}
+
+void launch_reset_perm(Engine& e, cudaStream_t s) {
+    if (e.N == 0) return;
+    k_reset_perm<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.perm, e.iperm);
+}
+
+// ---------------------------------------------------------------- splines
+
+// Natural cubic spline through knot values y_0..y_{n-1} on a uniform grid of
+// spacing h: second derivatives M from the tridiagonal system
+//   (h/6) M_{k-1} + (2h/3) M_k + (h/6) M_{k+1} = (y_{k+1} - 2 y_k + y_{k-1}) / h,
+// M_0 = M_{n-1} = 0 (Thomas algorithm), then per-interval coefficients of
+//   s(u) = y_k + b u + c u^2 + d u^3, u = t - t_k,
+//   b = (y_{k+1} - y_k)/h - h (2 M_k + M_{k+1})/6, c = M_k/2, d = (M_{k+1} - M_k)/(6h);
+// entry n-1 holds the value and slope at the last knot (extrapolation).
+__global__ void k_spline_setup(const double* __restrict__ y_all, double* __restrict__ work,
+                               double4_32a* __restrict__ coef, int n0, int n1, int n2, double h0, double h1, double h2) {
+    int w = threadIdx.x;
+    if (w >= 3) return;
+    int n = w == 0 ? n0 : (w == 1 ? n1 : n2);
+    int off = w == 0 ? 0 : (w == 1 ? n0 : n0 + n1);
+    double h = w == 0 ? h0 : (w == 1 ? h1 : h2);
+    const double* y = y_all + off;
+    double* cp = work + 3 * off;  // modified super-diagonal
+    double* dp = cp + n;          // modified right-hand side
+    double* M = dp + n;
+    double a = h / 6.0, bd = 2.0 * h / 3.0, cu = h / 6.0;
+    for (int k = 1; k <= n - 2; ++k) {
+        double rhs = (y[k + 1] - 2.0 * y[k] + y[k - 1]) / h;
+        double den = k == 1 ? bd : bd - a * cp[k - 1];
+        cp[k] = cu / den;
+        dp[k] = (k == 1 ? rhs : rhs - a * dp[k - 1]) / den;
+    }
+    M[0] = 0.0;
+    M[n - 1] = 0.0;
+    for (int k = n - 2; k >= 1; --k) M[k] = dp[k] - (k < n - 2 ? cp[k] * M[k + 1] : 0.0);
+    double4_32a* c = coef + off;
+    for (int k = 0; k < n - 1; ++k) {
+        double b = (y[k + 1] - y[k]) / h - h * (2.0 * M[k] + M[k + 1]) / 6.0;
+        c[k] = make_double4_32a(y[k], b, 0.5 * M[k], (M[k + 1] - M[k]) / (6.0 * h));
+    }
+    double4_32a l = c[n - 2];
+    c[n - 1] = make_double4_32a(y[n - 1], l.y + 2.0 * l.z * h + 3.0 * l.w * h * h, 0.0, 0.0);
+}
+
+void launch_spline_setup(Engine& e, cudaStream_t s) {
+    const md_potential& p = e.pot_host;
+    k_spline_setup<<<1, 32, 0, s>>>(e.knots_dev, e.spline_work, e.spline_coef, p.n_phi, p.n_f, p.n_F,
+                                    e.pot.sh[0], e.pot.sh[1], e.pot.sh[2]);
+}
+
+}  // namespace mdk

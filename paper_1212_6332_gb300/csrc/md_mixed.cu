@@ -1,0 +1,174 @@
+// Mixed-precision density and force passes.
+//
+// Positions, velocities and the integrator stay float64. For the pair math
+// each atom carries a float32 offset from the origin of the cell it was
+// binned into at the last list build (xo, refreshed after every drift), so
+// a separation is
+//     d = (c_j - c_i) * cell_side + (o_j - o_i)
+// with the cell difference taken as a minimum image in whole cells (exact)
+// and both offsets below one cell side plus the skin: the float32 rounding
+// error of d is ~1e-7 of a cell side, not of the box length. V, rho and
+// their derivatives are evaluated in float32 (hardware exp2 / rsqrt); the
+// per-atom sums rho_i, F_i and the pair energy use compensated float32
+// accumulation (Neumaier), and F(rho_i), F'(rho_i) are taken in float64.
+// The paper's own precedent is float32 positions inside its neighbour-list
+// kernel (Sec. 4).
+#include "md_device.cuh"
+
+namespace mdk {
+
+constexpr int kMNT = 128;
+
+struct CellSep {
+    float lx, ly, lz;     // cell sides
+    int nx, ny, nz;       // cells per axis
+    float Lx, Ly, Lz;     // box lengths
+};
+
+__device__ __forceinline__ int wrap_cells(int d, int n) {
+    if (2 * d > n) return d - n;
+    if (2 * d < -n) return d + n;
+    return d;
+}
+
+__device__ __forceinline__ void sep_mixed(const CellSep& cs, float4 oi, float4 oj, float& dx, float& dy, float& dz) {
+    int ci = __float_as_int(oi.w), cj = __float_as_int(oj.w);
+    int ddx = wrap_cells((cj & 1023) - (ci & 1023), cs.nx);
+    int ddy = wrap_cells(((cj >> 10) & 1023) - ((ci >> 10) & 1023), cs.ny);
+    int ddz = wrap_cells(((cj >> 20) & 1023) - ((ci >> 20) & 1023), cs.nz);
+    dx = minimgf(fmaf((float)ddx, cs.lx, oj.x - oi.x), cs.Lx, 0.5f * cs.Lx);
+    dy = minimgf(fmaf((float)ddy, cs.ly, oj.y - oi.y), cs.Ly, 0.5f * cs.Ly);
+    dz = minimgf(fmaf((float)ddz, cs.lz, oj.z - oi.z), cs.Lz, 0.5f * cs.Lz);
+}
+
+template <bool SINGLE>
+__device__ __forceinline__ CellSep cell_sep(const Geo& g, const CellSep& cs0, int64_t i) {
+    if (SINGLE) return cs0;
+    int b = g.atom_box[i];
+    CellSep cs;
+    cs.lx = g.cell_len_f[3 * b];
+    cs.ly = g.cell_len_f[3 * b + 1];
+    cs.lz = g.cell_len_f[3 * b + 2];
+    cs.nx = g.nc[3 * b];
+    cs.ny = g.nc[3 * b + 1];
+    cs.nz = g.nc[3 * b + 2];
+    cs.Lx = (float)g.L[3 * b];
+    cs.Ly = (float)g.L[3 * b + 1];
+    cs.Lz = (float)g.L[3 * b + 2];
+    return cs;
+}
+
+template <int KIND, bool SINGLE>
+__global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P,
+                                                        const float4* __restrict__ xo, const int* __restrict__ nn,
+                                                        const int* __restrict__ nl, int max_nb,
+                                                        double* __restrict__ rho, double* __restrict__ Fp,
+                                                        float* __restrict__ Fpf, double* __restrict__ e_atom,
+                                                        const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const CellSep cs = cell_sep<SINGLE>(g, cs0, i);
+    const float4 oi = xo[i];
+    const int n = min(nn[i], max_nb);
+    KSum acc;
+    for (int k = 0; k < n; ++k) {
+        int j = nl[(int64_t)k * Np + i];
+        float dx, dy, dz;
+        sep_mixed(cs, oi, xo[j], dx, dy, dz);
+        float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2)));
+    }
+    double r_i = acc.value();
+    double F, Fpi;
+    embed<KIND>(P, r_i, F, Fpi);
+    rho[i] = r_i;
+    Fp[i] = Fpi;
+    Fpf[i] = (float)Fpi;
+    e_atom[i] = F;
+}
+
+template <int KIND, bool SINGLE>
+__global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P,
+                                                      const float4* __restrict__ xo, const int* __restrict__ nn,
+                                                      const int* __restrict__ nl, int max_nb,
+                                                      const float* __restrict__ Fpf, double* __restrict__ f,
+                                                      double* __restrict__ e_atom, double* __restrict__ v,
+                                                      double c_kick, const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const CellSep cs = cell_sep<SINGLE>(g, cs0, i);
+    const float4 oi = xo[i];
+    const float Fpi = Fpf[i];
+    const int n = min(nn[i], max_nb);
+    KSum ax, ay, az, ae;
+    for (int k = 0; k < n; ++k) {
+        int j = nl[(int64_t)k * Np + i];
+        float dx, dy, dz;
+        sep_mixed(cs, oi, xo[j], dx, dy, dz);
+        float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < P.f_rc2) {
+            float rinv = rsqrtf(r2);
+            float r = r2 * rinv;
+            float phi, dphi, fr, dfr;
+            pair_allf<KIND>(P, r, phi, dphi, fr, dfr);
+            float s = (dphi + (Fpi + Fpf[j]) * dfr) * rinv;
+            ax.add(s * dx);
+            ay.add(s * dy);
+            az.add(s * dz);
+            ae.add(phi);
+        }
+    }
+    double fx = ax.value(), fy = ay.value(), fz = az.value();
+    f[i] = fx;
+    f[Np + i] = fy;
+    f[2 * Np + i] = fz;
+    e_atom[i] += 0.5 * ae.value();
+    if (v) {
+        v[i] += c_kick * fx;
+        v[Np + i] += c_kick * fy;
+        v[2 * Np + i] += c_kick * fz;
+    }
+}
+
+template <int KIND, bool SINGLE>
+static void run_mixed(Engine& e, int kick, cudaStream_t s) {
+    Geo g = make_geo(e);
+    CellSep cs{};
+    if (SINGLE) {
+        cs.lx = (float)(e.L_h[0] / e.nc_h[0]);
+        cs.ly = (float)(e.L_h[1] / e.nc_h[1]);
+        cs.lz = (float)(e.L_h[2] / e.nc_h[2]);
+        cs.nx = e.nc_h[0];
+        cs.ny = e.nc_h[1];
+        cs.nz = e.nc_h[2];
+        cs.Lx = (float)e.L_h[0];
+        cs.Ly = (float)e.L_h[1];
+        cs.Lz = (float)e.L_h[2];
+    }
+    int nb = (int)((e.N + kMNT - 1) / kMNT);
+    double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
+    k_density_mixed<KIND, SINGLE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.rho,
+                                                     e.Fp, e.Fpf, e.e_atom, e.ctl);
+    k_force_mixed<KIND, SINGLE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.Fpf,
+                                                   e.f, e.e_atom, kick ? e.v : nullptr, c_kick, e.ctl);
+}
+
+template <int KIND>
+static void run_mixed_k(Engine& e, int kick, cudaStream_t s) {
+    if (e.B == 1)
+        run_mixed<KIND, true>(e, kick, s);
+    else
+        run_mixed<KIND, false>(e, kick, s);
+}
+
+void launch_forces_mixed(Engine& e, int kick, cudaStream_t s) {
+    switch (e.pot.kind) {
+        case MD_POT_RGL: run_mixed_k<MD_POT_RGL>(e, kick, s); break;
+        case MD_POT_SC: run_mixed_k<MD_POT_SC>(e, kick, s); break;
+        default: run_mixed_k<MD_POT_SPLINE>(e, kick, s); break;
+    }
+}
+
+}  // namespace mdk
