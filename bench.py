@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Throughput of the many-body MD step on one GB300 (atom-steps/s).
+
+Default workload: fcc Cu, 100 x 100 x 100 conventional cells = 4,000,000
+atoms, a = 3.615 A, RGL (Cleri-Rosato) Cu with a quintic taper 4.5-5.0 A,
+skin 0.3 A, 300 K Maxwell velocities (seed 1), dt = 1 fs, float64. One bench
+step is one velocity-Verlet MD step of the whole box through the C ABI
+(kick-drift, device-decided list rebuild, density pass, force pass,
+second half-kick); inputs are resident in HBM when the timed region starts.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica of the box on its own
+GPU (the single-box path does not shard); value = all ranks' atom-steps over
+the slowest rank's time. --impl reference times the CPU oracle on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import pathlib
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = pathlib.Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_1212_6332_gb300 import inputs as I  # noqa: E402
+
+METRIC = "atom-steps/s on 1 GB300: 4M-atom box, 4096-box batch; FP64 vs mixed; grad/s"
+UNIT = "atom-steps/s"
+N_CELLS = 100            # fcc repeats per axis of the bench box
+SEED = 1
+TEMP = 300.0
+SKIN = 0.3
+DT = 1.0
+ORACLE_CELLS = 50        # CPU sample: 500,000 atoms of the same lattice
+
+# Algorithmic float64 work per neighbour-list entry, counting each add, mul
+# and compare as 1 flop, an FMA as 2, and exp, sqrt (or rsqrt) and a
+# division as 15, 8 and 8 flops (the cost of a table-free float64 evaluation
+# by polynomial / Newton steps).
+# Density pass, RGL, entry inside r_cut: separation 3, r^2 5, rsqrt 8, r 1,
+# two exp arguments 4, two exp 30, prefactors 2, A = V'/r and B = rho'/r 6,
+# sums 2 -> 61; entry outside r_cut: separation 3 + r^2 5 = 8.
+DENSITY_FLOPS_IN, DENSITY_FLOPS_OUT = 61.0, 8.0
+# Force pass, entry inside r_cut: separation 3, s = A + (F'_i + F'_j) B 3,
+# F_i += s d 6 -> 12; outside r_cut: 0 (skipped).
+FORCE_FLOPS_IN, FORCE_FLOPS_OUT = 12.0, 0.0
+# Bytes per atom (x_j, F'_j gathers counted once, as ideal cache reuse of
+# the Morton-sorted arrays). Density: list 4K + (A, B) write 16K + count 4 +
+# x_i 32 + rho, F', E_i writes 24. Force: list 4K + (A, B) read 16K + count 4
+# + x_i 32 + F'_i 8 + F write 24 + v read/write 48.
+DENSITY_BYTES = (20.0, 60.0)
+FORCE_BYTES = (20.0, 116.0)
+# Nominal GB300 float64 rate (no measured float64 peak is provided).
+FP64_PEAK_TFLOPS = 1.25
+
+REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+           0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+           0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+def measured_peaks() -> dict:
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text())
+    return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = ROOT / "gpurun_out" / f"clocks_bench_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.path.parent.mkdir(exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        try:
+            for line in self.path.read_text().splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 4:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                    bits = int(parts[3], 16)
+                except ValueError:
+                    continue
+                for b, name in REASONS.items():
+                    if bits & b and name != "gpu_idle":
+                        reasons.add(name)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def list_stats(sysm, x_dev, box, rc, sample: int = 65536):
+    """Mean list length K and mean entries inside r_cut over a sample of atoms."""
+    import torch
+    nn, nl = sysm.neighbors()
+    n = nn.shape[0]
+    idx = torch.linspace(0, n - 1, min(sample, n), device="cuda").long()
+    nns = nn[idx].long()
+    cols = nl[idx].long()
+    valid = torch.arange(cols.shape[1], device="cuda")[None, :] < nns[:, None]
+    cols = torch.where(valid, cols, torch.zeros_like(cols))
+    d = x_dev[cols] - x_dev[idx][:, None, :]
+    bt = torch.tensor(box, device="cuda", dtype=torch.float64)
+    d = d - bt * torch.round(d / bt)
+    r2 = (d * d).sum(-1)
+    inside = ((r2 < rc * rc) & valid).sum(1).double().mean().item()
+    K = nns.double().mean().item()
+    del nn, nl
+    return K, inside
+
+
+def oracle_sample(steps: int, cells: int = ORACLE_CELLS) -> dict:
+    """The CPU oracle (single thread) on a bounded sample of the workload: a
+    cells^3 fcc box of the same lattice, potential, temperature and seed."""
+    import oracle as O
+    bx = I.perturbed_fcc(cells, I.A_CU, TEMP, I.MASS_CU, SEED)
+    pot = O.Potential(I.RGL_CU)
+    t0 = time.perf_counter()
+    O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, DT, SKIN, 0)
+    t1 = time.perf_counter()
+    O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, DT, SKIN, steps)
+    t2 = time.perf_counter()
+    per_step = max((t2 - t1) - (t1 - t0), 1e-9) / steps
+    return dict(value=bx.n / per_step, per_step_s=per_step, n=bx.n, setup_s=t1 - t0,
+                sample=f"oracle on a {cells}^3-cell fcc Cu box ({bx.n} atoms, same lattice, RGL, {TEMP:.0f} K, "
+                       f"seed {SEED}), {steps} velocity-Verlet steps minus its setup run")
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    W, K = args.warmup, args.steps
+    cells = ORACLE_CELLS
+    bx = I.perturbed_fcc(cells, I.A_CU, TEMP, I.MASS_CU, SEED)
+    pot = O.Potential(I.RGL_CU)
+    st = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, DT, SKIN, max(W, 0))
+    t0 = time.perf_counter()
+    O.md_run(pot, st["x"], st["v"], bx.box, I.MASS_CU, DT, SKIN, 0)
+    t1 = time.perf_counter()
+    O.md_run(pot, st["x"], st["v"], bx.box, I.MASS_CU, DT, SKIN, K)
+    t2 = time.perf_counter()
+    per_step = max((t2 - t1) - (t1 - t0), 1e-9) / max(K, 1)
+    value = bx.n / per_step
+    sample = (f"oracle on a {cells}^3-cell fcc Cu box ({bx.n} atoms, same lattice, RGL, {TEMP:.0f} K, seed {SEED}); "
+              f"per-step time = ({K} steps run - setup run) / {K}")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": W, "ms_per_step": per_step * 1e3 * (4_000_000 / bx.n), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "fcc Cu RGL 300 K FP64 (4,000,000-atom box; CPU sample of 500,000 atoms)",
+                      "sample_atoms": bx.n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_variant(precision: str, W: int, K: int, x_h, v_h, box):
+    """atom-steps/s of the same box in another precision (same timing rules)."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    s = System(I.RGL_CU, box=box, n_atoms=len(x_h), skin=SKIN, dt=DT, mass=I.MASS_CU, precision=precision)
+    s.set_state(torch.tensor(x_h, device="cuda"), torch.tensor(v_h, device="cuda"))
+    s.step(W)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    th = s.step(K)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    s.close()
+    return dict(value=len(x_h) * K / (ms * 1e-3), ms_per_step=ms / K, n_rebuild=th["n_rebuild"])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=N_CELLS)
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-precision and oracle legs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    W = max(args.warmup, 3)
+    K = args.steps
+    world, rank, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1212_6332_gb300 import build
+    build.build()
+    from paper_1212_6332_gb300.md import System
+
+    bx = I.perturbed_fcc(args.cells, I.A_CU, TEMP, I.MASS_CU, SEED)
+    N = bx.n
+    x_dev = torch.tensor(bx.x, device="cuda")
+    v_dev = torch.tensor(bx.v, device="cuda")
+    s = System(I.RGL_CU, box=bx.box, n_atoms=N, skin=SKIN, dt=DT, mass=I.MASS_CU, precision="fp64")
+    s.set_state(x_dev, v_dev)
+    K_list, K_in = list_stats(s, x_dev, bx.box, I.RGL_CU["r_cut"])
+    s.step(W)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.profile_start(timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        th = s.step(K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    prof = s.profile_read()
+    ms = ev0.elapsed_time(ev1)
+    t_local = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = t_local.item()
+    value = world * N * K / (ms_max * 1e-3)
+
+    # dominant kernel (event-timed on the launching stream)
+    dom = "density" if prof["ms"]["density"] >= prof["ms"]["force"] else "force"
+    k_ms = prof["ms"][dom] / max(prof["timed"][dom], 1)
+    if dom == "density":
+        fin, fout, (bk, b0), kname = DENSITY_FLOPS_IN, DENSITY_FLOPS_OUT, DENSITY_BYTES, "k_density (float64 density pass)"
+    else:
+        fin, fout, (bk, b0), kname = FORCE_FLOPS_IN, FORCE_FLOPS_OUT, FORCE_BYTES, "k_force (float64 force pass)"
+    flops = N * (K_in * fin + (K_list - K_in) * fout)
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    bytes_k = N * (bk * K_list + b0)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal float64 rate (no measured float64 peak on this pool)",
+                "traffic": None, "flops_per_launch": flops, "launch_ms": k_ms,
+                "hbm": {"achieved": bytes_k / (k_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": bytes_k / (k_ms * 1e-3) / 1e9 / hbm,
+                        "peak_source": "measured" if "fallback" not in peaks else "fallback",
+                        "bytes_per_launch": bytes_k}}
+    phase_ms = {k: prof["ms"][k] / max(K, 1) for k in prof["ms"]}
+
+    # end to end through the C ABI with pinned host buffers: every step
+    # uploads the state, advances one step and downloads the state
+    xh = torch.empty((N, 3), dtype=torch.float64, pin_memory=True)
+    vh = torch.empty((N, 3), dtype=torch.float64, pin_memory=True)
+    s.get_state(xh, vh)
+    K_e2e = max(3, min(K, 10))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K_e2e):
+        s.set_state(xh, vh)
+        s.step(1)
+        s.get_state(xh, vh)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e_t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * N * K_e2e / e2e_t.item(), "unit": UNIT, "h2d_bytes_per_step": 2 * N * 3 * 8,
+           "d2h_bytes_per_step": 2 * N * 3 * 8 + 56,
+           "call": "md_set_state(host) + md_step(1) + md_get_state(host) per step", "steps": K_e2e}
+
+    variants = {}
+    cpu = None
+    if rank == 0 and not args.no_extras:
+        s.close()
+        del s
+        variants["mixed"] = run_variant("mixed", W, K, bx.x, bx.v, bx.box)
+        variants["fp64"] = {"value": value, "ms_per_step": ms_max / K}
+    if rank == 0 and not args.no_extras:
+        import oracle as O
+        O.build()
+        smp = oracle_sample(3)
+        cpu = {"value": smp["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp["sample"]}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+               "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64", "data": "synthetic",
+               "config": {"workload": f"fcc Cu {args.cells}^3 cells ({N} atoms), RGL Cu taper 4.5-5.0 A, "
+                                      f"skin {SKIN} A, {TEMP:.0f} K, dt {DT} fs, float64",
+                          "atoms": N, "parallelism": "replicas" if world > 1 else "single",
+                          "l2": "working set (list + positions) larger than L2",
+                          "mean_list_len": K_list, "mean_in_cutoff": K_in,
+                          "n_rebuild": th["n_rebuild"], "phase_ms_per_step": phase_ms},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],
+               "clocks": clk.summary(), "variants": variants}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -242,6 +242,42 @@ MD_API int md_param_grad(md_batch* b, const double* g_f, const double* g_e, doub
 /* Number of potential parameters (5 for RGL/SC, n_phi + n_f + n_F for a spline). */
 MD_API int md_num_params(const md_batch* b);
 
+/* ---------------------------------------------------------------- profiling */
+
+/* Phases of a step, for md_profile. */
+enum md_phase {
+    MD_PHASE_KICK_DRIFT = 0, /* first half-kick, drift, wrap, displacement check */
+    MD_PHASE_REBUILD = 1,    /* binning, sort and list build (early exit when not due) */
+    MD_PHASE_DENSITY = 2,    /* density pass and embedding derivative */
+    MD_PHASE_FORCE = 3,      /* force pass and second half-kick */
+    MD_PHASE_OTHER = 4,      /* step bookkeeping, reductions, copies */
+    MD_PHASE_COUNT = 5
+};
+
+/* Kernel launches issued by a handle since md_profile_start, and (when
+ * timing is on) device time per phase from CUDA events recorded around each
+ * phase on the caller's stream. */
+typedef struct md_profile {
+    int64_t launches;                 /* kernels launched (graph replays included) */
+    double ms[MD_PHASE_COUNT];        /* summed event time per phase, ms */
+    int64_t timed[MD_PHASE_COUNT];    /* timed launches per phase */
+} md_profile;
+
+/* Resets the counters. timing != 0 records events around every phase (and
+ * disables CUDA-graph replay while on); timing == 0 only counts launches. */
+MD_API int md_profile_start(md_batch* h, int timing);
+
+/* Reads the counters (synchronizes the device). */
+MD_API int md_profile_read(md_batch* h, md_profile* out);
+
+/* Diagnostics: evaluates the library's float64 elementary functions on n
+ * values x [n] (device) into out [n] (device): fn 0 = table-driven e^x
+ * (arguments |x| < 700), 1 = CUDA exp(x), 2 = 1/sqrt(x) by the library's
+ * float32 estimate plus one third-order Newton step (x > 0), 3 = CUDA
+ * rsqrt(x). Lets a caller bound the error of the hot-path functions.
+ * MD_ERR_ARG for an unknown fn or non-device pointers. */
+MD_API int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double* out, md_stream stream);
+
 /* ---------------------------------------------------------------- errors */
 
 MD_API const char* md_status_string(int status);

@@ -97,6 +97,13 @@ int check_potential(const md_potential* p, std::string& why) {
             return why = "r_cut must be positive and finite", MD_ERR_ARG;
         if (p->kind == MD_POT_RGL && !(p->p[4] > 0.0)) return why = "RGL r0 must be positive", MD_ERR_ARG;
         if (p->kind == MD_POT_SC && !(p->p[2] > 0.0)) return why = "Sutton-Chen a must be positive", MD_ERR_ARG;
+        if (p->kind == MD_POT_RGL) {
+            // exponent arguments p - p r/r0 and 2q - 2q r/r0 over 0 <= r < r_cut
+            double pp = p->p[2], q2 = 2.0 * p->p[3], r0 = p->p[4], rc = p->r_cut;
+            double lo = std::min({pp, pp - pp / r0 * rc, q2, q2 - q2 / r0 * rc});
+            double hi = std::max({pp, pp - pp / r0 * rc, q2, q2 - q2 / r0 * rc});
+            if (!(lo > -700.0 && hi < 700.0)) return why = "RGL exponents out of range (|arg| >= 700)", MD_ERR_ARG;
+        }
         return MD_OK;
     }
     if (p->kind == MD_POT_SPLINE) {
@@ -159,6 +166,8 @@ void fill_pot(Engine& e) {
         P.m = p.p[4];
         P.F_scale = p.p[1] * p.p[0];
     }
+    P.ek = e.exp_const;
+    P.exp_T = e.exp_T;
     P.f_rc2 = (float)P.rc2;
     P.f_rs = (float)P.rs;
     P.f_inv_w = (float)P.inv_w;
@@ -195,8 +204,10 @@ void free_engine(Engine& e) {
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
     dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
-    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.stage); dfree(e.red);
+    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.ab); dfree(e.exp_T); dfree(e.stage); dfree(e.red);
     dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl);
+    for (cudaEvent_t ev : e.ev_pool) cudaEventDestroy(ev);
+    e.ev_pool.clear();
     if (e.ctl_host) cudaFreeHost(e.ctl_host);
     e.ctl_host = nullptr;
 }
@@ -365,7 +376,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.Fp, Np);
     AL(e.Fpf, Np);
     AL(e.e_atom, Np);
-    if (cfg->precision == MD_MIXED) AL(e.xo, Np);
+    AL(e.xo, Np);
     AL(e.perm, Np);
     AL(e.perm_alt, Np);
     AL(e.iperm, Np);
@@ -378,6 +389,8 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.scan_tmp, tot / 1024 + 2);
     AL(e.nn, Np);
     AL(e.nl, (size_t)e.max_nb * Np);
+    if (cfg->precision == MD_FP64) AL(e.ab, (size_t)e.max_nb * Np);
+    AL(e.exp_T, kExpTable);
     AL(e.stage, 3 * std::max<size_t>(e.N, 1));
     AL(e.red, 2 * std::max(e.n_chunks, 1));
     AL(e.thermo_dev, 4 * (B + 1));
@@ -409,6 +422,16 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
             ce = ce != cudaSuccess ? ce : up(e.chunk_hi, chi.data(), chi.size() * sizeof(int64_t));
         }
         ce = ce != cudaSuccess ? ce : up(e.box_chunk_off, bco.data(), (B + 1) * sizeof(int));
+        {
+            // exponential table and reduction constants (long-double host arithmetic)
+            std::vector<double> T(kExpTable);
+            for (int j = 0; j < kExpTable; ++j) T[j] = (double)exp2l((long double)j / kExpTable);
+            long double ln2 = logl(2.0L);
+            e.exp_const.inv_l = (double)((long double)kExpTable / ln2);
+            e.exp_const.l1 = (double)(ln2 / kExpTable);
+            e.exp_const.l2 = (double)(ln2 / kExpTable - (long double)e.exp_const.l1);
+            ce = ce != cudaSuccess ? ce : up(e.exp_T, T.data(), kExpTable * sizeof(double));
+        }
         if (ce == cudaSuccess) ce = cudaMemset(e.cell_count, 0, tot * sizeof(int));
         if (ce == cudaSuccess) ce = cudaMemset(e.v, 0, 3 * Np * sizeof(double));
         if (ce == cudaSuccess) ce = cudaMemset(e.f, 0, 3 * Np * sizeof(double));
@@ -485,6 +508,15 @@ int grow_list(Engine* E, int needed) {
     m = (m + 7) / 8 * 8;
     int* nl = nullptr;
     if (dalloc(E, &nl, (size_t)m * e.N_pad) != MD_OK) return MD_ERR_NOMEM;
+    if (e.ab) {
+        double2* ab = nullptr;
+        if (dalloc(E, &ab, (size_t)m * e.N_pad) != MD_OK) {
+            cudaFree(nl);
+            return MD_ERR_NOMEM;
+        }
+        cudaFree(e.ab);
+        e.ab = ab;
+    }
     cudaFree(e.nl);
     e.nl = nl;
     e.max_nb = m;
@@ -565,12 +597,15 @@ void enqueue_step(Engine& e, bool hist, cudaStream_t s) {
     launch_end_step(e, hist ? 1 : 0, s);
 }
 
-int capture(md_batch* h, int steps, bool hist, cudaGraphExec_t* out) {
+int capture(md_batch* h, int steps, bool hist, cudaGraphExec_t* out, long long* kernels) {
     Engine* E = &h->e;
     cudaGraph_t g = nullptr;
+    long long before = E->launches;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < steps; ++k) enqueue_step(h->e, hist, h->cap_stream);
     cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+    *kernels = E->launches - before;
+    E->launches = before;
     if (ce != cudaSuccess) return fail(E, MD_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
     ce = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
@@ -583,7 +618,7 @@ constexpr int kGraphChunk = 8;
 int enqueue_steps(md_batch* h, int n, bool hist, bool use_graph, cudaStream_t s) {
     Engine* E = &h->e;
     Engine& e = *E;
-    if (!use_graph || e.N == 0) {
+    if (!use_graph || e.N == 0 || e.prof_timing) {
         for (int k = 0; k < n; ++k) enqueue_step(e, hist, s);
         CK(cudaGetLastError());
         return MD_OK;
@@ -591,10 +626,19 @@ int enqueue_steps(md_batch* h, int n, bool hist, bool use_graph, cudaStream_t s)
     if (e.graph_hist != hist) destroy_graphs(e);
     e.graph_hist = hist;
     int rc;
-    if (n >= kGraphChunk && !e.graph_chunk && (rc = capture(h, kGraphChunk, hist, &e.graph_chunk))) return rc;
-    if (n % kGraphChunk && !e.graph_step && (rc = capture(h, 1, hist, &e.graph_step))) return rc;
-    for (int k = 0; k < n / kGraphChunk; ++k) CK(cudaGraphLaunch(e.graph_chunk, s));
-    for (int k = 0; k < n % kGraphChunk; ++k) CK(cudaGraphLaunch(e.graph_step, s));
+    if (n >= kGraphChunk && !e.graph_chunk &&
+        (rc = capture(h, kGraphChunk, hist, &e.graph_chunk, &e.graph_chunk_kernels)))
+        return rc;
+    if (n % kGraphChunk && !e.graph_step && (rc = capture(h, 1, hist, &e.graph_step, &e.graph_step_kernels)))
+        return rc;
+    for (int k = 0; k < n / kGraphChunk; ++k) {
+        CK(cudaGraphLaunch(e.graph_chunk, s));
+        e.launches += e.graph_chunk_kernels;
+    }
+    for (int k = 0; k < n % kGraphChunk; ++k) {
+        CK(cudaGraphLaunch(e.graph_step, s));
+        e.launches += e.graph_step_kernels;
+    }
     return MD_OK;
 }
 
@@ -940,6 +984,41 @@ int md_num_params(const md_batch* b) {
     if (!b) return -1;
     const md_potential& p = b->e.pot_host;
     return p.kind == MD_POT_SPLINE ? p.n_phi + p.n_f + p.n_F : 5;
+}
+
+int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double* out, md_stream st) {
+    if (!h) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    if (fn < 0 || fn > 3) return fail(E, MD_ERR_ARG, "unknown function");
+    if (n < 0) return fail(E, MD_ERR_ARG, "n must be >= 0");
+    if (n > 0 && (!is_device_ptr(x) || !is_device_ptr(out))) return fail(E, MD_ERR_ARG, "x and out must be device pointers");
+    launch_eval_math(*E, fn, x, n, out, (cudaStream_t)st);
+    CK(cudaGetLastError());
+    return MD_OK;
+}
+
+int md_profile_start(md_batch* h, int timing) {
+    if (!h) return MD_ERR_ARG;
+    h->e.launches = 0;
+    h->e.ev_used = 0;
+    h->e.prof_timing = timing != 0;
+    return MD_OK;
+}
+
+int md_profile_read(md_batch* h, md_profile* out) {
+    if (!h || !out) return MD_ERR_ARG;
+    Engine* E = &h->e;
+    CK(cudaDeviceSynchronize());
+    memset(out, 0, sizeof(*out));
+    out->launches = E->launches;
+    for (size_t k = 0; k < E->ev_used; ++k) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, E->ev_pool[2 * k], E->ev_pool[2 * k + 1]));
+        int ph = E->ev_phase[k];
+        out->ms[ph] += ms;
+        out->timed[ph] += 1;
+    }
+    return MD_OK;
 }
 
 const char* md_status_string(int st) {

@@ -178,8 +178,9 @@ __global__ void k_permute(int64_t N, int64_t Np, const int* __restrict__ src, co
     cell_t_alt[t] = cell_of[s];
 }
 
-// Mixed precision: float32 offset of each atom from the origin of the cell
-// it was binned into (minimum image), w = packed cell coordinates.
+// Float32 offset of each atom from the origin of the cell it was binned
+// into (minimum image), w = packed cell coordinates: the list build's
+// prefilter and the mixed-precision pair math use it.
 __device__ __forceinline__ float4 cell_local(const Geo& g, int b, int gc, double4_32a p) {
     int xyz = g.cell_xyz[gc];
     int c[3] = {xyz & 1023, (xyz >> 10) & 1023, (xyz >> 20) & 1023};
@@ -230,6 +231,8 @@ static unsigned long long disp_threshold(const Engine& e) {
 
 void launch_rebuild(Engine& e, int mode, cudaStream_t s) {
     if (e.N == 0) return;
+    PhaseScope scope(e, MD_PHASE_REBUILD, s);
+    e.launches += 8;
     Geo g = make_geo(e);
     unsigned long long thr = disp_threshold(e);
     const int nt = 256;
@@ -247,7 +250,7 @@ void launch_rebuild(Engine& e, int mode, cudaStream_t s) {
                                       e.cell_of, e.cell_t_alt, e.ctl, mode, thr);
     k_copy_back<<<nb_atoms, nt, 0, s>>>(e.N, e.N_pad, g, e.x, e.x_alt, e.xb, e.v, e.v_alt, e.perm, e.perm_alt,
                                         e.iperm, e.cell_t, e.cell_t_alt,
-                                        e.cfg.precision == MD_MIXED ? e.xo : nullptr, e.ctl, mode, thr);
+                                        e.xo, e.ctl, mode, thr);
     launch_build_list(e, mode, s);
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "md_engine.cuh"
+#include "md_math.cuh"
 
 namespace mdk {
 
@@ -27,6 +28,19 @@ __device__ __forceinline__ double wrap_coord(double x, double L) {
     double y = __dsub_rn(x, __dmul_rn(L, k));
     if (y >= L) y = __dsub_rn(y, L);
     return y;
+}
+
+// The same result as wrap_coord without a division when -L <= x < 2L (one
+// step of drift): for x in [L, 2L) the rule gives x - L (exact), for x in
+// [-L, 0) it gives x + L, then -L if that rounded to L.
+__device__ __forceinline__ double wrap_step(double x, double L) {
+    if (x >= 0.0 && x < L) return x;
+    if (x >= L && x < 2.0 * L) return x - L;
+    if (x < 0.0 && x >= -L) {
+        double y = x + L;
+        return y >= L ? y - L : y;
+    }
+    return wrap_coord(x, L);
 }
 
 __device__ __forceinline__ int load_status(const Ctl* c) {
@@ -88,56 +102,49 @@ __device__ __forceinline__ double powr(double b, double e) {
     return pow(b, e);
 }
 
-// density function rho(r) only (r < rc)
+// Pair functions at r^2 < rc^2: V(r), rho(r), and A = V'(r)/r, B = rho'(r)/r
+// (the force pass needs only these two ratios). T: the exponential table in
+// shared memory.
 template <int KIND>
-__device__ __forceinline__ double dens_f(const Pot& P, double r) {
+__device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict__ T, double r2, double& phi,
+                                          double& fr, double& A, double& B) {
+    double rinv = rsqrt_nr(r2);
+    double r = r2 * rinv;
     if (KIND == MD_POT_RGL) {
         double S, dS;
         taper(P, r, S, dS);
-        return P.xi2 * exp(P.q2 - P.q2_r0 * r) * S;
-    } else if (KIND == MD_POT_SC) {
-        double S, dS;
-        taper(P, r, S, dS);
-        return powr(P.a / r, P.m) * S;
-    } else {
-        if (r >= P.rc) return 0.0;
-        double v, dv;
-        spline_eval(P, 1, r, v, dv);
-        return v;
-    }
-}
-
-// V, V', rho, rho' at r < rc
-template <int KIND>
-__device__ __forceinline__ void pair_all(const Pot& P, double r, double& phi, double& dphi, double& fr,
-                                         double& dfr) {
-    if (KIND == MD_POT_RGL) {
-        double S, dS;
-        taper(P, r, S, dS);
-        double e1 = P.A2 * exp(P.p - P.p_r0 * r);
-        double e2 = P.xi2 * exp(P.q2 - P.q2_r0 * r);
+        double e1 = P.A2 * exp_tab(P.p - P.p_r0 * r, T, P.ek);
+        double e2 = P.xi2 * exp_tab(P.q2 - P.q2_r0 * r, T, P.ek);
         phi = e1 * S;
-        dphi = e1 * (dS - P.p_r0 * S);
         fr = e2 * S;
-        dfr = e2 * (dS - P.q2_r0 * S);
+        A = e1 * (dS - P.p_r0 * S) * rinv;
+        B = e2 * (dS - P.q2_r0 * S) * rinv;
     } else if (KIND == MD_POT_SC) {
         double S, dS;
         taper(P, r, S, dS);
-        double rinv = 1.0 / r;
         double ar = P.a * rinv;
         double an = P.eps * powr(ar, P.n), am = powr(ar, P.m);
         phi = an * S;
-        dphi = an * (dS - P.n * rinv * S);
         fr = am * S;
-        dfr = am * (dS - P.m * rinv * S);
+        A = an * (dS - P.n * rinv * S) * rinv;
+        B = am * (dS - P.m * rinv * S) * rinv;
     } else {
         if (r >= P.rc) {
-            phi = dphi = fr = dfr = 0.0;
+            phi = fr = A = B = 0.0;
             return;
         }
+        double dphi, dfr;
         spline_eval(P, 0, r, phi, dphi);
         spline_eval(P, 1, r, fr, dfr);
+        A = dphi * rinv;
+        B = dfr * rinv;
     }
+}
+
+// Loads the exponential table into shared memory (whole block).
+__device__ __forceinline__ void load_exp_table(double* sT, const double* __restrict__ gT) {
+    for (int k = threadIdx.x; k < kExpTable; k += blockDim.x) sT[k] = gT[k];
+    __syncthreads();
 }
 
 // F(rho) and F'(rho); F = F' = 0 for rho <= 0 (RGL, SC)

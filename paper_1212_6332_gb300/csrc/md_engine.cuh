@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "md.h"
+#include "md_math.cuh"
 
 namespace mdk {
 
@@ -39,6 +40,9 @@ struct Pot {
     const double4_32a* sp[3];
     int sn[3];
     double st0[3], sh[3], sinvh[3];
+    // table-driven exponential (float64 path)
+    ExpConst ek;
+    const double* exp_T;  // [kExpTable] 2^(j/256)
     // float copies for the mixed-precision path
     float f_rc2, f_rs, f_inv_w, f_A2, f_xi2, f_p, f_p_r0, f_q2, f_q2_r0, f_eps, f_a, f_n, f_m;
 };
@@ -132,6 +136,9 @@ struct Engine {
     int* scan_tmp = nullptr;
     int* nn = nullptr;          // [N_pad]
     int* nl = nullptr;          // [max_nb][N_pad] column-major
+    double2* ab = nullptr;      // float64 path: [max_nb][N_pad] (V'/r, rho'/r) per list entry
+    double* exp_T = nullptr;    // exponential table
+    ExpConst exp_const{};
     double* stage = nullptr;    // [3N] staging for host copies / caller-order outputs
     double* red = nullptr;      // reduction scratch [2 * n_chunks]
     double* thermo_dev = nullptr;  // [B][4] + [4] totals
@@ -147,6 +154,44 @@ struct Engine {
     int graph_chunk_len = 0;
     bool graph_hist = false;
     int sched_choice = 0;  // autotuner result for batches (0 = unknown)
+    long long graph_chunk_kernels = 0, graph_step_kernels = 0;
+
+    // profiling: launch counter and phase events
+    long long launches = 0;
+    bool prof_timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_phase;
+    size_t ev_used = 0;  // pairs in use
+};
+
+// Records a start event for `phase` when timing is on; returns the pair index.
+inline int prof_begin(Engine& e, int phase, cudaStream_t s) {
+    if (!e.prof_timing) return -1;
+    if (2 * (e.ev_used + 1) > e.ev_pool.size()) {
+        for (int k = 0; k < 2; ++k) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) return -1;
+            e.ev_pool.push_back(ev);
+        }
+    }
+    int idx = (int)e.ev_used++;
+    if (e.ev_phase.size() <= (size_t)idx) e.ev_phase.resize(idx + 1);
+    e.ev_phase[idx] = phase;
+    cudaEventRecord(e.ev_pool[2 * idx], s);
+    return idx;
+}
+
+inline void prof_end(Engine& e, int idx, cudaStream_t s) {
+    if (idx >= 0) cudaEventRecord(e.ev_pool[2 * idx + 1], s);
+}
+
+// Scope guard: events around the launches of one phase.
+struct PhaseScope {
+    Engine& e;
+    cudaStream_t s;
+    int idx;
+    PhaseScope(Engine& e_, int phase, cudaStream_t s_) : e(e_), s(s_), idx(prof_begin(e_, phase, s_)) {}
+    ~PhaseScope() { prof_end(e, idx, s); }
 };
 
 Geo make_geo(const Engine& e);
@@ -174,6 +219,7 @@ void launch_store_scalar(Engine& e, const double* src_sorted, double* dst_caller
 void launch_get_neighbors(Engine& e, int32_t* nn_out, int32_t* nl_out, int32_t ld, cudaStream_t s);
 void launch_box_energy(Engine& e, double* e_box_dev, cudaStream_t s);
 void launch_reset_perm(Engine& e, cudaStream_t s);
+void launch_eval_math(Engine& e, int fn, const double* x, int64_t n, double* out, cudaStream_t s);
 // batched block-per-box schedule
 int launch_box_steps(Engine& e, int n_steps, cudaStream_t s);
 bool box_schedule_fits(const Engine& e);

@@ -34,9 +34,9 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
         double vx = v[i] + c_kick * f[i];
         double vy = v[Np + i] + c_kick * f[Np + i];
         double vz = v[2 * Np + i] + c_kick * f[2 * Np + i];
-        p.x = wrap_coord(p.x + dt * vx, L[0]);
-        p.y = wrap_coord(p.y + dt * vy, L[1]);
-        p.z = wrap_coord(p.z + dt * vz, L[2]);
+        p.x = wrap_step(p.x + dt * vx, L[0]);
+        p.y = wrap_step(p.y + dt * vy, L[1]);
+        p.z = wrap_step(p.z + dt * vz, L[2]);
         v[i] = vx;
         v[Np + i] = vy;
         v[2 * Np + i] = vz;
@@ -162,6 +162,8 @@ static void kick_drift_t(Engine& e, cudaStream_t s) {
     Geo g = make_geo(e);
     int nb = (int)((e.N + kINT - 1) / kINT);
     double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
+    PhaseScope scope(e, MD_PHASE_KICK_DRIFT, s);
+    e.launches += 1;
     k_kick_drift<SINGLE, MIXED><<<nb, kINT, 0, s>>>(e.N, e.N_pad, g, e.x, e.v, e.f, e.xb, c_kick, e.cfg.dt, e.xo,
                                                    e.cell_t, e.ctl);
 }
@@ -177,10 +179,14 @@ void launch_kick_drift(Engine& e, cudaStream_t s) {
 
 void launch_end_step(Engine& e, int record_hist, cudaStream_t s) {
     if (record_hist) launch_thermo_hist(e, s);
+    PhaseScope scope(e, MD_PHASE_OTHER, s);
+    e.launches += 1;
     k_end_step<<<1, 1, 0, s>>>(e.ctl);
 }
 
 static void thermo_impl(Engine& e, bool hist, cudaStream_t s) {
+    PhaseScope scope(e, MD_PHASE_OTHER, s);
+    e.launches += e.n_chunks > 0 ? 2 : 1;
     if (e.n_chunks > 0)
         k_chunk_sums<<<e.n_chunks, kRNT, 0, s>>>(e.N_pad, e.chunk_lo, e.chunk_hi, e.v, e.e_atom, e.red);
     double half_mv = 0.5 * e.cfg.mass * kMVV;
@@ -191,7 +197,10 @@ static void thermo_impl(Engine& e, bool hist, cudaStream_t s) {
 void launch_thermo(Engine& e, cudaStream_t s) { thermo_impl(e, false, s); }
 void launch_thermo_hist(Engine& e, cudaStream_t s) { thermo_impl(e, true, s); }
 
-void launch_reset_ctl(Engine& e, cudaStream_t s) { k_reset_ctl<<<1, 1, 0, s>>>(e.ctl); }
+void launch_reset_ctl(Engine& e, cudaStream_t s) {
+    e.launches += 1;
+    k_reset_ctl<<<1, 1, 0, s>>>(e.ctl);
+}
 
 // ---------------------------------------------------------------- copies
 
@@ -271,36 +280,66 @@ static int nblk(int64_t n, int nt) { return (int)((n + nt - 1) / nt); }
 
 void launch_load_positions(Engine& e, const double* src, cudaStream_t s) {
     if (e.N == 0) return;
+    e.launches += 1;
     k_load_pos<<<nblk(e.N, 256), 256, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x);
 }
 
 void launch_load_velocities(Engine& e, const double* src, cudaStream_t s) {
     if (e.N == 0) return;
+    e.launches += 1;
     k_load_vel<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, src, e.iperm, e.v);
 }
 
 void launch_store_vec(Engine& e, const double* soa, const double4_32a* x4, double* dst, cudaStream_t s) {
     if (e.N == 0) return;
+    e.launches += 1;
     k_store_vec<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, soa, x4, e.perm, dst);
 }
 
 void launch_store_scalar(Engine& e, const double* src, double* dst, cudaStream_t s) {
     if (e.N == 0) return;
+    e.launches += 1;
     k_store_scalar<<<nblk(e.N, 256), 256, 0, s>>>(e.N, src, e.perm, dst);
 }
 
 void launch_get_neighbors(Engine& e, int32_t* nn_out, int32_t* nl_out, int32_t ld, cudaStream_t s) {
     if (e.N == 0) return;
+    e.launches += 1;
     k_get_neighbors<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, e.nn, e.nl, e.max_nb, e.perm, nn_out, nl_out, ld);
 }
 
 void launch_box_energy(Engine& e, double* e_box, cudaStream_t s) {
+    e.launches += 1;
     k_box_energy<<<nblk(e.B, 256), 256, 0, s>>>(e.B, e.thermo_dev, e_box);
 }
 
 void launch_reset_perm(Engine& e, cudaStream_t s) {
     if (e.N == 0) return;
+    e.launches += 1;
     k_reset_perm<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.perm, e.iperm);
+}
+
+// ---------------------------------------------------------------- diagnostics
+
+__global__ void k_eval_math(int fn, const double* __restrict__ x, int64_t n, double* __restrict__ out,
+                            const double* __restrict__ gT, ExpConst K) {
+    __shared__ double sT[kExpTable];
+    load_exp_table(sT, gT);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = x[i];
+    switch (fn) {
+        case 0: out[i] = exp_tab(v, sT, K); break;
+        case 1: out[i] = exp(v); break;
+        case 2: out[i] = rsqrt_nr(v); break;
+        default: out[i] = rsqrt(v); break;
+    }
+}
+
+void launch_eval_math(Engine& e, int fn, const double* x, int64_t n, double* out, cudaStream_t s) {
+    if (n <= 0) return;
+    e.launches += 1;
+    k_eval_math<<<nblk(n, 256), 256, 0, s>>>(fn, x, n, out, e.exp_T, e.exp_const);
 }
 
 // ---------------------------------------------------------------- splines
@@ -344,6 +383,7 @@ __global__ void k_spline_setup(const double* __restrict__ y_all, double* __restr
 
 void launch_spline_setup(Engine& e, cudaStream_t s) {
     const md_potential& p = e.pot_host;
+    e.launches += 1;
     k_spline_setup<<<1, 32, 0, s>>>(e.knots_dev, e.spline_work, e.spline_coef, p.n_phi, p.n_f, p.n_F,
                                     e.pot.sh[0], e.pot.sh[1], e.pot.sh[2]);
 }

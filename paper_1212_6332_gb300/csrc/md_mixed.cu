@@ -149,8 +149,13 @@ static void run_mixed(Engine& e, int kick, cudaStream_t s) {
     }
     int nb = (int)((e.N + kMNT - 1) / kMNT);
     double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
-    k_density_mixed<KIND, SINGLE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.rho,
-                                                     e.Fp, e.Fpf, e.e_atom, e.ctl);
+    e.launches += 2;
+    {
+        PhaseScope scope(e, MD_PHASE_DENSITY, s);
+        k_density_mixed<KIND, SINGLE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb,
+                                                         e.rho, e.Fp, e.Fpf, e.e_atom, e.ctl);
+    }
+    PhaseScope scope(e, MD_PHASE_FORCE, s);
     k_force_mixed<KIND, SINGLE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.Fpf,
                                                    e.f, e.e_atom, kick ? e.v : nullptr, c_kick, e.ctl);
 }

@@ -26,7 +26,9 @@ SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_
            "md_max_count", "md_compute_forces", "md_get_forces", "md_step", "md_get_thermo", "md_batch_create",
            "md_batch_destroy", "md_batch_set_state", "md_batch_get_state", "md_batch_compute_forces",
            "md_batch_step", "md_batch_set_potential", "md_param_grad", "md_num_params", "md_status_string",
-           "md_last_error")
+           "md_last_error", "md_profile_start", "md_profile_read",
+           "md_eval_math")
+PHASES = ("kick_drift", "rebuild", "density", "force", "other")
 
 
 class MDError(RuntimeError):
@@ -54,6 +56,10 @@ class Thermo(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double * 5), ("timed", ctypes.c_int64 * 5)]
 
 
 _lib = None
@@ -93,6 +99,9 @@ def load(path: str | pathlib.Path | None = None) -> ctypes.CDLL:
         "md_num_params": [vp],
         "md_status_string": [i32],
         "md_last_error": [vp],
+        "md_profile_start": [vp, i32],
+        "md_profile_read": [vp, P(Profile)],
+        "md_eval_math": [vp, i32, dp, i64, dp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -299,6 +308,24 @@ class System:
     @property
     def n_params(self) -> int:
         return self.lib.md_num_params(self._h)
+
+    def profile_start(self, timing: bool = False):
+        self._check(self.lib.md_profile_start(self._h, int(timing)))
+
+    def profile_read(self) -> dict:
+        p = Profile()
+        self._check(self.lib.md_profile_read(self._h, ctypes.byref(p)))
+        return dict(launches=p.launches, ms={PHASES[k]: p.ms[k] for k in range(5)},
+                    timed={PHASES[k]: p.timed[k] for k in range(5)})
+
+    def eval_math(self, fn: str, x):
+        """The library's float64 functions on a CUDA tensor: fn in
+        {"exp", "exp_ref", "rsqrt", "rsqrt_ref"}."""
+        code = {"exp": 0, "exp_ref": 1, "rsqrt": 2, "rsqrt_ref": 3}[fn]
+        x = x.contiguous()
+        out = self._empty(x.numel())
+        self._check(self.lib.md_eval_math(self._h, code, _ptr(x), x.numel(), _ptr(out), _stream()))
+        return out
 
     def param_grad(self, g_f, g_e, grad=None):
         grad = grad if grad is not None else self._empty(self.n_params)
