@@ -278,6 +278,37 @@ MD_API int md_profile_read(md_batch* h, md_profile* out);
  * MD_ERR_ARG for an unknown fn or non-device pointers. */
 MD_API int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double* out, md_stream stream);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/* Largest atom count md_forces_noalloc accepts. */
+#define MD_NOALLOC_MAX_ATOMS 16384
+
+/* Forces and energies of one small periodic box without allocating any
+ * device memory. The paper has no counterpart: this exists for callers that
+ * cannot call cudaMalloc, such as plug-ins whose host application owns all
+ * device memory through its own pool or memory cap, and latency-bound loops
+ * that must not enter the driver's allocator (it can synchronize the device
+ * and take unbounded time).
+ * The caller passes x [n][3] (device), f [n][3] (device) and, optionally,
+ * e_atom [n] and e_total [1] (device; NULL skips them); box [3] is a host
+ * array; pot must be RGL or Sutton-Chen (MD_ERR_UNSUPPORTED otherwise).
+ * Results are those of md_compute_forces (Eq. 1-3) computed by an all-pairs
+ * minimum-image loop, O(n^2) per call, no cells and no list.
+ * Working memory is one file-scope device array of 2 * MD_NOALLOC_MAX_ATOMS
+ * doubles (256 KiB) that every GPU loading the library holds until the
+ * process exits. The first call on a device looks up that array's device
+ * address with the device current; make that first call before any stream
+ * capture. All calls share the array and each call overwrites the entries
+ * it reads before reading them, so nothing needs clearing between calls;
+ * calls that overlap on the GPU (for example on two streams) race on it and
+ * must be serialized by the caller.
+ * Errors: MD_ERR_ARG (n_atoms > MD_NOALLOC_MAX_ATOMS or < 0, a box length not
+ * above 2 r_cut, non-device x/f/e_atom/e_total), MD_ERR_UNSUPPORTED,
+ * MD_ERR_CUDA. Asynchronous: outputs are valid once `stream` reaches the
+ * call. */
+MD_API int md_forces_noalloc(const md_potential* pot, const double* box, int64_t n_atoms, const double* x,
+                             double* f, double* e_atom, double* e_total, md_stream stream);
+
 /* ---------------------------------------------------------------- errors */
 
 MD_API const char* md_status_string(int status);

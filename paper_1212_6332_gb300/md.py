@@ -27,7 +27,8 @@ SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_
            "md_batch_destroy", "md_batch_set_state", "md_batch_get_state", "md_batch_compute_forces",
            "md_batch_step", "md_batch_set_potential", "md_param_grad", "md_num_params", "md_status_string",
            "md_last_error", "md_profile_start", "md_profile_read",
-           "md_eval_math")
+           "md_eval_math", "md_forces_noalloc")
+NOALLOC_MAX_ATOMS = 16384
 PHASES = ("kick_drift", "rebuild", "density", "force", "other")
 
 
@@ -102,6 +103,7 @@ def load(path: str | pathlib.Path | None = None) -> ctypes.CDLL:
         "md_profile_start": [vp, i32],
         "md_profile_read": [vp, P(Profile)],
         "md_eval_math": [vp, i32, dp, i64, dp, vp],
+        "md_forces_noalloc": [P(Potential), dp, i64, dp, dp, dp, dp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -331,3 +333,23 @@ class System:
         grad = grad if grad is not None else self._empty(self.n_params)
         self._check(self.lib.md_param_grad(self._h, _ptr(g_f), _ptr(g_e), _ptr(grad), _stream()))
         return grad
+
+
+def forces_noalloc(potential: dict, box, x, f=None, e_atom=None, e_total=None):
+    """md_forces_noalloc: forces of one small box (at most NOALLOC_MAX_ATOMS
+    atoms) with no device allocation inside the library. x is a [n, 3]
+    float64 CUDA tensor; outputs are CUDA tensors (allocated here by torch
+    unless given)."""
+    torch = _torch()
+    lib = load()
+    n = x.shape[0]
+    f = f if f is not None else torch.empty((n, 3), dtype=torch.float64, device=x.device)
+    e_atom = e_atom if e_atom is not None else torch.empty(n, dtype=torch.float64, device=x.device)
+    e_total = e_total if e_total is not None else torch.empty(1, dtype=torch.float64, device=x.device)
+    pot, keep = potential_struct(potential)
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    rc = lib.md_forces_noalloc(ctypes.byref(pot), ctypes.c_void_p(b.ctypes.data), n, _ptr(x), _ptr(f),
+                               _ptr(e_atom), _ptr(e_total), _stream())
+    if rc != 0:
+        raise MDError(rc, "md_forces_noalloc failed")
+    return dict(f=f, e_atom=e_atom, energy=e_total)
