@@ -219,6 +219,126 @@ def run_variant(precision: str, W: int, K: int, x_h, v_h, box):
     return dict(value=len(x_h) * K / (ms * 1e-3), ms_per_step=ms / K, n_rebuild=th["n_rebuild"])
 
 
+def run_batch(precision: str, K: int, W: int, n_boxes: int = 4096, use_graph: bool = True,
+              schedule: str = "tile") -> dict:
+    """The 4096-box batch (n ~ U{3..10} fcc Cu repeats, T ~ U(300, 1500) K,
+    RGL Cu): all boxes advance together, one launch per phase (graph-replayed)."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bt = I.batch_of_boxes(n_boxes, I.A_CU, I.MASS_CU, seed=2024)
+    s = System(I.RGL_CU, boxes=bt.box, atom_offsets=bt.atom_offsets, skin=SKIN, dt=DT, mass=I.MASS_CU,
+               precision=precision)
+    s.set_state(torch.tensor(bt.x, device="cuda"), torch.tensor(bt.v, device="cuda"))
+    s.batch_step(W, schedule=schedule, use_graph=use_graph, per_box=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    s.batch_step(K, schedule=schedule, use_graph=use_graph, per_box=False)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    n = int(bt.atom_offsets[-1])
+    s.close()
+    return dict(value=n * K / (ms * 1e-3), ms_per_step=ms / K, atoms=n, boxes=n_boxes, schedule=schedule,
+                graph=use_graph and schedule == "tile")
+
+
+def run_per_box_sample(K: int, n_sample: int = 64, n_boxes: int = 4096) -> dict:
+    """One launch sequence per box: the first n_sample boxes of the same
+    batch, each in its own single-box context stepped on its own,
+    extrapolated to all boxes by atom count."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bt = I.batch_of_boxes(n_boxes, I.A_CU, I.MASS_CU, seed=2024)
+    systems = []
+    for k in range(n_sample):
+        lo, hi = int(bt.atom_offsets[k]), int(bt.atom_offsets[k + 1])
+        s = System(I.RGL_CU, box=bt.box[k], n_atoms=hi - lo, skin=SKIN, dt=DT, mass=I.MASS_CU)
+        s.set_state(torch.tensor(bt.x[lo:hi], device="cuda"), torch.tensor(bt.v[lo:hi], device="cuda"))
+        s.step(2)
+        systems.append(s)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in systems:
+        s.step(K)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    n_s = int(bt.atom_offsets[n_sample])
+    for s in systems:
+        s.close()
+    return dict(value=n_s * K / dt, sample_boxes=n_sample, sample_atoms=n_s,
+                note="each box its own context and launch sequence; rate extrapolates to any box count")
+
+
+def run_grad(K: int, W: int, precision: str = "fp64", kind: str = "rgl") -> dict:
+    """Force-matching loss + gradient over 256 configurations of 864 atoms
+    (6^3 fcc Cu, strain U(0.98, 1.02), N(0, 0.1 A) displacements); targets
+    from RGL Cu at the reference parameters, model RGL perturbed by 5%
+    (or its 3 x 200-knot spline tabulation)."""
+    import torch
+    from paper_1212_6332_gb300.fit import ForceField, force_matching_loss, make_batch, theta_of
+    cfgs = [I.strained_fcc(6, I.A_CU, seed=5000 + k) for k in range(256)]
+    ref = make_batch(I.RGL_CU, cfgs)
+    f_tgt = ref.get_forces()["f"].clone()
+    e_tgt = ref.batch_thermo()[:, 1].clone()
+    ref.close()
+    signs = np.where(I.uniform(77, 5) < 0.5, -1.0, 1.0)
+    model = dict(I.RGL_CU, **{k: I.RGL_CU[k] * (1 + 0.05 * sg) for k, sg in zip(("A", "xi", "p", "q", "r0"), signs)})
+    if kind == "spline":
+        model = spline_model(model)
+    s = make_batch(model, cfgs, precision=precision)
+    counts = torch.tensor([c.n for c in cfgs], device="cuda", dtype=torch.float64)
+    theta = theta_of(model).cuda().requires_grad_(True)
+
+    def once():
+        f, e = ForceField.apply(theta, s, model)
+        L = force_matching_loss(f, e, f_tgt, e_tgt, counts)
+        (g,) = torch.autograd.grad(L, theta)
+        return L, g
+
+    for _ in range(W):
+        once()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        L, g = once()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    n = sum(c.n for c in cfgs)
+    s.close()
+    return dict(value=K / dt, unit="(loss + gradient over 256 configs)/s", atom_grads_per_s=n * K / dt,
+                n_params=int(theta.numel()), loss=float(L.item()), precision=precision, model=kind)
+
+
+def spline_model(spec: dict) -> dict:
+    """Spline model tabulated from an RGL potential by the library itself
+    (md_eval of V, rho on 200 knots over [1.5, 5.0] A and F on 200 knots over
+    [0, 2 rho_eq])."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    x, box = I.fcc_lattice(6, I.A_CU)
+    s = System(spec, box=box, n_atoms=len(x), skin=0.0, mass=I.MASS_CU)
+    rho_eq = float(s.compute_forces(torch.tensor(x, device="cuda"))["rho"].mean().item())
+    s.close()
+    r = np.linspace(1.5, 5.0, 200)
+    pair = np.zeros((2, 200))
+    # V(r) and rho(r) from a two-atom box at each knot (the library's own evaluation)
+    d = System(spec, box=[20.0, 20.0, 20.0], n_atoms=2, skin=0.0, mass=I.MASS_CU)
+    for k, rk in enumerate(r):
+        xx = np.array([[1.0, 1.0, 1.0], [1.0 + rk, 1.0, 1.0]])
+        o = d.compute_forces(torch.tensor(xx, device="cuda"))
+        pair[1, k] = o["rho"][0].item()
+        pair[0, k] = o["e_atom"].sum().item() - 2 * (-spec_f_scale(spec) * np.sqrt(pair[1, k]))
+    d.close()
+    rg = np.linspace(0.0, 2 * rho_eq, 200)
+    F = -spec_f_scale(spec) * np.sqrt(rg)
+    return dict(kind="spline", phi=pair[0], f=pair[1], F=F, r_lo=1.5, r_hi=5.0, rho_lo=0.0, rho_hi=2 * rho_eq)
+
+
+def spec_f_scale(spec: dict) -> float:
+    return spec["c"] * spec["eps"] if spec["kind"] == "sc" else 1.0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -323,11 +443,20 @@ def main():
 
     variants = {}
     cpu = None
+    batch = grad = None
     if rank == 0 and not args.no_extras:
         s.close()
         del s
         variants["mixed"] = run_variant("mixed", W, K, bx.x, bx.v, bx.box)
         variants["fp64"] = {"value": value, "ms_per_step": ms_max / K}
+        del x_dev, v_dev
+        torch.cuda.empty_cache()
+        kb = max(5, min(K, 20))
+        batch = {"fp64": run_batch("fp64", kb, W), "fp64_box": run_batch("fp64", kb, W, schedule="box"),
+                 "mixed": run_batch("mixed", kb, W),
+                 "one_launch_per_box": run_per_box_sample(kb)}
+        grad = {"rgl_fp64": run_grad(max(3, min(K, 10)), 2, "fp64", "rgl"),
+                "spline_fp64": run_grad(max(3, min(K, 10)), 2, "fp64", "spline")}
     if rank == 0 and not args.no_extras:
         import oracle as O
         O.build()
@@ -345,7 +474,7 @@ def main():
                           "mean_list_len": K_list, "mean_in_cutoff": K_in,
                           "n_rebuild": th["n_rebuild"], "phase_ms_per_step": phase_ms},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],
-               "clocks": clk.summary(), "variants": variants}
+               "clocks": clk.summary(), "variants": variants, "batch": batch, "grad": grad}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -215,7 +215,9 @@ MD_API int md_batch_compute_forces(md_batch* b, const double* x, double* f, doub
 
 /* Schedules for md_batch_step. */
 enum md_schedule {
-    MD_SCHED_AUTO = 0, /* pick by the autotuner's cached choice, or time both once */
+    MD_SCHED_AUTO = 0, /* the autotuner's choice: the first call of >= 8 steps times 4
+                          steps of each schedule (they give the same bits) and keeps
+                          the faster for this handle */
     MD_SCHED_BOX = 1,  /* one persistent thread block owns a whole box for all
                           n_steps, positions held in shared memory */
     MD_SCHED_TILE = 2  /* one launch per phase over the atoms of all boxes */
@@ -226,7 +228,18 @@ enum md_schedule {
  * (ke, pe, etot, temperature). */
 MD_API int md_batch_step(md_batch* b, int n_steps, int schedule, int use_graph, double* thermo_box, md_stream stream);
 
-/* Replaces the potential's parameters (same kind and knot counts). */
+/* The schedule the autotuner picked for this batch (MD_SCHED_TILE or
+ * MD_SCHED_BOX; 0 before the first MD_SCHED_AUTO call that ran >= 8 steps)
+ * and the per-step times it measured, ms. Any output may be NULL. */
+MD_API int md_batch_schedule(const md_batch* b, int* choice, double* ms_tile, double* ms_box);
+
+/* Per-box (ke, pe, etot, temperature) of the current state into
+ * thermo_box [n_boxes][4] (host or device); pe is E_T of Eq. (2) per box. */
+MD_API int md_batch_thermo(md_batch* b, double* thermo_box, md_stream stream);
+
+/* Replaces the potential's parameters (same kind and knot counts) and
+ * re-evaluates forces at the current positions (no list rebuild; the cutoff
+ * may not grow). */
 MD_API int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream stream);
 
 /* Gradient of a scalar loss L with respect to the potential parameters

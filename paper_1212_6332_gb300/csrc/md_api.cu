@@ -159,6 +159,8 @@ void fill_pot(Engine& e) {
         P.p_r0 = pp / r0;
         P.q2 = 2.0 * q;
         P.q2_r0 = 2.0 * q / r0;
+        P.xi = xi;
+        P.r0 = r0;
     } else if (p.kind == MD_POT_SC) {
         P.eps = p.p[0];
         P.a = p.p[2];
@@ -204,8 +206,10 @@ void free_engine(Engine& e) {
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
     dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
-    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.ab); dfree(e.exp_T); dfree(e.stage); dfree(e.red);
-    dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl);
+    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.ab); dfree(e.exp_T);
+    dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
+    dfree(e.grad_g); dfree(e.grad_u); dfree(e.grad_Fpp); dfree(e.grad_partial); dfree(e.grad_coef); dfree(e.stage); dfree(e.red);
+    dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box);
     for (cudaEvent_t ev : e.ev_pool) cudaEventDestroy(ev);
     e.ev_pool.clear();
     if (e.ctl_host) cudaFreeHost(e.ctl_host);
@@ -243,7 +247,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     if (!atom_off || atom_off[0] != 0) return fail(nullptr, MD_ERR_ARG, "atom_offsets[0] must be 0");
     for (int b = 0; b < B; ++b)
         if (atom_off[b + 1] < atom_off[b]) return fail(nullptr, MD_ERR_ARG, "atom_offsets must not decrease");
-    if (atom_off[B] > (int64_t)INT32_MAX - 64) return fail(nullptr, MD_ERR_ARG, "too many atoms");
+    if (atom_off[B] >= ((int64_t)1 << 26)) return fail(nullptr, MD_ERR_ARG, "at most 2^26 - 1 atoms per handle");
     double rl = pot_cutoff(pot) + cfg->skin;
     for (int b = 0; b < 3 * B; ++b) {
         if (!(box[b] > 0.0) || !finite(box[b])) return fail(nullptr, MD_ERR_ARG, "box lengths must be > 0");
@@ -395,6 +399,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.red, 2 * std::max(e.n_chunks, 1));
     AL(e.thermo_dev, 4 * (B + 1));
     AL(e.ctl, 1);
+    AL(e.disp_box, B);
 #undef AL
     if (cudaMallocHost((void**)&e.ctl_host, sizeof(Ctl)) != cudaSuccess) {
         cudaGetLastError();
@@ -437,6 +442,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
         if (ce == cudaSuccess) ce = cudaMemset(e.f, 0, 3 * Np * sizeof(double));
         if (ce == cudaSuccess) ce = cudaMemset(e.e_atom, 0, Np * sizeof(double));
         if (ce == cudaSuccess) ce = cudaMemset(e.ctl, 0, sizeof(Ctl));
+        if (ce == cudaSuccess) ce = cudaMemset(e.disp_box, 0, sizeof(unsigned long long) * B);
         if (ce != cudaSuccess) {
             rc = fail(E, MD_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(ce));
             goto fail_alloc;
@@ -725,6 +731,28 @@ int thermo_impl(md_batch* h, md_thermo* out, double* per_box, cudaStream_t s) {
 
 md_batch* H(const md_batch* p) { return const_cast<md_batch*>(p); }
 
+// n steps of the block-per-box schedule, growing the list and relaunching
+// from where each box stopped when a box overflows it.
+int box_steps(md_batch* h, int n, cudaStream_t s) {
+    Engine* E = &h->e;
+    int rc;
+    for (int attempt = 0;; ++attempt) {
+        rc = launch_box_steps(*E, n, attempt == 0, s);
+        if (rc) return fail(E, rc, "box schedule launch failed");
+        if ((rc = read_ctl(E, s))) return rc;
+        int st = E->ctl_host->status;
+        if (st & kStNonFinite) return fail(E, MD_ERR_NONFINITE, "non-finite energy");
+        if (!(st & kStOverflow)) break;
+        if (attempt >= 4) return fail(E, MD_ERR_NEIGH_OVERFLOW, "neighbour list overflow (box schedule)");
+        if ((rc = grow_list(E, E->ctl_host->overflow_count))) return rc;
+        if ((rc = clear_status(E, s))) return rc;
+    }
+    launch_advance_steps(*E, n, s);
+    launch_thermo(*E, s);
+    CK(cudaGetLastError());
+    return finish_sync(E, s);
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -917,21 +945,66 @@ int md_batch_step(md_batch* b, int n_steps, int schedule, int use_graph, double*
     cudaStream_t s = (cudaStream_t)st;
     if (schedule < MD_SCHED_AUTO || schedule > MD_SCHED_TILE) return fail(E, MD_ERR_ARG, "unknown schedule");
     int rc;
-    bool box = schedule == MD_SCHED_BOX;
-    if (schedule == MD_SCHED_AUTO) box = E->sched_choice == MD_SCHED_BOX;
+    if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
+    if (n_steps < 0) return fail(E, MD_ERR_ARG, "n_steps must be >= 0");
+    if (schedule == MD_SCHED_BOX && !box_schedule_fits(*E))
+        return fail(E, MD_ERR_UNSUPPORTED, "the box schedule needs float64 and boxes that fit in shared memory");
+    int remaining = n_steps;
+    if (schedule == MD_SCHED_AUTO && E->sched_choice == 0) {
+        if (!box_schedule_fits(*E)) {
+            E->sched_choice = MD_SCHED_TILE;
+        } else if (remaining >= 8) {
+            // autotune on the first steps of the run: 4 steps each way, keep
+            // the faster per step (both schedules give the same bits)
+            float t_tile = 0.f, t_box = 0.f;
+            cudaEvent_t a, c;
+            CK(cudaEventCreate(&a));
+            CK(cudaEventCreate(&c));
+            CK(cudaEventRecord(a, s));
+            if ((rc = steps_impl(b, 4, nullptr, use_graph != 0, s))) return rc;
+            CK(cudaEventRecord(c, s));
+            CK(cudaEventSynchronize(c));
+            CK(cudaEventElapsedTime(&t_tile, a, c));
+            CK(cudaEventRecord(a, s));
+            if ((rc = box_steps(b, 4, s))) return rc;
+            CK(cudaEventRecord(c, s));
+            CK(cudaEventSynchronize(c));
+            CK(cudaEventElapsedTime(&t_box, a, c));
+            cudaEventDestroy(a);
+            cudaEventDestroy(c);
+            E->sched_choice = t_box < t_tile ? MD_SCHED_BOX : MD_SCHED_TILE;
+            E->sched_ms[0] = t_tile / 4;
+            E->sched_ms[1] = t_box / 4;
+            remaining -= 8;
+        }
+    }
+    bool box = schedule == MD_SCHED_BOX || (schedule == MD_SCHED_AUTO && E->sched_choice == MD_SCHED_BOX);
     if (box) {
-        if (!box_schedule_fits(*E)) return fail(E, MD_ERR_UNSUPPORTED, "a box is too large for the box schedule");
-        if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
-        if (n_steps < 0) return fail(E, MD_ERR_ARG, "n_steps must be >= 0");
-        rc = launch_box_steps(*E, n_steps, s);
-        if (rc) return fail(E, rc, "box schedule failed");
-        launch_thermo(*E, s);
-        CK(cudaGetLastError());
-        if ((rc = finish_sync(E, s))) return rc;
+        if ((rc = box_steps(b, remaining, s))) return rc;
     } else {
-        if ((rc = steps_impl(b, n_steps, nullptr, use_graph != 0, s))) return rc;
+        if ((rc = steps_impl(b, remaining, nullptr, use_graph != 0, s))) return rc;
     }
     if (thermo_box) return thermo_impl(b, nullptr, thermo_box, s);
+    return MD_OK;
+}
+
+int md_batch_thermo(md_batch* b, double* thermo_box, md_stream st) {
+    if (!b || !thermo_box) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    cudaStream_t s = (cudaStream_t)st;
+    if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
+    launch_thermo(*E, s);
+    CK(cudaGetLastError());
+    int rc = thermo_impl(b, nullptr, thermo_box, s);
+    if (rc) return rc;
+    return finish_sync(E, s);
+}
+
+int md_batch_schedule(const md_batch* b, int* choice, double* ms_tile, double* ms_box) {
+    if (!b) return MD_ERR_ARG;
+    if (choice) *choice = b->e.sched_choice;
+    if (ms_tile) *ms_tile = b->e.sched_ms[0];
+    if (ms_box) *ms_box = b->e.sched_ms[1];
     return MD_OK;
 }
 
@@ -974,6 +1047,19 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
     if (!grad || !is_device_ptr(grad)) return fail(E, MD_ERR_ARG, "grad must be a device pointer");
     if (E->N && (!g_f || !is_device_ptr(g_f))) return fail(E, MD_ERR_ARG, "g_f must be a device pointer");
     if (g_e && !is_device_ptr(g_e)) return fail(E, MD_ERR_ARG, "g_e must be a device pointer");
+    Engine& e = *E;
+    if (!e.grad_g && e.N > 0) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+        int nb = (int)((e.N + 127) / 128);
+        e.grad_blocks = std::max(1, std::min(nb, 4 * std::max(sms, 1)));
+        const md_potential& p = e.pot_host;
+        size_t ncoef = p.kind == MD_POT_SPLINE ? 4 * ((size_t)p.n_phi + p.n_f + p.n_F - 3) : 5;
+        if (dalloc(E, &e.grad_g, 3 * (size_t)e.N_pad) || dalloc(E, &e.grad_u, (size_t)e.N_pad) ||
+            dalloc(E, &e.grad_Fpp, (size_t)e.N_pad) || dalloc(E, &e.grad_partial, (size_t)e.grad_blocks * ncoef) ||
+            dalloc(E, &e.grad_coef, ncoef))
+            return MD_ERR_NOMEM;
+    }
     int rc = launch_param_grad(*E, g_f, g_e, grad, s);
     if (rc) return fail(E, rc, "parameter gradient failed");
     CK(cudaGetLastError());

@@ -8,28 +8,38 @@
 //   k_sort_cells   order each cell's atoms by caller id (deterministic)
 //   k_permute      gather x, v, ids into the new order (alternate buffers)
 //   k_copy_back    copy back, record positions at build, inverse map
-// Every kernel returns at once unless a rebuild is wanted (mode 1, or the
-// device displacement word exceeds (skin/2)^2), so the chain can be launched
-// every step, or captured in a CUDA graph, without a host decision.
+// Every box decides on the device whether it rebuilds (mode 1, or its
+// largest displacement since its last build exceeds skin/2); atoms and cells
+// of the other boxes are left untouched, so the chain can be launched every
+// step, or captured in a CUDA graph, without a host decision.
 #include <cstring>
 
 #include "md_device.cuh"
 
 namespace mdk {
 
-__device__ __forceinline__ bool rebuild_wanted(const Ctl* c, int mode, unsigned long long thr) {
+// A box rebuilds when mode is 1, or when its largest displacement since its
+// last build exceeds skin/2; boxes decide independently.
+__device__ __forceinline__ bool box_wants(const Ctl* c, const unsigned long long* disp, int b, int mode,
+                                         unsigned long long thr) {
     if (load_status(c)) return false;
     if (mode) return true;
-    return *((volatile const unsigned long long*)&c->disp2_bits) > thr;
+    return disp[b] > thr;
 }
 
-__global__ void k_bin(int64_t N, const double4_32a* __restrict__ x, Geo g, int* __restrict__ cell_of,
-                      int* __restrict__ cell_count, const Ctl* ctl, int mode, unsigned long long thr) {
-    if (!rebuild_wanted(ctl, mode, thr)) return;
+__global__ void k_bin(int64_t N, double4_32a* __restrict__ x, Geo g, int* __restrict__ cell_of,
+                      int* __restrict__ cell_count, const Ctl* ctl, const unsigned long long* __restrict__ disp,
+                      int mode, unsigned long long thr) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     int b = g.B == 1 ? 0 : g.atom_box[s];
+    if (!box_wants(ctl, disp, b, mode, thr)) return;
+    // positions drift unwrapped between builds; wrap them into the box here
     double4_32a p = x[s];
+    p.x = wrap_step(p.x, g.L[3 * b]);
+    p.y = wrap_step(p.y, g.L[3 * b + 1]);
+    p.z = wrap_step(p.z, g.L[3 * b + 2]);
+    x[s] = p;
     double pc[3] = {p.x, p.y, p.z};
     int c[3];
 #pragma unroll
@@ -48,8 +58,8 @@ constexpr int kScanNT = 1024;
 
 // Exclusive scan of counts[0..n) within blocks of kScanNT; block totals out.
 __global__ void k_scan_blocks(int n, const int* __restrict__ counts, int* __restrict__ start,
-                              int* __restrict__ block_tot, const Ctl* ctl, int mode, unsigned long long thr) {
-    if (!rebuild_wanted(ctl, mode, thr)) return;
+                              int* __restrict__ block_tot, const Ctl* ctl) {
+    if (load_status(ctl)) return;
     __shared__ int wsum[kScanNT / 32];
     int i = blockIdx.x * kScanNT + threadIdx.x;
     int v = i < n ? counts[i] : 0;
@@ -78,9 +88,8 @@ __global__ void k_scan_blocks(int n, const int* __restrict__ counts, int* __rest
 }
 
 // One block: exclusive scan of the block totals, serially over chunks.
-__global__ void k_scan_totals(int nb, int* __restrict__ block_tot, const Ctl* ctl, int mode,
-                              unsigned long long thr) {
-    if (!rebuild_wanted(ctl, mode, thr)) return;
+__global__ void k_scan_totals(int nb, int* __restrict__ block_tot, const Ctl* ctl) {
+    if (load_status(ctl)) return;
     __shared__ int wsum[kScanNT / 32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -115,39 +124,46 @@ __global__ void k_scan_totals(int nb, int* __restrict__ block_tot, const Ctl* ct
     }
 }
 
-// Adds block offsets, zeroes the counts (they become fill counters), and
-// closes the start array with N.
+// Adds block offsets, zeroes the counts (they become fill counters) and
+// closes the prefix array. The result S is an exclusive prefix over the
+// counted atoms of all cells; the atoms of cell c of box b occupy
+// [atom_off[b] + S[c] - S[cell_off[b]], atom_off[b] + S[c+1] - S[cell_off[b]])
+// (cell_range), so boxes that keep their lists are left where they are.
 __global__ void k_scan_add(int n, int* __restrict__ start, const int* __restrict__ block_tot,
-                           int* __restrict__ counts, int64_t N, const Ctl* ctl, int mode, unsigned long long thr) {
-    if (!rebuild_wanted(ctl, mode, thr)) return;
+                           int* __restrict__ counts, const Ctl* ctl) {
+    if (load_status(ctl)) return;
     int i = blockIdx.x * kScanNT + threadIdx.x;
     if (i < n) {
+        int v = counts[i];
         start[i] += block_tot[blockIdx.x];
         counts[i] = 0;
+        if (i == n - 1) start[n] = start[i] + v;
     }
-    if (i == 0) start[n] = (int)N;
 }
 
-__global__ void k_scatter(int64_t N, const int* __restrict__ cell_of, const int* __restrict__ start,
-                          int* __restrict__ fill, int* __restrict__ src, const Ctl* ctl, int mode,
-                          unsigned long long thr) {
-    if (!rebuild_wanted(ctl, mode, thr)) return;
+__global__ void k_scatter(int64_t N, Geo g, const int* __restrict__ cell_of, const int* __restrict__ start,
+                          int* __restrict__ fill, int* __restrict__ src, const Ctl* ctl,
+                          const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
+    int b = g.B == 1 ? 0 : g.atom_box[s];
+    if (!box_wants(ctl, disp, b, mode, thr)) return;
     int c = cell_of[s];
-    int t = start[c] + atomicAdd(&fill[c], 1);
+    int64_t t = g.atom_off[b] + (start[c] - start[g.cell_off[b]]) + atomicAdd(&fill[c], 1);
     src[t] = (int)s;
 }
 
 // Orders the atoms of each cell by caller id, so the sorted order (and every
 // sum over it) does not depend on the atomic order of k_scatter.
-__global__ void k_sort_cells(int n_cells, const int* __restrict__ start, int* __restrict__ fill,
-                             int* __restrict__ src, const int* __restrict__ perm, const Ctl* ctl, int mode,
-                             unsigned long long thr) {
-    if (!rebuild_wanted(ctl, mode, thr)) return;
+__global__ void k_sort_cells(int n_cells, Geo g, const int* __restrict__ start, int* __restrict__ fill,
+                             int* __restrict__ src, const int* __restrict__ perm, const Ctl* ctl,
+                             const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cells) return;
-    int a = start[c], e = start[c + 1];
+    int b = g.cell_box[c];
+    if (!box_wants(ctl, disp, b, mode, thr)) return;
+    int base = (int)g.atom_off[b] - start[g.cell_off[b]];
+    int a = base + start[c], e = base + start[c + 1];
     fill[c] = 0;
     for (int i = a + 1; i < e; ++i) {
         int s = src[i];
@@ -161,14 +177,15 @@ __global__ void k_sort_cells(int n_cells, const int* __restrict__ start, int* __
     }
 }
 
-__global__ void k_permute(int64_t N, int64_t Np, const int* __restrict__ src, const double4_32a* __restrict__ x,
-                          double4_32a* __restrict__ x_alt, const double* __restrict__ v, double* __restrict__ v_alt,
-                          const int* __restrict__ perm, int* __restrict__ perm_alt,
-                          const int* __restrict__ cell_of, int* __restrict__ cell_t_alt, const Ctl* ctl,
-                          int mode, unsigned long long thr) {
-    if (!rebuild_wanted(ctl, mode, thr)) return;
+__global__ void k_permute(int64_t N, int64_t Np, Geo g, const int* __restrict__ src,
+                          const double4_32a* __restrict__ x, double4_32a* __restrict__ x_alt,
+                          const double* __restrict__ v, double* __restrict__ v_alt, const int* __restrict__ perm,
+                          int* __restrict__ perm_alt, const int* __restrict__ cell_of, int* __restrict__ cell_t_alt,
+                          const Ctl* ctl, const unsigned long long* __restrict__ disp, int mode,
+                          unsigned long long thr) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
+    if (!box_wants(ctl, disp, g.B == 1 ? 0 : g.atom_box[t], mode, thr)) return;
     int s = src[t];
     x_alt[t] = x[s];
     v_alt[t] = v[s];
@@ -178,32 +195,18 @@ __global__ void k_permute(int64_t N, int64_t Np, const int* __restrict__ src, co
     cell_t_alt[t] = cell_of[s];
 }
 
-// Float32 offset of each atom from the origin of the cell it was binned
-// into (minimum image), w = packed cell coordinates: the list build's
-// prefilter and the mixed-precision pair math use it.
-__device__ __forceinline__ float4 cell_local(const Geo& g, int b, int gc, double4_32a p) {
-    int xyz = g.cell_xyz[gc];
-    int c[3] = {xyz & 1023, (xyz >> 10) & 1023, (xyz >> 20) & 1023};
-    double pc[3] = {p.x, p.y, p.z};
-    float o[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double L = g.L[3 * b + a];
-        double d = pc[a] - c[a] * g.cell_len[3 * b + a];
-        o[a] = (float)minimg(d, L, 0.5 * L);
-    }
-    return make_float4(o[0], o[1], o[2], __int_as_float(xyz));
-}
-
 __global__ void k_copy_back(int64_t N, int64_t Np, Geo g, double4_32a* __restrict__ x, const double4_32a* __restrict__ x_alt,
                             double4_32a* __restrict__ xb, double* __restrict__ v, const double* __restrict__ v_alt,
                             int* __restrict__ perm, const int* __restrict__ perm_alt, int* __restrict__ iperm,
                             int* __restrict__ cell_t, const int* __restrict__ cell_t_alt, float4* __restrict__ xo,
-                            Ctl* ctl, int mode, unsigned long long thr) {
-    if (!rebuild_wanted(ctl, mode, thr)) return;
+                            Ctl* ctl, const unsigned long long* __restrict__ disp, int mode,
+                            unsigned long long thr) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) ctl->rebuilt = 1;
     if (t >= N) return;
+    const int b = g.B == 1 ? 0 : g.atom_box[t];
+    if (!box_wants(ctl, disp, b, mode, thr)) return;
+    // count the list builds of the dynamics (one per box and step)
+    if (!mode && t == g.atom_off[b]) atomicAdd((unsigned long long*)&ctl->n_rebuild, 1ULL);
     double4_32a p = x_alt[t];
     x[t] = p;
     xb[t] = p;
@@ -215,10 +218,7 @@ __global__ void k_copy_back(int64_t N, int64_t Np, Geo g, double4_32a* __restric
     iperm[id] = (int)t;
     int gc = cell_t_alt[t];
     cell_t[t] = gc;
-    if (xo) {
-        int b = g.B == 1 ? 0 : g.atom_box[t];
-        xo[t] = cell_local(g, b, gc, p);
-    }
+    xo[t] = cell_local(g, b, gc, p);
 }
 
 static unsigned long long disp_threshold(const Engine& e) {
@@ -238,19 +238,18 @@ void launch_rebuild(Engine& e, int mode, cudaStream_t s) {
     const int nt = 256;
     int nb_atoms = (int)((e.N + nt - 1) / nt);
     int nb_scan = (e.n_cells + kScanNT - 1) / kScanNT;
-    k_bin<<<nb_atoms, nt, 0, s>>>(e.N, e.x, g, e.cell_of, e.cell_count, e.ctl, mode, thr);
-    k_scan_blocks<<<nb_scan, kScanNT, 0, s>>>(e.n_cells, e.cell_count, e.cell_start, e.scan_tmp, e.ctl, mode, thr);
-    k_scan_totals<<<1, kScanNT, 0, s>>>(nb_scan, e.scan_tmp, e.ctl, mode, thr);
-    k_scan_add<<<nb_scan, kScanNT, 0, s>>>(e.n_cells, e.cell_start, e.scan_tmp, e.cell_count, e.N, e.ctl, mode,
-                                          thr);
-    k_scatter<<<nb_atoms, nt, 0, s>>>(e.N, e.cell_of, e.cell_start, e.cell_count, e.src, e.ctl, mode, thr);
-    k_sort_cells<<<(e.n_cells + 127) / 128, 128, 0, s>>>(e.n_cells, e.cell_start, e.cell_count, e.src, e.perm,
-                                                          e.ctl, mode, thr);
-    k_permute<<<nb_atoms, nt, 0, s>>>(e.N, e.N_pad, e.src, e.x, e.x_alt, e.v, e.v_alt, e.perm, e.perm_alt,
-                                      e.cell_of, e.cell_t_alt, e.ctl, mode, thr);
+    const unsigned long long* disp = e.disp_box;
+    k_bin<<<nb_atoms, nt, 0, s>>>(e.N, e.x, g, e.cell_of, e.cell_count, e.ctl, disp, mode, thr);
+    k_scan_blocks<<<nb_scan, kScanNT, 0, s>>>(e.n_cells, e.cell_count, e.cell_start, e.scan_tmp, e.ctl);
+    k_scan_totals<<<1, kScanNT, 0, s>>>(nb_scan, e.scan_tmp, e.ctl);
+    k_scan_add<<<nb_scan, kScanNT, 0, s>>>(e.n_cells, e.cell_start, e.scan_tmp, e.cell_count, e.ctl);
+    k_scatter<<<nb_atoms, nt, 0, s>>>(e.N, g, e.cell_of, e.cell_start, e.cell_count, e.src, e.ctl, disp, mode, thr);
+    k_sort_cells<<<(e.n_cells + 127) / 128, 128, 0, s>>>(e.n_cells, g, e.cell_start, e.cell_count, e.src, e.perm,
+                                                          e.ctl, disp, mode, thr);
+    k_permute<<<nb_atoms, nt, 0, s>>>(e.N, e.N_pad, g, e.src, e.x, e.x_alt, e.v, e.v_alt, e.perm, e.perm_alt,
+                                      e.cell_of, e.cell_t_alt, e.ctl, disp, mode, thr);
     k_copy_back<<<nb_atoms, nt, 0, s>>>(e.N, e.N_pad, g, e.x, e.x_alt, e.xb, e.v, e.v_alt, e.perm, e.perm_alt,
-                                        e.iperm, e.cell_t, e.cell_t_alt,
-                                        e.xo, e.ctl, mode, thr);
+                                        e.iperm, e.cell_t, e.cell_t_alt, e.xo, e.ctl, disp, mode, thr);
     launch_build_list(e, mode, s);
 }
 

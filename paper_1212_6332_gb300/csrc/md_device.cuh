@@ -43,8 +43,117 @@ __device__ __forceinline__ double wrap_step(double x, double L) {
     return wrap_coord(x, L);
 }
 
+// A neighbour-list entry holds the neighbour's slot in its low 26 bits and
+// the periodic image of the pair in its top 6 bits (2 bits per axis, shift
+// + 1): x_j + shift * L is the image of atom j within the list radius of
+// atom i. Positions are not wrapped between list builds, so the image stays
+// valid for the life of the list and no minimum-image test is needed.
+constexpr int kSlotBits = 26;
+constexpr int kSlotMask = (1 << kSlotBits) - 1;
+constexpr unsigned kNoShift = 0x15u;  // shifts (0, 0, 0)
+
+__device__ __forceinline__ int entry_slot(int e) { return e & kSlotMask; }
+__device__ __forceinline__ unsigned entry_code(int e) { return (unsigned)e >> kSlotBits; }
+__device__ __forceinline__ int make_entry(int j, int sx, int sy, int sz) {
+    unsigned code = (unsigned)(sx + 1) | ((unsigned)(sy + 1) << 2) | ((unsigned)(sz + 1) << 4);
+    return (int)((unsigned)j | (code << kSlotBits));
+}
+
+__device__ __forceinline__ double image_shift(unsigned c2, double L) {
+    return c2 == 1u ? 0.0 : (c2 == 0u ? -L : L);
+}
+
+// separation x_j - x_i of a list entry with its stored image
+__device__ __forceinline__ void sep_entry(const double4_32a& xi, const double4_32a& xj, unsigned code,
+                                          const double* L, double& dx, double& dy, double& dz) {
+    dx = xj.x - xi.x;
+    dy = xj.y - xi.y;
+    dz = xj.z - xi.z;
+    if (code != kNoShift) {
+        dx += image_shift(code & 3u, L[0]);
+        dy += image_shift((code >> 2) & 3u, L[1]);
+        dz += image_shift((code >> 4) & 3u, L[2]);
+    }
+}
+
 __device__ __forceinline__ int load_status(const Ctl* c) {
     return *((volatile const int*)&c->status);
+}
+
+
+// Float32 offset of each atom from the origin of the cell it was binned
+// into (minimum image), w = packed cell coordinates: the list build's
+// prefilter and the mixed-precision pair math use it.
+__device__ __forceinline__ float4 cell_local(const Geo& g, int b, int gc, double4_32a p) {
+    int xyz = g.cell_xyz[gc];
+    int c[3] = {xyz & 1023, (xyz >> 10) & 1023, (xyz >> 20) & 1023};
+    double pc[3] = {p.x, p.y, p.z};
+    float o[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double L = g.L[3 * b + a];
+        double d = pc[a] - c[a] * g.cell_len[3 * b + a];
+        o[a] = (float)minimg(d, L, 0.5 * L);
+    }
+    return make_float4(o[0], o[1], o[2], __int_as_float(xyz));
+}
+
+// Minimum image of a cell-index difference on an axis of n cells.
+__device__ __forceinline__ int cell_delta(int cj, int ci, int n) {
+    int d = cj - ci;
+    if (2 * d > n) return d - n;
+    if (2 * d < -n) return d + n;
+    return d;
+}
+
+// Candidate test. A float32 separation from the cell-local offsets (exact
+// cell difference times the cell side plus the offset difference) decides
+// every candidate whose r^2 lies farther than `margin` from rl^2; the float32
+// error of that r^2 is below 2e-4 A^2 for the cell sides used here, and
+// margin = 4e-4 * rl A^2 covers it with a wide factor. The few candidates
+// inside the band (~0.01 per atom) take the exact float64 test, which alone
+// decides membership, so the list equals the oracle's bit for bit.
+
+__device__ __forceinline__ bool list_candidate(const float4& oi, const float4& oj, const double4_32a& xi,
+                                               const double4_32a* __restrict__ xall, int j, int cix, int ciy, int ciz,
+                                               int ncx, int ncy, int ncz, float lfx, float lfy, float lfz, float Lfx,
+                                               float Lfy, float Lfz, double Lx, double Ly, double Lz, double rl2,
+                                               float rl2f_lo, float rl2f_hi, int& sx, int& sy, int& sz) {
+    int cj = __float_as_int(oj.w);
+    // cell difference as a minimum image in whole cells; the wrap it needed
+    // is a shift of one box length
+    int rx = (cj & 1023) - cix, ry = ((cj >> 10) & 1023) - ciy, rz = ((cj >> 20) & 1023) - ciz;
+    int wx = cell_delta(cj & 1023, cix, ncx), wy = cell_delta((cj >> 10) & 1023, ciy, ncy),
+        wz = cell_delta((cj >> 20) & 1023, ciz, ncz);
+    sx = (wx - rx) / ncx;
+    sy = (wy - ry) / ncy;
+    sz = (wz - rz) / ncz;
+    float dx = fmaf((float)wx, lfx, oj.x - oi.x);
+    float dy = fmaf((float)wy, lfy, oj.y - oi.y);
+    float dz = fmaf((float)wz, lfz, oj.z - oi.z);
+    // one more box shift when the cell image is not the nearest (fewer than
+    // 3 cells on an axis)
+    if (dx > 0.5f * Lfx) { dx -= Lfx; sx -= 1; } else if (dx < -0.5f * Lfx) { dx += Lfx; sx += 1; }
+    if (dy > 0.5f * Lfy) { dy -= Lfy; sy -= 1; } else if (dy < -0.5f * Lfy) { dy += Lfy; sy += 1; }
+    if (dz > 0.5f * Lfz) { dz -= Lfz; sz -= 1; } else if (dz < -0.5f * Lfz) { dz += Lfz; sz += 1; }
+    float r2f = dx * dx + dy * dy + dz * dz;
+    // components within 1e-3 A of half a box take the exact path too, so the
+    // stored image is the float64 one
+    bool near_half =
+        fabsf(dx) > 0.5f * Lfx - 1e-3f || fabsf(dy) > 0.5f * Lfy - 1e-3f || fabsf(dz) > 0.5f * Lfz - 1e-3f;
+    if (r2f < rl2f_lo && !near_half) return true;
+    if (r2f > rl2f_hi && !near_half) return false;
+    const double4_32a xj = xall[j];
+    const double hx = 0.5 * Lx, hy = 0.5 * Ly, hz = 0.5 * Lz;
+    double ex = __dsub_rn(xj.x, xi.x), ey = __dsub_rn(xj.y, xi.y), ez = __dsub_rn(xj.z, xi.z);
+    sx = ex > hx ? -1 : (ex < -hx ? 1 : 0);
+    sy = ey > hy ? -1 : (ey < -hy ? 1 : 0);
+    sz = ez > hz ? -1 : (ez < -hz ? 1 : 0);
+    ex = minimg(ex, Lx, hx);
+    ey = minimg(ey, Ly, hy);
+    ez = minimg(ez, Lz, hz);
+    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+    return r2 < rl2;
 }
 
 // ---------------------------------------------------------------- float64

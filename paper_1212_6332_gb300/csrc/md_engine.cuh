@@ -32,6 +32,7 @@ struct Pot {
     double rc, rc2, rs, inv_w;  // cutoff, taper start, 1/(rc - rs); rs >= rc: hard cut
     // RGL: V = A2 exp(p - p_r0 r) S, rho = xi2 exp(q2 - q2_r0 r) S
     double A2, xi2, p, p_r0, q2, q2_r0;
+    double xi, r0;  // RGL xi and r0 (parameter derivatives)
     // SC: V = eps (a/r)^n S, rho = (a/r)^m S; F = -F_scale sqrt(rho)
     double eps, a, n, m;
     double F_scale;
@@ -68,12 +69,16 @@ struct Geo {
 struct Ctl {
     int status;                      // kSt* bits
     int overflow_count;              // largest neighbour count seen at overflow
-    unsigned long long disp2_bits;   // max squared displacement this step (double bits)
-    unsigned long long disp2_last;   // value of the last completed step
+    unsigned long long disp2_last;   // largest squared displacement of the last step (double bits)
     long long step;                  // completed steps since set_state
     long long n_rebuild;             // list builds since set_state
-    int rebuilt;                     // the current step rebuilt the list
     int max_count;                   // largest neighbour count of the current list
+};
+
+// Shared-memory size class of the block-per-box schedule.
+struct BoxClass {
+    int first, count, threads;
+    size_t smem;
 };
 
 struct Engine {
@@ -138,6 +143,13 @@ struct Engine {
     int* nl = nullptr;          // [max_nb][N_pad] column-major
     double2* ab = nullptr;      // float64 path: [max_nb][N_pad] (V'/r, rho'/r) per list entry
     double* exp_T = nullptr;    // exponential table
+    // parameter adjoint work arrays (allocated on the first gradient call)
+    double* grad_g = nullptr;        // [3][N_pad] dL/dF in sorted order
+    double* grad_u = nullptr;        // [N_pad] adjoint scalar u_i
+    double* grad_Fpp = nullptr;      // [N_pad] F''(rho_i)
+    double* grad_partial = nullptr;  // [grad_blocks][n_coef or 5]
+    double* grad_coef = nullptr;     // spline coefficient gradients
+    int grad_blocks = 0;
     ExpConst exp_const{};
     double* stage = nullptr;    // [3N] staging for host copies / caller-order outputs
     double* red = nullptr;      // reduction scratch [2 * n_chunks]
@@ -146,6 +158,7 @@ struct Engine {
     int hist_cap = 0;
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;       // pinned mirror
+    unsigned long long* disp_box = nullptr;  // [B] largest squared displacement since the box's last build
 
     bool have_state = false;
     // CUDA graph of one step (and of a chunk of steps)
@@ -154,6 +167,12 @@ struct Engine {
     int graph_chunk_len = 0;
     bool graph_hist = false;
     int sched_choice = 0;  // autotuner result for batches (0 = unknown)
+    double sched_ms[2] = {0.0, 0.0};  // autotuner timings per step: tile, box
+    // block-per-box schedule
+    int* box_order = nullptr;
+    int* box_done = nullptr;
+    int* box_state = nullptr;
+    std::vector<BoxClass> box_classes;
     long long graph_chunk_kernels = 0, graph_step_kernels = 0;
 
     // profiling: launch counter and phase events
@@ -221,7 +240,8 @@ void launch_box_energy(Engine& e, double* e_box_dev, cudaStream_t s);
 void launch_reset_perm(Engine& e, cudaStream_t s);
 void launch_eval_math(Engine& e, int fn, const double* x, int64_t n, double* out, cudaStream_t s);
 // batched block-per-box schedule
-int launch_box_steps(Engine& e, int n_steps, cudaStream_t s);
+int launch_box_steps(Engine& e, int n_steps, bool first, cudaStream_t s);
+void launch_advance_steps(Engine& e, long long n, cudaStream_t s);
 bool box_schedule_fits(const Engine& e);
 // parameter adjoint
 int launch_param_grad(Engine& e, const double* g_f, const double* g_e, double* grad, cudaStream_t s);

@@ -36,23 +36,19 @@ __global__ void __launch_bounds__(kFNT) k_density(int64_t N, int64_t Np, Geo g, 
     if (KIND == MD_POT_RGL) load_exp_table(sT, P.exp_T);
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double L[3], h[3];
+    double L[3];
     int b = SINGLE ? 0 : g.atom_box[i];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
-        h[a] = 0.5 * L[a];
-    }
+    for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
     const double4_32a xi = x[i];
     const int n = min(nn[i], max_nb);
     double r_i = 0.0, ep = 0.0;
     for (int k = 0; k < n; ++k) {
         const int64_t slot = (int64_t)k * Np + i;
-        int j = nl[slot];
-        double4_32a xj = x[j];
-        double dx = minimg(xj.x - xi.x, L[0], h[0]);
-        double dy = minimg(xj.y - xi.y, L[1], h[1]);
-        double dz = minimg(xj.z - xi.z, L[2], h[2]);
+        const int e = nl[slot];
+        const double4_32a xj = x[entry_slot(e)];
+        double dx, dy, dz;
+        sep_entry(xi, xj, entry_code(e), L, dx, dy, dz);
         double r2 = dx * dx + dy * dy + dz * dz;
         double2 c = make_double2(0.0, 0.0);
         if (r2 < P.rc2) {
@@ -79,13 +75,10 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
     if (load_status(ctl)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double L[3], h[3];
+    double L[3];
     int b = SINGLE ? 0 : g.atom_box[i];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
-        h[a] = 0.5 * L[a];
-    }
+    for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
     const double4_32a xi = x[i];
     const double Fpi = Fp[i];
     const int n = min(nn[i], max_nb);
@@ -95,11 +88,11 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
         double2 c = ab[slot];
         // entries outside r_cut carry (0, 0): skip them with an integer test
         if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
-        int j = nl[slot];
-        double4_32a xj = x[j];
-        double dx = minimg(xj.x - xi.x, L[0], h[0]);
-        double dy = minimg(xj.y - xi.y, L[1], h[1]);
-        double dz = minimg(xj.z - xi.z, L[2], h[2]);
+        const int e = nl[slot];
+        const int j = entry_slot(e);
+        const double4_32a xj = x[j];
+        double dx, dy, dz;
+        sep_entry(xi, xj, entry_code(e), L, dx, dy, dz);
         double s = fma(Fpi + Fp[j], c.y, c.x);
         fx = fma(s, dx, fx);
         fy = fma(s, dy, fy);

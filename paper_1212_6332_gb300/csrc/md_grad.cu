@@ -1,8 +1,384 @@
-// Parameter adjoint (placeholder until the adjoint kernels land).
+// Adjoint of the force evaluation with respect to the potential parameters
+// (no counterpart in the paper; it turns the force kernels into a
+// force-matching gradient).
+//
+// Given g_i = dL/dF_i and g_E(b) = dL/dE_b for every atom i and box b, and
+// the forces of Eq. (3) F_i = sum_j s_ij d_ij with d_ij = x_j - x_i,
+// s_ij = [V'(r) + (F'_i + F'_j) rho'(r)] / r (symmetric in i, j):
+//   dL/dtheta = sum_i sum_j { w_ij [dV' + (F'_i + F'_j) drho']
+//                             + (u_i F''_i + g_E F'_i) drho + g_E dV / 2 }
+//             + sum_i { u_i d_theta F'(rho_i) + g_E d_theta F(rho_i) },
+// where d = d/dtheta at fixed r and rho, w_ij = g_i . d_ij / r, and
+//   u_i = sum_j (g_i - g_j) . d_ij rho'(r_ij) / r_ij
+// is a per-atom adjoint scalar (a gather of g_j over the list). The two
+// passes of the forward pass become three:
+//   k_grad_rho    recompute rho_i, F'_i and F''_i (nothing per pair is stored)
+//   k_grad_u      u_i
+//   k_grad_param  per-pair terms into per-block parameter partials
+//                 (RGL: block reduction of 5 sums; spline: shared-memory
+//                 histogram over the cubic coefficients of each interval)
+// then a fixed-order reduction and, for splines, the transpose of the
+// knot-value -> coefficient map (one more tridiagonal solve per spline).
+#include <cstring>
+
 #include "md_device.cuh"
 
 namespace mdk {
 
-int launch_param_grad(Engine&, const double*, const double*, double*, cudaStream_t) { return MD_ERR_UNSUPPORTED; }
+constexpr int kGNT = 128;
+constexpr int kRglParams = 5;
+
+__device__ __forceinline__ double box_gE(const Geo& g, const double* gE, int64_t i) {
+    if (!gE) return 0.0;
+    return gE[g.B == 1 ? 0 : g.atom_box[i]];
+}
+
+__device__ __forceinline__ void sep(const Geo& g, const double4_32a* __restrict__ x, int64_t i, int j, double& dx,
+                                    double& dy, double& dz) {
+    int b = g.B == 1 ? 0 : g.atom_box[i];
+    double Lx = g.L[3 * b], Ly = g.L[3 * b + 1], Lz = g.L[3 * b + 2];
+    double4_32a xi = x[i], xj = x[j];
+    dx = minimg(xj.x - xi.x, Lx, 0.5 * Lx);
+    dy = minimg(xj.y - xi.y, Ly, 0.5 * Ly);
+    dz = minimg(xj.z - xi.z, Lz, 0.5 * Lz);
+}
+
+// rho_i, F'(rho_i), F''(rho_i) recomputed from the list.
+template <int KIND>
+__global__ void __launch_bounds__(kGNT) k_grad_rho(int64_t N, int64_t Np, Geo g, Pot P,
+                                                   const double4_32a* __restrict__ x, const int* __restrict__ nn,
+                                                   const int* __restrict__ nl, int max_nb, double* __restrict__ rho,
+                                                   double* __restrict__ Fp, double* __restrict__ Fpp) {
+    __shared__ double sT[kExpTable];
+    if (KIND == MD_POT_RGL) load_exp_table(sT, P.exp_T);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int n = min(nn[i], max_nb);
+    double r_i = 0.0;
+    for (int k = 0; k < n; ++k) {
+        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        double dx, dy, dz;
+        sep(g, x, i, j, dx, dy, dz);
+        double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= P.rc2) continue;
+        double phi, fr, A, B;
+        pair_eval<KIND>(P, sT, r2, phi, fr, A, B);
+        r_i += fr;
+    }
+    double F, Fpi, Fppi = 0.0;
+    embed<KIND>(P, r_i, F, Fpi);
+    if (KIND == MD_POT_SPLINE) {
+        double s = (r_i - P.st0[2]) * P.sinvh[2];
+        int k = (int)s;
+        if (s >= 0.0 && k < P.sn[2] - 1) {
+            double u = r_i - (P.st0[2] + P.sh[2] * k);
+            double4_32a c = P.sp[2][k];
+            Fppi = 2.0 * c.z + 6.0 * c.w * u;
+        }
+    } else if (r_i > 0.0) {
+        Fppi = 0.25 * P.F_scale / (r_i * sqrt(r_i));
+    }
+    rho[i] = r_i;
+    Fp[i] = Fpi;
+    Fpp[i] = Fppi;
+}
+
+// u_i = sum_j (g_i - g_j) . d_ij rho'(r)/r
+template <int KIND>
+__global__ void __launch_bounds__(kGNT) k_grad_u(int64_t N, int64_t Np, Geo g, Pot P,
+                                                 const double4_32a* __restrict__ x, const int* __restrict__ nn,
+                                                 const int* __restrict__ nl, int max_nb, const double* __restrict__ gs,
+                                                 double* __restrict__ u) {
+    __shared__ double sT[kExpTable];
+    if (KIND == MD_POT_RGL) load_exp_table(sT, P.exp_T);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int n = min(nn[i], max_nb);
+    const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) {
+        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        double dx, dy, dz;
+        sep(g, x, i, j, dx, dy, dz);
+        double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= P.rc2) continue;
+        double phi, fr, A, B;
+        pair_eval<KIND>(P, sT, r2, phi, fr, A, B);
+        acc += ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * B;
+    }
+    u[i] = acc;
+}
+
+// ---------------------------------------------------------------- RGL
+
+// Derivatives of V, V', rho, rho' with respect to (A, xi, p, q, r0) at r,
+// combined with the adjoint weights:
+//   a_dV' = w, a_drho' = w (F'_i + F'_j), a_drho = u_i F''_i + gE F'_i, a_dV = gE/2.
+__device__ __forceinline__ void rgl_param_terms(const Pot& P, const double* T, double r, double aVp, double aFp,
+                                                double aF, double aV, double* acc) {
+    double S, dS;
+    taper(P, r, S, dS);
+    const double p_r0 = P.p_r0, q2_r0 = P.q2_r0, r0 = P.r0;
+    const double u = r / r0 - 1.0;
+    const double E1 = exp_tab(P.p - p_r0 * r, T, P.ek);   // exp(-p u)
+    const double E2 = exp_tab(P.q2 - q2_r0 * r, T, P.ek);  // exp(-2q u)
+    const double gV = S, gVp = dS - p_r0 * S;    // V = 2A E1 gV, V' = 2A E1 gVp
+    const double gf = S, gfp = dS - q2_r0 * S;   // rho = xi^2 E2 gf, rho' = xi^2 E2 gfp
+    const double e1 = P.A2 * E1, e2 = P.xi2 * E2;
+    const double V = e1 * gV, Vp = e1 * gVp, f = e2 * gf, fp = e2 * gfp;
+    const double inv_r02 = 1.0 / (r0 * r0);
+    // d/dA: V = 2A E1 S
+    double dV_A = 2.0 * E1 * gV, dVp_A = 2.0 * E1 * gVp;
+    // d/dxi: rho = xi^2 E2 S
+    double df_xi = 2.0 * P.xi * E2 * gf, dfp_xi = 2.0 * P.xi * E2 * gfp;
+    // d/dp: dE1/dp = -u E1, d(p/r0)/dp = 1/r0
+    double dV_p = -u * V, dVp_p = -u * Vp - e1 * S / r0;
+    // d/dq: dE2/dq = -2u E2, d(2q/r0)/dq = 2/r0
+    double df_q = -2.0 * u * f, dfp_q = -2.0 * u * fp - 2.0 * e2 * S / r0;
+    // d/dr0: du/dr0 = -r/r0^2, d(p/r0)/dr0 = -p/r0^2
+    double c0 = r * inv_r02;
+    double dV_r0 = P.p * c0 * V, dVp_r0 = P.p * c0 * Vp + e1 * P.p * S * inv_r02;
+    double df_r0 = P.q2 * c0 * f, dfp_r0 = P.q2 * c0 * fp + e2 * P.q2 * S * inv_r02;
+    acc[0] += aVp * dVp_A + aV * dV_A;
+    acc[1] += aFp * dfp_xi + aF * df_xi;
+    acc[2] += aVp * dVp_p + aV * dV_p;
+    acc[3] += aFp * dfp_q + aF * df_q;
+    acc[4] += aVp * dVp_r0 + aV * dV_r0 + aFp * dfp_r0 + aF * df_r0;
+}
+
+__global__ void __launch_bounds__(kGNT) k_grad_param_rgl(int64_t N, int64_t Np, Geo g, Pot P,
+                                                         const double4_32a* __restrict__ x,
+                                                         const int* __restrict__ nn, const int* __restrict__ nl,
+                                                         int max_nb, const double* __restrict__ gs,
+                                                         const double* __restrict__ gE,
+                                                         const double* __restrict__ Fp,
+                                                         const double* __restrict__ Fpp,
+                                                         const double* __restrict__ u,
+                                                         double* __restrict__ partial) {
+    __shared__ double sT[kExpTable];
+    __shared__ double sh[kGNT / 32];
+    load_exp_table(sT, P.exp_T);
+    double acc[kRglParams] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = min(nn[i], max_nb);
+        const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
+        const double ge = box_gE(g, gE, i);
+        const double Fpi = Fp[i];
+        const double aF = u[i] * Fpp[i] + ge * Fpi;
+        for (int k = 0; k < n; ++k) {
+            int j = entry_slot(nl[(int64_t)k * Np + i]);
+            double dx, dy, dz;
+            sep(g, x, i, j, dx, dy, dz);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= P.rc2) continue;
+            double r = sqrt(r2);
+            double w = (gx * dx + gy * dy + gz * dz) / r;
+            rgl_param_terms(P, sT, r, w, w * (Fpi + Fp[j]), aF, 0.5 * ge, acc);
+        }
+    }
+    for (int k = 0; k < kRglParams; ++k) {
+        double t = block_sum<kGNT>(acc[k], sh);
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * kRglParams + k] = t;
+    }
+}
+
+// fixed-order sum of per-block partials, one block per output:
+// out[k] = sum_b partial[b * np + k]
+__global__ void __launch_bounds__(256) k_sum_partials(int nblocks, int np, const double* __restrict__ partial,
+                                                      double* __restrict__ out) {
+    __shared__ double sh[8];
+    int k = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) s += partial[(int64_t)b * np + k];
+    double t = block_sum<256>(s, sh);
+    if (threadIdx.x == 0) out[k] = t;
+}
+
+// ---------------------------------------------------------------- splines
+
+// Adjoint weights of one cubic piece c0 + c1 t + c2 t^2 + c3 t^3 (local
+// t): value weight aval, slope weight aslope -> coefficient gradients.
+__device__ __forceinline__ void piece_adj(double* sg, int k, double t, double aval, double aslope) {
+    double t2 = t * t;
+    atomicAdd(&sg[4 * k + 0], aval);
+    atomicAdd(&sg[4 * k + 1], aval * t + aslope);
+    atomicAdd(&sg[4 * k + 2], aval * t2 + 2.0 * t * aslope);
+    atomicAdd(&sg[4 * k + 3], aval * t2 * t + 3.0 * t2 * aslope);
+}
+
+// Adjoint of spline_eval for spline w at argument s (value weight aval,
+// slope weight aslope) into the coefficient gradients of spline w (layout:
+// per interval 4 values; the extrapolation entry above the range is mapped
+// onto the last interval: value c0+c1 h+c2 h^2+c3 h^3 and slope c1+2c2 h+3c3 h^2
+// at t = h, so the same piece adjoint with t = h covers it, plus the slope
+// weight times (s - t_end) on the value).
+__device__ __forceinline__ void spline_adj(const Pot& P, int w, double s, double aval, double aslope, double* sg) {
+    int n = P.sn[w];
+    double t0 = P.st0[w], h = P.sh[w];
+    double q = (s - t0) * P.sinvh[w];
+    if (q < 0.0) {
+        // value = c0 + c1 (s - t0) on interval 0, slope = c1
+        double t = s - t0;
+        atomicAdd(&sg[0], aval);
+        atomicAdd(&sg[1], aval * t + aslope);
+        return;
+    }
+    int k = (int)q;
+    if (k >= n - 1) {
+        // value = v_end + slope_end (s - t_end), slope = slope_end (last piece at t = h)
+        double te = s - (t0 + h * (n - 1));
+        piece_adj(sg, n - 2, h, aval, aslope + aval * te);
+        return;
+    }
+    piece_adj(sg, k, s - (t0 + h * k), aval, aslope);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_grad_param_spline(int64_t N, int64_t Np, Geo g, Pot P,
+                                                          const double4_32a* __restrict__ x,
+                                                          const int* __restrict__ nn, const int* __restrict__ nl,
+                                                          int max_nb, const double* __restrict__ gs,
+                                                          const double* __restrict__ gE,
+                                                          const double* __restrict__ rho,
+                                                          const double* __restrict__ Fp,
+                                                          const double* __restrict__ Fpp,
+                                                          const double* __restrict__ u, int ncoef,
+                                                          double* __restrict__ partial) {
+    extern __shared__ double sg[];  // [ncoef] coefficient gradients: V pieces, rho pieces, F pieces
+    for (int k = threadIdx.x; k < ncoef; k += NT) sg[k] = 0.0;
+    __syncthreads();
+    double* gV = sg;
+    double* gR = sg + 4 * (P.sn[0] - 1);
+    double* gF = gR + 4 * (P.sn[1] - 1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = min(nn[i], max_nb);
+        const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
+        const double ge = box_gE(g, gE, i);
+        const double Fpi = Fp[i];
+        const double aF = u[i] * Fpp[i] + ge * Fpi;
+        for (int k = 0; k < n; ++k) {
+            int j = entry_slot(nl[(int64_t)k * Np + i]);
+            double dx, dy, dz;
+            sep(g, x, i, j, dx, dy, dz);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= P.rc2) continue;
+            double r = sqrt(r2);
+            if (r >= P.rc) continue;
+            double w = (gx * dx + gy * dy + gz * dz) / r;
+            spline_adj(P, 0, r, 0.5 * ge, w, gV);
+            spline_adj(P, 1, r, aF, w * (Fpi + Fp[j]), gR);
+        }
+        // embedding: u_i dF'/dtheta + gE dF/dtheta at rho_i
+        spline_adj(P, 2, rho[i], ge, u[i], gF);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < ncoef; k += NT) partial[(int64_t)blockIdx.x * ncoef + k] = sg[k];
+}
+
+// Transpose of the knot-value -> coefficient map of one natural spline
+// (coefficients c0 = y_k, c1 = (y_{k+1}-y_k)/h - h(2M_k + M_{k+1})/6,
+// c2 = M_k/2, c3 = (M_{k+1}-M_k)/(6h), M = T^{-1} D y with T the symmetric
+// tridiagonal (h/6, 2h/3, h/6) on interior knots and (D y)_k =
+// (y_{k+1} - 2 y_k + y_{k-1})/h): gy = (d coef/d y)^T gc.
+__global__ void k_spline_adjoint(const double* __restrict__ gc_all, double* __restrict__ work,
+                                 double* __restrict__ gy_all, int n0, int n1, int n2, double h0, double h1,
+                                 double h2) {
+    int w = threadIdx.x;
+    if (w >= 3) return;
+    int n = w == 0 ? n0 : (w == 1 ? n1 : n2);
+    int koff = w == 0 ? 0 : (w == 1 ? n0 : n0 + n1);             // knot offset
+    int coff = w == 0 ? 0 : (w == 1 ? 4 * (n0 - 1) : 4 * (n0 - 1) + 4 * (n1 - 1));  // coefficient offset
+    double h = w == 0 ? h0 : (w == 1 ? h1 : h2);
+    const double* gc = gc_all + coff;
+    double* gy = gy_all + koff;
+    double* gM = work + 3 * koff;  // [n]
+    double* cp = gM + n;           // Thomas scratch
+    double* dp = cp + n;
+    for (int k = 0; k < n; ++k) {
+        gy[k] = 0.0;
+        gM[k] = 0.0;
+    }
+    for (int k = 0; k < n - 1; ++k) {
+        double g0 = gc[4 * k], g1 = gc[4 * k + 1], g2 = gc[4 * k + 2], g3 = gc[4 * k + 3];
+        gy[k] += g0 - g1 / h;
+        gy[k + 1] += g1 / h;
+        gM[k] += -g1 * h / 3.0 + 0.5 * g2 - g3 / (6.0 * h);
+        gM[k + 1] += -g1 * h / 6.0 + g3 / (6.0 * h);
+    }
+    // z = T^{-1} gM on the interior knots (T symmetric), Thomas algorithm
+    double a = h / 6.0, bd = 2.0 * h / 3.0, cu = h / 6.0;
+    for (int k = 1; k <= n - 2; ++k) {
+        double den = k == 1 ? bd : bd - a * cp[k - 1];
+        cp[k] = cu / den;
+        dp[k] = (k == 1 ? gM[k] : gM[k] - a * dp[k - 1]) / den;
+    }
+    for (int k = n - 2; k >= 1; --k) gM[k] = dp[k] - (k < n - 2 ? cp[k] * gM[k + 1] : 0.0);
+    // gy += D^T z
+    for (int k = 1; k <= n - 2; ++k) {
+        double z = gM[k] / h;
+        gy[k - 1] += z;
+        gy[k] -= 2.0 * z;
+        gy[k + 1] += z;
+    }
+}
+
+// ---------------------------------------------------------------- host
+
+__global__ void k_gather_g(int64_t N, int64_t Np, const double* __restrict__ g_f, const int* __restrict__ perm,
+                           double* __restrict__ gs) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    int64_t c = perm[t];
+    gs[t] = g_f ? g_f[3 * c] : 0.0;
+    gs[Np + t] = g_f ? g_f[3 * c + 1] : 0.0;
+    gs[2 * Np + t] = g_f ? g_f[3 * c + 2] : 0.0;
+}
+
+template <int KIND>
+static int grad_impl(Engine& e, const double* g_f, const double* g_e, double* grad, cudaStream_t s) {
+    Geo g = make_geo(e);
+    int nb = (int)((e.N + kGNT - 1) / kGNT);
+    int npb = e.grad_blocks;
+    k_gather_g<<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g_f, e.perm, e.grad_g);
+    k_grad_rho<KIND><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.rho, e.Fp, e.grad_Fpp);
+    k_grad_u<KIND><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.grad_g, e.grad_u);
+    e.launches += 3;
+    if (KIND == MD_POT_RGL) {
+        k_grad_param_rgl<<<npb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.grad_g, g_e,
+                                             e.Fp, e.grad_Fpp, e.grad_u, e.grad_partial);
+        k_sum_partials<<<kRglParams, 256, 0, s>>>(npb, kRglParams, e.grad_partial, grad);
+        e.launches += 2;
+    } else {
+        const md_potential& p = e.pot_host;
+        int ncoef = 4 * (p.n_phi - 1) + 4 * (p.n_f - 1) + 4 * (p.n_F - 1);
+        size_t smem = (size_t)ncoef * sizeof(double);
+        k_grad_param_spline<kGNT><<<npb, kGNT, smem, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb,
+                                                          e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp, e.grad_u, ncoef,
+                                                          e.grad_partial);
+        k_sum_partials<<<ncoef, 256, 0, s>>>(npb, ncoef, e.grad_partial, e.grad_coef);
+        k_spline_adjoint<<<1, 32, 0, s>>>(e.grad_coef, e.spline_work, grad, p.n_phi, p.n_f, p.n_F, e.pot.sh[0],
+                                          e.pot.sh[1], e.pot.sh[2]);
+        e.launches += 3;
+    }
+    return MD_OK;
+}
+
+int launch_param_grad(Engine& e, const double* g_f, const double* g_e, double* grad, cudaStream_t s) {
+    if (e.N == 0) return cudaMemsetAsync(grad, 0, sizeof(double) * (e.pot_host.kind == MD_POT_SPLINE ?
+                                              e.pot_host.n_phi + e.pot_host.n_f + e.pot_host.n_F : 5), s) ==
+                                  cudaSuccess ? MD_OK : MD_ERR_CUDA;
+    if (e.pot.kind == MD_POT_RGL) return grad_impl<MD_POT_RGL>(e, g_f, g_e, grad, s);
+    if (e.pot.kind == MD_POT_SPLINE) {
+        const md_potential& p = e.pot_host;
+        int ncoef = 4 * (p.n_phi - 1) + 4 * (p.n_f - 1) + 4 * (p.n_F - 1);
+        if ((size_t)ncoef * sizeof(double) > 200 * 1024) return MD_ERR_UNSUPPORTED;
+        if ((size_t)ncoef * sizeof(double) > 48 * 1024) {
+            cudaFuncSetAttribute(k_grad_param_spline<kGNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(ncoef * sizeof(double)));
+        }
+        return grad_impl<MD_POT_SPLINE>(e, g_f, g_e, grad, s);
+    }
+    return MD_ERR_UNSUPPORTED;
+}
 
 }  // namespace mdk

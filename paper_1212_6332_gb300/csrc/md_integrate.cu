@@ -1,6 +1,6 @@
 // Time integration, reductions and caller-order copies.
 //
-//   k_kick_drift   v += dt/2 F/m; x += dt v; wrap; largest displacement since
+//   k_kick_drift   v += dt/2 F/m; x += dt v; largest displacement since
 //                  the last list build (device rebuild trigger); mixed
 //                  precision: refresh the cell-local float32 offsets
 //   k_end_step     step bookkeeping on the device (no host round trip)
@@ -20,12 +20,13 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
                                                      double* __restrict__ v, const double* __restrict__ f,
                                                      const double4_32a* __restrict__ xb, double c_kick, double dt,
                                                      float4* __restrict__ xo, const int* __restrict__ cell_t,
-                                                     Ctl* ctl) {
+                                                     Ctl* ctl, unsigned long long* __restrict__ disp) {
     if (load_status(ctl)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double d2 = 0.0;
+    int b = -1;
     if (i < N) {
-        int b = SINGLE ? 0 : g.atom_box[i];
+        b = SINGLE ? 0 : g.atom_box[i];
         double L[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
@@ -34,16 +35,16 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
         double vx = v[i] + c_kick * f[i];
         double vy = v[Np + i] + c_kick * f[Np + i];
         double vz = v[2 * Np + i] + c_kick * f[2 * Np + i];
-        p.x = wrap_step(p.x + dt * vx, L[0]);
-        p.y = wrap_step(p.y + dt * vy, L[1]);
-        p.z = wrap_step(p.z + dt * vz, L[2]);
+        // no wrap here: positions stay continuous until the next list build
+        // (which wraps them), so the image stored in each list entry holds
+        p.x += dt * vx;
+        p.y += dt * vy;
+        p.z += dt * vz;
         v[i] = vx;
         v[Np + i] = vy;
         v[2 * Np + i] = vz;
         x[i] = p;
-        double dx = minimg(p.x - q.x, L[0], 0.5 * L[0]);
-        double dy = minimg(p.y - q.y, L[1], 0.5 * L[1]);
-        double dz = minimg(p.z - q.z, L[2], 0.5 * L[2]);
+        double dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
         d2 = dx * dx + dy * dy + dz * dz;
         if (MIXED) {
             int gc = cell_t[i];
@@ -59,37 +60,62 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
             xo[i] = make_float4(o[0], o[1], o[2], __int_as_float(xyz));
         }
     }
-    // block max of d2 (non-negative doubles order like their bit patterns)
+    // largest d2 per box (non-negative doubles order like their bit
+    // patterns): one atomic per block when the block lies in one box, per
+    // warp or per lane where a box boundary falls inside it
     __shared__ double sm[kINT / 32];
-    d2 = warp_max(d2);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2;
+    __shared__ int s_b0, s_b1;
+    if (threadIdx.x == 0) {
+        int64_t f = (int64_t)blockIdx.x * blockDim.x, l = min(f + blockDim.x, N) - 1;
+        s_b0 = SINGLE ? 0 : g.atom_box[f];
+        s_b1 = SINGLE ? 0 : g.atom_box[l];
+    }
+    __syncthreads();
+    if (s_b0 == s_b1) {
+        d2 = warp_max(d2);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int k = 0; k < kINT / 32; ++k) m = sm[k] > m ? sm[k] : m;
+            if (m > 0.0) atomicMax(&disp[s_b0], (unsigned long long)__double_as_longlong(m));
+        }
+    } else if (b >= 0 && d2 > 0.0) {
+        atomicMax(&disp[b], (unsigned long long)__double_as_longlong(d2));
+    }
+}
+
+// Closes a step: records the largest displacement over boxes, clears the
+// per-box displacement words and counts the step (one block, fixed order).
+__global__ void __launch_bounds__(1024) k_end_step(Ctl* ctl, int B, unsigned long long* __restrict__ disp) {
+    if (load_status(ctl)) return;
+    __shared__ unsigned long long sm[32];
+    unsigned long long m = 0ull;
+    for (int b = threadIdx.x; b < B; b += 1024) {
+        unsigned long long v = disp[b];
+        m = v > m ? v : m;
+        disp[b] = 0ull;
+    }
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int k = 0; k < kINT / 32; ++k) m = sm[k] > m ? sm[k] : m;
-        if (m > 0.0) atomicMax(&ctl->disp2_bits, (unsigned long long)__double_as_longlong(m));
+        unsigned long long t = 0ull;
+        for (int k = 0; k < 32; ++k) t = sm[k] > t ? sm[k] : t;
+        ctl->disp2_last = t;
+        ctl->step += 1;
     }
 }
 
-__global__ void k_end_step(Ctl* ctl) {
-    if (load_status(ctl)) return;
-    ctl->disp2_last = ctl->disp2_bits;
-    ctl->disp2_bits = 0ull;
-    ctl->step += 1;
-    if (ctl->rebuilt) {
-        ctl->n_rebuild += 1;
-        ctl->rebuilt = 0;
+__global__ void k_reset_ctl(Ctl* ctl, int B, unsigned long long* __restrict__ disp) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->status = 0;
+        ctl->overflow_count = 0;
+        ctl->disp2_last = 0ull;
+        ctl->step = 0;
+        ctl->n_rebuild = 0;
     }
-}
-
-__global__ void k_reset_ctl(Ctl* ctl) {
-    ctl->status = 0;
-    ctl->overflow_count = 0;
-    ctl->disp2_bits = 0ull;
-    ctl->disp2_last = 0ull;
-    ctl->step = 0;
-    ctl->n_rebuild = 0;
-    ctl->rebuilt = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) disp[b] = 0ull;
 }
 
 constexpr int kRNT = 256;
@@ -165,7 +191,7 @@ static void kick_drift_t(Engine& e, cudaStream_t s) {
     PhaseScope scope(e, MD_PHASE_KICK_DRIFT, s);
     e.launches += 1;
     k_kick_drift<SINGLE, MIXED><<<nb, kINT, 0, s>>>(e.N, e.N_pad, g, e.x, e.v, e.f, e.xb, c_kick, e.cfg.dt, e.xo,
-                                                   e.cell_t, e.ctl);
+                                                   e.cell_t, e.ctl, e.disp_box);
 }
 
 void launch_kick_drift(Engine& e, cudaStream_t s) {
@@ -181,7 +207,7 @@ void launch_end_step(Engine& e, int record_hist, cudaStream_t s) {
     if (record_hist) launch_thermo_hist(e, s);
     PhaseScope scope(e, MD_PHASE_OTHER, s);
     e.launches += 1;
-    k_end_step<<<1, 1, 0, s>>>(e.ctl);
+    k_end_step<<<1, 1024, 0, s>>>(e.ctl, e.B, e.disp_box);
 }
 
 static void thermo_impl(Engine& e, bool hist, cudaStream_t s) {
@@ -197,9 +223,16 @@ static void thermo_impl(Engine& e, bool hist, cudaStream_t s) {
 void launch_thermo(Engine& e, cudaStream_t s) { thermo_impl(e, false, s); }
 void launch_thermo_hist(Engine& e, cudaStream_t s) { thermo_impl(e, true, s); }
 
+__global__ void k_advance_steps(Ctl* ctl, long long n) { ctl->step += n; }
+
+void launch_advance_steps(Engine& e, long long n, cudaStream_t s) {
+    e.launches += 1;
+    k_advance_steps<<<1, 1, 0, s>>>(e.ctl, n);
+}
+
 void launch_reset_ctl(Engine& e, cudaStream_t s) {
     e.launches += 1;
-    k_reset_ctl<<<1, 1, 0, s>>>(e.ctl);
+    k_reset_ctl<<<(e.B + 255) / 256, 256, 0, s>>>(e.ctl, e.B, e.disp_box);
 }
 
 // ---------------------------------------------------------------- copies
@@ -229,7 +262,7 @@ __global__ void k_load_vel(int64_t N, int64_t Np, const double* __restrict__ src
 }
 
 __global__ void k_store_vec(int64_t N, int64_t Np, const double* __restrict__ soa, const double4_32a* __restrict__ x4,
-                            const int* __restrict__ perm, double* __restrict__ dst) {
+                            const int* __restrict__ perm, double* __restrict__ dst, Geo g) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
     int64_t c = perm[t];
@@ -238,10 +271,12 @@ __global__ void k_store_vec(int64_t N, int64_t Np, const double* __restrict__ so
         dst[3 * c + 1] = soa[Np + t];
         dst[3 * c + 2] = soa[2 * Np + t];
     } else {
+        // positions leave the library wrapped into the box
         double4_32a p = x4[t];
-        dst[3 * c] = p.x;
-        dst[3 * c + 1] = p.y;
-        dst[3 * c + 2] = p.z;
+        int b = g.B == 1 ? 0 : g.atom_box[t];
+        dst[3 * c] = wrap_step(p.x, g.L[3 * b]);
+        dst[3 * c + 1] = wrap_step(p.y, g.L[3 * b + 1]);
+        dst[3 * c + 2] = wrap_step(p.z, g.L[3 * b + 2]);
     }
 }
 
@@ -261,7 +296,7 @@ __global__ void k_get_neighbors(int64_t N, int64_t Np, const int* __restrict__ n
     int n = nn[t];
     nn_out[c] = n;
     int m = min(min(n, max_nb), ld);
-    for (int k = 0; k < m; ++k) nl_out[c * ld + k] = perm[nl[(int64_t)k * Np + t]];
+    for (int k = 0; k < m; ++k) nl_out[c * ld + k] = perm[entry_slot(nl[(int64_t)k * Np + t])];
 }
 
 __global__ void k_box_energy(int B, const double* __restrict__ thermo, double* __restrict__ e_box) {
@@ -293,7 +328,7 @@ void launch_load_velocities(Engine& e, const double* src, cudaStream_t s) {
 void launch_store_vec(Engine& e, const double* soa, const double4_32a* x4, double* dst, cudaStream_t s) {
     if (e.N == 0) return;
     e.launches += 1;
-    k_store_vec<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, soa, x4, e.perm, dst);
+    k_store_vec<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, soa, x4, e.perm, dst, make_geo(e));
 }
 
 void launch_store_scalar(Engine& e, const double* src, double* dst, cudaStream_t s) {

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, G
     const int n = min(nn[i], max_nb);
     KSum acc;
     for (int k = 0; k < n; ++k) {
-        int j = nl[(int64_t)k * Np + i];
+        int j = entry_slot(nl[(int64_t)k * Np + i]);
         float dx, dy, dz;
         sep_mixed(cs, oi, xo[j], dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
     const int n = min(nn[i], max_nb);
     KSum ax, ay, az, ae;
     for (int k = 0; k < n; ++k) {
-        int j = nl[(int64_t)k * Np + i];
+        int j = entry_slot(nl[(int64_t)k * Np + i]);
         float dx, dy, dz;
         sep_mixed(cs, oi, xo[j], dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;

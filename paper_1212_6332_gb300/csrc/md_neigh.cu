@@ -29,24 +29,11 @@ constexpr int kNlThreads = 128;
 constexpr int kNlCap = 1024;  // staged candidates per pass
 constexpr int kNlMaxI = 256;  // centre-cell atoms per pass
 
-__device__ __forceinline__ bool rebuild_wanted_nl(const Ctl* c, int mode, unsigned long long thr) {
+__device__ __forceinline__ bool box_wants_nl(const Ctl* c, const unsigned long long* disp, int b, int mode,
+                                             unsigned long long thr) {
     if (load_status(c)) return false;
     if (mode) return true;
-    return *((volatile const unsigned long long*)&c->disp2_bits) > thr;
-}
-
-// Candidate test. A float32 separation from the cell-local offsets (exact
-// cell difference times the cell side plus the offset difference) decides
-// every candidate whose r^2 lies farther than `margin` from rl^2; the float32
-// error of that r^2 is below 2e-4 A^2 for the cell sides used here, and
-// margin = 4e-4 * rl A^2 covers it with a wide factor. The few candidates
-// inside the band (~0.01 per atom) take the exact float64 test, which alone
-// decides membership, so the list equals the oracle's bit for bit.
-__device__ __forceinline__ int cell_delta(int cj, int ci, int n) {
-    int d = cj - ci;
-    if (2 * d > n) return d - n;
-    if (2 * d < -n) return d + n;
-    return d;
+    return disp[b] > thr;
 }
 
 __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_32a* __restrict__ x,
@@ -54,8 +41,8 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
                                                            const int* __restrict__ cell_start,
                                                            int* __restrict__ nn, int* __restrict__ nl, int max_nb,
                                                            int64_t N_pad, double rl2, float rl2f_lo, float rl2f_hi,
-                                                           Ctl* ctl, int mode, unsigned long long thr) {
-    if (!rebuild_wanted_nl(ctl, mode, thr)) return;
+                                                           Ctl* ctl, const unsigned long long* __restrict__ disp,
+                                                           int mode, unsigned long long thr) {
     __shared__ float4 so[kNlCap];
     __shared__ int sj[kNlCap];
     __shared__ int cnt[kNlMaxI];
@@ -64,11 +51,12 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
 
     const int c = blockIdx.x;
     const int b = g.cell_box[c];
+    if (!box_wants_nl(ctl, disp, b, mode, thr)) return;
+    const int base = (int)g.atom_off[b] - cell_start[g.cell_off[b]];
     const int xyz = g.cell_xyz[c];
     const int cc[3] = {xyz & 1023, (xyz >> 10) & 1023, (xyz >> 20) & 1023};
     const int ncx = g.nc[3 * b], ncy = g.nc[3 * b + 1], ncz = g.nc[3 * b + 2];
     const double Lx = g.L[3 * b], Ly = g.L[3 * b + 1], Lz = g.L[3 * b + 2];
-    const double hx = 0.5 * Lx, hy = 0.5 * Ly, hz = 0.5 * Lz;
     const float lfx = g.cell_len_f[3 * b], lfy = g.cell_len_f[3 * b + 1], lfz = g.cell_len_f[3 * b + 2];
     const float Lfx = (float)Lx, Lfy = (float)Ly, Lfz = (float)Lz;
 
@@ -83,7 +71,7 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
                     int ox = ncx >= 3 ? ix - 1 : ix, oy = ncy >= 3 ? iy - 1 : iy, oz = ncz >= 3 ? iz - 1 : iz;
                     int qx = (cc[0] + ox + ncx) % ncx, qy = (cc[1] + oy + ncy) % ncy, qz = (cc[2] + oz + ncz) % ncz;
                     int q = g.cell_rank[g.cell_off[b] + (qx * ncy + qy) * ncz + qz];
-                    int lo = cell_start[q], hi = cell_start[q + 1];
+                    int lo = base + cell_start[q], hi = base + cell_start[q + 1];
                     st_lo[k] = lo;
                     st_pre[k] = pre;
                     pre += hi - lo;
@@ -94,7 +82,7 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
     }
     __syncthreads();
     const int n_cand = st_pre[n_st];
-    const int i_lo = cell_start[c], i_hi = cell_start[c + 1];
+    const int i_lo = base + cell_start[c], i_hi = base + cell_start[c + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     int my_max = 0;
@@ -117,41 +105,24 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
             for (int ii = warp; ii < ni; ii += kNlThreads / 32) {
                 const int i = ib + ii;
                 const float4 oi = xo[i];
+                const double4_32a xi = x[i];
                 const int ci = __float_as_int(oi.w);
                 const int cix = ci & 1023, ciy = (ci >> 10) & 1023, ciz = (ci >> 20) & 1023;
                 int n = cnt[ii];
                 for (int jb = 0; jb < nc_; jb += 32) {
                     int jj = jb + lane;
                     bool ok = false;
-                    int j = -1;
+                    int j = -1, sx = 0, sy = 0, sz = 0;
                     if (jj < nc_) {
                         j = sj[jj];
-                        float4 oj = so[jj];
-                        int cj = __float_as_int(oj.w);
-                        float dx = fmaf((float)cell_delta(cj & 1023, cix, ncx), lfx, oj.x - oi.x);
-                        float dy = fmaf((float)cell_delta((cj >> 10) & 1023, ciy, ncy), lfy, oj.y - oi.y);
-                        float dz = fmaf((float)cell_delta((cj >> 20) & 1023, ciz, ncz), lfz, oj.z - oi.z);
-                        dx = minimgf(dx, Lfx, 0.5f * Lfx);
-                        dy = minimgf(dy, Lfy, 0.5f * Lfy);
-                        dz = minimgf(dz, Lfz, 0.5f * Lfz);
-                        float r2f = dx * dx + dy * dy + dz * dz;
-                        if (r2f < rl2f_lo) {
-                            ok = true;
-                        } else if (r2f <= rl2f_hi) {
-                            const double4_32a xi = x[i];
-                            const double4_32a xj = x[j];
-                            double ex = minimg(__dsub_rn(xj.x, xi.x), Lx, hx);
-                            double ey = minimg(__dsub_rn(xj.y, xi.y), Ly, hy);
-                            double ez = minimg(__dsub_rn(xj.z, xi.z), Lz, hz);
-                            double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-                            ok = r2 < rl2;
-                        }
-                        ok = ok && (j != i);
+                        ok = list_candidate(oi, so[jj], xi, x, j, cix, ciy, ciz, ncx, ncy, ncz, lfx, lfy, lfz, Lfx,
+                                            Lfy, Lfz, Lx, Ly, Lz, rl2, rl2f_lo, rl2f_hi, sx, sy, sz) &&
+                             (j != i);
                     }
                     unsigned m = __ballot_sync(0xffffffffu, ok);
                     if (ok) {
                         int pos = n + __popc(m & lt_mask);
-                        if (pos < max_nb) nl[(int64_t)pos * N_pad + i] = j;
+                        if (pos < max_nb) nl[(int64_t)pos * N_pad + i] = make_entry(j, sx, sy, sz);
                     }
                     n += __popc(m);
                 }
@@ -176,8 +147,10 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
     }
 }
 
-__global__ void k_reset_max_count(Ctl* ctl, int mode, unsigned long long thr) {
-    if (!rebuild_wanted_nl(ctl, mode, thr)) return;
+// A full rebuild restarts the largest-count record; partial rebuilds only
+// raise it, so it stays an upper bound of every current list.
+__global__ void k_reset_max_count(Ctl* ctl, int mode) {
+    if (load_status(ctl) || !mode) return;
     ctl->max_count = 0;
 }
 
@@ -191,9 +164,9 @@ void launch_build_list(Engine& e, int mode, cudaStream_t s) {
     double rl2 = e.rl * e.rl;
     double margin = 4e-4 * e.rl;
     float lo = (float)(rl2 - margin), hi = (float)(rl2 + margin);
-    k_reset_max_count<<<1, 1, 0, s>>>(e.ctl, mode, thr);
+    k_reset_max_count<<<1, 1, 0, s>>>(e.ctl, mode);
     k_build_list<<<e.n_cells, kNlThreads, 0, s>>>(g, e.x, e.xo, e.cell_start, e.nn, e.nl, e.max_nb, e.N_pad, rl2, lo,
-                                                 hi, e.ctl, mode, thr);
+                                                 hi, e.ctl, e.disp_box, mode, thr);
 }
 
 }  // namespace mdk

@@ -27,7 +27,8 @@ SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_
            "md_batch_destroy", "md_batch_set_state", "md_batch_get_state", "md_batch_compute_forces",
            "md_batch_step", "md_batch_set_potential", "md_param_grad", "md_num_params", "md_status_string",
            "md_last_error", "md_profile_start", "md_profile_read",
-           "md_eval_math", "md_forces_noalloc")
+           "md_eval_math", "md_forces_noalloc", "md_batch_thermo",
+           "md_batch_schedule")
 NOALLOC_MAX_ATOMS = 16384
 PHASES = ("kick_drift", "rebuild", "density", "force", "other")
 
@@ -104,6 +105,8 @@ def load(path: str | pathlib.Path | None = None) -> ctypes.CDLL:
         "md_profile_read": [vp, P(Profile)],
         "md_eval_math": [vp, i32, dp, i64, dp, vp],
         "md_forces_noalloc": [P(Potential), dp, i64, dp, dp, dp, dp, vp],
+        "md_batch_thermo": [vp, dp, vp],
+        "md_batch_schedule": [vp, P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_double)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -299,6 +302,19 @@ class System:
         sched = {"auto": SCHED_AUTO, "box": SCHED_BOX, "tile": SCHED_TILE}[schedule]
         tb = self._empty(self.n_boxes, 4) if per_box else None
         self._check(self.lib.md_batch_step(self._h, int(n), sched, int(use_graph), _ptr(tb), _stream()))
+        return tb
+
+    def schedule(self) -> dict:
+        """The autotuner's pick ("tile", "box" or None) and its timings (ms/step)."""
+        c, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.md_batch_schedule(self._h, ctypes.byref(c), ctypes.byref(a), ctypes.byref(b)))
+        return dict(choice={0: None, SCHED_BOX: "box", SCHED_TILE: "tile"}[c.value], ms_tile=a.value,
+                    ms_box=b.value)
+
+    def batch_thermo(self):
+        """[n_boxes, 4] (ke, pe, etot, T) of the current state (CUDA tensor)."""
+        tb = self._empty(self.n_boxes, 4)
+        self._check(self.lib.md_batch_thermo(self._h, _ptr(tb), _stream()))
         return tb
 
     def set_potential(self, spec: dict):

@@ -1,0 +1,78 @@
+"""Parameter adjoint (md_param_grad) against the oracle's forward-mode
+derivatives and against central finite differences of the loss."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1212_6332_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+RHO_EQ = 20.620605425592796
+MODEL = dict(I.RGL_CU, A=0.0855 * 1.05, xi=1.224 * 0.95, p=10.96 * 1.05, q=2.278 * 0.95, r0=2.5562 * 1.05)
+
+
+def configs(ns=(3, 4, 3), seed=10):
+    return [I.strained_fcc(n, I.A_CU, seed=seed + k) for k, n in enumerate(ns)]
+
+
+def oracle_grad(spec, cfgs, g_f, g_e):
+    pot = O.Potential(spec)
+    grad = np.zeros(pot.n_param)
+    off = 0
+    for c, ge in zip(cfgs, g_e):
+        O.param_grad(pot, c.x, c.box, g_f[off:off + c.n], ge, grad)
+        off += c.n
+    return grad
+
+
+@pytest.mark.parametrize("kind", ["rgl", "spline"])
+def test_adjoint_matches_oracle_forward_mode(kind):
+    import torch
+    from paper_1212_6332_gb300.fit import make_batch
+    spec = MODEL if kind == "rgl" else O.tabulate_spline(MODEL, n_knots=60, rho_hi=2 * RHO_EQ)
+    cfgs = configs()
+    s = make_batch(spec, cfgs)
+    n = sum(c.n for c in cfgs)
+    rng = np.random.default_rng(5)
+    g_f = rng.normal(size=(n, 3))
+    g_e = rng.normal(size=len(cfgs))
+    got = s.param_grad(torch.tensor(g_f, device="cuda"), torch.tensor(g_e, device="cuda")).cpu().numpy()
+    ref = oracle_grad(spec, cfgs, g_f, g_e)
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+
+
+def test_autograd_loss_gradient_matches_finite_differences():
+    import torch
+    from paper_1212_6332_gb300.fit import ForceField, force_matching_loss, make_batch, spec_of, theta_of
+    cfgs = configs((3, 3, 4, 3), seed=20)
+    ref = make_batch(I.RGL_CU, cfgs)
+    f_tgt = ref.get_forces()["f"].clone()
+    e_tgt = ref.batch_thermo()[:, 1].clone()
+    counts = torch.tensor([c.n for c in cfgs], device="cuda", dtype=torch.float64)
+    s = make_batch(MODEL, cfgs)
+    theta = theta_of(MODEL).requires_grad_(True)
+
+    def loss_at(th):
+        f, e = ForceField.apply(th, s, MODEL)
+        return force_matching_loss(f, e, f_tgt, e_tgt, counts)
+
+    L = loss_at(theta)
+    (g,) = torch.autograd.grad(L, theta)
+    for k in range(5):
+        h = 1e-6 * abs(theta[k].item())
+        tp, tm = theta.detach().clone(), theta.detach().clone()
+        tp[k] += h
+        tm[k] -= h
+        fd = (loss_at(tp).item() - loss_at(tm).item()) / (2 * h)
+        assert g[k].item() == pytest.approx(fd, rel=1e-6), (k, g[k].item(), fd)
+
+
+def test_adjoint_with_zero_upstream_is_zero():
+    import torch
+    from paper_1212_6332_gb300.fit import make_batch
+    cfgs = configs((3,), seed=3)
+    s = make_batch(MODEL, cfgs)
+    z = torch.zeros(cfgs[0].n, 3, dtype=torch.float64, device="cuda")
+    g = s.param_grad(z, torch.zeros(1, dtype=torch.float64, device="cuda"))
+    assert torch.count_nonzero(g) == 0
