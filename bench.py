@@ -43,20 +43,25 @@ ORACLE_CELLS = 50        # CPU sample: 500,000 atoms of the same lattice
 # Algorithmic float64 work per neighbour-list entry, counting each add, mul
 # and compare as 1 flop, an FMA as 2, and exp, sqrt (or rsqrt) and a
 # division as 15, 8 and 8 flops (the cost of a table-free float64 evaluation
-# by polynomial / Newton steps).
-# Density pass, RGL, entry inside r_cut: separation 3, r^2 5, rsqrt 8, r 1,
-# two exp arguments 4, two exp 30, prefactors 2, A = V'/r and B = rho'/r 6,
-# sums 2 -> 61; entry outside r_cut: separation 3 + r^2 5 = 8.
-DENSITY_FLOPS_IN, DENSITY_FLOPS_OUT = 61.0, 8.0
-# Force pass, entry inside r_cut: separation 3, s = A + (F'_i + F'_j) B 3,
-# F_i += s d 6 -> 12; outside r_cut: 0 (skipped).
-FORCE_FLOPS_IN, FORCE_FLOPS_OUT = 12.0, 0.0
-# Bytes per atom (x_j, F'_j gathers counted once, as ideal cache reuse of
-# the Morton-sorted arrays). Density: list 4K + (A, B) write 16K + count 4 +
-# x_i 32 + rho, F', E_i writes 24. Force: list 4K + (A, B) read 16K + count 4
-# + x_i 32 + F'_i 8 + F write 24 + v read/write 48.
-DENSITY_BYTES = (20.0, 60.0)
-FORCE_BYTES = (20.0, 116.0)
+# by polynomial / Newton steps). K = list length, K_in = entries inside r_cut.
+# Pair pass (k_pairs_half), RGL, per pair evaluated (the K/2 upper entries):
+# separation 3, r^2 5, rsqrt 8, r 1, two exp arguments 4, two exp 30,
+# prefactors 2, A = V'/r and B = rho'/r 6 -> 59 inside r_cut, 8 outside.
+# Density sums (k_rho_sum): 2 per entry. Force pass (k_force): separation
+# 3, s = A + (F'_i + F'_j) B 3, F_i += s d 6 -> 12 per entry inside r_cut.
+KERNELS = {
+    # phase: (kernel, flops(K, K_in), bytes(K, K_in)) per atom
+    "pairs": ("k_pairs_half (float64 pair functions)",
+              lambda K, Ki: Ki / 2 * 59.0 + (K - Ki) / 2 * 8.0,
+              # list 4K, reverse index 2K, (A,B) and (rho,V) written to both slots 32K, x 32
+              lambda K, Ki: 38.0 * K + 32.0),
+    "density": ("k_rho_sum (float64 density sums)", lambda K, Ki: 2.0 * K,
+                # count 4, (rho, V) reads 16K, rho/F'/E_i writes 24
+                lambda K, Ki: 16.0 * K + 28.0),
+    "force": ("k_force (float64 force pass)", lambda K, Ki: 12.0 * Ki,
+              # list 4K, (A,B) reads 16K, count 4, x_i 32, F'_i 8, F 24, v 48
+              lambda K, Ki: 20.0 * K + 116.0),
+}
 # Nominal GB300 float64 rate (no measured float64 peak is provided).
 FP64_PEAK_TFLOPS = 1.25
 
@@ -134,6 +139,20 @@ def dist_env():
     return world, rank, local
 
 
+def combine_ranks(local_ms: float, atoms_per_rank: int, steps: int, dist=None, device="cuda") -> tuple[float, float]:
+    """Whole-job rate of independent replicas: every rank advances its own
+    box; the job's time is the slowest rank's. Returns (atom-steps/s over
+    all ranks, slowest rank's ms)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms = float(t.item())
+    return world * atoms_per_rank * steps / (ms * 1e-3), ms
+
+
 def list_stats(sysm, x_dev, box, rc, sample: int = 65536):
     """Mean list length K and mean entries inside r_cut over a sample of atoms."""
     import torch
@@ -201,22 +220,27 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_variant(precision: str, W: int, K: int, x_h, v_h, box):
-    """atom-steps/s of the same box in another precision (same timing rules)."""
+def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=None) -> dict:
+    """atom-steps/s of a box in another precision or potential (same timing
+    rules), with its per-phase times."""
     import torch
     from paper_1212_6332_gb300.md import System
-    s = System(I.RGL_CU, box=box, n_atoms=len(x_h), skin=SKIN, dt=DT, mass=I.MASS_CU, precision=precision)
+    spec = spec or I.RGL_CU
+    s = System(spec, box=box, n_atoms=len(x_h), skin=SKIN, dt=DT, mass=mass or I.MASS_CU, precision=precision)
     s.set_state(torch.tensor(x_h, device="cuda"), torch.tensor(v_h, device="cuda"))
     s.step(W)
     torch.cuda.synchronize()
+    s.profile_start(timing=True)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     th = s.step(K)
     b.record()
     b.synchronize()
     ms = a.elapsed_time(b)
+    prof = s.profile_read()
     s.close()
-    return dict(value=len(x_h) * K / (ms * 1e-3), ms_per_step=ms / K, n_rebuild=th["n_rebuild"])
+    return dict(value=len(x_h) * K / (ms * 1e-3), ms_per_step=ms / K, n_rebuild=th["n_rebuild"],
+                phase_ms_per_step={k: v / max(K, 1) for k, v in prof["ms"].items()})
 
 
 def run_batch(precision: str, K: int, W: int, n_boxes: int = 4096, use_graph: bool = True,
@@ -346,7 +370,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS)
-    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-precision and oracle legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-precision, batch, gradient and oracle legs")
+    ap.add_argument("--e2e-steps", type=int, default=10, help="host-buffer end-to-end steps (0 skips the leg)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="precision of the headline box (default float64)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -369,7 +396,7 @@ def main():
     N = bx.n
     x_dev = torch.tensor(bx.x, device="cuda")
     v_dev = torch.tensor(bx.v, device="cuda")
-    s = System(I.RGL_CU, box=bx.box, n_atoms=N, skin=SKIN, dt=DT, mass=I.MASS_CU, precision="fp64")
+    s = System(I.RGL_CU, box=bx.box, n_atoms=N, skin=SKIN, dt=DT, mass=I.MASS_CU, precision=args.precision)
     s.set_state(x_dev, v_dev)
     K_list, K_in = list_stats(s, x_dev, bx.box, I.RGL_CU["r_cut"])
     s.step(W)
@@ -391,22 +418,15 @@ def main():
         barrier()
     prof = s.profile_read()
     ms = ev0.elapsed_time(ev1)
-    t_local = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = t_local.item()
-    value = world * N * K / (ms_max * 1e-3)
+    value, ms_max = combine_ranks(ms, N, K, dist)
 
     # dominant kernel (event-timed on the launching stream)
-    dom = "density" if prof["ms"]["density"] >= prof["ms"]["force"] else "force"
+    dom = max(KERNELS, key=lambda k: prof["ms"][k])
     k_ms = prof["ms"][dom] / max(prof["timed"][dom], 1)
-    if dom == "density":
-        fin, fout, (bk, b0), kname = DENSITY_FLOPS_IN, DENSITY_FLOPS_OUT, DENSITY_BYTES, "k_density (float64 density pass)"
-    else:
-        fin, fout, (bk, b0), kname = FORCE_FLOPS_IN, FORCE_FLOPS_OUT, FORCE_BYTES, "k_force (float64 force pass)"
-    flops = N * (K_in * fin + (K_list - K_in) * fout)
+    kname, ffl, fby = KERNELS[dom]
+    flops = N * ffl(K_list, K_in)
     achieved = flops / (k_ms * 1e-3) / 1e12
-    bytes_k = N * (bk * K_list + b0)
+    bytes_k = N * fby(K_list, K_in)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
@@ -424,7 +444,7 @@ def main():
     xh = torch.empty((N, 3), dtype=torch.float64, pin_memory=True)
     vh = torch.empty((N, 3), dtype=torch.float64, pin_memory=True)
     s.get_state(xh, vh)
-    K_e2e = max(3, min(K, 10))
+    K_e2e = min(args.e2e_steps, max(K, 3))
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
@@ -434,10 +454,9 @@ def main():
         s.get_state(xh, vh)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    e2e_t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * N * K_e2e / e2e_t.item(), "unit": UNIT, "h2d_bytes_per_step": 2 * N * 3 * 8,
+    e2e_value = combine_ranks(t_e2e * 1e3, N, K_e2e, dist)[0] if K_e2e > 0 else None
+    e2e = {"value": e2e_value, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * N * 3 * 8,
            "d2h_bytes_per_step": 2 * N * 3 * 8 + 56,
            "call": "md_set_state(host) + md_step(1) + md_get_state(host) per step", "steps": K_e2e}
 
@@ -449,6 +468,12 @@ def main():
         del s
         variants["mixed"] = run_variant("mixed", W, K, bx.x, bx.v, bx.box)
         variants["fp64"] = {"value": value, "ms_per_step": ms_max / K}
+        hot = I.perturbed_fcc(args.cells, I.A_CU, 1200.0, I.MASS_CU, 2)
+        variants["fp64_1200K"] = run_variant("fp64", W, K, hot.x, hot.v, hot.box)
+        variants["mixed_1200K"] = run_variant("mixed", W, K, hot.x, hot.v, hot.box)
+        variants["sc_fp64"] = run_variant("fp64", W, max(5, K // 3), bx.x, bx.v, bx.box, spec=I.SC_CU)
+        variants["sc_mixed"] = run_variant("mixed", W, K, bx.x, bx.v, bx.box, spec=I.SC_CU)
+        del hot
         del x_dev, v_dev
         torch.cuda.empty_cache()
         kb = max(5, min(K, 20))
@@ -466,9 +491,10 @@ def main():
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f64", "data": "synthetic",
+               "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
                "config": {"workload": f"fcc Cu {args.cells}^3 cells ({N} atoms), RGL Cu taper 4.5-5.0 A, "
-                                      f"skin {SKIN} A, {TEMP:.0f} K, dt {DT} fs, float64",
+                                      f"skin {SKIN} A, {TEMP:.0f} K, dt {DT} fs, "
+                                      + ("float64" if args.precision == "fp64" else "mixed precision"),
                           "atoms": N, "parallelism": "replicas" if world > 1 else "single",
                           "l2": "working set (list + positions) larger than L2",
                           "mean_list_len": K_list, "mean_in_cutoff": K_in,

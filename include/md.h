@@ -259,12 +259,14 @@ MD_API int md_num_params(const md_batch* b);
 
 /* Phases of a step, for md_profile. */
 enum md_phase {
-    MD_PHASE_KICK_DRIFT = 0, /* first half-kick, drift, wrap, displacement check */
+    MD_PHASE_KICK_DRIFT = 0, /* first half-kick, drift, displacement check */
     MD_PHASE_REBUILD = 1,    /* binning, sort and list build (early exit when not due) */
-    MD_PHASE_DENSITY = 2,    /* density pass and embedding derivative */
-    MD_PHASE_FORCE = 3,      /* force pass and second half-kick */
-    MD_PHASE_OTHER = 4,      /* step bookkeeping, reductions, copies */
-    MD_PHASE_COUNT = 5
+    MD_PHASE_PAIRS = 2,      /* float64: pair functions, once per pair, into both lists */
+    MD_PHASE_DENSITY = 3,    /* density sums and embedding derivative (mixed: the whole
+                                density pass) */
+    MD_PHASE_FORCE = 4,      /* force pass and second half-kick (box schedule: all phases) */
+    MD_PHASE_OTHER = 5,      /* step bookkeeping, reductions, copies */
+    MD_PHASE_COUNT = 6
 };
 
 /* Kernel launches issued by a handle since md_profile_start, and (when

@@ -206,7 +206,7 @@ void free_engine(Engine& e) {
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
     dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
-    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.ab); dfree(e.exp_T);
+    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.ab); dfree(e.fv); dfree(e.rev); dfree(e.n_up); dfree(e.exp_T);
     dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
     dfree(e.grad_g); dfree(e.grad_u); dfree(e.grad_Fpp); dfree(e.grad_partial); dfree(e.grad_coef); dfree(e.stage); dfree(e.red);
     dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box);
@@ -298,6 +298,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
         e.cell_off_h[b + 1] = (int)tot;
     }
     e.n_cells = (int)tot;
+    e.wide = *std::min_element(e.nc_h.begin(), e.nc_h.end()) >= 3;
     std::vector<int> rank(tot), xyz(tot), cbox(tot);
     for (int b = 0; b < B; ++b) {
         int nx = e.nc_h[3 * b], ny = e.nc_h[3 * b + 1], nz = e.nc_h[3 * b + 2];
@@ -393,7 +394,12 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.scan_tmp, tot / 1024 + 2);
     AL(e.nn, Np);
     AL(e.nl, (size_t)e.max_nb * Np);
-    if (cfg->precision == MD_FP64) AL(e.ab, (size_t)e.max_nb * Np);
+    if (cfg->precision == MD_FP64) {
+        AL(e.ab, (size_t)e.max_nb * Np);
+        AL(e.fv, (size_t)e.max_nb * Np);
+        AL(e.rev, (size_t)e.max_nb * Np);
+        AL(e.n_up, Np);
+    }
     AL(e.exp_T, kExpTable);
     AL(e.stage, 3 * std::max<size_t>(e.N, 1));
     AL(e.red, 2 * std::max(e.n_chunks, 1));
@@ -515,13 +521,21 @@ int grow_list(Engine* E, int needed) {
     int* nl = nullptr;
     if (dalloc(E, &nl, (size_t)m * e.N_pad) != MD_OK) return MD_ERR_NOMEM;
     if (e.ab) {
-        double2* ab = nullptr;
-        if (dalloc(E, &ab, (size_t)m * e.N_pad) != MD_OK) {
+        double2 *ab = nullptr, *fv = nullptr;
+        int* rev = nullptr;
+        if (dalloc(E, &ab, (size_t)m * e.N_pad) != MD_OK || dalloc(E, &fv, (size_t)m * e.N_pad) != MD_OK ||
+            dalloc(E, &rev, (size_t)m * e.N_pad) != MD_OK) {
             cudaFree(nl);
+            if (ab) cudaFree(ab);
+            if (fv) cudaFree(fv);
             return MD_ERR_NOMEM;
         }
         cudaFree(e.ab);
+        cudaFree(e.fv);
+        cudaFree(e.rev);
         e.ab = ab;
+        e.fv = fv;
+        e.rev = rev;
     }
     cudaFree(e.nl);
     e.nl = nl;
@@ -579,6 +593,7 @@ int set_positions(Engine* E, const double* x, const double* v, bool set_v, cudaS
         return MD_OK;
     }
     const double* xd = nullptr;
+    launch_reset_ctl(e, s);
     int rc = stage_in(E, x, 3 * (size_t)e.N, s, &xd);
     if (rc) return rc;
     launch_load_positions(e, xd, s);
@@ -587,8 +602,10 @@ int set_positions(Engine* E, const double* x, const double* v, bool set_v, cudaS
         if (v && (rc = stage_in(E, v, 3 * (size_t)e.N, s, &vd))) return rc;
         launch_load_velocities(e, vd, s);
     }
-    launch_reset_ctl(e, s);
     CK(cudaGetLastError());
+    // non-finite inputs: report before any list is built from them
+    if ((rc = read_ctl(E, s))) return rc;
+    if (E->ctl_host->status & kStNonFinite) return fail(E, MD_ERR_NONFINITE, "non-finite position or velocity");
     if ((rc = rebuild_and_forces(E, s))) return rc;
     e.have_state = true;
     return finish_sync(E, s);

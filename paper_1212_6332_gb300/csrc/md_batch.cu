@@ -42,6 +42,8 @@ struct BoxArgs {
     int* nn;
     int* nl;
     double2* ab;
+    int* n_up;  // float64 tile path's list layout data, kept valid across schedules
+    int* rev;
     Ctl* ctl;
     int* box_done;
     int* box_state;
@@ -143,15 +145,11 @@ __device__ int box_rebuild(const Geo& g, const BoxArgs& A, int b, int64_t a0, in
         const double4_32a xi = sx[i];
         const int ci = __float_as_int(oi.w);
         const int cix = ci & 1023, ciy = (ci >> 10) & 1023, ciz = (ci >> 20) & 1023;
-        int nx = nc[0] >= 3 ? 3 : nc[0], ny = nc[1] >= 3 ? 3 : nc[1], nz = nc[2] >= 3 ? 3 : nc[2];
+        int qs[27];
+        const int n_st = stencil_sorted(g, b, cix, ciy, ciz, qs);
         int n = 0;
-        for (int ix = 0; ix < nx; ++ix)
-            for (int iy = 0; iy < ny; ++iy)
-                for (int iz = 0; iz < nz; ++iz) {
-                    int ox = nc[0] >= 3 ? ix - 1 : ix, oy = nc[1] >= 3 ? iy - 1 : iy, oz = nc[2] >= 3 ? iz - 1 : iz;
-                    int qx = (cix + ox + nc[0]) % nc[0], qy = (ciy + oy + nc[1]) % nc[1],
-                        qz = (ciz + oz + nc[2]) % nc[2];
-                    int q = g.cell_rank[c0 + (qx * nc[1] + qy) * nc[2] + qz] - c0;
+        for (int st = 0; st < n_st; ++st) {
+                    int q = qs[st] - c0;
                     int lo = s_start[q], hi = s_start[q + 1];
                     for (int jb = lo; jb < hi; jb += 32) {
                         int jj = jb + lane;
@@ -171,12 +169,23 @@ __device__ int box_rebuild(const Geo& g, const BoxArgs& A, int b, int64_t a0, in
                         }
                         n += __popc(m);
                     }
-                }
+        }
         if (lane == 0) A.nn[a0 + i] = n;
         my_max = max(my_max, n);
     }
     if (lane == 0) atomicMax(s_max, my_max);
     __syncthreads();
+    // the same [upper | lower] layout and reverse index as the tile path,
+    // so either schedule can continue from the other
+    if (*s_max <= A.max_nb) {
+        for (int t = tid; t < nb; t += NT)
+            A.n_up[a0 + t] = rotate_list(A.Np, a0 + t, min(A.nn[a0 + t], A.max_nb), A.nl);
+        __syncthreads();
+        for (int t = tid; t < nb; t += NT)
+            reverse_index(A.Np, a0 + t, min(A.nn[a0 + t], A.max_nb), A.n_up[a0 + t], A.nn, A.nl, A.n_up, A.max_nb,
+                          A.rev);
+        __syncthreads();
+    }
     return *s_max;
 }
 
@@ -270,12 +279,12 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
                 sep_entry(xi, sx[entry_slot(e) - a0], entry_code(e), L, dx, dy, dz);
                 double r2 = dx * dx + dy * dy + dz * dz;
                 double2 c = make_double2(0.0, 0.0);
-                if (r2 < P.rc2) {
-                    double phi, fr;
-                    pair_eval<KIND>(P, sT, r2, phi, fr, c.x, c.y);
-                    r_i += fr;
-                    ep += phi;
-                }
+                double phi = 0.0, fr = 0.0;
+                if (r2 < P.rc2) pair_eval<KIND>(P, sT, r2, phi, fr, c.x, c.y);
+                // the tile schedule stores these values and sums them with
+                // round-to-nearest adds in list order: do exactly that
+                r_i = __dadd_rn(r_i, fr);
+                ep = __dadd_rn(ep, phi);
                 A.ab[slot] = c;
             }
             double F, Fpi;
@@ -283,7 +292,7 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
             A.rho[i] = r_i;
             A.Fp[i] = Fpi;
             sFp[t] = Fpi;
-            A.e_atom[i] = F + 0.5 * ep;
+            A.e_atom[i] = fma(0.5, ep, F);
         }
         __syncthreads();
         // force pass and second half-kick
@@ -409,6 +418,8 @@ static void box_launch(Engine& e, int n_steps, cudaStream_t s) {
     A.nn = e.nn;
     A.nl = e.nl;
     A.ab = e.ab;
+    A.n_up = e.n_up;
+    A.rev = e.rev;
     A.ctl = e.ctl;
     A.box_done = e.box_done;
     A.box_state = e.box_state;

@@ -98,6 +98,32 @@ __device__ __forceinline__ float4 cell_local(const Geo& g, int b, int gc, double
     return make_float4(o[0], o[1], o[2], __int_as_float(xyz));
 }
 
+// The (de-duplicated) 27-cell stencil of cell (cx, cy, cz) of box b, as
+// global cell ids in ascending order: atoms are sorted by cell id, so
+// visiting the stencil in this order lists neighbours by ascending slot,
+// which lets the partner's position in a list be found by binary search.
+__device__ __forceinline__ int stencil_sorted(const Geo& g, int b, int cx, int cy, int cz, int* q) {
+    const int ncx = g.nc[3 * b], ncy = g.nc[3 * b + 1], ncz = g.nc[3 * b + 2];
+    const int nx = ncx >= 3 ? 3 : ncx, ny = ncy >= 3 ? 3 : ncy, nz = ncz >= 3 ? 3 : ncz;
+    int k = 0;
+    for (int ix = 0; ix < nx; ++ix)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int iz = 0; iz < nz; ++iz) {
+                int ox = ncx >= 3 ? ix - 1 : ix, oy = ncy >= 3 ? iy - 1 : iy, oz = ncz >= 3 ? iz - 1 : iz;
+                int qx = (cx + ox + ncx) % ncx, qy = (cy + oy + ncy) % ncy, qz = (cz + oz + ncz) % ncz;
+                q[k++] = g.cell_rank[g.cell_off[b] + (qx * ncy + qy) * ncz + qz];
+            }
+    for (int a = 1; a < k; ++a) {
+        int v = q[a], j = a - 1;
+        while (j >= 0 && q[j] > v) {
+            q[j + 1] = q[j];
+            --j;
+        }
+        q[j + 1] = v;
+    }
+    return k;
+}
+
 // Minimum image of a cell-index difference on an axis of n cells.
 __device__ __forceinline__ int cell_delta(int cj, int ci, int n) {
     int d = cj - ci;
@@ -125,9 +151,10 @@ __device__ __forceinline__ bool list_candidate(const float4& oi, const float4& o
     int rx = (cj & 1023) - cix, ry = ((cj >> 10) & 1023) - ciy, rz = ((cj >> 20) & 1023) - ciz;
     int wx = cell_delta(cj & 1023, cix, ncx), wy = cell_delta((cj >> 10) & 1023, ciy, ncy),
         wz = cell_delta((cj >> 20) & 1023, ciz, ncz);
-    sx = (wx - rx) / ncx;
-    sy = (wy - ry) / ncy;
-    sz = (wz - rz) / ncz;
+    // w - r is -n, 0 or n: its sign is the shift in box lengths
+    sx = (wx > rx) - (wx < rx);
+    sy = (wy > ry) - (wy < ry);
+    sz = (wz > rz) - (wz < rz);
     float dx = fmaf((float)wx, lfx, oj.x - oi.x);
     float dy = fmaf((float)wy, lfy, oj.y - oi.y);
     float dz = fmaf((float)wz, lfz, oj.z - oi.z);
@@ -156,17 +183,55 @@ __device__ __forceinline__ bool list_candidate(const float4& oi, const float4& o
     return r2 < rl2;
 }
 
+// Each list leaves the build ascending by neighbour slot. It is rotated to
+// [upper entries (j > i) | lower entries (j < i)], both parts ascending, so
+// the pair pass reads row k of all lists together (coalesced) while it
+// walks only the upper entries, and the partner of an upper entry is found
+// by binary search in the partner's lower part. n_up[i] counts the upper
+// entries; lists longer than kRotMax keep the ascending order and
+// n_up = -1 (the pair pass then scans them whole).
+constexpr int kRotMax = 320;
+
+__device__ __forceinline__ int rotate_list(int64_t Np, int64_t i, int n, int* __restrict__ nl) {
+    if (n > kRotMax) return -1;
+    int lo = 0;
+    while (lo < n && entry_slot(nl[(int64_t)lo * Np + i]) < i) ++lo;
+    if (lo == 0 || lo == n) return n - lo;
+    int buf[kRotMax];
+    for (int k = 0; k < n; ++k) buf[k] = nl[(int64_t)k * Np + i];
+    for (int k = 0; k < n; ++k) nl[(int64_t)k * Np + i] = buf[(k + lo) % n];
+    return n - lo;
+}
+
+__device__ __forceinline__ void reverse_index(int64_t Np, int64_t i, int n, int nup, const int* __restrict__ nn,
+                                              const int* __restrict__ nl, const int* __restrict__ n_up, int max_nb,
+                                              int* __restrict__ rev) {
+    const int kmax = nup < 0 ? n : nup;
+    for (int k = 0; k < kmax; ++k) {
+        const int j = entry_slot(nl[(int64_t)k * Np + i]);
+        if (j <= i) continue;
+        const int nj = min(nn[j], max_nb);
+        const int uj = n_up[j];
+        int lo = uj < 0 ? 0 : uj, hi = uj < 0 ? nj : nj;  // j's lower part (or its whole ascending list)
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (entry_slot(nl[(int64_t)mid * Np + j]) < i)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        rev[(int64_t)k * Np + i] = lo;
+    }
+}
+
 // ---------------------------------------------------------------- float64
 
 // C2 smoothstep taper S(r) = 1 - 10x^3 + 15x^4 - 6x^5 on [rs, rc), x = (r - rs)/(rc - rs),
-// and dS/dr. The caller guarantees r < rc.
+// and dS/dr. The caller guarantees r < rc. Branch-free (x clamped at 0 gives
+// S = 1, dS = 0 exactly): the perturbed third fcc shell straddles r_taper, so
+// a branch would split most warps.
 __device__ __forceinline__ void taper(const Pot& P, double r, double& S, double& dS) {
-    if (r <= P.rs) {
-        S = 1.0;
-        dS = 0.0;
-        return;
-    }
-    double x = (r - P.rs) * P.inv_w;
+    double x = fmax((r - P.rs) * P.inv_w, 0.0);
     double x2 = x * x;
     S = 1.0 + x2 * x * (-10.0 + x * (15.0 - 6.0 * x));
     dS = x2 * (-30.0 + x * (60.0 - 30.0 * x)) * P.inv_w;

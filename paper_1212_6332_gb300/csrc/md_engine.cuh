@@ -91,6 +91,7 @@ struct Engine {
     int64_t N = 0, N_pad = 0;
     int n_cells = 0;
     int max_nb = 0;
+    bool wide = false;  // every box has at least 3 cells per axis
     double rl = 0.0;  // list radius r_cut + skin
     std::vector<int64_t> atom_off_h;
     std::vector<double> L_h;
@@ -142,6 +143,9 @@ struct Engine {
     int* nn = nullptr;          // [N_pad]
     int* nl = nullptr;          // [max_nb][N_pad] column-major
     double2* ab = nullptr;      // float64 path: [max_nb][N_pad] (V'/r, rho'/r) per list entry
+    double2* fv = nullptr;      // float64 path: [max_nb][N_pad] (rho(r), V(r)) per list entry
+    int* rev = nullptr;         // float64 path: [max_nb][N_pad] partner position of upper entries
+    int* n_up = nullptr;        // float64 path: [N_pad] upper entries of each list (lists are [upper | lower])
     double* exp_T = nullptr;    // exponential table
     // parameter adjoint work arrays (allocated on the first gradient call)
     double* grad_g = nullptr;        // [3][N_pad] dL/dF in sorted order

@@ -9,61 +9,146 @@
 // mostly from L1/L2.
 //
 // GB300 executes float64 at 1/64 of the float32 rate while its HBM sits
-// idle in this kernel pair, so the work is split to evaluate every pair
-// function once per step and to move bytes instead of float64 instructions:
-//   density: for each list entry inside r_cut, V, rho, A = V'/r and
-//            B = rho'/r from one rsqrt and two table-driven exponentials;
-//            rho_i = sum rho, 1/2 sum V; F(rho_i), F'(rho_i); the pair
-//            (A, B) is stored per list slot (zero outside r_cut);
+// idle in this kernel pair, so the work is split to evaluate every pair's
+// functions once per step and to move bytes instead of float64 instructions:
+//   pairs:   the lower slot of each pair (j > i in i's list) evaluates V,
+//            rho, A = V'/r and B = rho'/r (one rsqrt, two table-driven
+//            exponentials) and writes them into both lists' slots (the
+//            partner's position comes from the reverse index built with the
+//            list); all four are functions of r alone, so both slots get
+//            the same bits the partner would have computed;
+//   density: rho_i = sum rho, 1/2 sum V over i's slots in list order;
+//            F(rho_i), F'(rho_i);
 //   force:   F_i = sum_j [A + (F'_i + F'_j) B] (x_j - x_i)   [Eq. (3)]
 //            i.e. 5 float64 operations per pair after the separation,
 //            optionally followed by v_i += dt/2 F_i/m (second half-kick).
+// The sums run over each list in list order, as a full evaluation per atom
+// does (the block-per-box schedule evaluates every entry from its own
+// side), so both give identical results.
 #include "md_device.cuh"
 
 namespace mdk {
 
 constexpr int kFNT = 128;
 
+// Pair pass. Lanes walk their own lists (coalesced rows, cheap separation
+// and r^2), and the in-cutoff pairs are compacted through a per-warp queue
+// in shared memory: every batch of 32 queued pairs is evaluated with all 32
+// lanes active. On GB300 a masked lane still costs the float64 pipe its
+// cycles, and without compaction half the lanes of a warp would idle (list
+// lengths, the cutoff test).
+constexpr int kQueue = 64;
+
+template <int KIND>
+__device__ __forceinline__ void eval_pair_item(const Pot& P, const double* __restrict__ sT, double r2, int64_t own,
+                                               int64_t mir, double2* __restrict__ ab, double2* __restrict__ fv) {
+    double2 c, w;
+    pair_eval<KIND>(P, sT, r2, w.y, w.x, c.x, c.y);
+    ab[own] = c;
+    fv[own] = w;
+    ab[mir] = c;
+    fv[mir] = w;
+}
+
 template <int KIND, bool SINGLE>
-__global__ void __launch_bounds__(kFNT) k_density(int64_t N, int64_t Np, Geo g, Pot P,
-                                                  const double4_32a* __restrict__ x, const int* __restrict__ nn,
-                                                  const int* __restrict__ nl, int max_nb,
-                                                  double2* __restrict__ ab, double* __restrict__ rho,
+__global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo g, Pot P,
+                                                     const double4_32a* __restrict__ x, const int* __restrict__ nn,
+                                                     const int* __restrict__ nl, const int* __restrict__ rev,
+                                                     const int* __restrict__ n_up, int max_nb,
+                                                     double2* __restrict__ ab, double2* __restrict__ fv,
+                                                     const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    __shared__ double sT[kExpTable];
+    __shared__ double q_r2[kFNT / 32][kQueue];
+    __shared__ long long q_own[kFNT / 32][kQueue];
+    __shared__ long long q_mir[kFNT / 32][kQueue];
+    if (KIND == MD_POT_RGL) load_exp_table(sT, P.exp_T);
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < N;
+    double L[3] = {0.0, 0.0, 0.0};
+    double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    int kend = 0;
+    if (active) {
+        int b = SINGLE ? 0 : g.atom_box[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+        xi = x[i];
+        const int n = min(nn[i], max_nb);
+        // lists are [upper | lower]: the upper entries (j > i) are rows
+        // 0..n_up-1; the lower ones are written by the partners' threads (a
+        // list kept unrotated, n_up < 0, is scanned whole)
+        const int nup = n_up[i];
+        kend = nup < 0 ? n : nup;
+    }
+    const int kmax = warp_max(kend);
+    int qn = 0;
+    for (int k = 0; k < kmax; ++k) {
+        bool in = false;
+        double r2 = 0.0;
+        int64_t own = 0, mir = 0;
+        if (k < kend) {
+            own = (int64_t)k * Np + i;
+            const int e = nl[own];
+            const int j = entry_slot(e);
+            if (j > i) {
+                double dx, dy, dz;
+                sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
+                r2 = dx * dx + dy * dy + dz * dz;
+                mir = (int64_t)rev[own] * Np + j;
+                if (r2 < P.rc2) {
+                    in = true;
+                } else {
+                    const double2 z = make_double2(0.0, 0.0);
+                    ab[own] = z;
+                    fv[own] = z;
+                    ab[mir] = z;
+                    fv[mir] = z;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int p = qn + __popc(m & lt_mask);
+            q_r2[wq][p] = r2;
+            q_own[wq][p] = own;
+            q_mir[wq][p] = mir;
+        }
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            qn -= 32;
+            const int p = qn + lane;
+            eval_pair_item<KIND>(P, sT, q_r2[wq][p], q_own[wq][p], q_mir[wq][p], ab, fv);
+            __syncwarp();
+        }
+    }
+    if (lane < qn) eval_pair_item<KIND>(P, sT, q_r2[wq][lane], q_own[wq][lane], q_mir[wq][lane], ab, fv);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kFNT) k_rho_sum(int64_t N, int64_t Np, Pot P, const int* __restrict__ nn,
+                                                  int max_nb, const double2* __restrict__ fv, double* __restrict__ rho,
                                                   double* __restrict__ Fp, double* __restrict__ e_atom,
                                                   const Ctl* ctl) {
     if (load_status(ctl)) return;
-    __shared__ double sT[kExpTable];
-    if (KIND == MD_POT_RGL) load_exp_table(sT, P.exp_T);
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double L[3];
-    int b = SINGLE ? 0 : g.atom_box[i];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
-    const double4_32a xi = x[i];
     const int n = min(nn[i], max_nb);
+    // explicit round-to-nearest adds: the block-per-box schedule sums the
+    // same values in the same order and must not fuse them differently
     double r_i = 0.0, ep = 0.0;
     for (int k = 0; k < n; ++k) {
-        const int64_t slot = (int64_t)k * Np + i;
-        const int e = nl[slot];
-        const double4_32a xj = x[entry_slot(e)];
-        double dx, dy, dz;
-        sep_entry(xi, xj, entry_code(e), L, dx, dy, dz);
-        double r2 = dx * dx + dy * dy + dz * dz;
-        double2 c = make_double2(0.0, 0.0);
-        if (r2 < P.rc2) {
-            double phi, fr;
-            pair_eval<KIND>(P, sT, r2, phi, fr, c.x, c.y);
-            r_i += fr;
-            ep += phi;
-        }
-        ab[slot] = c;
+        double2 w = fv[(int64_t)k * Np + i];
+        r_i = __dadd_rn(r_i, w.x);
+        ep = __dadd_rn(ep, w.y);
     }
     double F, Fpi;
     embed<KIND>(P, r_i, F, Fpi);
     rho[i] = r_i;
     Fp[i] = Fpi;
-    e_atom[i] = F + 0.5 * ep;
+    e_atom[i] = fma(0.5, ep, F);
 }
 
 template <bool SINGLE>
@@ -115,11 +200,15 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s) {
     Geo g = make_geo(e);
     int nb = (int)((e.N + kFNT - 1) / kFNT);
     double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
-    e.launches += 2;
+    e.launches += 3;
+    {
+        PhaseScope scope(e, MD_PHASE_PAIRS, s);
+        k_pairs_half<KIND, SINGLE><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.rev, e.n_up,
+                                                      e.max_nb, e.ab, e.fv, e.ctl);
+    }
     {
         PhaseScope scope(e, MD_PHASE_DENSITY, s);
-        k_density<KIND, SINGLE><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.ab, e.rho,
-                                                   e.Fp, e.e_atom, e.ctl);
+        k_rho_sum<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.nn, e.max_nb, e.fv, e.rho, e.Fp, e.e_atom, e.ctl);
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     k_force<SINGLE><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.ab, e.Fp, e.f,

@@ -238,9 +238,11 @@ void launch_reset_ctl(Engine& e, cudaStream_t s) {
 // ---------------------------------------------------------------- copies
 
 __global__ void k_load_pos(int64_t N, const double* __restrict__ src, const int* __restrict__ iperm, Geo g,
-                           double4_32a* __restrict__ x) {
+                           double4_32a* __restrict__ x, Ctl* ctl) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
+    if (!isfinite(src[3 * c]) || !isfinite(src[3 * c + 1]) || !isfinite(src[3 * c + 2]))
+        atomicOr(&ctl->status, kStNonFinite);
     int b = g.B == 1 ? 0 : g.atom_box[c];
     int t = iperm[c];
     double4_32a p;
@@ -252,9 +254,11 @@ __global__ void k_load_pos(int64_t N, const double* __restrict__ src, const int*
 }
 
 __global__ void k_load_vel(int64_t N, int64_t Np, const double* __restrict__ src, const int* __restrict__ iperm,
-                           double* __restrict__ v) {
+                           double* __restrict__ v, Ctl* ctl) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
+    if (src && (!isfinite(src[3 * c]) || !isfinite(src[3 * c + 1]) || !isfinite(src[3 * c + 2])))
+        atomicOr(&ctl->status, kStNonFinite);
     int t = iperm[c];
     v[t] = src ? src[3 * c] : 0.0;
     v[Np + t] = src ? src[3 * c + 1] : 0.0;
@@ -316,13 +320,13 @@ static int nblk(int64_t n, int nt) { return (int)((n + nt - 1) / nt); }
 void launch_load_positions(Engine& e, const double* src, cudaStream_t s) {
     if (e.N == 0) return;
     e.launches += 1;
-    k_load_pos<<<nblk(e.N, 256), 256, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x);
+    k_load_pos<<<nblk(e.N, 256), 256, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x, e.ctl);
 }
 
 void launch_load_velocities(Engine& e, const double* src, cudaStream_t s) {
     if (e.N == 0) return;
     e.launches += 1;
-    k_load_vel<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, src, e.iperm, e.v);
+    k_load_vel<<<nblk(e.N, 256), 256, 0, s>>>(e.N, e.N_pad, src, e.iperm, e.v, e.ctl);
 }
 
 void launch_store_vec(Engine& e, const double* soa, const double4_32a* x4, double* dst, cudaStream_t s) {

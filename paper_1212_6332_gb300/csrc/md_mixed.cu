@@ -9,7 +9,8 @@
 // and both offsets below one cell side plus the skin: the float32 rounding
 // error of d is ~1e-7 of a cell side, not of the box length. V, rho and
 // their derivatives are evaluated in float32 (hardware exp2 / rsqrt); the
-// per-atom sums rho_i, F_i and the pair energy use compensated float32
+// per-atom sums rho_i, F_i and the pair energy add each group of 16 list
+// entries in plain float32 and combine the groups with compensated float32
 // accumulation (Neumaier), and F(rho_i), F'(rho_i) are taken in float64.
 // The paper's own precedent is float32 positions inside its neighbour-list
 // kernel (Sec. 4).
@@ -31,15 +32,40 @@ __device__ __forceinline__ int wrap_cells(int d, int n) {
     return d;
 }
 
+// WIDE: every box has at least 3 cells per axis, so the nearest cell image
+// is the nearest atom image and no box-length correction can be needed.
+template <bool WIDE>
 __device__ __forceinline__ void sep_mixed(const CellSep& cs, float4 oi, float4 oj, float& dx, float& dy, float& dz) {
     int ci = __float_as_int(oi.w), cj = __float_as_int(oj.w);
     int ddx = wrap_cells((cj & 1023) - (ci & 1023), cs.nx);
     int ddy = wrap_cells(((cj >> 10) & 1023) - ((ci >> 10) & 1023), cs.ny);
     int ddz = wrap_cells(((cj >> 20) & 1023) - ((ci >> 20) & 1023), cs.nz);
-    dx = minimgf(fmaf((float)ddx, cs.lx, oj.x - oi.x), cs.Lx, 0.5f * cs.Lx);
-    dy = minimgf(fmaf((float)ddy, cs.ly, oj.y - oi.y), cs.Ly, 0.5f * cs.Ly);
-    dz = minimgf(fmaf((float)ddz, cs.lz, oj.z - oi.z), cs.Lz, 0.5f * cs.Lz);
+    dx = fmaf((float)ddx, cs.lx, oj.x - oi.x);
+    dy = fmaf((float)ddy, cs.ly, oj.y - oi.y);
+    dz = fmaf((float)ddz, cs.lz, oj.z - oi.z);
+    if (!WIDE) {
+        dx = minimgf(dx, cs.Lx, 0.5f * cs.Lx);
+        dy = minimgf(dy, cs.Ly, 0.5f * cs.Ly);
+        dz = minimgf(dz, cs.Lz, 0.5f * cs.Lz);
+    }
 }
+
+// Plain float32 partial sum over a group of list entries, folded into a
+// compensated total at group ends.
+struct GSum {
+    float part = 0.0f;
+    KSum tot;
+    __device__ __forceinline__ void add(float x) { part += x; }
+    __device__ __forceinline__ void flush() {
+        tot.add(part);
+        part = 0.0f;
+    }
+    __device__ __forceinline__ double value() {
+        flush();
+        return tot.value();
+    }
+};
+constexpr int kGroupMask = 15;
 
 template <bool SINGLE>
 __device__ __forceinline__ CellSep cell_sep(const Geo& g, const CellSep& cs0, int64_t i) {
@@ -58,7 +84,7 @@ __device__ __forceinline__ CellSep cell_sep(const Geo& g, const CellSep& cs0, in
     return cs;
 }
 
-template <int KIND, bool SINGLE>
+template <int KIND, bool SINGLE, bool WIDE>
 __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P,
                                                         const float4* __restrict__ xo, const int* __restrict__ nn,
                                                         const int* __restrict__ nl, int max_nb,
@@ -71,13 +97,14 @@ __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, G
     const CellSep cs = cell_sep<SINGLE>(g, cs0, i);
     const float4 oi = xo[i];
     const int n = min(nn[i], max_nb);
-    KSum acc;
+    GSum acc;
     for (int k = 0; k < n; ++k) {
         int j = entry_slot(nl[(int64_t)k * Np + i]);
         float dx, dy, dz;
-        sep_mixed(cs, oi, xo[j], dx, dy, dz);
+        sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2)));
+        if ((k & kGroupMask) == kGroupMask) acc.flush();
     }
     double r_i = acc.value();
     double F, Fpi;
@@ -88,7 +115,7 @@ __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, G
     e_atom[i] = F;
 }
 
-template <int KIND, bool SINGLE>
+template <int KIND, bool SINGLE, bool WIDE>
 __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P,
                                                       const float4* __restrict__ xo, const int* __restrict__ nn,
                                                       const int* __restrict__ nl, int max_nb,
@@ -102,11 +129,17 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
     const float4 oi = xo[i];
     const float Fpi = Fpf[i];
     const int n = min(nn[i], max_nb);
-    KSum ax, ay, az, ae;
+    GSum ax, ay, az, ae;
     for (int k = 0; k < n; ++k) {
+        if ((k & kGroupMask) == 0 && k) {
+            ax.flush();
+            ay.flush();
+            az.flush();
+            ae.flush();
+        }
         int j = entry_slot(nl[(int64_t)k * Np + i]);
         float dx, dy, dz;
-        sep_mixed(cs, oi, xo[j], dx, dy, dz);
+        sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < P.f_rc2) {
             float rinv = rsqrtf(r2);
@@ -132,7 +165,7 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
     }
 }
 
-template <int KIND, bool SINGLE>
+template <int KIND, bool SINGLE, bool WIDE>
 static void run_mixed(Engine& e, int kick, cudaStream_t s) {
     Geo g = make_geo(e);
     CellSep cs{};
@@ -152,20 +185,20 @@ static void run_mixed(Engine& e, int kick, cudaStream_t s) {
     e.launches += 2;
     {
         PhaseScope scope(e, MD_PHASE_DENSITY, s);
-        k_density_mixed<KIND, SINGLE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb,
+        k_density_mixed<KIND, SINGLE, WIDE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb,
                                                          e.rho, e.Fp, e.Fpf, e.e_atom, e.ctl);
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
-    k_force_mixed<KIND, SINGLE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.Fpf,
+    k_force_mixed<KIND, SINGLE, WIDE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.Fpf,
                                                    e.f, e.e_atom, kick ? e.v : nullptr, c_kick, e.ctl);
 }
 
 template <int KIND>
 static void run_mixed_k(Engine& e, int kick, cudaStream_t s) {
     if (e.B == 1)
-        run_mixed<KIND, true>(e, kick, s);
+        e.wide ? run_mixed<KIND, true, true>(e, kick, s) : run_mixed<KIND, true, false>(e, kick, s);
     else
-        run_mixed<KIND, false>(e, kick, s);
+        e.wide ? run_mixed<KIND, false, true>(e, kick, s) : run_mixed<KIND, false, false>(e, kick, s);
 }
 
 void launch_forces_mixed(Engine& e, int kick, cudaStream_t s) {

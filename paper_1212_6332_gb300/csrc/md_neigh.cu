@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
     __shared__ float4 so[kNlCap];
     __shared__ int sj[kNlCap];
     __shared__ int cnt[kNlMaxI];
-    __shared__ int st_lo[27], st_pre[28];
+    __shared__ int st_lo[27], st_cnt[27], st_pre[28];
     __shared__ int n_st;
 
     const int c = blockIdx.x;
@@ -60,25 +60,41 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
     const float lfx = g.cell_len_f[3 * b], lfy = g.cell_len_f[3 * b + 1], lfz = g.cell_len_f[3 * b + 2];
     const float Lfx = (float)Lx, Lfy = (float)Ly, Lfz = (float)Lz;
 
-    if (threadIdx.x == 0) {
-        // distinct neighbour-cell offsets per axis: {-1,0,1} if >= 3 cells,
-        // {0,1} if 2, {0} if 1
-        int nx = ncx >= 3 ? 3 : ncx, ny = ncy >= 3 ? 3 : ncy, nz = ncz >= 3 ? 3 : ncz;
-        int k = 0, pre = 0;
-        for (int ix = 0; ix < nx; ++ix)
-            for (int iy = 0; iy < ny; ++iy)
-                for (int iz = 0; iz < nz; ++iz) {
-                    int ox = ncx >= 3 ? ix - 1 : ix, oy = ncy >= 3 ? iy - 1 : iy, oz = ncz >= 3 ? iz - 1 : iz;
-                    int qx = (cc[0] + ox + ncx) % ncx, qy = (cc[1] + oy + ncy) % ncy, qz = (cc[2] + oz + ncz) % ncz;
-                    int q = g.cell_rank[g.cell_off[b] + (qx * ncy + qy) * ncz + qz];
-                    int lo = base + cell_start[q], hi = base + cell_start[q + 1];
-                    st_lo[k] = lo;
-                    st_pre[k] = pre;
-                    pre += hi - lo;
-                    ++k;
-                }
-        st_pre[k] = pre;
-        n_st = k;
+    if (threadIdx.x < 32) {
+        // one lane per stencil cell (loads in parallel), then the cells in
+        // ascending id order (the rank of each id among the lanes), so every
+        // list comes out sorted by neighbour slot, as stencil_sorted orders
+        // them for the block-per-box schedule
+        const int lane = threadIdx.x;
+        const int nx = ncx >= 3 ? 3 : ncx, ny = ncy >= 3 ? 3 : ncy, nz = ncz >= 3 ? 3 : ncz;
+        const int total = nx * ny * nz;
+        int q = 0x7fffffff, lo = 0, cnt = 0;
+        if (lane < total) {
+            int ix = lane / (ny * nz), iy = (lane / nz) % ny, iz = lane % nz;
+            int ox = ncx >= 3 ? ix - 1 : ix, oy = ncy >= 3 ? iy - 1 : iy, oz = ncz >= 3 ? iz - 1 : iz;
+            int qx = (cc[0] + ox + ncx) % ncx, qy = (cc[1] + oy + ncy) % ncy, qz = (cc[2] + oz + ncz) % ncz;
+            q = g.cell_rank[g.cell_off[b] + (qx * ncy + qy) * ncz + qz];
+            lo = base + cell_start[q];
+            cnt = base + cell_start[q + 1] - lo;
+        }
+        int rank = 0;
+        for (int k = 0; k < total; ++k) rank += __shfl_sync(0xffffffffu, q, k) < q;
+        if (lane < total) {
+            st_lo[rank] = lo;
+            st_cnt[rank] = cnt;
+        }
+        __syncwarp();
+        int c = lane < total ? st_cnt[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) c += t;
+        }
+        if (lane < total) st_pre[lane + 1] = c;
+        if (lane == 0) {
+            st_pre[0] = 0;
+            n_st = total;
+        }
     }
     __syncthreads();
     const int n_cand = st_pre[n_st];
@@ -95,8 +111,15 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
             __syncthreads();
             for (int t = threadIdx.x; t < nc_; t += kNlThreads) {
                 int q = cb + t;
-                int k = 0;
-                while (st_pre[k + 1] <= q) ++k;
+                // the stencil cell holding candidate q: last k with st_pre[k] <= q
+                int k = 0, hk = n_st;
+                while (hk - k > 1) {
+                    int mid = (k + hk) >> 1;
+                    if (st_pre[mid] <= q)
+                        k = mid;
+                    else
+                        hk = mid;
+                }
                 int j = st_lo[k] + (q - st_pre[k]);
                 so[t] = xo[j];
                 sj[t] = j;
@@ -147,6 +170,24 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
     }
 }
 
+__global__ void k_rotate_lists(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn, int* __restrict__ nl,
+                               int max_nb, int* __restrict__ n_up, const Ctl* ctl,
+                               const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (!box_wants_nl(ctl, disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr)) return;
+    n_up[i] = rotate_list(Np, i, min(nn[i], max_nb), nl);
+}
+
+__global__ void k_build_rev(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn, const int* __restrict__ nl,
+                            int max_nb, const int* __restrict__ n_up, int* __restrict__ rev, const Ctl* ctl,
+                            const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (!box_wants_nl(ctl, disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr)) return;
+    reverse_index(Np, i, min(nn[i], max_nb), n_up[i], nn, nl, n_up, max_nb, rev);
+}
+
 // A full rebuild restarts the largest-count record; partial rebuilds only
 // raise it, so it stays an upper bound of every current list.
 __global__ void k_reset_max_count(Ctl* ctl, int mode) {
@@ -167,6 +208,13 @@ void launch_build_list(Engine& e, int mode, cudaStream_t s) {
     k_reset_max_count<<<1, 1, 0, s>>>(e.ctl, mode);
     k_build_list<<<e.n_cells, kNlThreads, 0, s>>>(g, e.x, e.xo, e.cell_start, e.nn, e.nl, e.max_nb, e.N_pad, rl2, lo,
                                                  hi, e.ctl, e.disp_box, mode, thr);
+    if (e.rev) {
+        int nb = (int)((e.N + 255) / 256);
+        k_rotate_lists<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.nl, e.max_nb, e.n_up, e.ctl, e.disp_box, mode, thr);
+        k_build_rev<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.nl, e.max_nb, e.n_up, e.rev, e.ctl, e.disp_box, mode,
+                                       thr);
+        e.launches += 2;
+    }
 }
 
 }  // namespace mdk

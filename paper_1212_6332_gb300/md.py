@@ -30,7 +30,7 @@ SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_
            "md_eval_math", "md_forces_noalloc", "md_batch_thermo",
            "md_batch_schedule")
 NOALLOC_MAX_ATOMS = 16384
-PHASES = ("kick_drift", "rebuild", "density", "force", "other")
+PHASES = ("kick_drift", "rebuild", "pairs", "density", "force", "other")
 
 
 class MDError(RuntimeError):
@@ -61,7 +61,7 @@ class Thermo(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double * 5), ("timed", ctypes.c_int64 * 5)]
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double * 6), ("timed", ctypes.c_int64 * 6)]
 
 
 _lib = None
@@ -333,8 +333,8 @@ class System:
     def profile_read(self) -> dict:
         p = Profile()
         self._check(self.lib.md_profile_read(self._h, ctypes.byref(p)))
-        return dict(launches=p.launches, ms={PHASES[k]: p.ms[k] for k in range(5)},
-                    timed={PHASES[k]: p.timed[k] for k in range(5)})
+        return dict(launches=p.launches, ms={PHASES[k]: p.ms[k] for k in range(6)},
+                    timed={PHASES[k]: p.timed[k] for k in range(6)})
 
     def eval_math(self, fn: str, x):
         """The library's float64 functions on a CUDA tensor: fn in

@@ -193,3 +193,23 @@ def test_host_and_device_buffers_agree():
     s.compute_forces(bx.x.copy(), f=f_host, energy=e_host)
     assert np.array_equal(f_host, dev["f"].cpu().numpy())
     assert e_host[0] == dev["energy"].item()
+
+
+def test_non_finite_inputs_are_reported():
+    """Failure injected on the host: a NaN position or an infinite velocity
+    makes set_state return MD_ERR_NONFINITE; the handle stays usable."""
+    from paper_1212_6332_gb300.md import MDError
+    bx = I.perturbed_fcc(4, I.A_CU, 300.0, I.MASS_CU, seed=6)
+    s = make_system(I.RGL_CU, bx.box, bx.n)
+    x = bx.x.copy()
+    x[17, 1] = np.nan
+    with pytest.raises(MDError) as err:
+        s.set_state(x, bx.v.copy())
+    assert err.value.code == 5
+    v = bx.v.copy()
+    v[3, 0] = np.inf
+    with pytest.raises(MDError) as err:
+        s.set_state(bx.x.copy(), v)
+    assert err.value.code == 5
+    s.set_state(bx.x.copy(), bx.v.copy())
+    assert s.step(5)["step"] == 5
