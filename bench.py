@@ -480,8 +480,9 @@ def main():
         batch = {"fp64": run_batch("fp64", kb, W), "fp64_box": run_batch("fp64", kb, W, schedule="box"),
                  "mixed": run_batch("mixed", kb, W),
                  "one_launch_per_box": run_per_box_sample(kb)}
-        grad = {"rgl_fp64": run_grad(max(3, min(K, 10)), 2, "fp64", "rgl"),
-                "spline_fp64": run_grad(max(3, min(K, 10)), 2, "fp64", "spline")}
+        kg = max(3, min(K, 10))
+        grad = {"rgl_fp64": run_grad(kg, 2, "fp64", "rgl"), "rgl_mixed": run_grad(kg, 2, "mixed", "rgl"),
+                "spline_fp64": run_grad(kg, 2, "fp64", "spline")}
     if rank == 0 and not args.no_extras:
         import oracle as O
         O.build()

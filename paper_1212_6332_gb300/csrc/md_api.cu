@@ -150,6 +150,7 @@ void fill_pot(Engine& e) {
         }
     }
     P.rc2 = P.rc * P.rc;
+    P.rs2 = P.rs * P.rs;
     P.F_scale = 1.0;
     if (p.kind == MD_POT_RGL) {
         double A = p.p[0], xi = p.p[1], pp = p.p[2], q = p.p[3], r0 = p.p[4];
@@ -161,6 +162,9 @@ void fill_pot(Engine& e) {
         P.q2_r0 = 2.0 * q / r0;
         P.xi = xi;
         P.r0 = r0;
+        P.fold = P.A2 > 0.0 && P.xi2 > 0.0;
+        P.pA = P.fold ? pp + std::log(P.A2) : 0.0;
+        P.qX = P.fold ? P.q2 + std::log(P.xi2) : 0.0;
     } else if (p.kind == MD_POT_SC) {
         P.eps = p.p[0];
         P.a = p.p[2];

@@ -284,24 +284,41 @@ __device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict
                                           double& fr, double& A, double& B) {
     double rinv = rsqrt_nr(r2);
     double r = r2 * rinv;
+    // pairs inside r_taper (r^2 <= r_taper^2) skip the taper (S = 1, S' = 0)
+    const bool tap = r2 > P.rs2;
     if (KIND == MD_POT_RGL) {
-        double S, dS;
-        taper(P, r, S, dS);
-        double e1 = P.A2 * exp_tab(P.p - P.p_r0 * r, T, P.ek);
-        double e2 = P.xi2 * exp_tab(P.q2 - P.q2_r0 * r, T, P.ek);
-        phi = e1 * S;
-        fr = e2 * S;
-        A = e1 * (dS - P.p_r0 * S) * rinv;
-        B = e2 * (dS - P.q2_r0 * S) * rinv;
+        // the prefactors 2A and xi^2 ride in the exponent when both are positive
+        double e1 = P.fold ? exp_tab(P.pA - P.p_r0 * r, T, P.ek) : P.A2 * exp_tab(P.p - P.p_r0 * r, T, P.ek);
+        double e2 = P.fold ? exp_tab(P.qX - P.q2_r0 * r, T, P.ek) : P.xi2 * exp_tab(P.q2 - P.q2_r0 * r, T, P.ek);
+        if (tap) {
+            double S, dS;
+            taper(P, r, S, dS);
+            phi = e1 * S;
+            fr = e2 * S;
+            A = e1 * (dS - P.p_r0 * S) * rinv;
+            B = e2 * (dS - P.q2_r0 * S) * rinv;
+        } else {
+            phi = e1;
+            fr = e2;
+            A = e1 * (-P.p_r0) * rinv;
+            B = e2 * (-P.q2_r0) * rinv;
+        }
     } else if (KIND == MD_POT_SC) {
-        double S, dS;
-        taper(P, r, S, dS);
         double ar = P.a * rinv;
         double an = P.eps * powr(ar, P.n), am = powr(ar, P.m);
-        phi = an * S;
-        fr = am * S;
-        A = an * (dS - P.n * rinv * S) * rinv;
-        B = am * (dS - P.m * rinv * S) * rinv;
+        if (tap) {
+            double S, dS;
+            taper(P, r, S, dS);
+            phi = an * S;
+            fr = am * S;
+            A = an * (dS - P.n * rinv * S) * rinv;
+            B = am * (dS - P.m * rinv * S) * rinv;
+        } else {
+            phi = an;
+            fr = am;
+            A = an * (-(P.n * rinv)) * rinv;
+            B = am * (-(P.m * rinv)) * rinv;
+        }
     } else {
         if (r >= P.rc) {
             phi = fr = A = B = 0.0;
@@ -459,6 +476,72 @@ struct KSum {
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
+
+// ---------------------------------------------------------------- mixed-precision separation
+
+struct CellSep {
+    float lx, ly, lz;     // cell sides
+    int nx, ny, nz;       // cells per axis
+    float Lx, Ly, Lz;     // box lengths
+};
+
+__device__ __forceinline__ int wrap_cells(int d, int n) {
+    if (2 * d > n) return d - n;
+    if (2 * d < -n) return d + n;
+    return d;
+}
+
+// WIDE: every box has at least 3 cells per axis, so the nearest cell image
+// is the nearest atom image and no box-length correction can be needed.
+template <bool WIDE>
+__device__ __forceinline__ void sep_mixed(const CellSep& cs, float4 oi, float4 oj, float& dx, float& dy, float& dz) {
+    int ci = __float_as_int(oi.w), cj = __float_as_int(oj.w);
+    int ddx = wrap_cells((cj & 1023) - (ci & 1023), cs.nx);
+    int ddy = wrap_cells(((cj >> 10) & 1023) - ((ci >> 10) & 1023), cs.ny);
+    int ddz = wrap_cells(((cj >> 20) & 1023) - ((ci >> 20) & 1023), cs.nz);
+    dx = fmaf((float)ddx, cs.lx, oj.x - oi.x);
+    dy = fmaf((float)ddy, cs.ly, oj.y - oi.y);
+    dz = fmaf((float)ddz, cs.lz, oj.z - oi.z);
+    if (!WIDE) {
+        dx = minimgf(dx, cs.Lx, 0.5f * cs.Lx);
+        dy = minimgf(dy, cs.Ly, 0.5f * cs.Ly);
+        dz = minimgf(dz, cs.Lz, 0.5f * cs.Lz);
+    }
+}
+
+// Plain float32 partial sum over a group of list entries, folded into a
+// compensated total at group ends.
+struct GSum {
+    float part = 0.0f;
+    KSum tot;
+    __device__ __forceinline__ void add(float x) { part += x; }
+    __device__ __forceinline__ void flush() {
+        tot.add(part);
+        part = 0.0f;
+    }
+    __device__ __forceinline__ double value() {
+        flush();
+        return tot.value();
+    }
+};
+constexpr int kGroupMask = 15;
+
+template <bool SINGLE>
+__device__ __forceinline__ CellSep cell_sep(const Geo& g, const CellSep& cs0, int64_t i) {
+    if (SINGLE) return cs0;
+    int b = g.atom_box[i];
+    CellSep cs;
+    cs.lx = g.cell_len_f[3 * b];
+    cs.ly = g.cell_len_f[3 * b + 1];
+    cs.lz = g.cell_len_f[3 * b + 2];
+    cs.nx = g.nc[3 * b];
+    cs.ny = g.nc[3 * b + 1];
+    cs.nz = g.nc[3 * b + 2];
+    cs.Lx = (float)g.L[3 * b];
+    cs.Ly = (float)g.L[3 * b + 1];
+    cs.Lz = (float)g.L[3 * b + 2];
+    return cs;
+}
 
 // ---------------------------------------------------------------- reductions
 

@@ -30,8 +30,11 @@ constexpr int kStTimeout = 4;
 struct Pot {
     int kind;
     double rc, rc2, rs, inv_w;  // cutoff, taper start, 1/(rc - rs); rs >= rc: hard cut
+    double rs2;                 // rs^2: pairs with r^2 <= rs2 have S = 1
     // RGL: V = A2 exp(p - p_r0 r) S, rho = xi2 exp(q2 - q2_r0 r) S
     double A2, xi2, p, p_r0, q2, q2_r0;
+    int fold;        // 2A > 0 and xi^2 > 0: exponent constants with the prefactors folded in
+    double pA, qX;   // p + ln(2A), 2q + ln(xi^2)
     double xi, r0;  // RGL xi and r0 (parameter derivatives)
     // SC: V = eps (a/r)^n S, rho = (a/r)^m S; F = -F_scale sqrt(rho)
     double eps, a, n, m;

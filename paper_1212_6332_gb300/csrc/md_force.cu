@@ -59,9 +59,11 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
                                                      const Ctl* ctl) {
     if (load_status(ctl)) return;
     __shared__ double sT[kExpTable];
-    __shared__ double q_r2[kFNT / 32][kQueue];
-    __shared__ long long q_own[kFNT / 32][kQueue];
-    __shared__ long long q_mir[kFNT / 32][kQueue];
+    // two queues per warp: pairs inside r_taper (no taper) and beyond it,
+    // so each evaluated batch takes one branch of pair_eval
+    __shared__ double q_r2[kFNT / 32][2][kQueue];
+    __shared__ long long q_own[kFNT / 32][2][kQueue];
+    __shared__ long long q_mir[kFNT / 32][2][kQueue];
     if (KIND == MD_POT_RGL) load_exp_table(sT, P.exp_T);
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
         kend = nup < 0 ? n : nup;
     }
     const int kmax = warp_max(kend);
-    int qn = 0;
+    int qn[2] = {0, 0};
     for (int k = 0; k < kmax; ++k) {
         bool in = false;
         double r2 = 0.0;
@@ -108,23 +110,33 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
                 }
             }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (in) {
-            const int p = qn + __popc(m & lt_mask);
-            q_r2[wq][p] = r2;
-            q_own[wq][p] = own;
-            q_mir[wq][p] = mir;
+        const bool tq = r2 > P.rs2;
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {
+            const bool mine = in && (tq == (qq == 1));
+            const unsigned m = __ballot_sync(0xffffffffu, mine);
+            if (mine) {
+                const int p = qn[qq] + __popc(m & lt_mask);
+                q_r2[wq][qq][p] = r2;
+                q_own[wq][qq][p] = own;
+                q_mir[wq][qq][p] = mir;
+            }
+            qn[qq] += __popc(m);
         }
-        qn += __popc(m);
         __syncwarp();
-        if (qn >= 32) {
-            qn -= 32;
-            const int p = qn + lane;
-            eval_pair_item<KIND>(P, sT, q_r2[wq][p], q_own[wq][p], q_mir[wq][p], ab, fv);
-            __syncwarp();
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {
+            if (qn[qq] >= 32) {
+                qn[qq] -= 32;
+                const int p = qn[qq] + lane;
+                eval_pair_item<KIND>(P, sT, q_r2[wq][qq][p], q_own[wq][qq][p], q_mir[wq][qq][p], ab, fv);
+                __syncwarp();
+            }
         }
     }
-    if (lane < qn) eval_pair_item<KIND>(P, sT, q_r2[wq][lane], q_own[wq][lane], q_mir[wq][lane], ab, fv);
+#pragma unroll
+    for (int qq = 0; qq < 2; ++qq)
+        if (lane < qn[qq]) eval_pair_item<KIND>(P, sT, q_r2[wq][qq][lane], q_own[wq][qq][lane], q_mir[wq][qq][lane], ab, fv);
 }
 
 template <int KIND>

@@ -19,6 +19,9 @@
 //                 histogram over the cubic coefficients of each interval)
 // then a fixed-order reduction and, for splines, the transpose of the
 // knot-value -> coefficient map (one more tridiagonal solve per spline).
+// In mixed precision the RGL adjoint evaluates its pair terms in float32
+// (cell-local offsets, as the mixed forward pass) and sums the parameter
+// terms in float64; the spline adjoint always runs in float64.
 #include <cstring>
 
 #include "md_device.cuh"
@@ -334,6 +337,143 @@ __global__ void k_gather_g(int64_t N, int64_t Np, const double* __restrict__ g_f
     gs[2 * Np + t] = g_f ? g_f[3 * c + 2] : 0.0;
 }
 
+// ---------------------------------------------------------------- mixed precision
+//
+// The same three passes with float32 pair math from the cell-local offsets
+// (as in the mixed force kernels), float32 sums grouped per 16 list entries
+// and compensated, and the per-thread parameter sums in float64.
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kGNT) k_grad_rho_mixed(int64_t N, int64_t Np, Geo g, Pot P,
+                                                         const float4* __restrict__ xo, const int* __restrict__ nn,
+                                                         const int* __restrict__ nl, int max_nb,
+                                                         double* __restrict__ rho, double* __restrict__ Fp,
+                                                         double* __restrict__ Fpp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const CellSep cs = cell_sep<false>(g, CellSep{}, i);
+    const float4 oi = xo[i];
+    const int n = min(nn[i], max_nb);
+    GSum acc;
+    for (int k = 0; k < n; ++k) {
+        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        float dx, dy, dz;
+        sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+        float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < P.f_rc2) acc.add(dens_ff<MD_POT_RGL>(P, r2 * rsqrtf(r2)));
+        if ((k & kGroupMask) == kGroupMask) acc.flush();
+    }
+    double r_i = acc.value();
+    double F, Fpi;
+    embed<MD_POT_RGL>(P, r_i, F, Fpi);
+    rho[i] = r_i;
+    Fp[i] = Fpi;
+    Fpp[i] = r_i > 0.0 ? 0.25 * P.F_scale / (r_i * sqrt(r_i)) : 0.0;
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kGNT) k_grad_u_mixed(int64_t N, int64_t Np, Geo g, Pot P,
+                                                       const float4* __restrict__ xo, const int* __restrict__ nn,
+                                                       const int* __restrict__ nl, int max_nb,
+                                                       const double* __restrict__ gs, double* __restrict__ u) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const CellSep cs = cell_sep<false>(g, CellSep{}, i);
+    const float4 oi = xo[i];
+    const int n = min(nn[i], max_nb);
+    const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
+    GSum acc;
+    for (int k = 0; k < n; ++k) {
+        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        float dx, dy, dz;
+        sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+        float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < P.f_rc2) {
+            float rinv = rsqrtf(r2);
+            float phi, dphi, fr, dfr;
+            pair_allf<MD_POT_RGL>(P, r2 * rinv, phi, dphi, fr, dfr);
+            float w = (float)(gx - gs[j]) * dx + (float)(gy - gs[Np + j]) * dy + (float)(gz - gs[2 * Np + j]) * dz;
+            acc.add(w * dfr * rinv);
+        }
+        if ((k & kGroupMask) == kGroupMask) acc.flush();
+    }
+    u[i] = acc.value();
+}
+
+__device__ __forceinline__ void rgl_param_terms_f(const Pot& P, float r, float aVp, float aFp, float aF, float aV,
+                                                  double* acc) {
+    float S, dS;
+    taperf(P, r, S, dS);
+    const float p_r0 = P.f_p_r0, q2_r0 = P.f_q2_r0, r0 = (float)P.r0;
+    const float u = r / r0 - 1.0f;
+    const float E1 = __expf(P.f_p - p_r0 * r), E2 = __expf(P.f_q2 - q2_r0 * r);
+    const float gV = S, gVp = dS - p_r0 * S, gf = S, gfp = dS - q2_r0 * S;
+    const float e1 = P.f_A2 * E1, e2 = P.f_xi2 * E2;
+    const float V = e1 * gV, Vp = e1 * gVp, f = e2 * gf, fp = e2 * gfp;
+    const float inv_r02 = 1.0f / (r0 * r0), c0 = r * inv_r02, pp = P.f_p, q2 = P.f_q2, xi = (float)P.xi;
+    acc[0] += (double)(aVp * (2.0f * E1 * gVp) + aV * (2.0f * E1 * gV));
+    acc[1] += (double)(aFp * (2.0f * xi * E2 * gfp) + aF * (2.0f * xi * E2 * gf));
+    acc[2] += (double)(aVp * (-u * Vp - e1 * S / r0) + aV * (-u * V));
+    acc[3] += (double)(aFp * (-2.0f * u * fp - 2.0f * e2 * S / r0) + aF * (-2.0f * u * f));
+    acc[4] += (double)(aVp * (pp * c0 * Vp + e1 * pp * S * inv_r02) + aV * (pp * c0 * V) +
+                       aFp * (q2 * c0 * fp + e2 * q2 * S * inv_r02) + aF * (q2 * c0 * f));
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kGNT) k_grad_param_rgl_mixed(int64_t N, int64_t Np, Geo g, Pot P,
+                                                               const float4* __restrict__ xo,
+                                                               const int* __restrict__ nn,
+                                                               const int* __restrict__ nl, int max_nb,
+                                                               const double* __restrict__ gs,
+                                                               const double* __restrict__ gE,
+                                                               const double* __restrict__ Fp,
+                                                               const double* __restrict__ Fpp,
+                                                               const double* __restrict__ u,
+                                                               double* __restrict__ partial) {
+    __shared__ double sh[kGNT / 32];
+    double acc[kRglParams] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const CellSep cs = cell_sep<false>(g, CellSep{}, i);
+        const float4 oi = xo[i];
+        const int n = min(nn[i], max_nb);
+        const float gx = (float)gs[i], gy = (float)gs[Np + i], gz = (float)gs[2 * Np + i];
+        const double ge = box_gE(g, gE, i);
+        const double Fpi = Fp[i];
+        const float aF = (float)(u[i] * Fpp[i] + ge * Fpi);
+        for (int k = 0; k < n; ++k) {
+            int j = entry_slot(nl[(int64_t)k * Np + i]);
+            float dx, dy, dz;
+            sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+            float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= P.f_rc2) continue;
+            float rinv = rsqrtf(r2);
+            float r = r2 * rinv;
+            float w = (gx * dx + gy * dy + gz * dz) * rinv;
+            rgl_param_terms_f(P, r, w, w * (float)(Fpi + Fp[j]), aF, (float)(0.5 * ge), acc);
+        }
+    }
+    for (int k = 0; k < kRglParams; ++k) {
+        double t = block_sum<kGNT>(acc[k], sh);
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * kRglParams + k] = t;
+    }
+}
+
+template <bool WIDE>
+static int grad_mixed_impl(Engine& e, const double* g_f, const double* g_e, double* grad, cudaStream_t s) {
+    Geo g = make_geo(e);
+    int nb = (int)((e.N + kGNT - 1) / kGNT);
+    k_gather_g<<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g_f, e.perm, e.grad_g);
+    k_grad_rho_mixed<WIDE><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.rho, e.Fp,
+                                               e.grad_Fpp);
+    k_grad_u_mixed<WIDE><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.grad_g, e.grad_u);
+    k_grad_param_rgl_mixed<WIDE><<<e.grad_blocks, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb,
+                                                               e.grad_g, g_e, e.Fp, e.grad_Fpp, e.grad_u,
+                                                               e.grad_partial);
+    k_sum_partials<<<kRglParams, 256, 0, s>>>(e.grad_blocks, kRglParams, e.grad_partial, grad);
+    e.launches += 5;
+    return MD_OK;
+}
+
 template <int KIND>
 static int grad_impl(Engine& e, const double* g_f, const double* g_e, double* grad, cudaStream_t s) {
     Geo g = make_geo(e);
@@ -367,7 +507,12 @@ int launch_param_grad(Engine& e, const double* g_f, const double* g_e, double* g
     if (e.N == 0) return cudaMemsetAsync(grad, 0, sizeof(double) * (e.pot_host.kind == MD_POT_SPLINE ?
                                               e.pot_host.n_phi + e.pot_host.n_f + e.pot_host.n_F : 5), s) ==
                                   cudaSuccess ? MD_OK : MD_ERR_CUDA;
-    if (e.pot.kind == MD_POT_RGL) return grad_impl<MD_POT_RGL>(e, g_f, g_e, grad, s);
+    if (e.pot.kind == MD_POT_RGL) {
+        // mixed precision: float32 pair math in the adjoint as in the forward
+        if (e.cfg.precision == MD_MIXED)
+            return e.wide ? grad_mixed_impl<true>(e, g_f, g_e, grad, s) : grad_mixed_impl<false>(e, g_f, g_e, grad, s);
+        return grad_impl<MD_POT_RGL>(e, g_f, g_e, grad, s);
+    }
     if (e.pot.kind == MD_POT_SPLINE) {
         const md_potential& p = e.pot_host;
         int ncoef = 4 * (p.n_phi - 1) + 4 * (p.n_f - 1) + 4 * (p.n_F - 1);

@@ -20,70 +20,6 @@ namespace mdk {
 
 constexpr int kMNT = 128;
 
-struct CellSep {
-    float lx, ly, lz;     // cell sides
-    int nx, ny, nz;       // cells per axis
-    float Lx, Ly, Lz;     // box lengths
-};
-
-__device__ __forceinline__ int wrap_cells(int d, int n) {
-    if (2 * d > n) return d - n;
-    if (2 * d < -n) return d + n;
-    return d;
-}
-
-// WIDE: every box has at least 3 cells per axis, so the nearest cell image
-// is the nearest atom image and no box-length correction can be needed.
-template <bool WIDE>
-__device__ __forceinline__ void sep_mixed(const CellSep& cs, float4 oi, float4 oj, float& dx, float& dy, float& dz) {
-    int ci = __float_as_int(oi.w), cj = __float_as_int(oj.w);
-    int ddx = wrap_cells((cj & 1023) - (ci & 1023), cs.nx);
-    int ddy = wrap_cells(((cj >> 10) & 1023) - ((ci >> 10) & 1023), cs.ny);
-    int ddz = wrap_cells(((cj >> 20) & 1023) - ((ci >> 20) & 1023), cs.nz);
-    dx = fmaf((float)ddx, cs.lx, oj.x - oi.x);
-    dy = fmaf((float)ddy, cs.ly, oj.y - oi.y);
-    dz = fmaf((float)ddz, cs.lz, oj.z - oi.z);
-    if (!WIDE) {
-        dx = minimgf(dx, cs.Lx, 0.5f * cs.Lx);
-        dy = minimgf(dy, cs.Ly, 0.5f * cs.Ly);
-        dz = minimgf(dz, cs.Lz, 0.5f * cs.Lz);
-    }
-}
-
-// Plain float32 partial sum over a group of list entries, folded into a
-// compensated total at group ends.
-struct GSum {
-    float part = 0.0f;
-    KSum tot;
-    __device__ __forceinline__ void add(float x) { part += x; }
-    __device__ __forceinline__ void flush() {
-        tot.add(part);
-        part = 0.0f;
-    }
-    __device__ __forceinline__ double value() {
-        flush();
-        return tot.value();
-    }
-};
-constexpr int kGroupMask = 15;
-
-template <bool SINGLE>
-__device__ __forceinline__ CellSep cell_sep(const Geo& g, const CellSep& cs0, int64_t i) {
-    if (SINGLE) return cs0;
-    int b = g.atom_box[i];
-    CellSep cs;
-    cs.lx = g.cell_len_f[3 * b];
-    cs.ly = g.cell_len_f[3 * b + 1];
-    cs.lz = g.cell_len_f[3 * b + 2];
-    cs.nx = g.nc[3 * b];
-    cs.ny = g.nc[3 * b + 1];
-    cs.nz = g.nc[3 * b + 2];
-    cs.Lx = (float)g.L[3 * b];
-    cs.Ly = (float)g.L[3 * b + 1];
-    cs.Lz = (float)g.L[3 * b + 2];
-    return cs;
-}
-
 template <int KIND, bool SINGLE, bool WIDE>
 __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P,
                                                         const float4* __restrict__ xo, const int* __restrict__ nn,
