@@ -37,6 +37,7 @@ Geo make_geo(const Engine& e) {
     g.cell_box = e.cell_box;
     g.cell_rank = e.cell_rank;
     g.cell_xyz = e.cell_xyz;
+    g.cell_org = e.cell_org;
     for (int a = 0; a < 3; ++a) g.L0[a] = e.L_h.size() >= 3 ? e.L_h[a] : 0.0;
     return g;
 }
@@ -205,7 +206,7 @@ void destroy_graphs(Engine& e) {
 void free_engine(Engine& e) {
     destroy_graphs(e);
     dfree(e.L); dfree(e.cell_len); dfree(e.cell_len_f); dfree(e.nc); dfree(e.cell_off); dfree(e.atom_off);
-    dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.spline_coef);
+    dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.cell_org); dfree(e.spline_coef);
     dfree(e.spline_work); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
     dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
@@ -303,6 +304,12 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     }
     e.n_cells = (int)tot;
     e.wide = *std::min_element(e.nc_h.begin(), e.nc_h.end()) >= 3;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&e.n_sm, cudaDevAttrMultiProcessorCount, dev);
+        e.n_sm = std::max(e.n_sm, 1);
+    }
     std::vector<int> rank(tot), xyz(tot), cbox(tot);
     for (int b = 0; b < B; ++b) {
         int nx = e.nc_h[3 * b], ny = e.nc_h[3 * b + 1], nz = e.nc_h[3 * b + 2];
@@ -367,6 +374,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.cell_box, tot);
     AL(e.cell_rank, tot);
     AL(e.cell_xyz, tot);
+    AL(e.cell_org, tot);
     if (pot->kind == MD_POT_SPLINE) {
         AL(e.spline_coef, nk);
         AL(e.spline_work, 3 * nk);
@@ -432,6 +440,20 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
         ce = ce != cudaSuccess ? ce : up(e.cell_box, cbox.data(), tot * sizeof(int));
         ce = ce != cudaSuccess ? ce : up(e.cell_rank, rank.data(), tot * sizeof(int));
         ce = ce != cudaSuccess ? ce : up(e.cell_xyz, xyz.data(), tot * sizeof(int));
+        {
+            std::vector<double4_32a> org(tot);
+            for (int c = 0; c < tot; ++c) {
+                const int b = cbox[c], v = xyz[c];
+                const int cc[3] = {v & 1023, (v >> 10) & 1023, (v >> 20) & 1023};
+                double o[3];
+                for (int a = 0; a < 3; ++a) o[a] = cc[a] * cl[3 * b + a];
+                long long w = v;
+                double wd;
+                memcpy(&wd, &w, sizeof(wd));
+                org[c] = make_double4_32a(o[0], o[1], o[2], wd);
+            }
+            ce = ce != cudaSuccess ? ce : up(e.cell_org, org.data(), tot * sizeof(double4_32a));
+        }
         if (e.n_chunks) {
             ce = ce != cudaSuccess ? ce : up(e.chunk_lo, clo.data(), clo.size() * sizeof(int64_t));
             ce = ce != cudaSuccess ? ce : up(e.chunk_hi, chi.data(), chi.size() * sizeof(int64_t));
@@ -1070,10 +1092,8 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
     if (g_e && !is_device_ptr(g_e)) return fail(E, MD_ERR_ARG, "g_e must be a device pointer");
     Engine& e = *E;
     if (!e.grad_g && e.N > 0) {
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
         int nb = (int)((e.N + 127) / 128);
-        e.grad_blocks = std::max(1, std::min(nb, 4 * std::max(sms, 1)));
+        e.grad_blocks = std::max(1, std::min(nb, 4 * e.n_sm));
         const md_potential& p = e.pot_host;
         size_t ncoef = p.kind == MD_POT_SPLINE ? 4 * ((size_t)p.n_phi + p.n_f + p.n_F - 3) : 5;
         if (dalloc(E, &e.grad_g, 3 * (size_t)e.N_pad) || dalloc(E, &e.grad_u, (size_t)e.N_pad) ||

@@ -277,10 +277,10 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
                 const int e = A.nl[slot];
                 double dx, dy, dz;
                 sep_entry(xi, sx[entry_slot(e) - a0], entry_code(e), L, dx, dy, dz);
-                double r2 = dx * dx + dy * dy + dz * dz;
+                double r2 = norm2(dx, dy, dz);
                 double2 c = make_double2(0.0, 0.0);
                 double phi = 0.0, fr = 0.0;
-                if (r2 < P.rc2) pair_eval<KIND>(P, sT, r2, phi, fr, c.x, c.y);
+                if (below(r2, P.rc2)) pair_eval<KIND>(P, sT, r2, phi, fr, c.x, c.y);
                 // the tile schedule stores these values and sums them with
                 // round-to-nearest adds in list order: do exactly that
                 r_i = __dadd_rn(r_i, fr);

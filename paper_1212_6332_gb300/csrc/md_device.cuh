@@ -76,6 +76,17 @@ __device__ __forceinline__ void sep_entry(const double4_32a& xi, const double4_3
     }
 }
 
+// |d|^2 with a fixed contraction, so every kernel that evaluates a pair
+// gets the same bits
+__device__ __forceinline__ double norm2(double dx, double dy, double dz) {
+    return fma(dz, dz, fma(dy, dy, dx * dx));
+}
+
+// r^2 < c^2 for non-negative, non-NaN doubles, as an integer compare
+__device__ __forceinline__ bool below(double r2, double c2) {
+    return __double_as_longlong(r2) < __double_as_longlong(c2);
+}
+
 __device__ __forceinline__ int load_status(const Ctl* c) {
     return *((volatile const int*)&c->status);
 }
@@ -284,8 +295,10 @@ __device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict
                                           double& fr, double& A, double& B) {
     double rinv = rsqrt_nr(r2);
     double r = r2 * rinv;
-    // pairs inside r_taper (r^2 <= r_taper^2) skip the taper (S = 1, S' = 0)
-    const bool tap = r2 > P.rs2;
+    // pairs inside r_taper (r^2 <= r_taper^2) skip the taper (S = 1, S' = 0);
+    // non-negative doubles order like their bit patterns, so the test runs
+    // on the integer pipe
+    const bool tap = __double_as_longlong(r2) > __double_as_longlong(P.rs2);
     if (KIND == MD_POT_RGL) {
         // the prefactors 2A and xi^2 ride in the exponent when both are positive
         double e1 = P.fold ? exp_tab(P.pA - P.p_r0 * r, T, P.ek) : P.A2 * exp_tab(P.p - P.p_r0 * r, T, P.ek);
@@ -478,12 +491,6 @@ struct KSum {
 };
 
 // ---------------------------------------------------------------- mixed-precision separation
-
-struct CellSep {
-    float lx, ly, lz;     // cell sides
-    int nx, ny, nz;       // cells per axis
-    float Lx, Ly, Lz;     // box lengths
-};
 
 __device__ __forceinline__ int wrap_cells(int d, int n) {
     if (2 * d > n) return d - n;

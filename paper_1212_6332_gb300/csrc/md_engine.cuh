@@ -46,7 +46,7 @@ struct Pot {
     double st0[3], sh[3], sinvh[3];
     // table-driven exponential (float64 path)
     ExpConst ek;
-    const double* exp_T;  // [kExpTable] 2^(j/256)
+    const double* exp_T;  // [kExpTable] 2^(j/kExpTable)
     // float copies for the mixed-precision path
     float f_rc2, f_rs, f_inv_w, f_A2, f_xi2, f_p, f_p_r0, f_q2, f_q2_r0, f_eps, f_a, f_n, f_m;
 };
@@ -64,6 +64,7 @@ struct Geo {
     const int* cell_box;      // [n_cells] box of each global cell
     const int* cell_rank;     // [n_cells] (box, row-major cell) -> global Morton-ordered cell
     const int* cell_xyz;      // [n_cells] global cell -> packed (cx | cy << 10 | cz << 20)
+    const double4_32a* cell_org;  // [n_cells] cell origin (x, y, z) and, in w's bits, the packed coordinates
     // single-box fast path
     double L0[3];
 };
@@ -76,6 +77,13 @@ struct Ctl {
     long long step;                  // completed steps since set_state
     long long n_rebuild;             // list builds since set_state
     int max_count;                   // largest neighbour count of the current list
+};
+
+// Float32 cell geometry of a box (mixed-precision separations).
+struct CellSep {
+    float lx, ly, lz;     // cell sides
+    int nx, ny, nz;       // cells per axis
+    float Lx, Ly, Lz;     // box lengths
 };
 
 // Shared-memory size class of the block-per-box schedule.
@@ -95,6 +103,7 @@ struct Engine {
     int n_cells = 0;
     int max_nb = 0;
     bool wide = false;  // every box has at least 3 cells per axis
+    int n_sm = 1;       // multiprocessors of the handle's device
     double rl = 0.0;  // list radius r_cut + skin
     std::vector<int64_t> atom_off_h;
     std::vector<double> L_h;
@@ -112,6 +121,7 @@ struct Engine {
     int* cell_box = nullptr;
     int* cell_rank = nullptr;
     int* cell_xyz = nullptr;
+    double4_32a* cell_org = nullptr;
     double4_32a* spline_coef = nullptr;  // 3 splines back to back
     double* spline_work = nullptr;   // [3 * total knots] setup scratch
     double* knots_dev = nullptr;
@@ -221,6 +231,8 @@ struct PhaseScope {
 };
 
 Geo make_geo(const Engine& e);
+// float32 cell geometry of a single-box handle (batches read it per box)
+CellSep single_cell_sep(const Engine& e);
 
 // ---- kernels' host launchers (all enqueue on `s`) ----
 // binning + sort + permute + list build; mode 1 = always, 0 = only when the

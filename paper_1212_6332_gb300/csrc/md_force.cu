@@ -31,19 +31,37 @@ namespace mdk {
 
 constexpr int kFNT = 128;
 
-// Pair pass. Lanes walk their own lists (coalesced rows, cheap separation
-// and r^2), and the in-cutoff pairs are compacted through a per-warp queue
-// in shared memory: every batch of 32 queued pairs is evaluated with all 32
-// lanes active. On GB300 a masked lane still costs the float64 pipe its
-// cycles, and without compaction half the lanes of a warp would idle (list
-// lengths, the cutoff test).
+// Pair pass. Each warp owns groups of 32 consecutive atoms in turn
+// (persistent warps, so queue tails are paid once per warp, not once per
+// group). Lanes walk their own lists (coalesced rows) and screen every upper
+// entry with a float32 r^2 from the cell-local offsets: an entry whose
+// float32 r^2 lies above rc^2 (1 + 1e-4) is outside r_cut in any image (the
+// float32 error of r^2 is below 1e-4 A^2, the margin 25 times more for
+// rc = 5 A) and gets zeros. For the rest the lane forms the exact float64
+// separation (x_j is loaded beside its offset, so this adds no latency) and
+// queues it in shared memory, in one of two per-warp queues split at
+// r_taper so that a batch takes one branch of pair_eval. Every batch of 32
+// takes r^2, the exact test r^2 < rc^2 (which alone decides, as in the list
+// build) and the pair functions with all 32 lanes active: on GB300 a masked
+// lane still costs the float64 pipe its cycles. The exponential table is
+// read through L1 (one 16 KB copy per multiprocessor instead of one per
+// block in shared memory, which leaves L1 room for the list streams).
 constexpr int kQueue = 64;
+constexpr double kScreen = 1e-4;  // relative r^2 margin of the float32 screen
+
+struct PairQueue {
+    double d[3][2][kQueue];    // separation x_j - x_i, per axis and region
+    long long own[2][kQueue];  // slot of the entry in i's list
+    long long mir[2][kQueue];  // slot of the mirror entry in j's list
+};
 
 template <int KIND>
-__device__ __forceinline__ void eval_pair_item(const Pot& P, const double* __restrict__ sT, double r2, int64_t own,
-                                               int64_t mir, double2* __restrict__ ab, double2* __restrict__ fv) {
-    double2 c, w;
-    pair_eval<KIND>(P, sT, r2, w.y, w.x, c.x, c.y);
+__device__ __forceinline__ void eval_queued(const Pot& P, const PairQueue& q, int r, int p,
+                                            double2* __restrict__ ab, double2* __restrict__ fv) {
+    const double r2 = norm2(q.d[0][r][p], q.d[1][r][p], q.d[2][r][p]);
+    double2 c = make_double2(0.0, 0.0), w = make_double2(0.0, 0.0);
+    if (below(r2, P.rc2)) pair_eval<KIND>(P, P.exp_T, r2, w.y, w.x, c.x, c.y);
+    const long long own = q.own[r][p], mir = q.mir[r][p];
     ab[own] = c;
     fv[own] = w;
     ab[mir] = c;
@@ -51,92 +69,106 @@ __device__ __forceinline__ void eval_pair_item(const Pot& P, const double* __res
 }
 
 template <int KIND, bool SINGLE>
-__global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo g, Pot P,
-                                                     const double4_32a* __restrict__ x, const int* __restrict__ nn,
+__global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P, float rc2f,
+                                                     float rs2f, const double4_32a* __restrict__ x,
+                                                     const float4* __restrict__ xo, const int* __restrict__ nn,
                                                      const int* __restrict__ nl, const int* __restrict__ rev,
                                                      const int* __restrict__ n_up, int max_nb,
                                                      double2* __restrict__ ab, double2* __restrict__ fv,
                                                      const Ctl* ctl) {
     if (load_status(ctl)) return;
-    __shared__ double sT[kExpTable];
-    // two queues per warp: pairs inside r_taper (no taper) and beyond it,
-    // so each evaluated batch takes one branch of pair_eval
-    __shared__ double q_r2[kFNT / 32][2][kQueue];
-    __shared__ long long q_own[kFNT / 32][2][kQueue];
-    __shared__ long long q_mir[kFNT / 32][2][kQueue];
-    if (KIND == MD_POT_RGL) load_exp_table(sT, P.exp_T);
-    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    __shared__ PairQueue queues[kFNT / 32];
+    const int lane = threadIdx.x & 31;
+    PairQueue& q = queues[threadIdx.x >> 5];
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < N;
-    double L[3] = {0.0, 0.0, 0.0};
-    double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    int kend = 0;
-    if (active) {
-        int b = SINGLE ? 0 : g.atom_box[i];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
-        xi = x[i];
-        const int n = min(nn[i], max_nb);
-        // lists are [upper | lower]: the upper entries (j > i) are rows
-        // 0..n_up-1; the lower ones are written by the partners' threads (a
-        // list kept unrotated, n_up < 0, is scanned whole)
-        const int nup = n_up[i];
-        kend = nup < 0 ? n : nup;
-    }
-    const int kmax = warp_max(kend);
+    const int64_t n_groups = (N + 31) >> 5, stride = (int64_t)gridDim.x * (kFNT / 32);
     int qn[2] = {0, 0};
-    for (int k = 0; k < kmax; ++k) {
-        bool in = false;
-        double r2 = 0.0;
-        int64_t own = 0, mir = 0;
-        if (k < kend) {
-            own = (int64_t)k * Np + i;
-            const int e = nl[own];
-            const int j = entry_slot(e);
-            if (j > i) {
-                double dx, dy, dz;
-                sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
-                r2 = dx * dx + dy * dy + dz * dz;
-                mir = (int64_t)rev[own] * Np + j;
-                if (r2 < P.rc2) {
-                    in = true;
-                } else {
-                    const double2 z = make_double2(0.0, 0.0);
-                    ab[own] = z;
-                    fv[own] = z;
-                    ab[mir] = z;
-                    fv[mir] = z;
+    for (int64_t grp = (int64_t)blockIdx.x * (kFNT / 32) + (threadIdx.x >> 5); grp < n_groups; grp += stride) {
+        const int64_t i = grp * 32 + lane;
+        CellSep cs = cs0;
+        float4 oi = make_float4(0.f, 0.f, 0.f, 0.f);
+        double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        double L[3] = {0.0, 0.0, 0.0};
+        int kend = 0;
+        if (i < N) {
+            cs = cell_sep<SINGLE>(g, cs0, i);
+            const int b = SINGLE ? 0 : g.atom_box[i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+            oi = xo[i];
+            xi = x[i];
+            // lists are [upper | lower]: the upper entries (j > i) are rows
+            // 0..n_up-1; the lower ones are written by the partners' lanes (a
+            // list kept unrotated, n_up < 0, is scanned whole)
+            const int nup = n_up[i];
+            kend = nup < 0 ? min(nn[i], max_nb) : nup;
+        }
+        const int kmax = warp_max(kend);
+        for (int k = 0; k < kmax; ++k) {
+            bool in = false, tq = false;
+            double dx = 0.0, dy = 0.0, dz = 0.0;
+            long long own = 0, mir = 0;
+            if (k < kend) {
+                own = (long long)k * Np + i;
+                const int e = nl[own];
+                const int j = entry_slot(e);
+                if (j > i) {
+                    const float4 oj = xo[j];
+                    const double4_32a xj = x[j];
+                    mir = (long long)rev[own] * Np + j;
+                    float fx, fy, fz;
+                    sep_mixed<false>(cs, oi, oj, fx, fy, fz);
+                    const float r2f = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
+                    if (r2f < rc2f) {
+                        in = true;
+                        tq = r2f > rs2f;
+                        sep_entry(xi, xj, entry_code(e), L, dx, dy, dz);
+                    } else {
+                        const double2 z = make_double2(0.0, 0.0);
+                        ab[own] = z;
+                        fv[own] = z;
+                        ab[mir] = z;
+                        fv[mir] = z;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const bool mine = in && (tq == (r == 1));
+                const unsigned m = __ballot_sync(0xffffffffu, mine);
+                if (mine) {
+                    const int p = qn[r] + __popc(m & lt_mask);
+                    q.d[0][r][p] = dx;
+                    q.d[1][r][p] = dy;
+                    q.d[2][r][p] = dz;
+                    q.own[r][p] = own;
+                    q.mir[r][p] = mir;
+                }
+                qn[r] += __popc(m);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (qn[r] >= 32) {
+                    qn[r] -= 32;
+                    eval_queued<KIND>(P, q, r, qn[r] + lane, ab, fv);
+                    __syncwarp();
                 }
             }
         }
-        const bool tq = r2 > P.rs2;
-#pragma unroll
-        for (int qq = 0; qq < 2; ++qq) {
-            const bool mine = in && (tq == (qq == 1));
-            const unsigned m = __ballot_sync(0xffffffffu, mine);
-            if (mine) {
-                const int p = qn[qq] + __popc(m & lt_mask);
-                q_r2[wq][qq][p] = r2;
-                q_own[wq][qq][p] = own;
-                q_mir[wq][qq][p] = mir;
-            }
-            qn[qq] += __popc(m);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int qq = 0; qq < 2; ++qq) {
-            if (qn[qq] >= 32) {
-                qn[qq] -= 32;
-                const int p = qn[qq] + lane;
-                eval_pair_item<KIND>(P, sT, q_r2[wq][qq][p], q_own[wq][qq][p], q_mir[wq][qq][p], ab, fv);
-                __syncwarp();
-            }
-        }
     }
+    // tails: one batch when both fit (lanes of the two regions diverge in
+    // pair_eval, which still costs less than two part-empty batches)
+    if (qn[0] + qn[1] <= 32) {
+        if (lane < qn[0])
+            eval_queued<KIND>(P, q, 0, lane, ab, fv);
+        else if (lane < qn[0] + qn[1])
+            eval_queued<KIND>(P, q, 1, lane - qn[0], ab, fv);
+    } else {
 #pragma unroll
-    for (int qq = 0; qq < 2; ++qq)
-        if (lane < qn[qq]) eval_pair_item<KIND>(P, sT, q_r2[wq][qq][lane], q_own[wq][qq][lane], q_mir[wq][qq][lane], ab, fv);
+        for (int r = 0; r < 2; ++r)
+            if (lane < qn[r]) eval_queued<KIND>(P, q, r, lane, ab, fv);
+    }
 }
 
 template <int KIND>
@@ -207,6 +239,27 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
 
 void launch_forces_mixed(Engine& e, int kick, cudaStream_t s);
 
+// float32 screen threshold: rc^2 (1 + margin), rounded up
+static float screen_r2f(double rc2) { return nextafterf((float)(rc2 * (1.0 + kScreen)), INFINITY); }
+
+// persistent pair pass: resident blocks on every SM, at most one group per warp
+static int pair_blocks(const Engine& e) {
+    static int per_sm[3] = {0, 0, 0};  // by potential kind, both SINGLE forms share the resources
+    int& r = per_sm[e.pot.kind];
+    if (!r) {
+        int b = 0;
+        if (e.pot.kind == MD_POT_RGL)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_half<MD_POT_RGL, false>, kFNT, 0);
+        else if (e.pot.kind == MD_POT_SC)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_half<MD_POT_SC, false>, kFNT, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_half<MD_POT_SPLINE, false>, kFNT, 0);
+        r = b > 0 ? b : 1;
+    }
+    const int64_t groups = (e.N + 31) / 32, per_block = kFNT / 32;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((groups + per_block - 1) / per_block, (int64_t)r * e.n_sm));
+}
+
 template <int KIND, bool SINGLE>
 static void run_fp64(Engine& e, int kick, cudaStream_t s) {
     Geo g = make_geo(e);
@@ -215,8 +268,10 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s) {
     e.launches += 3;
     {
         PhaseScope scope(e, MD_PHASE_PAIRS, s);
-        k_pairs_half<KIND, SINGLE><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.rev, e.n_up,
-                                                      e.max_nb, e.ab, e.fv, e.ctl);
+        k_pairs_half<KIND, SINGLE><<<pair_blocks(e), kFNT, 0, s>>>(e.N, e.N_pad, g, single_cell_sep(e), e.pot,
+                                                                   screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.x,
+                                                                   e.xo, e.nn, e.nl, e.rev, e.n_up, e.max_nb, e.ab,
+                                                                   e.fv, e.ctl);
     }
     {
         PhaseScope scope(e, MD_PHASE_DENSITY, s);

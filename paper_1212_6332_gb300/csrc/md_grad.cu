@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kGNT) k_grad_rho(int64_t N, int64_t Np, Geo g,
         int j = entry_slot(nl[(int64_t)k * Np + i]);
         double dx, dy, dz;
         sep(g, x, i, j, dx, dy, dz);
-        double r2 = dx * dx + dy * dy + dz * dz;
+        double r2 = norm2(dx, dy, dz);
         if (r2 >= P.rc2) continue;
         double phi, fr, A, B;
         pair_eval<KIND>(P, sT, r2, phi, fr, A, B);
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kGNT) k_grad_u(int64_t N, int64_t Np, Geo g, P
         int j = entry_slot(nl[(int64_t)k * Np + i]);
         double dx, dy, dz;
         sep(g, x, i, j, dx, dy, dz);
-        double r2 = dx * dx + dy * dy + dz * dz;
+        double r2 = norm2(dx, dy, dz);
         if (r2 >= P.rc2) continue;
         double phi, fr, A, B;
         pair_eval<KIND>(P, sT, r2, phi, fr, A, B);
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl(int64_t N, int64_t Np, 
             int j = entry_slot(nl[(int64_t)k * Np + i]);
             double dx, dy, dz;
             sep(g, x, i, j, dx, dy, dz);
-            double r2 = dx * dx + dy * dy + dz * dz;
+            double r2 = norm2(dx, dy, dz);
             if (r2 >= P.rc2) continue;
             double r = sqrt(r2);
             double w = (gx * dx + gy * dy + gz * dz) / r;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline(int64_t N, int64_t Np,
             int j = entry_slot(nl[(int64_t)k * Np + i]);
             double dx, dy, dz;
             sep(g, x, i, j, dx, dy, dz);
-            double r2 = dx * dx + dy * dy + dz * dz;
+            double r2 = norm2(dx, dy, dz);
             if (r2 >= P.rc2) continue;
             double r = sqrt(r2);
             if (r >= P.rc) continue;

@@ -1,8 +1,9 @@
 // Time integration, reductions and caller-order copies.
 //
 //   k_kick_drift   v += dt/2 F/m; x += dt v; largest displacement since
-//                  the last list build (device rebuild trigger); mixed
-//                  precision: refresh the cell-local float32 offsets
+//                  the last list build (device rebuild trigger); refresh
+//                  the cell-local float32 offsets (float32 screens and
+//                  mixed-precision pair math)
 //   k_end_step     step bookkeeping on the device (no host round trip)
 //   k_chunk_sums / k_thermo_final
 //                  deterministic fixed-order sums of kinetic and potential
@@ -15,7 +16,7 @@ namespace mdk {
 
 constexpr int kINT = 256;
 
-template <bool SINGLE, bool MIXED>
+template <bool SINGLE>
 __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo g, double4_32a* __restrict__ x,
                                                      double* __restrict__ v, const double* __restrict__ f,
                                                      const double4_32a* __restrict__ xb, double c_kick, double dt,
@@ -46,19 +47,12 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
         x[i] = p;
         double dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
         d2 = dx * dx + dy * dy + dz * dz;
-        if (MIXED) {
-            int gc = cell_t[i];
-            int xyz = g.cell_xyz[gc];
-            int c[3] = {xyz & 1023, (xyz >> 10) & 1023, (xyz >> 20) & 1023};
-            double pc[3] = {p.x, p.y, p.z};
-            float o[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                double d = pc[a] - c[a] * g.cell_len[3 * b + a];
-                o[a] = (float)minimg(d, L[a], 0.5 * L[a]);
-            }
-            xo[i] = make_float4(o[0], o[1], o[2], __int_as_float(xyz));
-        }
+        // offset from the origin of the atom's cell at the last build; it
+        // may leave [0, cell side) by the drift since then, which every user
+        // of the offsets allows for
+        const double4_32a org = g.cell_org[cell_t[i]];
+        xo[i] = make_float4((float)(p.x - org.x), (float)(p.y - org.y), (float)(p.z - org.z),
+                            __int_as_float((int)__double_as_longlong(org.w)));
     }
     // largest d2 per box (non-negative doubles order like their bit
     // patterns): one atomic per block when the block lies in one box, per
@@ -183,24 +177,23 @@ __global__ void __launch_bounds__(1024) k_thermo_final(int B, const int* __restr
     }
 }
 
-template <bool SINGLE, bool MIXED>
+template <bool SINGLE>
 static void kick_drift_t(Engine& e, cudaStream_t s) {
     Geo g = make_geo(e);
     int nb = (int)((e.N + kINT - 1) / kINT);
     double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
     PhaseScope scope(e, MD_PHASE_KICK_DRIFT, s);
     e.launches += 1;
-    k_kick_drift<SINGLE, MIXED><<<nb, kINT, 0, s>>>(e.N, e.N_pad, g, e.x, e.v, e.f, e.xb, c_kick, e.cfg.dt, e.xo,
+    k_kick_drift<SINGLE><<<nb, kINT, 0, s>>>(e.N, e.N_pad, g, e.x, e.v, e.f, e.xb, c_kick, e.cfg.dt, e.xo,
                                                    e.cell_t, e.ctl, e.disp_box);
 }
 
 void launch_kick_drift(Engine& e, cudaStream_t s) {
     if (e.N == 0) return;
-    bool mixed = e.cfg.precision == MD_MIXED;
     if (e.B == 1)
-        mixed ? kick_drift_t<true, true>(e, s) : kick_drift_t<true, false>(e, s);
+        kick_drift_t<true>(e, s);
     else
-        mixed ? kick_drift_t<false, true>(e, s) : kick_drift_t<false, false>(e, s);
+        kick_drift_t<false>(e, s);
 }
 
 void launch_end_step(Engine& e, int record_hist, cudaStream_t s) {

@@ -101,21 +101,25 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
     }
 }
 
+CellSep single_cell_sep(const Engine& e) {
+    CellSep cs{};
+    if (e.B != 1) return cs;
+    cs.lx = (float)(e.L_h[0] / e.nc_h[0]);
+    cs.ly = (float)(e.L_h[1] / e.nc_h[1]);
+    cs.lz = (float)(e.L_h[2] / e.nc_h[2]);
+    cs.nx = e.nc_h[0];
+    cs.ny = e.nc_h[1];
+    cs.nz = e.nc_h[2];
+    cs.Lx = (float)e.L_h[0];
+    cs.Ly = (float)e.L_h[1];
+    cs.Lz = (float)e.L_h[2];
+    return cs;
+}
+
 template <int KIND, bool SINGLE, bool WIDE>
 static void run_mixed(Engine& e, int kick, cudaStream_t s) {
     Geo g = make_geo(e);
-    CellSep cs{};
-    if (SINGLE) {
-        cs.lx = (float)(e.L_h[0] / e.nc_h[0]);
-        cs.ly = (float)(e.L_h[1] / e.nc_h[1]);
-        cs.lz = (float)(e.L_h[2] / e.nc_h[2]);
-        cs.nx = e.nc_h[0];
-        cs.ny = e.nc_h[1];
-        cs.nz = e.nc_h[2];
-        cs.Lx = (float)e.L_h[0];
-        cs.Ly = (float)e.L_h[1];
-        cs.Lz = (float)e.L_h[2];
-    }
+    const CellSep cs = single_cell_sep(e);
     int nb = (int)((e.N + kMNT - 1) / kMNT);
     double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
     e.launches += 2;

@@ -19,6 +19,7 @@
 // (below) settles all candidates that are not within a proven error band of
 // the list radius, so the float64 pipe is used for ~0.01 candidates per atom
 // instead of ~343.
+#include <algorithm>
 #include <cstring>
 
 #include "md_device.cuh"
@@ -36,7 +37,7 @@ __device__ __forceinline__ bool box_wants_nl(const Ctl* c, const unsigned long l
     return disp[b] > thr;
 }
 
-__global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_32a* __restrict__ x,
+__global__ void __launch_bounds__(kNlThreads) k_build_list(int n_cells, Geo g, const double4_32a* __restrict__ x,
                                                            const float4* __restrict__ xo,
                                                            const int* __restrict__ cell_start,
                                                            int* __restrict__ nn, int* __restrict__ nl, int max_nb,
@@ -49,9 +50,14 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
     __shared__ int st_lo[27], st_cnt[27], st_pre[28];
     __shared__ int n_st;
 
-    const int c = blockIdx.x;
+    // persistent blocks over the cells: a step that rebuilds no box costs
+    // one pass over the cell ids instead of one block launch per cell
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int my_max = 0;
+    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
     const int b = g.cell_box[c];
-    if (!box_wants_nl(ctl, disp, b, mode, thr)) return;
+    if (!box_wants_nl(ctl, disp, b, mode, thr)) continue;
     const int base = (int)g.atom_off[b] - cell_start[g.cell_off[b]];
     const int xyz = g.cell_xyz[c];
     const int cc[3] = {xyz & 1023, (xyz >> 10) & 1023, (xyz >> 20) & 1023};
@@ -99,9 +105,6 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
     __syncthreads();
     const int n_cand = st_pre[n_st];
     const int i_lo = base + cell_start[c], i_hi = base + cell_start[c + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    int my_max = 0;
 
     for (int ib = i_lo; ib < i_hi; ib += kNlMaxI) {
         const int ni = min(kNlMaxI, i_hi - ib);
@@ -160,6 +163,8 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
         }
         __syncthreads();
     }
+    __syncthreads();  // the next cell's stencil set-up overwrites st_*
+    }
     my_max = warp_max(my_max);
     if (lane == 0 && my_max > 0) {
         atomicMax(&ctl->max_count, my_max);
@@ -173,19 +178,17 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(Geo g, const double4_
 __global__ void k_rotate_lists(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn, int* __restrict__ nl,
                                int max_nb, int* __restrict__ n_up, const Ctl* ctl,
                                const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    if (!box_wants_nl(ctl, disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr)) return;
-    n_up[i] = rotate_list(Np, i, min(nn[i], max_nb), nl);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        if (box_wants_nl(ctl, disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr))
+            n_up[i] = rotate_list(Np, i, min(nn[i], max_nb), nl);
 }
 
 __global__ void k_build_rev(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn, const int* __restrict__ nl,
                             int max_nb, const int* __restrict__ n_up, int* __restrict__ rev, const Ctl* ctl,
                             const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    if (!box_wants_nl(ctl, disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr)) return;
-    reverse_index(Np, i, min(nn[i], max_nb), n_up[i], nn, nl, n_up, max_nb, rev);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        if (box_wants_nl(ctl, disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr))
+            reverse_index(Np, i, min(nn[i], max_nb), n_up[i], nn, nl, n_up, max_nb, rev);
 }
 
 // A full rebuild restarts the largest-count record; partial rebuilds only
@@ -206,10 +209,17 @@ void launch_build_list(Engine& e, int mode, cudaStream_t s) {
     double margin = 4e-4 * e.rl;
     float lo = (float)(rl2 - margin), hi = (float)(rl2 + margin);
     k_reset_max_count<<<1, 1, 0, s>>>(e.ctl, mode);
-    k_build_list<<<e.n_cells, kNlThreads, 0, s>>>(g, e.x, e.xo, e.cell_start, e.nn, e.nl, e.max_nb, e.N_pad, rl2, lo,
-                                                 hi, e.ctl, e.disp_box, mode, thr);
+    static int nl_per_sm = 0;
+    if (!nl_per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nl_per_sm, k_build_list, kNlThreads, 0);
+        nl_per_sm = std::max(nl_per_sm, 1);
+    }
+    const int nl_blocks = std::max(1, std::min(e.n_cells, nl_per_sm * e.n_sm));
+    k_build_list<<<nl_blocks, kNlThreads, 0, s>>>(e.n_cells, g, e.x, e.xo, e.cell_start, e.nn, e.nl, e.max_nb,
+                                                  e.N_pad, rl2, lo, hi, e.ctl, e.disp_box, mode, thr);
     if (e.rev) {
-        int nb = (int)((e.N + 255) / 256);
+        // grid-stride over the atoms, 8 blocks of 256 per multiprocessor
+        int nb = (int)std::min<int64_t>((e.N + 255) / 256, (int64_t)8 * e.n_sm);
         k_rotate_lists<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.nl, e.max_nb, e.n_up, e.ctl, e.disp_box, mode, thr);
         k_build_rev<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.nl, e.max_nb, e.n_up, e.rev, e.ctl, e.disp_box, mode,
                                        thr);
