@@ -214,7 +214,7 @@ void free_engine(Engine& e) {
     dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.ab); dfree(e.fv); dfree(e.rev); dfree(e.n_up); dfree(e.exp_T);
     dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
     dfree(e.grad_g); dfree(e.grad_u); dfree(e.grad_Fpp); dfree(e.grad_partial); dfree(e.grad_coef); dfree(e.stage); dfree(e.red);
-    dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box);
+    dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box); dfree(e.due_cells);
     for (cudaEvent_t ev : e.ev_pool) cudaEventDestroy(ev);
     e.ev_pool.clear();
     if (e.ctl_host) cudaFreeHost(e.ctl_host);
@@ -418,6 +418,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.thermo_dev, 4 * (B + 1));
     AL(e.ctl, 1);
     AL(e.disp_box, B);
+    AL(e.due_cells, tot);
 #undef AL
     if (cudaMallocHost((void**)&e.ctl_host, sizeof(Ctl)) != cudaSuccess) {
         cudaGetLastError();

@@ -77,6 +77,7 @@ struct Ctl {
     long long step;                  // completed steps since set_state
     long long n_rebuild;             // list builds since set_state
     int max_count;                   // largest neighbour count of the current list
+    int n_due;                       // cells queued for a partial list build
 };
 
 // Float32 cell geometry of a box (mixed-precision separations).
@@ -176,6 +177,7 @@ struct Engine {
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;       // pinned mirror
     unsigned long long* disp_box = nullptr;  // [B] largest squared displacement since the box's last build
+    int* due_cells = nullptr;                // [n_cells] cells of the boxes a partial build renews
 
     bool have_state = false;
     // CUDA graph of one step (and of a chunk of steps)

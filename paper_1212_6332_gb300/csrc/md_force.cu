@@ -104,13 +104,15 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
             kend = nup < 0 ? min(nn[i], max_nb) : nup;
         }
         const int kmax = warp_max(kend);
+        int e_next = kend > 0 ? nl[i] : 0;  // list rows are loaded one iteration ahead
         for (int k = 0; k < kmax; ++k) {
             bool in = false, tq = false;
             double dx = 0.0, dy = 0.0, dz = 0.0;
             long long own = 0, mir = 0;
+            const int e = e_next;
+            if (k + 1 < kend) e_next = nl[(int64_t)(k + 1) * Np + i];
             if (k < kend) {
                 own = (long long)k * Np + i;
-                const int e = nl[own];
                 const int j = entry_slot(e);
                 if (j > i) {
                     const float4 oj = xo[j];
@@ -171,23 +173,48 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
     }
 }
 
+// Both sums below skip the list entries that the pair pass zeroed (outside
+// r_cut). Each lane steps to its own next non-zero entry, so the float64
+// instructions of an iteration run with nearly all lanes active (in list-row
+// lockstep about a fifth of the lanes would idle on zero entries), and the
+// next entry's cache value is loaded one iteration ahead. Adding an exact
+// zero never changes a sum that starts at +0, so the sums are bit-identical
+// to adding every entry in list order.
+__device__ __forceinline__ bool is_zero2(double2 c) {
+    return (__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0;
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kFNT) k_rho_sum(int64_t N, int64_t Np, Pot P, const int* __restrict__ nn,
                                                   int max_nb, const double2* __restrict__ fv, double* __restrict__ rho,
                                                   double* __restrict__ Fp, double* __restrict__ e_atom,
                                                   const Ctl* ctl) {
     if (load_status(ctl)) return;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int n = min(nn[i], max_nb);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < N;
+    const int n = active ? min(nn[i], max_nb) : 0;
+    const double2 zero = make_double2(0.0, 0.0);
     // explicit round-to-nearest adds: the block-per-box schedule sums the
     // same values in the same order and must not fuse them differently
     double r_i = 0.0, ep = 0.0;
-    for (int k = 0; k < n; ++k) {
-        double2 w = fv[(int64_t)k * Np + i];
-        r_i = __dadd_rn(r_i, w.x);
-        ep = __dadd_rn(ep, w.y);
+    int k = 0;
+    double2 w = n > 0 ? fv[i] : zero;
+    while (true) {
+        while (k < n && is_zero2(w)) {
+            ++k;
+            w = k < n ? fv[(int64_t)k * Np + i] : zero;
+        }
+        const bool has = k < n;
+        if (!__any_sync(0xffffffffu, has)) break;
+        if (has) {
+            const double2 wn = k + 1 < n ? fv[(int64_t)(k + 1) * Np + i] : zero;
+            r_i = __dadd_rn(r_i, w.x);
+            ep = __dadd_rn(ep, w.y);
+            ++k;
+            w = wn;
+        }
     }
+    if (!active) return;
     double F, Fpi;
     embed<KIND>(P, r_i, F, Fpi);
     rho[i] = r_i;
@@ -202,31 +229,47 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
                                                 double* __restrict__ f, double* __restrict__ v, double c_kick,
                                                 const Ctl* ctl) {
     if (load_status(ctl)) return;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double L[3];
-    int b = SINGLE ? 0 : g.atom_box[i];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < N;
+    double L[3] = {0.0, 0.0, 0.0};
+    double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    double Fpi = 0.0;
+    int n = 0;
+    if (active) {
+        const int b = SINGLE ? 0 : g.atom_box[i];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
-    const double4_32a xi = x[i];
-    const double Fpi = Fp[i];
-    const int n = min(nn[i], max_nb);
-    double fx = 0.0, fy = 0.0, fz = 0.0;
-    for (int k = 0; k < n; ++k) {
-        const int64_t slot = (int64_t)k * Np + i;
-        double2 c = ab[slot];
-        // entries outside r_cut carry (0, 0): skip them with an integer test
-        if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
-        const int e = nl[slot];
-        const int j = entry_slot(e);
-        const double4_32a xj = x[j];
-        double dx, dy, dz;
-        sep_entry(xi, xj, entry_code(e), L, dx, dy, dz);
-        double s = fma(Fpi + Fp[j], c.y, c.x);
-        fx = fma(s, dx, fx);
-        fy = fma(s, dy, fy);
-        fz = fma(s, dz, fz);
+        for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+        xi = x[i];
+        Fpi = Fp[i];
+        n = min(nn[i], max_nb);
     }
+    const double2 zero = make_double2(0.0, 0.0);
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    int k = 0;
+    double2 c = n > 0 ? ab[i] : zero;
+    while (true) {
+        while (k < n && is_zero2(c)) {
+            ++k;
+            c = k < n ? ab[(int64_t)k * Np + i] : zero;
+        }
+        const bool has = k < n;
+        if (!__any_sync(0xffffffffu, has)) break;
+        if (has) {
+            const int64_t slot = (int64_t)k * Np + i;
+            const double2 cn = k + 1 < n ? ab[slot + Np] : zero;
+            const int e = nl[slot];
+            const int j = entry_slot(e);
+            double dx, dy, dz;
+            sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
+            const double s = fma(Fpi + Fp[j], c.y, c.x);
+            fx = fma(s, dx, fx);
+            fy = fma(s, dy, fy);
+            fz = fma(s, dz, fz);
+            ++k;
+            c = cn;
+        }
+    }
+    if (!active) return;
     f[i] = fx;
     f[Np + i] = fy;
     f[2 * Np + i] = fz;

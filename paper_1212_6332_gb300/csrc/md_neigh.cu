@@ -30,34 +30,28 @@ constexpr int kNlThreads = 128;
 constexpr int kNlCap = 1024;  // staged candidates per pass
 constexpr int kNlMaxI = 256;  // centre-cell atoms per pass
 
-__device__ __forceinline__ bool box_wants_nl(const Ctl* c, const unsigned long long* disp, int b, int mode,
-                                             unsigned long long thr) {
-    if (load_status(c)) return false;
-    if (mode) return true;
-    return disp[b] > thr;
+// Whether box b rebuilds in this call (the caller has checked the status
+// word once: an error raised by an earlier kernel skips the whole build).
+__device__ __forceinline__ bool box_due(const unsigned long long* disp, int b, int mode, unsigned long long thr) {
+    return mode || disp[b] > thr;
 }
 
-__global__ void __launch_bounds__(kNlThreads) k_build_list(int n_cells, Geo g, const double4_32a* __restrict__ x,
-                                                           const float4* __restrict__ xo,
-                                                           const int* __restrict__ cell_start,
-                                                           int* __restrict__ nn, int* __restrict__ nl, int max_nb,
-                                                           int64_t N_pad, double rl2, float rl2f_lo, float rl2f_hi,
-                                                           Ctl* ctl, const unsigned long long* __restrict__ disp,
-                                                           int mode, unsigned long long thr) {
+// Lists of the atoms of cell c (one block): the stencil's atoms are staged
+// in shared memory in ascending cell-id order and each warp sweeps them for
+// one centre atom at a time.
+__device__ __forceinline__ void build_cell_lists(int c, const Geo& g, const double4_32a* __restrict__ x,
+                                                 const float4* __restrict__ xo, const int* __restrict__ cell_start,
+                                                 int* __restrict__ nn, int* __restrict__ nl, int max_nb,
+                                                 int64_t N_pad, double rl2, float rl2f_lo, float rl2f_hi,
+                                                 int& my_max) {
     __shared__ float4 so[kNlCap];
     __shared__ int sj[kNlCap];
     __shared__ int cnt[kNlMaxI];
     __shared__ int st_lo[27], st_cnt[27], st_pre[28];
     __shared__ int n_st;
-
-    // persistent blocks over the cells: a step that rebuilds no box costs
-    // one pass over the cell ids instead of one block launch per cell
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    int my_max = 0;
-    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
     const int b = g.cell_box[c];
-    if (!box_wants_nl(ctl, disp, b, mode, thr)) continue;
     const int base = (int)g.atom_off[b] - cell_start[g.cell_off[b]];
     const int xyz = g.cell_xyz[c];
     const int cc[3] = {xyz & 1023, (xyz >> 10) & 1023, (xyz >> 20) & 1023};
@@ -164,7 +158,28 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(int n_cells, Geo g, c
         __syncthreads();
     }
     __syncthreads();  // the next cell's stencil set-up overwrites st_*
+}
+
+__global__ void __launch_bounds__(kNlThreads) k_build_list(int n_cells, Geo g, const double4_32a* __restrict__ x,
+                                                           const float4* __restrict__ xo,
+                                                           const int* __restrict__ cell_start,
+                                                           int* __restrict__ nn, int* __restrict__ nl, int max_nb,
+                                                           int64_t N_pad, double rl2, float rl2f_lo, float rl2f_hi,
+                                                           Ctl* ctl, const int* __restrict__ due, int mode) {
+    // persistent blocks: a full build walks every cell, a partial build the
+    // cells queued by k_due_cells (one block per cell at a time either way,
+    // so a few boxes that rebuild still spread over the whole GPU)
+    if (load_status(ctl)) return;
+    int my_max = 0;
+    if (mode) {
+        for (int c = blockIdx.x; c < n_cells; c += gridDim.x)
+            build_cell_lists(c, g, x, xo, cell_start, nn, nl, max_nb, N_pad, rl2, rl2f_lo, rl2f_hi, my_max);
+    } else {
+        const int n_due = ctl->n_due;
+        for (int t = blockIdx.x; t < n_due; t += gridDim.x)
+            build_cell_lists(due[t], g, x, xo, cell_start, nn, nl, max_nb, N_pad, rl2, rl2f_lo, rl2f_hi, my_max);
     }
+    const int lane = threadIdx.x & 31;
     my_max = warp_max(my_max);
     if (lane == 0 && my_max > 0) {
         atomicMax(&ctl->max_count, my_max);
@@ -178,24 +193,43 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(int n_cells, Geo g, c
 __global__ void k_rotate_lists(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn, int* __restrict__ nl,
                                int max_nb, int* __restrict__ n_up, const Ctl* ctl,
                                const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
+    if (load_status(ctl)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        if (box_wants_nl(ctl, disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr))
-            n_up[i] = rotate_list(Np, i, min(nn[i], max_nb), nl);
+        if (box_due(disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr)) n_up[i] = rotate_list(Np, i, min(nn[i], max_nb), nl);
 }
 
 __global__ void k_build_rev(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn, const int* __restrict__ nl,
                             int max_nb, const int* __restrict__ n_up, int* __restrict__ rev, const Ctl* ctl,
                             const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
+    if (load_status(ctl)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        if (box_wants_nl(ctl, disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr))
+        if (box_due(disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr))
             reverse_index(Np, i, min(nn[i], max_nb), n_up[i], nn, nl, n_up, max_nb, rev);
 }
 
 // A full rebuild restarts the largest-count record; partial rebuilds only
 // raise it, so it stays an upper bound of every current list.
 __global__ void k_reset_max_count(Ctl* ctl, int mode) {
-    if (load_status(ctl) || !mode) return;
-    ctl->max_count = 0;
+    if (load_status(ctl)) return;
+    ctl->n_due = 0;
+    if (mode) ctl->max_count = 0;
+}
+
+// Queues the cells of the boxes whose atoms moved more than half the skin
+// since their last build (one append per warp; the order of the queue does
+// not matter, every cell writes its own lists).
+__global__ void k_due_cells(int n_cells, Geo g, Ctl* ctl, const unsigned long long* __restrict__ disp,
+                            unsigned long long thr, int* __restrict__ due) {
+    if (load_status(ctl)) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool d = c < n_cells && disp[g.cell_box[c]] > thr;
+    const unsigned m = __ballot_sync(0xffffffffu, d);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&ctl->n_due, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (d) due[base + __popc(m & ((1u << lane) - 1u))] = c;
 }
 
 void launch_build_list(Engine& e, int mode, cudaStream_t s) {
@@ -214,12 +248,16 @@ void launch_build_list(Engine& e, int mode, cudaStream_t s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nl_per_sm, k_build_list, kNlThreads, 0);
         nl_per_sm = std::max(nl_per_sm, 1);
     }
+    if (!mode) {
+        k_due_cells<<<(e.n_cells + 255) / 256, 256, 0, s>>>(e.n_cells, g, e.ctl, e.disp_box, thr, e.due_cells);
+        e.launches += 1;
+    }
     const int nl_blocks = std::max(1, std::min(e.n_cells, nl_per_sm * e.n_sm));
     k_build_list<<<nl_blocks, kNlThreads, 0, s>>>(e.n_cells, g, e.x, e.xo, e.cell_start, e.nn, e.nl, e.max_nb,
-                                                  e.N_pad, rl2, lo, hi, e.ctl, e.disp_box, mode, thr);
+                                                  e.N_pad, rl2, lo, hi, e.ctl, e.due_cells, mode);
     if (e.rev) {
-        // grid-stride over the atoms, 8 blocks of 256 per multiprocessor
-        int nb = (int)std::min<int64_t>((e.N + 255) / 256, (int64_t)8 * e.n_sm);
+        // grid-stride over the atoms with four waves of resident blocks
+        int nb = (int)std::min<int64_t>((e.N + 255) / 256, (int64_t)32 * e.n_sm);
         k_rotate_lists<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.nl, e.max_nb, e.n_up, e.ctl, e.disp_box, mode, thr);
         k_build_rev<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.nl, e.max_nb, e.n_up, e.rev, e.ctl, e.disp_box, mode,
                                        thr);
