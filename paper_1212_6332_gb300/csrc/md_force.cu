@@ -285,22 +285,17 @@ void launch_forces_mixed(Engine& e, int kick, cudaStream_t s);
 // float32 screen threshold: rc^2 (1 + margin), rounded up
 static float screen_r2f(double rc2) { return nextafterf((float)(rc2 * (1.0 + kScreen)), INFINITY); }
 
-// persistent pair pass: resident blocks on every SM, at most one group per warp
+// persistent pair pass: all resident blocks of this instantiation on every
+// SM, at most one 32-atom group per warp
+template <int KIND, bool SINGLE>
 static int pair_blocks(const Engine& e) {
-    static int per_sm[3] = {0, 0, 0};  // by potential kind, both SINGLE forms share the resources
-    int& r = per_sm[e.pot.kind];
-    if (!r) {
-        int b = 0;
-        if (e.pot.kind == MD_POT_RGL)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_half<MD_POT_RGL, false>, kFNT, 0);
-        else if (e.pot.kind == MD_POT_SC)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_half<MD_POT_SC, false>, kFNT, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_half<MD_POT_SPLINE, false>, kFNT, 0);
-        r = b > 0 ? b : 1;
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_half<KIND, SINGLE>, kFNT, 0);
+        per_sm = std::max(per_sm, 1);
     }
     const int64_t groups = (e.N + 31) / 32, per_block = kFNT / 32;
-    return (int)std::max<int64_t>(1, std::min<int64_t>((groups + per_block - 1) / per_block, (int64_t)r * e.n_sm));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((groups + per_block - 1) / per_block, (int64_t)per_sm * e.n_sm));
 }
 
 template <int KIND, bool SINGLE>
@@ -311,7 +306,7 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s) {
     e.launches += 3;
     {
         PhaseScope scope(e, MD_PHASE_PAIRS, s);
-        k_pairs_half<KIND, SINGLE><<<pair_blocks(e), kFNT, 0, s>>>(e.N, e.N_pad, g, single_cell_sep(e), e.pot,
+        k_pairs_half<KIND, SINGLE><<<pair_blocks<KIND, SINGLE>(e), kFNT, 0, s>>>(e.N, e.N_pad, g, single_cell_sep(e), e.pot,
                                                                    screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.x,
                                                                    e.xo, e.nn, e.nl, e.rev, e.n_up, e.max_nb, e.ab,
                                                                    e.fv, e.ctl);
