@@ -243,6 +243,28 @@ def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=N
                 phase_ms_per_step={k: v / max(K, 1) for k, v in prof["ms"].items()})
 
 
+def run_small(K: int, use_graph: bool) -> dict:
+    """The 2048-atom Cu box (8^3 cells, RGL Cu, 300 K, seed 12345), K
+    velocity-Verlet steps in one call: launch-bound, the working set sits in
+    L2 (a latency figure, not an HBM one)."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bx = I.perturbed_fcc(8, I.A_CU, 300.0, I.MASS_CU, 12345)
+    s = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=SKIN, dt=DT, mass=I.MASS_CU)
+    s.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+    s.step(K, use_graph=use_graph)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    th = s.step(K, use_graph=use_graph)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    s.close()
+    return dict(value=bx.n * K / (ms * 1e-3), ms_per_step=ms / K, steps=K, n_rebuild=th["n_rebuild"],
+                graph=use_graph, l2="working set inside L2")
+
+
 def run_batch(precision: str, K: int, W: int, n_boxes: int = 4096, use_graph: bool = True,
               schedule: str = "tile") -> dict:
     """The 4096-box batch (n ~ U{3..10} fcc Cu repeats, T ~ U(300, 1500) K,
@@ -474,6 +496,12 @@ def main():
         variants["sc_fp64"] = run_variant("fp64", W, max(5, K // 3), bx.x, bx.v, bx.box, spec=I.SC_CU)
         variants["sc_mixed"] = run_variant("mixed", W, K, bx.x, bx.v, bx.box, spec=I.SC_CU)
         del hot
+        ni = I.perturbed_fcc(80, I.A_NI, 600.0, I.MASS_NI, 3)
+        variants["ni_2m_fp64"] = run_variant("fp64", W, K, ni.x, ni.v, ni.box, spec=I.RGL_NI, mass=I.MASS_NI)
+        variants["ni_2m_mixed"] = run_variant("mixed", W, K, ni.x, ni.v, ni.box, spec=I.RGL_NI, mass=I.MASS_NI)
+        del ni
+        variants["cu_2048_graph"] = run_small(200, True)
+        variants["cu_2048_nograph"] = run_small(200, False)
         del x_dev, v_dev
         torch.cuda.empty_cache()
         kb = max(5, min(K, 20))

@@ -588,7 +588,9 @@ int settle_overflow(Engine* E, cudaStream_t s, bool* had) {
                             std::to_string(E->max_nb));
         if ((rc = grow_list(E, E->ctl_host->overflow_count)) != MD_OK) return rc;
         if ((rc = clear_status(E, s)) != MD_OK) return rc;
-        launch_build_list(*E, 1, s);
+        // a full rebuild (binning too), so the lists and the build
+        // positions agree again whatever stage the failed build reached
+        launch_rebuild(*E, 1, s);
         CK(cudaGetLastError());
     }
 }
@@ -601,6 +603,21 @@ int rebuild_and_forces(Engine* E, cudaStream_t s) {
     if (rc) return rc;
     launch_forces(*E, 0, s);
     launch_thermo(*E, s);
+    CK(cudaGetLastError());
+    return MD_OK;
+}
+
+// Forces after a load that kept the lists: boxes whose atoms moved more
+// than half the skin from their build positions are rebuilt.
+int refresh_and_forces(Engine* E, cudaStream_t s) {
+    launch_rebuild(*E, 0, s);
+    CK(cudaGetLastError());
+    bool had;
+    int rc = settle_overflow(E, s, &had);
+    if (rc) return rc;
+    launch_forces(*E, 0, s);
+    launch_thermo(*E, s);
+    launch_after_load(*E, s);
     CK(cudaGetLastError());
     return MD_OK;
 }
@@ -620,10 +637,18 @@ int set_positions(Engine* E, const double* x, const double* v, bool set_v, cudaS
         return MD_OK;
     }
     const double* xd = nullptr;
+    // lists built for earlier positions stay usable for new ones within
+    // half the skin of the build positions (the rule the steps follow): a
+    // load then rebuilds only the boxes that moved farther
+    const bool keep = e.have_state && e.lists_ok;
+    e.lists_ok = false;
     launch_reset_ctl(e, s);
     int rc = stage_in(E, x, 3 * (size_t)e.N, s, &xd);
     if (rc) return rc;
-    launch_load_positions(e, xd, s);
+    if (keep)
+        launch_load_positions_keep(e, xd, s);
+    else
+        launch_load_positions(e, xd, s);
     if (set_v) {
         const double* vd = nullptr;
         if (v && (rc = stage_in(E, v, 3 * (size_t)e.N, s, &vd))) return rc;
@@ -633,9 +658,11 @@ int set_positions(Engine* E, const double* x, const double* v, bool set_v, cudaS
     // non-finite inputs: report before any list is built from them
     if ((rc = read_ctl(E, s))) return rc;
     if (E->ctl_host->status & kStNonFinite) return fail(E, MD_ERR_NONFINITE, "non-finite position or velocity");
-    if ((rc = rebuild_and_forces(E, s))) return rc;
+    if ((rc = keep ? refresh_and_forces(E, s) : rebuild_and_forces(E, s))) return rc;
     e.have_state = true;
-    return finish_sync(E, s);
+    if ((rc = finish_sync(E, s))) return rc;
+    e.lists_ok = true;
+    return MD_OK;
 }
 
 // ---- stepping ----
@@ -968,7 +995,10 @@ int md_step(md_ctx* h, int n_steps, md_thermo* out, double* thermo_hist, int use
     if (!h) return MD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)st;
     int rc = steps_impl(h, n_steps, thermo_hist, use_graph != 0, s);
-    if (rc) return rc;
+    if (rc) {
+        h->e.lists_ok = false;  // the next state load rebuilds everything
+        return rc;
+    }
     if (out) return thermo_impl(h, out, nullptr, s);
     return MD_OK;
 }
@@ -1005,12 +1035,18 @@ int md_batch_step(md_batch* b, int n_steps, int schedule, int use_graph, double*
             CK(cudaEventCreate(&a));
             CK(cudaEventCreate(&c));
             CK(cudaEventRecord(a, s));
-            if ((rc = steps_impl(b, 4, nullptr, use_graph != 0, s))) return rc;
+            if ((rc = steps_impl(b, 4, nullptr, use_graph != 0, s))) {
+                E->lists_ok = false;
+                return rc;
+            }
             CK(cudaEventRecord(c, s));
             CK(cudaEventSynchronize(c));
             CK(cudaEventElapsedTime(&t_tile, a, c));
             CK(cudaEventRecord(a, s));
-            if ((rc = box_steps(b, 4, s))) return rc;
+            if ((rc = box_steps(b, 4, s))) {
+                E->lists_ok = false;
+                return rc;
+            }
             CK(cudaEventRecord(c, s));
             CK(cudaEventSynchronize(c));
             CK(cudaEventElapsedTime(&t_box, a, c));
@@ -1023,10 +1059,10 @@ int md_batch_step(md_batch* b, int n_steps, int schedule, int use_graph, double*
         }
     }
     bool box = schedule == MD_SCHED_BOX || (schedule == MD_SCHED_AUTO && E->sched_choice == MD_SCHED_BOX);
-    if (box) {
-        if ((rc = box_steps(b, remaining, s))) return rc;
-    } else {
-        if ((rc = steps_impl(b, remaining, nullptr, use_graph != 0, s))) return rc;
+    rc = box ? box_steps(b, remaining, s) : steps_impl(b, remaining, nullptr, use_graph != 0, s);
+    if (rc) {
+        E->lists_ok = false;  // the next state load rebuilds everything
+        return rc;
     }
     if (thermo_box) return thermo_impl(b, nullptr, thermo_box, s);
     return MD_OK;

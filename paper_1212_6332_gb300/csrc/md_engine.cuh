@@ -180,6 +180,7 @@ struct Engine {
     int* due_cells = nullptr;                // [n_cells] cells of the boxes a partial build renews
 
     bool have_state = false;
+    bool lists_ok = false;  // lists, cells and build positions agree (a state load may keep them)
     // CUDA graph of one step (and of a chunk of steps)
     cudaGraphExec_t graph_step = nullptr;
     cudaGraphExec_t graph_chunk = nullptr;
@@ -252,6 +253,8 @@ void launch_prepare_mixed(Engine& e, cudaStream_t s);
 void launch_spline_setup(Engine& e, cudaStream_t s);
 // caller-order <-> sorted-order copies
 void launch_load_positions(Engine& e, const double* src_caller, cudaStream_t s);
+void launch_load_positions_keep(Engine& e, const double* src_caller, cudaStream_t s);
+void launch_after_load(Engine& e, cudaStream_t s);
 void launch_load_velocities(Engine& e, const double* src_caller, cudaStream_t s);
 void launch_store_vec(Engine& e, const double* soa_or_null, const double4_32a* x4_or_null, double* dst_caller,
                       cudaStream_t s);

@@ -68,6 +68,33 @@ __device__ __forceinline__ void eval_queued(const Pot& P, const PairQueue& q, in
     fv[mir] = w;
 }
 
+// One list row of a lane: the entry and, for an upper entry (j > i), the
+// partner's offset and position and the row of the mirror entry.
+struct PairRow {
+    float4 oj;
+    double4_32a xj;
+    int e, rv;
+    bool upper;
+};
+
+__device__ __forceinline__ PairRow load_pair_row(int e, bool valid, int64_t i, const float4* __restrict__ xo,
+                                                 const double4_32a* __restrict__ x, const int* __restrict__ rev,
+                                                 int64_t Np, int k) {
+    PairRow r;
+    r.e = e;
+    r.upper = valid && entry_slot(e) > i;
+    r.oj = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.xj = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    r.rv = 0;
+    if (r.upper) {
+        const int j = entry_slot(e);
+        r.oj = xo[j];
+        r.xj = x[j];
+        r.rv = rev[(int64_t)k * Np + i];
+    }
+    return r;
+}
+
 template <int KIND, bool SINGLE>
 __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P, float rc2f,
                                                      float rs2f, const double4_32a* __restrict__ x,
@@ -104,36 +131,35 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
             kend = nup < 0 ? min(nn[i], max_nb) : nup;
         }
         const int kmax = warp_max(kend);
-        int e_next = kend > 0 ? nl[i] : 0;  // list rows are loaded one iteration ahead
+        // software pipeline: the list entry two rows ahead and the partner
+        // data (offset, position, mirror row) one row ahead are in flight
+        // while a row is screened, so the loop does not wait on L2 / HBM
+        PairRow cur = load_pair_row(0 < kend ? nl[i] : 0, 0 < kend, i, xo, x, rev, Np, 0);
+        int e_ahead = 1 < kend ? nl[Np + i] : 0;
         for (int k = 0; k < kmax; ++k) {
+            const PairRow nxt = load_pair_row(e_ahead, k + 1 < kend, i, xo, x, rev, Np, k + 1);
+            e_ahead = k + 2 < kend ? nl[(int64_t)(k + 2) * Np + i] : 0;
             bool in = false, tq = false;
             double dx = 0.0, dy = 0.0, dz = 0.0;
-            long long own = 0, mir = 0;
-            const int e = e_next;
-            if (k + 1 < kend) e_next = nl[(int64_t)(k + 1) * Np + i];
-            if (k < kend) {
-                own = (long long)k * Np + i;
-                const int j = entry_slot(e);
-                if (j > i) {
-                    const float4 oj = xo[j];
-                    const double4_32a xj = x[j];
-                    mir = (long long)rev[own] * Np + j;
-                    float fx, fy, fz;
-                    sep_mixed<false>(cs, oi, oj, fx, fy, fz);
-                    const float r2f = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
-                    if (r2f < rc2f) {
-                        in = true;
-                        tq = r2f > rs2f;
-                        sep_entry(xi, xj, entry_code(e), L, dx, dy, dz);
-                    } else {
-                        const double2 z = make_double2(0.0, 0.0);
-                        ab[own] = z;
-                        fv[own] = z;
-                        ab[mir] = z;
-                        fv[mir] = z;
-                    }
+            const long long own = (long long)k * Np + i;
+            const long long mir = (long long)cur.rv * Np + entry_slot(cur.e);
+            if (cur.upper) {
+                float fx, fy, fz;
+                sep_mixed<false>(cs, oi, cur.oj, fx, fy, fz);
+                const float r2f = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
+                if (r2f < rc2f) {
+                    in = true;
+                    tq = r2f > rs2f;
+                    sep_entry(xi, cur.xj, entry_code(cur.e), L, dx, dy, dz);
+                } else {
+                    const double2 z = make_double2(0.0, 0.0);
+                    ab[own] = z;
+                    fv[own] = z;
+                    ab[mir] = z;
+                    fv[mir] = z;
                 }
             }
+            cur = nxt;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const bool mine = in && (tq == (r == 1));

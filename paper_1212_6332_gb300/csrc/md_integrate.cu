@@ -10,11 +10,42 @@
 //                  energy per box, totals, temperature, non-finite check
 // The paper integrates with a predictor-corrector (Sec. 3.3); velocity
 // Verlet replaces it here.
+#include <algorithm>
+
 #include "md_device.cuh"
 
 namespace mdk {
 
 constexpr int kINT = 256;
+
+// Largest squared displacement per box into disp[] (non-negative doubles
+// order like their bit patterns): one atomic per block when the block's
+// atoms lie in one box, per lane where a box boundary falls inside it.
+// b < 0 marks a thread without an atom. Every thread of the block calls it.
+template <bool SINGLE>
+__device__ __forceinline__ void record_disp(const Geo& g, int64_t N, int b, double d2,
+                                            unsigned long long* __restrict__ disp) {
+    __shared__ double sm[kINT / 32];
+    __shared__ int s_b0, s_b1;
+    if (threadIdx.x == 0) {
+        int64_t f = (int64_t)blockIdx.x * blockDim.x, l = min(f + blockDim.x, N) - 1;
+        s_b0 = SINGLE ? 0 : g.atom_box[f];
+        s_b1 = SINGLE ? 0 : g.atom_box[l];
+    }
+    __syncthreads();
+    if (s_b0 == s_b1) {
+        d2 = warp_max(d2);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int k = 0; k < kINT / 32; ++k) m = sm[k] > m ? sm[k] : m;
+            if (m > 0.0) atomicMax(&disp[s_b0], (unsigned long long)__double_as_longlong(m));
+        }
+    } else if (b >= 0 && d2 > 0.0) {
+        atomicMax(&disp[b], (unsigned long long)__double_as_longlong(d2));
+    }
+}
 
 template <bool SINGLE>
 __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo g, double4_32a* __restrict__ x,
@@ -54,29 +85,7 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
         xo[i] = make_float4((float)(p.x - org.x), (float)(p.y - org.y), (float)(p.z - org.z),
                             __int_as_float((int)__double_as_longlong(org.w)));
     }
-    // largest d2 per box (non-negative doubles order like their bit
-    // patterns): one atomic per block when the block lies in one box, per
-    // warp or per lane where a box boundary falls inside it
-    __shared__ double sm[kINT / 32];
-    __shared__ int s_b0, s_b1;
-    if (threadIdx.x == 0) {
-        int64_t f = (int64_t)blockIdx.x * blockDim.x, l = min(f + blockDim.x, N) - 1;
-        s_b0 = SINGLE ? 0 : g.atom_box[f];
-        s_b1 = SINGLE ? 0 : g.atom_box[l];
-    }
-    __syncthreads();
-    if (s_b0 == s_b1) {
-        d2 = warp_max(d2);
-        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double m = 0.0;
-            for (int k = 0; k < kINT / 32; ++k) m = sm[k] > m ? sm[k] : m;
-            if (m > 0.0) atomicMax(&disp[s_b0], (unsigned long long)__double_as_longlong(m));
-        }
-    } else if (b >= 0 && d2 > 0.0) {
-        atomicMax(&disp[b], (unsigned long long)__double_as_longlong(d2));
-    }
+    record_disp<SINGLE>(g, N, b, d2, disp);
 }
 
 // Closes a step: records the largest displacement over boxes, clears the
@@ -246,6 +255,55 @@ __global__ void k_load_pos(int64_t N, const double* __restrict__ src, const int*
     x[t] = p;
 }
 
+// Positions for a handle whose lists stay usable: each caller position is
+// wrapped and, where the atom crossed a face since the last build, moved to
+// the image next to its build position (positions stay continuous between
+// builds, as the image codes of the list entries require); otherwise the
+// caller's value is kept as is. The displacement from the build position
+// feeds the per-box rebuild decision, and the float32 offsets are refreshed.
+template <bool SINGLE>
+__global__ void __launch_bounds__(kINT) k_load_pos_keep(int64_t N, const double* __restrict__ src,
+                                                        const int* __restrict__ iperm, Geo g,
+                                                        double4_32a* __restrict__ x,
+                                                        const double4_32a* __restrict__ xb, float4* __restrict__ xo,
+                                                        const int* __restrict__ cell_t, Ctl* ctl,
+                                                        unsigned long long* __restrict__ disp) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double d2 = 0.0;
+    int b = -1;
+    if (c < N) {
+        if (!isfinite(src[3 * c]) || !isfinite(src[3 * c + 1]) || !isfinite(src[3 * c + 2]))
+            atomicOr(&ctl->status, kStNonFinite);
+        b = SINGLE ? 0 : g.atom_box[c];
+        const int t = iperm[c];
+        const double4_32a q = xb[t];
+        const double qa[3] = {q.x, q.y, q.z};
+        double pa[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double L = g.L[3 * b + a];
+            const double w = wrap_coord(src[3 * c + a], L);
+            const double d = w - qa[a];
+            pa[a] = d > 0.5 * L ? w - L : (d < -0.5 * L ? w + L : w);
+            const double e = pa[a] - qa[a];
+            d2 = fma(e, e, d2);
+        }
+        x[t] = make_double4_32a(pa[0], pa[1], pa[2], 0.0);
+        const double4_32a org = g.cell_org[cell_t[t]];
+        xo[t] = make_float4((float)(pa[0] - org.x), (float)(pa[1] - org.y), (float)(pa[2] - org.z),
+                            __int_as_float((int)__double_as_longlong(org.w)));
+    }
+    record_disp<SINGLE>(g, N, b, d2, disp);
+}
+
+// After a state load that kept the lists: the displacement record restarts
+// (each step recomputes it from the build positions) and the load's own
+// list builds are not counted as builds of the dynamics.
+__global__ void k_after_load(Ctl* ctl, int B, unsigned long long* __restrict__ disp) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) disp[b] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_rebuild = 0;
+}
+
 __global__ void k_load_vel(int64_t N, int64_t Np, const double* __restrict__ src, const int* __restrict__ iperm,
                            double* __restrict__ v, Ctl* ctl) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -314,6 +372,22 @@ void launch_load_positions(Engine& e, const double* src, cudaStream_t s) {
     if (e.N == 0) return;
     e.launches += 1;
     k_load_pos<<<nblk(e.N, 256), 256, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x, e.ctl);
+}
+
+void launch_load_positions_keep(Engine& e, const double* src, cudaStream_t s) {
+    if (e.N == 0) return;
+    e.launches += 1;
+    if (e.B == 1)
+        k_load_pos_keep<true><<<nblk(e.N, kINT), kINT, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x, e.xb, e.xo,
+                                                             e.cell_t, e.ctl, e.disp_box);
+    else
+        k_load_pos_keep<false><<<nblk(e.N, kINT), kINT, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x, e.xb, e.xo,
+                                                              e.cell_t, e.ctl, e.disp_box);
+}
+
+void launch_after_load(Engine& e, cudaStream_t s) {
+    e.launches += 1;
+    k_after_load<<<std::max(1, std::min((e.B + 255) / 256, 64)), 256, 0, s>>>(e.ctl, e.B, e.disp_box);
 }
 
 void launch_load_velocities(Engine& e, const double* src, cudaStream_t s) {

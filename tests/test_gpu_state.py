@@ -1,0 +1,96 @@
+"""State loads that keep the neighbour lists.
+
+A handle that already has lists keeps them when new positions stay within
+half the skin of the positions the lists were built from (the rule the
+steps follow); boxes that moved farther are rebuilt. Positions that crossed
+a periodic face since the build are taken as the image next to the build
+position. Every case is checked against the oracle on the same positions."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1212_6332_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-10
+
+
+def check(got, ref):
+    err = np.linalg.norm(got["f"] - ref["f"], axis=1).max() / np.linalg.norm(ref["f"], axis=1).max()
+    assert err <= F_TOL, err
+    assert abs(got["E"] - ref["E"]) <= 1e-10 * abs(ref["E"])
+
+
+def forces_of(s, x):
+    out = s.compute_forces(x)
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["E"] = float(res.pop("energy")[0])
+    return res
+
+
+def test_small_moves_keep_lists_and_match_oracle():
+    from paper_1212_6332_gb300.md import System
+    bx = I.perturbed_fcc(6, I.A_CU, 300.0, I.MASS_CU, seed=31)
+    s = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    pot = O.Potential(I.RGL_CU)
+    check(forces_of(s, bx.x.copy()), O.forces(pot, bx.x, bx.box, skin=0.3))
+    rng = np.random.default_rng(5)
+    # moves below skin/2 = 0.15 A (|d| <= 0.13 A): no box rebuilds, and the
+    # atoms near a face that are pushed across it come back wrapped
+    x = bx.x + rng.uniform(-0.05, 0.05, bx.x.shape)
+    near = np.where(bx.x[:, 0] < 0.03)[0][:5]
+    assert len(near) > 0
+    x[near, 0] -= 0.06
+    x = I.wrap(x, bx.box)
+    check(forces_of(s, x.copy()), O.forces(pot, x, bx.box, skin=0.3))
+    # a large move rebuilds the lists and is still exact
+    x2 = I.wrap(x + rng.uniform(-0.4, 0.4, x.shape), bx.box)
+    check(forces_of(s, x2.copy()), O.forces(pot, x2, bx.box, skin=0.3))
+
+
+def test_batch_rebuilds_only_the_boxes_that_moved():
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bt = I.batch_of_boxes(6, I.A_CU, I.MASS_CU, seed=17)
+    s = System(I.RGL_CU, boxes=bt.box, atom_offsets=bt.atom_offsets, skin=0.3, mass=I.MASS_CU)
+    s.set_state(torch.tensor(bt.x, device="cuda"), torch.tensor(bt.v, device="cuda"))
+    rng = np.random.default_rng(8)
+    x = bt.x.copy()
+    for k in range(6):
+        lo, hi = bt.atom_offsets[k], bt.atom_offsets[k + 1]
+        amp = 0.5 if k == 2 else 0.05
+        x[lo:hi] = I.wrap(x[lo:hi] + rng.uniform(-amp, amp, (hi - lo, 3)), bt.box[k])
+    f, e_box = s.batch_compute_forces(torch.tensor(x, device="cuda"))
+    f, e_box = f.cpu().numpy(), e_box.cpu().numpy()
+    pot = O.Potential(I.RGL_CU)
+    for k in range(6):
+        lo, hi = bt.atom_offsets[k], bt.atom_offsets[k + 1]
+        ref = O.forces(pot, x[lo:hi], bt.box[k], skin=0.3)
+        fb = f[lo:hi]
+        assert np.linalg.norm(fb - ref["f"], axis=1).max() <= F_TOL * np.linalg.norm(ref["f"], axis=1).max()
+        assert e_box[k] == pytest.approx(ref["E"], rel=1e-10)
+
+
+def test_reloading_the_own_state_continues_the_trajectory():
+    """Loading a handle's own state back (the end-to-end pattern: download,
+    upload, step) keeps its lists and follows the same trajectory as a
+    fresh handle loaded with that state."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bx = I.perturbed_fcc(5, I.A_CU, 900.0, I.MASS_CU, seed=8)
+    a = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    a.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+    a.step(40)
+    xa, va = (t.cpu().numpy().copy() for t in a.get_state())
+    b = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    b.set_state(xa.copy(), va.copy())
+    a.set_state(xa.copy(), va.copy())
+    assert a.thermo()["n_rebuild"] == 0
+    a.step(40)
+    b.step(40)
+    (x1, v1), (x2, v2) = a.get_state(), b.get_state()
+    d = (x1 - x2).cpu().numpy()
+    d -= bx.box * np.round(d / bx.box)
+    assert np.abs(d).max() < 1e-11
+    assert torch.allclose(v1, v2, rtol=0, atol=1e-12)
