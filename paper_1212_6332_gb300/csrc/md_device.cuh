@@ -151,6 +151,24 @@ __device__ __forceinline__ int cell_delta(int cj, int ci, int n) {
 // inside the band (~0.01 per atom) take the exact float64 test, which alone
 // decides membership, so the list equals the oracle's bit for bit.
 
+// The float64 list test, the definition both the oracle and the GPU lists
+// follow: d = x_j - x_i with one minimum-image shift per axis, r^2 rounded
+// after every operation (no fused multiply-add), accepted when r^2 < rl^2;
+// (sx, sy, sz) is the shift in box lengths.
+__device__ __forceinline__ bool exact_candidate(const double4_32a& xi, const double4_32a& xj, double Lx, double Ly,
+                                                double Lz, double rl2, int& sx, int& sy, int& sz) {
+    const double hx = 0.5 * Lx, hy = 0.5 * Ly, hz = 0.5 * Lz;
+    double ex = __dsub_rn(xj.x, xi.x), ey = __dsub_rn(xj.y, xi.y), ez = __dsub_rn(xj.z, xi.z);
+    sx = ex > hx ? -1 : (ex < -hx ? 1 : 0);
+    sy = ey > hy ? -1 : (ey < -hy ? 1 : 0);
+    sz = ez > hz ? -1 : (ez < -hz ? 1 : 0);
+    ex = minimg(ex, Lx, hx);
+    ey = minimg(ey, Ly, hy);
+    ez = minimg(ez, Lz, hz);
+    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+    return r2 < rl2;
+}
+
 __device__ __forceinline__ bool list_candidate(const float4& oi, const float4& oj, const double4_32a& xi,
                                                const double4_32a* __restrict__ xall, int j, int cix, int ciy, int ciz,
                                                int ncx, int ncy, int ncz, float lfx, float lfy, float lfz, float Lfx,
@@ -181,17 +199,7 @@ __device__ __forceinline__ bool list_candidate(const float4& oi, const float4& o
         fabsf(dx) > 0.5f * Lfx - 1e-3f || fabsf(dy) > 0.5f * Lfy - 1e-3f || fabsf(dz) > 0.5f * Lfz - 1e-3f;
     if (r2f < rl2f_lo && !near_half) return true;
     if (r2f > rl2f_hi && !near_half) return false;
-    const double4_32a xj = xall[j];
-    const double hx = 0.5 * Lx, hy = 0.5 * Ly, hz = 0.5 * Lz;
-    double ex = __dsub_rn(xj.x, xi.x), ey = __dsub_rn(xj.y, xi.y), ez = __dsub_rn(xj.z, xi.z);
-    sx = ex > hx ? -1 : (ex < -hx ? 1 : 0);
-    sy = ey > hy ? -1 : (ey < -hy ? 1 : 0);
-    sz = ez > hz ? -1 : (ez < -hz ? 1 : 0);
-    ex = minimg(ex, Lx, hx);
-    ey = minimg(ey, Ly, hy);
-    ez = minimg(ez, Lz, hz);
-    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-    return r2 < rl2;
+    return exact_candidate(xi, xall[j], Lx, Ly, Lz, rl2, sx, sy, sz);
 }
 
 // Each list leaves the build ascending by neighbour slot. It is rotated to

@@ -47,7 +47,8 @@ __device__ __forceinline__ void build_cell_lists(int c, const Geo& g, const doub
     __shared__ float4 so[kNlCap];
     __shared__ int sj[kNlCap];
     __shared__ int cnt[kNlMaxI];
-    __shared__ int st_lo[27], st_cnt[27], st_pre[28];
+    __shared__ int st_lo[27], st_cnt[27], st_pre[28], st_code[27];
+    __shared__ float st_off[27][3];
     __shared__ int n_st;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -59,6 +60,7 @@ __device__ __forceinline__ void build_cell_lists(int c, const Geo& g, const doub
     const double Lx = g.L[3 * b], Ly = g.L[3 * b + 1], Lz = g.L[3 * b + 2];
     const float lfx = g.cell_len_f[3 * b], lfy = g.cell_len_f[3 * b + 1], lfz = g.cell_len_f[3 * b + 2];
     const float Lfx = (float)Lx, Lfy = (float)Ly, Lfz = (float)Lz;
+    const bool wide = ncx >= 3 && ncy >= 3 && ncz >= 3;
 
     if (threadIdx.x < 32) {
         // one lane per stencil cell (loads in parallel), then the cells in
@@ -68,20 +70,32 @@ __device__ __forceinline__ void build_cell_lists(int c, const Geo& g, const doub
         const int lane = threadIdx.x;
         const int nx = ncx >= 3 ? 3 : ncx, ny = ncy >= 3 ? 3 : ncy, nz = ncz >= 3 ? 3 : ncz;
         const int total = nx * ny * nz;
-        int q = 0x7fffffff, lo = 0, cnt = 0;
+        int q = 0x7fffffff, lo = 0, cnt = 0, ox = 0, oy = 0, oz = 0, code = 0;
         if (lane < total) {
             int ix = lane / (ny * nz), iy = (lane / nz) % ny, iz = lane % nz;
-            int ox = ncx >= 3 ? ix - 1 : ix, oy = ncy >= 3 ? iy - 1 : iy, oz = ncz >= 3 ? iz - 1 : iz;
+            ox = ncx >= 3 ? ix - 1 : ix;
+            oy = ncy >= 3 ? iy - 1 : iy;
+            oz = ncz >= 3 ? iz - 1 : iz;
             int qx = (cc[0] + ox + ncx) % ncx, qy = (cc[1] + oy + ncy) % ncy, qz = (cc[2] + oz + ncz) % ncz;
             q = g.cell_rank[g.cell_off[b] + (qx * ncy + qy) * ncz + qz];
             lo = base + cell_start[q];
             cnt = base + cell_start[q + 1] - lo;
+            // with 3 or more cells per axis the stencil cell's offset is the
+            // minimum image, and the periodic shift is that of the wrap
+            const int sx = cc[0] + ox < 0 ? -1 : (cc[0] + ox >= ncx ? 1 : 0);
+            const int sy = cc[1] + oy < 0 ? -1 : (cc[1] + oy >= ncy ? 1 : 0);
+            const int sz = cc[2] + oz < 0 ? -1 : (cc[2] + oz >= ncz ? 1 : 0);
+            code = make_entry(0, sx, sy, sz);
         }
         int rank = 0;
         for (int k = 0; k < total; ++k) rank += __shfl_sync(0xffffffffu, q, k) < q;
         if (lane < total) {
             st_lo[rank] = lo;
             st_cnt[rank] = cnt;
+            st_code[rank] = code;
+            st_off[rank][0] = (float)ox * lfx;
+            st_off[rank][1] = (float)oy * lfy;
+            st_off[rank][2] = (float)oz * lfz;
         }
         __syncwarp();
         int c = lane < total ? st_cnt[lane] : 0;
@@ -118,7 +132,15 @@ __device__ __forceinline__ void build_cell_lists(int c, const Geo& g, const doub
                         hk = mid;
                 }
                 int j = st_lo[k] + (q - st_pre[k]);
-                so[t] = xo[j];
+                float4 o = xo[j];
+                if (wide) {
+                    // offset from the centre cell's origin, entry with its image
+                    o.x += st_off[k][0];
+                    o.y += st_off[k][1];
+                    o.z += st_off[k][2];
+                    j |= st_code[k];
+                }
+                so[t] = o;
                 sj[t] = j;
             }
             __syncthreads();
@@ -132,17 +154,34 @@ __device__ __forceinline__ void build_cell_lists(int c, const Geo& g, const doub
                 for (int jb = 0; jb < nc_; jb += 32) {
                     int jj = jb + lane;
                     bool ok = false;
-                    int j = -1, sx = 0, sy = 0, sz = 0;
+                    int entry = 0;
                     if (jj < nc_) {
-                        j = sj[jj];
-                        ok = list_candidate(oi, so[jj], xi, x, j, cix, ciy, ciz, ncx, ncy, ncz, lfx, lfy, lfz, Lfx,
-                                            Lfy, Lfz, Lx, Ly, Lz, rl2, rl2f_lo, rl2f_hi, sx, sy, sz) &&
-                             (j != i);
+                        if (wide) {
+                            entry = sj[jj];
+                            const int j = entry_slot(entry);
+                            const float4 oj = so[jj];
+                            const float dx = oj.x - oi.x, dy = oj.y - oi.y, dz = oj.z - oi.z;
+                            const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            if (r2f < rl2f_lo) {
+                                ok = j != i;
+                            } else if (!(r2f > rl2f_hi)) {
+                                int sx, sy, sz;
+                                ok = exact_candidate(xi, x[j], Lx, Ly, Lz, rl2, sx, sy, sz) && j != i;
+                                entry = make_entry(j, sx, sy, sz);
+                            }
+                        } else {
+                            const int j = sj[jj];
+                            int sx = 0, sy = 0, sz = 0;
+                            ok = list_candidate(oi, so[jj], xi, x, j, cix, ciy, ciz, ncx, ncy, ncz, lfx, lfy, lfz,
+                                                Lfx, Lfy, Lfz, Lx, Ly, Lz, rl2, rl2f_lo, rl2f_hi, sx, sy, sz) &&
+                                 (j != i);
+                            entry = make_entry(j, sx, sy, sz);
+                        }
                     }
                     unsigned m = __ballot_sync(0xffffffffu, ok);
                     if (ok) {
                         int pos = n + __popc(m & lt_mask);
-                        if (pos < max_nb) nl[(int64_t)pos * N_pad + i] = make_entry(j, sx, sy, sz);
+                        if (pos < max_nb) nl[(int64_t)pos * N_pad + i] = entry;
                     }
                     n += __popc(m);
                 }
