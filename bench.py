@@ -62,8 +62,15 @@ KERNELS = {
               # list 4K, (A,B) reads 16K, count 4, x_i 32, F'_i 8, F 24, v 48
               lambda K, Ki: 20.0 * K + 116.0),
 }
-# Nominal GB300 float64 rate (no measured float64 peak is provided).
-FP64_PEAK_TFLOPS = 1.25
+# GB300 float64 peak from unit counts and clock (no measured float64 peak
+# is provided): 152 SMs x 2 float64 FMA per clock x 2 flop x 2.07 GHz
+# (an FMA-chain probe measured 1.20 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per atom of one k_pairs_half launch, from the ncu
+# capture summarised in profiles/k_pairs_half_rgl_cu_1m_fp64.md (1,048,576
+# atoms of the same lattice, potential and temperature: 1.754 GB read +
+# 2.717 GB written); traffic grows in proportion to the atom count.
+PAIRS_DRAM_BYTES_PER_ATOM = (1.754257e9 + 2.717350e9) / 1048576
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
            0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
@@ -453,8 +460,10 @@ def main():
     hbm = peaks.get("hbm_gbs", 6800.0)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal float64 rate (no measured float64 peak on this pool)",
-                "traffic": None, "flops_per_launch": flops, "launch_ms": k_ms,
+                "peak_source": "derived: 152 SM x 2 float64 FMA/clock x 2 flop x 2.07 GHz",
+                "traffic": (PAIRS_DRAM_BYTES_PER_ATOM * N if dom == "pairs" and args.precision == "fp64" else None),
+                "traffic_source": "ncu capture of 1,048,576 atoms scaled by the atom count",
+                "flops_per_launch": flops, "launch_ms": k_ms,
                 "hbm": {"achieved": bytes_k / (k_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                         "frac": bytes_k / (k_ms * 1e-3) / 1e9 / hbm,
                         "peak_source": "measured" if "fallback" not in peaks else "fallback",
@@ -510,7 +519,8 @@ def main():
                  "one_launch_per_box": run_per_box_sample(kb)}
         kg = max(3, min(K, 10))
         grad = {"rgl_fp64": run_grad(kg, 2, "fp64", "rgl"), "rgl_mixed": run_grad(kg, 2, "mixed", "rgl"),
-                "spline_fp64": run_grad(kg, 2, "fp64", "spline")}
+                "spline_fp64": run_grad(kg, 2, "fp64", "spline"),
+                "spline_mixed": run_grad(kg, 2, "mixed", "spline")}
     if rank == 0 and not args.no_extras:
         import oracle as O
         O.build()

@@ -12,46 +12,43 @@
 // largest displacement since its last build exceeds skin/2); atoms and cells
 // of the other boxes are left untouched, so the chain can be launched every
 // step, or captured in a CUDA graph, without a host decision.
+#include <algorithm>
 #include <cstring>
 
 #include "md_device.cuh"
 
 namespace mdk {
 
-// A box rebuilds when mode is 1, or when its largest displacement since its
-// last build exceeds skin/2; boxes decide independently.
-__device__ __forceinline__ bool box_wants(const Ctl* c, const unsigned long long* disp, int b, int mode,
-                                         unsigned long long thr) {
-    if (load_status(c)) return false;
-    if (mode) return true;
-    return disp[b] > thr;
-}
+// The per-atom kernels below loop over the atoms with a fixed grid (a few
+// waves of resident blocks) and read the status word once, so a step that
+// rebuilds nothing costs a few microseconds per kernel.
 
 __global__ void k_bin(int64_t N, double4_32a* __restrict__ x, Geo g, int* __restrict__ cell_of,
                       int* __restrict__ cell_count, const Ctl* ctl, const unsigned long long* __restrict__ disp,
                       int mode, unsigned long long thr) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    int b = g.B == 1 ? 0 : g.atom_box[s];
-    if (!box_wants(ctl, disp, b, mode, thr)) return;
-    // positions drift unwrapped between builds; wrap them into the box here
-    double4_32a p = x[s];
-    p.x = wrap_step(p.x, g.L[3 * b]);
-    p.y = wrap_step(p.y, g.L[3 * b + 1]);
-    p.z = wrap_step(p.z, g.L[3 * b + 2]);
-    x[s] = p;
-    double pc[3] = {p.x, p.y, p.z};
-    int c[3];
+    if (load_status(ctl)) return;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        int b = g.B == 1 ? 0 : g.atom_box[s];
+        if (!box_due(disp, b, mode, thr)) continue;
+        // positions drift unwrapped between builds; wrap them into the box here
+        double4_32a p = x[s];
+        p.x = wrap_step(p.x, g.L[3 * b]);
+        p.y = wrap_step(p.y, g.L[3 * b + 1]);
+        p.z = wrap_step(p.z, g.L[3 * b + 2]);
+        x[s] = p;
+        double pc[3] = {p.x, p.y, p.z};
+        int c[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        int n = g.nc[3 * b + a];
-        int k = (int)floor(pc[a] / g.cell_len[3 * b + a]);
-        c[a] = k < 0 ? 0 : (k >= n ? n - 1 : k);
+        for (int a = 0; a < 3; ++a) {
+            int n = g.nc[3 * b + a];
+            int k = (int)floor(pc[a] / g.cell_len[3 * b + a]);
+            c[a] = k < 0 ? 0 : (k >= n ? n - 1 : k);
+        }
+        int lin = g.cell_off[b] + (c[0] * g.nc[3 * b + 1] + c[1]) * g.nc[3 * b + 2] + c[2];
+        int gc = g.cell_rank[lin];
+        cell_of[s] = gc;
+        atomicAdd(&cell_count[gc], 1);
     }
-    int lin = g.cell_off[b] + (c[0] * g.nc[3 * b + 1] + c[1]) * g.nc[3 * b + 2] + c[2];
-    int gc = g.cell_rank[lin];
-    cell_of[s] = gc;
-    atomicAdd(&cell_count[gc], 1);
 }
 
 constexpr int kScanNT = 1024;
@@ -144,13 +141,14 @@ __global__ void k_scan_add(int n, int* __restrict__ start, const int* __restrict
 __global__ void k_scatter(int64_t N, Geo g, const int* __restrict__ cell_of, const int* __restrict__ start,
                           int* __restrict__ fill, int* __restrict__ src, const Ctl* ctl,
                           const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    int b = g.B == 1 ? 0 : g.atom_box[s];
-    if (!box_wants(ctl, disp, b, mode, thr)) return;
-    int c = cell_of[s];
-    int64_t t = g.atom_off[b] + (start[c] - start[g.cell_off[b]]) + atomicAdd(&fill[c], 1);
-    src[t] = (int)s;
+    if (load_status(ctl)) return;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        int b = g.B == 1 ? 0 : g.atom_box[s];
+        if (!box_due(disp, b, mode, thr)) continue;
+        int c = cell_of[s];
+        int64_t t = g.atom_off[b] + (start[c] - start[g.cell_off[b]]) + atomicAdd(&fill[c], 1);
+        src[t] = (int)s;
+    }
 }
 
 // Orders the atoms of each cell by caller id, so the sorted order (and every
@@ -158,10 +156,11 @@ __global__ void k_scatter(int64_t N, Geo g, const int* __restrict__ cell_of, con
 __global__ void k_sort_cells(int n_cells, Geo g, const int* __restrict__ start, int* __restrict__ fill,
                              int* __restrict__ src, const int* __restrict__ perm, const Ctl* ctl,
                              const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
+    if (load_status(ctl)) return;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cells) return;
     int b = g.cell_box[c];
-    if (!box_wants(ctl, disp, b, mode, thr)) return;
+    if (!box_due(disp, b, mode, thr)) return;
     int base = (int)g.atom_off[b] - start[g.cell_off[b]];
     int a = base + start[c], e = base + start[c + 1];
     fill[c] = 0;
@@ -183,16 +182,17 @@ __global__ void k_permute(int64_t N, int64_t Np, Geo g, const int* __restrict__ 
                           int* __restrict__ perm_alt, const int* __restrict__ cell_of, int* __restrict__ cell_t_alt,
                           const Ctl* ctl, const unsigned long long* __restrict__ disp, int mode,
                           unsigned long long thr) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N) return;
-    if (!box_wants(ctl, disp, g.B == 1 ? 0 : g.atom_box[t], mode, thr)) return;
-    int s = src[t];
-    x_alt[t] = x[s];
-    v_alt[t] = v[s];
-    v_alt[Np + t] = v[Np + s];
-    v_alt[2 * Np + t] = v[2 * Np + s];
-    perm_alt[t] = perm[s];
-    cell_t_alt[t] = cell_of[s];
+    if (load_status(ctl)) return;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        if (!box_due(disp, g.B == 1 ? 0 : g.atom_box[t], mode, thr)) continue;
+        int s = src[t];
+        x_alt[t] = x[s];
+        v_alt[t] = v[s];
+        v_alt[Np + t] = v[Np + s];
+        v_alt[2 * Np + t] = v[2 * Np + s];
+        perm_alt[t] = perm[s];
+        cell_t_alt[t] = cell_of[s];
+    }
 }
 
 __global__ void k_copy_back(int64_t N, int64_t Np, Geo g, double4_32a* __restrict__ x, const double4_32a* __restrict__ x_alt,
@@ -201,24 +201,25 @@ __global__ void k_copy_back(int64_t N, int64_t Np, Geo g, double4_32a* __restric
                             int* __restrict__ cell_t, const int* __restrict__ cell_t_alt, float4* __restrict__ xo,
                             Ctl* ctl, const unsigned long long* __restrict__ disp, int mode,
                             unsigned long long thr) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N) return;
-    const int b = g.B == 1 ? 0 : g.atom_box[t];
-    if (!box_wants(ctl, disp, b, mode, thr)) return;
-    // count the list builds of the dynamics (one per box and step)
-    if (!mode && t == g.atom_off[b]) atomicAdd((unsigned long long*)&ctl->n_rebuild, 1ULL);
-    double4_32a p = x_alt[t];
-    x[t] = p;
-    xb[t] = p;
-    v[t] = v_alt[t];
-    v[Np + t] = v_alt[Np + t];
-    v[2 * Np + t] = v_alt[2 * Np + t];
-    int id = perm_alt[t];
-    perm[t] = id;
-    iperm[id] = (int)t;
-    int gc = cell_t_alt[t];
-    cell_t[t] = gc;
-    xo[t] = cell_local(g, b, gc, p);
+    if (load_status(ctl)) return;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int b = g.B == 1 ? 0 : g.atom_box[t];
+        if (!box_due(disp, b, mode, thr)) continue;
+        // count the list builds of the dynamics (one per box and step)
+        if (!mode && t == g.atom_off[b]) atomicAdd((unsigned long long*)&ctl->n_rebuild, 1ULL);
+        double4_32a p = x_alt[t];
+        x[t] = p;
+        xb[t] = p;
+        v[t] = v_alt[t];
+        v[Np + t] = v_alt[Np + t];
+        v[2 * Np + t] = v_alt[2 * Np + t];
+        int id = perm_alt[t];
+        perm[t] = id;
+        iperm[id] = (int)t;
+        int gc = cell_t_alt[t];
+        cell_t[t] = gc;
+        xo[t] = cell_local(g, b, gc, p);
+    }
 }
 
 static unsigned long long disp_threshold(const Engine& e) {
@@ -236,7 +237,8 @@ void launch_rebuild(Engine& e, int mode, cudaStream_t s) {
     Geo g = make_geo(e);
     unsigned long long thr = disp_threshold(e);
     const int nt = 256;
-    int nb_atoms = (int)((e.N + nt - 1) / nt);
+    // per-atom kernels: grid-stride over four waves of resident blocks
+    int nb_atoms = (int)std::min<int64_t>((e.N + nt - 1) / nt, (int64_t)32 * e.n_sm);
     int nb_scan = (e.n_cells + kScanNT - 1) / kScanNT;
     const unsigned long long* disp = e.disp_box;
     k_bin<<<nb_atoms, nt, 0, s>>>(e.N, e.x, g, e.cell_of, e.cell_count, e.ctl, disp, mode, thr);

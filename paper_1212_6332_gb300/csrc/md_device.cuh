@@ -91,6 +91,14 @@ __device__ __forceinline__ int load_status(const Ctl* c) {
     return *((volatile const int*)&c->status);
 }
 
+// Whether box b rebuilds in this call: always when mode is 1, else when its
+// largest displacement since its last build exceeds skin/2 (boxes decide
+// independently). The caller reads the status word once: an error raised
+// by an earlier kernel skips the whole build.
+__device__ __forceinline__ bool box_due(const unsigned long long* disp, int b, int mode, unsigned long long thr) {
+    return mode || disp[b] > thr;
+}
+
 
 // Float32 offset of each atom from the origin of the cell it was binned
 // into (minimum image), w = packed cell coordinates: the list build's

@@ -19,9 +19,10 @@
 //                 histogram over the cubic coefficients of each interval)
 // then a fixed-order reduction and, for splines, the transpose of the
 // knot-value -> coefficient map (one more tridiagonal solve per spline).
-// In mixed precision the RGL adjoint evaluates its pair terms in float32
-// (cell-local offsets, as the mixed forward pass) and sums the parameter
-// terms in float64; the spline adjoint always runs in float64.
+// In mixed precision the adjoint evaluates its pair geometry and pair
+// functions in float32 (cell-local offsets, as the mixed forward pass) and
+// sums the parameter terms in float64 (RGL: per-thread sums; splines: the
+// float64 coefficient histogram at the float32 pair distance).
 #include <cstring>
 
 #include "md_device.cuh"
@@ -46,6 +47,29 @@ __device__ __forceinline__ void sep(const Geo& g, const double4_32a* __restrict_
     dz = minimg(xj.z - xi.z, Lz, 0.5 * Lz);
 }
 
+// rho_i, F'(rho_i) and F''(rho_i) into the per-atom arrays (F'' of the
+// spline is that of its cubic piece; 0 on the linear extensions).
+template <int KIND>
+__device__ __forceinline__ void store_embedding(const Pot& P, double r_i, int64_t i, double* __restrict__ rho,
+                                                double* __restrict__ Fp, double* __restrict__ Fpp) {
+    double F, Fpi, Fppi = 0.0;
+    embed<KIND>(P, r_i, F, Fpi);
+    if (KIND == MD_POT_SPLINE) {
+        double s = (r_i - P.st0[2]) * P.sinvh[2];
+        int k = (int)s;
+        if (s >= 0.0 && k < P.sn[2] - 1) {
+            double u = r_i - (P.st0[2] + P.sh[2] * k);
+            double4_32a c = P.sp[2][k];
+            Fppi = 2.0 * c.z + 6.0 * c.w * u;
+        }
+    } else if (r_i > 0.0) {
+        Fppi = 0.25 * P.F_scale / (r_i * sqrt(r_i));
+    }
+    rho[i] = r_i;
+    Fp[i] = Fpi;
+    Fpp[i] = Fppi;
+}
+
 // rho_i, F'(rho_i), F''(rho_i) recomputed from the list.
 template <int KIND>
 __global__ void __launch_bounds__(kGNT) k_grad_rho(int64_t N, int64_t Np, Geo g, Pot P,
@@ -68,22 +92,7 @@ __global__ void __launch_bounds__(kGNT) k_grad_rho(int64_t N, int64_t Np, Geo g,
         pair_eval<KIND>(P, sT, r2, phi, fr, A, B);
         r_i += fr;
     }
-    double F, Fpi, Fppi = 0.0;
-    embed<KIND>(P, r_i, F, Fpi);
-    if (KIND == MD_POT_SPLINE) {
-        double s = (r_i - P.st0[2]) * P.sinvh[2];
-        int k = (int)s;
-        if (s >= 0.0 && k < P.sn[2] - 1) {
-            double u = r_i - (P.st0[2] + P.sh[2] * k);
-            double4_32a c = P.sp[2][k];
-            Fppi = 2.0 * c.z + 6.0 * c.w * u;
-        }
-    } else if (r_i > 0.0) {
-        Fppi = 0.25 * P.F_scale / (r_i * sqrt(r_i));
-    }
-    rho[i] = r_i;
-    Fp[i] = Fpi;
-    Fpp[i] = Fppi;
+    store_embedding<KIND>(P, r_i, i, rho, Fp, Fpp);
 }
 
 // u_i = sum_j (g_i - g_j) . d_ij rho'(r)/r
@@ -343,7 +352,7 @@ __global__ void k_gather_g(int64_t N, int64_t Np, const double* __restrict__ g_f
 // (as in the mixed force kernels), float32 sums grouped per 16 list entries
 // and compensated, and the per-thread parameter sums in float64.
 
-template <bool WIDE>
+template <int KIND, bool WIDE>
 __global__ void __launch_bounds__(kGNT) k_grad_rho_mixed(int64_t N, int64_t Np, Geo g, Pot P,
                                                          const float4* __restrict__ xo, const int* __restrict__ nn,
                                                          const int* __restrict__ nl, int max_nb,
@@ -360,18 +369,13 @@ __global__ void __launch_bounds__(kGNT) k_grad_rho_mixed(int64_t N, int64_t Np, 
         float dx, dy, dz;
         sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < P.f_rc2) acc.add(dens_ff<MD_POT_RGL>(P, r2 * rsqrtf(r2)));
+        if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2)));
         if ((k & kGroupMask) == kGroupMask) acc.flush();
     }
-    double r_i = acc.value();
-    double F, Fpi;
-    embed<MD_POT_RGL>(P, r_i, F, Fpi);
-    rho[i] = r_i;
-    Fp[i] = Fpi;
-    Fpp[i] = r_i > 0.0 ? 0.25 * P.F_scale / (r_i * sqrt(r_i)) : 0.0;
+    store_embedding<KIND>(P, acc.value(), i, rho, Fp, Fpp);
 }
 
-template <bool WIDE>
+template <int KIND, bool WIDE>
 __global__ void __launch_bounds__(kGNT) k_grad_u_mixed(int64_t N, int64_t Np, Geo g, Pot P,
                                                        const float4* __restrict__ xo, const int* __restrict__ nn,
                                                        const int* __restrict__ nl, int max_nb,
@@ -391,7 +395,7 @@ __global__ void __launch_bounds__(kGNT) k_grad_u_mixed(int64_t N, int64_t Np, Ge
         if (r2 < P.f_rc2) {
             float rinv = rsqrtf(r2);
             float phi, dphi, fr, dfr;
-            pair_allf<MD_POT_RGL>(P, r2 * rinv, phi, dphi, fr, dfr);
+            pair_allf<KIND>(P, r2 * rinv, phi, dphi, fr, dfr);
             float w = (float)(gx - gs[j]) * dx + (float)(gy - gs[Np + j]) * dy + (float)(gz - gs[2 * Np + j]) * dz;
             acc.add(w * dfr * rinv);
         }
@@ -458,19 +462,85 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_mixed(int64_t N, int64_
     }
 }
 
-template <bool WIDE>
+// Spline parameter terms with the pair geometry in float32 (cell-local
+// offsets): the adjoint weights and the coefficient histogram stay float64.
+template <int NT, bool WIDE>
+__global__ void __launch_bounds__(NT) k_grad_param_spline_mixed(int64_t N, int64_t Np, Geo g, Pot P,
+                                                                const float4* __restrict__ xo,
+                                                                const int* __restrict__ nn,
+                                                                const int* __restrict__ nl, int max_nb,
+                                                                const double* __restrict__ gs,
+                                                                const double* __restrict__ gE,
+                                                                const double* __restrict__ rho,
+                                                                const double* __restrict__ Fp,
+                                                                const double* __restrict__ Fpp,
+                                                                const double* __restrict__ u, int ncoef,
+                                                                double* __restrict__ partial) {
+    extern __shared__ double sg[];  // [ncoef] as in k_grad_param_spline
+    for (int k = threadIdx.x; k < ncoef; k += NT) sg[k] = 0.0;
+    __syncthreads();
+    double* gV = sg;
+    double* gR = sg + 4 * (P.sn[0] - 1);
+    double* gF = gR + 4 * (P.sn[1] - 1);
+    const float rcf = (float)P.rc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const CellSep cs = cell_sep<false>(g, CellSep{}, i);
+        const float4 oi = xo[i];
+        const int n = min(nn[i], max_nb);
+        const float gx = (float)gs[i], gy = (float)gs[Np + i], gz = (float)gs[2 * Np + i];
+        const double ge = box_gE(g, gE, i);
+        const double Fpi = Fp[i];
+        const double aF = u[i] * Fpp[i] + ge * Fpi;
+        for (int k = 0; k < n; ++k) {
+            int j = entry_slot(nl[(int64_t)k * Np + i]);
+            float dx, dy, dz;
+            sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+            float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= P.f_rc2) continue;
+            float rinv = rsqrtf(r2);
+            float r = r2 * rinv;
+            if (r >= rcf) continue;
+            const double w = (double)((gx * dx + gy * dy + gz * dz) * rinv);
+            spline_adj(P, 0, (double)r, 0.5 * ge, w, gV);
+            spline_adj(P, 1, (double)r, aF, w * (Fpi + Fp[j]), gR);
+        }
+        spline_adj(P, 2, rho[i], ge, u[i], gF);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < ncoef; k += NT) partial[(int64_t)blockIdx.x * ncoef + k] = sg[k];
+}
+
+template <int KIND, bool WIDE>
 static int grad_mixed_impl(Engine& e, const double* g_f, const double* g_e, double* grad, cudaStream_t s) {
     Geo g = make_geo(e);
     int nb = (int)((e.N + kGNT - 1) / kGNT);
     k_gather_g<<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g_f, e.perm, e.grad_g);
-    k_grad_rho_mixed<WIDE><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.rho, e.Fp,
-                                               e.grad_Fpp);
-    k_grad_u_mixed<WIDE><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.grad_g, e.grad_u);
-    k_grad_param_rgl_mixed<WIDE><<<e.grad_blocks, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb,
-                                                               e.grad_g, g_e, e.Fp, e.grad_Fpp, e.grad_u,
-                                                               e.grad_partial);
-    k_sum_partials<<<kRglParams, 256, 0, s>>>(e.grad_blocks, kRglParams, e.grad_partial, grad);
-    e.launches += 5;
+    k_grad_rho_mixed<KIND, WIDE><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.rho,
+                                                     e.Fp, e.grad_Fpp);
+    k_grad_u_mixed<KIND, WIDE><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.grad_g,
+                                                   e.grad_u);
+    e.launches += 3;
+    if (KIND == MD_POT_RGL) {
+        k_grad_param_rgl_mixed<WIDE><<<e.grad_blocks, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl,
+                                                                   e.max_nb, e.grad_g, g_e, e.Fp, e.grad_Fpp,
+                                                                   e.grad_u, e.grad_partial);
+        k_sum_partials<<<kRglParams, 256, 0, s>>>(e.grad_blocks, kRglParams, e.grad_partial, grad);
+        e.launches += 2;
+    } else {
+        const md_potential& p = e.pot_host;
+        int ncoef = 4 * (p.n_phi - 1) + 4 * (p.n_f - 1) + 4 * (p.n_F - 1);
+        size_t smem = (size_t)ncoef * sizeof(double);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_grad_param_spline_mixed<kGNT, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        k_grad_param_spline_mixed<kGNT, WIDE><<<e.grad_blocks, kGNT, smem, s>>>(
+            e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp, e.grad_u,
+            ncoef, e.grad_partial);
+        k_sum_partials<<<ncoef, 256, 0, s>>>(e.grad_blocks, ncoef, e.grad_partial, e.grad_coef);
+        k_spline_adjoint<<<1, 32, 0, s>>>(e.grad_coef, e.spline_work, grad, p.n_phi, p.n_f, p.n_F, e.pot.sh[0],
+                                          e.pot.sh[1], e.pot.sh[2]);
+        e.launches += 3;
+    }
     return MD_OK;
 }
 
@@ -507,16 +577,22 @@ int launch_param_grad(Engine& e, const double* g_f, const double* g_e, double* g
     if (e.N == 0) return cudaMemsetAsync(grad, 0, sizeof(double) * (e.pot_host.kind == MD_POT_SPLINE ?
                                               e.pot_host.n_phi + e.pot_host.n_f + e.pot_host.n_F : 5), s) ==
                                   cudaSuccess ? MD_OK : MD_ERR_CUDA;
+    // mixed precision: float32 pair geometry and pair functions in the
+    // adjoint as in the forward pass
+    const bool mixed = e.cfg.precision == MD_MIXED;
     if (e.pot.kind == MD_POT_RGL) {
-        // mixed precision: float32 pair math in the adjoint as in the forward
-        if (e.cfg.precision == MD_MIXED)
-            return e.wide ? grad_mixed_impl<true>(e, g_f, g_e, grad, s) : grad_mixed_impl<false>(e, g_f, g_e, grad, s);
+        if (mixed)
+            return e.wide ? grad_mixed_impl<MD_POT_RGL, true>(e, g_f, g_e, grad, s)
+                          : grad_mixed_impl<MD_POT_RGL, false>(e, g_f, g_e, grad, s);
         return grad_impl<MD_POT_RGL>(e, g_f, g_e, grad, s);
     }
     if (e.pot.kind == MD_POT_SPLINE) {
         const md_potential& p = e.pot_host;
         int ncoef = 4 * (p.n_phi - 1) + 4 * (p.n_f - 1) + 4 * (p.n_F - 1);
         if ((size_t)ncoef * sizeof(double) > 200 * 1024) return MD_ERR_UNSUPPORTED;
+        if (mixed)
+            return e.wide ? grad_mixed_impl<MD_POT_SPLINE, true>(e, g_f, g_e, grad, s)
+                          : grad_mixed_impl<MD_POT_SPLINE, false>(e, g_f, g_e, grad, s);
         if ((size_t)ncoef * sizeof(double) > 48 * 1024) {
             cudaFuncSetAttribute(k_grad_param_spline<kGNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(ncoef * sizeof(double)));

@@ -30,11 +30,6 @@ constexpr int kNlThreads = 128;
 constexpr int kNlCap = 1024;  // staged candidates per pass
 constexpr int kNlMaxI = 256;  // centre-cell atoms per pass
 
-// Whether box b rebuilds in this call (the caller has checked the status
-// word once: an error raised by an earlier kernel skips the whole build).
-__device__ __forceinline__ bool box_due(const unsigned long long* disp, int b, int mode, unsigned long long thr) {
-    return mode || disp[b] > thr;
-}
 
 // Lists of the atoms of cell c (one block): the stencil's atoms are staged
 // in shared memory in ascending cell-id order and each warp sweeps them for

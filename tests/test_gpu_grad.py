@@ -78,19 +78,22 @@ def test_adjoint_with_zero_upstream_is_zero():
     assert torch.count_nonzero(g) == 0
 
 
-def test_mixed_precision_adjoint_within_bound():
-    """Mixed precision (float32 pair terms, float64 parameter sums) against
-    the oracle's float64 forward-mode gradient: each component within 1e-4
-    of the largest (the pair terms carry ~1e-6 relative float32 error, and
-    the gradient is a sum of many such terms with partial cancellation)."""
+@pytest.mark.parametrize("kind", ["rgl", "spline"])
+def test_mixed_precision_adjoint_within_bound(kind):
+    """Mixed precision (float32 pair geometry and pair terms, float64
+    parameter sums) against the oracle's float64 forward-mode gradient: each
+    component within 1e-4 of the largest (the pair terms carry ~1e-6
+    relative float32 error, and the gradient is a sum of many such terms
+    with partial cancellation)."""
     import torch
     from paper_1212_6332_gb300.fit import make_batch
+    spec = MODEL if kind == "rgl" else O.tabulate_spline(MODEL, n_knots=60, rho_hi=2 * RHO_EQ)
     cfgs = configs((3, 4, 4), seed=31)
-    s = make_batch(MODEL, cfgs, precision="mixed")
+    s = make_batch(spec, cfgs, precision="mixed")
     n = sum(c.n for c in cfgs)
     rng = np.random.default_rng(6)
     g_f = rng.normal(size=(n, 3))
     g_e = rng.normal(size=len(cfgs))
     got = s.param_grad(torch.tensor(g_f, device="cuda"), torch.tensor(g_e, device="cuda")).cpu().numpy()
-    ref = oracle_grad(MODEL, cfgs, g_f, g_e)
-    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max(), np.abs(got - ref) / np.abs(ref).max()
+    ref = oracle_grad(spec, cfgs, g_f, g_e)
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
