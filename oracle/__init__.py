@@ -66,7 +66,7 @@ def _load():
     lib.orc_forces_pairs.restype = dbl
     lib.orc_forces_pairs.argtypes = [vp, i32, _D, _D, i64, _I, _I, _D, _D, _D, _D]
     lib.orc_md_run.restype = i64
-    lib.orc_md_run.argtypes = [vp, i32, _D, _D, _D, dbl, dbl, dbl, i32, _D]
+    lib.orc_md_run.argtypes = [vp, i32, _D, _D, _D, dbl, dbl, dbl, i32, _D, dbl, dbl]
     lib.orc_param_deriv.restype = dbl
     lib.orc_param_deriv.argtypes = [vp, i32, i32, _D, _D, i64, _I, _I, _D]
     lib.orc_param_grad.argtypes = [vp, i32, i32, _D, _D, i64, _I, _I, _D, dbl, _D]
@@ -186,14 +186,17 @@ def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs") -> 
     return dict(E=E, rho=rho, Fp=Fp, e_atom=e, f=f)
 
 
-def md_run(pot: Potential, x, v, box, mass: float, dt: float, skin: float, n_steps: int) -> dict:
+def md_run(pot: Potential, x, v, box, mass: float, dt: float, skin: float, n_steps: int,
+           tau_T: float = 0.0, T_e: float = 0.0) -> dict:
     """Velocity-Verlet trajectory; returns final x, v, per-step thermo rows
-    (KE, PE, E_tot, T) and the number of list rebuilds."""
+    (KE, PE, E_tot, T) and the number of list rebuilds. With tau_T > 0 the
+    electron-phonon friction of Eq. (4) couples every atom to the electronic
+    temperature T_e (K) with time constant tau_T (fs)."""
     lib = _load()
     x, v, box = _f64(x).copy(), _f64(v).copy(), _f64(box)
     thermo = np.zeros((n_steps + 1, 4))
     nreb = lib.orc_md_run(pot._h, x.shape[0], _dp(x), _dp(v), _dp(box), float(mass), float(dt), float(skin),
-                          int(n_steps), _dp(thermo))
+                          int(n_steps), _dp(thermo), float(tau_T), float(T_e))
     return dict(x=x, v=v, thermo=thermo, n_rebuild=int(nreb))
 
 

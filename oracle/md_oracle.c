@@ -20,6 +20,7 @@
  *   - Newton's third law in the CPU pair loops                     (Sec. 4.3)
  *   - Verlet neighbour list with a radius beyond the force cutoff
  *     (a skin)                                                     (Sec. 4.2)
+ *   - the electron-phonon friction of the temperature control      Eq. (4)
  *
  * Two independent routes for Eq. (1)-(3): orc_forces_brute() writes the double
  * sums out over all atom pairs (O(N^2), the definition), and
@@ -505,17 +506,42 @@ static double kinetic(int n, const double* v, double mass) {
     return 0.5 * mass * s * ORC_MVV;
 }
 
+/* Electron-phonon friction of Finnis et al. (Eq. 4): each atom feels
+ * -m (1/tau) (T_i - T_e)/T_i v_i, with T_i = m v_i^2 / (3 k_B) its own
+ * kinetic temperature and T_e the constant electronic temperature. On its
+ * own this term gives dT_i/dt = -(2/tau)(T_i - T_e) along the fixed direction
+ * of v_i, which is integrated exactly over an interval h:
+ *   T_i <- T_e + (T_i - T_e) exp(-2h/tau),  v_i <- v_i sqrt(T_i new / T_i old).
+ * An atom at rest is left at rest (its direction is undefined). */
+static void bath_half(int n, double* v, double mass, double T_e, double decay) {
+    for (int i = 0; i < n; ++i) {
+        double* vi = v + 3 * (size_t)i;
+        double v2 = vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2];
+        if (!(v2 > 0.0)) continue;
+        double Ti = mass * ORC_MVV * v2 / (3.0 * ORC_KB);
+        double Tn = T_e + (Ti - T_e) * decay;
+        double lam = sqrt(Tn / Ti);
+        vi[0] *= lam;
+        vi[1] *= lam;
+        vi[2] *= lam;
+    }
+}
+
 /* n_steps of velocity Verlet at time step dt (fs) for atoms of one mass (u):
- *   v += dt/2 * f/m;  x += dt * v;  wrap x;
+ *   [friction dt/2;] v += dt/2 * f/m;  x += dt * v;  wrap x;
  *   rebuild the list (radius r_cut + skin) when some atom moved more than
  *   skin/2 since the last build;
- *   f = forces(x);  v += dt/2 * f/m.
+ *   f = forces(x);  v += dt/2 * f/m[; friction dt/2].
+ * The bracketed friction half steps (Eq. 4, symmetric splitting) run when
+ * tau_T > 0, towards the electronic temperature T_e (K).
  * x, v: [n*3], updated in place. thermo (nullable): [(n_steps+1)*4] rows of
  * (kinetic, potential, total energy in eV, temperature in K with 3n-3
  * degrees of freedom), row 0 the initial state. Returns the number of list
  * builds after the initial one. */
 long orc_md_run(const orc_pot* P, int n, double* x, double* v, const double* box, double mass, double dt,
-                double skin, int n_steps, double* thermo) {
+                double skin, int n_steps, double* thermo, double tau_T, double T_e) {
+    const int bath = tau_T > 0.0;
+    const double decay = bath ? exp(-dt / tau_T) : 1.0; /* exp(-2 (dt/2) / tau) */
     size_t nn = (size_t)(n > 0 ? n : 1);
     double rl = P->r_cut + skin;
     double half2 = 0.25 * skin * skin;
@@ -537,6 +563,7 @@ long orc_md_run(const orc_pot* P, int n, double* x, double* v, const double* box
         thermo[3] = dof > 0 ? 2.0 * ke / (dof * ORC_KB) : 0.0;
     }
     for (int s = 1; s <= n_steps; ++s) {
+        if (bath) bath_half(n, v, mass, T_e, decay);
         for (int k = 0; k < 3 * n; ++k) {
             v[k] += 0.5 * dt * f[k] * acc;
             x[k] += dt * v[k];
@@ -558,6 +585,7 @@ long orc_md_run(const orc_pot* P, int n, double* x, double* v, const double* box
         }
         pe = orc_forces_pairs(P, n, x, box, B.np, B.pi, B.pj, NULL, NULL, NULL, f);
         for (int k = 0; k < 3 * n; ++k) v[k] += 0.5 * dt * f[k] * acc;
+        if (bath) bath_half(n, v, mass, T_e, decay);
         if (thermo) {
             double ke = kinetic(n, v, mass);
             double* t = thermo + 4 * (size_t)s;

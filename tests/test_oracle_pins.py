@@ -282,6 +282,56 @@ def test_time_reversibility():
     assert np.abs(back["v"] + bx.v).max() < 1e-10
 
 
+def gas(n_side=4, spacing=6.5, temperature=600.0, seed=21):
+    """Atoms on a simple cubic grid farther apart than r_cut + skin: no
+    forces act, only the friction of Eq. (4)."""
+    g = np.arange(n_side) * spacing + 1.0
+    x = np.array(list(itertools.product(g, g, g)), dtype=float)
+    box = np.full(3, n_side * spacing)
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=x.shape) * np.sqrt(I.KB_EV_PER_K * temperature / (I.MASS_CU * I.MVV_EV))
+    return x, v, box
+
+
+def atom_temperatures(v):
+    return I.MASS_CU * I.MVV_EV * np.sum(v * v, axis=1) / (3.0 * I.KB_EV_PER_K)
+
+
+def test_friction_free_atoms_follow_the_closed_form():
+    """With no forces, Eq. (4) reads dv/dt = -(1/tau)(1 - T_e/T_i) v, so each
+    atom keeps its direction and its temperature T_i = m v^2 / (3 k_B) obeys
+    dT_i/dt = -(2/tau)(T_i - T_e): T_i(t) = T_e + (T_i(0) - T_e) exp(-2t/tau)."""
+    x, v, box = gas()
+    tau, T_e, dt, n = 40.0, 300.0, 1.0, 60
+    out = O.md_run(O.Potential(I.RGL_CU), x, v, box, I.MASS_CU, dt, 0.3, n, tau_T=tau, T_e=T_e)
+    T0, T1 = atom_temperatures(v), atom_temperatures(out["v"])
+    expect = T_e + (T0 - T_e) * np.exp(-2.0 * n * dt / tau)
+    assert np.allclose(T1, expect, rtol=1e-12, atol=0)
+    cos = np.sum(out["v"] * v, axis=1) / np.linalg.norm(out["v"], axis=1) / np.linalg.norm(v, axis=1)
+    assert np.allclose(cos, 1.0, rtol=0, atol=1e-14)
+    # positions advance with the velocities (no forces): ballistic drift
+    assert out["thermo"][:, 1].max() == 0.0
+
+
+def test_friction_without_coupling_is_plain_verlet():
+    bx = I.perturbed_fcc(3, I.A_CU, 600.0, I.MASS_CU, seed=8)
+    pot = O.Potential(I.RGL_CU)
+    a = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 30)
+    b = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 30, tau_T=0.0, T_e=1000.0)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
+
+
+def test_friction_brings_a_hot_crystal_to_the_electron_temperature():
+    """A 900 K crystal coupled to a 300 K electron bath (tau = 50 fs) cools
+    to 300 K: the kinetic temperature, averaged over the last 300 of 1500
+    steps, is within 5% of T_e, and the energy it lost went to the bath."""
+    bx = I.perturbed_fcc(4, I.A_CU, 900.0, I.MASS_CU, seed=13)
+    out = O.md_run(O.Potential(I.RGL_CU), bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 1500, tau_T=50.0, T_e=300.0)
+    T = out["thermo"][:, 3]
+    assert T[-300:].mean() == pytest.approx(300.0, rel=0.05)
+    assert out["thermo"][-1, 2] < out["thermo"][0, 2]
+
+
 def test_dimer_small_oscillation_period():
     """A dimer near its bond length oscillates at omega = sqrt(k/mu), with
     k = E''(r_eq) of the closed-form dimer energy and mu = m/2."""
