@@ -242,6 +242,18 @@ MD_API int md_batch_thermo(md_batch* b, double* thermo_box, md_stream stream);
  * may not grow). */
 MD_API int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream stream);
 
+/* Temperature control of Sec. 2, Eq. (4) (Finnis et al.): every atom feels
+ * the friction force -m (1/tau_T) (T_i - T_e)/T_i v_i, with T_i = m v_i^2 /
+ * (3 k_B) its own kinetic temperature and T_e the electronic temperature
+ * (K). The velocity-Verlet steps apply it in two half steps around the
+ * force kicks, each the exact solution of the friction term alone
+ * (T_i <- T_e + (T_i - T_e) exp(-dt/tau_T), direction kept; an atom at rest
+ * stays at rest). tau_T (fs) <= 0 switches it off (the default). Affects the
+ * md_step / md_batch_step calls that follow, both schedules and both
+ * precisions. Errors: MD_ERR_ARG for a NULL handle, a negative or
+ * non-finite T_e or a non-finite tau_T. */
+MD_API int md_set_thermostat(md_batch* b, double T_e, double tau_T);
+
 /* Gradient of a scalar loss L with respect to the potential parameters
  * (RGL: A, xi, p, q, r0; spline: all knot values, V then rho then F), at
  * the batch's current positions, given g_f = dL/dF [n][3] (device, caller

@@ -1088,6 +1088,21 @@ int md_batch_schedule(const md_batch* b, int* choice, double* ms_tile, double* m
     return MD_OK;
 }
 
+int md_set_thermostat(md_batch* b, double T_e, double tau_T) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    if (!(T_e >= 0.0) || !std::isfinite(T_e)) return fail(E, MD_ERR_ARG, "T_e must be >= 0 and finite");
+    if (!std::isfinite(tau_T)) return fail(E, MD_ERR_ARG, "tau_T must be finite");
+    Bath bath{};
+    bath.on = tau_T > 0.0;
+    bath.T_e = T_e;
+    bath.decay = bath.on ? exp(-E->cfg.dt / tau_T) : 1.0;  // exp(-2 (dt/2) / tau_T)
+    bath.m_3kb = E->cfg.mass * kMVV / (3.0 * kBoltz);
+    E->bath = bath;
+    destroy_graphs(*E);  // captured launches carry the old parameters
+    return MD_OK;
+}
+
 int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream st) {
     if (!b) return MD_ERR_ARG;
     Engine* E = &b->e;

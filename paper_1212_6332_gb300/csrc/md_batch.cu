@@ -25,6 +25,7 @@ struct BoxArgs {
     double rl2;
     float rl2f_lo, rl2f_hi;
     double c_kick, dt, half_skin2;
+    Bath bath;
     double4_32a* x;
     double4_32a* x_alt;
     double4_32a* xb;
@@ -221,9 +222,11 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
                 const int64_t i = a0 + t;
                 double4_32a p = sx[t];
                 double4_32a q = A.xb[i];
-                double vx = A.v[i] + A.c_kick * A.f[i];
-                double vy = A.v[A.Np + i] + A.c_kick * A.f[A.Np + i];
-                double vz = A.v[2 * A.Np + i] + A.c_kick * A.f[2 * A.Np + i];
+                double vx = A.v[i], vy = A.v[A.Np + i], vz = A.v[2 * A.Np + i];
+                bath_half(A.bath, vx, vy, vz);  // friction half step before the kick
+                vx = vx + A.c_kick * A.f[i];
+                vy = vy + A.c_kick * A.f[A.Np + i];
+                vz = vz + A.c_kick * A.f[2 * A.Np + i];
                 p.x += A.dt * vx;
                 p.y += A.dt * vy;
                 p.z += A.dt * vz;
@@ -318,9 +321,12 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
             A.f[i] = fx;
             A.f[A.Np + i] = fy;
             A.f[2 * A.Np + i] = fz;
-            A.v[i] += A.c_kick * fx;
-            A.v[A.Np + i] += A.c_kick * fy;
-            A.v[2 * A.Np + i] += A.c_kick * fz;
+            double vx = A.v[i] + A.c_kick * fx, vy = A.v[A.Np + i] + A.c_kick * fy;
+            double vz = A.v[2 * A.Np + i] + A.c_kick * fz;
+            bath_half(A.bath, vx, vy, vz);  // friction half step after the kick
+            A.v[i] = vx;
+            A.v[A.Np + i] = vy;
+            A.v[2 * A.Np + i] = vz;
         }
         __syncthreads();
         ++done;
@@ -399,6 +405,7 @@ static void box_launch(Engine& e, int n_steps, cudaStream_t s) {
     A.rl2f_lo = (float)(A.rl2 - margin);
     A.rl2f_hi = (float)(A.rl2 + margin);
     A.c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
+    A.bath = e.bath;
     A.dt = e.cfg.dt;
     A.half_skin2 = 0.25 * e.cfg.skin * e.cfg.skin;
     A.x = e.x;

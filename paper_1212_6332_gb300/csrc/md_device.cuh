@@ -87,6 +87,19 @@ __device__ __forceinline__ bool below(double r2, double c2) {
     return __double_as_longlong(r2) < __double_as_longlong(c2);
 }
 
+// One friction half step of Eq. (4) on a velocity (see Bath); an atom at
+// rest stays at rest.
+__device__ __forceinline__ void bath_half(const Bath& B, double& vx, double& vy, double& vz) {
+    if (!B.on) return;
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    if (!(v2 > 0.0)) return;
+    const double Ti = B.m_3kb * v2;
+    const double lam = sqrt((B.T_e + (Ti - B.T_e) * B.decay) / Ti);
+    vx *= lam;
+    vy *= lam;
+    vz *= lam;
+}
+
 __device__ __forceinline__ int load_status(const Ctl* c) {
     return *((volatile const int*)&c->status);
 }

@@ -80,6 +80,17 @@ struct Ctl {
     int n_due;                       // cells queued for a partial list build
 };
 
+// Electron-phonon friction of Eq. (4) over one half step (off unless on):
+// each atom's kinetic temperature T_i = m_3kb v^2 relaxes towards T_e by
+// the exact factor of the friction term alone, T_i <- T_e + (T_i - T_e)
+// decay with decay = exp(-dt/tau_T), along the fixed direction of v.
+struct Bath {
+    double T_e;    // electronic temperature (K)
+    double decay;  // exp(-2 (dt/2) / tau_T)
+    double m_3kb;  // m / (3 k_B) in K per (A/fs)^2
+    int on;
+};
+
 // Float32 cell geometry of a box (mixed-precision separations).
 struct CellSep {
     float lx, ly, lz;     // cell sides
@@ -181,6 +192,7 @@ struct Engine {
 
     bool have_state = false;
     bool lists_ok = false;  // lists, cells and build positions agree (a state load may keep them)
+    Bath bath{};            // friction of Eq. (4) applied in the kicks (md_set_thermostat)
     // CUDA graph of one step (and of a chunk of steps)
     cudaGraphExec_t graph_step = nullptr;
     cudaGraphExec_t graph_chunk = nullptr;

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
                                                 const int* __restrict__ nn, const int* __restrict__ nl, int max_nb,
                                                 const double2* __restrict__ ab, const double* __restrict__ Fp,
                                                 double* __restrict__ f, double* __restrict__ v, double c_kick,
-                                                const Ctl* ctl) {
+                                                Bath bath, const Ctl* ctl) {
     if (load_status(ctl)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < N;
@@ -300,9 +300,11 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
     f[Np + i] = fy;
     f[2 * Np + i] = fz;
     if (v) {
-        v[i] += c_kick * fx;
-        v[Np + i] += c_kick * fy;
-        v[2 * Np + i] += c_kick * fz;
+        double vx = v[i] + c_kick * fx, vy = v[Np + i] + c_kick * fy, vz = v[2 * Np + i] + c_kick * fz;
+        bath_half(bath, vx, vy, vz);  // friction half step after the kick
+        v[i] = vx;
+        v[Np + i] = vy;
+        v[2 * Np + i] = vz;
     }
 }
 
@@ -343,7 +345,7 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s) {
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     k_force<SINGLE><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.ab, e.Fp, e.f,
-                                        kick ? e.v : nullptr, c_kick, e.ctl);
+                                        kick ? e.v : nullptr, c_kick, e.bath, e.ctl);
 }
 
 template <int KIND>

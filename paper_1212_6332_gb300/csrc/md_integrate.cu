@@ -50,7 +50,8 @@ __device__ __forceinline__ void record_disp(const Geo& g, int64_t N, int b, doub
 template <bool SINGLE>
 __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo g, double4_32a* __restrict__ x,
                                                      double* __restrict__ v, const double* __restrict__ f,
-                                                     const double4_32a* __restrict__ xb, double c_kick, double dt,
+                                                     const double4_32a* __restrict__ xb, double c_kick, Bath bath,
+                                                     double dt,
                                                      float4* __restrict__ xo, const int* __restrict__ cell_t,
                                                      Ctl* ctl, unsigned long long* __restrict__ disp) {
     if (load_status(ctl)) return;
@@ -64,9 +65,11 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
         for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
         double4_32a p = x[i];
         double4_32a q = xb[i];
-        double vx = v[i] + c_kick * f[i];
-        double vy = v[Np + i] + c_kick * f[Np + i];
-        double vz = v[2 * Np + i] + c_kick * f[2 * Np + i];
+        double vx = v[i], vy = v[Np + i], vz = v[2 * Np + i];
+        bath_half(bath, vx, vy, vz);  // friction half step before the kick
+        vx = vx + c_kick * f[i];
+        vy = vy + c_kick * f[Np + i];
+        vz = vz + c_kick * f[2 * Np + i];
         // no wrap here: positions stay continuous until the next list build
         // (which wraps them), so the image stored in each list entry holds
         p.x += dt * vx;
@@ -193,7 +196,7 @@ static void kick_drift_t(Engine& e, cudaStream_t s) {
     double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
     PhaseScope scope(e, MD_PHASE_KICK_DRIFT, s);
     e.launches += 1;
-    k_kick_drift<SINGLE><<<nb, kINT, 0, s>>>(e.N, e.N_pad, g, e.x, e.v, e.f, e.xb, c_kick, e.cfg.dt, e.xo,
+    k_kick_drift<SINGLE><<<nb, kINT, 0, s>>>(e.N, e.N_pad, g, e.x, e.v, e.f, e.xb, c_kick, e.bath, e.cfg.dt, e.xo,
                                                    e.cell_t, e.ctl, e.disp_box);
 }
 

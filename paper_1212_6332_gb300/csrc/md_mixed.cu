@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
                                                       const int* __restrict__ nl, int max_nb,
                                                       const float* __restrict__ Fpf, double* __restrict__ f,
                                                       double* __restrict__ e_atom, double* __restrict__ v,
-                                                      double c_kick, const Ctl* ctl) {
+                                                      double c_kick, Bath bath, const Ctl* ctl) {
     if (load_status(ctl)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -95,9 +95,11 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
     f[2 * Np + i] = fz;
     e_atom[i] += 0.5 * ae.value();
     if (v) {
-        v[i] += c_kick * fx;
-        v[Np + i] += c_kick * fy;
-        v[2 * Np + i] += c_kick * fz;
+        double vx = v[i] + c_kick * fx, vy = v[Np + i] + c_kick * fy, vz = v[2 * Np + i] + c_kick * fz;
+        bath_half(bath, vx, vy, vz);  // friction half step after the kick
+        v[i] = vx;
+        v[Np + i] = vy;
+        v[2 * Np + i] = vz;
     }
 }
 
@@ -130,7 +132,7 @@ static void run_mixed(Engine& e, int kick, cudaStream_t s) {
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     k_force_mixed<KIND, SINGLE, WIDE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.Fpf,
-                                                   e.f, e.e_atom, kick ? e.v : nullptr, c_kick, e.ctl);
+                                                   e.f, e.e_atom, kick ? e.v : nullptr, c_kick, e.bath, e.ctl);
 }
 
 template <int KIND>

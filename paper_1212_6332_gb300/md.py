@@ -25,7 +25,7 @@ STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_NOMEM", 4: "
 SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_neighbors", "md_get_neighbors",
            "md_max_count", "md_compute_forces", "md_get_forces", "md_step", "md_get_thermo", "md_batch_create",
            "md_batch_destroy", "md_batch_set_state", "md_batch_get_state", "md_batch_compute_forces",
-           "md_batch_step", "md_batch_set_potential", "md_param_grad", "md_num_params", "md_status_string",
+           "md_batch_step", "md_batch_set_potential", "md_set_thermostat", "md_param_grad", "md_num_params", "md_status_string",
            "md_last_error", "md_profile_start", "md_profile_read",
            "md_eval_math", "md_forces_noalloc", "md_batch_thermo",
            "md_batch_schedule")
@@ -97,6 +97,7 @@ def load(path: str | pathlib.Path | None = None) -> ctypes.CDLL:
         "md_batch_compute_forces": [vp, dp, dp, dp, vp],
         "md_batch_step": [vp, i32, i32, i32, dp, vp],
         "md_batch_set_potential": [vp, P(Potential), vp],
+        "md_set_thermostat": [vp, ctypes.c_double, ctypes.c_double],
         "md_param_grad": [vp, dp, dp, dp, vp],
         "md_num_params": [vp],
         "md_status_string": [i32],
@@ -322,6 +323,11 @@ class System:
         self._check(self.lib.md_batch_set_potential(self._h, ctypes.byref(pot), _stream()))
         self._keep = keep
         self.potential = dict(spec)
+
+    def set_thermostat(self, T_e: float, tau_T: float):
+        """Electron-phonon friction of Eq. (4) towards T_e (K) with time
+        constant tau_T (fs) in the following steps; tau_T <= 0 turns it off."""
+        self._check(self.lib.md_set_thermostat(self._h, float(T_e), float(tau_T)))
 
     @property
     def n_params(self) -> int:
