@@ -66,7 +66,9 @@ def _load():
     lib.orc_forces_pairs.restype = dbl
     lib.orc_forces_pairs.argtypes = [vp, i32, _D, _D, i64, _I, _I, _D, _D, _D, _D]
     lib.orc_md_run.restype = i64
-    lib.orc_md_run.argtypes = [vp, i32, _D, _D, _D, dbl, dbl, dbl, i32, _D, dbl, dbl]
+    lib.orc_md_run.argtypes = [vp, i32, _D, _D, _D, dbl, dbl, dbl, i32, _D, dbl, dbl, dbl, dbl, dbl, _D]
+    lib.orc_virial_pairs.restype = dbl
+    lib.orc_virial_pairs.argtypes = [vp, i32, _D, _D, i64, _I, _I]
     lib.orc_param_deriv.restype = dbl
     lib.orc_param_deriv.argtypes = [vp, i32, i32, _D, _D, i64, _I, _I, _D]
     lib.orc_param_grad.argtypes = [vp, i32, i32, _D, _D, i64, _I, _I, _D, dbl, _D]
@@ -187,17 +189,32 @@ def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs") -> 
 
 
 def md_run(pot: Potential, x, v, box, mass: float, dt: float, skin: float, n_steps: int,
-           tau_T: float = 0.0, T_e: float = 0.0) -> dict:
-    """Velocity-Verlet trajectory; returns final x, v, per-step thermo rows
-    (KE, PE, E_tot, T) and the number of list rebuilds. With tau_T > 0 the
-    electron-phonon friction of Eq. (4) couples every atom to the electronic
-    temperature T_e (K) with time constant tau_T (fs)."""
+           tau_T: float = 0.0, T_e: float = 0.0, tau_p: float = 0.0, P0: float = 0.0,
+           beta: float = 0.0) -> dict:
+    """Velocity-Verlet trajectory; returns final x, v, box, per-step thermo
+    rows (KE, PE, E_tot, T), per-step pressures (Eq. 6, eV/A^3) and the
+    number of list rebuilds. With tau_T > 0 the electron-phonon friction of
+    Eq. (4) couples every atom to the electronic temperature T_e (K) with
+    time constant tau_T (fs); with tau_p > 0 the Berendsen coupling of
+    Eq. (5) scales coordinates and box towards the pressure P0 (eV/A^3)
+    with compressibility beta (A^3/eV)."""
     lib = _load()
-    x, v, box = _f64(x).copy(), _f64(v).copy(), _f64(box)
+    x, v, box = _f64(x).copy(), _f64(v).copy(), _f64(box).copy()
     thermo = np.zeros((n_steps + 1, 4))
+    press = np.zeros(n_steps + 1)
     nreb = lib.orc_md_run(pot._h, x.shape[0], _dp(x), _dp(v), _dp(box), float(mass), float(dt), float(skin),
-                          int(n_steps), _dp(thermo), float(tau_T), float(T_e))
-    return dict(x=x, v=v, thermo=thermo, n_rebuild=int(nreb))
+                          int(n_steps), _dp(thermo), float(tau_T), float(T_e), float(tau_p), float(P0),
+                          float(beta), _dp(press))
+    return dict(x=x, v=v, box=box, thermo=thermo, pressure=press, n_rebuild=int(nreb))
+
+
+def virial(pot: Potential, x, box) -> float:
+    """Pair virial W = sum_i f_i . r_i of the forces of Eq. (3) (eV), the
+    interaction part of the pressure of Eq. (6)."""
+    lib = _load()
+    x, box = _f64(x), _f64(box)
+    pi, pj = pairs(x, box, pot.r_cut)
+    return lib.orc_virial_pairs(pot._h, x.shape[0], _dp(x), _dp(box), pi.size, _ip(pi), _ip(pj))
 
 
 def param_deriv(pot: Potential, which: int, x, box) -> tuple[float, np.ndarray]:

@@ -21,6 +21,7 @@
  *   - Verlet neighbour list with a radius beyond the force cutoff
  *     (a skin)                                                     (Sec. 4.2)
  *   - the electron-phonon friction of the temperature control      Eq. (4)
+ *   - the pair virial, the pressure and its Berendsen coupling   Eq. (5)-(6)
  *
  * Two independent routes for Eq. (1)-(3): orc_forces_brute() writes the double
  * sums out over all atom pairs (O(N^2), the definition), and
@@ -477,6 +478,41 @@ double orc_forces_pairs(const orc_pot* P, int n, const double* x, const double* 
     return E;
 }
 
+/* Virial of the forces of Eq. (3) for the pressure of Eq. (6). The sum
+ * W = sum_i f_i . r_i is written for a periodic box as a sum over pairs: the
+ * forces are pairwise, f_ij = -f_ji with f_ij = -(dE_T/dr_ij) (r_i - r_j)/r_ij
+ * (the bracket of Eq. (3) for the pair), so each pair i<j contributes
+ * f_ij . (r_i - r_j) = -(dE_T/dr_ij) r_ij. Returns W in eV. */
+double orc_virial_pairs(const orc_pot* P, int n, const double* x, const double* box, long np, const int* pi,
+                        const int* pj) {
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double rc2 = P->r_cut * P->r_cut;
+    double* rho = (double*)calloc(nn, sizeof(double));
+    double* Fp = (double*)calloc(nn, sizeof(double));
+    double d[3], phi, dphi, fr, dfr, F, Fpp;
+    for (long k = 0; k < np; ++k) {
+        int i = pi[k], j = pj[k];
+        double r2 = sep(x, i, j, box, d);
+        if (r2 >= rc2) continue;
+        pair_eval(P, sqrt(r2), &phi, &dphi, &fr, &dfr);
+        rho[i] += fr;
+        rho[j] += fr;
+    }
+    for (int i = 0; i < n; ++i) embed_eval(P, rho[i], &F, &Fp[i], &Fpp);
+    double W = 0.0;
+    for (long k = 0; k < np; ++k) {
+        int i = pi[k], j = pj[k];
+        double r2 = sep(x, i, j, box, d);
+        if (r2 >= rc2) continue;
+        double r = sqrt(r2);
+        pair_eval(P, r, &phi, &dphi, &fr, &dfr);
+        W -= (dphi + (Fp[i] + Fp[j]) * dfr) * r;
+    }
+    free(rho);
+    free(Fp);
+    return W;
+}
+
 /* ------------------------------------------------------------------ */
 /* velocity-Verlet dynamics                                            */
 /* ------------------------------------------------------------------ */
@@ -506,6 +542,16 @@ static double kinetic(int n, const double* v, double mass) {
     return 0.5 * mass * s * ORC_MVV;
 }
 
+/* Eq. (6): P = (N k_B T + W/3) / V with T the kinetic temperature (3n-3
+ * degrees of freedom) and W the pair virial over the current list. */
+static double pressure(const orc_pot* P, int n, const double* x, const double* v, const double* box, double mass,
+                       const pairbuf* B) {
+    double dof = 3.0 * n - 3.0;
+    double T = dof > 0 ? 2.0 * kinetic(n, v, mass) / (dof * ORC_KB) : 0.0;
+    double W = orc_virial_pairs(P, n, x, box, B->np, B->pi, B->pj);
+    return (n * ORC_KB * T + W / 3.0) / (box[0] * box[1] * box[2]);
+}
+
 /* Electron-phonon friction of Finnis et al. (Eq. 4): each atom feels
  * -m (1/tau) (T_i - T_e)/T_i v_i, with T_i = m v_i^2 / (3 k_B) its own
  * kinetic temperature and T_e the constant electronic temperature. On its
@@ -531,15 +577,24 @@ static void bath_half(int n, double* v, double mass, double T_e, double decay) {
  *   [friction dt/2;] v += dt/2 * f/m;  x += dt * v;  wrap x;
  *   rebuild the list (radius r_cut + skin) when some atom moved more than
  *   skin/2 since the last build;
- *   f = forces(x);  v += dt/2 * f/m[; friction dt/2].
+ *   f = forces(x);  v += dt/2 * f/m[; friction dt/2]
+ *   [; pressure P of Eq. (6); x and box scaled by mu of Eq. (5)].
  * The bracketed friction half steps (Eq. 4, symmetric splitting) run when
- * tau_T > 0, towards the electronic temperature T_e (K).
- * x, v: [n*3], updated in place. thermo (nullable): [(n_steps+1)*4] rows of
- * (kinetic, potential, total energy in eV, temperature in K with 3n-3
- * degrees of freedom), row 0 the initial state. Returns the number of list
- * builds after the initial one. */
-long orc_md_run(const orc_pot* P, int n, double* x, double* v, const double* box, double mass, double dt,
-                double skin, int n_steps, double* thermo, double tau_T, double T_e) {
+ * tau_T > 0, towards the electronic temperature T_e (K). The bracketed
+ * pressure coupling (Berendsen, Eq. 5) runs when tau_p > 0: with the
+ * instantaneous pressure P = (N k_B T + W/3)/V (T the kinetic temperature
+ * with 3n-3 degrees of freedom, W the pair virial), all coordinates and the
+ * box lengths are multiplied by mu = [1 - beta (dt/tau_p)(P0 - P)]^(1/3),
+ * beta the compressibility (A^3/eV), P0 the target (eV/A^3).
+ * x, v: [n*3], updated in place; box: [3], updated in place when the
+ * pressure is coupled. thermo (nullable): [(n_steps+1)*4] rows of (kinetic,
+ * potential, total energy in eV, temperature in K with 3n-3 degrees of
+ * freedom), row 0 the initial state, each row before that step's scaling.
+ * press (nullable): [n_steps+1] the pressure of each row (eV/A^3). Returns
+ * the number of list builds after the initial one. */
+long orc_md_run(const orc_pot* P, int n, double* x, double* v, double* box, double mass, double dt,
+                double skin, int n_steps, double* thermo, double tau_T, double T_e, double tau_p, double P0,
+                double beta, double* press) {
     const int bath = tau_T > 0.0;
     const double decay = bath ? exp(-dt / tau_T) : 1.0; /* exp(-2 (dt/2) / tau) */
     size_t nn = (size_t)(n > 0 ? n : 1);
@@ -562,6 +617,7 @@ long orc_md_run(const orc_pot* P, int n, double* x, double* v, const double* box
         thermo[2] = ke + pe;
         thermo[3] = dof > 0 ? 2.0 * ke / (dof * ORC_KB) : 0.0;
     }
+    if (press) press[0] = pressure(P, n, x, v, box, mass, &B);
     for (int s = 1; s <= n_steps; ++s) {
         if (bath) bath_half(n, v, mass, T_e, decay);
         for (int k = 0; k < 3 * n; ++k) {
@@ -593,6 +649,15 @@ long orc_md_run(const orc_pot* P, int n, double* x, double* v, const double* box
             t[1] = pe;
             t[2] = ke + pe;
             t[3] = dof > 0 ? 2.0 * ke / (dof * ORC_KB) : 0.0;
+        }
+        if (press || tau_p > 0.0) {
+            double p_now = pressure(P, n, x, v, box, mass, &B);
+            if (press) press[s] = p_now;
+            if (tau_p > 0.0) {
+                double mu = cbrt(1.0 - beta * (dt / tau_p) * (P0 - p_now));
+                for (int k = 0; k < 3 * n; ++k) x[k] *= mu;
+                for (int a = 0; a < 3; ++a) box[a] *= mu;
+            }
         }
     }
     free(B.pi);

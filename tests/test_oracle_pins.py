@@ -332,6 +332,59 @@ def test_friction_brings_a_hot_crystal_to_the_electron_temperature():
     assert out["thermo"][-1, 2] < out["thermo"][0, 2]
 
 
+# ---------------------------------------------------------------- pressure (Eq. 5-6)
+
+@pytest.mark.parametrize("case", ["rgl_cu", "rgl_ni", "sc_cu", "spline"])
+def test_virial_is_minus_the_volume_derivative(case):
+    """For a static configuration the interaction part of Eq. (6), W/(3V),
+    is -dE/dV: scaling every coordinate and the box by lambda changes V by
+    lambda^3, and dE/dlambda at 1 is -W."""
+    spec, a, n = {"rgl_cu": (I.RGL_CU, I.A_CU, 4), "rgl_ni": (I.RGL_NI, I.A_NI, 4),
+                  "sc_cu": (I.SC_CU, I.A_CU, 5), "spline": (None, I.A_CU, 4)}[case]
+    if spec is None:
+        spec = O.tabulate_spline(dict(I.RGL_CU, A=0.0855 * 1.05), n_knots=120, rho_hi=41.2)
+    bx = I.perturbed_fcc(n, a, 300.0, I.MASS_CU, seed=17)
+    pot = O.Potential(spec)
+    V = np.prod(bx.box)
+    W = O.virial(pot, bx.x, bx.box)
+    h = 1e-5
+    E = [O.forces(pot, bx.x * lam, bx.box * lam)["E"] for lam in (1 + h, 1 - h)]
+    dEdV = (E[0] - E[1]) / (2 * h) / (3 * V)
+    assert W / (3 * V) == pytest.approx(-dEdV, rel=1e-6)
+
+
+def test_pressure_of_free_atoms_is_the_ideal_gas_law():
+    x, v, box = gas()
+    out = O.md_run(O.Potential(I.RGL_CU), x, v, box, I.MASS_CU, 1.0, 0.3, 0)
+    n = len(x)
+    T = out["thermo"][0, 3]
+    assert out["pressure"][0] == pytest.approx(n * I.KB_EV_PER_K * T / np.prod(box), rel=1e-14)
+
+
+def test_barostat_drives_the_pressure_to_its_target():
+    """A Cu crystal at the fcc lattice constant is under ~2 GPa at 300 K
+    with this potential; the coupling of Eq. (5) (P0 = 0, beta = 1/140 GPa,
+    tau_p = 100 fs) expands the box until the mean pressure over the last
+    1000 of 3000 steps is zero within 1e-4 eV/A^3 (16 MPa)."""
+    bx = I.perturbed_fcc(4, I.A_CU, 300.0, I.MASS_CU, seed=1)
+    beta = 160.21766208 / 140.0
+    out = O.md_run(O.Potential(I.RGL_CU), bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 3000, tau_p=100.0, P0=0.0,
+                   beta=beta)
+    P = out["pressure"]
+    assert P[0] > 0.01
+    assert abs(P[-1000:].mean()) < 1e-4
+    assert out["box"][0] > bx.box[0] * 1.004 and np.allclose(out["box"], out["box"][0])
+
+
+def test_barostat_off_is_plain_verlet():
+    bx = I.perturbed_fcc(3, I.A_CU, 600.0, I.MASS_CU, seed=8)
+    pot = O.Potential(I.RGL_CU)
+    a = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 30)
+    b = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 30, tau_p=0.0, P0=1.0, beta=1.0)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
+    assert np.array_equal(b["box"], bx.box)
+
+
 def test_dimer_small_oscillation_period():
     """A dimer near its bond length oscillates at omega = sqrt(k/mu), with
     k = E''(r_eq) of the closed-form dimer energy and mu = m/2."""
