@@ -227,13 +227,20 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=None) -> dict:
+def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=None, thermostat=None,
+                barostat=None) -> dict:
     """atom-steps/s of a box in another precision or potential (same timing
-    rules), with its per-phase times."""
+    rules), with its per-phase times; optionally with the friction of
+    Eq. (4) (thermostat = (T_e, tau_T)) or the pressure coupling of Eq. (5)
+    (barostat = (P0, tau_p, beta))."""
     import torch
     from paper_1212_6332_gb300.md import System
     spec = spec or I.RGL_CU
     s = System(spec, box=box, n_atoms=len(x_h), skin=SKIN, dt=DT, mass=mass or I.MASS_CU, precision=precision)
+    if thermostat:
+        s.set_thermostat(*thermostat)
+    if barostat:
+        s.set_barostat(*barostat)
     s.set_state(torch.tensor(x_h, device="cuda"), torch.tensor(v_h, device="cuda"))
     s.step(W)
     torch.cuda.synchronize()
@@ -509,6 +516,9 @@ def main():
         variants["ni_2m_fp64"] = run_variant("fp64", W, K, ni.x, ni.v, ni.box, spec=I.RGL_NI, mass=I.MASS_NI)
         variants["ni_2m_mixed"] = run_variant("mixed", W, K, ni.x, ni.v, ni.box, spec=I.RGL_NI, mass=I.MASS_NI)
         del ni
+        variants["fp64_thermostat"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box, thermostat=(300.0, 100.0))
+        variants["fp64_barostat"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box,
+                                                barostat=(0.0, 1000.0, 160.21766208 / 140.0))
         variants["cu_2048_graph"] = run_small(200, True)
         variants["cu_2048_nograph"] = run_small(200, False)
         del x_dev, v_dev

@@ -254,6 +254,32 @@ MD_API int md_batch_set_potential(md_batch* b, const md_potential* pot, md_strea
  * non-finite T_e or a non-finite tau_T. */
 MD_API int md_set_thermostat(md_batch* b, double T_e, double tau_T);
 
+/* Instantaneous pressure of Eq. (6) of every box for the current state,
+ * P = (N k_B T + W/3)/V in eV/A^3 (1 eV/A^3 = 160.2177 GPa), with T the box's
+ * kinetic temperature (3N-3 degrees of freedom) and W = sum_i f_i . r_i the
+ * virial of the forces of Eq. (3), written for periodic boxes as the sum
+ * over pairs of -(dE_T/dr) r. The forces are re-evaluated with the virial
+ * (the same values). p_box: [n_boxes], host or device. Errors: MD_ERR_ARG
+ * for a NULL handle or p_box, or before any state was set. */
+MD_API int md_pressure(md_batch* b, double* p_box, md_stream stream);
+
+/* Pressure control of Eq. (5) (Berendsen et al.): after every step each
+ * box's coordinates and lengths are multiplied by
+ * mu = [1 - beta (dt/tau_p)(P0 - P)]^(1/3), P its pressure of Eq. (6) at the
+ * end of the step, P0 the target (eV/A^3) and beta the compressibility
+ * (A^3/eV) that the printed equation leaves implicit. tau_p (fs) <= 0
+ * switches it off (the default). While it is on, md_batch_step uses the
+ * tile schedule, a single box runs the batch kernels (its length lives on
+ * the device), and a step that would shrink a box below one list radius
+ * per cell (the cell grid is fixed at creation) fails with
+ * MD_ERR_UNSUPPORTED. md_get_box reads the current lengths. Errors:
+ * MD_ERR_ARG for a NULL handle, a non-finite argument, or beta <= 0 with
+ * tau_p > 0. */
+MD_API int md_set_barostat(md_batch* b, double P0, double tau_p, double beta);
+
+/* Current box lengths [n_boxes][3] (A) into a host or device array. */
+MD_API int md_get_box(md_batch* b, double* lengths, md_stream stream);
+
 /* Gradient of a scalar loss L with respect to the potential parameters
  * (RGL: A, xi, p, q, r0; spline: all knot values, V then rho then F), at
  * the batch's current positions, given g_f = dL/dF [n][3] (device, caller

@@ -214,7 +214,7 @@ void free_engine(Engine& e) {
     dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.ab); dfree(e.fv); dfree(e.rev); dfree(e.n_up); dfree(e.exp_T);
     dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
     dfree(e.grad_g); dfree(e.grad_u); dfree(e.grad_Fpp); dfree(e.grad_partial); dfree(e.grad_coef); dfree(e.stage); dfree(e.red);
-    dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box); dfree(e.due_cells);
+    dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box); dfree(e.due_cells); dfree(e.w_atom); dfree(e.red_w); dfree(e.press_box); dfree(e.mu_box);
     for (cudaEvent_t ev : e.ev_pool) cudaEventDestroy(ev);
     e.ev_pool.clear();
     if (e.ctl_host) cudaFreeHost(e.ctl_host);
@@ -627,6 +627,8 @@ int finish_sync(Engine* E, cudaStream_t s) {
     if (rc) return rc;
     if (E->ctl_host->status & kStNonFinite) return fail(E, MD_ERR_NONFINITE, "non-finite energy");
     if (E->ctl_host->status & kStOverflow) return fail(E, MD_ERR_NEIGH_OVERFLOW, "neighbour list overflow");
+    if (E->ctl_host->status & kStCellSide)
+        return fail(E, MD_ERR_UNSUPPORTED, "pressure coupling would shrink a box below one list radius per cell");
     return MD_OK;
 }
 
@@ -667,11 +669,21 @@ int set_positions(Engine* E, const double* x, const double* v, bool set_v, cudaS
 
 // ---- stepping ----
 
+// Forces, second half-kick, the pressure coupling of Eq. (5) when on, and
+// the step's bookkeeping.
+void finish_step(Engine& e, bool hist, cudaStream_t s) {
+    launch_forces(e, 1, s, e.baro.on);
+    if (e.baro.on) {
+        launch_thermo(e, s);
+        launch_pressure(e, true, s);
+    }
+    launch_end_step(e, hist ? 1 : 0, s);
+}
+
 void enqueue_step(Engine& e, bool hist, cudaStream_t s) {
     launch_kick_drift(e, s);
     launch_rebuild(e, 0, s);
-    launch_forces(e, 1, s);
-    launch_end_step(e, hist ? 1 : 0, s);
+    finish_step(e, hist, s);
 }
 
 int capture(md_batch* h, int steps, bool hist, cudaGraphExec_t* out, long long* kernels) {
@@ -747,12 +759,13 @@ int steps_impl(md_batch* h, int n, double* hist_out, bool use_graph, cudaStream_
         if ((rc = read_ctl(E, s))) return rc;
         int st = e.ctl_host->status;
         if (st & kStNonFinite) return fail(E, MD_ERR_NONFINITE, "non-finite energy");
+        if (st & kStCellSide)
+            return fail(E, MD_ERR_UNSUPPORTED, "pressure coupling would shrink a box below one list radius per cell");
         if (st & kStOverflow) {
             // the step that overflowed has drifted and re-sorted; finish it
             bool had;
             if ((rc = settle_overflow(E, s, &had))) return rc;
-            launch_forces(e, 1, s);
-            launch_end_step(e, hist ? 1 : 0, s);
+            finish_step(e, hist, s);
             CK(cudaGetLastError());
             if ((rc = read_ctl(E, s))) return rc;
         }
@@ -1100,6 +1113,74 @@ int md_set_thermostat(md_batch* b, double T_e, double tau_T) {
     bath.m_3kb = E->cfg.mass * kMVV / (3.0 * kBoltz);
     E->bath = bath;
     destroy_graphs(*E);  // captured launches carry the old parameters
+    return MD_OK;
+}
+
+static int ensure_pressure(Engine* E) {
+    Engine& e = *E;
+    if (e.w_atom) return MD_OK;
+    if (dalloc(E, &e.w_atom, (size_t)e.N_pad) || dalloc(E, &e.red_w, (size_t)std::max(e.n_chunks, 1)) ||
+        dalloc(E, &e.press_box, (size_t)e.B) || dalloc(E, &e.mu_box, (size_t)e.B))
+        return fail(E, MD_ERR_NOMEM, "cudaMalloc failed");
+    return MD_OK;
+}
+
+int md_set_barostat(md_batch* b, double P0, double tau_p, double beta) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    if (!std::isfinite(P0) || !std::isfinite(tau_p) || !std::isfinite(beta))
+        return fail(E, MD_ERR_ARG, "P0, tau_p and beta must be finite");
+    if (tau_p > 0.0 && !(beta > 0.0)) return fail(E, MD_ERR_ARG, "beta must be > 0");
+    int rc = ensure_pressure(E);
+    if (rc) return rc;
+    Baro baro{};
+    baro.on = tau_p > 0.0;
+    baro.P0 = P0;
+    baro.k = baro.on ? beta * (E->cfg.dt / tau_p) : 0.0;
+    if (E->baro.on && !baro.on && E->N) {
+        // the single-box kernels take the box from the host copy again
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(E->L_h.data(), E->L, sizeof(double) * 3 * E->B, cudaMemcpyDeviceToHost));
+    }
+    E->baro = baro;
+    destroy_graphs(*E);  // captured steps carry the old sequence
+    return MD_OK;
+}
+
+int md_pressure(md_batch* b, double* p_box, md_stream st) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    Engine& e = *E;
+    cudaStream_t s = (cudaStream_t)st;
+    if (!e.have_state) return fail(E, MD_ERR_ARG, "no state");
+    if (!p_box) return fail(E, MD_ERR_ARG, "p_box is NULL");
+    int rc = ensure_pressure(E);
+    if (rc) return rc;
+    if (e.N) {
+        launch_forces(e, 0, s, true);  // the same forces, with the virial
+        launch_thermo(e, s);
+        launch_pressure(e, false, s);
+        CK(cudaGetLastError());
+        OutDst o = out_dst(e, p_box, (size_t)e.B);
+        CK(cudaMemcpyAsync(o.dev, e.press_box, sizeof(double) * e.B, cudaMemcpyDeviceToDevice, s));
+        if ((rc = out_finish(E, o, s))) return rc;
+    } else {
+        std::vector<double> z(e.B, 0.0);
+        if (is_device_ptr(p_box))
+            CK(cudaMemcpyAsync(p_box, z.data(), sizeof(double) * e.B, cudaMemcpyHostToDevice, s));
+        else
+            std::copy(z.begin(), z.end(), p_box);
+    }
+    return finish_sync(E, s);
+}
+
+int md_get_box(md_batch* b, double* lengths, md_stream st) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    if (!lengths) return fail(E, MD_ERR_ARG, "lengths is NULL");
+    cudaStream_t s = (cudaStream_t)st;
+    CK(cudaMemcpyAsync(lengths, E->L, sizeof(double) * 3 * E->B, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
     return MD_OK;
 }
 

@@ -25,6 +25,7 @@ constexpr double kBoltz = 8.617333262e-5;  // eV/K
 constexpr int kStOverflow = 1;
 constexpr int kStNonFinite = 2;
 constexpr int kStTimeout = 4;
+constexpr int kStCellSide = 8;  // a pressure-coupled box shrank below one list radius per cell
 
 // Potential, passed by value to kernels.
 struct Pot {
@@ -88,6 +89,15 @@ struct Bath {
     double T_e;    // electronic temperature (K)
     double decay;  // exp(-2 (dt/2) / tau_T)
     double m_3kb;  // m / (3 k_B) in K per (A/fs)^2
+    int on;
+};
+
+// Berendsen pressure coupling of Eq. (5): after each step every box's
+// coordinates and lengths are scaled by mu = [1 - beta (dt/tau_p)(P0 - P)]^(1/3)
+// with P the box's instantaneous pressure of Eq. (6).
+struct Baro {
+    double P0;        // target pressure (eV/A^3)
+    double k;         // beta dt / tau_p (A^3/eV)
     int on;
 };
 
@@ -193,6 +203,11 @@ struct Engine {
     bool have_state = false;
     bool lists_ok = false;  // lists, cells and build positions agree (a state load may keep them)
     Bath bath{};            // friction of Eq. (4) applied in the kicks (md_set_thermostat)
+    Baro baro{};            // pressure coupling of Eq. (5) after each step (md_set_barostat)
+    double* w_atom = nullptr;   // [N_pad] per-atom virial -1/2 sum_j s_ij r_ij^2 (pressure users only)
+    double* red_w = nullptr;    // [n_chunks] chunk sums of w_atom
+    double* press_box = nullptr;  // [B] pressure of each box (eV/A^3)
+    double* mu_box = nullptr;     // [B] scaling factor of the last coupled step
     // CUDA graph of one step (and of a chunk of steps)
     cudaGraphExec_t graph_step = nullptr;
     cudaGraphExec_t graph_chunk = nullptr;
@@ -255,7 +270,13 @@ CellSep single_cell_sep(const Engine& e);
 void launch_rebuild(Engine& e, int mode, cudaStream_t s);
 void launch_build_list(Engine& e, int mode, cudaStream_t s);
 // density and force passes (fp64 or mixed); kick != 0 fuses v += dt/2 F/m
-void launch_forces(Engine& e, int kick, cudaStream_t s);
+void launch_forces(Engine& e, int kick, cudaStream_t s, bool virial = false);
+// A single box runs the specialised single-box kernels unless its length
+// changes on the device (pressure coupling), where the batch kernels read it.
+inline bool single_fast(const Engine& e) { return e.B == 1 && !e.baro.on; }
+// Pressure of every box from the per-atom virial of the last force pass
+// (and, when coupled, the scaling of Eq. (5)); needs launch_thermo first.
+void launch_pressure(Engine& e, bool couple, cudaStream_t s);
 void launch_kick_drift(Engine& e, cudaStream_t s);
 void launch_end_step(Engine& e, int record_hist, cudaStream_t s);
 void launch_thermo(Engine& e, cudaStream_t s);

@@ -248,12 +248,14 @@ __global__ void __launch_bounds__(kFNT) k_rho_sum(int64_t N, int64_t Np, Pot P, 
     e_atom[i] = fma(0.5, ep, F);
 }
 
-template <bool SINGLE>
+// VIR: also the per-atom virial w_i = -1/2 sum_j s_ij r_ij^2 (the pair
+// virial of Eq. (6) split evenly between the two atoms of each pair).
+template <bool SINGLE, bool VIR>
 __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, const double4_32a* __restrict__ x,
                                                 const int* __restrict__ nn, const int* __restrict__ nl, int max_nb,
                                                 const double2* __restrict__ ab, const double* __restrict__ Fp,
                                                 double* __restrict__ f, double* __restrict__ v, double c_kick,
-                                                Bath bath, const Ctl* ctl) {
+                                                Bath bath, double* __restrict__ w_atom, const Ctl* ctl) {
     if (load_status(ctl)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < N;
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
         n = min(nn[i], max_nb);
     }
     const double2 zero = make_double2(0.0, 0.0);
-    double fx = 0.0, fy = 0.0, fz = 0.0;
+    double fx = 0.0, fy = 0.0, fz = 0.0, w = 0.0;
     int k = 0;
     double2 c = n > 0 ? ab[i] : zero;
     while (true) {
@@ -291,6 +293,7 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
             fx = fma(s, dx, fx);
             fy = fma(s, dy, fy);
             fz = fma(s, dz, fz);
+            if (VIR) w = fma(s, norm2(dx, dy, dz), w);
             ++k;
             c = cn;
         }
@@ -299,6 +302,7 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
     f[i] = fx;
     f[Np + i] = fy;
     f[2 * Np + i] = fz;
+    if (VIR) w_atom[i] = -0.5 * w;
     if (v) {
         double vx = v[i] + c_kick * fx, vy = v[Np + i] + c_kick * fy, vz = v[2 * Np + i] + c_kick * fz;
         bath_half(bath, vx, vy, vz);  // friction half step after the kick
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
     }
 }
 
-void launch_forces_mixed(Engine& e, int kick, cudaStream_t s);
+void launch_forces_mixed(Engine& e, int kick, cudaStream_t s, bool virial);
 
 // float32 screen threshold: rc^2 (1 + margin), rounded up
 static float screen_r2f(double rc2) { return nextafterf((float)(rc2 * (1.0 + kScreen)), INFINITY); }
@@ -327,7 +331,7 @@ static int pair_blocks(const Engine& e) {
 }
 
 template <int KIND, bool SINGLE>
-static void run_fp64(Engine& e, int kick, cudaStream_t s) {
+static void run_fp64(Engine& e, int kick, cudaStream_t s, bool virial) {
     Geo g = make_geo(e);
     int nb = (int)((e.N + kFNT - 1) / kFNT);
     double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
@@ -344,28 +348,32 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s) {
         k_rho_sum<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.nn, e.max_nb, e.fv, e.rho, e.Fp, e.e_atom, e.ctl);
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
-    k_force<SINGLE><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.ab, e.Fp, e.f,
-                                        kick ? e.v : nullptr, c_kick, e.bath, e.ctl);
+    if (virial)
+        k_force<SINGLE, true><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.ab, e.Fp, e.f,
+                                                  kick ? e.v : nullptr, c_kick, e.bath, e.w_atom, e.ctl);
+    else
+        k_force<SINGLE, false><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.ab, e.Fp, e.f,
+                                                   kick ? e.v : nullptr, c_kick, e.bath, nullptr, e.ctl);
 }
 
 template <int KIND>
-static void run_fp64_k(Engine& e, int kick, cudaStream_t s) {
-    if (e.B == 1)
-        run_fp64<KIND, true>(e, kick, s);
+static void run_fp64_k(Engine& e, int kick, cudaStream_t s, bool virial) {
+    if (single_fast(e))
+        run_fp64<KIND, true>(e, kick, s, virial);
     else
-        run_fp64<KIND, false>(e, kick, s);
+        run_fp64<KIND, false>(e, kick, s, virial);
 }
 
-void launch_forces(Engine& e, int kick, cudaStream_t s) {
+void launch_forces(Engine& e, int kick, cudaStream_t s, bool virial) {
     if (e.N == 0) return;
     if (e.cfg.precision == MD_MIXED) {
-        launch_forces_mixed(e, kick, s);
+        launch_forces_mixed(e, kick, s, virial);
         return;
     }
     switch (e.pot.kind) {
-        case MD_POT_RGL: run_fp64_k<MD_POT_RGL>(e, kick, s); break;
-        case MD_POT_SC: run_fp64_k<MD_POT_SC>(e, kick, s); break;
-        default: run_fp64_k<MD_POT_SPLINE>(e, kick, s); break;
+        case MD_POT_RGL: run_fp64_k<MD_POT_RGL>(e, kick, s, virial); break;
+        case MD_POT_SC: run_fp64_k<MD_POT_SC>(e, kick, s, virial); break;
+        default: run_fp64_k<MD_POT_SPLINE>(e, kick, s, virial); break;
     }
 }
 

@@ -18,6 +18,8 @@ namespace mdk {
 
 constexpr int kINT = 256;
 
+static int nblk(int64_t n, int nt) { return (int)((n + nt - 1) / nt); }
+
 // Largest squared displacement per box into disp[] (non-negative doubles
 // order like their bit patterns): one atomic per block when the block's
 // atoms lie in one box, per lane where a box boundary falls inside it.
@@ -147,6 +149,88 @@ __global__ void __launch_bounds__(kRNT) k_chunk_sums(int64_t Np, const int64_t* 
     }
 }
 
+// ---- pressure (Eq. 6) and its Berendsen coupling (Eq. 5)
+
+// per-chunk sums of the per-atom virial, fixed order
+__global__ void __launch_bounds__(kRNT) k_chunk_virial(const int64_t* __restrict__ lo, const int64_t* __restrict__ hi,
+                                                       const double* __restrict__ w, double* __restrict__ part) {
+    __shared__ double sh[kRNT / 32];
+    const int c = blockIdx.x;
+    double sw = 0.0;
+    for (int64_t i = lo[c] + threadIdx.x; i < hi[c]; i += kRNT) sw += w[i];
+    const double t = block_sum<kRNT>(sw, sh);
+    if (threadIdx.x == 0) part[c] = t;
+}
+
+// Pressure of every box, P = (N k_B T + W/3)/V with T the box's kinetic
+// temperature of the thermo pass; when coupled, the factor
+// mu = [1 - beta (dt/tau_p)(P0 - P)]^(1/3). A box whose cells would fall
+// below one list radius raises kStCellSide, and then no box is scaled.
+__global__ void k_box_pressure(int B, const int* __restrict__ box_chunk_off, const int64_t* __restrict__ atom_off,
+                               const double* __restrict__ part_w, const double* __restrict__ thermo,
+                               const double* __restrict__ L, const int* __restrict__ nc, double rl, Baro baro,
+                               double* __restrict__ press, double* __restrict__ mu, Ctl* ctl) {
+    if (load_status(ctl)) return;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        double W = 0.0;
+        for (int c = box_chunk_off[b]; c < box_chunk_off[b + 1]; ++c) W += part_w[c];
+        const double n = (double)(atom_off[b + 1] - atom_off[b]);
+        const double V = L[3 * b] * L[3 * b + 1] * L[3 * b + 2];
+        const double P = (n * kBoltz * thermo[4 * b + 3] + W / 3.0) / V;
+        press[b] = P;
+        if (!baro.on) continue;
+        double m = cbrt(1.0 - baro.k * (baro.P0 - P));
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) ok = ok && L[3 * b + a] * m / nc[3 * b + a] >= rl;
+        if (!ok) {
+            atomicOr(&ctl->status, kStCellSide);
+            m = 1.0;
+        }
+        mu[b] = m;
+    }
+}
+
+// Applies the factors of k_box_pressure to the box and cell lengths (after
+// every box passed the cell check, so either all boxes scale or none).
+__global__ void k_scale_boxes(int B, const double* __restrict__ mu, double* __restrict__ L,
+                              double* __restrict__ cell_len, float* __restrict__ cell_len_f, const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        const double m = mu[b];
+        for (int a = 0; a < 3; ++a) {
+            L[3 * b + a] *= m;
+            cell_len[3 * b + a] *= m;
+            cell_len_f[3 * b + a] = (float)cell_len[3 * b + a];
+        }
+    }
+}
+
+__global__ void k_scale_atoms(int64_t N, Geo g, const double* __restrict__ mu, double4_32a* __restrict__ x,
+                              const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double m = mu[g.B == 1 ? 0 : g.atom_box[i]];
+        double4_32a p = x[i];
+        p.x *= m;
+        p.y *= m;
+        p.z *= m;
+        x[i] = p;
+    }
+}
+
+__global__ void k_scale_cells(int n_cells, Geo g, const double* __restrict__ mu, double4_32a* __restrict__ org,
+                              const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
+        const double m = mu[g.cell_box[c]];
+        double4_32a o = org[c];
+        o.x *= m;
+        o.y *= m;
+        o.z *= m;
+        org[c] = o;
+    }
+}
+
 // per-box and total (ke, pe, etot, T); optional history row
 __global__ void __launch_bounds__(1024) k_thermo_final(int B, const int* __restrict__ box_chunk_off,
                                                        const int64_t* __restrict__ atom_off,
@@ -202,10 +286,30 @@ static void kick_drift_t(Engine& e, cudaStream_t s) {
 
 void launch_kick_drift(Engine& e, cudaStream_t s) {
     if (e.N == 0) return;
-    if (e.B == 1)
+    if (single_fast(e))
         kick_drift_t<true>(e, s);
     else
         kick_drift_t<false>(e, s);
+}
+
+void launch_pressure(Engine& e, bool couple, cudaStream_t s) {
+    if (e.N == 0) return;
+    PhaseScope scope(e, MD_PHASE_OTHER, s);
+    Baro b = e.baro;
+    b.on = couple && e.baro.on;
+    e.launches += b.on ? 5 : 2;
+    k_chunk_virial<<<e.n_chunks, kRNT, 0, s>>>(e.chunk_lo, e.chunk_hi, e.w_atom, e.red_w);
+    k_box_pressure<<<std::max(1, std::min((e.B + 255) / 256, 64)), 256, 0, s>>>(
+        e.B, e.box_chunk_off, e.atom_off, e.red_w, e.thermo_dev, e.L, e.nc, e.rl, b, e.press_box, e.mu_box, e.ctl);
+    if (b.on) {
+        Geo g = make_geo(e);
+        k_scale_boxes<<<std::max(1, std::min((e.B + 255) / 256, 64)), 256, 0, s>>>(e.B, e.mu_box, e.L, e.cell_len,
+                                                                                  e.cell_len_f, e.ctl);
+        k_scale_atoms<<<(int)std::min<int64_t>(nblk(e.N, 256), (int64_t)8 * e.n_sm), 256, 0, s>>>(e.N, g, e.mu_box,
+                                                                                                   e.x, e.ctl);
+        k_scale_cells<<<std::max(1, std::min(nblk(e.n_cells, 256), 8 * e.n_sm)), 256, 0, s>>>(e.n_cells, g, e.mu_box,
+                                                                                              e.cell_org, e.ctl);
+    }
 }
 
 void launch_end_step(Engine& e, int record_hist, cudaStream_t s) {
@@ -369,7 +473,6 @@ __global__ void k_reset_perm(int64_t N, int* __restrict__ perm, int* __restrict_
     iperm[t] = (int)t;
 }
 
-static int nblk(int64_t n, int nt) { return (int)((n + nt - 1) / nt); }
 
 void launch_load_positions(Engine& e, const double* src, cudaStream_t s) {
     if (e.N == 0) return;
@@ -380,7 +483,7 @@ void launch_load_positions(Engine& e, const double* src, cudaStream_t s) {
 void launch_load_positions_keep(Engine& e, const double* src, cudaStream_t s) {
     if (e.N == 0) return;
     e.launches += 1;
-    if (e.B == 1)
+    if (single_fast(e))
         k_load_pos_keep<true><<<nblk(e.N, kINT), kINT, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x, e.xb, e.xo,
                                                              e.cell_t, e.ctl, e.disp_box);
     else

@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
                                                       const int* __restrict__ nl, int max_nb,
                                                       const float* __restrict__ Fpf, double* __restrict__ f,
                                                       double* __restrict__ e_atom, double* __restrict__ v,
-                                                      double c_kick, Bath bath, const Ctl* ctl) {
+                                                      double c_kick, Bath bath, double* __restrict__ w_atom,
+                                                      const Ctl* ctl) {
     if (load_status(ctl)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -65,13 +66,16 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
     const float4 oi = xo[i];
     const float Fpi = Fpf[i];
     const int n = min(nn[i], max_nb);
-    GSum ax, ay, az, ae;
+    // w_atom (pressure users only): per-atom virial -1/2 sum_j s_ij r_ij^2
+    const bool vir = w_atom != nullptr;
+    GSum ax, ay, az, ae, aw;
     for (int k = 0; k < n; ++k) {
         if ((k & kGroupMask) == 0 && k) {
             ax.flush();
             ay.flush();
             az.flush();
             ae.flush();
+            if (vir) aw.flush();
         }
         int j = entry_slot(nl[(int64_t)k * Np + i]);
         float dx, dy, dz;
@@ -87,6 +91,7 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
             ay.add(s * dy);
             az.add(s * dz);
             ae.add(phi);
+            if (vir) aw.add(s * r2);
         }
     }
     double fx = ax.value(), fy = ay.value(), fz = az.value();
@@ -94,6 +99,7 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
     f[Np + i] = fy;
     f[2 * Np + i] = fz;
     e_atom[i] += 0.5 * ae.value();
+    if (vir) w_atom[i] = -0.5 * aw.value();
     if (v) {
         double vx = v[i] + c_kick * fx, vy = v[Np + i] + c_kick * fy, vz = v[2 * Np + i] + c_kick * fz;
         bath_half(bath, vx, vy, vz);  // friction half step after the kick
@@ -119,7 +125,7 @@ CellSep single_cell_sep(const Engine& e) {
 }
 
 template <int KIND, bool SINGLE, bool WIDE>
-static void run_mixed(Engine& e, int kick, cudaStream_t s) {
+static void run_mixed(Engine& e, int kick, cudaStream_t s, bool virial) {
     Geo g = make_geo(e);
     const CellSep cs = single_cell_sep(e);
     int nb = (int)((e.N + kMNT - 1) / kMNT);
@@ -132,22 +138,23 @@ static void run_mixed(Engine& e, int kick, cudaStream_t s) {
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     k_force_mixed<KIND, SINGLE, WIDE><<<nb, kMNT, 0, s>>>(e.N, e.N_pad, g, cs, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.Fpf,
-                                                   e.f, e.e_atom, kick ? e.v : nullptr, c_kick, e.bath, e.ctl);
+                                                   e.f, e.e_atom, kick ? e.v : nullptr, c_kick, e.bath,
+                                                   virial ? e.w_atom : nullptr, e.ctl);
 }
 
 template <int KIND>
-static void run_mixed_k(Engine& e, int kick, cudaStream_t s) {
-    if (e.B == 1)
-        e.wide ? run_mixed<KIND, true, true>(e, kick, s) : run_mixed<KIND, true, false>(e, kick, s);
+static void run_mixed_k(Engine& e, int kick, cudaStream_t s, bool virial) {
+    if (single_fast(e))
+        e.wide ? run_mixed<KIND, true, true>(e, kick, s, virial) : run_mixed<KIND, true, false>(e, kick, s, virial);
     else
-        e.wide ? run_mixed<KIND, false, true>(e, kick, s) : run_mixed<KIND, false, false>(e, kick, s);
+        e.wide ? run_mixed<KIND, false, true>(e, kick, s, virial) : run_mixed<KIND, false, false>(e, kick, s, virial);
 }
 
-void launch_forces_mixed(Engine& e, int kick, cudaStream_t s) {
+void launch_forces_mixed(Engine& e, int kick, cudaStream_t s, bool virial) {
     switch (e.pot.kind) {
-        case MD_POT_RGL: run_mixed_k<MD_POT_RGL>(e, kick, s); break;
-        case MD_POT_SC: run_mixed_k<MD_POT_SC>(e, kick, s); break;
-        default: run_mixed_k<MD_POT_SPLINE>(e, kick, s); break;
+        case MD_POT_RGL: run_mixed_k<MD_POT_RGL>(e, kick, s, virial); break;
+        case MD_POT_SC: run_mixed_k<MD_POT_SC>(e, kick, s, virial); break;
+        default: run_mixed_k<MD_POT_SPLINE>(e, kick, s, virial); break;
     }
 }
 

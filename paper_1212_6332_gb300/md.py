@@ -25,7 +25,7 @@ STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_NOMEM", 4: "
 SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_neighbors", "md_get_neighbors",
            "md_max_count", "md_compute_forces", "md_get_forces", "md_step", "md_get_thermo", "md_batch_create",
            "md_batch_destroy", "md_batch_set_state", "md_batch_get_state", "md_batch_compute_forces",
-           "md_batch_step", "md_batch_set_potential", "md_set_thermostat", "md_param_grad", "md_num_params", "md_status_string",
+           "md_batch_step", "md_batch_set_potential", "md_set_thermostat", "md_pressure", "md_set_barostat", "md_get_box", "md_param_grad", "md_num_params", "md_status_string",
            "md_last_error", "md_profile_start", "md_profile_read",
            "md_eval_math", "md_forces_noalloc", "md_batch_thermo",
            "md_batch_schedule")
@@ -98,6 +98,9 @@ def load(path: str | pathlib.Path | None = None) -> ctypes.CDLL:
         "md_batch_step": [vp, i32, i32, i32, dp, vp],
         "md_batch_set_potential": [vp, P(Potential), vp],
         "md_set_thermostat": [vp, ctypes.c_double, ctypes.c_double],
+        "md_pressure": [vp, vp, vp],
+        "md_set_barostat": [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+        "md_get_box": [vp, vp, vp],
         "md_param_grad": [vp, dp, dp, dp, vp],
         "md_num_params": [vp],
         "md_status_string": [i32],
@@ -323,6 +326,26 @@ class System:
         self._check(self.lib.md_batch_set_potential(self._h, ctypes.byref(pot), _stream()))
         self._keep = keep
         self.potential = dict(spec)
+
+    def pressure(self):
+        """Instantaneous pressure of Eq. (6) of every box (eV/A^3), a device
+        tensor of one value per box."""
+        out = self._empty(self.n_boxes)
+        self._check(self.lib.md_pressure(self._h, _ptr(out), _stream()))
+        return out
+
+    def set_barostat(self, P0: float, tau_p: float, beta: float):
+        """Berendsen coupling of Eq. (5) towards P0 (eV/A^3) with time
+        constant tau_p (fs) and compressibility beta (A^3/eV); tau_p <= 0
+        turns it off."""
+        self._check(self.lib.md_set_barostat(self._h, float(P0), float(tau_p), float(beta)))
+
+    def box(self):
+        """Current box lengths, [n_boxes][3] numpy array (A)."""
+        import numpy as np
+        out = np.zeros((self.n_boxes, 3))
+        self._check(self.lib.md_get_box(self._h, out.ctypes.data_as(ctypes.c_void_p), _stream()))
+        return out
 
     def set_thermostat(self, T_e: float, tau_T: float):
         """Electron-phonon friction of Eq. (4) towards T_e (K) with time
