@@ -54,6 +54,9 @@ def _load():
     lib.orc_pot_new.restype = vp
     lib.orc_pot_new.argtypes = [i32, _D, dbl, dbl, i32, i32, i32, _D, dbl, dbl, dbl, dbl]
     lib.orc_pot_free.argtypes = [vp]
+    lib.orc_pot_new_alloy.restype = vp
+    lib.orc_pot_new_alloy.argtypes = [i32, i32, i32, _D, dbl, dbl, dbl, dbl]
+    lib.orc_pot_set_types.argtypes = [vp, _I]
     lib.orc_pot_eval.argtypes = [vp, i32, _D, _D, _D, _D, _D]
     lib.orc_embed_eval.argtypes = [vp, i32, _D, _D, _D, _D]
     lib.orc_wrap.argtypes = [i32, _D, _D]
@@ -92,7 +95,10 @@ class Potential:
     """Oracle-side potential. ``spec`` is a dict like
     ``{"kind": "rgl", "A":..., "xi":..., "p":..., "q":..., "r0":..., "r_taper":..., "r_cut":...}``,
     ``{"kind": "sc", "eps", "c", "a", "n", "m", "r_taper", "r_cut"}`` or
-    ``{"kind": "spline", "phi": knots, "f": knots, "F": knots, "r_lo", "r_hi", "rho_lo", "rho_hi"}``."""
+    ``{"kind": "spline", "phi": knots, "f": knots, "F": knots, "r_lo", "r_hi", "rho_lo", "rho_hi"}`` or,
+    for several species, ``{"kind": "alloy", "n_types": T, "phi": [V^(ab) knots per type pair],
+    "f": [rho^(ab) knots per type pair], "F": [F^(a) knots per type], "r_lo", "r_hi", "rho_lo",
+    "rho_hi"}`` with the type pairs a <= b in row-major order ((0,0), (0,1), ..., (1,1), ...)."""
 
     def __init__(self, spec: dict):
         lib = _load()
@@ -118,12 +124,39 @@ class Potential:
             rho_lo, rho_hi = float(spec["rho_lo"]), float(spec["rho_hi"])
             r_taper = r_cut = r_hi
             self.n_param = n_phi + n_f + n_F
+        elif kind == "alloy":
+            T = int(spec["n_types"])
+            phi = [_f64(a) for a in spec["phi"]]
+            f = [_f64(a) for a in spec["f"]]
+            F = [_f64(a) for a in spec["F"]]
+            if len(phi) != T * (T + 1) // 2 or len(f) != len(phi) or len(F) != T:
+                raise ValueError("alloy: T(T+1)/2 pair tables and T embedding tables")
+            knots = np.concatenate(phi + f + F)
+            r_lo, r_hi = float(spec["r_lo"]), float(spec["r_hi"])
+            rho_lo, rho_hi = float(spec["rho_lo"]), float(spec["rho_hi"])
+            r_cut = r_hi
+            self.n_param = knots.size
+            self.r_cut = r_cut
+            self.n_types = T
+            self._prm, self._knots = prm, knots
+            self._h = lib.orc_pot_new_alloy(T, len(phi[0]), len(F[0]), _dp(knots), r_lo, r_hi, rho_lo, rho_hi)
+            return
         else:
             raise ValueError(kind)
         self.r_cut = r_cut
+        self.n_types = 1
         self._prm, self._knots = prm, knots
         self._h = lib.orc_pot_new(KIND[kind], _dp(prm), r_taper, r_cut, n_phi, n_f, n_F, _dp(knots),
                                   r_lo, r_hi, rho_lo, rho_hi)
+
+    def use_types(self, types):
+        """Per-atom species for the following calls (None: all species 0)."""
+        if types is None:
+            self._types = None
+            _load().orc_pot_set_types(self._h, None)
+            return
+        self._types = np.ascontiguousarray(types, dtype=np.int32)
+        _load().orc_pot_set_types(self._h, self._types.ctypes.data_as(_I))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -168,10 +201,12 @@ def pairs(x, box, rl: float, method: str = "cells") -> tuple[np.ndarray, np.ndar
         cap = int(np_)
 
 
-def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs") -> dict:
+def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs", types=None) -> dict:
     """Energies and forces of Eq. (1)-(3). method "pairs" uses the half list
-    within r_cut + skin and Newton's third law; "brute" the O(N^2) double sums."""
+    within r_cut + skin and Newton's third law; "brute" the O(N^2) double
+    sums. types: per-atom species for an alloy potential."""
     lib = _load()
+    pot.use_types(types)
     x, box = _f64(x), _f64(box)
     n = x.shape[0]
     rho = np.zeros(n)
@@ -190,7 +225,7 @@ def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs") -> 
 
 def md_run(pot: Potential, x, v, box, mass: float, dt: float, skin: float, n_steps: int,
            tau_T: float = 0.0, T_e: float = 0.0, tau_p: float = 0.0, P0: float = 0.0,
-           beta: float = 0.0) -> dict:
+           beta: float = 0.0, types=None) -> dict:
     """Velocity-Verlet trajectory; returns final x, v, box, per-step thermo
     rows (KE, PE, E_tot, T), per-step pressures (Eq. 6, eV/A^3) and the
     number of list rebuilds. With tau_T > 0 the electron-phonon friction of
@@ -199,6 +234,7 @@ def md_run(pot: Potential, x, v, box, mass: float, dt: float, skin: float, n_ste
     Eq. (5) scales coordinates and box towards the pressure P0 (eV/A^3)
     with compressibility beta (A^3/eV)."""
     lib = _load()
+    pot.use_types(types)
     x, v, box = _f64(x).copy(), _f64(v).copy(), _f64(box).copy()
     thermo = np.zeros((n_steps + 1, 4))
     press = np.zeros(n_steps + 1)
@@ -208,10 +244,11 @@ def md_run(pot: Potential, x, v, box, mass: float, dt: float, skin: float, n_ste
     return dict(x=x, v=v, box=box, thermo=thermo, pressure=press, n_rebuild=int(nreb))
 
 
-def virial(pot: Potential, x, box) -> float:
+def virial(pot: Potential, x, box, types=None) -> float:
     """Pair virial W = sum_i f_i . r_i of the forces of Eq. (3) (eV), the
     interaction part of the pressure of Eq. (6)."""
     lib = _load()
+    pot.use_types(types)
     x, box = _f64(x), _f64(box)
     pi, pj = pairs(x, box, pot.r_cut)
     return lib.orc_virial_pairs(pot._h, x.shape[0], _dp(x), _dp(box), pi.size, _ip(pi), _ip(pj))

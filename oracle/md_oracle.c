@@ -138,7 +138,24 @@ typedef struct {
     double prm[8];
     double r_taper, r_cut;
     spline sp_phi, sp_f, sp_F;
+    /* several species (splines only, Eq. 1-3 with the type labels a, b):
+     * V^(ab) and rho^(ab) for each unordered pair a <= b (symmetric, as the
+     * common factor (F'_i + F'_j) of Eq. (3) requires), F^(a) for each type;
+     * one species uses sp_phi, sp_f, sp_F */
+    int n_types;
+    spline *aphi, *af, *aF;
+    const int* types; /* per-atom species of the current call (orc_pot_set_types) */
 } orc_pot;
+
+/* index of the unordered type pair (a, b), a, b < T: row-major upper triangle */
+static int pair_index(int T, int a, int b) {
+    if (a > b) {
+        int t = a;
+        a = b;
+        b = t;
+    }
+    return a * T - a * (a - 1) / 2 + (b - a);
+}
 
 orc_pot* orc_pot_new(int kind, const double* prm, double r_taper, double r_cut, int n_phi, int n_f, int n_F,
                      const double* knots, double r_lo, double r_hi, double rho_lo, double rho_hi) {
@@ -168,18 +185,82 @@ orc_pot* orc_pot_new(int kind, const double* prm, double r_taper, double r_cut, 
         P->r_cut = r_hi;
         P->r_taper = r_hi;
     }
+    P->n_types = 1;
+    P->aphi = &P->sp_phi;
+    P->af = &P->sp_f;
+    P->aF = &P->sp_F;
     return P;
 }
 
+static void spline_from(spline* s, int n, const double* y, double t0, double t_end) {
+    s->n = n;
+    s->y = (double*)malloc(sizeof(double) * (size_t)n);
+    s->m = (double*)malloc(sizeof(double) * (size_t)n);
+    memcpy(s->y, y, sizeof(double) * (size_t)n);
+    s->t0 = t0;
+    s->h = (t_end - t0) / (n - 1);
+    spline_setup(s);
+}
+
+/* Spline potential of n_types species. knots: V^(ab) for the P = T(T+1)/2
+ * unordered pairs in pair_index order (n_r values each over [r_lo, r_hi]),
+ * then rho^(ab) for the same pairs, then F^(a) for each type (n_rho values
+ * each over [rho_lo, rho_hi]). r_cut = r_hi. */
+orc_pot* orc_pot_new_alloy(int n_types, int n_r, int n_rho, const double* knots, double r_lo, double r_hi,
+                           double rho_lo, double rho_hi) {
+    orc_pot* P = (orc_pot*)calloc(1, sizeof(orc_pot));
+    int np = n_types * (n_types + 1) / 2;
+    P->kind = ORC_SPLINE;
+    P->r_cut = r_hi;
+    P->r_taper = r_hi;
+    P->n_types = n_types;
+    P->aphi = (spline*)calloc((size_t)np, sizeof(spline));
+    P->af = (spline*)calloc((size_t)np, sizeof(spline));
+    P->aF = (spline*)calloc((size_t)n_types, sizeof(spline));
+    const double* src = knots;
+    for (int k = 0; k < np; ++k, src += n_r) spline_from(&P->aphi[k], n_r, src, r_lo, r_hi);
+    for (int k = 0; k < np; ++k, src += n_r) spline_from(&P->af[k], n_r, src, r_lo, r_hi);
+    for (int k = 0; k < n_types; ++k, src += n_rho) spline_from(&P->aF[k], n_rho, src, rho_lo, rho_hi);
+    /* the single-species fields mirror the (0, 0) tables for the callers
+     * that ask for a table without types */
+    P->sp_phi = P->aphi[0];
+    P->sp_f = P->af[0];
+    P->sp_F = P->aF[0];
+    return P;
+}
+
+/* the per-atom species used by the following force calls (NULL: all 0);
+ * the array stays owned by the caller */
+void orc_pot_set_types(orc_pot* P, const int* types) { P->types = types; }
+
 void orc_pot_free(orc_pot* P) {
     if (!P) return;
-    if (P->kind == ORC_SPLINE) {
+    if (P->kind == ORC_SPLINE && P->n_types > 1) {
+        int np = P->n_types * (P->n_types + 1) / 2;
+        for (int k = 0; k < np; ++k) {
+            free(P->aphi[k].y); free(P->aphi[k].m);
+            free(P->af[k].y); free(P->af[k].m);
+        }
+        for (int k = 0; k < P->n_types; ++k) {
+            free(P->aF[k].y); free(P->aF[k].m);
+        }
+        free(P->aphi);
+        free(P->af);
+        free(P->aF);
+    } else if (P->kind == ORC_SPLINE) {
         free(P->sp_phi.y); free(P->sp_phi.m);
         free(P->sp_f.y); free(P->sp_f.m);
         free(P->sp_F.y); free(P->sp_F.m);
     }
     free(P);
 }
+
+/* type-pair table of atoms i, j and type of atom i for the current types */
+static int ptype(const orc_pot* P, int i, int j) {
+    if (P->n_types <= 1 || !P->types) return 0;
+    return pair_index(P->n_types, P->types[i], P->types[j]);
+}
+static int atype(const orc_pot* P, int i) { return P->n_types <= 1 || !P->types ? 0 : P->types[i]; }
 
 /* C2 smoothstep taper and its derivative */
 static void taper(double r, double rs, double rc, double* S, double* dS) {
@@ -201,7 +282,7 @@ static void taper(double r, double rs, double rc, double* S, double* dS) {
 }
 
 /* pair function V (phi) and density function rho (f), with r-derivatives */
-static void pair_eval(const orc_pot* P, double r, double* phi, double* dphi, double* f, double* df) {
+static void pair_eval(const orc_pot* P, int pt, double r, double* phi, double* dphi, double* f, double* df) {
     if (r >= P->r_cut) {
         *phi = *dphi = *f = *df = 0.0;
         return;
@@ -227,15 +308,15 @@ static void pair_eval(const orc_pot* P, double r, double* phi, double* dphi, dou
         *df = am * (-m / r * S + dS);
     } else {
         double d2;
-        spline_eval(&P->sp_phi, r, phi, dphi, &d2);
-        spline_eval(&P->sp_f, r, f, df, &d2);
+        spline_eval(&P->aphi[pt], r, phi, dphi, &d2);
+        spline_eval(&P->af[pt], r, f, df, &d2);
     }
 }
 
 /* embedding function F(rho), F'(rho), F''(rho) */
-static void embed_eval(const orc_pot* P, double rho, double* F, double* Fp, double* Fpp) {
+static void embed_eval(const orc_pot* P, int a, double rho, double* F, double* Fp, double* Fpp) {
     if (P->kind == ORC_SPLINE) {
-        spline_eval(&P->sp_F, rho, F, Fp, Fpp);
+        spline_eval(&P->aF[a], rho, F, Fp, Fpp);
         return;
     }
     if (rho <= 0.0) {
@@ -250,11 +331,11 @@ static void embed_eval(const orc_pot* P, double rho, double* F, double* Fp, doub
 }
 
 void orc_pot_eval(const orc_pot* P, int n, const double* r, double* phi, double* dphi, double* f, double* df) {
-    for (int k = 0; k < n; ++k) pair_eval(P, r[k], phi + k, dphi + k, f + k, df + k);
+    for (int k = 0; k < n; ++k) pair_eval(P, 0, r[k], phi + k, dphi + k, f + k, df + k);
 }
 
 void orc_embed_eval(const orc_pot* P, int n, const double* rho, double* F, double* Fp, double* Fpp) {
-    for (int k = 0; k < n; ++k) embed_eval(P, rho[k], F + k, Fp + k, Fpp + k);
+    for (int k = 0; k < n; ++k) embed_eval(P, 0, rho[k], F + k, Fp + k, Fpp + k);
 }
 
 /* ------------------------------------------------------------------ */
@@ -385,19 +466,19 @@ double orc_forces_brute(const orc_pot* P, int n, const double* x, const double* 
             if (j == i) continue;
             double r2 = sep(x, i, j, box, d);
             if (r2 >= rc2) continue;
-            pair_eval(P, sqrt(r2), &phi, &dphi, &f, &df);
+            pair_eval(P, ptype(P, i, j), sqrt(r2), &phi, &dphi, &f, &df);
             rho[i] += f;
         }
     /* E_i = F(rho_i) + 1/2 sum_{j != i} V(r_ij);  E_T = sum_i E_i */
     double E = 0.0;
     for (int i = 0; i < n; ++i) {
-        embed_eval(P, rho[i], &F, &Fp[i], &Fpp);
+        embed_eval(P, atype(P, i), rho[i], &F, &Fp[i], &Fpp);
         double e = F;
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
             double r2 = sep(x, i, j, box, d);
             if (r2 >= rc2) continue;
-            pair_eval(P, sqrt(r2), &phi, &dphi, &f, &df);
+            pair_eval(P, ptype(P, i, j), sqrt(r2), &phi, &dphi, &f, &df);
             e += 0.5 * phi;
         }
         if (e_out) e_out[i] = e;
@@ -412,7 +493,7 @@ double orc_forces_brute(const orc_pot* P, int n, const double* x, const double* 
                 double r2 = sep(x, i, j, box, d); /* d = x_j - x_i = -r_ij */
                 if (r2 >= rc2) continue;
                 double r = sqrt(r2);
-                pair_eval(P, r, &phi, &dphi, &f, &df);
+                pair_eval(P, ptype(P, i, j), r, &phi, &dphi, &f, &df);
                 double w = (Fp[i] + Fp[j]) * df + dphi;
                 for (int a = 0; a < 3; ++a) fi[a] -= w * (-d[a]) / r;
             }
@@ -442,12 +523,12 @@ double orc_forces_pairs(const orc_pot* P, int n, const double* x, const double* 
         int i = pi[k], j = pj[k];
         double r2 = sep(x, i, j, box, d);
         if (r2 >= rc2) continue;
-        pair_eval(P, sqrt(r2), &phi, &dphi, &fr, &dfr);
+        pair_eval(P, ptype(P, i, j), sqrt(r2), &phi, &dphi, &fr, &dfr);
         rho[i] += fr;
         rho[j] += fr;
     }
     for (int i = 0; i < n; ++i) {
-        embed_eval(P, rho[i], &F, &Fp[i], &Fpp);
+        embed_eval(P, atype(P, i), rho[i], &F, &Fp[i], &Fpp);
         e[i] = F;
     }
     for (long k = 0; k < np; ++k) {
@@ -455,7 +536,7 @@ double orc_forces_pairs(const orc_pot* P, int n, const double* x, const double* 
         double r2 = sep(x, i, j, box, d);
         if (r2 >= rc2) continue;
         double r = sqrt(r2);
-        pair_eval(P, r, &phi, &dphi, &fr, &dfr);
+        pair_eval(P, ptype(P, i, j), r, &phi, &dphi, &fr, &dfr);
         e[i] += 0.5 * phi;
         e[j] += 0.5 * phi;
         double s = dphi + (Fp[i] + Fp[j]) * dfr; /* dE_T / dr for this pair */
@@ -494,18 +575,18 @@ double orc_virial_pairs(const orc_pot* P, int n, const double* x, const double* 
         int i = pi[k], j = pj[k];
         double r2 = sep(x, i, j, box, d);
         if (r2 >= rc2) continue;
-        pair_eval(P, sqrt(r2), &phi, &dphi, &fr, &dfr);
+        pair_eval(P, ptype(P, i, j), sqrt(r2), &phi, &dphi, &fr, &dfr);
         rho[i] += fr;
         rho[j] += fr;
     }
-    for (int i = 0; i < n; ++i) embed_eval(P, rho[i], &F, &Fp[i], &Fpp);
+    for (int i = 0; i < n; ++i) embed_eval(P, atype(P, i), rho[i], &F, &Fp[i], &Fpp);
     double W = 0.0;
     for (long k = 0; k < np; ++k) {
         int i = pi[k], j = pj[k];
         double r2 = sep(x, i, j, box, d);
         if (r2 >= rc2) continue;
         double r = sqrt(r2);
-        pair_eval(P, r, &phi, &dphi, &fr, &dfr);
+        pair_eval(P, ptype(P, i, j), r, &phi, &dphi, &fr, &dfr);
         W -= (dphi + (Fp[i] + Fp[j]) * dfr) * r;
     }
     free(rho);

@@ -385,6 +385,96 @@ def test_barostat_off_is_plain_verlet():
     assert np.array_equal(b["box"], bx.box)
 
 
+# ---------------------------------------------------------------- several species (Eq. 1-3 with types)
+
+RGL_CUNI = dict(kind="rgl", A=0.5 * (0.0855 + 0.0376), xi=np.sqrt(1.224 * 1.070), p=0.5 * (10.960 + 16.999),
+                q=0.5 * (2.278 + 1.189), r0=0.5 * (2.5562 + 2.4911), r_taper=4.5, r_cut=5.0)
+
+
+def cuni_alloy(n_knots=150, rho_hi=45.0):
+    """Binary alloy tables: RGL Cu for (0, 0), RGL Ni (with the Cu taper) for
+    (1, 1), parameter means for (0, 1); F = -sqrt(rho) for both types."""
+    ni = dict(I.RGL_NI, r_taper=4.5, r_cut=5.0)
+    tabs = [O.tabulate_spline(sp, n_knots=n_knots, rho_hi=rho_hi) for sp in (I.RGL_CU, RGL_CUNI, ni)]
+    return dict(kind="alloy", n_types=2, phi=[t["phi"] for t in tabs], f=[t["f"] for t in tabs],
+                F=[tabs[0]["F"], tabs[2]["F"] * 0.9], r_lo=tabs[0]["r_lo"], r_hi=tabs[0]["r_hi"],
+                rho_lo=0.0, rho_hi=rho_hi)
+
+
+def alloy_box(seed=4):
+    bx = I.perturbed_fcc(4, 3.57, 300.0, I.MASS_CU, seed=seed)
+    types = np.random.default_rng(seed).integers(0, 2, bx.n)
+    return bx, types
+
+
+def test_alloy_with_identical_tables_equals_one_species():
+    sp = O.tabulate_spline(I.RGL_CU, n_knots=100, rho_hi=41.2)
+    al = dict(kind="alloy", n_types=3, phi=[sp["phi"]] * 6, f=[sp["f"]] * 6, F=[sp["F"]] * 3, r_lo=sp["r_lo"],
+              r_hi=sp["r_hi"], rho_lo=sp["rho_lo"], rho_hi=sp["rho_hi"])
+    bx = I.perturbed_fcc(4, I.A_CU, 300.0, I.MASS_CU, seed=1)
+    one = O.forces(O.Potential(sp), bx.x, bx.box)
+    many = O.forces(O.Potential(al), bx.x, bx.box, types=np.arange(bx.n) % 3)
+    assert one["E"] == many["E"] and np.array_equal(one["f"], many["f"])
+
+
+def test_alloy_half_list_equals_double_sums():
+    bx, t = alloy_box()
+    pot = O.Potential(cuni_alloy())
+    a = O.forces(pot, bx.x, bx.box, types=t)
+    b = O.forces(pot, bx.x, bx.box, method="brute", types=t)
+    assert a["E"] == pytest.approx(b["E"], rel=1e-13)
+    assert np.abs(a["f"] - b["f"]).max() < 1e-12
+    assert np.allclose(a["rho"], b["rho"], rtol=1e-13)
+
+
+def test_alloy_forces_are_minus_energy_gradient():
+    bx, t = alloy_box(seed=6)
+    pot = O.Potential(cuni_alloy())
+    f = O.forces(pot, bx.x, bx.box, types=t)["f"]
+    h = 1e-4  # central differences: O(h^2) truncation, roundoff of E ~ 1e3 eV
+    for i, a in [(0, 0), (17, 1), (100, 2), (255, 0)]:
+        xp, xm = bx.x.copy(), bx.x.copy()
+        xp[i, a] += h
+        xm[i, a] -= h
+        fd = -(O.forces(pot, xp, bx.box, types=t)["E"] - O.forces(pot, xm, bx.box, types=t)["E"]) / (2 * h)
+        assert f[i, a] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_alloy_dimer_closed_form():
+    """An isolated a-b pair: E = V^(ab)(r) + F_a(rho^(ab)(r)) + F_b(rho^(ab)(r))
+    and the force on each atom is -dE/dr along the bond, with every table
+    taken as scipy's natural cubic spline of the same knots."""
+    import scipy.interpolate as interp
+    al = cuni_alloy()
+    pot = O.Potential(al)
+    t = np.linspace(al["r_lo"], al["r_hi"], len(al["phi"][0]))
+    tF = np.linspace(al["rho_lo"], al["rho_hi"], len(al["F"][0]))
+    V = interp.CubicSpline(t, al["phi"][1], bc_type="natural")
+    R = interp.CubicSpline(t, al["f"][1], bc_type="natural")
+    Fa = interp.CubicSpline(tF, al["F"][0], bc_type="natural")
+    Fb = interp.CubicSpline(tF, al["F"][1], bc_type="natural")
+    box = np.array([30.0, 30.0, 30.0])
+    for r in (2.3, 2.7, 3.4, 4.7):
+        x = np.array([[10.0, 10.0, 10.0], [10.0 + r, 10.0, 10.0]])
+        out = O.forces(pot, x, box, types=np.array([0, 1]))
+        rho = R(r)
+        E = V(r) + Fa(rho) + Fb(rho)
+        dE = V(r, 1) + (Fa(rho, 1) + Fb(rho, 1)) * R(r, 1)
+        assert out["E"] == pytest.approx(E, rel=1e-12)
+        assert out["f"][1, 0] == pytest.approx(-dE, rel=1e-10, abs=1e-12)
+        assert out["f"][0, 0] == pytest.approx(dE, rel=1e-10, abs=1e-12)
+
+
+def test_alloy_relabelling_species_changes_nothing():
+    bx, t = alloy_box(seed=9)
+    al = cuni_alloy()
+    sw = dict(al, phi=al["phi"][::-1], f=al["f"][::-1], F=al["F"][::-1])
+    a = O.forces(O.Potential(al), bx.x, bx.box, types=t)
+    b = O.forces(O.Potential(sw), bx.x, bx.box, types=1 - t)
+    assert a["E"] == pytest.approx(b["E"], rel=1e-14)
+    assert np.abs(a["f"] - b["f"]).max() < 1e-13
+
+
 def test_dimer_small_oscillation_period():
     """A dimer near its bond length oscillates at omega = sqrt(k/mu), with
     k = E''(r_eq) of the closed-form dimer energy and mu = m/2."""
