@@ -225,10 +225,10 @@ def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs", typ
 
 def md_run(pot: Potential, x, v, box, mass: float, dt: float, skin: float, n_steps: int,
            tau_T: float = 0.0, T_e: float = 0.0, tau_p: float = 0.0, P0: float = 0.0,
-           beta: float = 0.0, types=None) -> dict:
+           beta: float = 0.0, types=None, want_pressure: bool = False) -> dict:
     """Velocity-Verlet trajectory; returns final x, v, box, per-step thermo
-    rows (KE, PE, E_tot, T), per-step pressures (Eq. 6, eV/A^3) and the
-    number of list rebuilds. With tau_T > 0 the electron-phonon friction of
+    rows (KE, PE, E_tot, T), per-step pressures (Eq. 6, eV/A^3; when
+    want_pressure or tau_p > 0, else None) and the number of list rebuilds. With tau_T > 0 the electron-phonon friction of
     Eq. (4) couples every atom to the electronic temperature T_e (K) with
     time constant tau_T (fs); with tau_p > 0 the Berendsen coupling of
     Eq. (5) scales coordinates and box towards the pressure P0 (eV/A^3)
@@ -237,10 +237,11 @@ def md_run(pot: Potential, x, v, box, mass: float, dt: float, skin: float, n_ste
     pot.use_types(types)
     x, v, box = _f64(x).copy(), _f64(v).copy(), _f64(box).copy()
     thermo = np.zeros((n_steps + 1, 4))
-    press = np.zeros(n_steps + 1)
+    # per-step pressures only when asked for or coupled (each costs a virial pass)
+    press = np.zeros(n_steps + 1) if (want_pressure or tau_p > 0.0) else None
     nreb = lib.orc_md_run(pot._h, x.shape[0], _dp(x), _dp(v), _dp(box), float(mass), float(dt), float(skin),
                           int(n_steps), _dp(thermo), float(tau_T), float(T_e), float(tau_p), float(P0),
-                          float(beta), _dp(press))
+                          float(beta), _dp(press) if press is not None else None)
     return dict(x=x, v=v, box=box, thermo=thermo, pressure=press, n_rebuild=int(nreb))
 
 

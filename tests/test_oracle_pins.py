@@ -355,7 +355,7 @@ def test_virial_is_minus_the_volume_derivative(case):
 
 def test_pressure_of_free_atoms_is_the_ideal_gas_law():
     x, v, box = gas()
-    out = O.md_run(O.Potential(I.RGL_CU), x, v, box, I.MASS_CU, 1.0, 0.3, 0)
+    out = O.md_run(O.Potential(I.RGL_CU), x, v, box, I.MASS_CU, 1.0, 0.3, 0, want_pressure=True)
     n = len(x)
     T = out["thermo"][0, 3]
     assert out["pressure"][0] == pytest.approx(n * I.KB_EV_PER_K * T / np.prod(box), rel=1e-14)
