@@ -228,7 +228,7 @@ def run_reference(args):
 
 
 def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=None, thermostat=None,
-                barostat=None) -> dict:
+                barostat=None, types=None) -> dict:
     """atom-steps/s of a box in another precision or potential (same timing
     rules), with its per-phase times; optionally with the friction of
     Eq. (4) (thermostat = (T_e, tau_T)) or the pressure coupling of Eq. (5)
@@ -237,6 +237,8 @@ def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=N
     from paper_1212_6332_gb300.md import System
     spec = spec or I.RGL_CU
     s = System(spec, box=box, n_atoms=len(x_h), skin=SKIN, dt=DT, mass=mass or I.MASS_CU, precision=precision)
+    if types is not None:
+        s.set_types(types)
     if thermostat:
         s.set_thermostat(*thermostat)
     if barostat:
@@ -395,6 +397,32 @@ def spline_model(spec: dict) -> dict:
     return dict(kind="spline", phi=pair[0], f=pair[1], F=F, r_lo=1.5, r_hi=5.0, rho_lo=0.0, rho_hi=2 * rho_eq)
 
 
+def alloy_model() -> dict:
+    """Two-species spline model tabulated by the library itself (as
+    spline_model): RGL Cu for the (0, 0) pair, RGL Ni with the Cu taper for
+    (1, 1), the parameter means for (0, 1); V and rho on 200 knots over
+    [1.5, 5.0] A, F = -sqrt(rho) for both species on 200 knots over [0, 45]."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    cuni = dict(kind="rgl", A=0.5 * (0.0855 + 0.0376), xi=float(np.sqrt(1.224 * 1.070)), p=0.5 * (10.960 + 16.999),
+                q=0.5 * (2.278 + 1.189), r0=0.5 * (2.5562 + 2.4911), r_taper=4.5, r_cut=5.0)
+    r = np.linspace(1.5, 5.0, 200)
+    phi, f = [], []
+    for spec in (I.RGL_CU, cuni, dict(I.RGL_NI, r_taper=4.5, r_cut=5.0)):
+        d = System(spec, box=[20.0, 20.0, 20.0], n_atoms=2, skin=0.0, mass=I.MASS_CU)
+        v, rho = np.zeros(200), np.zeros(200)
+        for k, rk in enumerate(r):
+            xx = np.array([[1.0, 1.0, 1.0], [1.0 + rk, 1.0, 1.0]])
+            o = d.compute_forces(torch.tensor(xx, device="cuda"))
+            rho[k] = o["rho"][0].item()
+            v[k] = o["e_atom"].sum().item() + 2.0 * np.sqrt(rho[k])
+        d.close()
+        phi.append(v)
+        f.append(rho)
+    F = -np.sqrt(np.linspace(0.0, 45.0, 200))
+    return dict(kind="alloy", n_types=2, phi=phi, f=f, F=[F, F], r_lo=1.5, r_hi=5.0, rho_lo=0.0, rho_hi=45.0)
+
+
 def spec_f_scale(spec: dict) -> float:
     return spec["c"] * spec["eps"] if spec["kind"] == "sc" else 1.0
 
@@ -519,6 +547,12 @@ def main():
         variants["fp64_thermostat"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box, thermostat=(300.0, 100.0))
         variants["fp64_barostat"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box,
                                                 barostat=(0.0, 1000.0, 160.21766208 / 140.0))
+        al = I.perturbed_fcc(args.cells, 3.57, TEMP, I.MASS_CU, 5)
+        al_types = np.random.default_rng(5).integers(0, 2, al.n).astype(np.int32)
+        al_spec = alloy_model()
+        variants["alloy_cuni_fp64"] = run_variant("fp64", W, K, al.x, al.v, al.box, spec=al_spec, types=al_types)
+        variants["alloy_cuni_mixed"] = run_variant("mixed", W, K, al.x, al.v, al.box, spec=al_spec, types=al_types)
+        del al
         variants["cu_2048_graph"] = run_small(200, True)
         variants["cu_2048_nograph"] = run_small(200, False)
         del x_dev, v_dev

@@ -102,6 +102,15 @@ typedef struct md_potential {
     int n_phi, n_f, n_F;   /* spline knot counts, each >= 4 */
     double r_lo, r_hi;     /* spline V and rho range */
     double rho_lo, rho_hi; /* spline F range */
+    int n_types;           /* species (splines only; 0 or 1: one). With T > 1
+                              species, Eq. (1)-(3) with type labels: V^(ab)
+                              and rho^(ab) per unordered type pair a <= b
+                              (symmetric, as the common factor (F'_i + F'_j)
+                              of Eq. (3) requires) and F^(a) per type; knots
+                              then hold the T(T+1)/2 V tables (pairs in
+                              row-major order (0,0), (0,1), ..., (1,1), ...,
+                              n_phi values each), the rho tables (n_f each)
+                              and the T F tables (n_F each). At most 4. */
 } md_potential;
 
 /* Run configuration. box[] is used by md_create only (md_batch_create takes
@@ -253,6 +262,14 @@ MD_API int md_batch_set_potential(md_batch* b, const md_potential* pot, md_strea
  * precisions. Errors: MD_ERR_ARG for a NULL handle, a negative or
  * non-finite T_e or a non-finite tau_T. */
 MD_API int md_set_thermostat(md_batch* b, double T_e, double tau_T);
+
+/* Species of every atom, types [n] in caller order (host or device), each
+ * in [0, n_types) of the potential; all atoms are species 0 until set.
+ * Applies to the current state at once (forces are re-evaluated) and to
+ * later state loads. Several species run the tile schedule; their
+ * parameter adjoint is not provided (MD_ERR_UNSUPPORTED). Errors:
+ * MD_ERR_ARG for a NULL handle or array or a type out of range. */
+MD_API int md_set_types(md_batch* b, const int32_t* types, md_stream stream);
 
 /* Instantaneous pressure of Eq. (6) of every box for the current state,
  * P = (N k_B T + W/3)/V in eV/A^3 (1 eV/A^3 = 160.2177 GPa), with T the box's

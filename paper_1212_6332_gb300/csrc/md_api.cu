@@ -107,6 +107,8 @@ int check_potential(const md_potential* p, std::string& why) {
         }
         return MD_OK;
     }
+    if (p->n_types < 0 || p->n_types > 4) return why = "n_types must be 0..4", MD_ERR_ARG;
+    if (p->n_types > 1 && p->kind != MD_POT_SPLINE) return why = "several species need spline tables", MD_ERR_ARG;
     if (p->kind == MD_POT_SPLINE) {
         if (!p->knots) return why = "spline knots are NULL", MD_ERR_ARG;
         if (p->n_phi < 4 || p->n_f < 4 || p->n_F < 4) return why = "each spline needs >= 4 knots", MD_ERR_ARG;
@@ -121,24 +123,33 @@ int check_potential(const md_potential* p, std::string& why) {
 
 double pot_cutoff(const md_potential* p) { return p->kind == MD_POT_SPLINE ? p->r_hi : p->r_cut; }
 
+// species, type-pair tables and knot values of a potential
+static int pot_types(const md_potential& p) { return p.kind == MD_POT_SPLINE && p.n_types > 1 ? p.n_types : 1; }
+static int pot_pairs(const md_potential& p) { return pot_types(p) * (pot_types(p) + 1) / 2; }
+static size_t knot_count(const md_potential& p) {
+    return (size_t)pot_pairs(p) * (p.n_phi + p.n_f) + (size_t)pot_types(p) * p.n_F;
+}
+
 void fill_pot(Engine& e) {
     const md_potential& p = e.pot_host;
     Pot P{};
     P.kind = p.kind;
+    P.n_types = pot_types(p);
     if (p.kind == MD_POT_SPLINE) {
         P.rc = p.r_hi;
         P.rs = p.r_hi;
         P.inv_w = 0.0;
         int ns[3] = {p.n_phi, p.n_f, p.n_F};
+        int ntab[3] = {pot_pairs(p), pot_pairs(p), pot_types(p)};  // tables of V, rho, F
         double lo[3] = {p.r_lo, p.r_lo, p.rho_lo}, hi[3] = {p.r_hi, p.r_hi, p.rho_hi};
-        int off = 0;
+        size_t off = 0;
         for (int w = 0; w < 3; ++w) {
             P.sp[w] = e.spline_coef + off;
             P.sn[w] = ns[w];
             P.st0[w] = lo[w];
             P.sh[w] = (hi[w] - lo[w]) / (ns[w] - 1);
             P.sinvh[w] = 1.0 / P.sh[w];
-            off += ns[w];
+            off += (size_t)ntab[w] * ns[w];
         }
     } else {
         P.rc = p.r_cut;
@@ -214,7 +225,7 @@ void free_engine(Engine& e) {
     dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.ab); dfree(e.fv); dfree(e.rev); dfree(e.n_up); dfree(e.exp_T);
     dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
     dfree(e.grad_g); dfree(e.grad_u); dfree(e.grad_Fpp); dfree(e.grad_partial); dfree(e.grad_coef); dfree(e.stage); dfree(e.red);
-    dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box); dfree(e.due_cells); dfree(e.w_atom); dfree(e.red_w); dfree(e.press_box); dfree(e.mu_box);
+    dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box); dfree(e.types); dfree(e.due_cells); dfree(e.w_atom); dfree(e.red_w); dfree(e.press_box); dfree(e.mu_box);
     for (cudaEvent_t ev : e.ev_pool) cudaEventDestroy(ev);
     e.ev_pool.clear();
     if (e.ctl_host) cudaFreeHost(e.ctl_host);
@@ -226,7 +237,7 @@ int upload_potential(md_batch* h, cudaStream_t s) {
     Engine& e = *E;
     fill_pot(e);
     if (e.pot_host.kind == MD_POT_SPLINE) {
-        size_t nk = (size_t)e.pot_host.n_phi + e.pot_host.n_f + e.pot_host.n_F;
+        size_t nk = knot_count(e.pot_host);
         CK(cudaMemcpyAsync(e.knots_dev, e.knots_host.data(), nk * sizeof(double), cudaMemcpyHostToDevice, s));
         launch_spline_setup(e, s);
         CK(cudaGetLastError());
@@ -268,7 +279,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     e.cfg = *cfg;
     e.pot_host = *pot;
     if (pot->kind == MD_POT_SPLINE) {
-        size_t nk = (size_t)pot->n_phi + pot->n_f + pot->n_F;
+        size_t nk = knot_count(*pot);
         e.knots_host.assign(pot->knots, pot->knots + nk);
         e.pot_host.knots = nullptr;
     }
@@ -361,7 +372,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
 
     int rc = MD_OK;
     size_t Np = (size_t)e.N_pad;
-    size_t nk = (size_t)pot->n_phi + pot->n_f + pot->n_F;
+    size_t nk = knot_count(*pot);
 #define AL(p, n) \
     if ((rc = dalloc(E, &(p), (n))) != MD_OK) goto fail_alloc;
     AL(e.L, 3 * B);
@@ -418,6 +429,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.thermo_dev, 4 * (B + 1));
     AL(e.ctl, 1);
     AL(e.disp_box, B);
+    AL(e.types, std::max<size_t>(Np, 1));
     AL(e.due_cells, tot);
 #undef AL
     if (cudaMallocHost((void**)&e.ctl_host, sizeof(Ctl)) != cudaSuccess) {
@@ -432,6 +444,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
         };
         cudaError_t ce = cudaSuccess;
         ce = ce != cudaSuccess ? ce : up(e.L, box, 3 * B * sizeof(double));
+        ce = ce != cudaSuccess ? ce : cudaMemset(e.types, 0, sizeof(int) * std::max<size_t>(Np, 1));
         ce = ce != cudaSuccess ? ce : up(e.cell_len, cl.data(), 3 * B * sizeof(double));
         ce = ce != cudaSuccess ? ce : up(e.cell_len_f, clf.data(), 3 * B * sizeof(float));
         ce = ce != cudaSuccess ? ce : up(e.nc, e.nc_h.data(), 3 * B * sizeof(int));
@@ -1147,6 +1160,35 @@ int md_set_barostat(md_batch* b, double P0, double tau_p, double beta) {
     return MD_OK;
 }
 
+int md_set_types(md_batch* b, const int32_t* types, md_stream st) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    Engine& e = *E;
+    cudaStream_t s = (cudaStream_t)st;
+    if (e.N && !types) return fail(E, MD_ERR_ARG, "types is NULL");
+    if (!e.N) return MD_OK;
+    const int T = pot_types(e.pot_host);
+    std::vector<int32_t> h((size_t)e.N);
+    if (is_device_ptr(types)) {
+        CK(cudaMemcpyAsync(h.data(), types, sizeof(int32_t) * e.N, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        std::copy(types, types + e.N, h.begin());
+    }
+    for (int64_t k = 0; k < e.N; ++k)
+        if (h[k] < 0 || h[k] >= T) return fail(E, MD_ERR_ARG, "type out of range for the potential's species");
+    CK(cudaMemcpyAsync(e.types, h.data(), sizeof(int32_t) * e.N, cudaMemcpyHostToDevice, s));
+    if (e.have_state) {
+        launch_apply_types(e, s);
+        launch_forces(e, 0, s);
+        launch_thermo(e, s);
+        CK(cudaGetLastError());
+        return finish_sync(E, s);
+    }
+    CK(cudaStreamSynchronize(s));
+    return MD_OK;
+}
+
 int md_pressure(md_batch* b, double* p_box, md_stream st) {
     if (!b) return MD_ERR_ARG;
     Engine* E = &b->e;
@@ -1194,12 +1236,12 @@ int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream st) {
     if (pot->kind != o.kind) return fail(E, MD_ERR_ARG, "potential kind differs");
     if (pot->kind == MD_POT_SPLINE &&
         (pot->n_phi != o.n_phi || pot->n_f != o.n_f || pot->n_F != o.n_F || pot->r_lo != o.r_lo ||
-         pot->r_hi != o.r_hi))
+         pot->r_hi != o.r_hi || pot_types(*pot) != pot_types(o)))
         return fail(E, MD_ERR_ARG, "spline knot counts or range differ");
     if (pot_cutoff(pot) > pot_cutoff(&o)) return fail(E, MD_ERR_ARG, "cutoff may not grow");
     E->pot_host = *pot;
     if (pot->kind == MD_POT_SPLINE) {
-        size_t nk = (size_t)pot->n_phi + pot->n_f + pot->n_F;
+        size_t nk = knot_count(*pot);
         E->knots_host.assign(pot->knots, pot->knots + nk);
         E->pot_host.knots = nullptr;
     }
@@ -1220,6 +1262,7 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
     cudaStream_t s = (cudaStream_t)st;
     if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
     if (E->pot_host.kind == MD_POT_SC) return fail(E, MD_ERR_UNSUPPORTED, "no gradient for Sutton-Chen");
+    if (pot_types(E->pot_host) > 1) return fail(E, MD_ERR_UNSUPPORTED, "no gradient for several species");
     if (!grad || !is_device_ptr(grad)) return fail(E, MD_ERR_ARG, "grad must be a device pointer");
     if (E->N && (!g_f || !is_device_ptr(g_f))) return fail(E, MD_ERR_ARG, "g_f must be a device pointer");
     if (g_e && !is_device_ptr(g_e)) return fail(E, MD_ERR_ARG, "g_e must be a device pointer");

@@ -345,9 +345,9 @@ static size_t box_smem(int atoms, int cells) {
 constexpr size_t kBoxSmemMax = 200 * 1024;
 
 bool box_schedule_fits(const Engine& e) {
-    // float64 only; the pressure coupling scales boxes between steps, which
-    // the in-block step loop does not do
-    if (e.cfg.precision != MD_FP64 || e.baro.on) return false;
+    // float64 and one species only; the pressure coupling scales boxes
+    // between steps, which the in-block step loop does not do
+    if (e.cfg.precision != MD_FP64 || e.baro.on || e.pot.n_types > 1) return false;
     for (int b = 0; b < e.B; ++b) {
         int nb = (int)(e.atom_off_h[b + 1] - e.atom_off_h[b]);
         int ncl = e.cell_off_h[b + 1] - e.cell_off_h[b];

@@ -59,6 +59,23 @@ __device__ __forceinline__ int make_entry(int j, int sx, int sy, int sz) {
     return (int)((unsigned)j | (code << kSlotBits));
 }
 
+// Species: the type of an atom rides in the w lane of its position (an
+// exact small integer), and in bits 30-31 of the packed cell coordinates of
+// its float32 offset; the tables of a type pair are in row-major upper
+// triangle order.
+__device__ __forceinline__ int pos_type(const double4_32a& p) { return (int)p.w; }
+__device__ __forceinline__ int off_type(const float4& o) { return (int)((unsigned)__float_as_int(o.w) >> 30); }
+__device__ __forceinline__ int pair_table(int T, int a, int b) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo * T - lo * (lo - 1) / 2 + (hi - lo);
+}
+// type-pair table of two atoms from their float32 offsets (splines only)
+template <int KIND>
+__device__ __forceinline__ int species_pair(const Pot& P, const float4& oi, const float4& oj) {
+    if (KIND != MD_POT_SPLINE || P.n_types <= 1) return 0;
+    return pair_table(P.n_types, off_type(oi), off_type(oj));
+}
+
 __device__ __forceinline__ double image_shift(unsigned c2, double L) {
     return c2 == 1u ? 0.0 : (c2 == 0u ? -L : L);
 }
@@ -127,7 +144,7 @@ __device__ __forceinline__ float4 cell_local(const Geo& g, int b, int gc, double
         double d = pc[a] - c[a] * g.cell_len[3 * b + a];
         o[a] = (float)minimg(d, L, 0.5 * L);
     }
-    return make_float4(o[0], o[1], o[2], __int_as_float(xyz));
+    return make_float4(o[0], o[1], o[2], __int_as_float(xyz | (pos_type(p) << 30)));
 }
 
 // The (de-duplicated) 27-cell stencil of cell (cx, cy, cz) of box b, as
@@ -277,10 +294,12 @@ __device__ __forceinline__ void taper(const Pot& P, double r, double& S, double&
     dS = x2 * (-30.0 + x * (60.0 - 30.0 * x)) * P.inv_w;
 }
 
-__device__ __forceinline__ void spline_eval(const Pot& P, int w, double t, double& v, double& dv) {
+// Spline w (0: V, 1: rho, 2: F) of table tab (a type pair for V and rho,
+// a type for F): every table of w has n = P.sn[w] coefficient entries.
+__device__ __forceinline__ void spline_eval(const Pot& P, int w, double t, double& v, double& dv, int tab = 0) {
     double s = (t - P.st0[w]) * P.sinvh[w];
     int n = P.sn[w];
-    const double4_32a* c = P.sp[w];
+    const double4_32a* c = P.sp[w] + (int64_t)tab * n;
     if (s < 0.0) {
         double4_32a c0 = c[0];
         v = c0.x + (t - P.st0[w]) * c0.y;
@@ -321,7 +340,7 @@ __device__ __forceinline__ double powr(double b, double e) {
 // shared memory.
 template <int KIND>
 __device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict__ T, double r2, double& phi,
-                                          double& fr, double& A, double& B) {
+                                          double& fr, double& A, double& B, int pt = 0) {
     double rinv = rsqrt_nr(r2);
     double r = r2 * rinv;
     // pairs inside r_taper (r^2 <= r_taper^2) skip the taper (S = 1, S' = 0);
@@ -367,8 +386,8 @@ __device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict
             return;
         }
         double dphi, dfr;
-        spline_eval(P, 0, r, phi, dphi);
-        spline_eval(P, 1, r, fr, dfr);
+        spline_eval(P, 0, r, phi, dphi, pt);
+        spline_eval(P, 1, r, fr, dfr, pt);
         A = dphi * rinv;
         B = dfr * rinv;
     }
@@ -382,9 +401,9 @@ __device__ __forceinline__ void load_exp_table(double* sT, const double* __restr
 
 // F(rho) and F'(rho); F = F' = 0 for rho <= 0 (RGL, SC)
 template <int KIND>
-__device__ __forceinline__ void embed(const Pot& P, double rho, double& F, double& Fp) {
+__device__ __forceinline__ void embed(const Pot& P, double rho, double& F, double& Fp, int a = 0) {
     if (KIND == MD_POT_SPLINE) {
-        spline_eval(P, 2, rho, F, Fp);
+        spline_eval(P, 2, rho, F, Fp, a);
     } else {
         if (rho <= 0.0) {
             F = 0.0;
@@ -425,12 +444,11 @@ __device__ __forceinline__ float powrf(float b, float e) {
     return powf(b, e);
 }
 
-__device__ __forceinline__ void spline_evalf(const Pot& P, int w, float t, float& v, float& dv) {
+__device__ __forceinline__ void spline_evalf(const Pot& P, int w, float t, float& v, float& dv, int tab = 0) {
     // spline tables stay float64; evaluation rounds them to float32
-    double vd, dvd;
     float s = (t - (float)P.st0[w]) * (float)P.sinvh[w];
     int n = P.sn[w];
-    const double4_32a* c = P.sp[w];
+    const double4_32a* c = P.sp[w] + (int64_t)tab * n;
     if (s < 0.0f) {
         double4_32a c0 = c[0];
         v = (float)c0.x + (t - (float)P.st0[w]) * (float)c0.y;
@@ -450,12 +468,10 @@ __device__ __forceinline__ void spline_evalf(const Pot& P, int w, float t, float
     float c0 = (float)ck.x, c1 = (float)ck.y, c2 = (float)ck.z, c3 = (float)ck.w;
     v = c0 + u * (c1 + u * (c2 + u * c3));
     dv = c1 + u * (2.0f * c2 + 3.0f * u * c3);
-    (void)vd;
-    (void)dvd;
 }
 
 template <int KIND>
-__device__ __forceinline__ float dens_ff(const Pot& P, float r) {
+__device__ __forceinline__ float dens_ff(const Pot& P, float r, int pt = 0) {
     if (KIND == MD_POT_RGL) {
         float S, dS;
         taperf(P, r, S, dS);
@@ -467,14 +483,14 @@ __device__ __forceinline__ float dens_ff(const Pot& P, float r) {
     } else {
         if (r >= (float)P.rc) return 0.0f;
         float v, dv;
-        spline_evalf(P, 1, r, v, dv);
+        spline_evalf(P, 1, r, v, dv, pt);
         return v;
     }
 }
 
 template <int KIND>
 __device__ __forceinline__ void pair_allf(const Pot& P, float r, float& phi, float& dphi, float& fr,
-                                          float& dfr) {
+                                          float& dfr, int pt = 0) {
     if (KIND == MD_POT_RGL) {
         float S, dS;
         taperf(P, r, S, dS);
@@ -499,8 +515,8 @@ __device__ __forceinline__ void pair_allf(const Pot& P, float r, float& phi, flo
             phi = dphi = fr = dfr = 0.0f;
             return;
         }
-        spline_evalf(P, 0, r, phi, dphi);
-        spline_evalf(P, 1, r, fr, dfr);
+        spline_evalf(P, 0, r, phi, dphi, pt);
+        spline_evalf(P, 1, r, fr, dfr, pt);
     }
 }
 

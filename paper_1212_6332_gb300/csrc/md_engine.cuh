@@ -29,6 +29,7 @@ constexpr int kStCellSide = 8;  // a pressure-coupled box shrank below one list 
 
 // Potential, passed by value to kernels.
 struct Pot {
+    int n_types;  // species (splines): V, rho tables per type pair, F per type
     int kind;
     double rc, rc2, rs, inv_w;  // cutoff, taper start, 1/(rc - rs); rs >= rc: hard cut
     double rs2;                 // rs^2: pairs with r^2 <= rs2 have S = 1
@@ -204,6 +205,7 @@ struct Engine {
     bool lists_ok = false;  // lists, cells and build positions agree (a state load may keep them)
     Bath bath{};            // friction of Eq. (4) applied in the kicks (md_set_thermostat)
     Baro baro{};            // pressure coupling of Eq. (5) after each step (md_set_barostat)
+    int* types = nullptr;   // [N] species of each atom, caller order (md_set_types; 0 by default)
     double* w_atom = nullptr;   // [N_pad] per-atom virial -1/2 sum_j s_ij r_ij^2 (pressure users only)
     double* red_w = nullptr;    // [n_chunks] chunk sums of w_atom
     double* press_box = nullptr;  // [B] pressure of each box (eV/A^3)
@@ -288,6 +290,7 @@ void launch_spline_setup(Engine& e, cudaStream_t s);
 void launch_load_positions(Engine& e, const double* src_caller, cudaStream_t s);
 void launch_load_positions_keep(Engine& e, const double* src_caller, cudaStream_t s);
 void launch_after_load(Engine& e, cudaStream_t s);
+void launch_apply_types(Engine& e, cudaStream_t s);
 void launch_load_velocities(Engine& e, const double* src_caller, cudaStream_t s);
 void launch_store_vec(Engine& e, const double* soa_or_null, const double4_32a* x4_or_null, double* dst_caller,
                       cudaStream_t s);

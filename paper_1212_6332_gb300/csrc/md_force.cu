@@ -53,6 +53,7 @@ struct PairQueue {
     double d[3][2][kQueue];    // separation x_j - x_i, per axis and region
     long long own[2][kQueue];  // slot of the entry in i's list
     long long mir[2][kQueue];  // slot of the mirror entry in j's list
+    int pt[2][kQueue];         // type-pair table (several species)
 };
 
 template <int KIND>
@@ -60,7 +61,8 @@ __device__ __forceinline__ void eval_queued(const Pot& P, const PairQueue& q, in
                                             double2* __restrict__ ab, double2* __restrict__ fv) {
     const double r2 = norm2(q.d[0][r][p], q.d[1][r][p], q.d[2][r][p]);
     double2 c = make_double2(0.0, 0.0), w = make_double2(0.0, 0.0);
-    if (below(r2, P.rc2)) pair_eval<KIND>(P, P.exp_T, r2, w.y, w.x, c.x, c.y);
+    const int pt = KIND == MD_POT_SPLINE ? q.pt[r][p] : 0;
+    if (below(r2, P.rc2)) pair_eval<KIND>(P, P.exp_T, r2, w.y, w.x, c.x, c.y, pt);
     const long long own = q.own[r][p], mir = q.mir[r][p];
     ab[own] = c;
     fv[own] = w;
@@ -143,6 +145,9 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
             double dx = 0.0, dy = 0.0, dz = 0.0;
             const long long own = (long long)k * Np + i;
             const long long mir = (long long)cur.rv * Np + entry_slot(cur.e);
+            const int pt = KIND == MD_POT_SPLINE && P.n_types > 1
+                               ? pair_table(P.n_types, pos_type(xi), pos_type(cur.xj))
+                               : 0;
             if (cur.upper) {
                 float fx, fy, fz;
                 sep_mixed<false>(cs, oi, cur.oj, fx, fy, fz);
@@ -171,6 +176,7 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
                     q.d[2][r][p] = dz;
                     q.own[r][p] = own;
                     q.mir[r][p] = mir;
+                    if (KIND == MD_POT_SPLINE) q.pt[r][p] = pt;
                 }
                 qn[r] += __popc(m);
             }
@@ -212,7 +218,8 @@ __device__ __forceinline__ bool is_zero2(double2 c) {
 
 template <int KIND>
 __global__ void __launch_bounds__(kFNT) k_rho_sum(int64_t N, int64_t Np, Pot P, const int* __restrict__ nn,
-                                                  int max_nb, const double2* __restrict__ fv, double* __restrict__ rho,
+                                                  int max_nb, const double2* __restrict__ fv,
+                                                  const double4_32a* __restrict__ x, double* __restrict__ rho,
                                                   double* __restrict__ Fp, double* __restrict__ e_atom,
                                                   const Ctl* ctl) {
     if (load_status(ctl)) return;
@@ -242,7 +249,7 @@ __global__ void __launch_bounds__(kFNT) k_rho_sum(int64_t N, int64_t Np, Pot P, 
     }
     if (!active) return;
     double F, Fpi;
-    embed<KIND>(P, r_i, F, Fpi);
+    embed<KIND>(P, r_i, F, Fpi, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0);
     rho[i] = r_i;
     Fp[i] = Fpi;
     e_atom[i] = fma(0.5, ep, F);
@@ -345,7 +352,8 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s, bool virial) {
     }
     {
         PhaseScope scope(e, MD_PHASE_DENSITY, s);
-        k_rho_sum<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.nn, e.max_nb, e.fv, e.rho, e.Fp, e.e_atom, e.ctl);
+        k_rho_sum<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.nn, e.max_nb, e.fv, e.x, e.rho, e.Fp, e.e_atom,
+                                            e.ctl);
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     if (virial)

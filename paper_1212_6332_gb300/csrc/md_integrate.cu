@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
         // of the offsets allows for
         const double4_32a org = g.cell_org[cell_t[i]];
         xo[i] = make_float4((float)(p.x - org.x), (float)(p.y - org.y), (float)(p.z - org.z),
-                            __int_as_float((int)__double_as_longlong(org.w)));
+                            __int_as_float((int)__double_as_longlong(org.w) | (pos_type(p) << 30)));
     }
     record_disp<SINGLE>(g, N, b, d2, disp);
 }
@@ -347,7 +347,7 @@ void launch_reset_ctl(Engine& e, cudaStream_t s) {
 // ---------------------------------------------------------------- copies
 
 __global__ void k_load_pos(int64_t N, const double* __restrict__ src, const int* __restrict__ iperm, Geo g,
-                           double4_32a* __restrict__ x, Ctl* ctl) {
+                           const int* __restrict__ types, double4_32a* __restrict__ x, Ctl* ctl) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     if (!isfinite(src[3 * c]) || !isfinite(src[3 * c + 1]) || !isfinite(src[3 * c + 2]))
@@ -358,7 +358,7 @@ __global__ void k_load_pos(int64_t N, const double* __restrict__ src, const int*
     p.x = wrap_coord(src[3 * c], g.L[3 * b]);
     p.y = wrap_coord(src[3 * c + 1], g.L[3 * b + 1]);
     p.z = wrap_coord(src[3 * c + 2], g.L[3 * b + 2]);
-    p.w = 0.0;
+    p.w = (double)types[c];  // the species rides in the pad lane
     x[t] = p;
 }
 
@@ -373,8 +373,8 @@ __global__ void __launch_bounds__(kINT) k_load_pos_keep(int64_t N, const double*
                                                         const int* __restrict__ iperm, Geo g,
                                                         double4_32a* __restrict__ x,
                                                         const double4_32a* __restrict__ xb, float4* __restrict__ xo,
-                                                        const int* __restrict__ cell_t, Ctl* ctl,
-                                                        unsigned long long* __restrict__ disp) {
+                                                        const int* __restrict__ cell_t, const int* __restrict__ types,
+                                                        Ctl* ctl, unsigned long long* __restrict__ disp) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double d2 = 0.0;
     int b = -1;
@@ -395,10 +395,11 @@ __global__ void __launch_bounds__(kINT) k_load_pos_keep(int64_t N, const double*
             const double e = pa[a] - qa[a];
             d2 = fma(e, e, d2);
         }
-        x[t] = make_double4_32a(pa[0], pa[1], pa[2], 0.0);
+        const int ty = types[c];
+        x[t] = make_double4_32a(pa[0], pa[1], pa[2], (double)ty);
         const double4_32a org = g.cell_org[cell_t[t]];
         xo[t] = make_float4((float)(pa[0] - org.x), (float)(pa[1] - org.y), (float)(pa[2] - org.z),
-                            __int_as_float((int)__double_as_longlong(org.w)));
+                            __int_as_float((int)__double_as_longlong(org.w) | (ty << 30)));
     }
     record_disp<SINGLE>(g, N, b, d2, disp);
 }
@@ -477,7 +478,7 @@ __global__ void k_reset_perm(int64_t N, int* __restrict__ perm, int* __restrict_
 void launch_load_positions(Engine& e, const double* src, cudaStream_t s) {
     if (e.N == 0) return;
     e.launches += 1;
-    k_load_pos<<<nblk(e.N, 256), 256, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x, e.ctl);
+    k_load_pos<<<nblk(e.N, 256), 256, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.types, e.x, e.ctl);
 }
 
 void launch_load_positions_keep(Engine& e, const double* src, cudaStream_t s) {
@@ -485,10 +486,30 @@ void launch_load_positions_keep(Engine& e, const double* src, cudaStream_t s) {
     e.launches += 1;
     if (single_fast(e))
         k_load_pos_keep<true><<<nblk(e.N, kINT), kINT, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x, e.xb, e.xo,
-                                                             e.cell_t, e.ctl, e.disp_box);
+                                                             e.cell_t, e.types, e.ctl, e.disp_box);
     else
         k_load_pos_keep<false><<<nblk(e.N, kINT), kINT, 0, s>>>(e.N, src, e.iperm, make_geo(e), e.x, e.xb, e.xo,
-                                                              e.cell_t, e.ctl, e.disp_box);
+                                                              e.cell_t, e.types, e.ctl, e.disp_box);
+}
+
+// New species for the current state: positions' pad lanes and the type
+// bits of the float32 offsets, in sorted order.
+__global__ void k_apply_types(int64_t N, const int* __restrict__ perm, const int* __restrict__ types,
+                              double4_32a* __restrict__ x, float4* __restrict__ xo) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int ty = types[perm[t]];
+        x[t].w = (double)ty;
+        float4 o = xo[t];
+        o.w = __int_as_float((__float_as_int(o.w) & 0x3fffffff) | (ty << 30));
+        xo[t] = o;
+    }
+}
+
+void launch_apply_types(Engine& e, cudaStream_t s) {
+    if (e.N == 0) return;
+    e.launches += 1;
+    k_apply_types<<<(int)std::min<int64_t>(nblk(e.N, 256), (int64_t)8 * e.n_sm), 256, 0, s>>>(e.N, e.perm, e.types,
+                                                                                               e.x, e.xo);
 }
 
 void launch_after_load(Engine& e, cudaStream_t s) {
@@ -563,13 +584,17 @@ void launch_eval_math(Engine& e, int fn, const double* x, int64_t n, double* out
 //   s(u) = y_k + b u + c u^2 + d u^3, u = t - t_k,
 //   b = (y_{k+1} - y_k)/h - h (2 M_k + M_{k+1})/6, c = M_k/2, d = (M_{k+1} - M_k)/(6h);
 // entry n-1 holds the value and slope at the last knot (extrapolation).
+// One thread per spline table: np_ V tables (n0 knots), np_ rho tables (n1)
+// and nt F tables (n2), back to back as the knot values are.
 __global__ void k_spline_setup(const double* __restrict__ y_all, double* __restrict__ work,
-                               double4_32a* __restrict__ coef, int n0, int n1, int n2, double h0, double h1, double h2) {
-    int w = threadIdx.x;
-    if (w >= 3) return;
-    int n = w == 0 ? n0 : (w == 1 ? n1 : n2);
-    int off = w == 0 ? 0 : (w == 1 ? n0 : n0 + n1);
-    double h = w == 0 ? h0 : (w == 1 ? h1 : h2);
+                               double4_32a* __restrict__ coef, int n0, int n1, int n2, double h0, double h1, double h2,
+                               int np_, int nt) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= 2 * np_ + nt) return;
+    const int kind = w < np_ ? 0 : (w < 2 * np_ ? 1 : 2);
+    const int n = kind == 0 ? n0 : (kind == 1 ? n1 : n2);
+    const int off = kind == 0 ? w * n0 : (kind == 1 ? np_ * n0 + (w - np_) * n1 : np_ * (n0 + n1) + (w - 2 * np_) * n2);
+    const double h = kind == 0 ? h0 : (kind == 1 ? h1 : h2);
     const double* y = y_all + off;
     double* cp = work + 3 * off;  // modified super-diagonal
     double* dp = cp + n;          // modified right-hand side
@@ -596,8 +621,9 @@ __global__ void k_spline_setup(const double* __restrict__ y_all, double* __restr
 void launch_spline_setup(Engine& e, cudaStream_t s) {
     const md_potential& p = e.pot_host;
     e.launches += 1;
-    k_spline_setup<<<1, 32, 0, s>>>(e.knots_dev, e.spline_work, e.spline_coef, p.n_phi, p.n_f, p.n_F,
-                                    e.pot.sh[0], e.pot.sh[1], e.pot.sh[2]);
+    const int nt = std::max(p.n_types, 1), np_ = nt * (nt + 1) / 2;
+    k_spline_setup<<<(2 * np_ + nt + 31) / 32, 32, 0, s>>>(e.knots_dev, e.spline_work, e.spline_coef, p.n_phi, p.n_f,
+                                                            p.n_F, e.pot.sh[0], e.pot.sh[1], e.pot.sh[2], np_, nt);
 }
 
 }  // namespace mdk

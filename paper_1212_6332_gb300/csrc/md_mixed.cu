@@ -36,15 +36,16 @@ __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, G
     GSum acc;
     for (int k = 0; k < n; ++k) {
         int j = entry_slot(nl[(int64_t)k * Np + i]);
+        const float4 oj = xo[j];
         float dx, dy, dz;
-        sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+        sep_mixed<WIDE>(cs, oi, oj, dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2)));
+        if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2), species_pair<KIND>(P, oi, oj)));
         if ((k & kGroupMask) == kGroupMask) acc.flush();
     }
     double r_i = acc.value();
     double F, Fpi;
-    embed<KIND>(P, r_i, F, Fpi);
+    embed<KIND>(P, r_i, F, Fpi, KIND == MD_POT_SPLINE ? off_type(oi) : 0);
     rho[i] = r_i;
     Fp[i] = Fpi;
     Fpf[i] = (float)Fpi;
@@ -78,14 +79,15 @@ __global__ void __launch_bounds__(kMNT) k_force_mixed(int64_t N, int64_t Np, Geo
             if (vir) aw.flush();
         }
         int j = entry_slot(nl[(int64_t)k * Np + i]);
+        const float4 oj = xo[j];
         float dx, dy, dz;
-        sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+        sep_mixed<WIDE>(cs, oi, oj, dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < P.f_rc2) {
             float rinv = rsqrtf(r2);
             float r = r2 * rinv;
             float phi, dphi, fr, dfr;
-            pair_allf<KIND>(P, r, phi, dphi, fr, dfr);
+            pair_allf<KIND>(P, r, phi, dphi, fr, dfr, species_pair<KIND>(P, oi, oj));
             float s = (dphi + (Fpi + Fpf[j]) * dfr) * rinv;
             ax.add(s * dx);
             ay.add(s * dy);

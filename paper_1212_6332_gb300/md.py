@@ -25,7 +25,7 @@ STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_NOMEM", 4: "
 SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_neighbors", "md_get_neighbors",
            "md_max_count", "md_compute_forces", "md_get_forces", "md_step", "md_get_thermo", "md_batch_create",
            "md_batch_destroy", "md_batch_set_state", "md_batch_get_state", "md_batch_compute_forces",
-           "md_batch_step", "md_batch_set_potential", "md_set_thermostat", "md_pressure", "md_set_barostat", "md_get_box", "md_param_grad", "md_num_params", "md_status_string",
+           "md_batch_step", "md_batch_set_potential", "md_set_thermostat", "md_set_types", "md_pressure", "md_set_barostat", "md_get_box", "md_param_grad", "md_num_params", "md_status_string",
            "md_last_error", "md_profile_start", "md_profile_read",
            "md_eval_math", "md_forces_noalloc", "md_batch_thermo",
            "md_batch_schedule")
@@ -43,7 +43,7 @@ class Potential(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("p", ctypes.c_double * 8), ("r_taper", ctypes.c_double),
                 ("r_cut", ctypes.c_double), ("knots", ctypes.POINTER(ctypes.c_double)), ("n_phi", ctypes.c_int),
                 ("n_f", ctypes.c_int), ("n_F", ctypes.c_int), ("r_lo", ctypes.c_double), ("r_hi", ctypes.c_double),
-                ("rho_lo", ctypes.c_double), ("rho_hi", ctypes.c_double)]
+                ("rho_lo", ctypes.c_double), ("rho_hi", ctypes.c_double), ("n_types", ctypes.c_int)]
 
 
 class Config(ctypes.Structure):
@@ -98,6 +98,7 @@ def load(path: str | pathlib.Path | None = None) -> ctypes.CDLL:
         "md_batch_step": [vp, i32, i32, i32, dp, vp],
         "md_batch_set_potential": [vp, P(Potential), vp],
         "md_set_thermostat": [vp, ctypes.c_double, ctypes.c_double],
+        "md_set_types": [vp, vp, vp],
         "md_pressure": [vp, vp, vp],
         "md_set_barostat": [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double],
         "md_get_box": [vp, vp, vp],
@@ -135,6 +136,22 @@ def potential_struct(spec: dict) -> tuple[Potential, object]:
     elif kind == "sc":
         P.kind = POT_SC
         vals = [spec[k] for k in ("eps", "c", "a", "n", "m")]
+    elif kind == "alloy":
+        # several species: V^(ab), rho^(ab) per type pair (row-major upper
+        # triangle), F^(a) per type, on shared grids
+        P.kind = POT_SPLINE
+        vals = []
+        T = int(spec["n_types"])
+        tabs = [np.asarray(a, dtype=np.float64) for key in ("phi", "f", "F") for a in spec[key]]
+        if len(spec["phi"]) != T * (T + 1) // 2 or len(spec["f"]) != len(spec["phi"]) or len(spec["F"]) != T:
+            raise ValueError("alloy: T(T+1)/2 pair tables and T embedding tables")
+        knots = np.ascontiguousarray(np.concatenate(tabs))
+        keep = knots
+        P.knots = knots.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        P.n_phi, P.n_f, P.n_F = len(spec["phi"][0]), len(spec["f"][0]), len(spec["F"][0])
+        P.r_lo, P.r_hi = float(spec["r_lo"]), float(spec["r_hi"])
+        P.rho_lo, P.rho_hi = float(spec["rho_lo"]), float(spec["rho_hi"])
+        P.n_types = T
     elif kind == "spline":
         P.kind = POT_SPLINE
         vals = []
@@ -326,6 +343,17 @@ class System:
         self._check(self.lib.md_batch_set_potential(self._h, ctypes.byref(pot), _stream()))
         self._keep = keep
         self.potential = dict(spec)
+
+    def set_types(self, types):
+        """Species of every atom in caller order (numpy array or CUDA
+        tensor of int32), for a potential with several species."""
+        import numpy as np
+        if hasattr(types, "data_ptr"):
+            t = types.to(dtype=__import__("torch").int32).contiguous()
+            self._check(self.lib.md_set_types(self._h, ctypes.c_void_p(t.data_ptr()), _stream()))
+        else:
+            t = np.ascontiguousarray(types, dtype=np.int32)
+            self._check(self.lib.md_set_types(self._h, t.ctypes.data_as(ctypes.c_void_p), _stream()))
 
     def pressure(self):
         """Instantaneous pressure of Eq. (6) of every box (eV/A^3), a device
