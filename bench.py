@@ -68,9 +68,9 @@ KERNELS = {
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per atom of one k_pairs_half launch, from the ncu
 # capture summarised in profiles/k_pairs_half_rgl_cu_1m_fp64.md (1,048,576
-# atoms of the same lattice, potential and temperature: 1.754 GB read +
-# 2.717 GB written); traffic grows in proportion to the atom count.
-PAIRS_DRAM_BYTES_PER_ATOM = (1.754257e9 + 2.717350e9) / 1048576
+# atoms of the same lattice, potential and temperature: 1.763 GB read +
+# 2.719 GB written); traffic grows in proportion to the atom count.
+PAIRS_DRAM_BYTES_PER_ATOM = (1.762863e9 + 2.718543e9) / 1048576
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
            0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
@@ -300,9 +300,17 @@ def run_batch(precision: str, K: int, W: int, n_boxes: int = 4096, use_graph: bo
     b.synchronize()
     ms = a.elapsed_time(b)
     n = int(bt.atom_offsets[-1])
+    phases = None
+    if schedule == "tile":
+        # phase split from a further, untimed stretch of the same run (phase
+        # events turn graph replay off, so they stay out of the timed steps)
+        s.profile_start(timing=True)
+        s.batch_step(K, schedule=schedule, use_graph=False, per_box=False)
+        prof = s.profile_read()
+        phases = {k: v / max(K, 1) for k, v in prof["ms"].items()}
     s.close()
     return dict(value=n * K / (ms * 1e-3), ms_per_step=ms / K, atoms=n, boxes=n_boxes, schedule=schedule,
-                graph=use_graph and schedule == "tile")
+                graph=use_graph and schedule == "tile", phase_ms_per_step=phases)
 
 
 def run_per_box_sample(K: int, n_sample: int = 64, n_boxes: int = 4096) -> dict:

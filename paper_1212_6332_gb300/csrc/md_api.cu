@@ -145,10 +145,14 @@ void fill_pot(Engine& e) {
         size_t off = 0;
         for (int w = 0; w < 3; ++w) {
             P.sp[w] = e.spline_coef + off;
+            P.spf[w] = e.spline_coef_f + off;
             P.sn[w] = ns[w];
             P.st0[w] = lo[w];
             P.sh[w] = (hi[w] - lo[w]) / (ns[w] - 1);
             P.sinvh[w] = 1.0 / P.sh[w];
+            P.st0f[w] = (float)P.st0[w];
+            P.shf[w] = (float)P.sh[w];
+            P.sinvhf[w] = (float)P.sinvh[w];
             off += (size_t)ntab[w] * ns[w];
         }
     } else {
@@ -217,7 +221,7 @@ void destroy_graphs(Engine& e) {
 void free_engine(Engine& e) {
     destroy_graphs(e);
     dfree(e.L); dfree(e.cell_len); dfree(e.cell_len_f); dfree(e.nc); dfree(e.cell_off); dfree(e.atom_off);
-    dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.cell_org); dfree(e.spline_coef);
+    dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.cell_org); dfree(e.spline_coef); dfree(e.spline_coef_f);
     dfree(e.spline_work); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
     dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
@@ -388,6 +392,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.cell_org, tot);
     if (pot->kind == MD_POT_SPLINE) {
         AL(e.spline_coef, nk);
+        AL(e.spline_coef_f, nk);
         AL(e.spline_work, 3 * nk);
         AL(e.knots_dev, nk);
     }

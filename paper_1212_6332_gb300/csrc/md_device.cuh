@@ -445,29 +445,28 @@ __device__ __forceinline__ float powrf(float b, float e) {
 }
 
 __device__ __forceinline__ void spline_evalf(const Pot& P, int w, float t, float& v, float& dv, int tab = 0) {
-    // spline tables stay float64; evaluation rounds them to float32
-    float s = (t - (float)P.st0[w]) * (float)P.sinvh[w];
-    int n = P.sn[w];
-    const double4_32a* c = P.sp[w] + (int64_t)tab * n;
+    // float32 copies of the coefficient tables; u from the interval position
+    const float s = (t - P.st0f[w]) * P.sinvhf[w];
+    const int n = P.sn[w];
+    const float4* c = P.spf[w] + (int64_t)tab * n;
     if (s < 0.0f) {
-        double4_32a c0 = c[0];
-        v = (float)c0.x + (t - (float)P.st0[w]) * (float)c0.y;
-        dv = (float)c0.y;
+        const float4 c0 = c[0];
+        v = c0.x + (t - P.st0f[w]) * c0.y;
+        dv = c0.y;
         return;
     }
-    int k = (int)s;
+    const int k = (int)s;
     if (k >= n - 1) {
-        double4_32a ce = c[n - 1];
-        float u = t - (float)(P.st0[w] + P.sh[w] * (n - 1));
-        v = (float)ce.x + u * (float)ce.y;
-        dv = (float)ce.y;
+        const float4 ce = c[n - 1];
+        const float u = (s - (float)(n - 1)) * P.shf[w];
+        v = ce.x + u * ce.y;
+        dv = ce.y;
         return;
     }
-    float u = t - (float)(P.st0[w] + P.sh[w] * k);
-    double4_32a ck = c[k];
-    float c0 = (float)ck.x, c1 = (float)ck.y, c2 = (float)ck.z, c3 = (float)ck.w;
-    v = c0 + u * (c1 + u * (c2 + u * c3));
-    dv = c1 + u * (2.0f * c2 + 3.0f * u * c3);
+    const float u = (s - (float)k) * P.shf[w];
+    const float4 ck = c[k];
+    v = ck.x + u * (ck.y + u * (ck.z + u * ck.w));
+    dv = ck.y + u * (2.0f * ck.z + 3.0f * u * ck.w);
 }
 
 template <int KIND>

@@ -46,6 +46,10 @@ struct Pot {
     const double4_32a* sp[3];
     int sn[3];
     double st0[3], sh[3], sinvh[3];
+    // the same coefficients rounded to float32 (mixed-precision path: no
+    // float64 loads or conversions per evaluation)
+    const float4* spf[3];
+    float st0f[3], shf[3], sinvhf[3];
     // table-driven exponential (float64 path)
     ExpConst ek;
     const double* exp_T;  // [kExpTable] 2^(j/kExpTable)
@@ -146,6 +150,7 @@ struct Engine {
     int* cell_xyz = nullptr;
     double4_32a* cell_org = nullptr;
     double4_32a* spline_coef = nullptr;  // 3 splines back to back
+    float4* spline_coef_f = nullptr;     // the same, float32
     double* spline_work = nullptr;   // [3 * total knots] setup scratch
     double* knots_dev = nullptr;
     // reduction chunks: (box, [lo, hi)) pieces of at most 4096 atoms

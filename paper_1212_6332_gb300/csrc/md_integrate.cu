@@ -587,8 +587,8 @@ void launch_eval_math(Engine& e, int fn, const double* x, int64_t n, double* out
 // One thread per spline table: np_ V tables (n0 knots), np_ rho tables (n1)
 // and nt F tables (n2), back to back as the knot values are.
 __global__ void k_spline_setup(const double* __restrict__ y_all, double* __restrict__ work,
-                               double4_32a* __restrict__ coef, int n0, int n1, int n2, double h0, double h1, double h2,
-                               int np_, int nt) {
+                               double4_32a* __restrict__ coef, float4* __restrict__ coef_f, int n0, int n1, int n2,
+                               double h0, double h1, double h2, int np_, int nt) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= 2 * np_ + nt) return;
     const int kind = w < np_ ? 0 : (w < 2 * np_ ? 1 : 2);
@@ -616,14 +616,17 @@ __global__ void k_spline_setup(const double* __restrict__ y_all, double* __restr
     }
     double4_32a l = c[n - 2];
     c[n - 1] = make_double4_32a(y[n - 1], l.y + 2.0 * l.z * h + 3.0 * l.w * h * h, 0.0, 0.0);
+    float4* cf = coef_f + off;
+    for (int k = 0; k < n; ++k) cf[k] = make_float4((float)c[k].x, (float)c[k].y, (float)c[k].z, (float)c[k].w);
 }
 
 void launch_spline_setup(Engine& e, cudaStream_t s) {
     const md_potential& p = e.pot_host;
     e.launches += 1;
     const int nt = std::max(p.n_types, 1), np_ = nt * (nt + 1) / 2;
-    k_spline_setup<<<(2 * np_ + nt + 31) / 32, 32, 0, s>>>(e.knots_dev, e.spline_work, e.spline_coef, p.n_phi, p.n_f,
-                                                            p.n_F, e.pot.sh[0], e.pot.sh[1], e.pot.sh[2], np_, nt);
+    k_spline_setup<<<(2 * np_ + nt + 31) / 32, 32, 0, s>>>(e.knots_dev, e.spline_work, e.spline_coef,
+                                                            e.spline_coef_f, p.n_phi, p.n_f, p.n_F, e.pot.sh[0],
+                                                            e.pot.sh[1], e.pot.sh[2], np_, nt);
 }
 
 }  // namespace mdk
