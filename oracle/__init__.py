@@ -255,9 +255,12 @@ def virial(pot: Potential, x, box, types=None) -> float:
     return lib.orc_virial_pairs(pot._h, x.shape[0], _dp(x), _dp(box), pi.size, _ip(pi), _ip(pj))
 
 
-def param_deriv(pot: Potential, which: int, x, box) -> tuple[float, np.ndarray]:
-    """(dE/dtheta, dF/dtheta [N,3]) for parameter index ``which``."""
+def param_deriv(pot: Potential, which: int, x, box, types=None) -> tuple[float, np.ndarray]:
+    """(dE/dtheta, dF/dtheta [N,3]) for parameter index ``which`` (for an
+    alloy: the knot index in the order V pair tables, rho pair tables, F
+    tables)."""
     lib = _load()
+    pot.use_types(types)
     x, box = _f64(x), _f64(box)
     pi, pj = pairs(x, box, pot.r_cut)
     dF = np.zeros((x.shape[0], 3))
@@ -266,9 +269,10 @@ def param_deriv(pot: Potential, which: int, x, box) -> tuple[float, np.ndarray]:
     return dE, dF
 
 
-def param_grad(pot: Potential, x, box, gF, gE: float, grad: np.ndarray | None = None) -> np.ndarray:
+def param_grad(pot: Potential, x, box, gF, gE: float, grad: np.ndarray | None = None, types=None) -> np.ndarray:
     """Accumulates sum_i gF_i . dF_i/dtheta + gE dE/dtheta into ``grad``."""
     lib = _load()
+    pot.use_types(types)
     x, box, gF = _f64(x), _f64(box), _f64(gF)
     if grad is None:
         grad = np.zeros(pot.n_param)

@@ -832,7 +832,10 @@ typedef struct {
     int kind;
     dual prm[8];
     double r_taper, r_cut;
-    dspline sp[3]; /* phi, f, F */
+    dspline sp[3]; /* phi, f, F (one species) */
+    /* several species: P V tables, P rho tables, T F tables (as orc_pot) */
+    int n_types, n_tab;
+    dspline* tab;
 } dpot;
 
 /* Builds the dual potential with parameter `which` seeded (d = 1).
@@ -844,6 +847,29 @@ static void dpot_init(dpot* D, const orc_pot* P, int which) {
     for (int k = 0; k < 8; ++k) D->prm[k] = dc(P->prm[k]);
     if (P->kind != ORC_SPLINE) {
         if (which >= 0 && which < 8) D->prm[which].d = 1.0;
+        return;
+    }
+    D->n_types = P->n_types;
+    D->tab = NULL;
+    if (P->n_types > 1) {
+        /* the tables in knot order: V pairs, rho pairs, F types */
+        int np = P->n_types * (P->n_types + 1) / 2;
+        D->n_tab = 2 * np + P->n_types;
+        D->tab = (dspline*)calloc((size_t)D->n_tab, sizeof(dspline));
+        int base = 0;
+        for (int t = 0; t < D->n_tab; ++t) {
+            const spline* src = t < np ? &P->aphi[t] : (t < 2 * np ? &P->af[t - np] : &P->aF[t - 2 * np]);
+            dspline* dst = &D->tab[t];
+            dst->n = src->n;
+            dst->t0 = src->t0;
+            dst->h = src->h;
+            dst->y = (dual*)malloc(sizeof(dual) * (size_t)src->n);
+            dst->m = (dual*)malloc(sizeof(dual) * (size_t)src->n);
+            for (int k = 0; k < src->n; ++k) dst->y[k] = dc(src->y[k]);
+            if (which >= base && which < base + src->n) dst->y[which - base].d = 1.0;
+            base += src->n;
+            dspline_setup(dst);
+        }
         return;
     }
     const spline* src[3] = {&P->sp_phi, &P->sp_f, &P->sp_F};
@@ -863,13 +889,21 @@ static void dpot_init(dpot* D, const orc_pot* P, int which) {
 
 static void dpot_free(dpot* D) {
     if (D->kind != ORC_SPLINE) return;
+    if (D->tab) {
+        for (int t = 0; t < D->n_tab; ++t) {
+            free(D->tab[t].y);
+            free(D->tab[t].m);
+        }
+        free(D->tab);
+        return;
+    }
     for (int s = 0; s < 3; ++s) {
         free(D->sp[s].y);
         free(D->sp[s].m);
     }
 }
 
-static void dpair_eval(const dpot* D, double r, dual* phi, dual* dphi, dual* f, dual* df) {
+static void dpair_eval(const dpot* D, int pt, double r, dual* phi, dual* dphi, dual* f, dual* df) {
     if (r >= D->r_cut) {
         *phi = *dphi = *f = *df = dc(0.0);
         return;
@@ -887,15 +921,22 @@ static void dpair_eval(const dpot* D, double r, dual* phi, dual* dphi, dual* f, 
         *dphi = dmul(a2, dadd(dscale(ddiv(p, r0), -S), dc(dS)));
         *f = dscale(dmul(xi2, e2), S);
         *df = dmul(dmul(xi2, e2), dadd(dscale(ddiv(q, r0), -2.0 * S), dc(dS)));
+    } else if (D->tab) {
+        int np = D->n_types * (D->n_types + 1) / 2;
+        dspline_eval(&D->tab[pt], dc(r), phi, dphi);
+        dspline_eval(&D->tab[np + pt], dc(r), f, df);
     } else {
         dspline_eval(&D->sp[0], dc(r), phi, dphi);
         dspline_eval(&D->sp[1], dc(r), f, df);
     }
 }
 
-static void dembed_eval(const dpot* D, dual rho, dual* F, dual* Fp) {
+static void dembed_eval(const dpot* D, int a, dual rho, dual* F, dual* Fp) {
     if (D->kind == ORC_SPLINE) {
-        dspline_eval(&D->sp[2], rho, F, Fp);
+        if (D->tab)
+            dspline_eval(&D->tab[D->n_types * (D->n_types + 1) + a], rho, F, Fp);
+        else
+            dspline_eval(&D->sp[2], rho, F, Fp);
         return;
     }
     if (rho.v <= 0.0) {
@@ -925,12 +966,12 @@ double orc_param_deriv(const orc_pot* P, int which, int n, const double* x, cons
         int i = pi[k], j = pj[k];
         double r2 = sep(x, i, j, box, d);
         if (r2 >= rc2) continue;
-        dpair_eval(&D, sqrt(r2), &phi, &dphi, &fr, &dfr);
+        dpair_eval(&D, ptype(P, i, j), sqrt(r2), &phi, &dphi, &fr, &dfr);
         rho[i] = dadd(rho[i], fr);
         rho[j] = dadd(rho[j], fr);
     }
     for (int i = 0; i < n; ++i) {
-        dembed_eval(&D, rho[i], &F, &Fp[i]);
+        dembed_eval(&D, atype(P, i), rho[i], &F, &Fp[i]);
         E = dadd(E, F);
     }
     for (int k = 0; k < 3 * n; ++k) dF[k] = 0.0;
@@ -939,7 +980,7 @@ double orc_param_deriv(const orc_pot* P, int which, int n, const double* x, cons
         double r2 = sep(x, i, j, box, d);
         if (r2 >= rc2) continue;
         double r = sqrt(r2);
-        dpair_eval(&D, r, &phi, &dphi, &fr, &dfr);
+        dpair_eval(&D, ptype(P, i, j), r, &phi, &dphi, &fr, &dfr);
         E = dadd(E, phi);
         dual s = dadd(dphi, dmul(dadd(Fp[i], Fp[j]), dfr));
         for (int a = 0; a < 3; ++a) {

@@ -475,6 +475,33 @@ def test_alloy_relabelling_species_changes_nothing():
     assert np.abs(a["f"] - b["f"]).max() < 1e-13
 
 
+def test_alloy_knot_derivatives_match_finite_differences():
+    """Forward-mode derivatives of E_T and of the forces with respect to
+    knot values of every kind of table (V pair, rho pair, F type) equal
+    central differences of the oracle's own energy and forces."""
+    al = cuni_alloy(n_knots=40)
+    bx, t = alloy_box()
+    pot = O.Potential(al)
+    knots = pot._knots
+    nr, P = len(al["phi"][0]), 3
+
+    def spec_with(k2):
+        return dict(al, phi=[k2[i * nr:(i + 1) * nr] for i in range(P)],
+                    f=[k2[(P + i) * nr:(P + i + 1) * nr] for i in range(P)],
+                    F=[k2[2 * P * nr + i * nr:2 * P * nr + (i + 1) * nr] for i in range(2)])
+
+    h = 1e-6
+    for which in (5, 45, 85, 130, 205):
+        dE, dF = O.param_deriv(pot, which, bx.x, bx.box, types=t)
+        kp, km = knots.copy(), knots.copy()
+        kp[which] += h
+        km[which] -= h
+        op = O.forces(O.Potential(spec_with(kp)), bx.x, bx.box, types=t)
+        om = O.forces(O.Potential(spec_with(km)), bx.x, bx.box, types=t)
+        assert dE == pytest.approx((op["E"] - om["E"]) / (2 * h), rel=1e-5, abs=1e-6)
+        assert np.abs(dF - (op["f"] - om["f"]) / (2 * h)).max() < 1e-5
+
+
 def test_dimer_small_oscillation_period():
     """A dimer near its bond length oscillates at omega = sqrt(k/mu), with
     k = E''(r_eq) of the closed-form dimer energy and mu = m/2."""
