@@ -344,19 +344,26 @@ def run_grad(K: int, W: int, precision: str = "fp64", kind: str = "rgl") -> dict
     """Force-matching loss + gradient over 256 configurations of 864 atoms
     (6^3 fcc Cu, strain U(0.98, 1.02), N(0, 0.1 A) displacements); targets
     from RGL Cu at the reference parameters, model RGL perturbed by 5%
-    (or its 3 x 200-knot spline tabulation)."""
+    (or its 3 x 200-knot spline tabulation, or the two-species alloy_model
+    with U{0, 1} labels: 3 V + 3 rho + 2 F tables of 200 knots)."""
     import torch
     from paper_1212_6332_gb300.fit import ForceField, force_matching_loss, make_batch, theta_of
     cfgs = [I.strained_fcc(6, I.A_CU, seed=5000 + k) for k in range(256)]
+    n = sum(c.n for c in cfgs)
     ref = make_batch(I.RGL_CU, cfgs)
     f_tgt = ref.get_forces()["f"].clone()
     e_tgt = ref.batch_thermo()[:, 1].clone()
     ref.close()
     signs = np.where(I.uniform(77, 5) < 0.5, -1.0, 1.0)
     model = dict(I.RGL_CU, **{k: I.RGL_CU[k] * (1 + 0.05 * sg) for k, sg in zip(("A", "xi", "p", "q", "r0"), signs)})
+    types = None
     if kind == "spline":
         model = spline_model(model)
-    s = make_batch(model, cfgs, precision=precision)
+    elif kind == "alloy":
+        # two species, labels U{0, 1} per atom
+        model = alloy_model()
+        types = (I.uniform(78, n) < 0.5).astype(np.int32)
+    s = make_batch(model, cfgs, precision=precision, types=types)
     counts = torch.tensor([c.n for c in cfgs], device="cuda", dtype=torch.float64)
     theta = theta_of(model).cuda().requires_grad_(True)
 
@@ -374,7 +381,6 @@ def run_grad(K: int, W: int, precision: str = "fp64", kind: str = "rgl") -> dict
         L, g = once()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    n = sum(c.n for c in cfgs)
     s.close()
     return dict(value=K / dt, unit="(loss + gradient over 256 configs)/s", atom_grads_per_s=n * K / dt,
                 n_params=int(theta.numel()), loss=float(L.item()), precision=precision, model=kind)
@@ -572,7 +578,8 @@ def main():
         kg = max(3, min(K, 10))
         grad = {"rgl_fp64": run_grad(kg, 2, "fp64", "rgl"), "rgl_mixed": run_grad(kg, 2, "mixed", "rgl"),
                 "spline_fp64": run_grad(kg, 2, "fp64", "spline"),
-                "spline_mixed": run_grad(kg, 2, "mixed", "spline")}
+                "spline_mixed": run_grad(kg, 2, "mixed", "spline"),
+                "alloy_fp64": run_grad(kg, 2, "fp64", "alloy"), "alloy_mixed": run_grad(kg, 2, "mixed", "alloy")}
     if rank == 0 and not args.no_extras:
         import oracle as O
         O.build()

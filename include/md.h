@@ -298,7 +298,8 @@ MD_API int md_set_barostat(md_batch* b, double P0, double tau_p, double beta);
 MD_API int md_get_box(md_batch* b, double* lengths, md_stream stream);
 
 /* Gradient of a scalar loss L with respect to the potential parameters
- * (RGL: A, xi, p, q, r0; spline: all knot values, V then rho then F), at
+ * (RGL: A, xi, p, q, r0; spline: all knot values in md_potential's knot
+ * order, V then rho then F, each per type pair or type for T > 1), at
  * the batch's current positions, given g_f = dL/dF [n][3] (device, caller
  * order) and g_e = dL/dE_T per box [n_boxes] (device):
  *   grad = sum_i g_f_i . dF_i/dtheta + sum_b g_e_b dE_b/dtheta.
@@ -307,7 +308,8 @@ MD_API int md_get_box(md_batch* b, double* lengths, md_stream stream);
  * paper. MD_ERR_UNSUPPORTED for Sutton-Chen. */
 MD_API int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* grad, md_stream stream);
 
-/* Number of potential parameters (5 for RGL/SC, n_phi + n_f + n_F for a spline). */
+/* Number of potential parameters (5 for RGL/SC; for a spline the knot
+ * count, P (n_phi + n_f) + T n_F with T species and P = T (T + 1) / 2). */
 MD_API int md_num_params(const md_batch* b);
 
 /* ---------------------------------------------------------------- profiling */

@@ -1267,7 +1267,6 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
     cudaStream_t s = (cudaStream_t)st;
     if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
     if (E->pot_host.kind == MD_POT_SC) return fail(E, MD_ERR_UNSUPPORTED, "no gradient for Sutton-Chen");
-    if (pot_types(E->pot_host) > 1) return fail(E, MD_ERR_UNSUPPORTED, "no gradient for several species");
     if (!grad || !is_device_ptr(grad)) return fail(E, MD_ERR_ARG, "grad must be a device pointer");
     if (E->N && (!g_f || !is_device_ptr(g_f))) return fail(E, MD_ERR_ARG, "g_f must be a device pointer");
     if (g_e && !is_device_ptr(g_e)) return fail(E, MD_ERR_ARG, "g_e must be a device pointer");
@@ -1276,7 +1275,8 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
         int nb = (int)((e.N + 127) / 128);
         e.grad_blocks = std::max(1, std::min(nb, 4 * e.n_sm));
         const md_potential& p = e.pot_host;
-        size_t ncoef = p.kind == MD_POT_SPLINE ? 4 * ((size_t)p.n_phi + p.n_f + p.n_F - 3) : 5;
+        // spline coefficients: 4 per interval of every table
+        size_t ncoef = p.kind == MD_POT_SPLINE ? 4 * (knot_count(p) - 2 * pot_pairs(p) - pot_types(p)) : 5;
         if (dalloc(E, &e.grad_g, 3 * (size_t)e.N_pad) || dalloc(E, &e.grad_u, (size_t)e.N_pad) ||
             dalloc(E, &e.grad_Fpp, (size_t)e.N_pad) || dalloc(E, &e.grad_partial, (size_t)e.grad_blocks * ncoef) ||
             dalloc(E, &e.grad_coef, ncoef))
@@ -1291,7 +1291,7 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
 int md_num_params(const md_batch* b) {
     if (!b) return -1;
     const md_potential& p = b->e.pot_host;
-    return p.kind == MD_POT_SPLINE ? p.n_phi + p.n_f + p.n_F : 5;
+    return p.kind == MD_POT_SPLINE ? (int)knot_count(p) : 5;
 }
 
 int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double* out, md_stream st) {

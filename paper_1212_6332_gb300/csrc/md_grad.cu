@@ -47,19 +47,30 @@ __device__ __forceinline__ void sep(const Geo& g, const double4_32a* __restrict_
     dz = minimg(xj.z - xi.z, Lz, 0.5 * Lz);
 }
 
+// Species of atom i and type-pair table of (i, j) from the positions' pad
+// lanes (splines with several species; 0 otherwise).
+template <int KIND>
+__device__ __forceinline__ int atom_tab(const Pot& P, const double4_32a* __restrict__ x, int64_t i) {
+    return KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0;
+}
+template <int KIND>
+__device__ __forceinline__ int pair_tab(const Pot& P, const double4_32a* __restrict__ x, int64_t i, int j) {
+    return KIND == MD_POT_SPLINE && P.n_types > 1 ? pair_table(P.n_types, pos_type(x[i]), pos_type(x[j])) : 0;
+}
+
 // rho_i, F'(rho_i) and F''(rho_i) into the per-atom arrays (F'' of the
 // spline is that of its cubic piece; 0 on the linear extensions).
 template <int KIND>
 __device__ __forceinline__ void store_embedding(const Pot& P, double r_i, int64_t i, double* __restrict__ rho,
-                                                double* __restrict__ Fp, double* __restrict__ Fpp) {
+                                                double* __restrict__ Fp, double* __restrict__ Fpp, int a = 0) {
     double F, Fpi, Fppi = 0.0;
-    embed<KIND>(P, r_i, F, Fpi);
+    embed<KIND>(P, r_i, F, Fpi, a);
     if (KIND == MD_POT_SPLINE) {
         double s = (r_i - P.st0[2]) * P.sinvh[2];
         int k = (int)s;
         if (s >= 0.0 && k < P.sn[2] - 1) {
             double u = r_i - (P.st0[2] + P.sh[2] * k);
-            double4_32a c = P.sp[2][k];
+            double4_32a c = P.sp[2][(int64_t)a * P.sn[2] + k];
             Fppi = 2.0 * c.z + 6.0 * c.w * u;
         }
     } else if (r_i > 0.0) {
@@ -89,10 +100,10 @@ __global__ void __launch_bounds__(kGNT) k_grad_rho(int64_t N, int64_t Np, Geo g,
         double r2 = norm2(dx, dy, dz);
         if (r2 >= P.rc2) continue;
         double phi, fr, A, B;
-        pair_eval<KIND>(P, sT, r2, phi, fr, A, B);
+        pair_eval<KIND>(P, sT, r2, phi, fr, A, B, pair_tab<KIND>(P, x, i, j));
         r_i += fr;
     }
-    store_embedding<KIND>(P, r_i, i, rho, Fp, Fpp);
+    store_embedding<KIND>(P, r_i, i, rho, Fp, Fpp, atom_tab<KIND>(P, x, i));
 }
 
 // u_i = sum_j (g_i - g_j) . d_ij rho'(r)/r
@@ -115,7 +126,7 @@ __global__ void __launch_bounds__(kGNT) k_grad_u(int64_t N, int64_t Np, Geo g, P
         double r2 = norm2(dx, dy, dz);
         if (r2 >= P.rc2) continue;
         double phi, fr, A, B;
-        pair_eval<KIND>(P, sT, r2, phi, fr, A, B);
+        pair_eval<KIND>(P, sT, r2, phi, fr, A, B, pair_tab<KIND>(P, x, i, j));
         acc += ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * B;
     }
     u[i] = acc;
@@ -259,9 +270,12 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline(int64_t N, int64_t Np,
     extern __shared__ double sg[];  // [ncoef] coefficient gradients: V pieces, rho pieces, F pieces
     for (int k = threadIdx.x; k < ncoef; k += NT) sg[k] = 0.0;
     __syncthreads();
+    // per table 4 (n - 1) coefficients: V pair tables, rho pair tables, F tables
+    const int np_ = P.n_types * (P.n_types + 1) / 2;
+    const int cV = 4 * (P.sn[0] - 1), cR = 4 * (P.sn[1] - 1), cF = 4 * (P.sn[2] - 1);
     double* gV = sg;
-    double* gR = sg + 4 * (P.sn[0] - 1);
-    double* gF = gR + 4 * (P.sn[1] - 1);
+    double* gR = sg + np_ * cV;
+    double* gF = gR + np_ * cR;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int n = min(nn[i], max_nb);
         const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
@@ -277,11 +291,12 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline(int64_t N, int64_t Np,
             double r = sqrt(r2);
             if (r >= P.rc) continue;
             double w = (gx * dx + gy * dy + gz * dz) / r;
-            spline_adj(P, 0, r, 0.5 * ge, w, gV);
-            spline_adj(P, 1, r, aF, w * (Fpi + Fp[j]), gR);
+            const int pt = pair_tab<MD_POT_SPLINE>(P, x, i, j);
+            spline_adj(P, 0, r, 0.5 * ge, w, gV + pt * cV);
+            spline_adj(P, 1, r, aF, w * (Fpi + Fp[j]), gR + pt * cR);
         }
         // embedding: u_i dF'/dtheta + gE dF/dtheta at rho_i
-        spline_adj(P, 2, rho[i], ge, u[i], gF);
+        spline_adj(P, 2, rho[i], ge, u[i], gF + atom_tab<MD_POT_SPLINE>(P, x, i) * cF);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < ncoef; k += NT) partial[(int64_t)blockIdx.x * ncoef + k] = sg[k];
@@ -292,15 +307,21 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline(int64_t N, int64_t Np,
 // c2 = M_k/2, c3 = (M_{k+1}-M_k)/(6h), M = T^{-1} D y with T the symmetric
 // tridiagonal (h/6, 2h/3, h/6) on interior knots and (D y)_k =
 // (y_{k+1} - 2 y_k + y_{k-1})/h): gy = (d coef/d y)^T gc.
+// One thread per table: np_ V tables (n0 knots), np_ rho tables (n1), nt F
+// tables (n2), in the knot order.
 __global__ void k_spline_adjoint(const double* __restrict__ gc_all, double* __restrict__ work,
                                  double* __restrict__ gy_all, int n0, int n1, int n2, double h0, double h1,
-                                 double h2) {
-    int w = threadIdx.x;
-    if (w >= 3) return;
-    int n = w == 0 ? n0 : (w == 1 ? n1 : n2);
-    int koff = w == 0 ? 0 : (w == 1 ? n0 : n0 + n1);             // knot offset
-    int coff = w == 0 ? 0 : (w == 1 ? 4 * (n0 - 1) : 4 * (n0 - 1) + 4 * (n1 - 1));  // coefficient offset
-    double h = w == 0 ? h0 : (w == 1 ? h1 : h2);
+                                 double h2, int np_, int nt) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= 2 * np_ + nt) return;
+    const int kind = w < np_ ? 0 : (w < 2 * np_ ? 1 : 2);
+    const int n = kind == 0 ? n0 : (kind == 1 ? n1 : n2);
+    const int t = kind == 0 ? w : (kind == 1 ? w - np_ : w - 2 * np_);  // table within its kind
+    const int koff = kind == 0 ? t * n0 : (kind == 1 ? np_ * n0 + t * n1 : np_ * (n0 + n1) + t * n2);
+    const int coff = kind == 0 ? t * 4 * (n0 - 1)
+                               : (kind == 1 ? np_ * 4 * (n0 - 1) + t * 4 * (n1 - 1)
+                                            : np_ * 4 * (n0 - 1 + n1 - 1) + t * 4 * (n2 - 1));
+    const double h = kind == 0 ? h0 : (kind == 1 ? h1 : h2);
     const double* gc = gc_all + coff;
     double* gy = gy_all + koff;
     double* gM = work + 3 * koff;  // [n]
@@ -369,10 +390,10 @@ __global__ void __launch_bounds__(kGNT) k_grad_rho_mixed(int64_t N, int64_t Np, 
         float dx, dy, dz;
         sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2)));
+        if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2), species_pair<KIND>(P, oi, xo[j])));
         if ((k & kGroupMask) == kGroupMask) acc.flush();
     }
-    store_embedding<KIND>(P, acc.value(), i, rho, Fp, Fpp);
+    store_embedding<KIND>(P, acc.value(), i, rho, Fp, Fpp, KIND == MD_POT_SPLINE ? off_type(oi) : 0);
 }
 
 template <int KIND, bool WIDE>
@@ -395,7 +416,7 @@ __global__ void __launch_bounds__(kGNT) k_grad_u_mixed(int64_t N, int64_t Np, Ge
         if (r2 < P.f_rc2) {
             float rinv = rsqrtf(r2);
             float phi, dphi, fr, dfr;
-            pair_allf<KIND>(P, r2 * rinv, phi, dphi, fr, dfr);
+            pair_allf<KIND>(P, r2 * rinv, phi, dphi, fr, dfr, species_pair<KIND>(P, oi, xo[j]));
             float w = (float)(gx - gs[j]) * dx + (float)(gy - gs[Np + j]) * dy + (float)(gz - gs[2 * Np + j]) * dz;
             acc.add(w * dfr * rinv);
         }
@@ -479,9 +500,11 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline_mixed(int64_t N, int64
     extern __shared__ double sg[];  // [ncoef] as in k_grad_param_spline
     for (int k = threadIdx.x; k < ncoef; k += NT) sg[k] = 0.0;
     __syncthreads();
+    const int np_ = P.n_types * (P.n_types + 1) / 2;
+    const int cV = 4 * (P.sn[0] - 1), cR = 4 * (P.sn[1] - 1), cF = 4 * (P.sn[2] - 1);
     double* gV = sg;
-    double* gR = sg + 4 * (P.sn[0] - 1);
-    double* gF = gR + 4 * (P.sn[1] - 1);
+    double* gR = sg + np_ * cV;
+    double* gF = gR + np_ * cR;
     const float rcf = (float)P.rc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const CellSep cs = cell_sep<false>(g, CellSep{}, i);
@@ -501,13 +524,33 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline_mixed(int64_t N, int64
             float r = r2 * rinv;
             if (r >= rcf) continue;
             const double w = (double)((gx * dx + gy * dy + gz * dz) * rinv);
-            spline_adj(P, 0, (double)r, 0.5 * ge, w, gV);
-            spline_adj(P, 1, (double)r, aF, w * (Fpi + Fp[j]), gR);
+            const int pt = species_pair<MD_POT_SPLINE>(P, oi, xo[j]);
+            spline_adj(P, 0, (double)r, 0.5 * ge, w, gV + pt * cV);
+            spline_adj(P, 1, (double)r, aF, w * (Fpi + Fp[j]), gR + pt * cR);
         }
-        spline_adj(P, 2, rho[i], ge, u[i], gF);
+        spline_adj(P, 2, rho[i], ge, u[i], gF + off_type(oi) * cF);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < ncoef; k += NT) partial[(int64_t)blockIdx.x * ncoef + k] = sg[k];
+}
+
+// Spline coefficient count over all tables: P pair tables each for V and rho,
+// T embedding tables, 4 (n - 1) coefficients per table.
+static int spline_ncoef(const Engine& e) {
+    const md_potential& p = e.pot_host;
+    const int T = e.pot.n_types, P = T * (T + 1) / 2;
+    return 4 * (P * (p.n_phi - 1) + P * (p.n_f - 1) + T * (p.n_F - 1));
+}
+static int spline_nknots(const Engine& e) {
+    const md_potential& p = e.pot_host;
+    const int T = e.pot.n_types, P = T * (T + 1) / 2;
+    return P * p.n_phi + P * p.n_f + T * p.n_F;
+}
+static void launch_spline_adjoint(Engine& e, double* grad, cudaStream_t s) {
+    const md_potential& p = e.pot_host;
+    const int T = e.pot.n_types, P = T * (T + 1) / 2;
+    k_spline_adjoint<<<1, 32, 0, s>>>(e.grad_coef, e.spline_work, grad, p.n_phi, p.n_f, p.n_F, e.pot.sh[0],
+                                      e.pot.sh[1], e.pot.sh[2], P, T);
 }
 
 template <int KIND, bool WIDE>
@@ -527,8 +570,7 @@ static int grad_mixed_impl(Engine& e, const double* g_f, const double* g_e, doub
         k_sum_partials<<<kRglParams, 256, 0, s>>>(e.grad_blocks, kRglParams, e.grad_partial, grad);
         e.launches += 2;
     } else {
-        const md_potential& p = e.pot_host;
-        int ncoef = 4 * (p.n_phi - 1) + 4 * (p.n_f - 1) + 4 * (p.n_F - 1);
+        int ncoef = spline_ncoef(e);
         size_t smem = (size_t)ncoef * sizeof(double);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_grad_param_spline_mixed<kGNT, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -537,8 +579,7 @@ static int grad_mixed_impl(Engine& e, const double* g_f, const double* g_e, doub
             e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp, e.grad_u,
             ncoef, e.grad_partial);
         k_sum_partials<<<ncoef, 256, 0, s>>>(e.grad_blocks, ncoef, e.grad_partial, e.grad_coef);
-        k_spline_adjoint<<<1, 32, 0, s>>>(e.grad_coef, e.spline_work, grad, p.n_phi, p.n_f, p.n_F, e.pot.sh[0],
-                                          e.pot.sh[1], e.pot.sh[2]);
+        launch_spline_adjoint(e, grad, s);
         e.launches += 3;
     }
     return MD_OK;
@@ -559,24 +600,22 @@ static int grad_impl(Engine& e, const double* g_f, const double* g_e, double* gr
         k_sum_partials<<<kRglParams, 256, 0, s>>>(npb, kRglParams, e.grad_partial, grad);
         e.launches += 2;
     } else {
-        const md_potential& p = e.pot_host;
-        int ncoef = 4 * (p.n_phi - 1) + 4 * (p.n_f - 1) + 4 * (p.n_F - 1);
+        int ncoef = spline_ncoef(e);
         size_t smem = (size_t)ncoef * sizeof(double);
         k_grad_param_spline<kGNT><<<npb, kGNT, smem, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb,
                                                           e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp, e.grad_u, ncoef,
                                                           e.grad_partial);
         k_sum_partials<<<ncoef, 256, 0, s>>>(npb, ncoef, e.grad_partial, e.grad_coef);
-        k_spline_adjoint<<<1, 32, 0, s>>>(e.grad_coef, e.spline_work, grad, p.n_phi, p.n_f, p.n_F, e.pot.sh[0],
-                                          e.pot.sh[1], e.pot.sh[2]);
+        launch_spline_adjoint(e, grad, s);
         e.launches += 3;
     }
     return MD_OK;
 }
 
 int launch_param_grad(Engine& e, const double* g_f, const double* g_e, double* grad, cudaStream_t s) {
-    if (e.N == 0) return cudaMemsetAsync(grad, 0, sizeof(double) * (e.pot_host.kind == MD_POT_SPLINE ?
-                                              e.pot_host.n_phi + e.pot_host.n_f + e.pot_host.n_F : 5), s) ==
-                                  cudaSuccess ? MD_OK : MD_ERR_CUDA;
+    if (e.N == 0)
+        return cudaMemsetAsync(grad, 0, sizeof(double) * (e.pot.kind == MD_POT_SPLINE ? spline_nknots(e) : 5), s) ==
+                       cudaSuccess ? MD_OK : MD_ERR_CUDA;
     // mixed precision: float32 pair geometry and pair functions in the
     // adjoint as in the forward pass
     const bool mixed = e.cfg.precision == MD_MIXED;
@@ -587,8 +626,7 @@ int launch_param_grad(Engine& e, const double* g_f, const double* g_e, double* g
         return grad_impl<MD_POT_RGL>(e, g_f, g_e, grad, s);
     }
     if (e.pot.kind == MD_POT_SPLINE) {
-        const md_potential& p = e.pot_host;
-        int ncoef = 4 * (p.n_phi - 1) + 4 * (p.n_f - 1) + 4 * (p.n_F - 1);
+        int ncoef = spline_ncoef(e);
         if ((size_t)ncoef * sizeof(double) > 200 * 1024) return MD_ERR_UNSUPPORTED;
         if (mixed)
             return e.wide ? grad_mixed_impl<MD_POT_SPLINE, true>(e, g_f, g_e, grad, s)

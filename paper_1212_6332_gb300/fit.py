@@ -5,8 +5,9 @@ forward(theta) sets the potential parameters of a batch of fixed
 configurations (md_batch_set_potential re-evaluates forces at the stored
 positions and neighbour lists) and returns forces [N, 3] and per-box
 energies [B]; backward(dL/dF, dL/dE) returns dL/dtheta from the adjoint
-kernels. theta is a float64 tensor: (A, xi, p, q, r0) for RGL, or the
-concatenated V, rho and F knot values for a spline model.
+kernels. theta is a float64 tensor: (A, xi, p, q, r0) for RGL, the
+concatenated V, rho and F knot values for a spline model, or for several
+species all V pair tables, then all rho pair tables, then the F tables.
 """
 from __future__ import annotations
 
@@ -23,7 +24,10 @@ def theta_of(spec: dict) -> torch.Tensor:
         return torch.tensor([spec[k] for k in RGL_KEYS], dtype=torch.float64)
     if spec["kind"] == "spline":
         return torch.tensor(np.concatenate([spec["phi"], spec["f"], spec["F"]]), dtype=torch.float64)
-    raise ValueError("fitting supports RGL and spline potentials")
+    if spec["kind"] == "alloy":
+        tabs = [np.asarray(t, dtype=np.float64) for key in ("phi", "f", "F") for t in spec[key]]
+        return torch.tensor(np.concatenate(tabs), dtype=torch.float64)
+    raise ValueError("fitting supports RGL, spline and alloy potentials")
 
 
 def spec_of(theta: torch.Tensor, template: dict) -> dict:
@@ -31,6 +35,14 @@ def spec_of(theta: torch.Tensor, template: dict) -> dict:
     spec = dict(template)
     if template["kind"] == "rgl":
         spec.update({k: float(v) for k, v in zip(RGL_KEYS, vals)})
+    elif template["kind"] == "alloy":
+        off = 0
+        for key in ("phi", "f", "F"):
+            tabs = []
+            for t in template[key]:
+                tabs.append(vals[off:off + len(t)].copy())
+                off += len(t)
+            spec[key] = tabs
     else:
         a, b = len(template["phi"]), len(template["f"])
         spec["phi"], spec["f"], spec["F"] = vals[:a].copy(), vals[a:a + b].copy(), vals[a + b:].copy()
@@ -70,12 +82,17 @@ def force_matching_loss(f, e_box, f_tgt, e_tgt, counts, w_e: float = 0.1):
     return (per_cfg + w_e * de * de).mean()
 
 
-def make_batch(spec: dict, configs, skin: float = 0.0, precision: str = "fp64", mass: float = 63.546) -> System:
-    """A batch System holding fixed configurations (inputs.Box objects)."""
+def make_batch(spec: dict, configs, skin: float = 0.0, precision: str = "fp64", mass: float = 63.546,
+               types=None) -> System:
+    """A batch System holding fixed configurations (inputs.Box objects);
+    types (one label per atom, configurations concatenated) for a potential
+    with several species."""
     offs = np.zeros(len(configs) + 1, dtype=np.int64)
     offs[1:] = np.cumsum([c.n for c in configs])
     s = System(spec, boxes=np.stack([c.box for c in configs]), atom_offsets=offs, skin=skin, mass=mass,
                precision=precision)
+    if types is not None:
+        s.set_types(types)
     x = torch.tensor(np.concatenate([c.x for c in configs]), device="cuda")
     s.set_state(x)
     return s
