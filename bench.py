@@ -66,11 +66,11 @@ KERNELS = {
 # is provided): 152 SMs x 2 float64 FMA per clock x 2 flop x 2.07 GHz
 # (an FMA-chain probe measured 1.20 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per atom of one k_pairs_half launch, from the ncu
-# capture summarised in profiles/k_pairs_half_rgl_cu_1m_fp64.md (1,048,576
-# atoms of the same lattice, potential and temperature: 1.763 GB read +
-# 2.719 GB written); traffic grows in proportion to the atom count.
-PAIRS_DRAM_BYTES_PER_ATOM = (1.762863e9 + 2.718543e9) / 1048576
+# DRAM bytes (read + write) per atom of one k_pairs_half launch, from an ncu
+# capture of 1,048,576 atoms of the same lattice, potential and temperature
+# (0.454 GB read + 1.776 GB written); traffic grows in proportion to the
+# atom count.
+PAIRS_DRAM_BYTES_PER_ATOM = (0.454266e9 + 1.775963e9) / 1048576
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
            0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
@@ -228,17 +228,20 @@ def run_reference(args):
 
 
 def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=None, thermostat=None,
-                barostat=None, types=None) -> dict:
+                barostat=None, types=None, newton3=False) -> dict:
     """atom-steps/s of a box in another precision or potential (same timing
     rules), with its per-phase times; optionally with the friction of
-    Eq. (4) (thermostat = (T_e, tau_T)) or the pressure coupling of Eq. (5)
-    (barostat = (P0, tau_p, beta))."""
+    Eq. (4) (thermostat = (T_e, tau_T)), the pressure coupling of Eq. (5)
+    (barostat = (P0, tau_p, beta)) or the half-list sums with Newton's
+    third law."""
     import torch
     from paper_1212_6332_gb300.md import System
     spec = spec or I.RGL_CU
     s = System(spec, box=box, n_atoms=len(x_h), skin=SKIN, dt=DT, mass=mass or I.MASS_CU, precision=precision)
     if types is not None:
         s.set_types(types)
+    if newton3:
+        s.set_newton3(True)
     if thermostat:
         s.set_thermostat(*thermostat)
     if barostat:
@@ -452,6 +455,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10, help="host-buffer end-to-end steps (0 skips the leg)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the headline box (default float64)")
+    ap.add_argument("--batch-boxes", type=int, default=0,
+                    help="only the tile-schedule batch leg with this many boxes (profiling runs; prints its dict)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -468,6 +473,9 @@ def main():
 
     from paper_1212_6332_gb300 import build
     build.build()
+    if args.batch_boxes:
+        print(json.dumps(run_batch(args.precision, K, W, n_boxes=args.batch_boxes)))
+        return
     from paper_1212_6332_gb300.md import System
 
     bx = I.perturbed_fcc(args.cells, I.A_CU, TEMP, I.MASS_CU, SEED)
@@ -558,6 +566,9 @@ def main():
         variants["ni_2m_fp64"] = run_variant("fp64", W, K, ni.x, ni.v, ni.box, spec=I.RGL_NI, mass=I.MASS_NI)
         variants["ni_2m_mixed"] = run_variant("mixed", W, K, ni.x, ni.v, ni.box, spec=I.RGL_NI, mass=I.MASS_NI)
         del ni
+        # full-list sums against Newton's third law, both with phase events
+        variants["fp64_phases"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box)
+        variants["fp64_newton3"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box, newton3=True)
         variants["fp64_thermostat"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box, thermostat=(300.0, 100.0))
         variants["fp64_barostat"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box,
                                                 barostat=(0.0, 1000.0, 160.21766208 / 140.0))

@@ -263,6 +263,20 @@ MD_API int md_batch_set_potential(md_batch* b, const md_potential* pot, md_strea
  * non-finite T_e or a non-finite tau_T. */
 MD_API int md_set_thermostat(md_batch* b, double T_e, double tau_T);
 
+/* Float64 force evaluation with Newton's third law (the paper's CPU scheme,
+ * Sec. 4.3) instead of full-list sums: the density and force passes walk
+ * only the upper half of each neighbour list (j > i) and add every pair's
+ * rho, V and force to both atoms, to the partner by float64 atomic adds.
+ * Half the cached bytes and float64 operations of the two sums; the order
+ * in which the atomics land varies, so results agree with the full-list
+ * passes to rounding, not bit for bit, and repeated runs may differ in the
+ * last bits (the full-list default is reproducible). Per-atom virials hold
+ * each pair once (box pressures are unchanged). on = 0 restores the
+ * default. Applies to single-box and tile-schedule steps; the box schedule
+ * keeps its own in-shared-memory sums. Errors: MD_ERR_ARG for a NULL
+ * handle; MD_ERR_UNSUPPORTED for a mixed-precision handle. */
+MD_API int md_set_newton3(md_batch* b, int on);
+
 /* Species of every atom, types [n] in caller order (host or device), each
  * in [0, n_types) of the potential; all atoms are species 0 until set.
  * Applies to the current state at once (forces are re-evaluated) and to

@@ -226,7 +226,7 @@ void free_engine(Engine& e) {
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
     dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
-    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.ab); dfree(e.fv); dfree(e.rev); dfree(e.n_up); dfree(e.exp_T);
+    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.pc); dfree(e.rev); dfree(e.n_up); dfree(e.exp_T);
     dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
     dfree(e.grad_g); dfree(e.grad_u); dfree(e.grad_Fpp); dfree(e.grad_partial); dfree(e.grad_coef); dfree(e.stage); dfree(e.red);
     dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box); dfree(e.types); dfree(e.due_cells); dfree(e.w_atom); dfree(e.red_w); dfree(e.press_box); dfree(e.mu_box);
@@ -423,8 +423,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.nn, Np);
     AL(e.nl, (size_t)e.max_nb * Np);
     if (cfg->precision == MD_FP64) {
-        AL(e.ab, (size_t)e.max_nb * Np);
-        AL(e.fv, (size_t)e.max_nb * Np);
+        AL(e.pc, (size_t)e.max_nb * Np);
         AL(e.rev, (size_t)e.max_nb * Np);
         AL(e.n_up, Np);
     }
@@ -565,21 +564,17 @@ int grow_list(Engine* E, int needed) {
     m = (m + 7) / 8 * 8;
     int* nl = nullptr;
     if (dalloc(E, &nl, (size_t)m * e.N_pad) != MD_OK) return MD_ERR_NOMEM;
-    if (e.ab) {
-        double2 *ab = nullptr, *fv = nullptr;
+    if (e.pc) {
+        double4_32a* pc = nullptr;
         int* rev = nullptr;
-        if (dalloc(E, &ab, (size_t)m * e.N_pad) != MD_OK || dalloc(E, &fv, (size_t)m * e.N_pad) != MD_OK ||
-            dalloc(E, &rev, (size_t)m * e.N_pad) != MD_OK) {
+        if (dalloc(E, &pc, (size_t)m * e.N_pad) != MD_OK || dalloc(E, &rev, (size_t)m * e.N_pad) != MD_OK) {
             cudaFree(nl);
-            if (ab) cudaFree(ab);
-            if (fv) cudaFree(fv);
+            if (pc) cudaFree(pc);
             return MD_ERR_NOMEM;
         }
-        cudaFree(e.ab);
-        cudaFree(e.fv);
+        cudaFree(e.pc);
         cudaFree(e.rev);
-        e.ab = ab;
-        e.fv = fv;
+        e.pc = pc;
         e.rev = rev;
     }
     cudaFree(e.nl);
@@ -1131,6 +1126,15 @@ int md_set_thermostat(md_batch* b, double T_e, double tau_T) {
     bath.m_3kb = E->cfg.mass * kMVV / (3.0 * kBoltz);
     E->bath = bath;
     destroy_graphs(*E);  // captured launches carry the old parameters
+    return MD_OK;
+}
+
+int md_set_newton3(md_batch* b, int on) {
+    if (!b) return MD_ERR_ARG;
+    Engine* E = &b->e;
+    if (on && E->cfg.precision != MD_FP64) return fail(E, MD_ERR_UNSUPPORTED, "Newton's third law variant is float64 only");
+    E->newton3 = on != 0;
+    destroy_graphs(*E);  // captured launches are those of the other variant
     return MD_OK;
 }
 

@@ -42,7 +42,7 @@ struct BoxArgs {
     int* cell_t;
     int* nn;
     int* nl;
-    double2* ab;
+    double2* ab;  // (V'/r, rho'/r) halves of the float64 pair cache entries: ab[2 slot]
     int* n_up;  // float64 tile path's list layout data, kept valid across schedules
     int* rev;
     Ctl* ctl;
@@ -288,7 +288,7 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
                 // round-to-nearest adds in list order: do exactly that
                 r_i = __dadd_rn(r_i, fr);
                 ep = __dadd_rn(ep, phi);
-                A.ab[slot] = c;
+                A.ab[2 * slot] = c;
             }
             double F, Fpi;
             embed<KIND>(P, r_i, F, Fpi);
@@ -307,7 +307,7 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
             double fx = 0.0, fy = 0.0, fz = 0.0;
             for (int k = 0; k < n; ++k) {
                 const int64_t slot = (int64_t)k * A.Np + i;
-                double2 c = A.ab[slot];
+                double2 c = A.ab[2 * slot];
                 if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
                 const int e = A.nl[slot];
                 const int jl = entry_slot(e) - (int)a0;
@@ -426,7 +426,7 @@ static void box_launch(Engine& e, int n_steps, cudaStream_t s) {
     A.cell_t = e.cell_t;
     A.nn = e.nn;
     A.nl = e.nl;
-    A.ab = e.ab;
+    A.ab = reinterpret_cast<double2*>(e.pc);
     A.n_up = e.n_up;
     A.rev = e.rev;
     A.ctl = e.ctl;

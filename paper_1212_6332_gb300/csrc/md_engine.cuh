@@ -183,8 +183,10 @@ struct Engine {
     int* scan_tmp = nullptr;
     int* nn = nullptr;          // [N_pad]
     int* nl = nullptr;          // [max_nb][N_pad] column-major
-    double2* ab = nullptr;      // float64 path: [max_nb][N_pad] (V'/r, rho'/r) per list entry
-    double2* fv = nullptr;      // float64 path: [max_nb][N_pad] (rho(r), V(r)) per list entry
+    // float64 path: [max_nb][N_pad] pair cache, per list entry (V'/r, rho'/r,
+    // rho(r), V(r)) in one 32-byte sector, so the scattered mirror writes of
+    // the pair pass are whole sectors (no read-modify-write fills)
+    double4_32a* pc = nullptr;
     int* rev = nullptr;         // float64 path: [max_nb][N_pad] partner position of upper entries
     int* n_up = nullptr;        // float64 path: [N_pad] upper entries of each list (lists are [upper | lower])
     double* exp_T = nullptr;    // exponential table
@@ -209,6 +211,7 @@ struct Engine {
     bool have_state = false;
     bool lists_ok = false;  // lists, cells and build positions agree (a state load may keep them)
     Bath bath{};            // friction of Eq. (4) applied in the kicks (md_set_thermostat)
+    bool newton3 = false;   // float64 half-list sums with Newton's third law (md_set_newton3)
     Baro baro{};            // pressure coupling of Eq. (5) after each step (md_set_barostat)
     int* types = nullptr;   // [N] species of each atom, caller order (md_set_types; 0 by default)
     double* w_atom = nullptr;   // [N_pad] per-atom virial -1/2 sum_j s_ij r_ij^2 (pressure users only)

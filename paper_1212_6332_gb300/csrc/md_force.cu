@@ -56,18 +56,25 @@ struct PairQueue {
     int pt[2][kQueue];         // type-pair table (several species)
 };
 
-template <int KIND>
+// Pair cache entry (V'/r, rho'/r, rho(r), V(r)): written as one 32-byte
+// sector, read by the sums as its (V'/r, rho'/r) or (rho, V) half.
+__device__ __forceinline__ double2 cache_ab(const double4_32a* __restrict__ pc, int64_t slot) {
+    return reinterpret_cast<const double2*>(pc)[2 * slot];
+}
+__device__ __forceinline__ double2 cache_fv(const double4_32a* __restrict__ pc, int64_t slot) {
+    return reinterpret_cast<const double2*>(pc)[2 * slot + 1];
+}
+
+template <int KIND, bool MIRROR>
 __device__ __forceinline__ void eval_queued(const Pot& P, const PairQueue& q, int r, int p,
-                                            double2* __restrict__ ab, double2* __restrict__ fv) {
+                                            double4_32a* __restrict__ pc) {
     const double r2 = norm2(q.d[0][r][p], q.d[1][r][p], q.d[2][r][p]);
-    double2 c = make_double2(0.0, 0.0), w = make_double2(0.0, 0.0);
+    double A = 0.0, B = 0.0, V = 0.0, fr = 0.0;
     const int pt = KIND == MD_POT_SPLINE ? q.pt[r][p] : 0;
-    if (below(r2, P.rc2)) pair_eval<KIND>(P, P.exp_T, r2, w.y, w.x, c.x, c.y, pt);
-    const long long own = q.own[r][p], mir = q.mir[r][p];
-    ab[own] = c;
-    fv[own] = w;
-    ab[mir] = c;
-    fv[mir] = w;
+    if (below(r2, P.rc2)) pair_eval<KIND>(P, P.exp_T, r2, V, fr, A, B, pt);
+    const double4_32a c = make_double4_32a(A, B, fr, V);
+    pc[q.own[r][p]] = c;
+    if (MIRROR) pc[q.mir[r][p]] = c;
 }
 
 // One list row of a lane: the entry and, for an upper entry (j > i), the
@@ -79,6 +86,7 @@ struct PairRow {
     bool upper;
 };
 
+template <bool MIRROR>
 __device__ __forceinline__ PairRow load_pair_row(int e, bool valid, int64_t i, const float4* __restrict__ xo,
                                                  const double4_32a* __restrict__ x, const int* __restrict__ rev,
                                                  int64_t Np, int k) {
@@ -92,19 +100,20 @@ __device__ __forceinline__ PairRow load_pair_row(int e, bool valid, int64_t i, c
         const int j = entry_slot(e);
         r.oj = xo[j];
         r.xj = x[j];
-        r.rv = rev[(int64_t)k * Np + i];
+        if (MIRROR) r.rv = rev[(int64_t)k * Np + i];
     }
     return r;
 }
 
-template <int KIND, bool SINGLE>
+// MIRROR = false (Newton's third law variant): only the upper slot of each
+// pair is written; the lower slots are never read.
+template <int KIND, bool SINGLE, bool MIRROR>
 __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P, float rc2f,
                                                      float rs2f, const double4_32a* __restrict__ x,
                                                      const float4* __restrict__ xo, const int* __restrict__ nn,
                                                      const int* __restrict__ nl, const int* __restrict__ rev,
                                                      const int* __restrict__ n_up, int max_nb,
-                                                     double2* __restrict__ ab, double2* __restrict__ fv,
-                                                     const Ctl* ctl) {
+                                                     double4_32a* __restrict__ pc, const Ctl* ctl) {
     if (load_status(ctl)) return;
     __shared__ PairQueue queues[kFNT / 32];
     const int lane = threadIdx.x & 31;
@@ -136,10 +145,10 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
         // software pipeline: the list entry two rows ahead and the partner
         // data (offset, position, mirror row) one row ahead are in flight
         // while a row is screened, so the loop does not wait on L2 / HBM
-        PairRow cur = load_pair_row(0 < kend ? nl[i] : 0, 0 < kend, i, xo, x, rev, Np, 0);
+        PairRow cur = load_pair_row<MIRROR>(0 < kend ? nl[i] : 0, 0 < kend, i, xo, x, rev, Np, 0);
         int e_ahead = 1 < kend ? nl[Np + i] : 0;
         for (int k = 0; k < kmax; ++k) {
-            const PairRow nxt = load_pair_row(e_ahead, k + 1 < kend, i, xo, x, rev, Np, k + 1);
+            const PairRow nxt = load_pair_row<MIRROR>(e_ahead, k + 1 < kend, i, xo, x, rev, Np, k + 1);
             e_ahead = k + 2 < kend ? nl[(int64_t)(k + 2) * Np + i] : 0;
             bool in = false, tq = false;
             double dx = 0.0, dy = 0.0, dz = 0.0;
@@ -157,11 +166,9 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
                     tq = r2f > rs2f;
                     sep_entry(xi, cur.xj, entry_code(cur.e), L, dx, dy, dz);
                 } else {
-                    const double2 z = make_double2(0.0, 0.0);
-                    ab[own] = z;
-                    fv[own] = z;
-                    ab[mir] = z;
-                    fv[mir] = z;
+                    const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+                    pc[own] = z;
+                    if (MIRROR) pc[mir] = z;
                 }
             }
             cur = nxt;
@@ -185,7 +192,7 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
             for (int r = 0; r < 2; ++r) {
                 if (qn[r] >= 32) {
                     qn[r] -= 32;
-                    eval_queued<KIND>(P, q, r, qn[r] + lane, ab, fv);
+                    eval_queued<KIND, MIRROR>(P, q, r, qn[r] + lane, pc);
                     __syncwarp();
                 }
             }
@@ -195,13 +202,13 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
     // pair_eval, which still costs less than two part-empty batches)
     if (qn[0] + qn[1] <= 32) {
         if (lane < qn[0])
-            eval_queued<KIND>(P, q, 0, lane, ab, fv);
+            eval_queued<KIND, MIRROR>(P, q, 0, lane, pc);
         else if (lane < qn[0] + qn[1])
-            eval_queued<KIND>(P, q, 1, lane - qn[0], ab, fv);
+            eval_queued<KIND, MIRROR>(P, q, 1, lane - qn[0], pc);
     } else {
 #pragma unroll
         for (int r = 0; r < 2; ++r)
-            if (lane < qn[r]) eval_queued<KIND>(P, q, r, lane, ab, fv);
+            if (lane < qn[r]) eval_queued<KIND, MIRROR>(P, q, r, lane, pc);
     }
 }
 
@@ -218,7 +225,7 @@ __device__ __forceinline__ bool is_zero2(double2 c) {
 
 template <int KIND>
 __global__ void __launch_bounds__(kFNT) k_rho_sum(int64_t N, int64_t Np, Pot P, const int* __restrict__ nn,
-                                                  int max_nb, const double2* __restrict__ fv,
+                                                  int max_nb, const double4_32a* __restrict__ pc,
                                                   const double4_32a* __restrict__ x, double* __restrict__ rho,
                                                   double* __restrict__ Fp, double* __restrict__ e_atom,
                                                   const Ctl* ctl) {
@@ -231,16 +238,16 @@ __global__ void __launch_bounds__(kFNT) k_rho_sum(int64_t N, int64_t Np, Pot P, 
     // same values in the same order and must not fuse them differently
     double r_i = 0.0, ep = 0.0;
     int k = 0;
-    double2 w = n > 0 ? fv[i] : zero;
+    double2 w = n > 0 ? cache_fv(pc, i) : zero;
     while (true) {
         while (k < n && is_zero2(w)) {
             ++k;
-            w = k < n ? fv[(int64_t)k * Np + i] : zero;
+            w = k < n ? cache_fv(pc, (int64_t)k * Np + i) : zero;
         }
         const bool has = k < n;
         if (!__any_sync(0xffffffffu, has)) break;
         if (has) {
-            const double2 wn = k + 1 < n ? fv[(int64_t)(k + 1) * Np + i] : zero;
+            const double2 wn = k + 1 < n ? cache_fv(pc, (int64_t)(k + 1) * Np + i) : zero;
             r_i = __dadd_rn(r_i, w.x);
             ep = __dadd_rn(ep, w.y);
             ++k;
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(kFNT) k_rho_sum(int64_t N, int64_t Np, Pot P, 
 template <bool SINGLE, bool VIR>
 __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, const double4_32a* __restrict__ x,
                                                 const int* __restrict__ nn, const int* __restrict__ nl, int max_nb,
-                                                const double2* __restrict__ ab, const double* __restrict__ Fp,
+                                                const double4_32a* __restrict__ pc, const double* __restrict__ Fp,
                                                 double* __restrict__ f, double* __restrict__ v, double c_kick,
                                                 Bath bath, double* __restrict__ w_atom, const Ctl* ctl) {
     if (load_status(ctl)) return;
@@ -281,17 +288,17 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
     const double2 zero = make_double2(0.0, 0.0);
     double fx = 0.0, fy = 0.0, fz = 0.0, w = 0.0;
     int k = 0;
-    double2 c = n > 0 ? ab[i] : zero;
+    double2 c = n > 0 ? cache_ab(pc, i) : zero;
     while (true) {
         while (k < n && is_zero2(c)) {
             ++k;
-            c = k < n ? ab[(int64_t)k * Np + i] : zero;
+            c = k < n ? cache_ab(pc, (int64_t)k * Np + i) : zero;
         }
         const bool has = k < n;
         if (!__any_sync(0xffffffffu, has)) break;
         if (has) {
             const int64_t slot = (int64_t)k * Np + i;
-            const double2 cn = k + 1 < n ? ab[slot + Np] : zero;
+            const double2 cn = k + 1 < n ? cache_ab(pc, slot + Np) : zero;
             const int e = nl[slot];
             const int j = entry_slot(e);
             double dx, dy, dz;
@@ -319,6 +326,122 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
     }
 }
 
+// ---------------------------------------------------------------- Newton's third law
+//
+// Float64 variant in the style of the paper's CPU code (Sec. 4.3): the pair
+// pass writes only the upper slot of each pair, and the density and force
+// passes walk only the upper entries of each list, adding every pair's term
+// to both atoms, to the partner by a float64 atomic add (rho_j, V_ij, and
+// -s_ij d_ij for the force). That halves the cache bytes and the float64
+// work of both sums at the price of one atomic per pair and component; the
+// order in which the atomics land varies, so the last bits of rho, F and
+// e_atom vary from run to run (the full-list passes are reproducible).
+// rho, e_atom and f are zeroed before their passes.
+
+// Upper entries of a list: rows 0..n_up-1 of a rotated list, else (a list
+// kept ascending) the entries with j > i among all rows.
+__device__ __forceinline__ int upper_rows(const int* __restrict__ nn, const int* __restrict__ n_up, int max_nb,
+                                          int64_t i) {
+    const int nup = n_up[i];
+    return nup < 0 ? min(nn[i], max_nb) : nup;
+}
+
+__global__ void __launch_bounds__(kFNT) k_rho_n3(int64_t N, int64_t Np, const int* __restrict__ nn,
+                                                 const int* __restrict__ nl, const int* __restrict__ n_up, int max_nb,
+                                                 const double4_32a* __restrict__ pc, double* __restrict__ rho,
+                                                 double* __restrict__ ep, const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int n = upper_rows(nn, n_up, max_nb, i);
+    double r_i = 0.0, e_i = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const int64_t slot = (int64_t)k * Np + i;
+        const double2 w = cache_fv(pc, slot);
+        if (is_zero2(w)) continue;
+        const int j = entry_slot(nl[slot]);
+        if (j <= i) continue;
+        r_i += w.x;
+        e_i += w.y;
+        atomicAdd(&rho[j], w.x);
+        atomicAdd(&ep[j], w.y);
+    }
+    atomicAdd(&rho[i], r_i);
+    atomicAdd(&ep[i], e_i);
+}
+
+// F(rho_i), F'(rho_i); e_atom arrives holding sum_j V_ij and leaves holding
+// F(rho_i) + 1/2 sum_j V_ij.
+template <int KIND>
+__global__ void __launch_bounds__(kFNT) k_embed_n3(int64_t N, Pot P, const double4_32a* __restrict__ x,
+                                                   const double* __restrict__ rho, double* __restrict__ Fp,
+                                                   double* __restrict__ e_atom, const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double F, Fpi;
+    embed<KIND>(P, rho[i], F, Fpi, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0);
+    Fp[i] = Fpi;
+    e_atom[i] = fma(0.5, e_atom[i], F);
+}
+
+// VIR: w_atom[i] = -sum over i's upper pairs of s_ij r_ij^2 (each pair
+// counted once, at its lower slot; the box sums are those of k_force).
+template <bool SINGLE, bool VIR>
+__global__ void __launch_bounds__(kFNT) k_force_n3(int64_t N, int64_t Np, Geo g, const double4_32a* __restrict__ x,
+                                                   const int* __restrict__ nn, const int* __restrict__ nl,
+                                                   const int* __restrict__ n_up, int max_nb,
+                                                   const double4_32a* __restrict__ pc, const double* __restrict__ Fp,
+                                                   double* __restrict__ f, double* __restrict__ w_atom,
+                                                   const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double L[3];
+    const int b = SINGLE ? 0 : g.atom_box[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+    const double4_32a xi = x[i];
+    const double Fpi = Fp[i];
+    const int n = upper_rows(nn, n_up, max_nb, i);
+    double fx = 0.0, fy = 0.0, fz = 0.0, w = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const int64_t slot = (int64_t)k * Np + i;
+        const double2 c = cache_ab(pc, slot);
+        if (is_zero2(c)) continue;
+        const int e = nl[slot];
+        const int j = entry_slot(e);
+        if (j <= i) continue;
+        double dx, dy, dz;
+        sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
+        const double s = fma(Fpi + Fp[j], c.y, c.x);
+        fx = fma(s, dx, fx);
+        fy = fma(s, dy, fy);
+        fz = fma(s, dz, fz);
+        atomicAdd(&f[j], -s * dx);
+        atomicAdd(&f[Np + j], -s * dy);
+        atomicAdd(&f[2 * Np + j], -s * dz);
+        if (VIR) w = fma(s, norm2(dx, dy, dz), w);
+    }
+    atomicAdd(&f[i], fx);
+    atomicAdd(&f[Np + i], fy);
+    atomicAdd(&f[2 * Np + i], fz);
+    if (VIR) w_atom[i] = -w;
+}
+
+// second half-kick (and friction half step) once all force atomics landed
+__global__ void __launch_bounds__(kFNT) k_kick_n3(int64_t N, int64_t Np, const double* __restrict__ f,
+                                                  double* __restrict__ v, double c_kick, Bath bath, const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double vx = v[i] + c_kick * f[i], vy = v[Np + i] + c_kick * f[Np + i], vz = v[2 * Np + i] + c_kick * f[2 * Np + i];
+    bath_half(bath, vx, vy, vz);
+    v[i] = vx;
+    v[Np + i] = vy;
+    v[2 * Np + i] = vz;
+}
+
 void launch_forces_mixed(Engine& e, int kick, cudaStream_t s, bool virial);
 
 // float32 screen threshold: rc^2 (1 + margin), rounded up
@@ -326,11 +449,11 @@ static float screen_r2f(double rc2) { return nextafterf((float)(rc2 * (1.0 + kSc
 
 // persistent pair pass: all resident blocks of this instantiation on every
 // SM, at most one 32-atom group per warp
-template <int KIND, bool SINGLE>
+template <int KIND, bool SINGLE, bool MIRROR>
 static int pair_blocks(const Engine& e) {
     static int per_sm = 0;
     if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_half<KIND, SINGLE>, kFNT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_half<KIND, SINGLE, MIRROR>, kFNT, 0);
         per_sm = std::max(per_sm, 1);
     }
     const int64_t groups = (e.N + 31) / 32, per_block = kFNT / 32;
@@ -345,28 +468,60 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s, bool virial) {
     e.launches += 3;
     {
         PhaseScope scope(e, MD_PHASE_PAIRS, s);
-        k_pairs_half<KIND, SINGLE><<<pair_blocks<KIND, SINGLE>(e), kFNT, 0, s>>>(e.N, e.N_pad, g, single_cell_sep(e), e.pot,
+        k_pairs_half<KIND, SINGLE, true><<<pair_blocks<KIND, SINGLE, true>(e), kFNT, 0, s>>>(e.N, e.N_pad, g, single_cell_sep(e), e.pot,
                                                                    screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.x,
-                                                                   e.xo, e.nn, e.nl, e.rev, e.n_up, e.max_nb, e.ab,
-                                                                   e.fv, e.ctl);
+                                                                   e.xo, e.nn, e.nl, e.rev, e.n_up, e.max_nb, e.pc,
+                                                                   e.ctl);
     }
     {
         PhaseScope scope(e, MD_PHASE_DENSITY, s);
-        k_rho_sum<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.nn, e.max_nb, e.fv, e.x, e.rho, e.Fp, e.e_atom,
+        k_rho_sum<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.nn, e.max_nb, e.pc, e.x, e.rho, e.Fp, e.e_atom,
                                             e.ctl);
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     if (virial)
-        k_force<SINGLE, true><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.ab, e.Fp, e.f,
+        k_force<SINGLE, true><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.pc, e.Fp, e.f,
                                                   kick ? e.v : nullptr, c_kick, e.bath, e.w_atom, e.ctl);
     else
-        k_force<SINGLE, false><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.ab, e.Fp, e.f,
+        k_force<SINGLE, false><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.pc, e.Fp, e.f,
                                                    kick ? e.v : nullptr, c_kick, e.bath, nullptr, e.ctl);
+}
+
+template <int KIND, bool SINGLE>
+static void run_fp64_n3(Engine& e, int kick, cudaStream_t s, bool virial) {
+    Geo g = make_geo(e);
+    const int nb = (int)((e.N + kFNT - 1) / kFNT);
+    const double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
+    e.launches += 4 + (kick ? 1 : 0);
+    {
+        PhaseScope scope(e, MD_PHASE_PAIRS, s);
+        k_pairs_half<KIND, SINGLE, false><<<pair_blocks<KIND, SINGLE, false>(e), kFNT, 0, s>>>(
+            e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.x, e.xo, e.nn,
+            e.nl, e.rev, e.n_up, e.max_nb, e.pc, e.ctl);
+    }
+    {
+        PhaseScope scope(e, MD_PHASE_DENSITY, s);
+        cudaMemsetAsync(e.rho, 0, sizeof(double) * e.N, s);
+        cudaMemsetAsync(e.e_atom, 0, sizeof(double) * e.N, s);
+        k_rho_n3<<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.nn, e.nl, e.n_up, e.max_nb, e.pc, e.rho, e.e_atom, e.ctl);
+        k_embed_n3<KIND><<<nb, kFNT, 0, s>>>(e.N, e.pot, e.x, e.rho, e.Fp, e.e_atom, e.ctl);
+    }
+    PhaseScope scope(e, MD_PHASE_FORCE, s);
+    cudaMemsetAsync(e.f, 0, sizeof(double) * 3 * e.N_pad, s);
+    if (virial)
+        k_force_n3<SINGLE, true><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.n_up, e.max_nb, e.pc, e.Fp,
+                                                     e.f, e.w_atom, e.ctl);
+    else
+        k_force_n3<SINGLE, false><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.n_up, e.max_nb, e.pc,
+                                                      e.Fp, e.f, nullptr, e.ctl);
+    if (kick) k_kick_n3<<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.f, e.v, c_kick, e.bath, e.ctl);
 }
 
 template <int KIND>
 static void run_fp64_k(Engine& e, int kick, cudaStream_t s, bool virial) {
-    if (single_fast(e))
+    if (e.newton3)
+        single_fast(e) ? run_fp64_n3<KIND, true>(e, kick, s, virial) : run_fp64_n3<KIND, false>(e, kick, s, virial);
+    else if (single_fast(e))
         run_fp64<KIND, true>(e, kick, s, virial);
     else
         run_fp64<KIND, false>(e, kick, s, virial);

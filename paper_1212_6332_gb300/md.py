@@ -25,7 +25,7 @@ STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_NOMEM", 4: "
 SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_neighbors", "md_get_neighbors",
            "md_max_count", "md_compute_forces", "md_get_forces", "md_step", "md_get_thermo", "md_batch_create",
            "md_batch_destroy", "md_batch_set_state", "md_batch_get_state", "md_batch_compute_forces",
-           "md_batch_step", "md_batch_set_potential", "md_set_thermostat", "md_set_types", "md_pressure", "md_set_barostat", "md_get_box", "md_param_grad", "md_num_params", "md_status_string",
+           "md_batch_step", "md_batch_set_potential", "md_set_thermostat", "md_set_newton3", "md_set_types", "md_pressure", "md_set_barostat", "md_get_box", "md_param_grad", "md_num_params", "md_status_string",
            "md_last_error", "md_profile_start", "md_profile_read",
            "md_eval_math", "md_forces_noalloc", "md_batch_thermo",
            "md_batch_schedule")
@@ -98,6 +98,7 @@ def load(path: str | pathlib.Path | None = None) -> ctypes.CDLL:
         "md_batch_step": [vp, i32, i32, i32, dp, vp],
         "md_batch_set_potential": [vp, P(Potential), vp],
         "md_set_thermostat": [vp, ctypes.c_double, ctypes.c_double],
+        "md_set_newton3": [vp, ctypes.c_int],
         "md_set_types": [vp, vp, vp],
         "md_pressure": [vp, vp, vp],
         "md_set_barostat": [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double],
@@ -379,6 +380,12 @@ class System:
         """Electron-phonon friction of Eq. (4) towards T_e (K) with time
         constant tau_T (fs) in the following steps; tau_T <= 0 turns it off."""
         self._check(self.lib.md_set_thermostat(self._h, float(T_e), float(tau_T)))
+
+    def set_newton3(self, on: bool = True):
+        """Float64 density and force sums over the upper half of each list
+        with Newton's third law (atomic partner updates; agrees with the
+        default full-list sums to rounding, not bit for bit)."""
+        self._check(self.lib.md_set_newton3(self._h, int(bool(on))))
 
     @property
     def n_params(self) -> int:
