@@ -457,6 +457,8 @@ def main():
                     help="precision of the headline box (default float64)")
     ap.add_argument("--batch-boxes", type=int, default=0,
                     help="only the tile-schedule batch leg with this many boxes (profiling runs; prints its dict)")
+    ap.add_argument("--alloy-only", action="store_true",
+                    help="only the two-species spline alloy box of --cells (profiling runs; prints its dict)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -475,6 +477,11 @@ def main():
     build.build()
     if args.batch_boxes:
         print(json.dumps(run_batch(args.precision, K, W, n_boxes=args.batch_boxes)))
+        return
+    if args.alloy_only:
+        al = I.perturbed_fcc(args.cells, 3.57, TEMP, I.MASS_CU, 5)
+        al_types = np.random.default_rng(5).integers(0, 2, al.n).astype(np.int32)
+        print(json.dumps(run_variant(args.precision, W, K, al.x, al.v, al.box, spec=alloy_model(), types=al_types)))
         return
     from paper_1212_6332_gb300.md import System
 

@@ -155,6 +155,10 @@ void fill_pot(Engine& e) {
             P.sinvhf[w] = (float)P.sinvh[w];
             off += (size_t)ntab[w] * ns[w];
         }
+        P.sq = e.spline_pair_rec;
+        P.sq_n = p.n_phi;
+        P.sq_invhf = (float)P.sinvh[0];
+        P.sq_c0f = (float)(-p.r_lo * P.sinvh[0]);
     } else {
         P.rc = p.r_cut;
         if (p.r_taper < p.r_cut) {
@@ -222,7 +226,7 @@ void free_engine(Engine& e) {
     destroy_graphs(e);
     dfree(e.L); dfree(e.cell_len); dfree(e.cell_len_f); dfree(e.nc); dfree(e.cell_off); dfree(e.atom_off);
     dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.cell_org); dfree(e.spline_coef); dfree(e.spline_coef_f);
-    dfree(e.spline_work); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
+    dfree(e.spline_work); dfree(e.spline_pair_rec); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
     dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
@@ -393,6 +397,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     if (pot->kind == MD_POT_SPLINE) {
         AL(e.spline_coef, nk);
         AL(e.spline_coef_f, nk);
+        if (pot->n_phi == pot->n_f) AL(e.spline_pair_rec, (size_t)pot_pairs(*pot) * (pot->n_phi + 1) * 4);
         AL(e.spline_work, 3 * nk);
         AL(e.knots_dev, nk);
     }

@@ -381,13 +381,30 @@ __device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict
             B = am * (-(P.m * rinv)) * rinv;
         }
     } else {
-        if (r >= P.rc) {
+        if (__double_as_longlong(r) >= __double_as_longlong(P.rc)) {  // r >= rc (both non-negative)
             phi = fr = A = B = 0.0;
             return;
         }
         double dphi, dfr;
-        spline_eval(P, 0, r, phi, dphi, pt);
-        spline_eval(P, 1, r, fr, dfr, pt);
+        if (P.sq) {
+            // the record is chosen from r in float32 (integer-formed copy):
+            // next to a knot the neighbouring interval may be taken, whose
+            // cubic agrees there in value and first two derivatives (C2),
+            // so V and rho change by rounding only; the clamp keeps any r
+            // (also a non-finite one) inside the table
+            const float sf = fmaf(narrow_f32(r), P.sq_invhf, P.sq_c0f);
+            const int kk = min(max(__float2int_rd(sf) + 1, 0), P.sq_n);
+            const double4_32a* q = P.sq + ((int64_t)pt * (P.sq_n + 1) + kk) * 4;
+            const double4_32a q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+            const double u = r - q0.x;
+            phi = fma(u, fma(u, fma(u, q1.x, q0.w), q0.z), q0.y);
+            dphi = fma(u, fma(u, q1.z, q1.y), q0.z);
+            fr = fma(u, fma(u, fma(u, q2.z, q2.y), q2.x), q1.w);
+            dfr = fma(u, fma(u, q3.x, q2.w), q2.x);
+        } else {
+            spline_eval(P, 0, r, phi, dphi, pt);
+            spline_eval(P, 1, r, fr, dfr, pt);
+        }
         A = dphi * rinv;
         B = dfr * rinv;
     }

@@ -50,6 +50,16 @@ struct Pot {
     // float64 loads or conversions per evaluation)
     const float4* spf[3];
     float st0f[3], shf[3], sinvhf[3];
+    // float64 pair path when V and rho share one grid (n_phi == n_f): per
+    // type pair n + 1 records of 16 doubles (128 bytes), record 0 the linear
+    // continuation below r_lo, records 1..n-1 the intervals, record n the
+    // linear continuation above r_hi; each record holds
+    //   (t_k, v0, v1, v2 | v3, 2 v2, 3 v3, f0 | f1, f2, f3, 2 f2 | 3 f3, 0, 0, 0)
+    // so that V, V', rho, rho' at u = r - t_k take 10 float64 instructions
+    // and the interval is found from a float32 copy of r
+    const double4_32a* sq;  // null: V and rho on different grids
+    int sq_n;               // knots per table (records per table: sq_n + 1)
+    float sq_invhf, sq_c0f; // 1/h and -r_lo/h in float32
     // table-driven exponential (float64 path)
     ExpConst ek;
     const double* exp_T;  // [kExpTable] 2^(j/kExpTable)
@@ -151,6 +161,7 @@ struct Engine {
     double4_32a* cell_org = nullptr;
     double4_32a* spline_coef = nullptr;  // 3 splines back to back
     float4* spline_coef_f = nullptr;     // the same, float32
+    double4_32a* spline_pair_rec = nullptr;  // [P][n_phi + 1][4] float64 pair records (n_phi == n_f only)
     double* spline_work = nullptr;   // [3 * total knots] setup scratch
     double* knots_dev = nullptr;
     // reduction chunks: (box, [lo, hi)) pieces of at most 4096 atoms

@@ -620,6 +620,40 @@ __global__ void k_spline_setup(const double* __restrict__ y_all, double* __restr
     for (int k = 0; k < n; ++k) cf[k] = make_float4((float)c[k].x, (float)c[k].y, (float)c[k].z, (float)c[k].w);
 }
 
+// Float64 pair records from the V and rho coefficients of each type pair
+// (both on the grid t_k = r_lo + k h, n knots): record 0 continues interval
+// 0 linearly below r_lo, record k + 1 is interval k, record n continues
+// linearly above r_hi with the end value and slope. Derivative coefficients
+// 2 c2 and 3 c3 are stored beside c0..c3.
+__global__ void k_pair_records(const double4_32a* __restrict__ coef, double4_32a* __restrict__ rec, int n,
+                               double t0, double h, int np_) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np_ * (n + 1)) return;
+    const int pt = t / (n + 1), q = t % (n + 1);
+    const double4_32a* cv = coef + (int64_t)pt * n;             // V of pair pt
+    const double4_32a* cr = coef + (int64_t)np_ * n + (int64_t)pt * n;  // rho of pair pt
+    double tk;
+    double4_32a v, f;
+    if (q == 0) {
+        tk = t0;
+        v = make_double4_32a(cv[0].x, cv[0].y, 0.0, 0.0);
+        f = make_double4_32a(cr[0].x, cr[0].y, 0.0, 0.0);
+    } else if (q == n) {
+        tk = fma(h, (double)(n - 1), t0);
+        v = make_double4_32a(cv[n - 1].x, cv[n - 1].y, 0.0, 0.0);
+        f = make_double4_32a(cr[n - 1].x, cr[n - 1].y, 0.0, 0.0);
+    } else {
+        tk = fma(h, (double)(q - 1), t0);
+        v = cv[q - 1];
+        f = cr[q - 1];
+    }
+    double4_32a* o = rec + (int64_t)t * 4;
+    o[0] = make_double4_32a(tk, v.x, v.y, v.z);
+    o[1] = make_double4_32a(v.w, 2.0 * v.z, 3.0 * v.w, f.x);
+    o[2] = make_double4_32a(f.y, f.z, f.w, 2.0 * f.z);
+    o[3] = make_double4_32a(3.0 * f.w, 0.0, 0.0, 0.0);
+}
+
 void launch_spline_setup(Engine& e, cudaStream_t s) {
     const md_potential& p = e.pot_host;
     e.launches += 1;
@@ -627,6 +661,12 @@ void launch_spline_setup(Engine& e, cudaStream_t s) {
     k_spline_setup<<<(2 * np_ + nt + 31) / 32, 32, 0, s>>>(e.knots_dev, e.spline_work, e.spline_coef,
                                                             e.spline_coef_f, p.n_phi, p.n_f, p.n_F, e.pot.sh[0],
                                                             e.pot.sh[1], e.pot.sh[2], np_, nt);
+    if (e.spline_pair_rec) {
+        e.launches += 1;
+        const int nrec = np_ * (p.n_phi + 1);
+        k_pair_records<<<(nrec + 127) / 128, 128, 0, s>>>(e.spline_coef, e.spline_pair_rec, p.n_phi, e.pot.st0[0],
+                                                          e.pot.sh[0], np_);
+    }
 }
 
 }  // namespace mdk

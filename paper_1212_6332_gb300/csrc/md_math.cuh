@@ -52,11 +52,18 @@ __device__ __forceinline__ double exp_tab(double y, const double* __restrict__ T
 // The float32 argument and the widened estimate are formed from the bit
 // patterns by integer arithmetic (exponent re-biased, mantissa truncated or
 // zero-padded), so no conversion instruction occupies the float64 pipe.
-__device__ __forceinline__ double rsqrt_nr(double x) {
+// float32 copy of a positive double in the float32 normal range, mantissa
+// truncated, formed on the integer pipe
+__device__ __forceinline__ float narrow_f32(double x) {
     const int kRebias = (1023 - 127) << 20;
     const unsigned hi = (unsigned)(__double2hiint(x) - kRebias);
     const unsigned lo = (unsigned)__double2loint(x);
-    const unsigned yb = __float_as_uint(rsqrtf(__uint_as_float((hi << 3) | (lo >> 29))));
+    return __uint_as_float((hi << 3) | (lo >> 29));
+}
+
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    const int kRebias = (1023 - 127) << 20;
+    const unsigned yb = __float_as_uint(rsqrtf(narrow_f32(x)));
     const double y = __hiloint2double((int)(yb >> 3) + kRebias, (int)(yb << 29));
     double e = fma(-(x * y), y, 1.0);
     double c = fma(0.375, e, 0.5);
