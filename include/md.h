@@ -154,7 +154,14 @@ MD_API int md_destroy(md_ctx* ctx);
 /* Sets positions x [n][3] and velocities v [n][3] (host or device; v may be
  * NULL for zero velocities). Positions are wrapped into the box, atoms are
  * binned and sorted, the neighbour list is built and forces are evaluated,
- * so that md_step can start. Resets the step and rebuild counters. */
+ * so that md_step can start. Resets the step and rebuild counters.
+ * Lists built before are kept for positions within half the skin of their
+ * build positions (boxes that moved farther are rebuilt). A position equal
+ * to the one md_get_state reports for the current state keeps the current
+ * one exactly, and when every position does so (a state read back and
+ * loaded again, or new velocities only) the current forces are kept too:
+ * they are the forces of these positions (not after a step with the
+ * pressure coupling of Eq. (5), whose box scaling follows the force pass). */
 MD_API int md_set_state(md_ctx* ctx, const double* x, const double* v, md_stream stream);
 
 /* Copies the current positions and/or velocities (either may be NULL) to

@@ -47,10 +47,12 @@ Geo make_geo(const Engine& e) {
 namespace {
 
 int fail(Engine* e, int code, const std::string& msg) {
-    if (e)
+    if (e) {
         e->err = msg;
-    else
+        e->forces_ok = false;
+    } else {
         g_err = msg;
+    }
     return code;
 }
 
@@ -661,7 +663,9 @@ int set_positions(Engine* E, const double* x, const double* v, bool set_v, cudaS
     // half the skin of the build positions (the rule the steps follow): a
     // load then rebuilds only the boxes that moved farther
     const bool keep = e.have_state && e.lists_ok;
+    const bool had_forces = e.forces_ok;
     e.lists_ok = false;
+    e.forces_ok = false;
     launch_reset_ctl(e, s);
     int rc = stage_in(E, x, 3 * (size_t)e.N, s, &xd);
     if (rc) return rc;
@@ -678,10 +682,19 @@ int set_positions(Engine* E, const double* x, const double* v, bool set_v, cudaS
     // non-finite inputs: report before any list is built from them
     if ((rc = read_ctl(E, s))) return rc;
     if (E->ctl_host->status & kStNonFinite) return fail(E, MD_ERR_NONFINITE, "non-finite position or velocity");
-    if ((rc = keep ? refresh_and_forces(E, s) : rebuild_and_forces(E, s))) return rc;
+    if (keep && had_forces && E->ctl_host->pos_changed == 0) {
+        // every position is the current one: lists and forces stay valid,
+        // only the energies follow the new velocities
+        launch_thermo(e, s);
+        launch_after_load(e, s);
+        CK(cudaGetLastError());
+    } else if ((rc = keep ? refresh_and_forces(E, s) : rebuild_and_forces(E, s))) {
+        return rc;
+    }
     e.have_state = true;
     if ((rc = finish_sync(E, s))) return rc;
     e.lists_ok = true;
+    e.forces_ok = true;
     return MD_OK;
 }
 
@@ -1025,11 +1038,14 @@ int md_batch_compute_forces(md_batch* b, const double* x, double* f, double* e_b
 int md_step(md_ctx* h, int n_steps, md_thermo* out, double* thermo_hist, int use_graph, md_stream st) {
     if (!h) return MD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)st;
+    h->e.forces_ok = false;
     int rc = steps_impl(h, n_steps, thermo_hist, use_graph != 0, s);
     if (rc) {
         h->e.lists_ok = false;  // the next state load rebuilds everything
         return rc;
     }
+    // the last force pass saw the final positions unless a box scaling followed it
+    h->e.forces_ok = n_steps > 0 && !h->e.baro.on;
     if (out) return thermo_impl(h, out, nullptr, s);
     return MD_OK;
 }
@@ -1090,11 +1106,13 @@ int md_batch_step(md_batch* b, int n_steps, int schedule, int use_graph, double*
         }
     }
     bool box = schedule == MD_SCHED_BOX || (schedule == MD_SCHED_AUTO && E->sched_choice == MD_SCHED_BOX);
+    E->forces_ok = false;
     rc = box ? box_steps(b, remaining, s) : steps_impl(b, remaining, nullptr, use_graph != 0, s);
     if (rc) {
         E->lists_ok = false;  // the next state load rebuilds everything
         return rc;
     }
+    E->forces_ok = !box && remaining > 0 && !E->baro.on;
     if (thermo_box) return thermo_impl(b, nullptr, thermo_box, s);
     return MD_OK;
 }
@@ -1137,6 +1155,7 @@ int md_set_thermostat(md_batch* b, double T_e, double tau_T) {
 int md_set_newton3(md_batch* b, int on) {
     if (!b) return MD_ERR_ARG;
     Engine* E = &b->e;
+    E->forces_ok = false;  // a later state load recomputes the forces
     if (on && E->cfg.precision != MD_FP64) return fail(E, MD_ERR_UNSUPPORTED, "Newton's third law variant is float64 only");
     E->newton3 = on != 0;
     destroy_graphs(*E);  // captured launches are those of the other variant
@@ -1155,6 +1174,7 @@ static int ensure_pressure(Engine* E) {
 int md_set_barostat(md_batch* b, double P0, double tau_p, double beta) {
     if (!b) return MD_ERR_ARG;
     Engine* E = &b->e;
+    E->forces_ok = false;  // a later state load recomputes the forces
     if (!std::isfinite(P0) || !std::isfinite(tau_p) || !std::isfinite(beta))
         return fail(E, MD_ERR_ARG, "P0, tau_p and beta must be finite");
     if (tau_p > 0.0 && !(beta > 0.0)) return fail(E, MD_ERR_ARG, "beta must be > 0");
@@ -1177,6 +1197,7 @@ int md_set_barostat(md_batch* b, double P0, double tau_p, double beta) {
 int md_set_types(md_batch* b, const int32_t* types, md_stream st) {
     if (!b) return MD_ERR_ARG;
     Engine* E = &b->e;
+    E->forces_ok = false;  // a later state load recomputes the forces
     Engine& e = *E;
     cudaStream_t s = (cudaStream_t)st;
     if (e.N && !types) return fail(E, MD_ERR_ARG, "types is NULL");
@@ -1243,6 +1264,7 @@ int md_get_box(md_batch* b, double* lengths, md_stream st) {
 int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream st) {
     if (!b) return MD_ERR_ARG;
     Engine* E = &b->e;
+    E->forces_ok = false;  // a later state load recomputes the forces
     cudaStream_t s = (cudaStream_t)st;
     std::string why;
     if (check_potential(pot, why) != MD_OK) return fail(E, MD_ERR_ARG, why);
@@ -1275,6 +1297,7 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
     Engine* E = &b->e;
     cudaStream_t s = (cudaStream_t)st;
     if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
+    E->forces_ok = false;  // the adjoint rewrites rho and F'
     if (E->pot_host.kind == MD_POT_SC) return fail(E, MD_ERR_UNSUPPORTED, "no gradient for Sutton-Chen");
     if (!grad || !is_device_ptr(grad)) return fail(E, MD_ERR_ARG, "grad must be a device pointer");
     if (E->N && (!g_f || !is_device_ptr(g_f))) return fail(E, MD_ERR_ARG, "g_f must be a device pointer");

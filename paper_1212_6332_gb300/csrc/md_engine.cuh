@@ -94,6 +94,7 @@ struct Ctl {
     long long n_rebuild;             // list builds since set_state
     int max_count;                   // largest neighbour count of the current list
     int n_due;                       // cells queued for a partial list build
+    int pos_changed;                 // a state load that kept the lists met a position unlike the current one
 };
 
 // Electron-phonon friction of Eq. (4) over one half step (off unless on):
@@ -221,6 +222,7 @@ struct Engine {
 
     bool have_state = false;
     bool lists_ok = false;  // lists, cells and build positions agree (a state load may keep them)
+    bool forces_ok = false; // f, rho, F', e_atom are those of the current positions (not after a box scaling)
     Bath bath{};            // friction of Eq. (4) applied in the kicks (md_set_thermostat)
     bool newton3 = false;   // float64 half-list sums with Newton's third law (md_set_newton3)
     Baro baro{};            // pressure coupling of Eq. (5) after each step (md_set_barostat)

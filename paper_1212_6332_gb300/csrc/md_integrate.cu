@@ -122,6 +122,7 @@ __global__ void k_reset_ctl(Ctl* ctl, int B, unsigned long long* __restrict__ di
         ctl->disp2_last = 0ull;
         ctl->step = 0;
         ctl->n_rebuild = 0;
+        ctl->pos_changed = 0;
     }
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) disp[b] = 0ull;
 }
@@ -378,6 +379,7 @@ __global__ void __launch_bounds__(kINT) k_load_pos_keep(int64_t N, const double*
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double d2 = 0.0;
     int b = -1;
+    bool changed = false;
     if (c < N) {
         if (!isfinite(src[3 * c]) || !isfinite(src[3 * c + 1]) || !isfinite(src[3 * c + 2]))
             atomicOr(&ctl->status, kStNonFinite);
@@ -385,22 +387,37 @@ __global__ void __launch_bounds__(kINT) k_load_pos_keep(int64_t N, const double*
         const int t = iperm[c];
         const double4_32a q = xb[t];
         const double qa[3] = {q.x, q.y, q.z};
+        // a position equal to what md_get_state reports for the current
+        // state (the current one wrapped into the box) keeps the current,
+        // unwrapped representation: a state read back and loaded again is
+        // the same state, bit for bit
+        const double4_32a cur = x[t];
+        const double ca[3] = {cur.x, cur.y, cur.z};
         double pa[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const double L = g.L[3 * b + a];
-            const double w = wrap_coord(src[3 * c + a], L);
-            const double d = w - qa[a];
-            pa[a] = d > 0.5 * L ? w - L : (d < -0.5 * L ? w + L : w);
+            const double s = src[3 * c + a];
+            if (wrap_step(ca[a], L) == s) {
+                pa[a] = ca[a];
+            } else {
+                changed = true;
+                const double w = wrap_coord(s, L);
+                const double d = w - qa[a];
+                pa[a] = d > 0.5 * L ? w - L : (d < -0.5 * L ? w + L : w);
+            }
             const double e = pa[a] - qa[a];
             d2 = fma(e, e, d2);
         }
-        const int ty = types[c];
-        x[t] = make_double4_32a(pa[0], pa[1], pa[2], (double)ty);
-        const double4_32a org = g.cell_org[cell_t[t]];
-        xo[t] = make_float4((float)(pa[0] - org.x), (float)(pa[1] - org.y), (float)(pa[2] - org.z),
-                            __int_as_float((int)__double_as_longlong(org.w) | (ty << 30)));
+        if (changed) {
+            const int ty = types[c];
+            x[t] = make_double4_32a(pa[0], pa[1], pa[2], (double)ty);
+            const double4_32a org = g.cell_org[cell_t[t]];
+            xo[t] = make_float4((float)(pa[0] - org.x), (float)(pa[1] - org.y), (float)(pa[2] - org.z),
+                                __int_as_float((int)__double_as_longlong(org.w) | (ty << 30)));
+        }
     }
+    if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) atomicOr(&ctl->pos_changed, 1);
     record_disp<SINGLE>(g, N, b, d2, disp);
 }
 

@@ -6,8 +6,9 @@ the test cuts that cluster (minimum image, plus a margin) out of the full
 box, places it in a large isolated box, and lets the oracle compute the
 centre atom's values, which must then equal the GPU's at the usual bars.
 Workloads: the 4,000,000-atom Cu box (RGL and Sutton-Chen, float64), the
-2,048,000-atom Ni box (mixed precision), the 4096-box batch, and the
-gradient over the 256-configuration fitting set.
+4,000,000-atom two-species spline alloy (float64), the 2,048,000-atom Ni
+box (mixed precision), the 4096-box batch, and the gradient over the
+256-configuration fitting set.
 """
 import numpy as np
 import pytest
@@ -18,16 +19,17 @@ from paper_1212_6332_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-def cluster_values(spec, x, box, idx, margin=0.5):
+def cluster_values(spec, x, box, idx, margin=0.5, types=None):
     """Oracle rho, E_i, F_i of atom idx from its 2 r_cut neighbourhood."""
-    rc = spec["r_cut"]
+    rc = spec.get("r_cut", spec.get("r_hi"))
     d = x - x[idx]
     d -= box * np.round(d / box)
     keep = np.where(np.sum(d * d, axis=1) < (2 * rc + margin) ** 2)[0]
     centre = int(np.where(keep == idx)[0][0])
     L = 4 * (2 * rc + margin) + 10.0
     xc = d[keep] + L / 2
-    out = O.forces(O.Potential(spec), xc, np.array([L, L, L]), method="pairs")
+    out = O.forces(O.Potential(spec), xc, np.array([L, L, L]), method="pairs",
+                   types=None if types is None else types[keep])
     return out["rho"][centre], out["e_atom"][centre], out["f"][centre]
 
 
@@ -56,6 +58,35 @@ def test_4m_atom_box_sampled_atoms(spec, name):
     # properties of the whole box: net force, energy per atom near the lattice value
     assert np.abs(got["f"].sum(axis=0)).max() <= 1e-9 * bx.n * 1e-3
     assert -3.6 < got["energy"][0] / bx.n < -3.3
+
+
+def test_4m_atom_alloy_box_sampled_atoms():
+    """The 4,000,000-atom two-species spline alloy (a = 3.57 A, random 50/50
+    labels), float64: the tabulated pair path at full size."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    ni = dict(I.RGL_NI, r_taper=4.5, r_cut=5.0)
+    cuni = dict(kind="rgl", A=0.5 * (0.0855 + 0.0376), xi=np.sqrt(1.224 * 1.070), p=0.5 * (10.960 + 16.999),
+                q=0.5 * (2.278 + 1.189), r0=0.5 * (2.5562 + 2.4911), r_taper=4.5, r_cut=5.0)
+    tabs = [O.tabulate_spline(sp, n_knots=200, rho_hi=45.0) for sp in (I.RGL_CU, cuni, ni)]
+    spec = dict(kind="alloy", n_types=2, phi=[t["phi"] for t in tabs], f=[t["f"] for t in tabs],
+                F=[tabs[0]["F"], tabs[2]["F"]], r_lo=tabs[0]["r_lo"], r_hi=tabs[0]["r_hi"], rho_lo=0.0,
+                rho_hi=45.0)
+    bx = I.perturbed_fcc(100, 3.57, 300.0, I.MASS_CU, seed=5)
+    types = np.random.default_rng(5).integers(0, 2, bx.n).astype(np.int32)
+    s = System(spec, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    s.set_types(types)
+    got = {k: v.cpu().numpy() for k, v in s.compute_forces(torch.tensor(bx.x, device="cuda")).items()}
+    s.close()
+    rng = np.random.default_rng(8)
+    sample = np.concatenate([rng.choice(bx.n, 12, replace=False), [0, bx.n - 1]])
+    fscale = np.abs(got["f"]).max()
+    for i in sample:
+        rho, e, f = cluster_values(spec, bx.x, bx.box, i, types=types)
+        assert got["rho"][i] == pytest.approx(rho, rel=1e-12)
+        assert got["e_atom"][i] == pytest.approx(e, rel=1e-10)
+        assert np.abs(got["f"][i] - f).max() <= 1e-10 * fscale
+    assert np.abs(got["f"].sum(axis=0)).max() <= 1e-9 * bx.n * 1e-3
 
 
 def test_2m_atom_nickel_box_mixed_precision():

@@ -94,3 +94,66 @@ def test_reloading_the_own_state_continues_the_trajectory():
     d -= bx.box * np.round(d / bx.box)
     assert np.abs(d).max() < 1e-11
     assert torch.allclose(v1, v2, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_round_trip_of_the_state_changes_nothing(precision):
+    """A state read back with md_get_state and loaded again is the current
+    state: the forces are kept, and a run interrupted by such a round trip
+    (through host buffers) follows the uninterrupted run bit for bit."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bx = I.perturbed_fcc(6, I.A_CU, 900.0, I.MASS_CU, seed=41)
+    runs = []
+    for split in (False, True):
+        s = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU, precision=precision)
+        s.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+        if split:
+            s.step(60)
+            xh = torch.empty((bx.n, 3), dtype=torch.float64, pin_memory=True)
+            vh = torch.empty((bx.n, 3), dtype=torch.float64, pin_memory=True)
+            s.get_state(xh, vh)
+            f0 = s.get_forces()["f"].clone()
+            s.set_state(xh, vh)
+            assert torch.equal(s.get_forces()["f"], f0)
+            s.step(60)
+        else:
+            s.step(120)
+        runs.append([t.cpu() for t in s.get_state()] + [s.get_forces()["f"].cpu()])
+        s.close()
+    for a, b in zip(*runs):
+        assert torch.equal(a, b)
+
+
+def test_new_velocities_keep_forces_and_new_positions_do_not():
+    """Loading the current positions with new velocities (a host-side
+    velocity change) keeps the forces; loading moved positions recomputes
+    them. Both continue like a fresh handle given the same state."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bx = I.perturbed_fcc(6, I.A_CU, 600.0, I.MASS_CU, seed=43)
+    s = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    s.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+    s.step(30)
+    x, v = s.get_state()
+    v2 = v * 0.5
+    s.set_state(x, v2)
+    th = s.thermo()
+    assert th["ke"] == pytest.approx(0.25 * float((0.5 * I.MASS_CU * I.MVV_EV * (v * v).sum()).item()), rel=1e-12)
+    out = s.step(40, history=True)
+    fresh = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    fresh.set_state(x.clone(), v2.clone())
+    ref = fresh.step(40, history=True)
+    xa, va = (t.cpu().numpy() for t in s.get_state())
+    xb, vb = (t.cpu().numpy() for t in fresh.get_state())
+    d = xa - xb
+    d -= bx.box * np.round(d / bx.box)
+    assert np.abs(d).max() < 1e-11
+    assert np.abs(va - vb).max() < 1e-10 * np.abs(vb).max()
+    assert np.allclose(out["history"].cpu().numpy(), ref["history"].cpu().numpy(), rtol=1e-11, atol=1e-12)
+    # moved positions: forces recomputed, equal to the oracle's
+    x3 = I.wrap(x.cpu().numpy() + 0.01, bx.box)
+    s.set_state(torch.tensor(x3, device="cuda"), v2)
+    got = s.get_forces()["f"].cpu().numpy()
+    ref_f = O.forces(O.Potential(I.RGL_CU), x3, bx.box, skin=0.3)["f"]
+    assert np.linalg.norm(got - ref_f, axis=1).max() <= F_TOL * np.linalg.norm(ref_f, axis=1).max()
