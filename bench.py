@@ -58,7 +58,7 @@ KERNELS = {
     "density": ("k_rho_sum (float64 density sums)", lambda K, Ki: 2.0 * K,
                 # count 4, (rho, V) reads 16K, rho/F'/E_i writes 24
                 lambda K, Ki: 16.0 * K + 28.0),
-    "force": ("k_force (float64 force pass)", lambda K, Ki: 12.0 * Ki,
+    "force": ("k_force (float64 force pass)", lambda K, Ki: 10.0 * Ki,
               # list 4K, (A,B) reads 16K, count 4, x_i 32, F'_i 8, F 24, v 48
               lambda K, Ki: 20.0 * K + 116.0),
 }

@@ -304,20 +304,26 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
             const double4_32a xi = sx[t];
             const double Fpi = sFp[t];
             const int n = min(A.nn[i], A.max_nb);
-            double fx = 0.0, fy = 0.0, fz = 0.0;
+            // the tile schedule's regrouped sum, sum_j s_ij x_j - x_i sum_j s_ij,
+            // in the same order: the same bits
+            double fx = 0.0, fy = 0.0, fz = 0.0, ssum = 0.0;
             for (int k = 0; k < n; ++k) {
                 const int64_t slot = (int64_t)k * A.Np + i;
                 double2 c = A.ab[2 * slot];
                 if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
                 const int e = A.nl[slot];
                 const int jl = entry_slot(e) - (int)a0;
-                double dx, dy, dz;
-                sep_entry(xi, sx[jl], entry_code(e), L, dx, dy, dz);
+                double px, py, pz;
+                image_pos(sx[jl], entry_code(e), L, px, py, pz);
                 double s = fma(Fpi + sFp[jl], c.y, c.x);
-                fx = fma(s, dx, fx);
-                fy = fma(s, dy, fy);
-                fz = fma(s, dz, fz);
+                ssum += s;
+                fx = fma(s, px, fx);
+                fy = fma(s, py, fy);
+                fz = fma(s, pz, fz);
             }
+            fx = fma(-xi.x, ssum, fx);
+            fy = fma(-xi.y, ssum, fy);
+            fz = fma(-xi.z, ssum, fz);
             A.f[i] = fx;
             A.f[A.Np + i] = fy;
             A.f[2 * A.Np + i] = fz;

@@ -93,6 +93,19 @@ __device__ __forceinline__ void sep_entry(const double4_32a& xi, const double4_3
     }
 }
 
+// The partner's position in the image of a list entry: x_j plus the shift.
+__device__ __forceinline__ void image_pos(const double4_32a& xj, unsigned code, const double* L, double& px,
+                                          double& py, double& pz) {
+    px = xj.x;
+    py = xj.y;
+    pz = xj.z;
+    if (code != kNoShift) {
+        px += image_shift(code & 3u, L[0]);
+        py += image_shift((code >> 2) & 3u, L[1]);
+        pz += image_shift((code >> 4) & 3u, L[2]);
+    }
+}
+
 // |d|^2 with a fixed contraction, so every kernel that evaluates a pair
 // gets the same bits
 __device__ __forceinline__ double norm2(double dx, double dy, double dz) {
