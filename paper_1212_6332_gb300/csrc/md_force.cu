@@ -273,15 +273,15 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
     if (load_status(ctl)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < N;
+    // x_i is read again after the loop rather than held through it (39
+    // registers instead of 45: one more resident block per multiprocessor)
     double L[3] = {0.0, 0.0, 0.0};
-    double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     double Fpi = 0.0;
     int n = 0;
     if (active) {
         const int b = SINGLE ? 0 : g.atom_box[i];
 #pragma unroll
         for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
-        xi = x[i];
         Fpi = Fp[i];
         n = min(nn[i], max_nb);
     }
@@ -312,12 +312,16 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
             fx = fma(s, px, fx);
             fy = fma(s, py, fy);
             fz = fma(s, pz, fz);
-            if (VIR) w = fma(s, norm2(px - xi.x, py - xi.y, pz - xi.z), w);
+            if (VIR) {
+                const double4_32a xi = x[i];
+                w = fma(s, norm2(px - xi.x, py - xi.y, pz - xi.z), w);
+            }
             ++k;
             c = cn;
         }
     }
     if (!active) return;
+    const double4_32a xi = x[i];
     fx = fma(-xi.x, ssum, fx);
     fy = fma(-xi.y, ssum, fy);
     fz = fma(-xi.z, ssum, fz);
