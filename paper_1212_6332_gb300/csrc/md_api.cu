@@ -196,6 +196,20 @@ void fill_pot(Engine& e) {
     }
     P.ek = e.exp_const;
     P.exp_T = e.exp_T;
+    if (p.kind == MD_POT_RGL && e.rx_tab) {
+        // r table from 0.3 r_cut (closer pairs take exp_tab) to past r_cut
+        P.rx = e.rx_tab;
+        P.rx_k0 = (int)std::floor(0.3 * P.rc * kRxPerA);
+        P.rx_n = (int)std::ceil(P.rc * kRxPerA) + 2 - P.rx_k0;
+        const double b[2] = {P.p_r0, P.q2_r0};
+        double* c[2] = {P.rx_c1, P.rx_c2};
+        for (int f = 0; f < 2; ++f) {
+            c[f][0] = -b[f];
+            c[f][1] = b[f] * b[f] / 2.0;
+            c[f][2] = -b[f] * b[f] * b[f] / 6.0;
+            c[f][3] = b[f] * b[f] * b[f] * b[f] / 24.0;
+        }
+    }
     P.f_rc2 = (float)P.rc2;
     P.f_rs = (float)P.rs;
     P.f_inv_w = (float)P.inv_w;
@@ -228,7 +242,7 @@ void free_engine(Engine& e) {
     destroy_graphs(e);
     dfree(e.L); dfree(e.cell_len); dfree(e.cell_len_f); dfree(e.nc); dfree(e.cell_off); dfree(e.atom_off);
     dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.cell_org); dfree(e.spline_coef); dfree(e.spline_coef_f);
-    dfree(e.spline_work); dfree(e.spline_pair_rec); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
+    dfree(e.spline_work); dfree(e.spline_pair_rec); dfree(e.rx_tab); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
     dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
@@ -246,6 +260,18 @@ int upload_potential(md_batch* h, cudaStream_t s) {
     Engine* E = &h->e;
     Engine& e = *E;
     fill_pot(e);
+    if (e.pot.rx) {
+        // E_k = 2A exp(p - p_r0 r_k), xi^2 exp(2q - (2q/r0) r_k) at r_k = k h;
+        // the exponent with one rounding (fma), exp from the C library
+        const Pot& P = e.pot;
+        e.rx_host.resize(P.rx_n);
+        for (int k = 0; k < P.rx_n; ++k) {
+            const double rk = (P.rx_k0 + k) / kRxPerA;
+            e.rx_host[k] = make_double2(P.A2 * std::exp(std::fma(-P.p_r0, rk, P.p)),
+                                        P.xi2 * std::exp(std::fma(-P.q2_r0, rk, P.q2)));
+        }
+        CK(cudaMemcpyAsync(e.rx_tab, e.rx_host.data(), P.rx_n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    }
     if (e.pot_host.kind == MD_POT_SPLINE) {
         size_t nk = knot_count(e.pot_host);
         CK(cudaMemcpyAsync(e.knots_dev, e.knots_host.data(), nk * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -435,6 +461,11 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
         AL(e.n_up, Np);
     }
     AL(e.exp_T, kExpTable);
+    if (pot->kind == MD_POT_RGL) {
+        // the r table for this cutoff (a later potential may not raise it)
+        const double rcut = pot->r_cut;
+        AL(e.rx_tab, (size_t)(std::ceil(rcut * kRxPerA) + 2 - std::floor(0.3 * rcut * kRxPerA)));
+    }
     AL(e.stage, 3 * std::max<size_t>(e.N, 1));
     AL(e.red, 2 * std::max(e.n_chunks, 1));
     AL(e.thermo_dev, 4 * (B + 1));

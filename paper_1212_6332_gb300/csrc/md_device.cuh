@@ -361,9 +361,24 @@ __device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict
     // on the integer pipe
     const bool tap = __double_as_longlong(r2) > __double_as_longlong(P.rs2);
     if (KIND == MD_POT_RGL) {
-        // the prefactors 2A and xi^2 ride in the exponent when both are positive
-        double e1 = P.fold ? exp_tab(P.pA - P.p_r0 * r, T, P.ek) : P.A2 * exp_tab(P.p - P.p_r0 * r, T, P.ek);
-        double e2 = P.fold ? exp_tab(P.qX - P.q2_r0 * r, T, P.ek) : P.xi2 * exp_tab(P.q2 - P.q2_r0 * r, T, P.ek);
+        double e1, e2;
+        // r = k h + d with k the nearest integer (the 1.5 * 2^52 shift puts
+        // it in the low word), d exact; both exponentials share it
+        const double shift = 6755399441055744.0;
+        const double t = fma(r, kRxPerA, shift);
+        const int kk = __double2loint(t) - P.rx_k0;
+        if (P.rx && (unsigned)kk < (unsigned)P.rx_n) {
+            const double d = fma(-(t - shift), 1.0 / kRxPerA, r);
+            const double2 E = P.rx[kk];
+            const double R1 = fma(fma(fma(P.rx_c1[3], d, P.rx_c1[2]), d, P.rx_c1[1]), d, P.rx_c1[0]);
+            const double R2 = fma(fma(fma(P.rx_c2[3], d, P.rx_c2[2]), d, P.rx_c2[1]), d, P.rx_c2[0]);
+            e1 = fma(E.x * d, R1, E.x);
+            e2 = fma(E.y * d, R2, E.y);
+        } else {
+            // the prefactors 2A and xi^2 ride in the exponent when both are positive
+            e1 = P.fold ? exp_tab(P.pA - P.p_r0 * r, T, P.ek) : P.A2 * exp_tab(P.p - P.p_r0 * r, T, P.ek);
+            e2 = P.fold ? exp_tab(P.qX - P.q2_r0 * r, T, P.ek) : P.xi2 * exp_tab(P.q2 - P.q2_r0 * r, T, P.ek);
+        }
         if (tap) {
             double S, dS;
             taper(P, r, S, dS);

@@ -63,6 +63,15 @@ struct Pot {
     // table-driven exponential (float64 path)
     ExpConst ek;
     const double* exp_T;  // [kExpTable] 2^(j/kExpTable)
+    // RGL float64 pair path: both exponentials from one table over r,
+    // r = k h + d (h = 1/kRxPerA, k the nearest integer, |d| <= h/2):
+    //   e_1(r) = E1_k (1 + d R_1(d)),  E1_k = 2A exp(p - p_r0 k h),
+    // R_1 the degree-3 Taylor remainder of exp(-p_r0 d) (truncation below
+    // 4e-16 relative); the same for rho with (xi^2, 2q, 2q/r0). Entries
+    // cover k in [rx_k0, rx_k0 + rx_n); other r take exp_tab.
+    const double2* rx;  // [rx_n] (E1_k, E2_k); null: no table
+    int rx_k0, rx_n;
+    double rx_c1[4], rx_c2[4];  // R_1, R_2 coefficients: -b, b^2/2, -b^3/6, b^4/24
     // float copies for the mixed-precision path
     float f_rc2, f_rs, f_inv_w, f_A2, f_xi2, f_p, f_p_r0, f_q2, f_q2_r0, f_eps, f_a, f_n, f_m;
 };
@@ -163,6 +172,8 @@ struct Engine {
     double4_32a* spline_coef = nullptr;  // 3 splines back to back
     float4* spline_coef_f = nullptr;     // the same, float32
     double4_32a* spline_pair_rec = nullptr;  // [P][n_phi + 1][4] float64 pair records (n_phi == n_f only)
+    double2* rx_tab = nullptr;               // RGL: [rx_n] exponential table over r (Pot.rx)
+    std::vector<double2> rx_host;            // its host copy (kept alive for the upload)
     double* spline_work = nullptr;   // [3 * total knots] setup scratch
     double* knots_dev = nullptr;
     // reduction chunks: (box, [lo, hi)) pieces of at most 4096 atoms

@@ -19,6 +19,7 @@ struct ExpConst {
 };
 
 constexpr int kExpBits = 11;
+constexpr double kRxPerA = 1024.0;  // r-table points per Angstrom (RGL pair path)
 constexpr int kExpTable = 1 << kExpBits;  // 16 KB of shared memory per block
 
 // e^y by Tang's table-driven method (P. T. P. Tang, "Table-driven

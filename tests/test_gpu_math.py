@@ -45,3 +45,41 @@ def test_refined_rsqrt_within_two_ulp(sysm):
     assert ulp_err(mine, host).max() <= 2.0
     assert ulp_err(ref, host).max() <= 2.0
     assert mine[-3] == 1.0 and mine[-2] == 0.5 and abs(mine[-1] - 0.2) <= np.spacing(0.2)
+
+
+@pytest.mark.parametrize("spec", [I.RGL_CU, I.RGL_NI])
+def test_rgl_pair_functions_from_the_r_table(spec):
+    """The float64 pair path takes both RGL exponentials from a table over r
+    (points 1/1024 A apart, a degree-4 correction). Two-atom boxes at 6001
+    separations from 0.5 A (below the table: the exp_tab path) to r_cut,
+    through every taper and table cell boundary: rho_i and the pair force
+    against the oracle's libm evaluation within a few ulp (plus 1e-15
+    absolute: next to r_cut the taper itself cancels to ~1e-25)."""
+    import torch
+    import oracle as O
+    from paper_1212_6332_gb300.md import System
+    rc = spec["r_cut"]
+    r = np.concatenate([np.linspace(0.5, rc - 1e-9, 6001), np.arange(1536, int(rc * 1024)) / 1024.0])
+    n = len(r)
+    L = 2.0 * rc + 2.0
+    x = np.zeros((n, 2, 3))
+    x[:, :] = [1.0, 1.0, 1.0]
+    x[:, 1, 0] = 1.0 + r * 0.6
+    x[:, 1, 1] = 1.0 + r * 0.8
+    boxes = np.full((n, 3), L)
+    offs = np.arange(n + 1, dtype=np.int64) * 2
+    s = System(spec, boxes=boxes, atom_offsets=offs, skin=0.0, mass=I.MASS_CU)
+    f, _ = s.batch_compute_forces(torch.tensor(x.reshape(-1, 3), device="cuda"))
+    rho = s.get_forces()["rho"].cpu().numpy().reshape(n, 2)[:, 0]
+    f = f.cpu().numpy().reshape(n, 2, 3)[:, 0]
+    pot = O.Potential(spec)
+    ref_rho = np.empty(n)
+    ref_f = np.empty((n, 3))
+    for k in range(n):
+        o = O.forces(pot, x[k], boxes[k], method="brute")
+        ref_rho[k] = o["rho"][0]
+        ref_f[k] = o["f"][0]
+    inside = r < rc
+    assert np.all(np.abs(rho[inside] - ref_rho[inside]) <= 8 * np.spacing(np.abs(ref_rho[inside])) + 1e-15)
+    fmag = np.linalg.norm(ref_f, axis=1)
+    assert np.all(np.linalg.norm(f - ref_f, axis=1) <= 1e-13 * fmag + 1e-15)
