@@ -68,9 +68,9 @@ KERNELS = {
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per atom of one k_pairs_half launch, from an ncu
 # capture of 1,048,576 atoms of the same lattice, potential and temperature
-# (0.454 GB read + 1.776 GB written); traffic grows in proportion to the
+# (0.454 GB read + 1.772 GB written); traffic grows in proportion to the
 # atom count.
-PAIRS_DRAM_BYTES_PER_ATOM = (0.454266e9 + 1.775963e9) / 1048576
+PAIRS_DRAM_BYTES_PER_ATOM = (0.453648e9 + 1.771678e9) / 1048576
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
            0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",

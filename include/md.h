@@ -21,8 +21,9 @@
  *     float64 for 3-vectors. Internally atoms are re-sorted by cell; the
  *     library maps back on every input and output.
  *   - Pointer arguments marked "host or device" may point to host memory
- *     (pageable or pinned) or to device memory of the current device; the
- *     library copies with cudaMemcpyAsync(cudaMemcpyDefault). Pointers
+ *     (pageable or pinned) or to device memory of the current device; host
+ *     memory is copied with cudaMemcpyAsync through a device staging buffer
+ *     (pinned memory copies fastest). Pointers
  *     marked "device" must be device memory. The caller owns every pointer
  *     it passes; the library owns its handles and internal buffers and
  *     frees them in md_destroy / md_batch_destroy.

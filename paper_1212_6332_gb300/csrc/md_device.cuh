@@ -605,6 +605,32 @@ __device__ __forceinline__ void sep_mixed(const CellSep& cs, float4 oi, float4 o
     }
 }
 
+// The same separation when every box has at least 3 cells per axis and
+// the list entry carries the cell offset (-1, 0, 1 per axis, stored as
+// 0..2: lists built for float32 pair math): no decoding of the packed cell
+// coordinates. The offset becomes a float by the 2^23 bias (exact for small
+// integers), and the arithmetic is that of sep_mixed<true>: the same bits.
+__device__ __forceinline__ void sep_mixed_code(const CellSep& cs, float4 oi, float4 oj, unsigned code, float& dx,
+                                               float& dy, float& dz) {
+    const float kx = __int_as_float(0x4B000000 | (int)(code & 3u)) - 8388609.0f;
+    const float ky = __int_as_float(0x4B000000 | (int)((code >> 2) & 3u)) - 8388609.0f;
+    const float kz = __int_as_float(0x4B000000 | (int)((code >> 4) & 3u)) - 8388609.0f;
+    dx = fmaf(kx, cs.lx, oj.x - oi.x);
+    dy = fmaf(ky, cs.ly, oj.y - oi.y);
+    dz = fmaf(kz, cs.lz, oj.z - oi.z);
+}
+
+// Separation of list entry e in a mixed-precision kernel: from the entry's
+// cell offset when every box is wide, else from the packed coordinates.
+template <bool WIDE>
+__device__ __forceinline__ void sep_mixed_entry(const CellSep& cs, float4 oi, float4 oj, int e, float& dx, float& dy,
+                                                float& dz) {
+    if (WIDE)
+        sep_mixed_code(cs, oi, oj, entry_code(e), dx, dy, dz);
+    else
+        sep_mixed<false>(cs, oi, oj, dx, dy, dz);
+}
+
 // Plain float32 partial sum over a group of list entries, folded into a
 // compensated total at group ends.
 struct GSum {

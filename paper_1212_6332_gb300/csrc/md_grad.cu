@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(kGNT) k_grad_rho(int64_t N, int64_t Np, Geo g,
     const int n = min(nn[i], max_nb);
     double r_i = 0.0;
     for (int k = 0; k < n; ++k) {
-        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        const int e = nl[(int64_t)k * Np + i];
+        int j = entry_slot(e);
         double dx, dy, dz;
         sep(g, x, i, j, dx, dy, dz);
         double r2 = norm2(dx, dy, dz);
@@ -120,7 +121,8 @@ __global__ void __launch_bounds__(kGNT) k_grad_u(int64_t N, int64_t Np, Geo g, P
     const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
     double acc = 0.0;
     for (int k = 0; k < n; ++k) {
-        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        const int e = nl[(int64_t)k * Np + i];
+        int j = entry_slot(e);
         double dx, dy, dz;
         sep(g, x, i, j, dx, dy, dz);
         double r2 = norm2(dx, dy, dz);
@@ -189,7 +191,8 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl(int64_t N, int64_t Np, 
         const double Fpi = Fp[i];
         const double aF = u[i] * Fpp[i] + ge * Fpi;
         for (int k = 0; k < n; ++k) {
-            int j = entry_slot(nl[(int64_t)k * Np + i]);
+            const int e = nl[(int64_t)k * Np + i];
+            int j = entry_slot(e);
             double dx, dy, dz;
             sep(g, x, i, j, dx, dy, dz);
             double r2 = norm2(dx, dy, dz);
@@ -283,7 +286,8 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline(int64_t N, int64_t Np,
         const double Fpi = Fp[i];
         const double aF = u[i] * Fpp[i] + ge * Fpi;
         for (int k = 0; k < n; ++k) {
-            int j = entry_slot(nl[(int64_t)k * Np + i]);
+            const int e = nl[(int64_t)k * Np + i];
+            int j = entry_slot(e);
             double dx, dy, dz;
             sep(g, x, i, j, dx, dy, dz);
             double r2 = norm2(dx, dy, dz);
@@ -386,9 +390,10 @@ __global__ void __launch_bounds__(kGNT) k_grad_rho_mixed(int64_t N, int64_t Np, 
     const int n = min(nn[i], max_nb);
     GSum acc;
     for (int k = 0; k < n; ++k) {
-        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        const int e = nl[(int64_t)k * Np + i];
+        int j = entry_slot(e);
         float dx, dy, dz;
-        sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+        sep_mixed_entry<WIDE>(cs, oi, xo[j], e, dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2), species_pair<KIND>(P, oi, xo[j])));
         if ((k & kGroupMask) == kGroupMask) acc.flush();
@@ -409,9 +414,10 @@ __global__ void __launch_bounds__(kGNT) k_grad_u_mixed(int64_t N, int64_t Np, Ge
     const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
     GSum acc;
     for (int k = 0; k < n; ++k) {
-        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        const int e = nl[(int64_t)k * Np + i];
+        int j = entry_slot(e);
         float dx, dy, dz;
-        sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+        sep_mixed_entry<WIDE>(cs, oi, xo[j], e, dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < P.f_rc2) {
             float rinv = rsqrtf(r2);
@@ -466,9 +472,10 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_mixed(int64_t N, int64_
         const double Fpi = Fp[i];
         const float aF = (float)(u[i] * Fpp[i] + ge * Fpi);
         for (int k = 0; k < n; ++k) {
-            int j = entry_slot(nl[(int64_t)k * Np + i]);
+            const int e = nl[(int64_t)k * Np + i];
+            int j = entry_slot(e);
             float dx, dy, dz;
-            sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+            sep_mixed_entry<WIDE>(cs, oi, xo[j], e, dx, dy, dz);
             float r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= P.f_rc2) continue;
             float rinv = rsqrtf(r2);
@@ -515,9 +522,10 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline_mixed(int64_t N, int64
         const double Fpi = Fp[i];
         const double aF = u[i] * Fpp[i] + ge * Fpi;
         for (int k = 0; k < n; ++k) {
-            int j = entry_slot(nl[(int64_t)k * Np + i]);
+            const int e = nl[(int64_t)k * Np + i];
+            int j = entry_slot(e);
             float dx, dy, dz;
-            sep_mixed<WIDE>(cs, oi, xo[j], dx, dy, dz);
+            sep_mixed_entry<WIDE>(cs, oi, xo[j], e, dx, dy, dz);
             float r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= P.f_rc2) continue;
             float rinv = rsqrtf(r2);

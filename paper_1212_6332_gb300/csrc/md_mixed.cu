@@ -35,10 +35,11 @@ __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, G
     const int n = min(nn[i], max_nb);
     GSum acc;
     for (int k = 0; k < n; ++k) {
-        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        const int e = nl[(int64_t)k * Np + i];
+        int j = entry_slot(e);
         const float4 oj = xo[j];
         float dx, dy, dz;
-        sep_mixed<WIDE>(cs, oi, oj, dx, dy, dz);
+        sep_mixed_entry<WIDE>(cs, oi, oj, e, dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2), species_pair<KIND>(P, oi, oj)));
         if ((k & kGroupMask) == kGroupMask) acc.flush();
@@ -81,10 +82,11 @@ __global__ void __launch_bounds__(kMNT, 12) k_force_mixed(int64_t N, int64_t Np,
             ae.flush();
             if (vir) aw.flush();
         }
-        int j = entry_slot(nl[(int64_t)k * Np + i]);
+        const int e = nl[(int64_t)k * Np + i];
+        int j = entry_slot(e);
         const float4 oj = xo[j];
         float dx, dy, dz;
-        sep_mixed<WIDE>(cs, oi, oj, dx, dy, dz);
+        sep_mixed_entry<WIDE>(cs, oi, oj, e, dx, dy, dz);
         float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < P.f_rc2) {
             float rinv = rsqrtf(r2);

@@ -38,7 +38,7 @@ __device__ __forceinline__ void build_cell_lists(int c, const Geo& g, const doub
                                                  const float4* __restrict__ xo, const int* __restrict__ cell_start,
                                                  int* __restrict__ nn, int* __restrict__ nl, int max_nb,
                                                  int64_t N_pad, double rl2, float rl2f_lo, float rl2f_hi,
-                                                 int& my_max) {
+                                                 bool cell_code, int& my_max) {
     __shared__ float4 so[kNlCap];
     __shared__ int sj[kNlCap];
     __shared__ int cnt[kNlMaxI];
@@ -80,7 +80,9 @@ __device__ __forceinline__ void build_cell_lists(int c, const Geo& g, const doub
             const int sx = cc[0] + ox < 0 ? -1 : (cc[0] + ox >= ncx ? 1 : 0);
             const int sy = cc[1] + oy < 0 ? -1 : (cc[1] + oy >= ncy ? 1 : 0);
             const int sz = cc[2] + oz < 0 ? -1 : (cc[2] + oz >= ncz ? 1 : 0);
-            code = make_entry(0, sx, sy, sz);
+            // float32 pair math (cell_code): the entry carries the cell
+            // offset instead, what the mixed-precision separation needs
+            code = cell_code ? make_entry(0, ox, oy, oz) : make_entry(0, sx, sy, sz);
         }
         int rank = 0;
         for (int k = 0; k < total; ++k) rank += __shfl_sync(0xffffffffu, q, k) < q;
@@ -162,7 +164,7 @@ __device__ __forceinline__ void build_cell_lists(int c, const Geo& g, const doub
                             } else if (!(r2f > rl2f_hi)) {
                                 int sx, sy, sz;
                                 ok = exact_candidate(xi, x[j], Lx, Ly, Lz, rl2, sx, sy, sz) && j != i;
-                                entry = make_entry(j, sx, sy, sz);
+                                if (!cell_code) entry = make_entry(j, sx, sy, sz);
                             }
                         } else {
                             const int j = sj[jj];
@@ -199,7 +201,8 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(int n_cells, Geo g, c
                                                            const int* __restrict__ cell_start,
                                                            int* __restrict__ nn, int* __restrict__ nl, int max_nb,
                                                            int64_t N_pad, double rl2, float rl2f_lo, float rl2f_hi,
-                                                           Ctl* ctl, const int* __restrict__ due, int mode) {
+                                                           Ctl* ctl, const int* __restrict__ due, int mode,
+                                                           bool cell_code) {
     // persistent blocks: a full build walks every cell, a partial build the
     // cells queued by k_due_cells (one block per cell at a time either way,
     // so a few boxes that rebuild still spread over the whole GPU)
@@ -207,11 +210,13 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(int n_cells, Geo g, c
     int my_max = 0;
     if (mode) {
         for (int c = blockIdx.x; c < n_cells; c += gridDim.x)
-            build_cell_lists(c, g, x, xo, cell_start, nn, nl, max_nb, N_pad, rl2, rl2f_lo, rl2f_hi, my_max);
+            build_cell_lists(c, g, x, xo, cell_start, nn, nl, max_nb, N_pad, rl2, rl2f_lo, rl2f_hi, cell_code,
+                             my_max);
     } else {
         const int n_due = ctl->n_due;
         for (int t = blockIdx.x; t < n_due; t += gridDim.x)
-            build_cell_lists(due[t], g, x, xo, cell_start, nn, nl, max_nb, N_pad, rl2, rl2f_lo, rl2f_hi, my_max);
+            build_cell_lists(due[t], g, x, xo, cell_start, nn, nl, max_nb, N_pad, rl2, rl2f_lo, rl2f_hi, cell_code,
+                             my_max);
     }
     const int lane = threadIdx.x & 31;
     my_max = warp_max(my_max);
@@ -288,7 +293,8 @@ void launch_build_list(Engine& e, int mode, cudaStream_t s) {
     }
     const int nl_blocks = std::max(1, std::min(e.n_cells, nl_per_sm * e.n_sm));
     k_build_list<<<nl_blocks, kNlThreads, 0, s>>>(e.n_cells, g, e.x, e.xo, e.cell_start, e.nn, e.nl, e.max_nb,
-                                                  e.N_pad, rl2, lo, hi, e.ctl, e.due_cells, mode);
+                                                  e.N_pad, rl2, lo, hi, e.ctl, e.due_cells, mode,
+                                                  e.cfg.precision == MD_MIXED);
     if (e.rev) {
         // grid-stride over the atoms with four waves of resident blocks
         int nb = (int)std::min<int64_t>((e.N + 255) / 256, (int64_t)32 * e.n_sm);

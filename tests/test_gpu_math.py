@@ -52,9 +52,13 @@ def test_rgl_pair_functions_from_the_r_table(spec):
     """The float64 pair path takes both RGL exponentials from a table over r
     (points 1/1024 A apart, a degree-4 correction). Two-atom boxes at 6001
     separations from 0.5 A (below the table: the exp_tab path) to r_cut,
-    through every taper and table cell boundary: rho_i and the pair force
-    against the oracle's libm evaluation within a few ulp (plus 1e-15
-    absolute: next to r_cut the taper itself cancels to ~1e-25)."""
+    through every taper and table cell boundary: rho_i within 1e-14 and the
+    pair force within 1e-13 (inside r_taper) of the oracle's libm evaluation
+    (plus 1e-15 absolute: next to r_cut the taper itself cancels to ~1e-25). The two
+    sides form r differently (refined rsqrt against sqrt, an ulp or two),
+    and exp(-b r) amplifies that by b r (up to ~20), so a few tens of ulp
+    separate them; a table off by one point would be 1e-3 off, a wrong
+    correction coefficient 1e-6."""
     import torch
     import oracle as O
     from paper_1212_6332_gb300.md import System
@@ -80,6 +84,25 @@ def test_rgl_pair_functions_from_the_r_table(spec):
         ref_rho[k] = o["rho"][0]
         ref_f[k] = o["f"][0]
     inside = r < rc
-    assert np.all(np.abs(rho[inside] - ref_rho[inside]) <= 8 * np.spacing(np.abs(ref_rho[inside])) + 1e-15)
+    rerr = np.abs(rho[inside] - ref_rho[inside]) / (np.abs(ref_rho[inside]) + 1e-1)
+    assert rerr.max() <= 1e-14, (rerr.max(), r[inside][np.argmax(rerr)])
     fmag = np.linalg.norm(ref_f, axis=1)
-    assert np.all(np.linalg.norm(f - ref_f, axis=1) <= 1e-13 * fmag + 1e-15)
+    ferr = np.linalg.norm(f - ref_f, axis=1)
+    # the pair force is the difference of a repulsive and an attractive term
+    # (it vanishes at the dimer's equilibrium): measure it against their
+    # sum, |V'| + 2 |F'(rho) rho'| = 2A (p/r0) e^(p(1 - r/r0)) + (2q/r0) sqrt(rho)
+    # inside r_taper; inside the taper rho carries the taper's cancellation
+    # (rho -> 1e-9 at r_cut) and F'(rho) = -1/(2 sqrt(rho)) amplifies it on
+    # both sides alike
+    scale = 2 * spec["A"] * spec["p"] / spec["r0"] * np.exp(spec["p"] * (1 - r / spec["r0"])) + \
+        2 * spec["q"] / spec["r0"] * np.sqrt(ref_rho)
+    flat = r < spec["r_taper"]
+    worst = np.max(ferr[flat] / scale[flat])
+    assert worst <= 1e-13, (worst, r[flat][np.argmax(ferr[flat] / scale[flat])])
+    # (next to r_cut S ~ 1e-7 and its float64 polynomial carries ~1e-9 of
+    # relative rounding on either side, 4e-9 of the force at r_cut - 1e-3 A
+    # for Ni, and the force crosses zero inside the taper too: the bound is
+    # taken against the region's largest force; a table error would be 1e-6
+    # of it or more)
+    tap = inside & ~flat
+    assert ferr[tap].max() <= 1e-8 * fmag[tap].max(), (ferr[tap].max(), r[tap][np.argmax(ferr[tap])])
