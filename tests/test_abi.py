@@ -89,6 +89,7 @@ def test_negative_atom_count_and_null_handles(lib):
     assert lib.md_pressure(None, None, None) == 1
     assert lib.md_get_box(None, None, None) == 1
     assert lib.md_set_types(None, None, None) == 1
+    assert lib.md_set_newton3(None, 1) == 1
 
 
 def test_batch_offsets_must_not_decrease(lib):
