@@ -1323,7 +1323,11 @@ int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream st) {
         launch_thermo(*E, s);
         CK(cudaGetLastError());
     }
-    return finish_sync(E, s);
+    int rc2 = finish_sync(E, s);
+    // the forces (and the pair cache) are those of the stored positions and
+    // the new potential
+    if (rc2 == MD_OK && E->have_state) E->forces_ok = true;
+    return rc2;
 }
 
 int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* grad, md_stream st) {
@@ -1331,7 +1335,9 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
     Engine* E = &b->e;
     cudaStream_t s = (cudaStream_t)st;
     if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
-    E->forces_ok = false;  // the adjoint rewrites rho and F'
+    // the float64 adjoint reads the forward pass's values when they are
+    // current and leaves them so; otherwise it rewrites rho and F'
+    const bool keep = E->forces_ok && !E->newton3 && E->cfg.precision == MD_FP64;
     if (E->pot_host.kind == MD_POT_SC) return fail(E, MD_ERR_UNSUPPORTED, "no gradient for Sutton-Chen");
     if (!grad || !is_device_ptr(grad)) return fail(E, MD_ERR_ARG, "grad must be a device pointer");
     if (E->N && (!g_f || !is_device_ptr(g_f))) return fail(E, MD_ERR_ARG, "g_f must be a device pointer");
@@ -1349,6 +1355,7 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
             return MD_ERR_NOMEM;
     }
     int rc = launch_param_grad(*E, g_f, g_e, grad, s);
+    E->forces_ok = keep;
     if (rc) return fail(E, rc, "parameter gradient failed");
     CK(cudaGetLastError());
     return finish_sync(E, s);

@@ -12,9 +12,11 @@
 //   u_i = sum_j (g_i - g_j) . d_ij rho'(r_ij) / r_ij
 // is a per-atom adjoint scalar (a gather of g_j over the list). The two
 // passes of the forward pass become three:
-//   k_grad_rho    recompute rho_i, F'_i and F''_i (nothing per pair is stored)
-//   k_grad_u      u_i
-//   k_grad_param  per-pair terms into per-block parameter partials
+//   k_grad_rho    recompute rho_i, F'_i and F''_i (or, when the float64
+//                 forward values are current, k_grad_embed: F''_i from rho_i)
+//   k_grad_u      u_i (k_grad_u_cached: rho'/r from the pair cache)
+//   k_grad_param  per-pair terms into per-block parameter partials (RGL
+//                 from the cached V, V', rho, rho' when current)
 //                 (RGL: block reduction of 5 sums; spline: shared-memory
 //                 histogram over the cubic coefficients of each interval)
 // then a fixed-order reduction and, for splines, the transpose of the
@@ -132,6 +134,135 @@ __global__ void __launch_bounds__(kGNT) k_grad_u(int64_t N, int64_t Np, Geo g, P
         acc += ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * B;
     }
     u[i] = acc;
+}
+
+// ---------------------------------------------------------------- from the forward pass
+//
+// When the float64 pair cache, rho and F' are those of the current positions
+// and potential (the forward pass that produced the forces being fitted),
+// the adjoint reads them instead of evaluating the pair functions again:
+// F'' from the stored rho, u_i with rho'/r from the cache (the same bits as
+// recomputing them), and the RGL parameter terms from the cached V, V',
+// rho and rho' alone (every derivative of Eq. (1)-(3) with respect to
+// (A, xi, p, q, r0) is a multiple of these four at fixed r).
+
+// the cached (V'/r, rho'/r) and (rho, V) halves of a list entry
+__device__ __forceinline__ double2 grad_ab(const double4_32a* __restrict__ pc, int64_t slot) {
+    return reinterpret_cast<const double2*>(pc)[2 * slot];
+}
+__device__ __forceinline__ double2 grad_fv(const double4_32a* __restrict__ pc, int64_t slot) {
+    return reinterpret_cast<const double2*>(pc)[2 * slot + 1];
+}
+
+// F''(rho_i) from the stored rho_i
+template <int KIND>
+__global__ void __launch_bounds__(kGNT) k_grad_embed(int64_t N, Pot P, const double4_32a* __restrict__ x,
+                                                     const double* __restrict__ rho, double* __restrict__ Fpp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double r_i = rho[i];
+    double Fppi = 0.0;
+    if (KIND == MD_POT_SPLINE) {
+        const int a = atom_tab<KIND>(P, x, i);
+        double s = (r_i - P.st0[2]) * P.sinvh[2];
+        int k = (int)s;
+        if (s >= 0.0 && k < P.sn[2] - 1) {
+            double u = r_i - (P.st0[2] + P.sh[2] * k);
+            double4_32a c = P.sp[2][(int64_t)a * P.sn[2] + k];
+            Fppi = 2.0 * c.z + 6.0 * c.w * u;
+        }
+    } else if (r_i > 0.0) {
+        Fppi = 0.25 * P.F_scale / (r_i * sqrt(r_i));
+    }
+    Fpp[i] = Fppi;
+}
+
+// u_i = sum_j (g_i - g_j) . d_ij rho'(r)/r with rho'/r from the cache and
+// d_ij from the entry's image (zero cache entries lie beyond r_cut)
+__global__ void __launch_bounds__(kGNT) k_grad_u_cached(int64_t N, int64_t Np, Geo g,
+                                                        const double4_32a* __restrict__ x,
+                                                        const int* __restrict__ nn, const int* __restrict__ nl,
+                                                        int max_nb, const double4_32a* __restrict__ pc,
+                                                        const double* __restrict__ gs, double* __restrict__ u) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = g.B == 1 ? 0 : g.atom_box[i];
+    const double L[3] = {g.L[3 * b], g.L[3 * b + 1], g.L[3 * b + 2]};
+    const double4_32a xi = x[i];
+    const int n = min(nn[i], max_nb);
+    const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const int64_t slot = (int64_t)k * Np + i;
+        const double2 c = grad_ab(pc, slot);
+        if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
+        const int e = nl[slot];
+        const int j = entry_slot(e);
+        double dx, dy, dz;
+        sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
+        acc += ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * c.y;
+    }
+    u[i] = acc;
+}
+
+// RGL parameter terms from the cached values: with u = r/r0 - 1,
+//   dV/dA = V/A, dV'/dA = V'/A;  drho/dxi = 2 rho/xi, drho'/dxi = 2 rho'/xi;
+//   dV/dp = -u V, dV'/dp = -u V' - V/r0;  drho/dq = -2u rho, drho'/dq = -2u rho' - 2 rho/r0;
+//   dV/dr0 = p (r/r0^2) V, dV'/dr0 = p (r/r0^2) V' + p V/r0^2 (likewise rho with 2q);
+// the taper S(r) does not depend on the parameters and rides in V, rho.
+__global__ void __launch_bounds__(kGNT) k_grad_param_rgl_cached(int64_t N, int64_t Np, Geo g, Pot P,
+                                                                const double4_32a* __restrict__ x,
+                                                                const int* __restrict__ nn,
+                                                                const int* __restrict__ nl, int max_nb,
+                                                                const double4_32a* __restrict__ pc,
+                                                                const double* __restrict__ gs,
+                                                                const double* __restrict__ gE,
+                                                                const double* __restrict__ Fp,
+                                                                const double* __restrict__ Fpp,
+                                                                const double* __restrict__ u,
+                                                                double inv_A, double two_inv_xi,
+                                                                double* __restrict__ partial) {
+    __shared__ double sh[kGNT / 32];
+    const double inv_r0 = 1.0 / P.r0, inv_r02 = inv_r0 * inv_r0, pp = P.p, q2 = P.q2;
+    double acc[kRglParams] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = g.B == 1 ? 0 : g.atom_box[i];
+        const double L[3] = {g.L[3 * b], g.L[3 * b + 1], g.L[3 * b + 2]};
+        const double4_32a xi = x[i];
+        const int n = min(nn[i], max_nb);
+        const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
+        const double ge = box_gE(g, gE, i);
+        const double Fpi = Fp[i];
+        const double aF = u[i] * Fpp[i] + ge * Fpi;
+        const double aV = 0.5 * ge;
+        for (int k = 0; k < n; ++k) {
+            const int64_t slot = (int64_t)k * Np + i;
+            const double2 c = grad_ab(pc, slot);
+            if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
+            const double2 fv = grad_fv(pc, slot);
+            const int e = nl[slot];
+            const int j = entry_slot(e);
+            double dx, dy, dz;
+            sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
+            const double r2 = norm2(dx, dy, dz);
+            const double rinv = rsqrt_nr(r2);
+            const double r = r2 * rinv;
+            const double aVp = (gx * dx + gy * dy + gz * dz) * rinv;  // w
+            const double aFp = aVp * (Fpi + Fp[j]);
+            const double V = fv.y, rh = fv.x, Vp = c.x * r, rhp = c.y * r;
+            const double uu = fma(r, inv_r0, -1.0), c0 = r * inv_r02;
+            const double tV = aVp * Vp + aV * V, tR = aFp * rhp + aF * rh;
+            acc[0] += tV * inv_A;
+            acc[1] += tR * two_inv_xi;
+            acc[2] += -uu * tV - aVp * V * inv_r0;
+            acc[3] += -2.0 * uu * tR - 2.0 * aFp * rh * inv_r0;
+            acc[4] += pp * (c0 * tV + aVp * V * inv_r02) + q2 * (c0 * tR + aFp * rh * inv_r02);
+        }
+    }
+    for (int k = 0; k < kRglParams; ++k) {
+        double t = block_sum<kGNT>(acc[k], sh);
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * kRglParams + k] = t;
+    }
 }
 
 // ---------------------------------------------------------------- RGL
@@ -598,13 +729,28 @@ static int grad_impl(Engine& e, const double* g_f, const double* g_e, double* gr
     Geo g = make_geo(e);
     int nb = (int)((e.N + kGNT - 1) / kGNT);
     int npb = e.grad_blocks;
+    // the forward pass's cache, rho and F' are those of these positions and
+    // this potential: read them (the Newton's-third-law variant leaves the
+    // lower cache slots unwritten)
+    const bool cached = e.forces_ok && !e.newton3 && e.pc;
     k_gather_g<<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g_f, e.perm, e.grad_g);
-    k_grad_rho<KIND><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.rho, e.Fp, e.grad_Fpp);
-    k_grad_u<KIND><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.grad_g, e.grad_u);
+    if (cached) {
+        k_grad_embed<KIND><<<nb, kGNT, 0, s>>>(e.N, e.pot, e.x, e.rho, e.grad_Fpp);
+        k_grad_u_cached<<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.pc, e.grad_g, e.grad_u);
+    } else {
+        k_grad_rho<KIND><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.rho, e.Fp,
+                                             e.grad_Fpp);
+        k_grad_u<KIND><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.grad_g, e.grad_u);
+    }
     e.launches += 3;
     if (KIND == MD_POT_RGL) {
-        k_grad_param_rgl<<<npb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.grad_g, g_e,
-                                             e.Fp, e.grad_Fpp, e.grad_u, e.grad_partial);
+        if (cached && e.pot.A2 != 0.0 && e.pot.xi != 0.0)
+            k_grad_param_rgl_cached<<<npb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.pc,
+                                                         e.grad_g, g_e, e.Fp, e.grad_Fpp, e.grad_u,
+                                                         2.0 / e.pot.A2, 2.0 / e.pot.xi, e.grad_partial);
+        else
+            k_grad_param_rgl<<<npb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb, e.grad_g, g_e,
+                                                 e.Fp, e.grad_Fpp, e.grad_u, e.grad_partial);
         k_sum_partials<<<kRglParams, 256, 0, s>>>(npb, kRglParams, e.grad_partial, grad);
         e.launches += 2;
     } else {
