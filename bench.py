@@ -459,6 +459,8 @@ def main():
                     help="only the tile-schedule batch leg with this many boxes (profiling runs; prints its dict)")
     ap.add_argument("--alloy-only", action="store_true",
                     help="only the two-species spline alloy box of --cells (profiling runs; prints its dict)")
+    ap.add_argument("--grad-only", default="", choices=["", "rgl", "spline", "alloy"],
+                    help="only the fitting-gradient leg of this model, K iterations (profiling runs; prints its dict)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -477,6 +479,9 @@ def main():
     build.build()
     if args.batch_boxes:
         print(json.dumps(run_batch(args.precision, K, W, n_boxes=args.batch_boxes)))
+        return
+    if args.grad_only:
+        print(json.dumps(run_grad(K, W, args.precision, args.grad_only)))
         return
     if args.alloy_only:
         al = I.perturbed_fcc(args.cells, 3.57, TEMP, I.MASS_CU, 5)

@@ -1335,9 +1335,9 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
     Engine* E = &b->e;
     cudaStream_t s = (cudaStream_t)st;
     if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
-    // the float64 adjoint reads the forward pass's values when they are
-    // current and leaves them so; otherwise it rewrites rho and F'
-    const bool keep = E->forces_ok && !E->newton3 && E->cfg.precision == MD_FP64;
+    // the adjoint reads the forward pass's values when they are current and
+    // leaves them so; otherwise it rewrites rho and F'
+    const bool keep = E->forces_ok && !E->newton3;
     if (E->pot_host.kind == MD_POT_SC) return fail(E, MD_ERR_UNSUPPORTED, "no gradient for Sutton-Chen");
     if (!grad || !is_device_ptr(grad)) return fail(E, MD_ERR_ARG, "grad must be a device pointer");
     if (E->N && (!g_f || !is_device_ptr(g_f))) return fail(E, MD_ERR_ARG, "g_f must be a device pointer");

@@ -697,8 +697,13 @@ static int grad_mixed_impl(Engine& e, const double* g_f, const double* g_e, doub
     Geo g = make_geo(e);
     int nb = (int)((e.N + kGNT - 1) / kGNT);
     k_gather_g<<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g_f, e.perm, e.grad_g);
-    k_grad_rho_mixed<KIND, WIDE><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.rho,
-                                                     e.Fp, e.grad_Fpp);
+    // rho and F' of the forward pass are current (it sums the same float32
+    // terms in the same groups): F'' from rho alone
+    if (e.forces_ok)
+        k_grad_embed<KIND><<<nb, kGNT, 0, s>>>(e.N, e.pot, e.x, e.rho, e.grad_Fpp);
+    else
+        k_grad_rho_mixed<KIND, WIDE><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb,
+                                                         e.rho, e.Fp, e.grad_Fpp);
     k_grad_u_mixed<KIND, WIDE><<<nb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.grad_g,
                                                    e.grad_u);
     e.launches += 3;
