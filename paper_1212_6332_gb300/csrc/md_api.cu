@@ -246,7 +246,7 @@ void free_engine(Engine& e) {
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
     dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
-    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.pc); dfree(e.rev); dfree(e.n_up); dfree(e.exp_T);
+    dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.pc); dfree(e.rev); dfree(e.nl_lo); dfree(e.n_up); dfree(e.exp_T);
     dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
     dfree(e.grad_g); dfree(e.grad_u); dfree(e.grad_Fpp); dfree(e.grad_partial); dfree(e.grad_coef); dfree(e.stage); dfree(e.red);
     dfree(e.thermo_dev); dfree(e.hist); dfree(e.ctl); dfree(e.disp_box); dfree(e.types); dfree(e.due_cells); dfree(e.w_atom); dfree(e.red_w); dfree(e.press_box); dfree(e.mu_box);
@@ -458,6 +458,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     if (cfg->precision == MD_FP64) {
         AL(e.pc, (size_t)e.max_nb * Np);
         AL(e.rev, (size_t)e.max_nb * Np);
+        AL(e.nl_lo, (size_t)e.max_nb * Np);
         AL(e.n_up, Np);
     }
     AL(e.exp_T, kExpTable);
@@ -607,16 +608,20 @@ int grow_list(Engine* E, int needed) {
     if (dalloc(E, &nl, (size_t)m * e.N_pad) != MD_OK) return MD_ERR_NOMEM;
     if (e.pc) {
         double4_32a* pc = nullptr;
-        int* rev = nullptr;
-        if (dalloc(E, &pc, (size_t)m * e.N_pad) != MD_OK || dalloc(E, &rev, (size_t)m * e.N_pad) != MD_OK) {
+        int *rev = nullptr, *nl_lo = nullptr;
+        if (dalloc(E, &pc, (size_t)m * e.N_pad) != MD_OK || dalloc(E, &rev, (size_t)m * e.N_pad) != MD_OK ||
+            dalloc(E, &nl_lo, (size_t)m * e.N_pad) != MD_OK) {
             cudaFree(nl);
             if (pc) cudaFree(pc);
+            if (rev) cudaFree(rev);
             return MD_ERR_NOMEM;
         }
         cudaFree(e.pc);
         cudaFree(e.rev);
+        cudaFree(e.nl_lo);
         e.pc = pc;
         e.rev = rev;
+        e.nl_lo = nl_lo;
     }
     cudaFree(e.nl);
     e.nl = nl;

@@ -45,6 +45,7 @@ struct BoxArgs {
     double2* ab;  // (V'/r, rho'/r) halves of the float64 pair cache entries: ab[2 slot]
     int* n_up;  // float64 tile path's list layout data, kept valid across schedules
     int* rev;
+    int* nl_lo;  // row-major lower parts for the reverse-index search
     Ctl* ctl;
     int* box_done;
     int* box_state;
@@ -180,11 +181,11 @@ __device__ int box_rebuild(const Geo& g, const BoxArgs& A, int b, int64_t a0, in
     // so either schedule can continue from the other
     if (*s_max <= A.max_nb) {
         for (int t = tid; t < nb; t += NT)
-            A.n_up[a0 + t] = rotate_list(A.Np, a0 + t, min(A.nn[a0 + t], A.max_nb), A.nl);
+            A.n_up[a0 + t] = rotate_list(A.Np, a0 + t, min(A.nn[a0 + t], A.max_nb), A.nl, A.nl_lo, A.max_nb);
         __syncthreads();
         for (int t = tid; t < nb; t += NT)
-            reverse_index(A.Np, a0 + t, min(A.nn[a0 + t], A.max_nb), A.n_up[a0 + t], A.nn, A.nl, A.n_up, A.max_nb,
-                          A.rev);
+            reverse_index(A.Np, a0 + t, min(A.nn[a0 + t], A.max_nb), A.n_up[a0 + t], A.nn, A.nl, A.nl_lo, A.n_up,
+                          A.max_nb, A.rev);
         __syncthreads();
     }
     return *s_max;
@@ -435,6 +436,7 @@ static void box_launch(Engine& e, int n_steps, cudaStream_t s) {
     A.ab = reinterpret_cast<double2*>(e.pc);
     A.n_up = e.n_up;
     A.rev = e.rev;
+    A.nl_lo = e.nl_lo;
     A.ctl = e.ctl;
     A.box_done = e.box_done;
     A.box_state = e.box_state;

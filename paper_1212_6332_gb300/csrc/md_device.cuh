@@ -259,13 +259,24 @@ __device__ __forceinline__ bool list_candidate(const float4& oi, const float4& o
 // walks only the upper entries, and the partner of an upper entry is found
 // by binary search in the partner's lower part. n_up[i] counts the upper
 // entries; lists longer than kRotMax keep the ascending order and
-// n_up = -1 (the pair pass then scans them whole).
+// n_up = -1 (the pair pass then scans them whole). The lower part (or the
+// whole list when it is not rotated) is also copied row-major into
+// nl_lo[i * max_nb + m], so that the search reads a few contiguous sectors
+// of the partner's list instead of one column-major row per probe.
 constexpr int kRotMax = 320;
 
-__device__ __forceinline__ int rotate_list(int64_t Np, int64_t i, int n, int* __restrict__ nl) {
-    if (n > kRotMax) return -1;
+__device__ __forceinline__ int rotate_list(int64_t Np, int64_t i, int n, int* __restrict__ nl,
+                                           int* __restrict__ nl_lo, int max_nb) {
+    int* lo_out = nl_lo + i * (int64_t)max_nb;
+    if (n > kRotMax) {
+        for (int k = 0; k < n; ++k) lo_out[k] = nl[(int64_t)k * Np + i];
+        return -1;
+    }
     int lo = 0;
-    while (lo < n && entry_slot(nl[(int64_t)lo * Np + i]) < i) ++lo;
+    while (lo < n && entry_slot(nl[(int64_t)lo * Np + i]) < i) {
+        lo_out[lo] = nl[(int64_t)lo * Np + i];
+        ++lo;
+    }
     if (lo == 0 || lo == n) return n - lo;
     int buf[kRotMax];
     for (int k = 0; k < n; ++k) buf[k] = nl[(int64_t)k * Np + i];
@@ -274,23 +285,25 @@ __device__ __forceinline__ int rotate_list(int64_t Np, int64_t i, int n, int* __
 }
 
 __device__ __forceinline__ void reverse_index(int64_t Np, int64_t i, int n, int nup, const int* __restrict__ nn,
-                                              const int* __restrict__ nl, const int* __restrict__ n_up, int max_nb,
-                                              int* __restrict__ rev) {
+                                              const int* __restrict__ nl, const int* __restrict__ nl_lo,
+                                              const int* __restrict__ n_up, int max_nb, int* __restrict__ rev) {
     const int kmax = nup < 0 ? n : nup;
     for (int k = 0; k < kmax; ++k) {
         const int j = entry_slot(nl[(int64_t)k * Np + i]);
         if (j <= i) continue;
         const int nj = min(nn[j], max_nb);
         const int uj = n_up[j];
-        int lo = uj < 0 ? 0 : uj, hi = uj < 0 ? nj : nj;  // j's lower part (or its whole ascending list)
+        // j's lower part (or its whole ascending list), row-major
+        const int* lst = nl_lo + (int64_t)j * max_nb;
+        int lo = 0, hi = uj < 0 ? nj : nj - uj;
         while (lo < hi) {
             int mid = (lo + hi) >> 1;
-            if (entry_slot(nl[(int64_t)mid * Np + j]) < i)
+            if (entry_slot(lst[mid]) < i)
                 lo = mid + 1;
             else
                 hi = mid;
         }
-        rev[(int64_t)k * Np + i] = lo;
+        rev[(int64_t)k * Np + i] = (uj < 0 ? 0 : uj) + lo;
     }
 }
 

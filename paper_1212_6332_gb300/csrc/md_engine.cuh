@@ -211,6 +211,7 @@ struct Engine {
     // the pair pass are whole sectors (no read-modify-write fills)
     double4_32a* pc = nullptr;
     int* rev = nullptr;         // float64 path: [max_nb][N_pad] partner position of upper entries
+    int* nl_lo = nullptr;       // float64 path: [N_pad][max_nb] row-major lower parts (reverse-index search)
     int* n_up = nullptr;        // float64 path: [N_pad] upper entries of each list (lists are [upper | lower])
     double* exp_T = nullptr;    // exponential table
     // parameter adjoint work arrays (allocated on the first gradient call)
