@@ -634,11 +634,12 @@ __device__ __forceinline__ void sep_mixed_code(const CellSep& cs, float4 oi, flo
 }
 
 // Separation of list entry e in a mixed-precision kernel: from the entry's
-// cell offset when every box is wide, else from the packed coordinates.
+// cell offset when the atom's box has 3 or more cells per axis (every box,
+// WIDE), else from the packed coordinates.
 template <bool WIDE>
 __device__ __forceinline__ void sep_mixed_entry(const CellSep& cs, float4 oi, float4 oj, int e, float& dx, float& dy,
                                                 float& dz) {
-    if (WIDE)
+    if (WIDE || (cs.nx >= 3 && cs.ny >= 3 && cs.nz >= 3))
         sep_mixed_code(cs, oi, oj, entry_code(e), dx, dy, dz);
     else
         sep_mixed<false>(cs, oi, oj, dx, dy, dz);

@@ -157,3 +157,29 @@ def test_new_velocities_keep_forces_and_new_positions_do_not():
     got = s.get_forces()["f"].cpu().numpy()
     ref_f = O.forces(O.Potential(I.RGL_CU), x3, bx.box, skin=0.3)["f"]
     assert np.linalg.norm(got - ref_f, axis=1).max() <= F_TOL * np.linalg.norm(ref_f, axis=1).max()
+
+
+def test_round_trip_after_pressure_coupling_recomputes_forces():
+    """With the Eq. (5) coupling the box scaling follows the last force
+    pass, so the forces held after a step are not those of the final
+    positions: a state load of those positions must evaluate them again
+    (they then equal a fresh handle's forces at the same positions)."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bx = I.perturbed_fcc(5, I.A_CU, 300.0, I.MASS_CU, seed=45)
+    beta = 160.21766208 / 140.0
+    s = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    s.set_barostat(0.0, 50.0, beta)
+    s.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+    s.step(20)
+    box = s.box()[0]
+    assert not np.allclose(box, bx.box)
+    x, v = s.get_state()
+    held = s.get_forces()["f"].clone()
+    s.set_state(x, v)
+    got = s.get_forces()["f"]
+    fresh = System(I.RGL_CU, box=box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    ref = fresh.compute_forces(x.clone())["f"]
+    scale = ref.abs().max().item()
+    assert (got - ref).abs().max().item() <= 1e-12 * scale
+    assert (held - ref).abs().max().item() > 1e-9 * scale  # the held forces were of the unscaled positions
