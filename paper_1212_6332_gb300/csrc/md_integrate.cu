@@ -57,14 +57,16 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
                                                      float4* __restrict__ xo, const int* __restrict__ cell_t,
                                                      Ctl* ctl, unsigned long long* __restrict__ disp) {
     if (load_status(ctl)) return;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // one box: a grid-stride loop over a few waves of blocks, so that the
+    // per-block displacement maxima meet in few atomics on the box's word
+    // (one atomic per 256 atoms serialised on that one address); several
+    // boxes: one atom per thread (a block's atoms span one or two boxes)
     double d2 = 0.0;
     int b = -1;
-    if (i < N) {
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = SINGLE ? (int64_t)gridDim.x * blockDim.x : N;
+    for (int64_t i = i0; i < N; i += stride) {
         b = SINGLE ? 0 : g.atom_box[i];
-        double L[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
         double4_32a p = x[i];
         double4_32a q = xb[i];
         double vx = v[i], vy = v[Np + i], vz = v[2 * Np + i];
@@ -82,7 +84,8 @@ __global__ void __launch_bounds__(kINT) k_kick_drift(int64_t N, int64_t Np, Geo 
         v[2 * Np + i] = vz;
         x[i] = p;
         double dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-        d2 = dx * dx + dy * dy + dz * dz;
+        const double di = dx * dx + dy * dy + dz * dz;
+        d2 = di > d2 ? di : d2;
         // offset from the origin of the atom's cell at the last build; it
         // may leave [0, cell side) by the drift since then, which every user
         // of the offsets allows for
@@ -278,6 +281,7 @@ template <bool SINGLE>
 static void kick_drift_t(Engine& e, cudaStream_t s) {
     Geo g = make_geo(e);
     int nb = (int)((e.N + kINT - 1) / kINT);
+    if (SINGLE) nb = std::min(nb, 8 * e.n_sm);  // one wave of 8 resident blocks per SM, grid-stride
     double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
     PhaseScope scope(e, MD_PHASE_KICK_DRIFT, s);
     e.launches += 1;
