@@ -106,6 +106,15 @@ __device__ __forceinline__ void image_pos(const double4_32a& xj, unsigned code, 
     }
 }
 
+// Float64 pair cache entry (V'/r, rho'/r, rho(r), V(r)): written as one
+// 32-byte sector, read by the sums as its (V'/r, rho'/r) or (rho, V) half.
+__device__ __forceinline__ double2 cache_ab(const double4_32a* __restrict__ pc, int64_t slot) {
+    return reinterpret_cast<const double2*>(pc)[2 * slot];
+}
+__device__ __forceinline__ double2 cache_fv(const double4_32a* __restrict__ pc, int64_t slot) {
+    return reinterpret_cast<const double2*>(pc)[2 * slot + 1];
+}
+
 // |d|^2 with a fixed contraction, so every kernel that evaluates a pair
 // gets the same bits
 __device__ __forceinline__ double norm2(double dx, double dy, double dz) {

@@ -56,15 +56,6 @@ struct PairQueue {
     int pt[2][kQueue];         // type-pair table (several species)
 };
 
-// Pair cache entry (V'/r, rho'/r, rho(r), V(r)): written as one 32-byte
-// sector, read by the sums as its (V'/r, rho'/r) or (rho, V) half.
-__device__ __forceinline__ double2 cache_ab(const double4_32a* __restrict__ pc, int64_t slot) {
-    return reinterpret_cast<const double2*>(pc)[2 * slot];
-}
-__device__ __forceinline__ double2 cache_fv(const double4_32a* __restrict__ pc, int64_t slot) {
-    return reinterpret_cast<const double2*>(pc)[2 * slot + 1];
-}
-
 template <int KIND, bool MIRROR>
 __device__ __forceinline__ void eval_queued(const Pot& P, const PairQueue& q, int r, int p,
                                             double4_32a* __restrict__ pc) {

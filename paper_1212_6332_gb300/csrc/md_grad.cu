@@ -146,14 +146,6 @@ __global__ void __launch_bounds__(kGNT) k_grad_u(int64_t N, int64_t Np, Geo g, P
 // rho and rho' alone (every derivative of Eq. (1)-(3) with respect to
 // (A, xi, p, q, r0) is a multiple of these four at fixed r).
 
-// the cached (V'/r, rho'/r) and (rho, V) halves of a list entry
-__device__ __forceinline__ double2 grad_ab(const double4_32a* __restrict__ pc, int64_t slot) {
-    return reinterpret_cast<const double2*>(pc)[2 * slot];
-}
-__device__ __forceinline__ double2 grad_fv(const double4_32a* __restrict__ pc, int64_t slot) {
-    return reinterpret_cast<const double2*>(pc)[2 * slot + 1];
-}
-
 // F''(rho_i) from the stored rho_i
 template <int KIND>
 __global__ void __launch_bounds__(kGNT) k_grad_embed(int64_t N, Pot P, const double4_32a* __restrict__ x,
@@ -194,7 +186,7 @@ __global__ void __launch_bounds__(kGNT) k_grad_u_cached(int64_t N, int64_t Np, G
     double acc = 0.0;
     for (int k = 0; k < n; ++k) {
         const int64_t slot = (int64_t)k * Np + i;
-        const double2 c = grad_ab(pc, slot);
+        const double2 c = cache_ab(pc, slot);
         if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
         const int e = nl[slot];
         const int j = entry_slot(e);
@@ -237,9 +229,9 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_cached(int64_t N, int64
         const double aV = 0.5 * ge;
         for (int k = 0; k < n; ++k) {
             const int64_t slot = (int64_t)k * Np + i;
-            const double2 c = grad_ab(pc, slot);
+            const double2 c = cache_ab(pc, slot);
             if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
-            const double2 fv = grad_fv(pc, slot);
+            const double2 fv = cache_fv(pc, slot);
             const int e = nl[slot];
             const int j = entry_slot(e);
             double dx, dy, dz;
