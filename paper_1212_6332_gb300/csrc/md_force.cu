@@ -12,15 +12,18 @@
 // idle in this kernel pair, so the work is split to evaluate every pair's
 // functions once per step and to move bytes instead of float64 instructions:
 //   pairs:   the lower slot of each pair (j > i in i's list) evaluates V,
-//            rho, A = V'/r and B = rho'/r (one rsqrt, two table-driven
-//            exponentials) and writes them into both lists' slots (the
-//            partner's position comes from the reverse index built with the
-//            list); all four are functions of r alone, so both slots get
-//            the same bits the partner would have computed;
+//            rho, A = V'/r and B = rho'/r (one rsqrt; RGL: both
+//            exponentials from one reduction over an r table; splines: one
+//            interval record) and writes them as one 32-byte entry into
+//            both lists' slots (the partner's slot comes from the reverse
+//            index built with the list); all four are functions of r
+//            alone, so both slots get the same bits the partner would have
+//            computed;
 //   density: rho_i = sum rho, 1/2 sum V over i's slots in list order;
 //            F(rho_i), F'(rho_i);
-//   force:   F_i = sum_j [A + (F'_i + F'_j) B] (x_j - x_i)   [Eq. (3)]
-//            i.e. 5 float64 operations per pair after the separation,
+//   force:   F_i = sum_j s_ij x_j - x_i sum_j s_ij with
+//            s_ij = A + (F'_i + F'_j) B   [Eq. (3) regrouped]
+//            i.e. 6 float64 operations per entry and no separation,
 //            optionally followed by v_i += dt/2 F_i/m (second half-kick).
 // The sums run over each list in list order, as a full evaluation per atom
 // does (the block-per-box schedule evaluates every entry from its own
