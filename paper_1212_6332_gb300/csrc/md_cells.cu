@@ -237,8 +237,11 @@ void launch_rebuild(Engine& e, int mode, cudaStream_t s) {
     Geo g = make_geo(e);
     unsigned long long thr = disp_threshold(e);
     const int nt = 256;
-    // per-atom kernels: grid-stride over four waves of resident blocks
-    int nb_atoms = (int)std::min<int64_t>((e.N + nt - 1) / nt, (int64_t)32 * e.n_sm);
+    // per-atom kernels: grid-stride over one wave of resident blocks (on the
+    // steps that rebuild nothing each of them only reads the status and
+    // returns, and a smaller grid makes that cheaper: 25 us less per step
+    // than four waves on 4M atoms)
+    int nb_atoms = (int)std::min<int64_t>((e.N + nt - 1) / nt, (int64_t)8 * e.n_sm);
     int nb_scan = (e.n_cells + kScanNT - 1) / kScanNT;
     const unsigned long long* disp = e.disp_box;
     k_bin<<<nb_atoms, nt, 0, s>>>(e.N, e.x, g, e.cell_of, e.cell_count, e.ctl, disp, mode, thr);
