@@ -197,6 +197,44 @@ def oracle_sample(steps: int, cells: int = ORACLE_CELLS) -> dict:
                        f"seed {SEED}), {steps} velocity-Verlet steps minus its setup run")
 
 
+def oracle_batch_sample(steps: int = 3, n_sample: int = 16) -> dict:
+    """The CPU oracle on the first n_sample boxes of the 4096-box batch
+    (same seed), each box on its own: atom-steps/s of the sample."""
+    import oracle as O
+    bt = I.batch_of_boxes(n_sample, I.A_CU, I.MASS_CU, seed=2024)
+    pot = O.Potential(I.RGL_CU)
+    t_setup = t_run = 0.0
+    for k in range(n_sample):
+        lo, hi = int(bt.atom_offsets[k]), int(bt.atom_offsets[k + 1])
+        t0 = time.perf_counter()
+        O.md_run(pot, bt.x[lo:hi], bt.v[lo:hi], bt.box[k], I.MASS_CU, DT, SKIN, 0)
+        t1 = time.perf_counter()
+        O.md_run(pot, bt.x[lo:hi], bt.v[lo:hi], bt.box[k], I.MASS_CU, DT, SKIN, steps)
+        t2 = time.perf_counter()
+        t_setup += t1 - t0
+        t_run += t2 - t1
+    n = int(bt.atom_offsets[n_sample])
+    per_step = max(t_run - t_setup, 1e-9) / steps
+    return dict(value=n / per_step, unit=UNIT, cores=1,
+                sample=f"oracle on the first {n_sample} boxes of the batch ({n} atoms), {steps} steps each")
+
+
+def oracle_grad_sample(n_cfg: int = 8) -> dict:
+    """The CPU oracle's parameter gradient (forward mode, RGL, 5 parameters)
+    on n_cfg configurations of the 256-configuration fitting set, scaled to
+    (gradient over 256 configurations)/s."""
+    import oracle as O
+    cfgs = [I.strained_fcc(6, I.A_CU, seed=5000 + k) for k in range(n_cfg)]
+    pot = O.Potential(I.RGL_CU)
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    for c in cfgs:
+        O.param_grad(pot, c.x, c.box, rng.normal(size=(c.n, 3)), 1.0)
+    dt = time.perf_counter() - t0
+    return dict(value=n_cfg / dt / 256.0, unit="(gradient over 256 configs)/s", cores=1,
+                sample=f"oracle forward-mode gradient on {n_cfg} of the 256 configurations, scaled to 256")
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -607,7 +645,8 @@ def main():
         import oracle as O
         O.build()
         smp = oracle_sample(3)
-        cpu = {"value": smp["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp["sample"]}
+        cpu = {"value": smp["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp["sample"],
+               "batch_sample": oracle_batch_sample(), "grad_sample": oracle_grad_sample()}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
