@@ -90,7 +90,11 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = ROOT / "gpurun_out" / f"clocks_bench_{os.getpid()}.csv"
+        # the raw samples go to MD_CLOCKS_DIR (default: the system's temporary
+        # directory); the JSON line carries their summary
+        import tempfile
+        base = pathlib.Path(os.environ.get("MD_CLOCKS_DIR", tempfile.gettempdir()))
+        self.path = base / f"clocks_bench_{os.getpid()}.csv"
 
     def __enter__(self):
         try:
