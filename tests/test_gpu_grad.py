@@ -97,3 +97,28 @@ def test_mixed_precision_adjoint_within_bound(kind):
     got = s.param_grad(torch.tensor(g_f, device="cuda"), torch.tensor(g_e, device="cuda")).cpu().numpy()
     ref = oracle_grad(spec, cfgs, g_f, g_e)
     assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("kind", ["rgl", "spline"])
+def test_adjoint_from_the_forward_cache_equals_the_recomputed_one(kind):
+    """The float64 adjoint reads the forward pass's pair cache, rho and F'
+    when they are current; after a call that leaves them stale it evaluates
+    the pair functions again. Both paths give the same gradient (to
+    rounding), and with the Newton's-third-law sums on (lower cache slots
+    unwritten) the recomputing path serves and still matches the oracle."""
+    import torch
+    from paper_1212_6332_gb300.fit import make_batch
+    spec = MODEL if kind == "rgl" else O.tabulate_spline(MODEL, n_knots=60, rho_hi=2 * RHO_EQ)
+    cfgs = configs((3, 4), seed=71)
+    s = make_batch(spec, cfgs)
+    n = sum(c.n for c in cfgs)
+    rng = np.random.default_rng(8)
+    g_f = torch.tensor(rng.normal(size=(n, 3)), device="cuda")
+    g_e = torch.tensor(rng.normal(size=len(cfgs)), device="cuda")
+    cached = s.param_grad(g_f, g_e).cpu().numpy()
+    s.set_newton3(True)  # the adjoint may no longer read the cache
+    recomputed = s.param_grad(g_f, g_e).cpu().numpy()
+    ref = oracle_grad(spec, cfgs, g_f.cpu().numpy(), g_e.cpu().numpy())
+    scale = np.abs(ref).max()
+    assert np.abs(cached - recomputed).max() <= 1e-12 * scale
+    assert np.abs(recomputed - ref).max() <= 1e-10 * scale
