@@ -230,6 +230,31 @@ static unsigned long long disp_threshold(const Engine& e) {
     return bits;
 }
 
+// Gate of a graph-captured step: the rebuild body (binning, sort, list
+// build) runs only when some box moved more than half the skin since its
+// last build and no error is pending; otherwise every kernel of the body
+// would return at once, and skipping them saves their launches.
+__global__ void k_rebuild_gate(int B, const unsigned long long* __restrict__ disp, unsigned long long thr, Ctl* ctl,
+                               cudaGraphConditionalHandle h) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) mine |= disp[b] > thr;
+    if (mine) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool run = any && !load_status(ctl);
+        cudaGraphSetConditional(h, run ? 1u : 0u);
+        if (!run) atomicAdd(&ctl->n_gate_skip, 1ull);
+    }
+}
+
+void launch_rebuild_gate(Engine& e, cudaGraphConditionalHandle h, cudaStream_t s) {
+    e.launches += 1;
+    k_rebuild_gate<<<1, 256, 0, s>>>(e.B, e.disp_box, disp_threshold(e), e.ctl, h);
+}
+
 void launch_rebuild(Engine& e, int mode, cudaStream_t s) {
     if (e.N == 0) return;
     PhaseScope scope(e, MD_PHASE_REBUILD, s);

@@ -103,6 +103,7 @@ struct Ctl {
     long long n_rebuild;             // list builds since set_state
     int max_count;                   // largest neighbour count of the current list
     int n_due;                       // cells queued for a partial list build
+    unsigned long long n_gate_skip;  // graph-replayed steps whose rebuild body the gate skipped (never reset)
     int pos_changed;                 // a state load that kept the lists met a position unlike the current one
 };
 
@@ -237,6 +238,12 @@ struct Engine {
     bool forces_ok = false; // f, rho, F', e_atom are those of the current positions (not after a box scaling)
     Bath bath{};            // friction of Eq. (4) applied in the kicks (md_set_thermostat)
     bool newton3 = false;   // float64 half-list sums with Newton's third law (md_set_newton3)
+    // captured steps skip their rebuild kernels through a graph conditional
+    // node when no box is due (cond_off: the capture fell back to plain
+    // launches); the launch count subtracts the skipped bodies
+    bool cond_off = false;
+    long long graph_body_kernels = 0;
+    unsigned long long gate_skip_seen = 0;
     Baro baro{};            // pressure coupling of Eq. (5) after each step (md_set_barostat)
     int* types = nullptr;   // [N] species of each atom, caller order (md_set_types; 0 by default)
     double* w_atom = nullptr;   // [N_pad] per-atom virial -1/2 sum_j s_ij r_ij^2 (pressure users only)
@@ -303,6 +310,7 @@ CellSep single_cell_sep(const Engine& e);
 // binning + sort + permute + list build; mode 1 = always, 0 = only when the
 // device displacement word exceeds (skin/2)^2
 void launch_rebuild(Engine& e, int mode, cudaStream_t s);
+void launch_rebuild_gate(Engine& e, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_build_list(Engine& e, int mode, cudaStream_t s);
 // density and force passes (fp64 or mixed); kick != 0 fuses v += dt/2 F/m
 void launch_forces(Engine& e, int kick, cudaStream_t s, bool virial = false);

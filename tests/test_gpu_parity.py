@@ -156,6 +156,30 @@ def test_trajectory_matches_oracle_small_box():
         assert out["step"] == 200 and out["n_rebuild"] >= 1
 
 
+def test_graph_replay_gates_the_rebuild_and_matches_plain_launches():
+    """Graph-replayed steps of one box skip the binning and list kernels on
+    the steps that rebuild nothing (a conditional node set on the device by
+    the half-skin test), and end bit for bit where plain launches end."""
+    torch = torch_cuda()
+    bx = I.perturbed_fcc(8, I.A_CU, 600.0, I.MASS_CU, seed=12346)
+    K = 400
+    res = {}
+    for use_graph in (False, True):
+        s = make_system(I.RGL_CU, bx.box, bx.n)
+        s.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+        s.profile_start()
+        out = s.step(K, use_graph=use_graph)
+        res[use_graph] = (out["n_rebuild"], s.profile_read()["launches"], [t.cpu().numpy() for t in s.get_state()])
+        s.close()
+    (nr, ln, sn), (ng, lg, sg) = res[False], res[True]
+    assert nr == ng and 1 <= nr < K // 4
+    assert np.array_equal(sn[0], sg[0]) and np.array_equal(sn[1], sg[1])
+    # plain launches: L per step; replays: L + 1 (the gate) less the body on
+    # each of the K - n_rebuild steps without a list build
+    saved = ln - lg + K
+    assert saved % (K - nr) == 0 and saved // (K - nr) >= 10
+
+
 def test_runs_are_bitwise_deterministic():
     torch = torch_cuda()
     bx = I.perturbed_fcc(6, I.A_CU, 1200.0, I.MASS_CU, seed=4)
