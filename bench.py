@@ -239,6 +239,12 @@ def oracle_grad_sample(n_cfg: int = 8) -> dict:
                 sample=f"oracle forward-mode gradient on {n_cfg} of the 256 configurations, scaled to 256")
 
 
+def workload_name(cells: int, precision: str) -> str:
+    """The timed single-box workload, named by what it is."""
+    return (f"fcc Cu {cells}^3 cells ({4 * cells ** 3} atoms), RGL Cu taper 4.5-5.0 A, skin {SKIN} A, "
+            f"{TEMP:.0f} K, dt {DT} fs, " + ("float64" if precision == "fp64" else "mixed precision"))
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -260,9 +266,9 @@ def run_reference(args):
     sample = (f"oracle on a {cells}^3-cell fcc Cu box ({bx.n} atoms, same lattice, RGL, {TEMP:.0f} K, seed {SEED}); "
               f"per-step time = ({K} steps run - setup run) / {K}")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-           "warmup": W, "ms_per_step": per_step * 1e3 * (4_000_000 / bx.n), "higher_is_better": True,
+           "warmup": W, "ms_per_step": per_step * 1e3 * (4 * args.cells ** 3 / bx.n), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "fcc Cu RGL 300 K FP64 (4,000,000-atom box; CPU sample of 500,000 atoms)",
+           "config": {"workload": workload_name(args.cells, "fp64"), "atoms": 4 * args.cells ** 3,
                       "sample_atoms": bx.n},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -656,9 +662,7 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-               "config": {"workload": f"fcc Cu {args.cells}^3 cells ({N} atoms), RGL Cu taper 4.5-5.0 A, "
-                                      f"skin {SKIN} A, {TEMP:.0f} K, dt {DT} fs, "
-                                      + ("float64" if args.precision == "fp64" else "mixed precision"),
+               "config": {"workload": workload_name(args.cells, args.precision),
                           "atoms": N, "parallelism": "replicas" if world > 1 else "single",
                           "l2": "working set (list + positions) larger than L2",
                           "mean_list_len": K_list, "mean_in_cutoff": K_in,
