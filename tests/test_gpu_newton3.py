@@ -156,3 +156,42 @@ def test_newton3_switch_back_is_reproducible_and_mixed_is_refused():
     with pytest.raises(MDError) as err:
         m.set_newton3(True)
     assert err.value.code == 7
+
+
+@pytest.mark.parametrize("newton3", [False, True])
+def test_list_overflow_under_compression_regrows_mid_run(newton3):
+    """Pressure coupling towards 20 GPa shrinks the box by a few per cent, so
+    the neighbour counts outgrow a list sized to the initial maximum: the
+    overflow is caught on the device, the lists regrow and the trajectory
+    stays the oracle's, with plain launches and with graph replay alike (bit
+    for bit alike with the full-list sums)."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bx = I.perturbed_fcc(7, I.A_CU, 600.0, I.MASS_CU, seed=91)
+    P0 = 20.0 / 160.21766208  # eV/A^3
+    probe = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    probe.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+    cap = probe.max_count()
+    probe.close()
+    ref = O.md_run(O.Potential(I.RGL_CU), bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 150, tau_p=50.0, P0=P0,
+                   beta=BETA)
+    assert ref["box"][0] < 0.975 * bx.box[0]
+    runs = []
+    for use_graph in (False, True):
+        s = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU, max_neighbors=cap)
+        s.set_newton3(newton3)
+        s.set_barostat(P0, 50.0, BETA)
+        s.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+        s.step(150, use_graph=use_graph)
+        assert s.max_count() > cap
+        box = s.box()[0]
+        assert np.allclose(box, ref["box"], rtol=1e-11, atol=0)
+        x, v = (t.cpu().numpy() for t in s.get_state())
+        d = x - ref["x"]
+        d -= box * np.round(d / box)
+        assert np.abs(d).max() < 1e-9
+        assert np.abs(v - ref["v"]).max() < 1e-8 * np.abs(ref["v"]).max()
+        runs.append((x, v))
+        s.close()
+    if not newton3:  # the half-list partner updates are atomic adds in no fixed order
+        assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
