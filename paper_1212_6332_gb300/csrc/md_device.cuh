@@ -293,6 +293,32 @@ __device__ __forceinline__ int rotate_list(int64_t Np, int64_t i, int n, int* __
     return n - lo;
 }
 
+// The same rotation for the kernel-built lists, which the list build wrote
+// into a scratch array of the same layout (raw): each row is gathered from
+// its rotated source row, so no per-thread staging is needed.
+__device__ __forceinline__ int rotate_list_from(int64_t Np, int64_t i, int n, const int* __restrict__ raw,
+                                                int* __restrict__ nl, int* __restrict__ nl_lo, int max_nb) {
+    int* lo_out = nl_lo + i * (int64_t)max_nb;
+    if (n > kRotMax) {
+        for (int k = 0; k < n; ++k) {
+            const int v = raw[(int64_t)k * Np + i];
+            lo_out[k] = v;
+            nl[(int64_t)k * Np + i] = v;
+        }
+        return -1;
+    }
+    int lo = 0;
+    while (lo < n && entry_slot(raw[(int64_t)lo * Np + i]) < i) {
+        lo_out[lo] = raw[(int64_t)lo * Np + i];
+        ++lo;
+    }
+    for (int k = 0; k < n; ++k) {
+        const int src = k + lo < n ? k + lo : k + lo - n;
+        nl[(int64_t)k * Np + i] = raw[(int64_t)src * Np + i];
+    }
+    return n - lo;
+}
+
 __device__ __forceinline__ void reverse_index(int64_t Np, int64_t i, int n, int nup, const int* __restrict__ nn,
                                               const int* __restrict__ nl, const int* __restrict__ nl_lo,
                                               const int* __restrict__ n_up, int max_nb, int* __restrict__ rev) {

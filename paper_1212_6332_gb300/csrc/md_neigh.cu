@@ -229,13 +229,16 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(int n_cells, Geo g, c
     }
 }
 
-__global__ void k_rotate_lists(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn, int* __restrict__ nl,
-                               int* __restrict__ nl_lo, int max_nb, int* __restrict__ n_up, const Ctl* ctl,
+// raw: the lists as built (ascending), in the reverse-index array, which
+// k_build_rev overwrites next
+__global__ void k_rotate_lists(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn,
+                               const int* __restrict__ raw, int* __restrict__ nl, int* __restrict__ nl_lo,
+                               int max_nb, int* __restrict__ n_up, const Ctl* ctl,
                                const unsigned long long* __restrict__ disp, int mode, unsigned long long thr) {
     if (load_status(ctl)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
         if (box_due(disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr))
-            n_up[i] = rotate_list(Np, i, min(nn[i], max_nb), nl, nl_lo, max_nb);
+            n_up[i] = rotate_list_from(Np, i, min(nn[i], max_nb), raw, nl, nl_lo, max_nb);
 }
 
 __global__ void k_build_rev(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn, const int* __restrict__ nl,
@@ -294,14 +297,17 @@ void launch_build_list(Engine& e, int mode, cudaStream_t s) {
         e.launches += 1;
     }
     const int nl_blocks = std::max(1, std::min(e.n_cells, nl_per_sm * e.n_sm));
-    k_build_list<<<nl_blocks, kNlThreads, 0, s>>>(e.n_cells, g, e.x, e.xo, e.cell_start, e.nn, e.nl, e.max_nb,
+    // float64 lists are built into the reverse-index array and rotated from
+    // there into nl (the reverse index is rebuilt right after)
+    int* built = e.rev ? e.rev : e.nl;
+    k_build_list<<<nl_blocks, kNlThreads, 0, s>>>(e.n_cells, g, e.x, e.xo, e.cell_start, e.nn, built, e.max_nb,
                                                   e.N_pad, rl2, lo, hi, e.ctl, e.due_cells, mode,
                                                   e.cfg.precision == MD_MIXED);
     if (e.rev) {
         // grid-stride over the atoms with four waves of resident blocks
         int nb = (int)std::min<int64_t>((e.N + 255) / 256, (int64_t)32 * e.n_sm);
-        k_rotate_lists<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.nl, e.nl_lo, e.max_nb, e.n_up, e.ctl, e.disp_box,
-                                          mode, thr);
+        k_rotate_lists<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.rev, e.nl, e.nl_lo, e.max_nb, e.n_up, e.ctl,
+                                          e.disp_box, mode, thr);
         k_build_rev<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.nl, e.nl_lo, e.max_nb, e.n_up, e.rev, e.ctl,
                                        e.disp_box, mode, thr);
         e.launches += 2;
