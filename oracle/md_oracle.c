@@ -42,7 +42,8 @@
  *   F(rho) = F'(rho) = 0 for rho <= 0 (an isolated atom).
  *
  * Periodic rules (shared in meaning, not in code, with the CUDA side):
- *   wrap:          x <- x - L*floor(x/L); if x >= L then x <- x - L
+ *   wrap:          x <- x - L*floor(x/L); if x < 0 then x <- x + L;
+ *                  if x >= L then x <- x - L
  *   minimum image: d = x_j - x_i; if d > L/2 then d -= L
  *                                 else if d < -L/2 then d += L
  *   list test:     dx*dx + dy*dy + dz*dz < rl*rl, left to right, rounded
@@ -342,8 +343,11 @@ void orc_embed_eval(const orc_pot* P, int n, const double* rho, double* F, doubl
 /* periodic geometry                                                   */
 /* ------------------------------------------------------------------ */
 
+/* x - L*floor(x/L) can round to a tiny negative value (x just below k*L,
+ * |k| >= 2, where L*k rounds above x) or to L; both are folded into [0, L). */
 static double wrap1(double x, double L) {
     double y = x - L * floor(x / L);
+    if (y < 0.0) y += L;
     if (y >= L) y -= L;
     return y;
 }
@@ -770,6 +774,9 @@ static dual ddiv(dual a, dual b) {
 static dual dscale(dual a, double s) { dual r = {a.v * s, a.d * s}; return r; }
 static dual dexp(dual a) { double e = exp(a.v); dual r = {e, e * a.d}; return r; }
 static dual dsqrt(dual a) { double s = sqrt(a.v); dual r = {s, 0.5 * a.d / s}; return r; }
+static dual dlog(dual a) { dual r = {log(a.v), a.d / a.v}; return r; }
+/* b^e for b > 0, both dual: exp(e log b) */
+static dual dpow(dual b, dual e) { return dexp(dmul(e, dlog(b))); }
 
 typedef struct {
     int n;
@@ -839,18 +846,20 @@ typedef struct {
 } dpot;
 
 /* Builds the dual potential with parameter `which` seeded (d = 1).
- * RGL order: A, xi, p, q, r0. Spline order: phi knots, f knots, F knots. */
+ * RGL order: A, xi, p, q, r0. Sutton-Chen order: eps, c, a, n, m.
+ * Spline order: phi knots, f knots, F knots. */
 static void dpot_init(dpot* D, const orc_pot* P, int which) {
     D->kind = P->kind;
     D->r_taper = P->r_taper;
     D->r_cut = P->r_cut;
+    D->n_types = P->n_types;
+    D->n_tab = 0;
+    D->tab = NULL;
     for (int k = 0; k < 8; ++k) D->prm[k] = dc(P->prm[k]);
     if (P->kind != ORC_SPLINE) {
         if (which >= 0 && which < 8) D->prm[which].d = 1.0;
         return;
     }
-    D->n_types = P->n_types;
-    D->tab = NULL;
     if (P->n_types > 1) {
         /* the tables in knot order: V pairs, rho pairs, F types */
         int np = P->n_types * (P->n_types + 1) / 2;
@@ -921,6 +930,17 @@ static void dpair_eval(const dpot* D, int pt, double r, dual* phi, dual* dphi, d
         *dphi = dmul(a2, dadd(dscale(ddiv(p, r0), -S), dc(dS)));
         *f = dscale(dmul(xi2, e2), S);
         *df = dmul(dmul(xi2, e2), dadd(dscale(ddiv(q, r0), -2.0 * S), dc(dS)));
+    } else if (D->kind == ORC_SC) {
+        dual eps = D->prm[0], a = D->prm[2], n = D->prm[3], m = D->prm[4];
+        double S, dS;
+        taper(r, D->r_taper, D->r_cut, &S, &dS);
+        dual ar = ddiv(a, dc(r));
+        dual an = dpow(ar, n), am = dpow(ar, m);
+        dual ean = dmul(eps, an);
+        *phi = dscale(ean, S);
+        *dphi = dmul(ean, dadd(dscale(ddiv(n, dc(r)), -S), dc(dS)));
+        *f = dscale(am, S);
+        *df = dmul(am, dadd(dscale(ddiv(m, dc(r)), -S), dc(dS)));
     } else if (D->tab) {
         int np = D->n_types * (D->n_types + 1) / 2;
         dspline_eval(&D->tab[pt], dc(r), phi, dphi);
@@ -943,9 +963,11 @@ static void dembed_eval(const dpot* D, int a, dual rho, dual* F, dual* Fp) {
         *F = *Fp = dc(0.0);
         return;
     }
+    /* F = -scale sqrt(rho): scale 1 for RGL, c*eps for Sutton-Chen */
+    dual scale = D->kind == ORC_SC ? dmul(D->prm[1], D->prm[0]) : dc(1.0);
     dual sq = dsqrt(rho);
-    *F = dscale(sq, -1.0);
-    *Fp = ddiv(dc(-0.5), sq);
+    *F = dscale(dmul(scale, sq), -1.0);
+    *Fp = ddiv(dscale(scale, -0.5), sq);
 }
 
 /* Directional derivatives of the forces and the energy of one configuration

@@ -62,10 +62,11 @@ def normal(seed: int, count: int, start: int = 0) -> np.ndarray:
 
 
 def wrap(x: np.ndarray, box) -> np.ndarray:
-    """Maps coordinates into [0, L) per axis: x - L*floor(x/L), then one
-    more subtraction of L if rounding left x == L."""
+    """Maps coordinates into [0, L) per axis: x - L*floor(x/L), one addition
+    of L if rounding left it negative, then one subtraction of L if it is L."""
     box = np.asarray(box, dtype=np.float64)
     y = x - box * np.floor(x / box)
+    y = np.where(y < 0.0, y + box, y)
     return np.where(y >= box, y - box, y)
 
 

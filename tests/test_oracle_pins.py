@@ -282,6 +282,68 @@ def test_time_reversibility():
     assert np.abs(back["v"] + bx.v).max() < 1e-10
 
 
+def exact_residue(x, L):
+    """x mod L in exact rational arithmetic, in [0, L)."""
+    from fractions import Fraction
+    import math
+    fx, fL = Fraction(float(x)), Fraction(float(L))
+    return fx - fL * math.floor(fx / fL)
+
+
+@pytest.mark.parametrize("L", [3.615, 28.92, 361.5, 281.84])
+def test_wrap_rule_special_values(L):
+    """Periodic wrap of Sec. 3.2 into [0, L): named values, including the case
+    where x - L*floor(x/L) rounds to L (x = -1e-17) and must become 0."""
+    ulp_below_L = np.nextafter(L, 0.0)
+    cases = {-L: 0.0, -1e-17: 0.0, -np.nextafter(0.0, 1.0): 0.0, 0.0: 0.0, ulp_below_L: ulp_below_L, L: 0.0,
+             2 * L: 0.0, 1.25: 1.25 if 1.25 < L else None}
+    for x, want in cases.items():
+        if want is None:
+            continue
+        got = O.wrap(np.array([[x, x, x]]), np.array([L, L, L]))[0]
+        assert got.tolist() == [want] * 3, (x, got)
+    delta = 0.3125
+    got = O.wrap(np.array([[2 * L + delta] * 3]), np.array([L] * 3))[0, 0]
+    assert got == pytest.approx(delta, abs=4 * np.spacing(2 * L)) and 0.0 <= got < L
+
+
+@pytest.mark.parametrize("L", [3.615, 28.92, 361.5, 281.84, 10.845, 0.1, 7.0])
+def test_wrap_lands_in_the_box_next_to_every_multiple(L):
+    """Coordinates a few ulp either side of k*L, |k| <= 150, land in [0, L) and
+    equal the exact residue x mod L (rational arithmetic) to a few ulp, or
+    its image across the boundary. Without the fold of negative results,
+    x just below k*L (|k| >= 2) wraps to about -1e-14."""
+    xs = []
+    for k in range(-150, 151):
+        c = k * L
+        lo = hi = c
+        xs.append(c)
+        for _ in range(3):
+            lo, hi = np.nextafter(lo, -np.inf), np.nextafter(hi, np.inf)
+            xs += [lo, hi]
+    xs = np.array(xs)
+    got = O.wrap(np.repeat(xs[:, None], 3, axis=1), np.array([L, L, L]))[:, 0]
+    assert np.all(got >= 0.0) and np.all(got < L)
+    for x, y in zip(xs, got):
+        r = float(exact_residue(x, L))
+        tol = 4 * np.spacing(max(abs(x), L))
+        assert min(abs(y - r), abs(y - r + L), abs(y - r - L)) <= tol, (x, y, r)
+
+
+def test_trajectory_positions_stay_in_the_box():
+    """Every position that velocity Verlet returns lies in [0, L), also from
+    a start given far outside the box (unwrapped by several box lengths)."""
+    bx = I.perturbed_fcc(4, I.A_CU, 1200.0, I.MASS_CU, seed=31)
+    shift = np.array([-3.0, 2.0, 7.0]) * bx.box
+    x0 = bx.x + shift[None, :] * (np.arange(len(bx.x)) % 2)[:, None]
+    out = O.md_run(O.Potential(I.RGL_CU), x0, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 30)
+    assert np.all(out["x"] >= 0.0) and np.all(out["x"] < bx.box)
+    ref = O.md_run(O.Potential(I.RGL_CU), bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 30)
+    d = out["x"] - ref["x"]
+    d -= bx.box * np.round(d / bx.box)
+    assert np.abs(d).max() < 1e-9
+
+
 def gas(n_side=4, spacing=6.5, temperature=600.0, seed=21):
     """Atoms on a simple cubic grid farther apart than r_cut + skin: no
     forces act, only the friction of Eq. (4)."""
@@ -557,6 +619,21 @@ def test_rgl_param_derivatives_match_finite_differences():
         assert dE == pytest.approx((rp["E"] - rm["E"]) / (2 * h), rel=1e-6)
         fd = (rp["f"] - rm["f"]) / (2 * h)
         assert np.abs(dF - fd).max() <= 1e-6 * np.abs(fd).max()
+
+
+def test_sutton_chen_param_derivatives_match_finite_differences():
+    """Forward-mode derivatives for Sutton-Chen (eps, c, a, n, m), including
+    the c*eps factor of its embedding, against central differences."""
+    bx = I.strained_fcc(5, I.A_CU, seed=9)
+    pot = O.Potential(I.SC_CU)
+    for k, name in enumerate(O.SC_ORDER):
+        dE, dF = O.param_deriv(pot, k, bx.x, bx.box)
+        h = 1e-6 * abs(I.SC_CU[name])
+        rp = O.forces(O.Potential(dict(I.SC_CU, **{name: I.SC_CU[name] + h})), bx.x, bx.box)
+        rm = O.forces(O.Potential(dict(I.SC_CU, **{name: I.SC_CU[name] - h})), bx.x, bx.box)
+        assert dE == pytest.approx((rp["E"] - rm["E"]) / (2 * h), rel=1e-6), name
+        fd = (rp["f"] - rm["f"]) / (2 * h)
+        assert np.abs(dF - fd).max() <= 1e-6 * np.abs(fd).max(), name
 
 
 def test_loss_gradient_matches_finite_differences():
