@@ -22,10 +22,12 @@ __device__ __forceinline__ float minimgf(float d, float L, float h) {
 }
 
 // Wraps a coordinate into [0, L): x - L*floor(x/L) rounded after each
-// operation (no fused multiply-add), then one more -L if rounding gave L.
+// operation (no fused multiply-add); +L if rounding left it negative (x just
+// below k*L with |k| >= 2, where L*k rounds above x), then -L if it is L.
 __device__ __forceinline__ double wrap_coord(double x, double L) {
     double k = floor(__ddiv_rn(x, L));
     double y = __dsub_rn(x, __dmul_rn(L, k));
+    if (y < 0.0) y = __dadd_rn(y, L);
     if (y >= L) y = __dsub_rn(y, L);
     return y;
 }

@@ -183,3 +183,28 @@ def test_round_trip_after_pressure_coupling_recomputes_forces():
     scale = ref.abs().max().item()
     assert (got - ref).abs().max().item() <= 1e-12 * scale
     assert (held - ref).abs().max().item() > 1e-9 * scale  # the held forces were of the unscaled positions
+
+
+def test_far_unwrapped_positions_wrap_by_the_oracle_rule():
+    """Positions given several box lengths away (and a few ulp below a
+    multiple of L, where x - L floor(x/L) rounds below zero) are wrapped on
+    the device by the same rule as the oracle: md_get_state returns exactly
+    the oracle's wrapped coordinates, all in [0, L), and the forces are
+    those of the wrapped box."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bx = I.perturbed_fcc(5, I.A_CU, 300.0, I.MASS_CU, seed=57)
+    k = np.zeros_like(bx.x)
+    k[0::4, 0], k[1::4, 1], k[2::4, 2], k[3::4] = 3.0, -5.0, 7.0, -2.0
+    x_far = bx.x + k * bx.box
+    # atoms placed a few ulp below k*L on one axis
+    for i, kk in zip(range(0, 40, 4), range(-6, 4)):
+        x_far[i, 0] = np.nextafter(kk * bx.box[0], -np.inf)
+    want = O.wrap(x_far, bx.box)
+    assert np.all(want >= 0.0) and np.all(want < bx.box)
+    s = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    s.set_state(torch.tensor(x_far, device="cuda"))
+    x, _ = (t.cpu().numpy() for t in s.get_state())
+    assert np.array_equal(x, want)
+    check(forces_of(s, torch.tensor(x_far, device="cuda")),
+          O.forces(O.Potential(I.RGL_CU), want, bx.box, skin=0.3))
