@@ -142,18 +142,27 @@ typedef struct md_thermo {
 
 /* ---------------------------------------------------------------- single box */
 
-/* Creates a single-box context for n_atoms atoms. Allocates every device
- * buffer (positions, velocities, forces, cells, neighbour list). No state
- * is set: call md_set_state or md_compute_forces next. *out receives the
- * handle. Errors: MD_ERR_ARG (bad config or potential, box too small for
- * the list radius), MD_ERR_NOMEM, MD_ERR_CUDA. */
+/* Creates a single-box context for n_atoms atoms: the initialisation of
+ * Sec. 3.1, which allocates the device arrays of positions, velocities,
+ * forces, neighbour counts, the neighbour list with a maximum count per atom
+ * (MN there; max_neighbors here, regrown on overflow) and densities, for a
+ * system whose energy is Eq. (1)-(2) with the potential `pot` (Sec. 2).
+ * Cell tables (Sec. 3.2) are allocated as well. No state is set: call
+ * md_set_state or md_compute_forces next. *out receives the handle.
+ * Errors: MD_ERR_ARG (bad config or potential, box too small for the list
+ * radius), MD_ERR_NOMEM, MD_ERR_CUDA. */
 MD_API int md_create(const md_config* cfg, const md_potential* pot, int64_t n_atoms, md_ctx** out);
 
-/* Frees the handle and all its device memory (synchronizes its streams). */
+/* Frees the handle and all the device arrays that md_create allocated
+ * (those of Sec. 3.1; the paper does not describe releasing them, so this
+ * call has no counterpart in the paper). Synchronizes the device.
+ * MD_ERR_ARG for a NULL handle. */
 MD_API int md_destroy(md_ctx* ctx);
 
 /* Sets positions x [n][3] and velocities v [n][3] (host or device; v may be
- * NULL for zero velocities). Positions are wrapped into the box, atoms are
+ * NULL for zero velocities): the state of Sec. 2 that Sec. 3.1 copies to the
+ * device arrays of positions and velocities. Positions are wrapped into the
+ * box (x - L floor(x/L), folded into [0, L)), atoms are
  * binned and sorted, the neighbour list is built and forces are evaluated,
  * so that md_step can start. Resets the step and rebuild counters.
  * Lists built before are kept for positions within half the skin of their
@@ -166,7 +175,10 @@ MD_API int md_destroy(md_ctx* ctx);
 MD_API int md_set_state(md_ctx* ctx, const double* x, const double* v, md_stream stream);
 
 /* Copies the current positions and/or velocities (either may be NULL) to
- * x, v [n][3] (host or device), caller order. */
+ * x, v [n][3] (host or device), caller order: the copy of the device
+ * arrays of positions and velocities back to the host of Sec. 3.3 (Fig. 4),
+ * mapped back through the cell sort of Sec. 3.2 (the paper's index array
+ * from sorted to original atoms). Positions are wrapped into [0, L). */
 MD_API int md_get_state(md_ctx* ctx, double* x, double* v, md_stream stream);
 
 /* Rebuilds cells and the neighbour list from the current positions
@@ -177,13 +189,15 @@ MD_API int md_get_state(md_ctx* ctx, double* x, double* v, md_stream stream);
  * retries on overflow (up to 4 times; then MD_ERR_NEIGH_OVERFLOW). */
 MD_API int md_build_neighbors(md_ctx* ctx, md_stream stream);
 
-/* Copies the current neighbour list in caller ids: nn [n] (device) gets
- * each atom's count, nl [n][ld] (device) its neighbours (unordered; slots
+/* Copies the current neighbour list of Sec. 3.2 (Fig. 3) in caller ids:
+ * nn [n] (device) gets each atom's count, nl [n][ld] (device) its
+ * neighbours (unordered; slots
  * beyond the count are left untouched). MD_ERR_ARG if ld is smaller than
  * the largest count (query it with md_max_count). */
 MD_API int md_get_neighbors(md_ctx* ctx, int32_t* nn, int32_t* nl, int32_t ld, md_stream stream);
 
-/* Largest neighbour count of the current list (synchronizes). */
+/* Largest neighbour count of the current list (synchronizes): the quantity
+ * that bounds MN, the list capacity of Sec. 3.1. */
 MD_API int md_max_count(md_ctx* ctx, int32_t* out);
 
 /* Sets positions x [n][3] (host or device; velocities are kept), rebuilds
@@ -194,14 +208,17 @@ MD_API int md_max_count(md_ctx* ctx, int32_t* out);
 MD_API int md_compute_forces(md_ctx* ctx, const double* x, double* f, double* e_atom, double* rho, double* e_total,
                       md_stream stream);
 
-/* Copies forces, per-atom energies and densities of the current state
- * (each optional; host or device). */
+/* Copies forces f_i of Eq. (3), per-atom energies E_i of Eq. (1) and
+ * densities rho_i of Sec. 2 of the current state (each optional; host or
+ * device). */
 MD_API int md_get_forces(md_ctx* ctx, double* f, double* e_atom, double* rho, md_stream stream);
 
-/* Advances n_steps velocity-Verlet steps of dt:
- *   v += dt/2 F/m; x += dt v; wrap; rebuild the list if some atom moved
- *   more than skin/2 since the last build; density pass; force pass;
- *   v += dt/2 F/m.
+/* Advances n_steps steps of dt, each the step of Sec. 3.3 (Fig. 4):
+ * predict, density pass (Fig. 5), force pass of Eq. (3) (Fig. 6), correct,
+ * with velocity Verlet as the predictor and corrector:
+ *   v += dt/2 F/m; x += dt v; wrap; rebuild the list (Sec. 3.2) if some
+ *   atom moved more than skin/2 since the last build (the paper rebuilds
+ *   every ten steps, Sec. 4.3); density pass; force pass; v += dt/2 F/m.
  * The rebuild decision is taken on the device (no host synchronization
  * per step). thermo_hist (optional, host or device) receives n_steps rows
  * of (ke, pe, etot, temperature); out (optional, host) the final state's
@@ -209,7 +226,8 @@ MD_API int md_get_forces(md_ctx* ctx, double* f, double* e_atom, double* rho, md
  * (faster for small systems; same results). */
 MD_API int md_step(md_ctx* ctx, int n_steps, md_thermo* out, double* thermo_hist, int use_graph, md_stream stream);
 
-/* The current md_thermo (host). Synchronizes the stream. */
+/* The current md_thermo (host): kinetic energy, E_T of Eq. (2) and the
+ * temperature of Sec. 2. Synchronizes the stream. */
 MD_API int md_get_thermo(md_ctx* ctx, md_thermo* out, md_stream stream);
 
 /* ---------------------------------------------------------------- batches */
@@ -222,10 +240,14 @@ MD_API int md_get_thermo(md_ctx* ctx, md_thermo* out, md_stream stream);
 MD_API int md_batch_create(const md_config* cfg, const md_potential* pot, int n_boxes, const int64_t* atom_offsets,
                     const double* box_lengths, md_batch** out);
 
+/* Frees a batch and its device arrays (no counterpart in the paper, as
+ * md_destroy). MD_ERR_ARG for a NULL handle. */
 MD_API int md_batch_destroy(md_batch* b);
 
 /* As md_set_state, md_get_state and md_compute_forces, over all boxes back
- * to back. e_box [n_boxes] (optional, host or device) gets each box's E_T. */
+ * to back (the combined boxes of Sec. 4.4; each box keeps its own periodic
+ * images). e_box [n_boxes] (optional, host or device) gets each box's E_T
+ * of Eq. (2). */
 MD_API int md_batch_set_state(md_batch* b, const double* x, const double* v, md_stream stream);
 MD_API int md_batch_get_state(md_batch* b, double* x, double* v, md_stream stream);
 MD_API int md_batch_compute_forces(md_batch* b, const double* x, double* f, double* e_box, md_stream stream);
@@ -240,12 +262,17 @@ enum md_schedule {
     MD_SCHED_TILE = 2  /* one launch per phase over the atoms of all boxes */
 };
 
-/* Advances every box by n_steps velocity-Verlet steps (as md_step).
+/* Advances every box by n_steps steps of Sec. 3.3 (as md_step): the
+ * multiple-box-in-one-run scheme of Sec. 4.4 (Table 1), all boxes in one
+ * run, with cells numbered box after box and neighbour cells only inside
+ * their own box. The state comes from md_batch_set_state and stays on the
+ * device between calls (there is no x, v argument).
  * thermo_box [n_boxes][4] (optional, host or device) gets each box's final
  * (ke, pe, etot, temperature). */
 MD_API int md_batch_step(md_batch* b, int n_steps, int schedule, int use_graph, double* thermo_box, md_stream stream);
 
-/* The schedule the autotuner picked for this batch (MD_SCHED_TILE or
+/* The schedule (no counterpart in the paper, which has one: the tile
+ * form of Sec. 4.4) the autotuner picked for this batch (MD_SCHED_TILE or
  * MD_SCHED_BOX; 0 before the first MD_SCHED_AUTO call that ran >= 8 steps)
  * and the per-step times it measured, ms. Any output may be NULL. */
 MD_API int md_batch_schedule(const md_batch* b, int* choice, double* ms_tile, double* ms_box);
@@ -254,9 +281,10 @@ MD_API int md_batch_schedule(const md_batch* b, int* choice, double* ms_tile, do
  * thermo_box [n_boxes][4] (host or device); pe is E_T of Eq. (2) per box. */
 MD_API int md_batch_thermo(md_batch* b, double* thermo_box, md_stream stream);
 
-/* Replaces the potential's parameters (same kind and knot counts) and
- * re-evaluates forces at the current positions (no list rebuild; the cutoff
- * may not grow). */
+/* Replaces the parameters of the potential of Eq. (1) (Sec. 2; same kind
+ * and knot counts) and re-evaluates forces at the current positions (no
+ * list rebuild; the cutoff may not grow). This is how a fitting loop sets
+ * theta before md_param_grad. */
 MD_API int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream stream);
 
 /* Temperature control of Sec. 2, Eq. (4) (Finnis et al.): every atom feels
@@ -285,7 +313,8 @@ MD_API int md_set_thermostat(md_batch* b, double T_e, double tau_T);
  * handle; MD_ERR_UNSUPPORTED for a mixed-precision handle. */
 MD_API int md_set_newton3(md_batch* b, int on);
 
-/* Species of every atom, types [n] in caller order (host or device), each
+/* Species of every atom (the type array of Sec. 3.1; Eq. (1)-(3) with
+ * type-dependent V, rho and F, Sec. 2), types [n] in caller order (host or device), each
  * in [0, n_types) of the potential; all atoms are species 0 until set.
  * Applies to the current state at once (forces are re-evaluated) and to
  * later state loads. Several species run the tile schedule; their
@@ -316,7 +345,8 @@ MD_API int md_pressure(md_batch* b, double* p_box, md_stream stream);
  * tau_p > 0. */
 MD_API int md_set_barostat(md_batch* b, double P0, double tau_p, double beta);
 
-/* Current box lengths [n_boxes][3] (A) into a host or device array. */
+/* Current box lengths [n_boxes][3] (A), as scaled by the coupling of
+ * Eq. (5), into a host or device array. */
 MD_API int md_get_box(md_batch* b, double* lengths, md_stream stream);
 
 /* Gradient of a scalar loss L with respect to the potential parameters
@@ -330,7 +360,8 @@ MD_API int md_get_box(md_batch* b, double* lengths, md_stream stream);
  * paper. MD_ERR_UNSUPPORTED for Sutton-Chen. */
 MD_API int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* grad, md_stream stream);
 
-/* Number of potential parameters (5 for RGL/SC; for a spline the knot
+/* Number of potential parameters of md_param_grad (no counterpart in the
+ * paper; 5 for RGL/SC; for a spline the knot
  * count, P (n_phi + n_f) + T n_F with T species and P = T (T + 1) / 2). */
 MD_API int md_num_params(const md_batch* b);
 
@@ -350,21 +381,26 @@ enum md_phase {
 
 /* Kernel launches issued by a handle since md_profile_start, and (when
  * timing is on) device time per phase from CUDA events recorded around each
- * phase on the caller's stream. */
+ * phase on the caller's stream. The phases are those of a step of Sec. 3.3
+ * (Fig. 4); the paper times the list build and the two force kernels
+ * separately in Sec. 4.1-4.2. */
 typedef struct md_profile {
     int64_t launches;                 /* kernels launched (graph replays included) */
     double ms[MD_PHASE_COUNT];        /* summed event time per phase, ms */
     int64_t timed[MD_PHASE_COUNT];    /* timed launches per phase */
 } md_profile;
 
-/* Resets the counters. timing != 0 records events around every phase (and
- * disables CUDA-graph replay while on); timing == 0 only counts launches. */
+/* Resets the counters (phases of Sec. 3.3, as md_profile). timing != 0
+ * records events around every phase (and disables CUDA-graph replay while
+ * on); timing == 0 only counts launches. */
 MD_API int md_profile_start(md_batch* h, int timing);
 
-/* Reads the counters (synchronizes the device). */
+/* Reads the counters of md_profile_start (phases of Sec. 3.3;
+ * synchronizes the device). */
 MD_API int md_profile_read(md_batch* h, md_profile* out);
 
-/* Diagnostics: evaluates the library's float64 elementary functions on n
+/* Diagnostics (no counterpart in the paper, whose pair functions come from
+ * lookup tables, Sec. 3.3): evaluates the library's float64 elementary functions on n
  * values x [n] (device) into out [n] (device): fn 0 = table-driven e^x
  * (arguments |x| < 700), 1 = CUDA exp(x), 2 = 1/sqrt(x) by the library's
  * float32 estimate plus one third-order Newton step (x > 0), 3 = CUDA
@@ -374,7 +410,8 @@ MD_API int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double*
 
 /* ---------------------------------------------------------------- allocation-free variant */
 
-/* Largest atom count md_forces_noalloc accepts. */
+/* Largest atom count md_forces_noalloc accepts (no counterpart in the
+ * paper). */
 #define MD_NOALLOC_MAX_ATOMS 16384
 
 /* Forces and energies of one small periodic box without allocating any
@@ -384,12 +421,16 @@ MD_API int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double*
  * that must not enter the driver's allocator (it can synchronize the device
  * and take unbounded time).
  * The caller passes x [n][3] (device), f [n][3] (device) and, optionally,
- * e_atom [n] and e_total [1] (device; NULL skips them); box [3] is a host
- * array; pot must be RGL or Sutton-Chen (MD_ERR_UNSUPPORTED otherwise).
- * Results are those of md_compute_forces (Eq. 1-3) computed by an all-pairs
- * minimum-image loop, O(n^2) per call, no cells and no list.
- * Working memory is one file-scope device array of 2 * MD_NOALLOC_MAX_ATOMS
- * doubles (256 KiB) that every GPU loading the library holds until the
+ * e_atom [n] and e_total [1] (device; NULL skips them), all memory of the
+ * current device (or managed memory); box [3] is a host array; pot must be
+ * RGL or Sutton-Chen (MD_ERR_UNSUPPORTED otherwise). With n_atoms == 0, x
+ * and f may be NULL and *e_total (when given) is set to 0 on the stream.
+ * Results are the forces and energies md_compute_forces gives for the same
+ * positions, computed by an all-pairs minimum-image loop, O(n^2) per call,
+ * no cells and no list. Positions may lie outside the box (any number of
+ * box lengths away); the minimum image is taken by rounding.
+ * Working memory is one file-scope device array of 5 * MD_NOALLOC_MAX_ATOMS
+ * doubles (640 KiB) that every GPU loading the library holds until the
  * process exits. The first call on a device looks up that array's device
  * address with the device current; make that first call before any stream
  * capture. All calls share the array and each call overwrites the entries
@@ -397,7 +438,8 @@ MD_API int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double*
  * calls that overlap on the GPU (for example on two streams) race on it and
  * must be serialized by the caller.
  * Errors: MD_ERR_ARG (n_atoms > MD_NOALLOC_MAX_ATOMS or < 0, a box length not
- * above 2 r_cut, non-device x/f/e_atom/e_total), MD_ERR_UNSUPPORTED,
+ * above 2 r_cut, x/f/e_atom/e_total not memory of the current device),
+ * MD_ERR_UNSUPPORTED,
  * MD_ERR_CUDA. Asynchronous: outputs are valid once `stream` reaches the
  * call. */
 MD_API int md_forces_noalloc(const md_potential* pot, const double* box, int64_t n_atoms, const double* x,
@@ -405,9 +447,11 @@ MD_API int md_forces_noalloc(const md_potential* pot, const double* box, int64_t
 
 /* ---------------------------------------------------------------- errors */
 
+/* Name of a status code (no counterpart in the paper). */
 MD_API const char* md_status_string(int status);
 /* Text of the last failure on the handle (or of the last failed create
- * when h is NULL). Valid until the next call on the handle. */
+ * when h is NULL). Valid until the next call on the handle. No counterpart
+ * in the paper. */
 MD_API const char* md_last_error(const md_batch* h);
 
 #ifdef __cplusplus

@@ -1,7 +1,6 @@
-// Cell binning and sorting (Sec. 3.2): the paper computes each atom's cell
-// on the GPU (its steps G1-G3) and builds linked lists and the sorted order
-// on the host (H1-H22). Here the whole partition runs on the device as a
-// counting sort:
+// Cell binning and sorting (Sec. 3.2, Fig. 2): the paper computes each
+// atom's cell on the GPU and builds linked lists and the sorted order on the
+// host. Here the whole partition runs on the device as a counting sort:
 //   k_bin          cell of every atom, atomic count per cell
 //   k_scan_*       exclusive scan of the counts -> first atom of each cell
 //   k_scatter      atomic slot inside the cell

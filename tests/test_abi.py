@@ -30,6 +30,31 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+CITATION = re.compile(r"(Sec\.|Eq\.|Eqs\.|Fig\.|Table\s+\d)|no counterpart in\s+(the\s+)?paper|paper has no counterpart", re.S | re.I)
+
+
+def declaration_comments():
+    """(name, comment) for every MD_API declaration: the comment is the last
+    block comment that starts a line before it (one comment may introduce
+    several declarations that follow it)."""
+    text = (ROOT / "include" / "md.h").read_text()
+    out = []
+    last_comment = ""
+    for m in re.finditer(r"^/\*.*?\*/|^MD_API\s+[\w\s\*]+?\b(md_\w+)\s*\(", text, flags=re.M | re.S):
+        if m.group(0).startswith("/*"):
+            last_comment = re.sub(r"\s*\n\s*\*(?!/)\s?", " ", m.group(0))
+        else:
+            out.append((m.group(1), last_comment))
+    return out
+
+
+def test_every_declaration_cites_its_passage_or_says_it_has_none():
+    decls = declaration_comments()
+    assert {n for n, _ in decls} == set(declared_symbols())
+    missing = [n for n, c in decls if not CITATION.search(c)]
+    assert not missing, f"declarations without a passage or 'no counterpart in the paper': {missing}"
+
+
 def test_library_exports_every_declared_symbol(lib):
     from paper_1212_6332_gb300 import md
     names = declared_symbols()
