@@ -8,8 +8,10 @@
 // memory is a fixed file-scope device array (g_noalloc_scratch) that every
 // GPU loading this library holds until the process exits.
 //
-// The evaluation is the same physics as md_compute_forces (Eq. 1-3: a
+// The evaluation gives the forces and energies md_compute_forces gives (a
 // density pass, F'(rho), a force pass) without cells or a neighbour list:
+// positions are first wrapped into the box by the same rule (so unwrapped
+// coordinates, any number of box lengths away, give the same result), then
 // every thread loops over all atoms with the minimum-image convention,
 // which is the right trade for the few thousand atoms this entry point is
 // limited to.
@@ -22,8 +24,11 @@
 
 namespace {
 
-// Scratch: F'(rho_i) for the first n atoms, then E_i for the first n atoms.
-__device__ __align__(256) double g_noalloc_scratch[2 * MD_NOALLOC_MAX_ATOMS];
+// Scratch (5 * MD_NOALLOC_MAX_ATOMS doubles, 640 KiB): F'(rho_i) at [0, n),
+// E_i at [MAX, MAX + n), wrapped positions [n][3] at [2 MAX, 2 MAX + 3n).
+constexpr int kScrE = MD_NOALLOC_MAX_ATOMS;
+constexpr int kScrX = 2 * MD_NOALLOC_MAX_ATOMS;
+__device__ __align__(256) double g_noalloc_scratch[5 * MD_NOALLOC_MAX_ATOMS];
 
 constexpr int kNT = 128;
 constexpr int kMaxDevices = 64;
@@ -38,6 +43,17 @@ struct PotS {
     double eps, a, n, m, F_scale;        // SC
 };
 
+// x - L floor(x/L) with each operation rounded, folded into [0, L): the
+// wrap md_compute_forces applies to its input positions.
+__device__ __forceinline__ double na_wrap(double x, double L) {
+    double k = floor(__ddiv_rn(x, L));
+    double y = __dsub_rn(x, __dmul_rn(L, k));
+    if (y < 0.0) y = __dadd_rn(y, L);
+    if (y >= L) y = __dsub_rn(y, L);
+    return y;
+}
+
+// minimum image of a separation of two wrapped coordinates (|d| < L)
 __device__ __forceinline__ double mi(double d, double L) {
     double h = 0.5 * L;
     if (d > h) return d - L;
@@ -70,10 +86,21 @@ __device__ __forceinline__ void pair_fn(const PotS& P, double r, double& V, doub
     }
 }
 
-__global__ void __launch_bounds__(kNT) k_na_density(int n, const double* __restrict__ x, double Lx, double Ly,
-                                                    double Lz, PotS P, double* __restrict__ scratch) {
+__global__ void __launch_bounds__(kNT) k_na_wrap(int n, const double* __restrict__ x_in, double Lx, double Ly,
+                                                 double Lz, double* __restrict__ scratch) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    double* x = scratch + kScrX;
+    x[3 * i] = na_wrap(x_in[3 * i], Lx);
+    x[3 * i + 1] = na_wrap(x_in[3 * i + 1], Ly);
+    x[3 * i + 2] = na_wrap(x_in[3 * i + 2], Lz);
+}
+
+__global__ void __launch_bounds__(kNT) k_na_density(int n, double Lx, double Ly, double Lz, PotS P,
+                                                    double* __restrict__ scratch) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* x = scratch + kScrX;
     double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
     double rho = 0.0, ep = 0.0;
     for (int j = 0; j < n; ++j) {
@@ -93,14 +120,15 @@ __global__ void __launch_bounds__(kNT) k_na_density(int n, const double* __restr
         Fp = -0.5 * P.F_scale / s;
     }
     scratch[i] = Fp;
-    scratch[MD_NOALLOC_MAX_ATOMS + i] = F + 0.5 * ep;
+    scratch[kScrE + i] = F + 0.5 * ep;
 }
 
-__global__ void __launch_bounds__(kNT) k_na_force(int n, const double* __restrict__ x, double Lx, double Ly,
-                                                  double Lz, PotS P, const double* __restrict__ scratch,
-                                                  double* __restrict__ f_out, double* __restrict__ e_atom) {
+__global__ void __launch_bounds__(kNT) k_na_force(int n, double Lx, double Ly, double Lz, PotS P,
+                                                  const double* __restrict__ scratch, double* __restrict__ f_out,
+                                                  double* __restrict__ e_atom) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double* x = scratch + kScrX;
     double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
     double Fpi = scratch[i];
     double fx = 0.0, fy = 0.0, fz = 0.0;
@@ -120,14 +148,14 @@ __global__ void __launch_bounds__(kNT) k_na_force(int n, const double* __restric
     f_out[3 * i] = fx;
     f_out[3 * i + 1] = fy;
     f_out[3 * i + 2] = fz;
-    if (e_atom) e_atom[i] = scratch[MD_NOALLOC_MAX_ATOMS + i];
+    if (e_atom) e_atom[i] = scratch[kScrE + i];
 }
 
 // One block sums E_i in a fixed order (deterministic).
 __global__ void __launch_bounds__(1024) k_na_total(int n, const double* __restrict__ scratch, double* e_total) {
     __shared__ double sh[32];
     double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += 1024) s += scratch[MD_NOALLOC_MAX_ATOMS + i];
+    for (int i = threadIdx.x; i < n; i += 1024) s += scratch[kScrE + i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -138,13 +166,15 @@ __global__ void __launch_bounds__(1024) k_na_total(int n, const double* __restri
     }
 }
 
-bool dev_ptr(const void* p) {
+// Device memory of device `dev` (the current one), or managed memory.
+bool dev_ptr(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -167,14 +197,25 @@ int md_forces_noalloc(const md_potential* pot, const double* box, int64_t n_atom
     for (int a = 0; a < 3; ++a)
         if (!(box[a] > 0.0) || !std::isfinite(box[a]) || !(pot->r_cut < 0.5 * box[a]))
             return MD_ERR_ARG;  // box lengths must exceed twice r_cut (minimum image)
-    if (n_atoms == 0) return MD_OK;
-    if (!x || !f || !dev_ptr(x) || !dev_ptr(f) || (e_atom && !dev_ptr(e_atom)) || (e_total && !dev_ptr(e_total)))
-        return MD_ERR_ARG;  // x, f (and e_atom, e_total when given) must be device pointers
-
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return MD_ERR_CUDA;  // cudaGetDevice failed
+    }
+    // x and f may be NULL only when there are no atoms; every pointer given
+    // must be device (or managed) memory of the current device
+    if (n_atoms > 0 && (!x || !f)) return MD_ERR_ARG;  // x and f are required
+    if ((x && !dev_ptr(x, dev)) || (f && !dev_ptr(f, dev)) || (e_atom && !dev_ptr(e_atom, dev)) ||
+        (e_total && !dev_ptr(e_total, dev)))
+        return MD_ERR_ARG;  // x, f, e_atom, e_total must be memory of the current device
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_atoms == 0) {
+        // no atoms: E_T = 0 (a memset enqueued on the stream, no allocation)
+        if (e_total && cudaMemsetAsync(e_total, 0, sizeof(double), s) != cudaSuccess) {
+            cudaGetLastError();
+            return MD_ERR_CUDA;  // the memset could not be enqueued
+        }
+        return MD_OK;
     }
     double* scratch = nullptr;
     {
@@ -219,9 +260,9 @@ int md_forces_noalloc(const md_potential* pot, const double* box, int64_t n_atom
     }
     int n = (int)n_atoms;
     int nb = (n + kNT - 1) / kNT;
-    cudaStream_t s = (cudaStream_t)stream;
-    k_na_density<<<nb, kNT, 0, s>>>(n, x, box[0], box[1], box[2], P, scratch);
-    k_na_force<<<nb, kNT, 0, s>>>(n, x, box[0], box[1], box[2], P, scratch, f, e_atom);
+    k_na_wrap<<<nb, kNT, 0, s>>>(n, x, box[0], box[1], box[2], scratch);
+    k_na_density<<<nb, kNT, 0, s>>>(n, box[0], box[1], box[2], P, scratch);
+    k_na_force<<<nb, kNT, 0, s>>>(n, box[0], box[1], box[2], P, scratch, f, e_atom);
     if (e_total) k_na_total<<<1, 1024, 0, s>>>(n, scratch, e_total);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return MD_ERR_CUDA;  // a launch failed

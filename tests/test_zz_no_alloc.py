@@ -3,13 +3,15 @@
 that must not enter the driver's allocator). It keeps its working memory in
 a fixed device array inside the library; here it is called through the C ABI
 twice in a row, on two different boxes, and each result is compared with
-md_compute_forces (the regular entry point) at the tolerance of the float64
-parity tests. This file is collected last on purpose."""
+md_compute_forces (the regular entry point) and with the CPU oracle at the
+tolerance of the float64 parity tests. This file is collected last on
+purpose."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1212_6332_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -28,12 +30,17 @@ def regular(spec, bx):
     return res
 
 
-def noalloc(spec, bx):
+def from_oracle(spec, bx):
+    r = O.forces(O.Potential(spec), bx.x, bx.box)
+    return dict(f=r["f"], e_atom=r["e_atom"], energy=np.array([r["E"]]))
+
+
+def noalloc(spec, bx, x_in=None):
     """Direct C-ABI call with caller-owned device buffers."""
     import torch
     from paper_1212_6332_gb300 import md
     lib = md.load()
-    x = torch.tensor(bx.x, device="cuda")
+    x = torch.tensor(bx.x if x_in is None else x_in, device="cuda")
     f = torch.full((bx.n, 3), np.nan, dtype=torch.float64, device="cuda")
     e = torch.full((bx.n,), np.nan, dtype=torch.float64, device="cuda")
     et = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
@@ -62,8 +69,51 @@ def test_noalloc_matches_compute_forces_on_two_calls_in_a_row():
     got2 = noalloc(I.SC_CU, second)
     check(got1, regular(I.RGL_CU, first))
     check(got2, regular(I.SC_CU, second))
+    check(got1, from_oracle(I.RGL_CU, first))
+    check(got2, from_oracle(I.SC_CU, second))
     # and back to the first box: nothing left over from the larger call
     check(noalloc(I.RGL_CU, first), regular(I.RGL_CU, first))
+
+
+def test_noalloc_takes_unwrapped_positions():
+    """Atoms shifted by whole box lengths (+-2L, as an MD loop that never
+    wraps would leave them) give the forces of the wrapped box."""
+    bx = I.perturbed_fcc(5, I.A_CU, 600.0, I.MASS_CU, seed=43)
+    k = np.zeros_like(bx.x)
+    k[0::3, 0], k[1::3, 1], k[2::3, 2] = 2.0, -2.0, 3.0
+    k[5::7] *= -1.0
+    got = noalloc(I.RGL_CU, bx, x_in=bx.x + k * bx.box)
+    check(got, regular(I.RGL_CU, bx))
+    check(got, from_oracle(I.RGL_CU, bx))
+
+
+def test_noalloc_with_no_atoms_sets_the_energy_to_zero():
+    import torch
+    from paper_1212_6332_gb300 import md
+    lib = md.load()
+    et = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+    pot, keep = md.potential_struct(I.RGL_CU)
+    box = np.full(3, 30.0)
+    rc = lib.md_forces_noalloc(ctypes.byref(pot), ctypes.c_void_p(box.ctypes.data), 0, None, None, None,
+                               ctypes.c_void_p(et.data_ptr()), None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert et.item() == 0.0
+
+
+def test_noalloc_rejects_host_memory():
+    """Pointer checks run on the host before anything is enqueued."""
+    import torch
+    from paper_1212_6332_gb300 import md
+    lib = md.load()
+    bx = I.perturbed_fcc(3, I.A_CU, 300.0, I.MASS_CU, seed=44)
+    x_host = np.ascontiguousarray(bx.x)
+    f = torch.zeros((bx.n, 3), dtype=torch.float64, device="cuda")
+    pot, keep = md.potential_struct(I.RGL_CU)
+    box = np.ascontiguousarray(bx.box) * 2.0
+    rc = lib.md_forces_noalloc(ctypes.byref(pot), ctypes.c_void_p(box.ctypes.data), bx.n,
+                               ctypes.c_void_p(x_host.ctypes.data), ctypes.c_void_p(f.data_ptr()), None, None, None)
+    assert rc == 1  # MD_ERR_ARG
 
 
 def test_noalloc_rejects_more_atoms_than_its_scratch():
