@@ -35,7 +35,11 @@ def build(force: bool = False) -> pathlib.Path:
     tmp = _SO.with_suffix(f".{os.getpid()}.tmp")
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            str(src), "-o", str(tmp), "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP serves only the all-cores timing (orc_set_threads > 1); without
+    # it the library builds serial and reports one thread
+    r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True)
+    if r.returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
 
@@ -75,6 +79,13 @@ def _load():
     lib.orc_param_deriv.restype = dbl
     lib.orc_param_deriv.argtypes = [vp, i32, i32, _D, _D, i64, _I, _I, _D]
     lib.orc_param_grad.argtypes = [vp, i32, i32, _D, _D, i64, _I, _I, _D, dbl, _D]
+    lib.orc_set_threads.restype = i32
+    lib.orc_set_threads.argtypes = [i32]
+    lib.orc_max_threads.restype = i32
+    lib.orc_pairs_cells_par.restype = i64
+    lib.orc_pairs_cells_par.argtypes = [i32, _D, _D, dbl, _I, _I, i64, i32]
+    lib.orc_forces_pairs_par.restype = dbl
+    lib.orc_forces_pairs_par.argtypes = [vp, i32, _D, _D, i64, _I, _I, _D, _D, _D, _D, i32]
     _lib = lib
     return lib
 
@@ -185,12 +196,29 @@ def wrap(x, box) -> np.ndarray:
     return x
 
 
-def pairs(x, box, rl: float, method: str = "cells") -> tuple[np.ndarray, np.ndarray]:
-    """Half list (i < j) of pairs with minimum-image r^2 < rl^2."""
+def set_threads(t: int) -> int:
+    """Threads for md_run's pair list and force sums (1 = the plain serial
+    functions, the default); returns the count in effect (1 when the
+    library was built without OpenMP)."""
+    return int(_load().orc_set_threads(int(t)))
+
+
+def max_threads() -> int:
+    """Threads OpenMP would use by default (the host's cores), 1 without OpenMP."""
+    return int(_load().orc_max_threads())
+
+
+def pairs(x, box, rl: float, method: str = "cells", threads: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Half list (i < j) of pairs with minimum-image r^2 < rl^2. threads > 0
+    with method "cells" uses the all-cores form (the same list)."""
     lib = _load()
     x, box = _f64(x), _f64(box)
     n = x.shape[0]
-    fn = lib.orc_pairs_cells if method == "cells" else lib.orc_pairs_brute
+    if method == "cells" and threads > 0:
+        def fn(*a):
+            return lib.orc_pairs_cells_par(*a, int(threads))
+    else:
+        fn = lib.orc_pairs_cells if method == "cells" else lib.orc_pairs_brute
     cap = max(64, n * 80)
     while True:
         pi = np.empty(cap, dtype=np.int32)
@@ -201,10 +229,11 @@ def pairs(x, box, rl: float, method: str = "cells") -> tuple[np.ndarray, np.ndar
         cap = int(np_)
 
 
-def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs", types=None) -> dict:
+def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs", types=None, threads: int = 0) -> dict:
     """Energies and forces of Eq. (1)-(3). method "pairs" uses the half list
     within r_cut + skin and Newton's third law; "brute" the O(N^2) double
-    sums. types: per-atom species for an alloy potential."""
+    sums. types: per-atom species for an alloy potential. threads > 0 runs
+    the half-list sums in their all-cores form."""
     lib = _load()
     pot.use_types(types)
     x, box = _f64(x), _f64(box)
@@ -216,10 +245,14 @@ def forces(pot: Potential, x, box, skin: float = 0.0, method: str = "pairs", typ
         E = lib.orc_forces_brute(pot._h, n, _dp(x), _dp(box), _dp(rho), _dp(e), _dp(f))
         Fp = pot.embed(rho)[1] if n else np.zeros(0)
         return dict(E=E, rho=rho, Fp=Fp, e_atom=e, f=f)
-    pi, pj = pairs(x, box, pot.r_cut + skin)
+    pi, pj = pairs(x, box, pot.r_cut + skin, threads=threads)
     Fp = np.zeros(n)
-    E = lib.orc_forces_pairs(pot._h, n, _dp(x), _dp(box), pi.size, _ip(pi), _ip(pj), _dp(rho), _dp(Fp),
-                             _dp(e), _dp(f))
+    if threads > 0:
+        E = lib.orc_forces_pairs_par(pot._h, n, _dp(x), _dp(box), pi.size, _ip(pi), _ip(pj), _dp(rho), _dp(Fp),
+                                     _dp(e), _dp(f), int(threads))
+    else:
+        E = lib.orc_forces_pairs(pot._h, n, _dp(x), _dp(box), pi.size, _ip(pi), _ip(pj), _dp(rho), _dp(Fp),
+                                 _dp(e), _dp(f))
     return dict(E=E, rho=rho, Fp=Fp, e_atom=e, f=f)
 
 

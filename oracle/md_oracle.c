@@ -28,6 +28,12 @@
  * orc_forces_pairs() takes a half list of pairs i<j and applies Newton's third
  * law. The two are compared against each other by the tests.
  *
+ * For timing the CPU baseline on all host cores, orc_pairs_cells_par() and
+ * orc_forces_pairs_par() split the same loops over OpenMP threads with
+ * thread-private sums added in a fixed order (one thread reproduces the
+ * serial functions bit for bit); orc_md_run uses them when orc_set_threads()
+ * asked for more than one thread. Every pin runs the serial functions.
+ *
  * The potential forms (the paper leaves them to the literature):
  *   RGL (Cleri-Rosato) : V(r) = 2A exp(-p(r/r0-1)) S(r),
  *                        rho(r) = xi^2 exp(-2q(r/r0-1)) S(r), F = -sqrt(rho)
@@ -55,6 +61,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_RGL 0
 #define ORC_SC 1
@@ -563,6 +572,222 @@ double orc_forces_pairs(const orc_pot* P, int n, const double* x, const double* 
     return E;
 }
 
+/* ------------------------------------------------------------------ */
+/* all-cores variants (CPU-baseline timing)                            */
+/* ------------------------------------------------------------------ */
+
+/* Threads used by orc_md_run for its pair list and force sums; 1 (the
+ * default) runs the plain serial functions above. */
+static int orc_threads = 1;
+
+int orc_set_threads(int t) {
+#ifdef _OPENMP
+    orc_threads = t < 1 ? 1 : t;
+#else
+    (void)t;
+    orc_threads = 1;
+#endif
+    return orc_threads;
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int thread_id(void) {
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+typedef struct {
+    int* a;
+    int* b;
+    long n, cap;
+} pairvec;
+
+static void pv_push(pairvec* v, int i, int j) {
+    if (v->n == v->cap) {
+        v->cap = v->cap ? 2 * v->cap : 4096;
+        v->a = (int*)realloc(v->a, sizeof(int) * (size_t)v->cap);
+        v->b = (int*)realloc(v->b, sizeof(int) * (size_t)v->cap);
+    }
+    v->a[v->n] = i;
+    v->b[v->n] = j;
+    ++v->n;
+}
+
+/* orc_pairs_cells with its loop over cells cut into `threads` contiguous
+ * slabs of the first cell index, each thread appending to its own buffer;
+ * the buffers are joined in slab order, so the list (pairs and their order)
+ * is that of orc_pairs_cells for any thread count. */
+long orc_pairs_cells_par(int n, const double* x, const double* box, double rl, int* pi, int* pj, long cap,
+                         int threads) {
+    int nc[3];
+    for (int a = 0; a < 3; ++a) nc[a] = (int)floor(box[a] / (rl * (1.0 + 1e-12)));
+    if (nc[0] < 3 || nc[1] < 3 || nc[2] < 3) return orc_pairs_brute(n, x, box, rl, pi, pj, cap);
+    int T = threads < 1 ? 1 : threads;
+    if (T > nc[0]) T = nc[0];
+    long ncell = (long)nc[0] * nc[1] * nc[2];
+    int* head = (int*)malloc(sizeof(int) * (size_t)ncell);
+    int* next = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (long c = 0; c < ncell; ++c) head[c] = -1;
+    for (int i = 0; i < n; ++i) {
+        int ci[3];
+        for (int a = 0; a < 3; ++a) {
+            int c = (int)floor(x[3 * i + a] / (box[a] / nc[a]));
+            if (c < 0) c = 0;
+            if (c >= nc[a]) c = nc[a] - 1;
+            ci[a] = c;
+        }
+        long c = ((long)ci[0] * nc[1] + ci[1]) * nc[2] + ci[2];
+        next[i] = head[c];
+        head[c] = i;
+    }
+    double rl2 = rl * rl;
+    pairvec* buf = (pairvec*)calloc((size_t)T, sizeof(pairvec));
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+#endif
+    for (int t = 0; t < T; ++t) {
+        int c0 = (int)((long)nc[0] * t / T), c1 = (int)((long)nc[0] * (t + 1) / T);
+        double d[3];
+        for (int cx = c0; cx < c1; ++cx)
+            for (int cy = 0; cy < nc[1]; ++cy)
+                for (int cz = 0; cz < nc[2]; ++cz) {
+                    long c = ((long)cx * nc[1] + cy) * nc[2] + cz;
+                    for (int ox = -1; ox <= 1; ++ox)
+                        for (int oy = -1; oy <= 1; ++oy)
+                            for (int oz = -1; oz <= 1; ++oz) {
+                                int qx = (cx + ox + nc[0]) % nc[0];
+                                int qy = (cy + oy + nc[1]) % nc[1];
+                                int qz = (cz + oz + nc[2]) % nc[2];
+                                long q = ((long)qx * nc[1] + qy) * nc[2] + qz;
+                                for (int i = head[c]; i >= 0; i = next[i])
+                                    for (int j = head[q]; j >= 0; j = next[j]) {
+                                        if (i >= j) continue;
+                                        if (sep(x, i, j, box, d) < rl2) pv_push(&buf[t], i, j);
+                                    }
+                            }
+                }
+    }
+    long np = 0;
+    for (int t = 0; t < T; ++t) {
+        for (long k = 0; k < buf[t].n; ++k, ++np)
+            if (np < cap) {
+                pi[np] = buf[t].a[k];
+                pj[np] = buf[t].b[k];
+            }
+        free(buf[t].a);
+        free(buf[t].b);
+    }
+    free(buf);
+    free(head);
+    free(next);
+    return np;
+}
+
+/* orc_forces_pairs over `threads` threads: the pair list is cut into
+ * contiguous chunks, each thread sums its chunk into its own rho, E_i and
+ * force arrays (thread 0's E_i start from F(rho_i), the others from 0), and
+ * the partial arrays are added in thread order. One thread gives the
+ * serial function's result bit for bit; more threads reorder the sums. */
+double orc_forces_pairs_par(const orc_pot* P, int n, const double* x, const double* box, long np, const int* pi,
+                            const int* pj, double* rho_out, double* Fp_out, double* e_out, double* f_out,
+                            int threads) {
+    int T = threads < 1 ? 1 : threads;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double rc2 = P->r_cut * P->r_cut;
+    double* rho_t = (double*)calloc(nn * (size_t)T, sizeof(double));
+    double* e_t = (double*)calloc(nn * (size_t)T, sizeof(double));
+    double* f_t = (double*)calloc(3 * nn * (size_t)T, sizeof(double));
+    double* rho = (double*)calloc(nn, sizeof(double));
+    double* Fp = (double*)calloc(nn, sizeof(double));
+    double* e = (double*)calloc(nn, sizeof(double));
+    double* f = (double*)calloc(3 * nn, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(T)
+#endif
+    {
+        int t = thread_id();
+        long k0 = np * t / T, k1 = np * (t + 1) / T;
+        int i0 = (int)((long)n * t / T), i1 = (int)((long)n * (t + 1) / T);
+        double d[3], phi, dphi, fr, dfr, F, Fpp;
+        double* rho_p = rho_t + nn * (size_t)t;
+        double* e_p = e_t + nn * (size_t)t;
+        double* f_p = f_t + 3 * nn * (size_t)t;
+        for (long k = k0; k < k1; ++k) {
+            int i = pi[k], j = pj[k];
+            double r2 = sep(x, i, j, box, d);
+            if (r2 >= rc2) continue;
+            pair_eval(P, ptype(P, i, j), sqrt(r2), &phi, &dphi, &fr, &dfr);
+            rho_p[i] += fr;
+            rho_p[j] += fr;
+        }
+#ifdef _OPENMP
+#pragma omp barrier
+#endif
+        for (int i = i0; i < i1; ++i) {
+            double r = rho_t[i];
+            for (int u = 1; u < T; ++u) r += rho_t[nn * (size_t)u + i];
+            rho[i] = r;
+            embed_eval(P, atype(P, i), r, &F, &Fp[i], &Fpp);
+            e_t[i] = F; /* thread 0's E_i start from F(rho_i) */
+        }
+#ifdef _OPENMP
+#pragma omp barrier
+#endif
+        for (long k = k0; k < k1; ++k) {
+            int i = pi[k], j = pj[k];
+            double r2 = sep(x, i, j, box, d);
+            if (r2 >= rc2) continue;
+            double r = sqrt(r2);
+            pair_eval(P, ptype(P, i, j), r, &phi, &dphi, &fr, &dfr);
+            e_p[i] += 0.5 * phi;
+            e_p[j] += 0.5 * phi;
+            double s = dphi + (Fp[i] + Fp[j]) * dfr;
+            for (int a = 0; a < 3; ++a) {
+                double c = s * d[a] / r;
+                f_p[3 * i + a] += c;
+                f_p[3 * j + a] -= c;
+            }
+        }
+#ifdef _OPENMP
+#pragma omp barrier
+#endif
+        for (int i = i0; i < i1; ++i) {
+            double ei = e_t[i];
+            for (int u = 1; u < T; ++u) ei += e_t[nn * (size_t)u + i];
+            e[i] = ei;
+            for (int a = 0; a < 3; ++a) {
+                double fa = f_t[3 * i + a];
+                for (int u = 1; u < T; ++u) fa += f_t[3 * nn * (size_t)u + 3 * i + a];
+                f[3 * i + a] = fa;
+            }
+        }
+    }
+    double E = 0.0;
+    for (int i = 0; i < n; ++i) E += e[i];
+    if (rho_out) memcpy(rho_out, rho, sizeof(double) * (size_t)n);
+    if (Fp_out) memcpy(Fp_out, Fp, sizeof(double) * (size_t)n);
+    if (e_out) memcpy(e_out, e, sizeof(double) * (size_t)n);
+    if (f_out) memcpy(f_out, f, sizeof(double) * 3 * (size_t)n);
+    free(rho_t);
+    free(e_t);
+    free(f_t);
+    free(rho);
+    free(Fp);
+    free(e);
+    free(f);
+    return E;
+}
+
 /* Virial of the forces of Eq. (3) for the pressure of Eq. (6). The sum
  * W = sum_i f_i . r_i is written for a periodic box as a sum over pairs: the
  * forces are pairwise, f_ij = -f_ji with f_ij = -(dE_T/dr_ij) (r_i - r_j)/r_ij
@@ -610,7 +835,8 @@ typedef struct {
 
 static void pairs_rebuild(pairbuf* B, int n, const double* x, const double* box, double rl) {
     for (;;) {
-        long np = orc_pairs_cells(n, x, box, rl, B->pi, B->pj, B->cap);
+        long np = orc_threads > 1 ? orc_pairs_cells_par(n, x, box, rl, B->pi, B->pj, B->cap, orc_threads)
+                                  : orc_pairs_cells(n, x, box, rl, B->pi, B->pj, B->cap);
         if (np <= B->cap) {
             B->np = np;
             return;
@@ -619,6 +845,15 @@ static void pairs_rebuild(pairbuf* B, int n, const double* x, const double* box,
         B->pi = (int*)realloc(B->pi, sizeof(int) * (size_t)B->cap);
         B->pj = (int*)realloc(B->pj, sizeof(int) * (size_t)B->cap);
     }
+}
+
+/* forces and E_T of a step: the serial half-list sums, or their threaded
+ * form when orc_set_threads asked for more than one thread */
+static double step_forces(const orc_pot* P, int n, const double* x, const double* box, const pairbuf* B,
+                          double* f) {
+    if (orc_threads > 1)
+        return orc_forces_pairs_par(P, n, x, box, B->np, B->pi, B->pj, NULL, NULL, NULL, f, orc_threads);
+    return orc_forces_pairs(P, n, x, box, B->np, B->pi, B->pj, NULL, NULL, NULL, f);
 }
 
 static double kinetic(int n, const double* v, double mass) {
@@ -693,7 +928,7 @@ long orc_md_run(const orc_pot* P, int n, double* x, double* v, double* box, doub
     orc_wrap(n, x, box);
     pairs_rebuild(&B, n, x, box, rl);
     memcpy(xb, x, sizeof(double) * 3 * (size_t)n);
-    double pe = orc_forces_pairs(P, n, x, box, B.np, B.pi, B.pj, NULL, NULL, NULL, f);
+    double pe = step_forces(P, n, x, box, &B, f);
     long rebuilds = 0;
     if (thermo) {
         double ke = kinetic(n, v, mass);
@@ -724,7 +959,7 @@ long orc_md_run(const orc_pot* P, int n, double* x, double* v, double* box, doub
             memcpy(xb, x, sizeof(double) * 3 * (size_t)n);
             ++rebuilds;
         }
-        pe = orc_forces_pairs(P, n, x, box, B.np, B.pi, B.pj, NULL, NULL, NULL, f);
+        pe = step_forces(P, n, x, box, &B, f);
         for (int k = 0; k < 3 * n; ++k) v[k] += 0.5 * dt * f[k] * acc;
         if (bath) bath_half(n, v, mass, T_e, decay);
         if (thermo) {

@@ -677,3 +677,53 @@ def test_loss_gradient_matches_finite_differences():
         fd = (loss_of(O.Potential(up), configs, targets) - loss_of(O.Potential(dn), configs, targets)) / (2 * h)
         g = grad[offs[key] + idx]
         assert g == pytest.approx(fd, rel=1e-5, abs=1e-9 * max(1.0, abs(grad).max()))
+
+
+# ---------------------------------------------------------------- all-cores form
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_threaded_pair_list_is_the_serial_list(threads):
+    """The all-cores linked-cell list joins per-slab buffers in slab order:
+    the same pairs in the same order as the serial linked-cell list."""
+    bx = I.perturbed_fcc(7, I.A_CU, 600.0, I.MASS_CU, seed=61)
+    a = O.pairs(bx.x, bx.box, 5.3)
+    b = O.pairs(bx.x, bx.box, 5.3, threads=threads)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_threaded_sums_with_one_thread_are_the_serial_sums_bit_for_bit():
+    bx = I.perturbed_fcc(6, I.A_CU, 900.0, I.MASS_CU, seed=62)
+    for spec in (I.RGL_CU, I.SC_CU):
+        if spec is I.SC_CU:
+            bx = I.perturbed_fcc(7, I.A_CU, 900.0, I.MASS_CU, seed=63)
+        pot = O.Potential(spec)
+        a = O.forces(pot, bx.x, bx.box, skin=0.3)
+        b = O.forces(pot, bx.x, bx.box, skin=0.3, threads=1)
+        assert a["E"] == b["E"]
+        for k in ("rho", "Fp", "e_atom", "f"):
+            assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("threads", [2, 5, 8])
+def test_threaded_sums_equal_the_serial_sums_to_rounding(threads):
+    bx = I.perturbed_fcc(6, I.A_CU, 900.0, I.MASS_CU, seed=64)
+    pot = O.Potential(I.RGL_CU)
+    a = O.forces(pot, bx.x, bx.box, skin=0.3)
+    b = O.forces(pot, bx.x, bx.box, skin=0.3, threads=threads)
+    assert abs(a["E"] - b["E"]) <= 1e-13 * abs(a["E"])
+    assert np.abs(a["rho"] - b["rho"]).max() <= 1e-13 * np.abs(a["rho"]).max()
+    assert np.abs(a["f"] - b["f"]).max() <= 1e-12 * np.abs(a["f"]).max()
+
+
+def test_threaded_trajectory_follows_the_serial_one():
+    bx = I.perturbed_fcc(5, I.A_CU, 600.0, I.MASS_CU, seed=65)
+    pot = O.Potential(I.RGL_CU)
+    ref = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 40)
+    try:
+        O.set_threads(4)
+        par = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, 1.0, 0.3, 40)
+    finally:
+        O.set_threads(1)
+    assert par["n_rebuild"] == ref["n_rebuild"]
+    assert np.abs(par["x"] - ref["x"]).max() < 1e-10
+    assert np.allclose(par["thermo"], ref["thermo"], rtol=1e-11, atol=1e-11)
