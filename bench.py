@@ -8,11 +8,17 @@ step is one velocity-Verlet MD step of the whole box through the C ABI
 (kick-drift, device-decided list rebuild, density pass, force pass,
 second half-kick); inputs are resident in HBM when the timed region starts.
 
+The timed steps are the ones a user runs: md_step with CUDA-graph replay.
+Per-kernel times come from a further, untimed stretch of the same run with
+per-phase CUDA events (which turn graph replay off). The roofline
+denominators are measured in the same process: float64 and float32 FMA
+rates by the library's probe kernel, HBM bandwidth from MEASURED_PEAKS.json.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs an independent replica of the box on its own
 GPU (the single-box path does not shard); value = all ranks' atom-steps over
-the slowest rank's time. --impl reference times the CPU oracle on a bounded
-sample of the same workload on the host cores.
+the slowest rank's time. --impl reference times the CPU oracle on the same
+4M-atom box on all host cores (OpenMP).
 """
 from __future__ import annotations
 
@@ -40,32 +46,74 @@ SKIN = 0.3
 DT = 1.0
 ORACLE_CELLS = 50        # CPU sample: 500,000 atoms of the same lattice
 
-# Algorithmic float64 work per neighbour-list entry, counting each add, mul
-# and compare as 1 flop, an FMA as 2, and exp, sqrt (or rsqrt) and a
-# division as 15, 8 and 8 flops (the cost of a table-free float64 evaluation
-# by polynomial / Newton steps). K = list length, K_in = entries inside r_cut.
-# Pair pass (k_pairs_half), RGL, per pair evaluated (the K/2 upper entries):
-# separation 3, r^2 5, rsqrt 8, r 1, two exp arguments 4, two exp 30,
-# prefactors 2, A = V'/r and B = rho'/r 6 -> 59 inside r_cut, 8 outside.
-# Density sums (k_rho_sum): 2 per entry. Force pass (k_force): separation
-# 3, s = A + (F'_i + F'_j) B 3, F_i += s d 6 -> 12 per entry inside r_cut.
-KERNELS = {
-    # phase: (kernel, flops(K, K_in), bytes(K, K_in)) per atom
-    "pairs": ("k_pairs_half (float64 pair functions)",
-              lambda K, Ki: Ki / 2 * 59.0 + (K - Ki) / 2 * 8.0,
-              # list 4K, reverse index 2K, (A,B) and (rho,V) written to both slots 32K, x 32
-              lambda K, Ki: 38.0 * K + 32.0),
-    "density": ("k_rho_sum (float64 density sums)", lambda K, Ki: 2.0 * K,
-                # count 4, (rho, V) reads 16K, rho/F'/E_i writes 24
-                lambda K, Ki: 16.0 * K + 28.0),
-    "force": ("k_force (float64 force pass)", lambda K, Ki: 10.0 * Ki,
-              # list 4K, (A,B) reads 16K, count 4, x_i 32, F'_i 8, F 24, v 48
-              lambda K, Ki: 20.0 * K + 116.0),
-}
-# GB300 float64 peak from unit counts and clock (no measured float64 peak
-# is provided): 152 SMs x 2 float64 FMA per clock x 2 flop x 2.07 GHz
-# (an FMA-chain probe measured 1.20 TFLOP/s).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Algorithmic work per atom of each hot kernel, counting each add, mul and
+# compare as 1 flop, an FMA as 2, and exp, sqrt (or rsqrt) and a division
+# as 15, 8 and 8 flops in float64 (the cost of a table-free evaluation by
+# polynomial / Newton steps) and 4 in float32 (one special-function
+# instruction and its scaling). K = list length, Ki = entries inside r_cut;
+# positions and F' of partners are counted once per atom (ideal L2 reuse in
+# cell order). Counted by hand from the kernel sources.
+#
+# float64 pair pass (k_pairs_half), per pair evaluated (the K/2 upper entries):
+#   RGL: separation 3, r^2 5, rsqrt 8, r 1, two exp arguments 4, two exp 30,
+#        prefactors 2, A = V'/r and B = rho'/r 6 -> 59 inside r_cut, 8 outside
+#   Sutton-Chen: separation 3, r^2 5, rsqrt 8, r 1, a/r 1, (a/r)^9 and
+#        (a/r)^6 by squarings 9, eps 1, A and B 6 -> 34 (+ taper share 1)
+#   spline: separation 3, r^2 5, rsqrt 8, r 1, u 1, V, V', rho, rho' 20,
+#        A and B 2 -> 40
+#   bytes: list 4K, reverse index 2K, the 32-byte cache entry written to
+#   both slots 32K, x 32
+# float64 density sums (k_rho_sum): 2 per entry; count 4, (rho, V) reads
+#   16K, rho/F'/E_i writes 24
+# float64 force pass (k_force): s = A + (F'_i + F'_j) B 3 and F_i += s x_j
+#   6, +1 for the total -> 10 per entry inside r_cut; list 4K, (A, B) 16K,
+#   count 4, x_i 32, F'_i 8, F 24, v 48
+# float32 density pass (k_density_mixed): separation 9, r^2 5, compare 1 per
+#   entry; rsqrt 4, r 1, exp argument 2, exp 5, f = xi^2 e S 2, sum 2 per
+#   pair inside r_cut (SC: (a/r)^6 6 instead of the exponential); list 4K,
+#   offset 16, count 4, rho/F'/F'32/E_i writes 28
+# float32 force pass (k_force_mixed): 15 per entry as above; rsqrt 4, r 1,
+#   two exponentials 14, V, V', rho, rho' 6, s 4, three products and four
+#   sums 7, taper share 3 per pair inside r_cut -> 39; list 4K, offset 16,
+#   count 4, F' 4, F 24, E_i 16, v 48
+# adjoint (md_param_grad, the fitting leg): per entry inside r_cut, float64
+#   with cached pair values: u_i terms 12 and the five RGL parameter terms
+#   30 -> 42; float32 from offsets: 15 per entry + 60 per pair; bytes: two
+#   passes over list and cache (2 x (4K + 32K)) float64, 2 x 4K float32
+SEP64 = 3.0
+PAIR64 = {"rgl": 59.0, "sc": 35.0, "spline": 40.0, "alloy": 40.0}
+
+
+def kernel_model(phase: str, precision: str, kind: str, K: float, Ki: float):
+    """(kernel name, flops per atom, bytes per atom, pipe) of a phase's
+    dominant kernel, after the counts above."""
+    if precision == "fp64":
+        if phase == "pairs":
+            return ("k_pairs_half (float64 pair functions)",
+                    Ki / 2 * PAIR64.get(kind, 40.0) + (K - Ki) / 2 * 8.0, 38.0 * K + 32.0, "fp64")
+        if phase == "density":
+            return "k_rho_sum (float64 density sums)", 2.0 * K, 16.0 * K + 28.0, "fp64"
+        if phase == "force":
+            return "k_force (float64 force pass)", 10.0 * Ki, 20.0 * K + 116.0, "fp64"
+        if phase == "grad":
+            return "adjoint kernels (float64, cached pair values)", 42.0 * Ki, 72.0 * K + 64.0, "fp64"
+    else:
+        dens = 16.0 if kind == "rgl" else 17.0
+        if phase == "density":
+            return "k_density_mixed (float32 pair math)", 15.0 * K + dens * Ki, 4.0 * K + 48.0, "fp32"
+        if phase == "force":
+            return "k_force_mixed (float32 pair math)", 15.0 * K + 39.0 * Ki, 4.0 * K + 116.0, "fp32"
+        if phase == "grad":
+            return "adjoint kernels (float32 pair math)", 15.0 * K + 60.0 * Ki, 8.0 * K + 64.0, "fp32"
+    return f"{phase} phase", None, None, None
+
+
+# Derived float64 peak, kept as a note beside the measured one: 152 SMs x 2
+# float64 FMA per clock x 2 flop x 2.07 GHz.
+FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Bytes per atom-step of the whole step by the north-star definition: the
+# list (4 B per entry) and positions (24 B) read by both force passes.
+STEP_BYTES = lambda K: 2 * 4.0 * K + 2 * 24.0  # noqa: E731
 # DRAM bytes (read + write) per atom of one k_pairs_half launch, from an ncu
 # capture of 1,048,576 atoms of the same lattice, potential and temperature
 # (0.454 GB read + 1.772 GB written); traffic grows in proportion to the
@@ -82,6 +130,84 @@ def measured_peaks() -> dict:
     if p.exists():
         return json.loads(p.read_text())
     return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def probe_peaks(gpu_index: int) -> dict:
+    """float64 and float32 FMA rates of this GPU by the library's probe
+    kernel (md_fma_probe), each launch sized to about 5 ms, best of three,
+    with the SM clock sampled meanwhile."""
+    from paper_1212_6332_gb300 import md
+    res = {}
+    with ClockSampler(gpu_index) as clk:
+        for prec, it0 in (("fp64", 512), ("fp32", 16384)):
+            md.fma_probe(prec, it0)
+            r = md.fma_probe(prec, it0)
+            iters = int(it0 * max(1.0, 5.0 / max(r["ms"], 1e-3)))
+            res[prec] = max((md.fma_probe(prec, iters) for _ in range(3)), key=lambda d: d["flops"])
+    c = clk.summary()
+    return {"fp64_tflops": res["fp64"]["flops"] / 1e12, "fp32_tflops": res["fp32"]["flops"] / 1e12,
+            "sm_count": res["fp64"]["n_sm"], "fp64_launch_ms": res["fp64"]["ms"],
+            "fp32_launch_ms": res["fp32"]["ms"], "clocks": c,
+            "how": "md_fma_probe: every resident thread runs 8 independent FMA chains; best of 3 launches of ~5 ms",
+            "fp64_derived_tflops": FP64_DERIVED_TFLOPS}
+
+
+def cpu_info() -> dict:
+    """Host CPU: logical cores and the model line(s) of /proc/cpuinfo."""
+    model = None
+    try:
+        txt = pathlib.Path("/proc/cpuinfo").read_text()
+        for key in ("model name", "Model", "CPU part"):
+            for line in txt.splitlines():
+                if line.lower().startswith(key.lower()):
+                    model = line.split(":", 1)[1].strip()
+                    if key == "CPU part":
+                        impl = [ln.split(":", 1)[1].strip() for ln in txt.splitlines()
+                                if ln.startswith("CPU implementer")]
+                        model = f"CPU implementer {impl[0] if impl else '?'}, part {model}"
+                    break
+            if model:
+                break
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+def roofline_block(prof: dict, N: int, precision: str, kind: str, K: float, Ki: float, peaks: dict,
+                   hbm_gbs: float, phases=("pairs", "density", "force", "grad"), note: str | None = None) -> dict:
+    """The dominant kernel of one run (largest event time among the hot
+    phases) against both ceilings: algorithmic bytes over time against the
+    measured HBM bandwidth, algorithmic flops over time against the measured
+    FMA rate of its pipe (float64 or float32); the binding ceiling is the
+    larger fraction."""
+    ms = {p: prof["ms"].get(p, 0.0) for p in phases if prof["ms"].get(p, 0.0) > 0}
+    if not ms:
+        return {"kernel": None, "note": "no timed hot phase"}
+    dom = max(ms, key=ms.get)
+    launches = max(prof["timed"].get(dom, 1), 1)
+    launch_ms = ms[dom] / launches
+    kname, fl, by, pipe = kernel_model(dom, precision, kind, K, Ki)
+    out = {"phase": dom, "kernel": kname, "launch_ms": launch_ms, "launches": launches,
+           "share_of_timed": ms[dom] / max(sum(prof["ms"].values()), 1e-12), "mean_list_len": K, "mean_in_cutoff": Ki}
+    if fl is None:
+        out["note"] = "no work model for this phase"
+        return out
+    peak_alu = peaks["fp64_tflops"] if pipe == "fp64" else peaks["fp32_tflops"]
+    a_alu = N * fl / (launch_ms * 1e-3) / 1e12
+    a_hbm = N * by / (launch_ms * 1e-3) / 1e9
+    out["alu"] = {"pipe": pipe, "achieved": a_alu, "peak": peak_alu, "unit": "TFLOP/s", "frac": a_alu / peak_alu,
+                  "flops_per_launch": N * fl, "peak_source": "measured (md_fma_probe)"}
+    out["hbm"] = {"achieved": a_hbm, "peak": hbm_gbs, "unit": "GB/s", "frac": a_hbm / hbm_gbs,
+                  "bytes_per_launch": N * by, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    fa, fh = a_alu / peak_alu, a_hbm / hbm_gbs
+    out["binding"] = pipe if fa >= fh else "hbm"
+    if max(fa, fh) < 0.5:
+        out["binding_note"] = "both below half: latency / issue bound"
+    if note:
+        out["note"] = note
+    return out
 
 
 class ClockSampler:
@@ -165,7 +291,8 @@ def combine_ranks(local_ms: float, atoms_per_rank: int, steps: int, dist=None, d
 
 
 def list_stats(sysm, x_dev, box, rc, sample: int = 65536):
-    """Mean list length K and mean entries inside r_cut over a sample of atoms."""
+    """Mean list length K and mean entries inside r_cut over a sample of
+    atoms. box: [3] or per-atom [N, 3] box lengths."""
     import torch
     nn, nl = sysm.neighbors()
     n = nn.shape[0]
@@ -175,7 +302,9 @@ def list_stats(sysm, x_dev, box, rc, sample: int = 65536):
     valid = torch.arange(cols.shape[1], device="cuda")[None, :] < nns[:, None]
     cols = torch.where(valid, cols, torch.zeros_like(cols))
     d = x_dev[cols] - x_dev[idx][:, None, :]
-    bt = torch.tensor(box, device="cuda", dtype=torch.float64)
+    bt = torch.as_tensor(np.asarray(box, dtype=np.float64), device="cuda")
+    if bt.dim() == 2:
+        bt = bt[idx][:, None, :]
     d = d - bt * torch.round(d / bt)
     r2 = (d * d).sum(-1)
     inside = ((r2 < rc * rc) & valid).sum(1).double().mean().item()
@@ -184,21 +313,29 @@ def list_stats(sysm, x_dev, box, rc, sample: int = 65536):
     return K, inside
 
 
-def oracle_sample(steps: int, cells: int = ORACLE_CELLS) -> dict:
-    """The CPU oracle (single thread) on a bounded sample of the workload: a
-    cells^3 fcc box of the same lattice, potential, temperature and seed."""
+def oracle_sample(steps: int, cells: int = ORACLE_CELLS, threads: int = 1, spec=None, a=I.A_CU, mass=I.MASS_CU,
+                  temp=TEMP, seed=SEED, label="fcc Cu, RGL Cu") -> dict:
+    """The CPU oracle on a cells^3 fcc box of the workload's lattice,
+    potential, temperature and seed: `steps` velocity-Verlet steps, minus a
+    run of no steps (its list build and first forces). threads > 1 runs the
+    oracle's all-cores form (OpenMP, thread-private sums)."""
     import oracle as O
-    bx = I.perturbed_fcc(cells, I.A_CU, TEMP, I.MASS_CU, SEED)
-    pot = O.Potential(I.RGL_CU)
-    t0 = time.perf_counter()
-    O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, DT, SKIN, 0)
-    t1 = time.perf_counter()
-    O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, DT, SKIN, steps)
-    t2 = time.perf_counter()
+    spec = spec or I.RGL_CU
+    bx = I.perturbed_fcc(cells, a, temp, mass, seed)
+    pot = O.Potential(spec)
+    used = O.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        O.md_run(pot, bx.x, bx.v, bx.box, mass, DT, SKIN, 0)
+        t1 = time.perf_counter()
+        O.md_run(pot, bx.x, bx.v, bx.box, mass, DT, SKIN, steps)
+        t2 = time.perf_counter()
+    finally:
+        O.set_threads(1)
     per_step = max((t2 - t1) - (t1 - t0), 1e-9) / steps
-    return dict(value=bx.n / per_step, per_step_s=per_step, n=bx.n, setup_s=t1 - t0,
-                sample=f"oracle on a {cells}^3-cell fcc Cu box ({bx.n} atoms, same lattice, RGL, {TEMP:.0f} K, "
-                       f"seed {SEED}), {steps} velocity-Verlet steps minus its setup run")
+    return dict(value=bx.n / per_step, unit=UNIT, cores=used, per_step_s=per_step, n=bx.n, setup_s=t1 - t0,
+                sample=f"oracle on a {cells}^3-cell box ({bx.n} atoms; {label}, {temp:.0f} K, seed {seed}), "
+                       f"{steps} velocity-Verlet steps minus a run of none, {used} thread(s)")
 
 
 def oracle_batch_sample(steps: int = 3, n_sample: int = 16) -> dict:
@@ -246,31 +383,41 @@ def workload_name(cells: int, precision: str) -> str:
 
 
 def run_reference(args):
+    """The CPU oracle on the timed arm's own box (fcc Cu, --cells^3 cells,
+    RGL Cu, 300 K, seed 1) on all host cores: W untimed steps, then K timed
+    steps minus a run of none (the list build and first forces every run
+    starts with)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle as O
     O.build()
-    W, K = args.warmup, args.steps
-    cells = ORACLE_CELLS
-    bx = I.perturbed_fcc(cells, I.A_CU, TEMP, I.MASS_CU, SEED)
+    W, K = args.warmup, max(args.steps, 1)
+    threads = O.max_threads()
+    bx = I.perturbed_fcc(args.cells, I.A_CU, TEMP, I.MASS_CU, SEED)
     pot = O.Potential(I.RGL_CU)
-    st = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, DT, SKIN, max(W, 0))
-    t0 = time.perf_counter()
-    O.md_run(pot, st["x"], st["v"], bx.box, I.MASS_CU, DT, SKIN, 0)
-    t1 = time.perf_counter()
-    O.md_run(pot, st["x"], st["v"], bx.box, I.MASS_CU, DT, SKIN, K)
-    t2 = time.perf_counter()
-    per_step = max((t2 - t1) - (t1 - t0), 1e-9) / max(K, 1)
+    used = O.set_threads(threads)
+    try:
+        st = O.md_run(pot, bx.x, bx.v, bx.box, I.MASS_CU, DT, SKIN, max(W, 0))
+        t0 = time.perf_counter()
+        O.md_run(pot, st["x"], st["v"], bx.box, I.MASS_CU, DT, SKIN, 0)
+        t1 = time.perf_counter()
+        run = O.md_run(pot, st["x"], st["v"], bx.box, I.MASS_CU, DT, SKIN, K)
+        t2 = time.perf_counter()
+    finally:
+        O.set_threads(1)
+    per_step = max((t2 - t1) - (t1 - t0), 1e-9) / K
     value = bx.n / per_step
-    sample = (f"oracle on a {cells}^3-cell fcc Cu box ({bx.n} atoms, same lattice, RGL, {TEMP:.0f} K, seed {SEED}); "
-              f"per-step time = ({K} steps run - setup run) / {K}")
+    cpu = cpu_info()
+    sample = (f"the oracle on the whole timed box ({bx.n} atoms) on {used} thread(s) (OpenMP, thread-private "
+              f"sums); per-step time = ({K} steps - a run of none) / {K}, after {W} untimed steps")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-           "warmup": W, "ms_per_step": per_step * 1e3 * (4 * args.cells ** 3 / bx.n), "higher_is_better": True,
+           "warmup": W, "ms_per_step": per_step * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(args.cells, "fp64"), "atoms": 4 * args.cells ** 3,
-                      "sample_atoms": bx.n},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": workload_name(args.cells, "fp64"), "atoms": bx.n, "n_rebuild": run["n_rebuild"],
+                      "timed_s": t2 - t1, "setup_s": t1 - t0},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                            "nproc": cpu["nproc"], "cpu_model": cpu["model"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -294,20 +441,27 @@ def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=N
         s.set_thermostat(*thermostat)
     if barostat:
         s.set_barostat(*barostat)
-    s.set_state(torch.tensor(x_h, device="cuda"), torch.tensor(v_h, device="cuda"))
-    s.step(W)
+    x_dev = torch.tensor(x_h, device="cuda")
+    s.set_state(x_dev, torch.tensor(v_h, device="cuda"))
+    Kl, Ki = list_stats(s, x_dev, box, spec.get("r_cut", spec.get("r_hi", 5.0)))
+    del x_dev
+    s.step(W, use_graph=True)
     torch.cuda.synchronize()
-    s.profile_start(timing=True)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    th = s.step(K)
+    th = s.step(K, use_graph=True)
     b.record()
     b.synchronize()
     ms = a.elapsed_time(b)
+    # per-phase event times from a further, untimed stretch (events turn
+    # graph replay off)
+    s.profile_start(timing=True)
+    s.step(K)
     prof = s.profile_read()
     s.close()
-    return dict(value=len(x_h) * K / (ms * 1e-3), ms_per_step=ms / K, n_rebuild=th["n_rebuild"],
-                phase_ms_per_step={k: v / max(K, 1) for k, v in prof["ms"].items()})
+    return dict(value=len(x_h) * K / (ms * 1e-3), ms_per_step=ms / K, n_rebuild=th["n_rebuild"], graph=True,
+                phase_ms_per_step={k: v / max(K, 1) for k, v in prof["ms"].items()},
+                mean_list_len=Kl, mean_in_cutoff=Ki, _prof=prof)
 
 
 def run_small(K: int, use_graph: bool) -> dict:
@@ -318,7 +472,9 @@ def run_small(K: int, use_graph: bool) -> dict:
     from paper_1212_6332_gb300.md import System
     bx = I.perturbed_fcc(8, I.A_CU, 300.0, I.MASS_CU, 12345)
     s = System(I.RGL_CU, box=bx.box, n_atoms=bx.n, skin=SKIN, dt=DT, mass=I.MASS_CU)
-    s.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+    x_dev = torch.tensor(bx.x, device="cuda")
+    s.set_state(x_dev, torch.tensor(bx.v, device="cuda"))
+    Kl, Ki = list_stats(s, x_dev, bx.box, I.RGL_CU["r_cut"])
     s.step(K, use_graph=use_graph)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -327,9 +483,13 @@ def run_small(K: int, use_graph: bool) -> dict:
     b.record()
     b.synchronize()
     ms = a.elapsed_time(b)
+    s.profile_start(timing=True)
+    s.step(K)
+    prof = s.profile_read()
     s.close()
     return dict(value=bx.n * K / (ms * 1e-3), ms_per_step=ms / K, steps=K, n_rebuild=th["n_rebuild"],
-                graph=use_graph, l2="working set inside L2")
+                graph=use_graph, l2="working set inside L2", mean_list_len=Kl, mean_in_cutoff=Ki, atoms=bx.n,
+                phase_ms_per_step={k: v / max(K, 1) for k, v in prof["ms"].items()}, _prof=prof)
 
 
 def run_batch(precision: str, K: int, W: int, n_boxes: int = 4096, use_graph: bool = True,
@@ -341,7 +501,11 @@ def run_batch(precision: str, K: int, W: int, n_boxes: int = 4096, use_graph: bo
     bt = I.batch_of_boxes(n_boxes, I.A_CU, I.MASS_CU, seed=2024)
     s = System(I.RGL_CU, boxes=bt.box, atom_offsets=bt.atom_offsets, skin=SKIN, dt=DT, mass=I.MASS_CU,
                precision=precision)
-    s.set_state(torch.tensor(bt.x, device="cuda"), torch.tensor(bt.v, device="cuda"))
+    x_dev = torch.tensor(bt.x, device="cuda")
+    s.set_state(x_dev, torch.tensor(bt.v, device="cuda"))
+    counts = np.diff(np.asarray(bt.atom_offsets))
+    Kl, Ki = list_stats(s, x_dev, np.repeat(np.asarray(bt.box), counts, axis=0), I.RGL_CU["r_cut"])
+    del x_dev
     s.batch_step(W, schedule=schedule, use_graph=use_graph, per_box=False)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -351,7 +515,7 @@ def run_batch(precision: str, K: int, W: int, n_boxes: int = 4096, use_graph: bo
     b.synchronize()
     ms = a.elapsed_time(b)
     n = int(bt.atom_offsets[-1])
-    phases = None
+    phases = prof = None
     if schedule == "tile":
         # phase split from a further, untimed stretch of the same run (phase
         # events turn graph replay off, so they stay out of the timed steps)
@@ -361,7 +525,8 @@ def run_batch(precision: str, K: int, W: int, n_boxes: int = 4096, use_graph: bo
         phases = {k: v / max(K, 1) for k, v in prof["ms"].items()}
     s.close()
     return dict(value=n * K / (ms * 1e-3), ms_per_step=ms / K, atoms=n, boxes=n_boxes, schedule=schedule,
-                graph=use_graph and schedule == "tile", phase_ms_per_step=phases)
+                graph=use_graph and schedule == "tile", phase_ms_per_step=phases, mean_list_len=Kl,
+                mean_in_cutoff=Ki, _prof=prof)
 
 
 def run_per_box_sample(K: int, n_sample: int = 64, n_boxes: int = 4096) -> dict:
@@ -432,9 +597,20 @@ def run_grad(K: int, W: int, precision: str = "fp64", kind: str = "rgl") -> dict
         L, g = once()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    # per-phase device time of one further iteration (forward passes and
+    # the adjoint), untimed
+    s.profile_start(timing=True)
+    once()
+    prof = s.profile_read()
+    Kl = Ki = None
+    if kind == "rgl":
+        x_all = torch.tensor(np.concatenate([c.x for c in cfgs]), device="cuda")
+        boxes = np.repeat(np.stack([c.box for c in cfgs]), [c.n for c in cfgs], axis=0)
+        Kl, Ki = list_stats(s, x_all, boxes, I.RGL_CU["r_cut"])
     s.close()
     return dict(value=K / dt, unit="(loss + gradient over 256 configs)/s", atom_grads_per_s=n * K / dt,
-                n_params=int(theta.numel()), loss=float(L.item()), precision=precision, model=kind)
+                n_params=int(theta.numel()), loss=float(L.item()), precision=precision, model=kind, atoms=n,
+                phase_ms_per_iter=prof["ms"], mean_list_len=Kl, mean_in_cutoff=Ki, _prof=prof)
 
 
 def spline_model(spec: dict) -> dict:
@@ -538,6 +714,11 @@ def main():
         return
     from paper_1212_6332_gb300.md import System
 
+    peaks = probe_peaks(local)
+    mp = measured_peaks()
+    hbm = mp.get("hbm_gbs", 6800.0)
+    hbm_src = "fallback" if "fallback" in mp else "measured"
+
     bx = I.perturbed_fcc(args.cells, I.A_CU, TEMP, I.MASS_CU, SEED)
     N = bx.n
     x_dev = torch.tensor(bx.x, device="cuda")
@@ -545,47 +726,63 @@ def main():
     s = System(I.RGL_CU, box=bx.box, n_atoms=N, skin=SKIN, dt=DT, mass=I.MASS_CU, precision=args.precision)
     s.set_state(x_dev, v_dev)
     K_list, K_in = list_stats(s, x_dev, bx.box, I.RGL_CU["r_cut"])
-    s.step(W)
+    s.step(W, use_graph=True)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
+    # the timed steps: md_step with CUDA-graph replay, as a user runs it;
+    # launches are counted (not timed) meanwhile
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.profile_start(timing=True)
+    s.profile_start(timing=False)
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
-        th = s.step(K)
+        th = s.step(K, use_graph=True)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    prof = s.profile_read()
+    launches = s.profile_read()["launches"]
     ms = ev0.elapsed_time(ev1)
     value, ms_max = combine_ranks(ms, N, K, dist)
 
-    # dominant kernel (event-timed on the launching stream)
-    dom = max(KERNELS, key=lambda k: prof["ms"][k])
-    k_ms = prof["ms"][dom] / max(prof["timed"][dom], 1)
-    kname, ffl, fby = KERNELS[dom]
-    flops = N * ffl(K_list, K_in)
-    achieved = flops / (k_ms * 1e-3) / 1e12
-    bytes_k = N * fby(K_list, K_in)
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SM x 2 float64 FMA/clock x 2 flop x 2.07 GHz",
+    # per-kernel times: K further steps with per-phase CUDA events on the
+    # launching stream (graph replay off while they record), untimed
+    s.profile_start(timing=True)
+    th_p = s.step(K)
+    prof = s.profile_read()
+    phase_ms = {k: prof["ms"][k] / max(K, 1) for k in prof["ms"]}
+    phase_sum = sum(phase_ms.values())
+
+    # dominant kernel of the headline against the measured float64 FMA rate
+    kind = "rgl"
+    main_block = roofline_block(prof, N, args.precision, kind, K_list, K_in, peaks, hbm)
+    dom = main_block["phase"]
+    alu = main_block.get("alu", {})
+    roofline = {"bound": "alu", "kernel": main_block["kernel"], "achieved": alu.get("achieved"),
+                "peak": alu.get("peak"), "unit": "TFLOP/s", "frac": alu.get("frac"),
+                "peak_source": f"measured: md_fma_probe {'float64' if alu.get('pipe') == 'fp64' else 'float32'} "
+                               f"FMA rate in this run ({peaks['sm_count']} SMs, "
+                               f"SM clock {peaks['clocks'].get('sm_mhz')} MHz); derived "
+                               f"{FP64_DERIVED_TFLOPS:.3f} TFLOP/s float64 from unit counts",
                 "traffic": (PAIRS_DRAM_BYTES_PER_ATOM * N if dom == "pairs" and args.precision == "fp64" else None),
                 "traffic_source": "ncu capture of 1,048,576 atoms scaled by the atom count",
-                "flops_per_launch": flops, "launch_ms": k_ms,
-                "hbm": {"achieved": bytes_k / (k_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                        "frac": bytes_k / (k_ms * 1e-3) / 1e9 / hbm,
-                        "peak_source": "measured" if "fallback" not in peaks else "fallback",
-                        "bytes_per_launch": bytes_k}}
-    phase_ms = {k: prof["ms"][k] / max(K, 1) for k in prof["ms"]}
+                "flops_per_launch": alu.get("flops_per_launch"), "launch_ms": main_block["launch_ms"],
+                "launch_ms_source": "CUDA events around each launch of the kernel on its stream, over K steps "
+                                    "after the timed ones",
+                "hbm": main_block.get("hbm"), "binding": main_block.get("binding"),
+                "peaks": peaks}
+    # the whole step against HBM by the spec byte count (list and
+    # positions read by both force passes)
+    step_bytes = N * STEP_BYTES(K_list)
+    roofline["step_hbm"] = {"bytes_per_step": step_bytes, "achieved": step_bytes / (ms_max / K * 1e-3) / 1e9,
+                            "peak": hbm, "unit": "GB/s",
+                            "frac": step_bytes / (ms_max / K * 1e-3) / 1e9 / hbm, "peak_source": hbm_src,
+                            "definition": "2 x 4K + 2 x 24 B per atom-step, K the mean list length"}
+    configs = {"C2_rgl_fp64_300K": main_block}
 
     # end to end through the C ABI with pinned host buffers: every step
     # uploads the state, advances one step and downloads the state
@@ -608,55 +805,98 @@ def main():
            "d2h_bytes_per_step": 2 * N * 3 * 8 + 56,
            "call": "md_set_state(host) + md_step(1) + md_get_state(host) per step", "steps": K_e2e}
 
+    def strip(d):
+        return {k: v for k, v in d.items() if not k.startswith("_")}
+
     variants = {}
     cpu = None
     batch = grad = None
     if rank == 0 and not args.no_extras:
         s.close()
         del s
-        variants["mixed"] = run_variant("mixed", W, K, bx.x, bx.v, bx.box)
+        v = run_variant("mixed", W, K, bx.x, bx.v, bx.box)
+        configs["C2_rgl_mixed_300K"] = roofline_block(v["_prof"], N, "mixed", "rgl", v["mean_list_len"],
+                                                      v["mean_in_cutoff"], peaks, hbm)
+        variants["mixed"] = strip(v)
         variants["fp64"] = {"value": value, "ms_per_step": ms_max / K}
         hot = I.perturbed_fcc(args.cells, I.A_CU, 1200.0, I.MASS_CU, 2)
-        variants["fp64_1200K"] = run_variant("fp64", W, K, hot.x, hot.v, hot.box)
-        variants["mixed_1200K"] = run_variant("mixed", W, K, hot.x, hot.v, hot.box)
-        variants["sc_fp64"] = run_variant("fp64", W, max(5, K // 3), bx.x, bx.v, bx.box, spec=I.SC_CU)
-        variants["sc_mixed"] = run_variant("mixed", W, K, bx.x, bx.v, bx.box, spec=I.SC_CU)
+        variants["fp64_1200K"] = strip(run_variant("fp64", W, K, hot.x, hot.v, hot.box))
+        variants["mixed_1200K"] = strip(run_variant("mixed", W, K, hot.x, hot.v, hot.box))
         del hot
+        v = run_variant("fp64", W, max(5, K // 3), bx.x, bx.v, bx.box, spec=I.SC_CU)
+        configs["C2_sc_fp64"] = roofline_block(v["_prof"], N, "fp64", "sc", v["mean_list_len"], v["mean_in_cutoff"],
+                                               peaks, hbm)
+        variants["sc_fp64"] = strip(v)
+        v = run_variant("mixed", W, K, bx.x, bx.v, bx.box, spec=I.SC_CU)
+        configs["C2_sc_mixed"] = roofline_block(v["_prof"], N, "mixed", "sc", v["mean_list_len"], v["mean_in_cutoff"],
+                                                peaks, hbm)
+        variants["sc_mixed"] = strip(v)
         ni = I.perturbed_fcc(80, I.A_NI, 600.0, I.MASS_NI, 3)
-        variants["ni_2m_fp64"] = run_variant("fp64", W, K, ni.x, ni.v, ni.box, spec=I.RGL_NI, mass=I.MASS_NI)
-        variants["ni_2m_mixed"] = run_variant("mixed", W, K, ni.x, ni.v, ni.box, spec=I.RGL_NI, mass=I.MASS_NI)
+        for prec in ("fp64", "mixed"):
+            v = run_variant(prec, W, K, ni.x, ni.v, ni.box, spec=I.RGL_NI, mass=I.MASS_NI)
+            configs[f"C3_ni_{prec}"] = roofline_block(v["_prof"], ni.n, prec, "rgl", v["mean_list_len"],
+                                                      v["mean_in_cutoff"], peaks, hbm)
+            variants[f"ni_2m_{prec}"] = strip(v)
         del ni
-        # full-list sums against Newton's third law, both with phase events
-        variants["fp64_phases"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box)
-        variants["fp64_newton3"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box, newton3=True)
-        variants["fp64_thermostat"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box, thermostat=(300.0, 100.0))
-        variants["fp64_barostat"] = run_variant("fp64", W, K, bx.x, bx.v, bx.box,
-                                                barostat=(0.0, 1000.0, 160.21766208 / 140.0))
+        variants["fp64_newton3"] = strip(run_variant("fp64", W, K, bx.x, bx.v, bx.box, newton3=True))
+        variants["fp64_thermostat"] = strip(run_variant("fp64", W, K, bx.x, bx.v, bx.box, thermostat=(300.0, 100.0)))
+        variants["fp64_barostat"] = strip(run_variant("fp64", W, K, bx.x, bx.v, bx.box,
+                                                      barostat=(0.0, 1000.0, 160.21766208 / 140.0)))
         al = I.perturbed_fcc(args.cells, 3.57, TEMP, I.MASS_CU, 5)
         al_types = np.random.default_rng(5).integers(0, 2, al.n).astype(np.int32)
         al_spec = alloy_model()
-        variants["alloy_cuni_fp64"] = run_variant("fp64", W, K, al.x, al.v, al.box, spec=al_spec, types=al_types)
-        variants["alloy_cuni_mixed"] = run_variant("mixed", W, K, al.x, al.v, al.box, spec=al_spec, types=al_types)
+        variants["alloy_cuni_fp64"] = strip(run_variant("fp64", W, K, al.x, al.v, al.box, spec=al_spec,
+                                                        types=al_types))
+        variants["alloy_cuni_mixed"] = strip(run_variant("mixed", W, K, al.x, al.v, al.box, spec=al_spec,
+                                                         types=al_types))
         del al
-        variants["cu_2048_graph"] = run_small(200, True)
-        variants["cu_2048_nograph"] = run_small(200, False)
+        v = run_small(200, True)
+        configs["C1_cu_2048_fp64"] = roofline_block(
+            v["_prof"], v["atoms"], "fp64", "rgl", v["mean_list_len"], v["mean_in_cutoff"], peaks, hbm,
+            note="2048 atoms: the working set sits in L2 and the step is launch-bound; the kernel figures are "
+                 "from per-phase events with graph replay off")
+        variants["cu_2048_graph"] = strip(v)
+        variants["cu_2048_nograph"] = strip(run_small(200, False))
         del x_dev, v_dev
         torch.cuda.empty_cache()
         kb = max(5, min(K, 20))
-        batch = {"fp64": run_batch("fp64", kb, W), "fp64_box": run_batch("fp64", kb, W, schedule="box"),
-                 "mixed": run_batch("mixed", kb, W),
-                 "one_launch_per_box": run_per_box_sample(kb)}
+        b64 = run_batch("fp64", kb, W)
+        bmx = run_batch("mixed", kb, W)
+        configs["C4_batch_fp64"] = roofline_block(b64["_prof"], b64["atoms"], "fp64", "rgl", b64["mean_list_len"],
+                                                  b64["mean_in_cutoff"], peaks, hbm)
+        configs["C4_batch_mixed"] = roofline_block(bmx["_prof"], bmx["atoms"], "mixed", "rgl",
+                                                   bmx["mean_list_len"], bmx["mean_in_cutoff"], peaks, hbm)
+        batch = {"fp64": strip(b64), "fp64_box": strip(run_batch("fp64", kb, W, schedule="box")),
+                 "mixed": strip(bmx), "one_launch_per_box": run_per_box_sample(kb)}
         kg = max(3, min(K, 10))
-        grad = {"rgl_fp64": run_grad(kg, 2, "fp64", "rgl"), "rgl_mixed": run_grad(kg, 2, "mixed", "rgl"),
-                "spline_fp64": run_grad(kg, 2, "fp64", "spline"),
-                "spline_mixed": run_grad(kg, 2, "mixed", "spline"),
-                "alloy_fp64": run_grad(kg, 2, "fp64", "alloy"), "alloy_mixed": run_grad(kg, 2, "mixed", "alloy")}
+        grad = {}
+        for name, prec, model in (("rgl_fp64", "fp64", "rgl"), ("rgl_mixed", "mixed", "rgl"),
+                                  ("spline_fp64", "fp64", "spline"), ("spline_mixed", "mixed", "spline"),
+                                  ("alloy_fp64", "fp64", "alloy"), ("alloy_mixed", "mixed", "alloy")):
+            g = run_grad(kg, 2, prec, model)
+            if model == "rgl":
+                configs[f"C5_grad_rgl_{prec}"] = roofline_block(
+                    g["_prof"], g["atoms"], prec, "rgl", g["mean_list_len"], g["mean_in_cutoff"], peaks, hbm,
+                    note="one loss + gradient iteration: forward passes of the new parameters and the adjoint")
+            grad[name] = strip(g)
     if rank == 0 and not args.no_extras:
         import oracle as O
         O.build()
-        smp = oracle_sample(3)
-        cpu = {"value": smp["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp["sample"],
+        info = cpu_info()
+        all_cores = O.max_threads()
+        one = oracle_sample(3)
+        full = oracle_sample(3, cells=args.cells, threads=all_cores)
+        sc = oracle_sample(2, cells=args.cells, threads=all_cores, spec=I.SC_CU, label="fcc Cu, Sutton-Chen Cu")
+        ni_o = oracle_sample(100, cells=80, threads=all_cores, spec=I.RGL_NI, a=I.A_NI, mass=I.MASS_NI, temp=600.0,
+                             seed=3, label="fcc Ni, RGL Ni")
+        cpu = {"value": full["value"], "unit": UNIT, "cores": full["cores"], "kind": "oracle",
+               "sample": full["sample"], "nproc": info["nproc"], "cpu_model": info["model"],
+               "one_core": {k: one[k] for k in ("value", "cores", "sample")},
+               "all_cores": {k: full[k] for k in ("value", "cores", "sample")},
+               "sc_all_cores": {k: sc[k] for k in ("value", "cores", "sample")},
+               "ni_2m_all_cores_100_steps": {k: ni_o[k] for k in ("value", "cores", "sample")},
                "batch_sample": oracle_batch_sample(), "grad_sample": oracle_grad_sample()}
+    roofline["configs"] = configs
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -665,9 +905,12 @@ def main():
                "config": {"workload": workload_name(args.cells, args.precision),
                           "atoms": N, "parallelism": "replicas" if world > 1 else "single",
                           "l2": "working set (list + positions) larger than L2",
+                          "timing": "md_step with CUDA-graph replay (the user path); phases from K further "
+                                    "steps with per-phase events",
                           "mean_list_len": K_list, "mean_in_cutoff": K_in,
-                          "n_rebuild": th["n_rebuild"], "phase_ms_per_step": phase_ms},
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],
+                          "n_rebuild": th["n_rebuild"], "phase_ms_per_step": phase_ms,
+                          "phase_sum_ms": phase_sum, "phase_stretch_n_rebuild": th_p["n_rebuild"]},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(), "variants": variants, "batch": batch, "grad": grad}
         print(json.dumps(out), flush=True)
     if dist is not None:

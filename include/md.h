@@ -376,7 +376,8 @@ enum md_phase {
                                 density pass) */
     MD_PHASE_FORCE = 4,      /* force pass and second half-kick (box schedule: all phases) */
     MD_PHASE_OTHER = 5,      /* step bookkeeping, reductions, copies */
-    MD_PHASE_COUNT = 6
+    MD_PHASE_GRAD = 6,       /* md_param_grad: the adjoint kernels */
+    MD_PHASE_COUNT = 7
 };
 
 /* Kernel launches issued by a handle since md_profile_start, and (when
@@ -407,6 +408,18 @@ MD_API int md_profile_read(md_batch* h, md_profile* out);
  * rsqrt(x). Lets a caller bound the error of the hot-path functions.
  * MD_ERR_ARG for an unknown fn or non-device pointers. */
 MD_API int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double* out, md_stream stream);
+
+/* Diagnostics (no counterpart in the paper): the device's fused
+ * multiply-add rate, the denominator of the float64 (precision 0) and
+ * float32 (precision 1) rooflines of the pair math. Every resident thread
+ * (the device full of 256-thread blocks) runs 8 independent chains
+ * x <- x a + b for `iters` steps (rounded up to a multiple of 8). The call
+ * times its one launch with CUDA events on `stream`, synchronizes, and
+ * writes (host) the rate in flop/s (2 per FMA) to *flops, the launch time
+ * in ms to *ms and the multiprocessor count to *n_sm. It allocates a small
+ * output array of its own. Errors: MD_ERR_ARG (precision not 0 or 1,
+ * iters < 1, a NULL output), MD_ERR_NOMEM, MD_ERR_CUDA. */
+MD_API int md_fma_probe(int precision, int64_t iters, double* flops, double* ms, int* n_sm, md_stream stream);
 
 /* ---------------------------------------------------------------- allocation-free variant */
 

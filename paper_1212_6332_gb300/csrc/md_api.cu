@@ -1430,7 +1430,11 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
             dalloc(E, &e.grad_coef, ncoef))
             return MD_ERR_NOMEM;
     }
-    int rc = launch_param_grad(*E, g_f, g_e, grad, s);
+    int rc;
+    {
+        PhaseScope scope(e, MD_PHASE_GRAD, s);
+        rc = launch_param_grad(*E, g_f, g_e, grad, s);
+    }
     E->forces_ok = keep;
     if (rc) return fail(E, rc, "parameter gradient failed");
     CK(cudaGetLastError());

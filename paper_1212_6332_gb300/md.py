@@ -28,9 +28,9 @@ SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_
            "md_batch_step", "md_batch_set_potential", "md_set_thermostat", "md_set_newton3", "md_set_types", "md_pressure", "md_set_barostat", "md_get_box", "md_param_grad", "md_num_params", "md_status_string",
            "md_last_error", "md_profile_start", "md_profile_read",
            "md_eval_math", "md_forces_noalloc", "md_batch_thermo",
-           "md_batch_schedule")
+           "md_batch_schedule", "md_fma_probe")
 NOALLOC_MAX_ATOMS = 16384
-PHASES = ("kick_drift", "rebuild", "pairs", "density", "force", "other")
+PHASES = ("kick_drift", "rebuild", "pairs", "density", "force", "other", "grad")
 
 
 class MDError(RuntimeError):
@@ -61,7 +61,7 @@ class Thermo(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double * 6), ("timed", ctypes.c_int64 * 6)]
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double * len(PHASES)), ("timed", ctypes.c_int64 * len(PHASES))]
 
 
 _lib = None
@@ -113,6 +113,7 @@ def load(path: str | pathlib.Path | None = None) -> ctypes.CDLL:
         "md_forces_noalloc": [P(Potential), dp, i64, dp, dp, dp, dp, vp],
         "md_batch_thermo": [vp, dp, vp],
         "md_batch_schedule": [vp, P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_double)],
+        "md_fma_probe": [i32, i64, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int), vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -397,8 +398,8 @@ class System:
     def profile_read(self) -> dict:
         p = Profile()
         self._check(self.lib.md_profile_read(self._h, ctypes.byref(p)))
-        return dict(launches=p.launches, ms={PHASES[k]: p.ms[k] for k in range(6)},
-                    timed={PHASES[k]: p.timed[k] for k in range(6)})
+        return dict(launches=p.launches, ms={PHASES[k]: p.ms[k] for k in range(len(PHASES))},
+                    timed={PHASES[k]: p.timed[k] for k in range(len(PHASES))})
 
     def eval_math(self, fn: str, x):
         """The library's float64 functions on a CUDA tensor: fn in
@@ -413,6 +414,18 @@ class System:
         grad = grad if grad is not None else self._empty(self.n_params)
         self._check(self.lib.md_param_grad(self._h, _ptr(g_f), _ptr(g_e), _ptr(grad), _stream()))
         return grad
+
+
+def fma_probe(precision: str = "fp64", iters: int = 1024) -> dict:
+    """md_fma_probe: the device's measured FMA rate (flop/s), the launch time
+    (ms) and the multiprocessor count, on the current stream."""
+    lib = load()
+    fl, ms, n_sm = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    rc = lib.md_fma_probe({"fp64": 0, "fp32": 1}[precision], int(iters), ctypes.byref(fl), ctypes.byref(ms),
+                          ctypes.byref(n_sm), _stream())
+    if rc != 0:
+        raise MDError(rc, "md_fma_probe failed")
+    return dict(flops=fl.value, ms=ms.value, n_sm=n_sm.value, iters=int(iters))
 
 
 def forces_noalloc(potential: dict, box, x, f=None, e_atom=None, e_total=None):
