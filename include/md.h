@@ -412,11 +412,12 @@ MD_API int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double*
 /* Diagnostics (no counterpart in the paper): the device's fused
  * multiply-add rate, the denominator of the float64 (precision 0) and
  * float32 (precision 1) rooflines of the pair math. Every resident thread
- * (the device full of 256-thread blocks) runs 8 independent chains
- * x <- x a + b for `iters` steps (rounded up to a multiple of 8). The call
- * times its one launch with CUDA events on `stream`, synchronizes, and
- * writes (host) the rate in flop/s (2 per FMA) to *flops, the launch time
- * in ms to *ms and the multiprocessor count to *n_sm. It allocates a small
+ * (the device full of 256-thread blocks) runs 8 x iters (iters rounded up
+ * to a multiple of 16) FMAs x <- x a + b in 4, 8 and then 16 independent
+ * chains, one launch each timed with CUDA events on `stream`; the call
+ * synchronizes and writes (host) the fastest launch's rate in flop/s (2 per
+ * FMA) to *flops, its time in ms to *ms and the multiprocessor count to
+ * *n_sm. It allocates a small
  * output array of its own. Errors: MD_ERR_ARG (precision not 0 or 1,
  * iters < 1, a NULL output), MD_ERR_NOMEM, MD_ERR_CUDA. */
 MD_API int md_fma_probe(int precision, int64_t iters, double* flops, double* ms, int* n_sm, md_stream stream);

@@ -332,6 +332,208 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
     }
 }
 
+// ---------------------------------------------------------------- small systems
+//
+// For a few thousand atoms the passes above are latency-bound: the pair
+// pass gives each warp 32 atoms of float64 work on one scheduler, and each
+// thread of the two sums walks its list with one load in flight. The
+// variants below do the same arithmetic with more parallelism:
+//   k_pairs_flat: one thread per atom and upper list row (32 row slots per
+//     atom, each looping over rows 32 apart), the screen and the pair
+//     functions of k_pairs_half with the same operands (the bits of a pair
+//     depend on r alone, not on the lane that evaluates it); it beats the
+//     queued pass up to about 20,000 atoms (measured), the sums up to
+//     32,768 at least;
+//   k_rho_small / k_force_small: 128 threads per 32 atoms stage a chunk of
+//     32 list rows of their atoms in shared memory (all loads in flight, and
+//     for the force pass s_ij and the partner's image position formed at the
+//     same time), then one lane per atom adds them in list order with the
+//     operations of k_rho_sum / k_force. The per-atom sums therefore keep
+//     their order and the results are bit-identical to the passes above.
+#ifndef MD_SMALL_ATOMS
+#define MD_SMALL_ATOMS 32768
+#endif
+#ifndef MD_SMALL_PAIR_ATOMS
+#define MD_SMALL_PAIR_ATOMS 16384
+#endif
+constexpr int kSmallAtoms = MD_SMALL_ATOMS;            // largest system whose sums take these kernels
+constexpr int kSmallPairAtoms = MD_SMALL_PAIR_ATOMS;   // ... whose pair pass takes k_pairs_flat
+constexpr int kSmallRows = 32;  // list rows staged per chunk; row slots per atom in k_pairs_flat
+
+// One upper list row k of atom i: the screen and, inside it, the pair
+// functions, written to the entry's slot and its mirror.
+template <int KIND, bool SINGLE, bool MIRROR>
+__device__ __forceinline__ void pair_flat_row(int64_t i, int64_t k, int64_t Np, const Geo& g, const CellSep& cs0,
+                                              const Pot& P, float rc2f, const double4_32a* __restrict__ x,
+                                              const float4* __restrict__ xo, const int* __restrict__ nl,
+                                              const int* __restrict__ rev, double4_32a* __restrict__ pc) {
+    const int64_t own = k * Np + i;
+    const int e = nl[own];
+    const int j = entry_slot(e);
+    if (j <= i) return;  // lower entries of an unrotated list
+    const CellSep cs = cell_sep<SINGLE>(g, cs0, i);
+    const int b = SINGLE ? 0 : g.atom_box[i];
+    double L[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+    const float4 oi = xo[i], oj = xo[j];
+    const long long mir = MIRROR ? (long long)rev[own] * Np + j : 0;
+    float fx, fy, fz;
+    sep_mixed<false>(cs, oi, oj, fx, fy, fz);
+    const float r2f = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
+    double A = 0.0, B = 0.0, V = 0.0, fr = 0.0;
+    if (r2f < rc2f) {
+        const double4_32a xi = x[i], xj = x[j];
+        double dx, dy, dz;
+        sep_entry(xi, xj, entry_code(e), L, dx, dy, dz);
+        const double r2 = norm2(dx, dy, dz);
+        const int pt = KIND == MD_POT_SPLINE && P.n_types > 1 ? pair_table(P.n_types, pos_type(xi), pos_type(xj)) : 0;
+        if (below(r2, P.rc2)) pair_eval<KIND>(P, P.exp_T, r2, V, fr, A, B, pt);
+    }
+    const double4_32a c = make_double4_32a(A, B, fr, V);
+    pc[own] = c;
+    if (MIRROR) pc[mir] = c;
+}
+
+template <int KIND, bool SINGLE, bool MIRROR>
+__global__ void __launch_bounds__(kFNT) k_pairs_flat(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P, float rc2f,
+                                                     const double4_32a* __restrict__ x, const float4* __restrict__ xo,
+                                                     const int* __restrict__ nn, const int* __restrict__ nl,
+                                                     const int* __restrict__ rev, const int* __restrict__ n_up,
+                                                     int max_nb, double4_32a* __restrict__ pc, const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t % N;
+    const int64_t k0 = t / N;
+    if (k0 >= kSmallRows) return;
+    const int nup = n_up[i];
+    const int kend = nup < 0 ? min(nn[i], max_nb) : nup;
+    for (int64_t k = k0; k < kend; k += kSmallRows) pair_flat_row<KIND, SINGLE, MIRROR>(i, k, Np, g, cs0, P, rc2f, x, xo, nl, rev, pc);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kFNT) k_rho_small(int64_t N, int64_t Np, Pot P, const int* __restrict__ nn,
+                                                    int max_nb, const double4_32a* __restrict__ pc,
+                                                    const double4_32a* __restrict__ x, double* __restrict__ rho,
+                                                    double* __restrict__ Fp, double* __restrict__ e_atom,
+                                                    const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    __shared__ double2 sw[kSmallRows][32];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    const bool active = i < N;
+    const int n = active ? min(nn[i], max_nb) : 0;
+    const int kmax = warp_max(n);  // the same 32 atoms in every warp of the block
+    double r_i = 0.0, ep = 0.0;
+    for (int k0 = 0; k0 < kmax; k0 += kSmallRows) {
+#pragma unroll
+        for (int r = wq; r < kSmallRows; r += kFNT / 32) {
+            const int k = k0 + r;
+            sw[r][lane] = k < n ? cache_fv(pc, (int64_t)k * Np + i) : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        if (wq == 0) {
+            // round-to-nearest adds in list order, as k_rho_sum (whose
+            // skipped zero entries leave its sums unchanged)
+            const int kend = min(n - k0, kSmallRows);
+            for (int r = 0; r < kend; ++r) {
+                const double2 w = sw[r][lane];
+                r_i = __dadd_rn(r_i, w.x);
+                ep = __dadd_rn(ep, w.y);
+            }
+        }
+        __syncthreads();
+    }
+    if (wq != 0 || !active) return;
+    double F, Fpi;
+    embed<KIND>(P, r_i, F, Fpi, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0);
+    rho[i] = r_i;
+    Fp[i] = Fpi;
+    e_atom[i] = fma(0.5, ep, F);
+}
+
+template <bool SINGLE, bool VIR>
+__global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo g, const double4_32a* __restrict__ x,
+                                                      const int* __restrict__ nn, const int* __restrict__ nl,
+                                                      int max_nb, const double4_32a* __restrict__ pc,
+                                                      const double* __restrict__ Fp, double* __restrict__ f,
+                                                      double* __restrict__ v, double c_kick, Bath bath,
+                                                      double* __restrict__ w_atom, const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    __shared__ double4_32a sv[kSmallRows][32];  // (s_ij, image position of j)
+    __shared__ unsigned char sok[kSmallRows][32];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    const bool active = i < N;
+    double L[3] = {0.0, 0.0, 0.0};
+    double Fpi = 0.0;
+    int n = 0;
+    if (active) {
+        const int b = SINGLE ? 0 : g.atom_box[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+        Fpi = Fp[i];
+        n = min(nn[i], max_nb);
+    }
+    const int kmax = warp_max(n);
+    double fx = 0.0, fy = 0.0, fz = 0.0, w = 0.0, ssum = 0.0;
+    double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    if (VIR && active && wq == 0) xi = x[i];
+    for (int k0 = 0; k0 < kmax; k0 += kSmallRows) {
+#pragma unroll 4
+        for (int r = wq; r < kSmallRows; r += kFNT / 32) {
+            const int k = k0 + r;
+            unsigned char ok = 0;
+            if (k < n) {
+                const int64_t slot = (int64_t)k * Np + i;
+                const double2 c = cache_ab(pc, slot);
+                if (!is_zero2(c)) {
+                    const int e = nl[slot];
+                    const int j = entry_slot(e);
+                    double4_32a q;
+                    q.x = fma(Fpi + Fp[j], c.y, c.x);
+                    image_pos(x[j], entry_code(e), L, q.y, q.z, q.w);
+                    sv[r][lane] = q;
+                    ok = 1;
+                }
+            }
+            sok[r][lane] = ok;
+        }
+        __syncthreads();
+        if (wq == 0) {
+            // the operations and order of k_force
+            const int kend = min(n - k0, kSmallRows);
+            for (int r = 0; r < kend; ++r) {
+                if (!sok[r][lane]) continue;
+                const double4_32a q = sv[r][lane];
+                const double s = q.x;
+                ssum += s;
+                fx = fma(s, q.y, fx);
+                fy = fma(s, q.z, fy);
+                fz = fma(s, q.w, fz);
+                if (VIR) w = fma(s, norm2(q.y - xi.x, q.z - xi.y, q.w - xi.z), w);
+            }
+        }
+        __syncthreads();
+    }
+    if (wq != 0 || !active) return;
+    xi = x[i];
+    fx = fma(-xi.x, ssum, fx);
+    fy = fma(-xi.y, ssum, fy);
+    fz = fma(-xi.z, ssum, fz);
+    f[i] = fx;
+    f[Np + i] = fy;
+    f[2 * Np + i] = fz;
+    if (VIR) w_atom[i] = -0.5 * w;
+    if (v) {
+        double vx = v[i] + c_kick * fx, vy = v[Np + i] + c_kick * fy, vz = v[2 * Np + i] + c_kick * fz;
+        bath_half(bath, vx, vy, vz);  // friction half step after the kick
+        v[i] = vx;
+        v[Np + i] = vy;
+        v[2 * Np + i] = vz;
+    }
+}
+
 // ---------------------------------------------------------------- Newton's third law
 //
 // Float64 variant in the style of the paper's CPU code (Sec. 4.3): the pair
@@ -466,8 +668,45 @@ static int pair_blocks(const Engine& e) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((groups + per_block - 1) / per_block, (int64_t)per_sm * e.n_sm));
 }
 
+// The small-system kernels: same results, more parallelism (see above).
+template <int KIND, bool SINGLE>
+static void run_fp64_small(Engine& e, int kick, cudaStream_t s, bool virial) {
+    Geo g = make_geo(e);
+    const int nb32 = (int)((e.N + 31) / 32);
+    const int64_t flat = e.N * (int64_t)kSmallRows;
+    const double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);
+    e.launches += 3;
+    {
+        PhaseScope scope(e, MD_PHASE_PAIRS, s);
+        if (e.N <= kSmallPairAtoms)
+            k_pairs_flat<KIND, SINGLE, true><<<(int)((flat + kFNT - 1) / kFNT), kFNT, 0, s>>>(
+                e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), e.x, e.xo, e.nn, e.nl, e.rev,
+                e.n_up, e.max_nb, e.pc, e.ctl);
+        else
+            k_pairs_half<KIND, SINGLE, true><<<pair_blocks<KIND, SINGLE, true>(e), kFNT, 0, s>>>(
+                e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.x, e.xo, e.nn,
+                e.nl, e.rev, e.n_up, e.max_nb, e.pc, e.ctl);
+    }
+    {
+        PhaseScope scope(e, MD_PHASE_DENSITY, s);
+        k_rho_small<KIND><<<nb32, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.nn, e.max_nb, e.pc, e.x, e.rho, e.Fp,
+                                                e.e_atom, e.ctl);
+    }
+    PhaseScope scope(e, MD_PHASE_FORCE, s);
+    if (virial)
+        k_force_small<SINGLE, true><<<nb32, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.pc, e.Fp,
+                                                          e.f, kick ? e.v : nullptr, c_kick, e.bath, e.w_atom, e.ctl);
+    else
+        k_force_small<SINGLE, false><<<nb32, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.pc, e.Fp,
+                                                           e.f, kick ? e.v : nullptr, c_kick, e.bath, nullptr, e.ctl);
+}
+
 template <int KIND, bool SINGLE>
 static void run_fp64(Engine& e, int kick, cudaStream_t s, bool virial) {
+    if (e.N <= kSmallAtoms) {
+        run_fp64_small<KIND, SINGLE>(e, kick, s, virial);
+        return;
+    }
     Geo g = make_geo(e);
     int nb = (int)((e.N + kFNT - 1) / kFNT);
     double c_kick = 0.5 * e.cfg.dt / (e.cfg.mass * kMVV);

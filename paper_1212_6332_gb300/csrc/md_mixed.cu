@@ -19,6 +19,15 @@
 namespace mdk {
 
 constexpr int kMNT = 128;
+// List entries whose partner data (offset, F') are loaded together before
+// their pair math: more loads in flight per thread, the sums in the same
+// order and groups (4 entries: the 4M-atom step 1.98 -> 1.74 ms, 2 entries:
+// 1.92 ms; the compiler's float32 contractions may differ between batch
+// sizes, so results differ by float32 rounding).
+#ifndef MD_MIXED_BATCH
+#define MD_MIXED_BATCH 4
+#endif
+constexpr int kMB = MD_MIXED_BATCH;
 
 template <int KIND, bool SINGLE, bool WIDE>
 __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P,
@@ -34,15 +43,23 @@ __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, G
     const float4 oi = xo[i];
     const int n = min(nn[i], max_nb);
     GSum acc;
-    for (int k = 0; k < n; ++k) {
-        const int e = nl[(int64_t)k * Np + i];
-        int j = entry_slot(e);
-        const float4 oj = xo[j];
-        float dx, dy, dz;
-        sep_mixed_entry<WIDE>(cs, oi, oj, e, dx, dy, dz);
-        float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2), species_pair<KIND>(P, oi, oj)));
-        if ((k & kGroupMask) == kGroupMask) acc.flush();
+    for (int k0 = 0; k0 < n; k0 += kMB) {
+        int eb[kMB];
+        float4 ob[kMB];
+#pragma unroll
+        for (int u = 0; u < kMB; ++u) eb[u] = k0 + u < n ? nl[(int64_t)(k0 + u) * Np + i] : 0;
+#pragma unroll
+        for (int u = 0; u < kMB; ++u) ob[u] = k0 + u < n ? xo[entry_slot(eb[u])] : oi;
+#pragma unroll
+        for (int u = 0; u < kMB; ++u) {
+            const int k = k0 + u;
+            if (k >= n) break;
+            float dx, dy, dz;
+            sep_mixed_entry<WIDE>(cs, oi, ob[u], eb[u], dx, dy, dz);
+            float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < P.f_rc2) acc.add(dens_ff<KIND>(P, r2 * rsqrtf(r2), species_pair<KIND>(P, oi, ob[u])));
+            if ((k & kGroupMask) == kGroupMask) acc.flush();
+        }
     }
     double r_i = acc.value();
     double F, Fpi;
@@ -53,11 +70,16 @@ __global__ void __launch_bounds__(kMNT) k_density_mixed(int64_t N, int64_t Np, G
     e_atom[i] = F;
 }
 
-// 12 blocks per multiprocessor (40 registers, a few spilled to L1): the
-// pass waits on gathered offsets and F', and the extra resident warps hide
-// more of that than the spills cost (measured 8% faster than 54 registers).
+// Resident blocks per multiprocessor: with one entry in flight per thread
+// the pass waits on gathered offsets and F', and 12 blocks (40 registers, a
+// few spilled to L1) hid more of that than the spills cost (8% faster than
+// 54 registers); with a batch of entries in flight the registers go to the
+// batch instead.
+#ifndef MD_MIXED_FORCE_BLOCKS
+#define MD_MIXED_FORCE_BLOCKS (kMB == 1 ? 12 : 8)
+#endif
 template <int KIND, bool SINGLE, bool WIDE>
-__global__ void __launch_bounds__(kMNT, 12) k_force_mixed(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P,
+__global__ void __launch_bounds__(kMNT, MD_MIXED_FORCE_BLOCKS) k_force_mixed(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P,
                                                       const float4* __restrict__ xo, const int* __restrict__ nn,
                                                       const int* __restrict__ nl, int max_nb,
                                                       const float* __restrict__ Fpf, double* __restrict__ f,
@@ -74,31 +96,44 @@ __global__ void __launch_bounds__(kMNT, 12) k_force_mixed(int64_t N, int64_t Np,
     // w_atom (pressure users only): per-atom virial -1/2 sum_j s_ij r_ij^2
     const bool vir = w_atom != nullptr;
     GSum ax, ay, az, ae, aw;
-    for (int k = 0; k < n; ++k) {
-        if ((k & kGroupMask) == 0 && k) {
-            ax.flush();
-            ay.flush();
-            az.flush();
-            ae.flush();
-            if (vir) aw.flush();
+    for (int k0 = 0; k0 < n; k0 += kMB) {
+        int eb[kMB];
+        float4 ob[kMB];
+        float fb[kMB];
+#pragma unroll
+        for (int u = 0; u < kMB; ++u) eb[u] = k0 + u < n ? nl[(int64_t)(k0 + u) * Np + i] : 0;
+#pragma unroll
+        for (int u = 0; u < kMB; ++u) {
+            const bool ok = k0 + u < n;
+            ob[u] = ok ? xo[entry_slot(eb[u])] : oi;
+            fb[u] = ok ? Fpf[entry_slot(eb[u])] : 0.0f;
         }
-        const int e = nl[(int64_t)k * Np + i];
-        int j = entry_slot(e);
-        const float4 oj = xo[j];
-        float dx, dy, dz;
-        sep_mixed_entry<WIDE>(cs, oi, oj, e, dx, dy, dz);
-        float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < P.f_rc2) {
-            float rinv = rsqrtf(r2);
-            float r = r2 * rinv;
-            float phi, dphi, fr, dfr;
-            pair_allf<KIND>(P, r, phi, dphi, fr, dfr, species_pair<KIND>(P, oi, oj));
-            float s = (dphi + (Fpi + Fpf[j]) * dfr) * rinv;
-            ax.add(s * dx);
-            ay.add(s * dy);
-            az.add(s * dz);
-            ae.add(phi);
-            if (vir) aw.add(s * r2);
+#pragma unroll
+        for (int u = 0; u < kMB; ++u) {
+            const int k = k0 + u;
+            if (k >= n) break;
+            if ((k & kGroupMask) == 0 && k) {
+                ax.flush();
+                ay.flush();
+                az.flush();
+                ae.flush();
+                if (vir) aw.flush();
+            }
+            float dx, dy, dz;
+            sep_mixed_entry<WIDE>(cs, oi, ob[u], eb[u], dx, dy, dz);
+            float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < P.f_rc2) {
+                float rinv = rsqrtf(r2);
+                float r = r2 * rinv;
+                float phi, dphi, fr, dfr;
+                pair_allf<KIND>(P, r, phi, dphi, fr, dfr, species_pair<KIND>(P, oi, ob[u]));
+                float s = (dphi + (Fpi + fb[u]) * dfr) * rinv;
+                ax.add(s * dx);
+                ay.add(s * dy);
+                az.add(s * dz);
+                ae.add(phi);
+                if (vir) aw.add(s * r2);
+            }
         }
     }
     double fx = ax.value(), fy = ay.value(), fz = az.value();

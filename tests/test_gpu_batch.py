@@ -94,3 +94,42 @@ def test_mixed_precision_batch_uses_the_tile_schedule():
         s.batch_step(2, schedule="box")
     s.batch_step(10, schedule="auto")
     assert s.schedule()["choice"] == "tile"
+
+
+@pytest.mark.parametrize("spec,n_cells,temp", [(I.RGL_CU, 8, 300.0), (I.SC_CU, 6, 1200.0)])
+def test_small_single_box_kernels_give_the_box_schedule_bits(spec, n_cells, temp):
+    """A single box of a few thousand atoms takes the small-system float64
+    kernels (one thread per pair row; sums staged in shared memory); its
+    trajectory equals, bit for bit, the block-per-box schedule's (whose
+    passes equal the large-system kernels', as the test above checks).
+    Sutton-Chen lists (140 entries) span several staged chunks."""
+    import torch
+    from paper_1212_6332_gb300.md import System
+    bx = I.perturbed_fcc(n_cells, I.A_CU, temp, I.MASS_CU, seed=90 + n_cells)
+    one = System(spec, box=bx.box, n_atoms=bx.n, skin=0.3, mass=I.MASS_CU)
+    one.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+    th = one.step(60, history=True, use_graph=True)
+    offs = np.array([0, bx.n], dtype=np.int64)
+    b = System(spec, boxes=bx.box[None, :], atom_offsets=offs, skin=0.3, mass=I.MASS_CU)
+    b.set_state(torch.tensor(bx.x, device="cuda"), torch.tensor(bx.v, device="cuda"))
+    b.batch_step(60, schedule="box")
+    (x1, v1), (x2, v2) = one.get_state(), b.get_state()
+    assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+    assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy())
+    assert th["n_rebuild"] >= 1
+    f1, f2 = one.get_forces(), b.get_forces()
+    assert np.array_equal(f1["f"].cpu().numpy(), f2["f"].cpu().numpy())
+
+
+def test_small_batch_tile_equals_box_schedule():
+    """Sixteen boxes (under the small-system threshold, per-box geometry):
+    the tile schedule's small kernels and the box schedule agree bit for bit."""
+    bt = small_batch(16, seed=21)
+    assert int(bt.atom_offsets[-1]) <= 32768
+    a, b = batch_system(bt), batch_system(bt)
+    ta = a.batch_step(50, schedule="tile").cpu().numpy()
+    tb = b.batch_step(50, schedule="box").cpu().numpy()
+    (xa, va), (xb, vb) = a.get_state(), b.get_state()
+    assert np.array_equal(xa.cpu().numpy(), xb.cpu().numpy())
+    assert np.array_equal(va.cpu().numpy(), vb.cpu().numpy())
+    assert np.array_equal(ta, tb)
