@@ -230,7 +230,63 @@ __global__ void __launch_bounds__(kNlThreads) k_build_list(int n_cells, Geo g, c
 }
 
 // raw: the lists as built (ascending), in the reverse-index array, which
-// k_build_rev overwrites next
+// k_build_rev overwrites next. Tiles of 32 consecutive atoms: the block
+// loads the tile's rows of raw into shared memory (row k of 32 atoms is one
+// 128-byte line), finds each list's split, and writes the rotated rows back
+// as whole lines and each lower part as one contiguous run of nl_lo: the
+// arrays of rotate_list_from, with every global access coalesced (the
+// thread-per-atom form gathers one 4-byte word per lane from 32 rows).
+constexpr int kRotNT = 128;
+constexpr size_t kRotSmemMax = 200 * 1024;  // lists up to 1600 entries per atom
+
+__global__ void __launch_bounds__(kRotNT) k_rotate_tiles(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn,
+                                                         const int* __restrict__ raw, int* __restrict__ nl,
+                                                         int* __restrict__ nl_lo, int max_nb, int* __restrict__ n_up,
+                                                         const Ctl* ctl, const unsigned long long* __restrict__ disp,
+                                                         int mode, unsigned long long thr) {
+    if (load_status(ctl)) return;
+    extern __shared__ int s_tile[];  // [max_nb][32]
+    __shared__ int s_lo[32];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int64_t n_tiles = (N + 31) / 32;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t i = tile * 32 + lane;
+        const bool due = i < N && box_due(disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr);
+        const int n = due ? min(nn[i], max_nb) : 0;
+        const int kmax = warp_max(n);
+        for (int k = wq; k < kmax; k += kRotNT / 32) s_tile[k * 32 + lane] = k < n ? raw[(int64_t)k * Np + i] : 0;
+        __syncthreads();
+        if (wq == 0) {
+            int lo = 0;
+            if (n > kRotMax) {
+                lo = n;  // kept ascending: the whole list is its searchable part
+            } else {
+                while (lo < n && entry_slot(s_tile[lo * 32 + lane]) < i) ++lo;
+            }
+            if (due) n_up[i] = n > kRotMax ? -1 : n - lo;
+            s_lo[lane] = lo;
+        }
+        __syncthreads();
+        // lower parts, row-major: a warp per atom, lanes along the run
+        for (int a = wq; a < 32; a += kRotNT / 32) {
+            const int lo = s_lo[a];
+            int* out = nl_lo + (tile * 32 + a) * (int64_t)max_nb;
+            for (int m = lane; m < lo; m += 32) out[m] = s_tile[m * 32 + a];
+        }
+        // rotated rows [upper | lower], whole lines
+        const int lo = s_lo[lane];
+        const bool rot = n <= kRotMax;
+        for (int k = wq; k < kmax; k += kRotNT / 32) {
+            if (k < n) {
+                int src = k;
+                if (rot) src = k + lo < n ? k + lo : k + lo - n;
+                nl[(int64_t)k * Np + i] = s_tile[src * 32 + lane];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_rotate_lists(int64_t N, int64_t Np, Geo g, const int* __restrict__ nn,
                                const int* __restrict__ raw, int* __restrict__ nl, int* __restrict__ nl_lo,
                                int max_nb, int* __restrict__ n_up, const Ctl* ctl,
@@ -306,8 +362,17 @@ void launch_build_list(Engine& e, int mode, cudaStream_t s) {
     if (e.rev) {
         // grid-stride over the atoms with four waves of resident blocks
         int nb = (int)std::min<int64_t>((e.N + 255) / 256, (int64_t)32 * e.n_sm);
-        k_rotate_lists<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.rev, e.nl, e.nl_lo, e.max_nb, e.n_up, e.ctl,
-                                          e.disp_box, mode, thr);
+        const size_t rot_smem = (size_t)e.max_nb * 32 * sizeof(int);
+        if (rot_smem <= kRotSmemMax) {
+            if (rot_smem > 48 * 1024)
+                cudaFuncSetAttribute(k_rotate_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem);
+            const int nt = (int)std::min<int64_t>((e.N + 31) / 32, (int64_t)16 * e.n_sm);
+            k_rotate_tiles<<<nt, kRotNT, rot_smem, s>>>(e.N, e.N_pad, g, e.nn, e.rev, e.nl, e.nl_lo, e.max_nb,
+                                                       e.n_up, e.ctl, e.disp_box, mode, thr);
+        } else {
+            k_rotate_lists<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.rev, e.nl, e.nl_lo, e.max_nb, e.n_up, e.ctl,
+                                              e.disp_box, mode, thr);
+        }
         k_build_rev<<<nb, 256, 0, s>>>(e.N, e.N_pad, g, e.nn, e.nl, e.nl_lo, e.max_nb, e.n_up, e.rev, e.ctl,
                                        e.disp_box, mode, thr);
         e.launches += 2;
