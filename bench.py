@@ -680,7 +680,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the headline box (default float64)")
     ap.add_argument("--batch-boxes", type=int, default=0,
-                    help="only the tile-schedule batch leg with this many boxes (profiling runs; prints its dict)")
+                    help="only the batch leg with this many boxes (profiling runs; prints its dict)")
+    ap.add_argument("--schedule", default="tile", choices=["tile", "box"],
+                    help="schedule of the --batch-boxes leg")
     ap.add_argument("--alloy-only", action="store_true",
                     help="only the two-species spline alloy box of --cells (profiling runs; prints its dict)")
     ap.add_argument("--grad-only", default="", choices=["", "rgl", "spline", "alloy"],
@@ -702,7 +704,7 @@ def main():
     from paper_1212_6332_gb300 import build
     build.build()
     if args.batch_boxes:
-        print(json.dumps(run_batch(args.precision, K, W, n_boxes=args.batch_boxes)))
+        print(json.dumps(run_batch(args.precision, K, W, n_boxes=args.batch_boxes, schedule=args.schedule)))
         return
     if args.grad_only:
         print(json.dumps(run_grad(K, W, args.precision, args.grad_only)))

@@ -210,6 +210,10 @@ void fill_pot(Engine& e) {
             c[f][2] = -b[f] * b[f] * b[f] / 6.0;
             c[f][3] = b[f] * b[f] * b[f] * b[f] / 24.0;
         }
+        P.rx_f1[0] = (float)P.rx_c1[2];
+        P.rx_f1[1] = (float)P.rx_c1[3];
+        P.rx_f2[0] = (float)P.rx_c2[2];
+        P.rx_f2[1] = (float)P.rx_c2[3];
     }
     P.f_rc2 = (float)P.rc2;
     P.f_rs = (float)P.rs;

@@ -412,18 +412,27 @@ __device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict
     const bool tap = __double_as_longlong(r2) > __double_as_longlong(P.rs2);
     if (KIND == MD_POT_RGL) {
         double e1, e2;
-        // r = k h + d with k the nearest integer (the 1.5 * 2^52 shift puts
-        // it in the low word), d exact; both exponentials share it
-        const double shift = 6755399441055744.0;
-        const double t = fma(r, kRxPerA, shift);
-        const int kk = __double2loint(t) - P.rx_k0;
+        // r = k h + d with k an integer next to r/h, chosen in float32 from
+        // a float32 copy of r (integer and float32 pipes; k may be the
+        // neighbour of the nearest one next to a half point, |d| <= h/2 +
+        // 1e-6 A), d exact from one fused multiply-add; both exponentials
+        // share it
+        const int k = __float2int_rn(narrow_f32(r) * (float)kRxPerA);
+        const int kk = k - P.rx_k0;
         if (P.rx && (unsigned)kk < (unsigned)P.rx_n) {
-            const double d = fma(-(t - shift), 1.0 / kRxPerA, r);
+            const double d = fma(widen_f32((float)k), -1.0 / kRxPerA, r);
             const double2 E = P.rx[kk];
-            const double R1 = fma(fma(fma(P.rx_c1[3], d, P.rx_c1[2]), d, P.rx_c1[1]), d, P.rx_c1[0]);
-            const double R2 = fma(fma(fma(P.rx_c2[3], d, P.rx_c2[2]), d, P.rx_c2[1]), d, P.rx_c2[0]);
-            e1 = fma(E.x * d, R1, E.x);
-            e2 = fma(E.y * d, R2, E.y);
+            // e^(-b d) = 1 + d (c0 + c1 d) + d^3 (c2 + c3 d): the first two
+            // orders in float64, the rest (below |b d|^3/6 < 6e-9 for
+            // |d| <= 1/2048 A and b <= 7 / A) in float32, whose error of a few
+            // 1e-7 of that term stays below 1e-15 of the result; d and the
+            // term cross between the precisions on the integer pipe
+            const float df = narrow_f32_signed(d);
+            const float d3 = df * df * df;
+            const double h1 = widen_f32(d3 * fmaf(P.rx_f1[1], df, P.rx_f1[0]));
+            const double h2 = widen_f32(d3 * fmaf(P.rx_f2[1], df, P.rx_f2[0]));
+            e1 = fma(E.x, fma(d, fma(P.rx_c1[1], d, P.rx_c1[0]), h1), E.x);
+            e2 = fma(E.y, fma(d, fma(P.rx_c2[1], d, P.rx_c2[0]), h2), E.y);
         } else {
             // the prefactors 2A and xi^2 ride in the exponent when both are positive
             e1 = P.fold ? exp_tab(P.pA - P.p_r0 * r, T, P.ek) : P.A2 * exp_tab(P.p - P.p_r0 * r, T, P.ek);

@@ -72,6 +72,7 @@ struct Pot {
     const double2* rx;  // [rx_n] (E1_k, E2_k); null: no table
     int rx_k0, rx_n;
     double rx_c1[4], rx_c2[4];  // R_1, R_2 coefficients: -b, b^2/2, -b^3/6, b^4/24
+    float rx_f1[2], rx_f2[2];   // float32 copies of the d^3 and d^4 coefficients
     // float copies for the mixed-precision path
     float f_rc2, f_rs, f_inv_w, f_A2, f_xi2, f_p, f_p_r0, f_q2, f_q2_r0, f_eps, f_a, f_n, f_m;
 };

@@ -62,6 +62,28 @@ __device__ __forceinline__ float narrow_f32(double x) {
     return __uint_as_float((hi << 3) | (lo >> 29));
 }
 
+// float32 copy of a double of either sign with |x| < 2^128, mantissa
+// truncated, formed on the integer pipe; |x| below the float32 normal range
+// gives 0.
+__device__ __forceinline__ float narrow_f32_signed(double x) {
+    const int kRebias = (1023 - 127) << 20;
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned ahi = hi & 0x7fffffffu;
+    if (ahi < (unsigned)(kRebias + (1 << 20))) return 0.0f;
+    const unsigned lo = (unsigned)__double2loint(x);
+    return __uint_as_float(((ahi - kRebias) << 3) | (lo >> 29) | (hi & 0x80000000u));
+}
+
+// The double of a float32 value (exact), formed on the integer pipe;
+// zero and subnormal inputs give 0.
+__device__ __forceinline__ double widen_f32(float f) {
+    const int kRebias = (1023 - 127) << 20;
+    const unsigned u = __float_as_uint(f);
+    const unsigned a = u & 0x7fffffffu;
+    if (a < 0x00800000u) return 0.0;
+    return __hiloint2double((int)(((a >> 3) + kRebias) | (u & 0x80000000u)), (int)(a << 29));
+}
+
 __device__ __forceinline__ double rsqrt_nr(double x) {
     const int kRebias = (1023 - 127) << 20;
     const unsigned yb = __float_as_uint(rsqrtf(narrow_f32(x)));
