@@ -563,7 +563,7 @@ def run_grad(K: int, W: int, precision: str = "fp64", kind: str = "rgl") -> dict
     (or its 3 x 200-knot spline tabulation, or the two-species alloy_model
     with U{0, 1} labels: 3 V + 3 rho + 2 F tables of 200 knots)."""
     import torch
-    from paper_1212_6332_gb300.fit import ForceField, force_matching_loss, make_batch, theta_of
+    from paper_1212_6332_gb300.fit import ForceField, config_index, force_matching_loss, make_batch, theta_of
     cfgs = [I.strained_fcc(6, I.A_CU, seed=5000 + k) for k in range(256)]
     n = sum(c.n for c in cfgs)
     ref = make_batch(I.RGL_CU, cfgs)
@@ -581,11 +581,12 @@ def run_grad(K: int, W: int, precision: str = "fp64", kind: str = "rgl") -> dict
         types = (I.uniform(78, n) < 0.5).astype(np.int32)
     s = make_batch(model, cfgs, precision=precision, types=types)
     counts = torch.tensor([c.n for c in cfgs], device="cuda", dtype=torch.float64)
+    idx = config_index(counts)
     theta = theta_of(model).cuda().requires_grad_(True)
 
     def once():
         f, e = ForceField.apply(theta, s, model)
-        L = force_matching_loss(f, e, f_tgt, e_tgt, counts)
+        L = force_matching_loss(f, e, f_tgt, e_tgt, counts, idx=idx)
         (g,) = torch.autograd.grad(L, theta)
         return L, g
 

@@ -56,7 +56,7 @@ class ForceField(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, system: System, template: dict):
         system.set_potential(spec_of(theta, template))
-        f = system.get_forces()["f"]
+        f = system.get_forces(e_atom=False, rho=False)["f"]
         e_box = system.batch_thermo()[:, 1].contiguous()
         ctx.system = system
         ctx.dev = theta.device
@@ -71,11 +71,20 @@ class ForceField(torch.autograd.Function):
         return grad.to(ctx.dev), None, None
 
 
-def force_matching_loss(f, e_box, f_tgt, e_tgt, counts, w_e: float = 0.1):
+def config_index(counts: torch.Tensor) -> torch.Tensor:
+    """Configuration of every atom (configurations back to back). Building
+    it waits for the device (the output size depends on the counts), so a
+    fitting loop builds it once and passes it to force_matching_loss."""
+    return torch.repeat_interleave(torch.arange(counts.shape[0], device=counts.device), counts.long())
+
+
+def force_matching_loss(f, e_box, f_tgt, e_tgt, counts, w_e: float = 0.1, idx=None):
     """Mean over configurations of mean squared force error plus w_e times
-    the squared per-atom energy error."""
+    the squared per-atom energy error. idx: config_index(counts), built
+    here when not given."""
     n_cfg = counts.shape[0]
-    idx = torch.repeat_interleave(torch.arange(n_cfg, device=f.device), counts.long())
+    if idx is None:
+        idx = config_index(counts)
     sq = ((f - f_tgt) ** 2).sum(dim=1)
     per_cfg = torch.zeros(n_cfg, dtype=f.dtype, device=f.device).index_add_(0, idx, sq) / (3.0 * counts)
     de = (e_box - e_tgt) / counts

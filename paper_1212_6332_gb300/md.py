@@ -277,10 +277,14 @@ class System:
                                                _stream()))
         return dict(f=f, e_atom=e_atom, rho=rho, energy=energy)
 
-    def get_forces(self):
-        f, e, r = self._empty(self.n, 3), self._empty(self.n), self._empty(self.n)
-        self._check(self.lib.md_get_forces(self._h, _ptr(f), _ptr(e), _ptr(r), _stream()))
-        return dict(f=f, e_atom=e, rho=r)
+    def get_forces(self, f: bool = True, e_atom: bool = True, rho: bool = True):
+        """Forces, per-atom energies and densities of the current state (the
+        ones not asked for are not copied)."""
+        fo = self._empty(self.n, 3) if f else None
+        e = self._empty(self.n) if e_atom else None
+        r = self._empty(self.n) if rho else None
+        self._check(self.lib.md_get_forces(self._h, _ptr(fo), _ptr(e), _ptr(r), _stream()))
+        return dict(f=fo, e_atom=e, rho=r)
 
     def build_neighbors(self):
         self._check(self.lib.md_build_neighbors(self._h, _stream()))

@@ -130,3 +130,10 @@ def test_batch_offsets_must_not_decrease(lib):
     rc = lib.md_batch_create(ctypes.byref(cfg), ctypes.byref(pot), 2, ctypes.c_void_p(offs.ctypes.data),
                              ctypes.c_void_p(boxes.ctypes.data), ctypes.byref(h))
     assert rc == 1 and "decrease" in lib.md_last_error(None).decode()
+
+
+def test_fma_probe_rejects_bad_arguments_before_any_cuda_call(lib):
+    d, m, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    assert lib.md_fma_probe(2, 16, ctypes.byref(d), ctypes.byref(m), ctypes.byref(n), None) == 1
+    assert lib.md_fma_probe(0, 0, ctypes.byref(d), ctypes.byref(m), ctypes.byref(n), None) == 1
+    assert lib.md_fma_probe(1, 16, None, ctypes.byref(m), ctypes.byref(n), None) == 1

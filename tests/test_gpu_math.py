@@ -106,3 +106,15 @@ def test_rgl_pair_functions_from_the_r_table(spec):
     # of it or more)
     tap = inside & ~flat
     assert ferr[tap].max() <= 1e-8 * fmag[tap].max(), (ferr[tap].max(), r[tap][np.argmax(ferr[tap])])
+
+
+def test_fma_probe_measures_both_pipes():
+    """md_fma_probe (the roofline denominators): a positive float64 and a
+    larger float32 FMA rate, and the device's multiprocessor count."""
+    import torch
+    from paper_1212_6332_gb300 import md
+    r64 = md.fma_probe("fp64", 256)
+    r32 = md.fma_probe("fp32", 4096)
+    assert r64["n_sm"] == torch.cuda.get_device_properties(0).multi_processor_count
+    assert r64["flops"] > 1e11 and r32["flops"] > 8 * r64["flops"]
+    assert r64["ms"] > 0 and r32["ms"] > 0
