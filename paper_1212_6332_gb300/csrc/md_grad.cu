@@ -734,6 +734,64 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline_mixed(int64_t N, int64
     for (int k = threadIdx.x; k < ncoef; k += NT) partial[(int64_t)blockIdx.x * ncoef + k] = sg[k];
 }
 
+// The same histogram with every pair visited once, from the atom of the
+// lower slot (the upper rows of its rotated list, or its entries j > i when
+// the list was kept ascending): the adjoint weights of (i, j) and (j, i)
+// add up (values 2 (g_E / 2) and a_F,i + a_F,j, slopes w_i + w_j =
+// (g_i - g_j) . d / r), the type pair and r are the same from both sides,
+// so one visit adds their sum. Half the geometry and the shared-memory
+// atomics.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_grad_param_spline_pairs(int64_t N, int64_t Np, Geo g, Pot P,
+                                                                const double4_32a* __restrict__ x,
+                                                                const int* __restrict__ nn,
+                                                                const int* __restrict__ nl,
+                                                                const int* __restrict__ n_up, int max_nb,
+                                                                const double* __restrict__ gs,
+                                                                const double* __restrict__ gE,
+                                                                const double* __restrict__ rho,
+                                                                const double* __restrict__ Fp,
+                                                                const double* __restrict__ Fpp,
+                                                                const double* __restrict__ u, int ncoef,
+                                                                double* __restrict__ partial) {
+    extern __shared__ double sg[];  // [ncoef], as in k_grad_param_spline
+    for (int k = threadIdx.x; k < ncoef; k += NT) sg[k] = 0.0;
+    __syncthreads();
+    const int np_ = P.n_types * (P.n_types + 1) / 2;
+    const int cV = 4 * (P.sn[0] - 1), cR = 4 * (P.sn[1] - 1), cF = 4 * (P.sn[2] - 1);
+    double* gV = sg;
+    double* gR = sg + np_ * cV;
+    double* gF = gR + np_ * cR;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int nup = n_up[i];
+        const int n = nup < 0 ? min(nn[i], max_nb) : nup;
+        const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
+        const double ge = box_gE(g, gE, i);
+        const double Fpi = Fp[i];
+        const double aFi = u[i] * Fpp[i] + ge * Fpi;
+        for (int k = 0; k < n; ++k) {
+            const int e = nl[(int64_t)k * Np + i];
+            const int j = entry_slot(e);
+            if (j <= i) continue;
+            double dx, dy, dz;
+            sep(g, x, i, j, dx, dy, dz);
+            double r2 = norm2(dx, dy, dz);
+            if (r2 >= P.rc2) continue;
+            double r = sqrt(r2);
+            if (r >= P.rc) continue;
+            const double W = ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) / r;
+            const double AF = aFi + (u[j] * Fpp[j] + ge * Fp[j]);
+            const int pt = pair_tab<MD_POT_SPLINE>(P, x, i, j);
+            spline_adj(P, 0, r, ge, W, gV + pt * cV);
+            spline_adj(P, 1, r, AF, W * (Fpi + Fp[j]), gR + pt * cR);
+        }
+        // embedding: u_i dF'/dtheta + gE dF/dtheta at rho_i
+        spline_adj(P, 2, rho[i], ge, u[i], gF + atom_tab<MD_POT_SPLINE>(P, x, i) * cF);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < ncoef; k += NT) partial[(int64_t)blockIdx.x * ncoef + k] = sg[k];
+}
+
 // Spline coefficient count over all tables: P pair tables each for V and rho,
 // T embedding tables, 4 (n - 1) coefficients per table.
 static int spline_ncoef(const Engine& e) {
@@ -826,9 +884,14 @@ static int grad_impl(Engine& e, const double* g_f, const double* g_e, double* gr
     } else {
         int ncoef = spline_ncoef(e);
         size_t smem = (size_t)ncoef * sizeof(double);
-        k_grad_param_spline<kGNT><<<npb, kGNT, smem, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb,
-                                                          e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp, e.grad_u, ncoef,
-                                                          e.grad_partial);
+        if (e.n_up)
+            k_grad_param_spline_pairs<kGNT><<<npb, kGNT, smem, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.n_up,
+                                                                    e.max_nb, e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp,
+                                                                    e.grad_u, ncoef, e.grad_partial);
+        else
+            k_grad_param_spline<kGNT><<<npb, kGNT, smem, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb,
+                                                              e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp, e.grad_u, ncoef,
+                                                              e.grad_partial);
         k_sum_partials<<<ncoef, 256, 0, s>>>(npb, ncoef, e.grad_partial, e.grad_coef);
         launch_spline_adjoint(e, grad, s);
         e.launches += 3;
@@ -857,6 +920,8 @@ int launch_param_grad(Engine& e, const double* g_f, const double* g_e, double* g
                           : grad_mixed_impl<MD_POT_SPLINE, false>(e, g_f, g_e, grad, s);
         if ((size_t)ncoef * sizeof(double) > 48 * 1024) {
             cudaFuncSetAttribute(k_grad_param_spline<kGNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(ncoef * sizeof(double)));
+            cudaFuncSetAttribute(k_grad_param_spline_pairs<kGNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(ncoef * sizeof(double)));
         }
         return grad_impl<MD_POT_SPLINE>(e, g_f, g_e, grad, s);
