@@ -116,9 +116,9 @@ FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 STEP_BYTES = lambda K: 2 * 4.0 * K + 2 * 24.0  # noqa: E731
 # DRAM bytes (read + write) per atom of one k_pairs_half launch, from an ncu
 # capture of 1,048,576 atoms of the same lattice, potential and temperature
-# (0.454 GB read + 1.772 GB written); traffic grows in proportion to the
-# atom count.
-PAIRS_DRAM_BYTES_PER_ATOM = (0.453648e9 + 1.771678e9) / 1048576
+# (0.453 GB read + 1.777 GB written; profiles/k_pairs_half_rgl_cu_1m_fp64.md);
+# traffic grows in proportion to the atom count.
+PAIRS_DRAM_BYTES_PER_ATOM = (0.452660224e9 + 1.777106e9) / 1048576
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
            0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
@@ -376,10 +376,21 @@ def oracle_grad_sample(n_cfg: int = 8) -> dict:
                 sample=f"oracle forward-mode gradient on {n_cfg} of the 256 configurations, scaled to 256")
 
 
-def workload_name(cells: int, precision: str) -> str:
+# Single-box workloads of the --spec option (profiling runs; the default
+# is the timed 4M-atom Cu box): potential, lattice constant, mass,
+# temperature, seed and name.
+SPECS = {
+    "rgl_cu": (I.RGL_CU, I.A_CU, I.MASS_CU, TEMP, SEED, "fcc Cu", "RGL Cu taper 4.5-5.0 A"),
+    "sc_cu": (I.SC_CU, I.A_CU, I.MASS_CU, TEMP, SEED, "fcc Cu", "Sutton-Chen Cu taper 6.92-7.22 A"),
+    "rgl_ni": (I.RGL_NI, I.A_NI, I.MASS_NI, 600.0, 3, "fcc Ni", "RGL Ni taper 4.3-4.8 A"),
+}
+
+
+def workload_name(cells: int, precision: str, spec: str = "rgl_cu") -> str:
     """The timed single-box workload, named by what it is."""
-    return (f"fcc Cu {cells}^3 cells ({4 * cells ** 3} atoms), RGL Cu taper 4.5-5.0 A, skin {SKIN} A, "
-            f"{TEMP:.0f} K, dt {DT} fs, " + ("float64" if precision == "fp64" else "mixed precision"))
+    _, _, _, temp, _, lat, pot = SPECS[spec]
+    return (f"{lat} {cells}^3 cells ({4 * cells ** 3} atoms), {pot}, skin {SKIN} A, "
+            f"{temp:.0f} K, dt {DT} fs, " + ("float64" if precision == "fp64" else "mixed precision"))
 
 
 def run_reference(args):
@@ -684,6 +695,8 @@ def main():
                     help="only the batch leg with this many boxes (profiling runs; prints its dict)")
     ap.add_argument("--schedule", default="tile", choices=["tile", "box"],
                     help="schedule of the --batch-boxes leg")
+    ap.add_argument("--spec", default="rgl_cu", choices=sorted(SPECS),
+                    help="potential and lattice of the single box (profiling runs; the timed workload is rgl_cu)")
     ap.add_argument("--alloy-only", action="store_true",
                     help="only the two-species spline alloy box of --cells (profiling runs; prints its dict)")
     ap.add_argument("--grad-only", default="", choices=["", "rgl", "spline", "alloy"],
@@ -722,13 +735,14 @@ def main():
     hbm = mp.get("hbm_gbs", 6800.0)
     hbm_src = "fallback" if "fallback" in mp else "measured"
 
-    bx = I.perturbed_fcc(args.cells, I.A_CU, TEMP, I.MASS_CU, SEED)
+    pspec, a_lat, mass, temp, seed, _, _ = SPECS[args.spec]
+    bx = I.perturbed_fcc(args.cells, a_lat, temp, mass, seed)
     N = bx.n
     x_dev = torch.tensor(bx.x, device="cuda")
     v_dev = torch.tensor(bx.v, device="cuda")
-    s = System(I.RGL_CU, box=bx.box, n_atoms=N, skin=SKIN, dt=DT, mass=I.MASS_CU, precision=args.precision)
+    s = System(pspec, box=bx.box, n_atoms=N, skin=SKIN, dt=DT, mass=mass, precision=args.precision)
     s.set_state(x_dev, v_dev)
-    K_list, K_in = list_stats(s, x_dev, bx.box, I.RGL_CU["r_cut"])
+    K_list, K_in = list_stats(s, x_dev, bx.box, pspec["r_cut"])
     s.step(W, use_graph=True)
 
     def barrier():
@@ -761,7 +775,7 @@ def main():
     phase_sum = sum(phase_ms.values())
 
     # dominant kernel of the headline against the measured float64 FMA rate
-    kind = "rgl"
+    kind = pspec["kind"]
     main_block = roofline_block(prof, N, args.precision, kind, K_list, K_in, peaks, hbm)
     dom = main_block["phase"]
     alu = main_block.get("alu", {})
@@ -771,7 +785,8 @@ def main():
                                f"FMA rate in this run ({peaks['sm_count']} SMs, "
                                f"SM clock {peaks['clocks'].get('sm_mhz')} MHz); derived "
                                f"{FP64_DERIVED_TFLOPS:.3f} TFLOP/s float64 from unit counts",
-                "traffic": (PAIRS_DRAM_BYTES_PER_ATOM * N if dom == "pairs" and args.precision == "fp64" else None),
+                "traffic": (PAIRS_DRAM_BYTES_PER_ATOM * N
+                            if dom == "pairs" and args.precision == "fp64" and args.spec == "rgl_cu" else None),
                 "traffic_source": "ncu capture of 1,048,576 atoms scaled by the atom count",
                 "flops_per_launch": alu.get("flops_per_launch"), "launch_ms": main_block["launch_ms"],
                 "launch_ms_source": "CUDA events around each launch of the kernel on its stream, over K steps "
@@ -905,7 +920,7 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-               "config": {"workload": workload_name(args.cells, args.precision),
+               "config": {"workload": workload_name(args.cells, args.precision, args.spec),
                           "atoms": N, "parallelism": "replicas" if world > 1 else "single",
                           "l2": "working set (list + positions) larger than L2",
                           "timing": "md_step with CUDA-graph replay (the user path); phases from K further "
