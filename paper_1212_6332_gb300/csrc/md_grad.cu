@@ -169,32 +169,60 @@ __global__ void __launch_bounds__(kGNT) k_grad_embed(int64_t N, Pot P, const dou
     Fpp[i] = Fppi;
 }
 
+__device__ __forceinline__ bool zero_entry(double2 c) {
+    return (__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0;
+}
+
 // u_i = sum_j (g_i - g_j) . d_ij rho'(r)/r with rho'/r from the cache and
-// d_ij from the entry's image (zero cache entries lie beyond r_cut)
+// d_ij from the entry's image (zero cache entries lie beyond r_cut). Each
+// lane steps to its own next non-zero entry, so the float64 work of an
+// iteration runs with nearly all lanes active (a branch over the zero
+// entries leaves them masked); the sum keeps its order.
 __global__ void __launch_bounds__(kGNT) k_grad_u_cached(int64_t N, int64_t Np, Geo g,
                                                         const double4_32a* __restrict__ x,
                                                         const int* __restrict__ nn, const int* __restrict__ nl,
                                                         int max_nb, const double4_32a* __restrict__ pc,
                                                         const double* __restrict__ gs, double* __restrict__ u) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int b = g.B == 1 ? 0 : g.atom_box[i];
-    const double L[3] = {g.L[3 * b], g.L[3 * b + 1], g.L[3 * b + 2]};
-    const double4_32a xi = x[i];
-    const int n = min(nn[i], max_nb);
-    const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
-    double acc = 0.0;
-    for (int k = 0; k < n; ++k) {
-        const int64_t slot = (int64_t)k * Np + i;
-        const double2 c = cache_ab(pc, slot);
-        if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
-        const int e = nl[slot];
-        const int j = entry_slot(e);
-        double dx, dy, dz;
-        sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
-        acc += ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * c.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < N;
+    double L[3] = {0.0, 0.0, 0.0};
+    double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    int n = 0;
+    if (active) {
+        const int b = g.B == 1 ? 0 : g.atom_box[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) L[a] = g.L[3 * b + a];
+        xi = x[i];
+        n = min(nn[i], max_nb);
+        gx = gs[i];
+        gy = gs[Np + i];
+        gz = gs[2 * Np + i];
     }
-    u[i] = acc;
+    const double2 zero = make_double2(0.0, 0.0);
+    double acc = 0.0;
+    int k = 0;
+    double2 c = n > 0 ? cache_ab(pc, i) : zero;
+    while (true) {
+        while (k < n && zero_entry(c)) {
+            ++k;
+            c = k < n ? cache_ab(pc, (int64_t)k * Np + i) : zero;
+        }
+        const bool has = k < n;
+        if (!__any_sync(0xffffffffu, has)) break;
+        if (has) {
+            const int64_t slot = (int64_t)k * Np + i;
+            const double2 cn = k + 1 < n ? cache_ab(pc, slot + Np) : zero;
+            const int e = nl[slot];
+            const int j = entry_slot(e);
+            double dx, dy, dz;
+            sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
+            acc += ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * c.y;
+            ++k;
+            c = cn;
+        }
+    }
+    if (active) u[i] = acc;
 }
 
 // RGL parameter terms from the cached values: with u = r/r0 - 1,
@@ -278,25 +306,48 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_pairs(int64_t N, int64_
                                                                double two_inv_xi, double* __restrict__ partial) {
     __shared__ double sh[kGNT / 32];
     const double inv_r0 = 1.0 / P.r0, inv_r02 = inv_r0 * inv_r0, pp = P.p, q2 = P.q2;
+    const double2 zero = make_double2(0.0, 0.0);
     double acc[kRglParams] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int b = g.B == 1 ? 0 : g.atom_box[i];
-        const double L[3] = {g.L[3 * b], g.L[3 * b + 1], g.L[3 * b + 2]};
-        const double4_32a xi = x[i];
-        const int nup = n_up[i];
-        const int n = nup < 0 ? min(nn[i], max_nb) : nup;
-        const double gx = gs[i], gy = gs[Np + i], gz = gs[2 * Np + i];
-        const double ge = box_gE(g, gE, i);
-        const double Fpi = Fp[i];
-        const double aFi = u[i] * Fpp[i] + ge * Fpi;
+    // warp-uniform outer loop (all lanes take part in the vote below); each
+    // lane steps to its own next non-zero upper entry, as k_grad_u_cached
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool active = i < N;
+        double L[3] = {0.0, 0.0, 0.0};
+        double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        double gx = 0.0, gy = 0.0, gz = 0.0, ge = 0.0, Fpi = 0.0, aFi = 0.0;
+        int n = 0;
+        if (active) {
+            const int b = g.B == 1 ? 0 : g.atom_box[i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) L[a] = g.L[3 * b + a];
+            xi = x[i];
+            const int nup = n_up[i];
+            n = nup < 0 ? min(nn[i], max_nb) : nup;
+            gx = gs[i];
+            gy = gs[Np + i];
+            gz = gs[2 * Np + i];
+            ge = box_gE(g, gE, i);
+            Fpi = Fp[i];
+            aFi = u[i] * Fpp[i] + ge * Fpi;
+        }
         const double aV2 = ge;  // 1/2 g_E from each side
-        for (int k = 0; k < n; ++k) {
+        int k = 0;
+        double2 c = n > 0 ? cache_ab(pc, i) : zero;
+        while (true) {
+            // next non-zero entry of an upper row (an unrotated list also
+            // holds entries j < i, skipped here)
+            while (k < n && (zero_entry(c) || entry_slot(nl[(int64_t)k * Np + i]) <= i)) {
+                ++k;
+                c = k < n ? cache_ab(pc, (int64_t)k * Np + i) : zero;
+            }
+            const bool has = k < n;
+            if (!__any_sync(0xffffffffu, has)) break;
+            if (has) {
             const int64_t slot = (int64_t)k * Np + i;
-            const double2 c = cache_ab(pc, slot);
-            if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
+            const double2 cn = k + 1 < n ? cache_ab(pc, slot + Np) : zero;
             const int e = nl[slot];
             const int j = entry_slot(e);
-            if (j <= i) continue;
             const double2 fv = cache_fv(pc, slot);
             double dx, dy, dz;
             sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
@@ -314,6 +365,9 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_pairs(int64_t N, int64_
             acc[2] += -uu * tV - W * V * inv_r0;
             acc[3] += -2.0 * uu * tR - 2.0 * AFp * rh * inv_r0;
             acc[4] += pp * (c0 * tV + W * V * inv_r02) + q2 * (c0 * tR + AFp * rh * inv_r02);
+            ++k;
+            c = cn;
+            }
         }
     }
     for (int k = 0; k < kRglParams; ++k) {
