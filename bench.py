@@ -456,7 +456,7 @@ def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=N
     s.set_state(x_dev, torch.tensor(v_h, device="cuda"))
     Kl, Ki = list_stats(s, x_dev, box, spec.get("r_cut", spec.get("r_hi", 5.0)))
     del x_dev
-    s.step(W, use_graph=True)
+    th_w = s.step(W, use_graph=True)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
@@ -470,7 +470,8 @@ def run_variant(precision: str, W: int, K: int, x_h, v_h, box, spec=None, mass=N
     s.step(K)
     prof = s.profile_read()
     s.close()
-    return dict(value=len(x_h) * K / (ms * 1e-3), ms_per_step=ms / K, n_rebuild=th["n_rebuild"], graph=True,
+    return dict(value=len(x_h) * K / (ms * 1e-3), ms_per_step=ms / K, n_rebuild=th["n_rebuild"] - th_w["n_rebuild"],
+                graph=True,
                 phase_ms_per_step={k: v / max(K, 1) for k, v in prof["ms"].items()},
                 mean_list_len=Kl, mean_in_cutoff=Ki, _prof=prof)
 
@@ -486,7 +487,7 @@ def run_small(K: int, use_graph: bool) -> dict:
     x_dev = torch.tensor(bx.x, device="cuda")
     s.set_state(x_dev, torch.tensor(bx.v, device="cuda"))
     Kl, Ki = list_stats(s, x_dev, bx.box, I.RGL_CU["r_cut"])
-    s.step(K, use_graph=use_graph)
+    th_w = s.step(K, use_graph=use_graph)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
@@ -498,7 +499,7 @@ def run_small(K: int, use_graph: bool) -> dict:
     s.step(K)
     prof = s.profile_read()
     s.close()
-    return dict(value=bx.n * K / (ms * 1e-3), ms_per_step=ms / K, steps=K, n_rebuild=th["n_rebuild"],
+    return dict(value=bx.n * K / (ms * 1e-3), ms_per_step=ms / K, steps=K, n_rebuild=th["n_rebuild"] - th_w["n_rebuild"],
                 graph=use_graph, l2="working set inside L2", mean_list_len=Kl, mean_in_cutoff=Ki, atoms=bx.n,
                 phase_ms_per_step={k: v / max(K, 1) for k, v in prof["ms"].items()}, _prof=prof)
 
@@ -743,7 +744,7 @@ def main():
     s = System(pspec, box=bx.box, n_atoms=N, skin=SKIN, dt=DT, mass=mass, precision=args.precision)
     s.set_state(x_dev, v_dev)
     K_list, K_in = list_stats(s, x_dev, bx.box, pspec["r_cut"])
-    s.step(W, use_graph=True)
+    th_w = s.step(W, use_graph=True)
 
     def barrier():
         if dist is not None:
@@ -773,6 +774,13 @@ def main():
     prof = s.profile_read()
     phase_ms = {k: prof["ms"][k] / max(K, 1) for k in prof["ms"]}
     phase_sum = sum(phase_ms.values())
+    # the stretch may catch another number of list builds than the timed
+    # steps: the phase sum with its build time rescaled to the timed count
+    # (md_step counts builds since the state was set: differences per stretch)
+    reb_timed = th["n_rebuild"] - th_w["n_rebuild"]
+    reb_stretch = th_p["n_rebuild"] - th["n_rebuild"]
+    reb_fixed = phase_ms.get("rebuild", 0.0) * (reb_timed / reb_stretch if reb_stretch else 1.0)
+    phase_sum_same_builds = phase_sum - phase_ms.get("rebuild", 0.0) + reb_fixed
 
     # dominant kernel of the headline against the measured float64 FMA rate
     kind = pspec["kind"]
@@ -926,8 +934,9 @@ def main():
                           "timing": "md_step with CUDA-graph replay (the user path); phases from K further "
                                     "steps with per-phase events",
                           "mean_list_len": K_list, "mean_in_cutoff": K_in,
-                          "n_rebuild": th["n_rebuild"], "phase_ms_per_step": phase_ms,
-                          "phase_sum_ms": phase_sum, "phase_stretch_n_rebuild": th_p["n_rebuild"]},
+                          "n_rebuild": reb_timed, "phase_ms_per_step": phase_ms,
+                          "phase_sum_ms": phase_sum, "phase_stretch_n_rebuild": reb_stretch,
+                          "phase_sum_same_builds_ms": phase_sum_same_builds},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(), "variants": variants, "batch": batch, "grad": grad}
         print(json.dumps(out), flush=True)
