@@ -111,8 +111,8 @@ def kernel_model(phase: str, precision: str, kind: str, K: float, Ki: float):
 # Derived float64 peak, kept as a note beside the measured one: 152 SMs x 2
 # float64 FMA per clock x 2 flop x 2.07 GHz.
 FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# Bytes per atom-step of the whole step by the spec definition: the
-# list (4 B per entry) and positions (24 B) read by both force passes.
+# Algorithmic bytes per atom-step of the whole step: the list (4 B per
+# entry) and positions (24 B) read by both force passes.
 STEP_BYTES = lambda K: 2 * 4.0 * K + 2 * 24.0  # noqa: E731
 # DRAM bytes (read + write) per atom of one k_pairs_half launch, from an ncu
 # capture of 1,048,576 atoms of the same lattice, potential and temperature
@@ -801,7 +801,7 @@ def main():
                                     "after the timed ones",
                 "hbm": main_block.get("hbm"), "binding": main_block.get("binding"),
                 "peaks": peaks}
-    # the whole step against HBM by the spec byte count (list and
+    # the whole step against HBM by its algorithmic byte count (list and
     # positions read by both force passes)
     step_bytes = N * STEP_BYTES(K_list)
     roofline["step_hbm"] = {"bytes_per_step": step_bytes, "achieved": step_bytes / (ms_max / K * 1e-3) / 1e9,
