@@ -821,7 +821,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(K_e2e):
         s.set_state(xh, vh)
-        s.step(1)
+        s.step(1, use_graph=True)
         s.get_state(xh, vh)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
@@ -829,7 +829,8 @@ def main():
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": 2 * N * 3 * 8,
            "d2h_bytes_per_step": 2 * N * 3 * 8 + 56,
-           "call": "md_set_state(host) + md_step(1) + md_get_state(host) per step", "steps": K_e2e}
+           "call": "md_set_state(host) + md_step(1, graph replay) + md_get_state(host) per step",
+           "steps": K_e2e}
 
     def strip(d):
         return {k: v for k, v in d.items() if not k.startswith("_")}

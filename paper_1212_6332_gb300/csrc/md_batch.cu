@@ -9,8 +9,10 @@
 // synchronization and no global gather of neighbour positions. Each box
 // decides its own list rebuild and re-sorts its own atoms inside the block:
 //   kick-drift -> [wrap, bin, counting sort, list build] -> density -> force
-// with __syncthreads between phases. The arithmetic and the list order are
-// those of the tile kernels, so both schedules give the same bits.
+// with __syncthreads between phases; the pair functions are evaluated once
+// per pair (from the lower slot, both cache slots written through the
+// reverse index) and summed in list order, the arithmetic and the order of
+// the tile kernels, so both schedules give the same bits.
 // Boxes are launched largest first in shared-memory size classes.
 #include <algorithm>
 #include <vector>
@@ -43,6 +45,7 @@ struct BoxArgs {
     int* nn;
     int* nl;
     double2* ab;  // (V'/r, rho'/r) halves of the float64 pair cache entries: ab[2 slot]
+    double4_32a* pc;  // the whole 32-byte entries (V'/r, rho'/r, rho, V)
     int* n_up;  // float64 tile path's list layout data, kept valid across schedules
     int* rev;
     int* nl_lo;  // row-major lower parts for the reverse-index search
@@ -270,26 +273,41 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
                 return;
             }
         }
-        // density pass
+        // pair functions once per pair, as the tile schedule's pair pass:
+        // the atom of the lower slot evaluates each of its upper entries
+        // (j > i) and writes the 32-byte entry to its slot and, through the
+        // reverse index, to the partner's
         for (int t = tid; t < nb; t += NT) {
             const int64_t i = a0 + t;
             const double4_32a xi = sx[t];
-            const int n = min(A.nn[i], A.max_nb);
-            double r_i = 0.0, ep = 0.0;
+            const int nup = A.n_up[i];
+            const int n = nup < 0 ? min(A.nn[i], A.max_nb) : nup;
             for (int k = 0; k < n; ++k) {
                 const int64_t slot = (int64_t)k * A.Np + i;
                 const int e = A.nl[slot];
+                const int jg = entry_slot(e);
+                if (jg <= i) continue;
                 double dx, dy, dz;
-                sep_entry(xi, sx[entry_slot(e) - a0], entry_code(e), L, dx, dy, dz);
-                double r2 = norm2(dx, dy, dz);
-                double2 c = make_double2(0.0, 0.0);
-                double phi = 0.0, fr = 0.0;
-                if (below(r2, P.rc2)) pair_eval<KIND>(P, sT, r2, phi, fr, c.x, c.y);
-                // the tile schedule stores these values and sums them with
-                // round-to-nearest adds in list order: do exactly that
-                r_i = __dadd_rn(r_i, fr);
-                ep = __dadd_rn(ep, phi);
-                A.ab[2 * slot] = c;
+                sep_entry(xi, sx[jg - a0], entry_code(e), L, dx, dy, dz);
+                const double r2 = norm2(dx, dy, dz);
+                double Av = 0.0, Bv = 0.0, phi = 0.0, fr = 0.0;
+                if (below(r2, P.rc2)) pair_eval<KIND>(P, sT, r2, phi, fr, Av, Bv);
+                const double4_32a c = make_double4_32a(Av, Bv, fr, phi);
+                A.pc[slot] = c;
+                A.pc[(int64_t)A.rev[slot] * A.Np + jg] = c;
+            }
+        }
+        __syncthreads();
+        // density sums: round-to-nearest adds of the cached values in list
+        // order, as the tile schedule's sums
+        for (int t = tid; t < nb; t += NT) {
+            const int64_t i = a0 + t;
+            const int n = min(A.nn[i], A.max_nb);
+            double r_i = 0.0, ep = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const double2 w = cache_fv(A.pc, (int64_t)k * A.Np + i);
+                r_i = __dadd_rn(r_i, w.x);
+                ep = __dadd_rn(ep, w.y);
             }
             double F, Fpi;
             embed<KIND>(P, r_i, F, Fpi);
@@ -434,6 +452,7 @@ static void box_launch(Engine& e, int n_steps, cudaStream_t s) {
     A.nn = e.nn;
     A.nl = e.nl;
     A.ab = reinterpret_cast<double2*>(e.pc);
+    A.pc = e.pc;
     A.n_up = e.n_up;
     A.rev = e.rev;
     A.nl_lo = e.nl_lo;
