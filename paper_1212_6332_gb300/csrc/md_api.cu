@@ -228,6 +228,15 @@ void fill_pot(Engine& e) {
     P.f_a = (float)P.a;
     P.f_n = (float)P.n;
     P.f_m = (float)P.m;
+    const double log2e = 1.4426950408889634;
+    P.f_g1[0] = (float)(P.p * log2e);
+    P.f_g1[1] = (float)(-P.p_r0 * log2e);
+    P.f_g2[0] = (float)(P.q2 * log2e);
+    P.f_g2[1] = (float)(-P.q2_r0 * log2e);
+    P.f_x0 = (float)(-P.rs * P.inv_w);
+    P.f_dS[0] = (float)(-30.0 * P.inv_w);
+    P.f_dS[1] = (float)(60.0 * P.inv_w);
+    P.f_dS[2] = (float)(-30.0 * P.inv_w);
     e.pot = P;
 }
 
@@ -249,7 +258,7 @@ void free_engine(Engine& e) {
     dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.cell_org); dfree(e.spline_coef); dfree(e.spline_coef_f);
     dfree(e.spline_work); dfree(e.spline_pair_rec); dfree(e.rx_tab); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
-    dfree(e.Fpf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
+    dfree(e.xf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
     dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.pc); dfree(e.rev); dfree(e.nl_lo); dfree(e.n_up); dfree(e.exp_T);
     dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
@@ -445,7 +454,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.f, 3 * Np);
     AL(e.rho, Np);
     AL(e.Fp, Np);
-    AL(e.Fpf, Np);
+    AL(e.xf, Np);
     AL(e.e_atom, Np);
     AL(e.xo, Np);
     AL(e.perm, Np);

@@ -75,6 +75,10 @@ struct Pot {
     float rx_f1[2], rx_f2[2];   // float32 copies of the d^3 and d^4 coefficients
     // float copies for the mixed-precision path
     float f_rc2, f_rs, f_inv_w, f_A2, f_xi2, f_p, f_p_r0, f_q2, f_q2_r0, f_eps, f_a, f_n, f_m;
+    // mixed RGL in base 2: exp(p - p_r0 r) = 2^(f_g1[0] + f_g1[1] r) and the
+    // same for (2q, 2q/r0) in f_g2; taper variable x = sat(r inv_w + f_x0)
+    // and dS/dx inv_w = x^2 (f_dS[0] + x (f_dS[1] + x f_dS[2]))
+    float f_g1[2], f_g2[2], f_x0, f_dS[3];
 };
 
 // Geometry of the boxes, passed by value to kernels.
@@ -193,7 +197,7 @@ struct Engine {
     double* f = nullptr;     // [3][N_pad] SoA
     double* rho = nullptr;
     double* Fp = nullptr;
-    float* Fpf = nullptr;    // mixed: float copy of F'(rho)
+    float4* xf = nullptr;    // mixed: cell-local offset with float32 F'(rho) in w
     double* e_atom = nullptr;
     float4* xo = nullptr;    // mixed: cell-local offsets, w = packed cell coords
     int* perm = nullptr;     // sorted slot -> caller index
