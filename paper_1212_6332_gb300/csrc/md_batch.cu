@@ -214,6 +214,8 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
     if (KIND == MD_POT_RGL) load_exp_table(sT, P.exp_T);
     if (nb == 0) return;
     const double L[3] = {g.L[3 * b], g.L[3 * b + 1], g.L[3 * b + 2]};
+    const int kq = box_kq(L[0], L[1], L[2]);
+    const long long qL[3] = {to_fixed(L[0], kq), to_fixed(L[1], kq), to_fixed(L[2], kq)};
     for (int t = tid; t < nb; t += NT) sx[t] = A.x[a0 + t];
     int done = A.box_done[b];
     bool pending = A.box_state[b] == 1;
@@ -280,6 +282,7 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
         for (int t = tid; t < nb; t += NT) {
             const int64_t i = a0 + t;
             const double4_32a xi = sx[t];
+            const long long qi[3] = {to_fixed(xi.x, kq), to_fixed(xi.y, kq), to_fixed(xi.z, kq)};
             const int nup = A.n_up[i];
             const int n = nup < 0 ? min(A.nn[i], A.max_nb) : nup;
             for (int k = 0; k < n; ++k) {
@@ -287,9 +290,7 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
                 const int e = A.nl[slot];
                 const int jg = entry_slot(e);
                 if (jg <= i) continue;
-                double dx, dy, dz;
-                sep_entry(xi, sx[jg - a0], entry_code(e), L, dx, dy, dz);
-                const double r2 = norm2(dx, dy, dz);
+                const double r2 = r2_exact(qi, sx[jg - a0], entry_code(e), qL, kq);
                 double Av = 0.0, Bv = 0.0, phi = 0.0, fr = 0.0;
                 if (below(r2, P.rc2)) pair_eval<KIND>(P, sT, r2, phi, fr, Av, Bv);
                 const double4_32a c = make_double4_32a(Av, Bv, fr, phi);

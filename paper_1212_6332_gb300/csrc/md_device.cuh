@@ -123,6 +123,76 @@ __device__ __forceinline__ double norm2(double dx, double dy, double dz) {
     return fma(dz, dz, fma(dy, dy, dx * dx));
 }
 
+// ---------------------------------------------------------------- exact r^2
+//
+// GB300 issues float64 at 1/64 of its float32 and integer rate, so the
+// squared separation that the pair functions take is formed on the integer
+// pipe: each coordinate as a 64-bit fixed-point number x 2^kq (exact for
+// |x| >= 2^(52 - kq); below that the bits under 2^-kq are dropped, under
+// 2^-50 A), the separation including its periodic image and the sum of its
+// squares exact in 128-bit integers, and r^2 rounded once to the nearest
+// double. This takes 6 float64 instructions (3 subtractions, the 3
+// operations of |d|^2) off every pair, and the result is at least as
+// accurate as the float64 form, which rounds up to four times. The scale
+// kq is a function of the box alone (box_kq), so a box gives the same bits
+// alone and inside a batch.
+
+// Fixed-point scale of a box with sides L: every position lies within a few
+// box lengths of its box (wrapped at each list build, drifting less than the
+// skin in between), |x| < 4 L < 2^(ex + 2) for the longest side L < 2^ex,
+// so kq = 60 - ex keeps |x| 2^kq below 2^62; separations below 8 A keep the
+// sum of three squares below 2^(2 kq + 8) <= 2^126 (L is taken as at least
+// 1 A, so kq <= 59).
+__device__ __forceinline__ int box_kq(double Lx, double Ly, double Lz) {
+    const double L = fmax(fmax(Lx, Ly), fmax(Lz, 1.0));
+    const int ex = (int)((__double_as_longlong(L) >> 52) & 0x7ff) - 1022;  // L = f 2^ex, f in [1/2, 1)
+    return 60 - ex;
+}
+
+// x 2^kq as a 64-bit integer, toward zero, formed from the bit pattern
+__device__ __forceinline__ long long to_fixed(double x, int kq) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = e - 1075 + kq;  // x = m 2^(e - 1075)
+    unsigned long long v = 0;
+    if (e != 0) v = sh >= 0 ? m << sh : (sh > -64 ? m >> -sh : 0ull);
+    return (b >> 63) ? -(long long)v : (long long)v;
+}
+
+// v 2^-scale rounded to the nearest double (ties to even); v < 2^127
+__device__ __forceinline__ double u128_to_double(unsigned __int128 v, int scale) {
+    if (v == 0) return 0.0;
+    const unsigned long long hi = (unsigned long long)(v >> 64);
+    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)(unsigned long long)v);
+    const unsigned __int128 n = v << lz;  // leading one at bit 127
+    const unsigned long long top = (unsigned long long)(n >> 64);
+    unsigned long long m = top >> 11;     // 53 bits
+    const unsigned long long rb = top & 0x7ffull;
+    const bool sticky = (unsigned long long)n != 0ull;
+    if (rb > 0x400ull || (rb == 0x400ull && (sticky || (m & 1ull)))) ++m;
+    // the leading one of the result is 2^(127 - lz - scale); m carries the
+    // implicit bit, so a carry out of the rounding moves the exponent up
+    const long long E = 127 - lz - scale;
+    return __longlong_as_double((long long)(((unsigned long long)(E + 1022) << 52) + m));
+}
+
+// |x_j + shift L - x_i|^2 of a list entry; qi and qL are x_i and L in fixed
+// point (to_fixed)
+__device__ __forceinline__ double r2_exact(const long long (&qi)[3], const double4_32a& xj, unsigned code,
+                                           const long long (&qL)[3], int kq) {
+    const double c[3] = {xj.x, xj.y, xj.z};
+    unsigned __int128 s = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long sh = (long long)((int)((code >> (2 * a)) & 3u) - 1);
+        const long long d = to_fixed(c[a], kq) - qi[a] + sh * qL[a];
+        const unsigned long long u = d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
+        s += (unsigned __int128)u * u;
+    }
+    return u128_to_double(s, 2 * kq);
+}
+
 // r^2 < c^2 for non-negative, non-NaN doubles, as an integer compare
 __device__ __forceinline__ bool below(double r2, double c2) {
     return __double_as_longlong(r2) < __double_as_longlong(c2);

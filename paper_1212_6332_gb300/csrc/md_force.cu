@@ -56,7 +56,7 @@ constexpr double kScreen = 1e-4;  // relative r^2 margin of the float32 screen
 // array fits (less queue traffic in shared memory), 64-bit otherwise.
 template <typename ST>
 struct PairQueue {
-    double d[3][2][kQueue];  // separation x_j - x_i, per axis and region
+    double r2[2][kQueue];    // exact r^2 of the pair, per region
     ST own[2][kQueue];       // slot of the entry in i's list
     ST mir[2][kQueue];       // slot of the mirror entry in j's list
     int pt[2][kQueue];       // type-pair table (several species)
@@ -65,7 +65,7 @@ struct PairQueue {
 template <int KIND, bool MIRROR, typename ST>
 __device__ __forceinline__ void eval_queued(const Pot& P, const PairQueue<ST>& q, int r, int p,
                                             double4_32a* __restrict__ pc) {
-    const double r2 = norm2(q.d[0][r][p], q.d[1][r][p], q.d[2][r][p]);
+    const double r2 = q.r2[r][p];
     double A = 0.0, B = 0.0, V = 0.0, fr = 0.0;
     const int pt = KIND == MD_POT_SPLINE ? q.pt[r][p] : 0;
     if (below(r2, P.rc2)) pair_eval<KIND>(P, P.exp_T, r2, V, fr, A, B, pt);
@@ -123,15 +123,23 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
         CellSep cs = cs0;
         float4 oi = make_float4(0.f, 0.f, 0.f, 0.f);
         double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-        double L[3] = {0.0, 0.0, 0.0};
+        long long qi[3] = {0, 0, 0}, qL[3] = {0, 0, 0};
+        int kq = 0;
         int kend = 0;
         if (i < N) {
             cs = cell_sep<SINGLE>(g, cs0, i);
             const int b = SINGLE ? 0 : g.atom_box[i];
+            double L[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+            kq = box_kq(L[0], L[1], L[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) qL[a] = to_fixed(L[a], kq);
             oi = xo[i];
             xi = x[i];
+            qi[0] = to_fixed(xi.x, kq);
+            qi[1] = to_fixed(xi.y, kq);
+            qi[2] = to_fixed(xi.z, kq);
             // lists are [upper | lower]: the upper entries (j > i) are rows
             // 0..n_up-1; the lower ones are written by the partners' lanes (a
             // list kept unrotated, n_up < 0, is scanned whole)
@@ -148,7 +156,7 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
             const PairRow nxt = load_pair_row<MIRROR>(e_ahead, k + 1 < kend, i, xo, x, rev, Np, k + 1);
             e_ahead = k + 2 < kend ? nl[(int64_t)(k + 2) * Np + i] : 0;
             bool in = false, tq = false;
-            double dx = 0.0, dy = 0.0, dz = 0.0;
+            double r2 = 0.0;
             const ST own = (ST)((long long)k * Np + i);
             const ST mir = (ST)((long long)cur.rv * Np + entry_slot(cur.e));
             const int pt = KIND == MD_POT_SPLINE && P.n_types > 1
@@ -161,7 +169,7 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
                 if (r2f < rc2f) {
                     in = true;
                     tq = r2f > rs2f;
-                    sep_entry(xi, cur.xj, entry_code(cur.e), L, dx, dy, dz);
+                    r2 = r2_exact(qi, cur.xj, entry_code(cur.e), qL, kq);
                 } else {
                     const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
                     pc[own] = z;
@@ -175,9 +183,7 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
                 const unsigned m = __ballot_sync(0xffffffffu, mine);
                 if (mine) {
                     const int p = qn[r] + __popc(m & lt_mask);
-                    q.d[0][r][p] = dx;
-                    q.d[1][r][p] = dy;
-                    q.d[2][r][p] = dz;
+                    q.r2[r][p] = r2;
                     q.own[r][p] = own;
                     q.mir[r][p] = mir;
                     if (KIND == MD_POT_SPLINE) q.pt[r][p] = pt;
@@ -376,9 +382,6 @@ __device__ __forceinline__ void pair_flat_row(int64_t i, int64_t k, int64_t Np, 
     if (j <= i) return;  // lower entries of an unrotated list
     const CellSep cs = cell_sep<SINGLE>(g, cs0, i);
     const int b = SINGLE ? 0 : g.atom_box[i];
-    double L[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
     const float4 oi = xo[i], oj = xo[j];
     const long long mir = MIRROR ? (long long)rev[own] * Np + j : 0;
     float fx, fy, fz;
@@ -387,9 +390,17 @@ __device__ __forceinline__ void pair_flat_row(int64_t i, int64_t k, int64_t Np, 
     double A = 0.0, B = 0.0, V = 0.0, fr = 0.0;
     if (r2f < rc2f) {
         const double4_32a xi = x[i], xj = x[j];
-        double dx, dy, dz;
-        sep_entry(xi, xj, entry_code(e), L, dx, dy, dz);
-        const double r2 = norm2(dx, dy, dz);
+        double L[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+        const int kq = box_kq(L[0], L[1], L[2]);
+        long long qi[3], qL[3];
+        qi[0] = to_fixed(xi.x, kq);
+        qi[1] = to_fixed(xi.y, kq);
+        qi[2] = to_fixed(xi.z, kq);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) qL[a] = to_fixed(L[a], kq);
+        const double r2 = r2_exact(qi, xj, entry_code(e), qL, kq);
         const int pt = KIND == MD_POT_SPLINE && P.n_types > 1 ? pair_table(P.n_types, pos_type(xi), pos_type(xj)) : 0;
         if (below(r2, P.rc2)) pair_eval<KIND>(P, P.exp_T, r2, V, fr, A, B, pt);
     }
