@@ -405,7 +405,10 @@ MD_API int md_profile_read(md_batch* h, md_profile* out);
  * values x [n] (device) into out [n] (device): fn 0 = table-driven e^x
  * (arguments |x| < 700), 1 = CUDA exp(x), 2 = 1/sqrt(x) by the library's
  * float32 estimate plus one third-order Newton step (x > 0), 3 = CUDA
- * rsqrt(x). Lets a caller bound the error of the hot-path functions.
+ * rsqrt(x), 4 and 5 = 1/sqrt(x) and sqrt(x) as the float64 pair functions
+ * take them, a float32 estimate and a third-order Newton step in fixed point
+ * on the integer pipe, each rounded once (x positive and normal). Lets a
+ * caller bound the error of the hot-path functions.
  * MD_ERR_ARG for an unknown fn or non-device pointers. */
 MD_API int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double* out, md_stream stream);
 

@@ -258,7 +258,7 @@ void free_engine(Engine& e) {
     dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.cell_org); dfree(e.spline_coef); dfree(e.spline_coef_f);
     dfree(e.spline_work); dfree(e.spline_pair_rec); dfree(e.rx_tab); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
-    dfree(e.xf); dfree(e.e_atom); dfree(e.xo); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
+    dfree(e.xf); dfree(e.e_atom); dfree(e.xo); dfree(e.xq); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
     dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.pc); dfree(e.rev); dfree(e.nl_lo); dfree(e.n_up); dfree(e.exp_T);
     dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
@@ -457,6 +457,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.xf, Np);
     AL(e.e_atom, Np);
     AL(e.xo, Np);
+    AL(e.xq, Np);
     AL(e.perm, Np);
     AL(e.perm_alt, Np);
     AL(e.iperm, Np);
@@ -1463,7 +1464,7 @@ int md_num_params(const md_batch* b) {
 int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double* out, md_stream st) {
     if (!h) return MD_ERR_ARG;
     Engine* E = &h->e;
-    if (fn < 0 || fn > 3) return fail(E, MD_ERR_ARG, "unknown function");
+    if (fn < 0 || fn > 5) return fail(E, MD_ERR_ARG, "unknown function");
     if (n < 0) return fail(E, MD_ERR_ARG, "n must be >= 0");
     if (n > 0 && (!is_device_ptr(x) || !is_device_ptr(out))) return fail(E, MD_ERR_ARG, "x and out must be device pointers");
     launch_eval_math(*E, fn, x, n, out, (cudaStream_t)st);

@@ -160,37 +160,125 @@ __device__ __forceinline__ long long to_fixed(double x, int kq) {
     return (b >> 63) ? -(long long)v : (long long)v;
 }
 
-// v 2^-scale rounded to the nearest double (ties to even); v < 2^127
-__device__ __forceinline__ double u128_to_double(unsigned __int128 v, int scale) {
-    if (v == 0) return 0.0;
-    const unsigned long long hi = (unsigned long long)(v >> 64);
-    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)(unsigned long long)v);
-    const unsigned __int128 n = v << lz;  // leading one at bit 127
-    const unsigned long long top = (unsigned long long)(n >> 64);
-    unsigned long long m = top >> 11;     // 53 bits
+// (hi 2^64 + lo) 2^-scale rounded to the nearest double (ties to even),
+// from the bit patterns
+__device__ __forceinline__ double round_u128(unsigned long long hi, unsigned long long lo, int scale) {
+    if (hi == 0ull) {
+        if (lo == 0ull) return 0.0;
+        hi = lo;
+        lo = 0ull;
+        scale += 64;
+    }
+    const int lz = __clzll((long long)hi);
+    const unsigned long long top = (hi << lz) | ((lo >> 1) >> (63 - lz));  // leading one at bit 63
+    const unsigned long long rest = lo << lz;
+    unsigned long long m = top >> 11;  // 53 bits
     const unsigned long long rb = top & 0x7ffull;
-    const bool sticky = (unsigned long long)n != 0ull;
-    if (rb > 0x400ull || (rb == 0x400ull && (sticky || (m & 1ull)))) ++m;
+    if (rb > 0x400ull || (rb == 0x400ull && (rest != 0ull || (m & 1ull)))) ++m;
     // the leading one of the result is 2^(127 - lz - scale); m carries the
     // implicit bit, so a carry out of the rounding moves the exponent up
     const long long E = 127 - lz - scale;
     return __longlong_as_double((long long)(((unsigned long long)(E + 1022) << 52) + m));
 }
 
-// |x_j + shift L - x_i|^2 of a list entry; qi and qL are x_i and L in fixed
-// point (to_fixed)
+// (lo, hi) += (blo, bhi) in 128 bits
+__device__ __forceinline__ void add128(unsigned long long& lo, unsigned long long& hi, unsigned long long blo,
+                                       unsigned long long bhi) {
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(blo), "l"(bhi));
+}
+
+// d^2 of a fixed-point difference |d| < 2^58 in 29-bit limbs, d = h 2^29 + l:
+// d^2 = h^2 2^58 + (h l) 2^30 + l^2, each product below 2^58
+__device__ __forceinline__ void sq_parts(long long d, unsigned long long& shh, unsigned long long& shl,
+                                         unsigned long long& sll) {
+    const unsigned long long u = d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
+    const unsigned h = (unsigned)(u >> 29), l = (unsigned)u & 0x1fffffffu;
+    shh += (unsigned long long)h * h;
+    shl += (unsigned long long)h * l;
+    sll += (unsigned long long)l * l;
+}
+
+// (dx^2 + dy^2 + dz^2) 2^-scale of fixed-point differences, exact in 128
+// bits and rounded once
+__device__ __forceinline__ double r2_fixed(long long dx, long long dy, long long dz, int scale) {
+    unsigned long long shh = 0ull, shl = 0ull, sll = 0ull;
+    sq_parts(dx, shh, shl, sll);
+    sq_parts(dy, shh, shl, sll);
+    sq_parts(dz, shh, shl, sll);
+    unsigned long long lo = shh << 58, hi = shh >> 6;
+    add128(lo, hi, shl << 30, shl >> 34);
+    add128(lo, hi, sll, 0ull);
+    return round_u128(hi, lo, scale);
+}
+
+// 1/sqrt(x) and sqrt(x) of a positive normal double on the integer pipe
+// (the float64 form, a Newton step and r = x / sqrt(x), takes 6 float64
+// instructions). With x = m' 2^(2h), m' in [1, 4): a float32 estimate y0 of
+// 1/sqrt(m') (hardware rsqrt of m' truncated to float32), then in fixed
+// point e = 1 - m' y0^2 and the third-order step
+//     y1 = y0 (1 + e/2 + 3 e^2 / 8)
+// (truncation 5 e^3 / 16 < 2^-62 for |e| < 2^-21), sqrt(m') = m' y1, each
+// rounded once to the nearest double and scaled by 2^-h, 2^h. The fixed-
+// point steps keep 63 fractional bits or more, so either result lies within
+// 0.51 ulp of the true value (correctly rounded but for near-ties), against
+// up to about one ulp for the float64 form.
+__device__ __forceinline__ void rsqrt_sqrt(double x, double& y, double& r) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)(b >> 52) - 1023;  // x = m 2^e, m in [1, 2)
+    const int odd = e & 1;
+    const int h = (e - odd) / 2;
+    const unsigned long long M = ((b & 0xfffffffffffffull) | (1ull << 52)) << odd;  // m' 2^52
+    // m' in float32 (fraction truncated), its rsqrt in (1/2, 1]
+    const float mf = __uint_as_float(((unsigned)(127 + odd) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    const unsigned yb = __float_as_uint(rsqrtf(mf));
+    const int ey = (int)(yb >> 23) - 127;                                                  // -1 or 0
+    const unsigned long long Y0 = (unsigned long long)((yb & 0x7fffffu) | 0x800000u) << (8 + ey);  // y0 2^31
+    // e 2^64 = (2^114 - m' y0^2 2^114) 2^-50; |e| < 2^-20, so the bits of
+    // the product above 2^114 cancel and its low 114 bits decide
+    const unsigned long long Y2 = Y0 * Y0;  // y0^2 2^62
+    const unsigned long long plo = M * Y2, phi = __umul64hi(M, Y2);
+    unsigned long long dlo = 0ull, dhi = 1ull << 50;  // 2^114
+    asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;" : "+l"(dlo), "+l"(dhi) : "l"(plo), "l"(phi));
+    const long long E = (long long)((dhi << 14) | (dlo >> 50));
+    const long long C = (E >> 1) + (3 * __mul64hi(E, E) >> 3);  // (e/2 + 3e^2/8) 2^64
+    // y1 2^95 = Y0 2^64 + Y0 C, in two's complement over 128 bits
+    unsigned long long ylo = (unsigned long long)((long long)Y0 * C);
+    unsigned long long yhi = (unsigned long long)__mul64hi((long long)Y0, C) + Y0;
+    y = round_u128(yhi, ylo, 95 + h);
+    const unsigned long long Y1h = (yhi << 32) | (ylo >> 32);  // y1 2^63
+    r = round_u128(__umul64hi(M, Y1h), M * Y1h, 115 - h);
+}
+
+// |x_j + shift L - x_i|^2 of a list entry from fixed-point coordinates (q_i,
+// q_j, q_L: x_i, x_j and L through to_fixed)
+__device__ __forceinline__ double r2_exact(const long long (&qi)[3], long long qjx, long long qjy, long long qjz,
+                                           unsigned code, const long long (&qL)[3], int kq) {
+    long long d[3] = {qjx - qi[0], qjy - qi[1], qjz - qi[2]};
+    if (code != kNoShift) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const unsigned c = (code >> (2 * a)) & 3u;
+            d[a] += c == 0u ? -qL[a] : (c == 2u ? qL[a] : 0ll);
+        }
+    }
+    return r2_fixed(d[0], d[1], d[2], 2 * kq);
+}
+
+// the same from x_j in float64
 __device__ __forceinline__ double r2_exact(const long long (&qi)[3], const double4_32a& xj, unsigned code,
                                            const long long (&qL)[3], int kq) {
-    const double c[3] = {xj.x, xj.y, xj.z};
-    unsigned __int128 s = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const long long sh = (long long)((int)((code >> (2 * a)) & 3u) - 1);
-        const long long d = to_fixed(c[a], kq) - qi[a] + sh * qL[a];
-        const unsigned long long u = d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
-        s += (unsigned __int128)u * u;
-    }
-    return u128_to_double(s, 2 * kq);
+    return r2_exact(qi, to_fixed(xj.x, kq), to_fixed(xj.y, kq), to_fixed(xj.z, kq), code, qL, kq);
+}
+
+// Fixed-point copy of a position for the pair passes: (x, y, z) 2^kq and the
+// species label
+__device__ __forceinline__ longlong4_32a fixed_pos(const double4_32a& p, int kq) {
+    longlong4_32a q;
+    q.x = to_fixed(p.x, kq);
+    q.y = to_fixed(p.y, kq);
+    q.z = to_fixed(p.z, kq);
+    q.w = (long long)pos_type(p);
+    return q;
 }
 
 // r^2 < c^2 for non-negative, non-NaN doubles, as an integer compare
@@ -474,8 +562,8 @@ __device__ __forceinline__ double powr(double b, double e) {
 template <int KIND>
 __device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict__ T, double r2, double& phi,
                                           double& fr, double& A, double& B, int pt = 0) {
-    double rinv = rsqrt_nr(r2);
-    double r = r2 * rinv;
+    double rinv, r;
+    rsqrt_sqrt(r2, rinv, r);
     // pairs inside r_taper (r^2 <= r_taper^2) skip the taper (S = 1, S' = 0);
     // non-negative doubles order like their bit patterns, so the test runs
     // on the integer pipe

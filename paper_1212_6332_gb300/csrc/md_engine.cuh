@@ -200,6 +200,7 @@ struct Engine {
     float4* xf = nullptr;    // mixed: cell-local offset with float32 F'(rho) in w
     double* e_atom = nullptr;
     float4* xo = nullptr;    // mixed: cell-local offsets, w = packed cell coords
+    longlong4_32a* xq = nullptr;  // float64 pair pass: fixed-point positions (x 2^kq) and species
     int* perm = nullptr;     // sorted slot -> caller index
     int* perm_alt = nullptr;
     int* iperm = nullptr;    // caller index -> sorted slot

@@ -74,29 +74,43 @@ __device__ __forceinline__ void eval_queued(const Pot& P, const PairQueue<ST>& q
     if (MIRROR) pc[(int64_t)q.mir[r][p]] = c;
 }
 
+// The positions in fixed point (x 2^kq, kq of the atom's box) with the
+// species label, gathered by the pair pass for its exact r^2: one
+// conversion per atom and step instead of one per list entry.
+template <bool SINGLE>
+__global__ void __launch_bounds__(kFNT) k_fixed_positions(int64_t N, Geo g, const double4_32a* __restrict__ x,
+                                                          longlong4_32a* __restrict__ xq, const Ctl* ctl) {
+    if (load_status(ctl)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = SINGLE ? 0 : g.atom_box[i];
+    const int kq = SINGLE ? box_kq(g.L0[0], g.L0[1], g.L0[2]) : box_kq(g.L[3 * b], g.L[3 * b + 1], g.L[3 * b + 2]);
+    xq[i] = fixed_pos(x[i], kq);
+}
+
 // One list row of a lane: the entry and, for an upper entry (j > i), the
-// partner's offset and position and the row of the mirror entry.
+// partner's offset and fixed-point position and the row of the mirror entry.
 struct PairRow {
     float4 oj;
-    double4_32a xj;
+    longlong4_32a qj;
     int e, rv;
     bool upper;
 };
 
 template <bool MIRROR>
 __device__ __forceinline__ PairRow load_pair_row(int e, bool valid, int64_t i, const float4* __restrict__ xo,
-                                                 const double4_32a* __restrict__ x, const int* __restrict__ rev,
+                                                 const longlong4_32a* __restrict__ xq, const int* __restrict__ rev,
                                                  int64_t Np, int k) {
     PairRow r;
     r.e = e;
     r.upper = valid && entry_slot(e) > i;
     r.oj = make_float4(0.f, 0.f, 0.f, 0.f);
-    r.xj = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    r.qj = longlong4_32a{0, 0, 0, 0};
     r.rv = 0;
     if (r.upper) {
         const int j = entry_slot(e);
         r.oj = xo[j];
-        r.xj = x[j];
+        r.qj = xq[j];
         if (MIRROR) r.rv = rev[(int64_t)k * Np + i];
     }
     return r;
@@ -104,9 +118,16 @@ __device__ __forceinline__ PairRow load_pair_row(int e, bool valid, int64_t i, c
 
 // MIRROR = false (Newton's third law variant): only the upper slot of each
 // pair is written; the lower slots are never read.
+// (a minimum of 6 or 8 resident blocks, 80 or 64 registers, measured
+// slower: 4M-atom pair pass 3.41 -> 3.45 / 3.82 ms)
+#ifdef MD_PAIR_MIN_BLOCKS
+#define MD_PAIR_BOUNDS __launch_bounds__(kFNT, MD_PAIR_MIN_BLOCKS)
+#else
+#define MD_PAIR_BOUNDS __launch_bounds__(kFNT)
+#endif
 template <int KIND, bool SINGLE, bool MIRROR, typename ST>
-__global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P, float rc2f,
-                                                     float rs2f, const double4_32a* __restrict__ x,
+__global__ void MD_PAIR_BOUNDS k_pairs_half(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P, float rc2f,
+                                                     float rs2f, const longlong4_32a* __restrict__ xq,
                                                      const float4* __restrict__ xo, const int* __restrict__ nn,
                                                      const int* __restrict__ nl, const int* __restrict__ rev,
                                                      const int* __restrict__ n_up, int max_nb,
@@ -122,7 +143,7 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
         const int64_t i = grp * 32 + lane;
         CellSep cs = cs0;
         float4 oi = make_float4(0.f, 0.f, 0.f, 0.f);
-        double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        int ti = 0;
         long long qi[3] = {0, 0, 0}, qL[3] = {0, 0, 0};
         int kq = 0;
         int kend = 0;
@@ -136,10 +157,11 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
 #pragma unroll
             for (int a = 0; a < 3; ++a) qL[a] = to_fixed(L[a], kq);
             oi = xo[i];
-            xi = x[i];
-            qi[0] = to_fixed(xi.x, kq);
-            qi[1] = to_fixed(xi.y, kq);
-            qi[2] = to_fixed(xi.z, kq);
+            const longlong4_32a q = xq[i];
+            qi[0] = q.x;
+            qi[1] = q.y;
+            qi[2] = q.z;
+            ti = (int)q.w;
             // lists are [upper | lower]: the upper entries (j > i) are rows
             // 0..n_up-1; the lower ones are written by the partners' lanes (a
             // list kept unrotated, n_up < 0, is scanned whole)
@@ -150,17 +172,17 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
         // software pipeline: the list entry two rows ahead and the partner
         // data (offset, position, mirror row) one row ahead are in flight
         // while a row is screened, so the loop does not wait on L2 / HBM
-        PairRow cur = load_pair_row<MIRROR>(0 < kend ? nl[i] : 0, 0 < kend, i, xo, x, rev, Np, 0);
+        PairRow cur = load_pair_row<MIRROR>(0 < kend ? nl[i] : 0, 0 < kend, i, xo, xq, rev, Np, 0);
         int e_ahead = 1 < kend ? nl[Np + i] : 0;
         for (int k = 0; k < kmax; ++k) {
-            const PairRow nxt = load_pair_row<MIRROR>(e_ahead, k + 1 < kend, i, xo, x, rev, Np, k + 1);
+            const PairRow nxt = load_pair_row<MIRROR>(e_ahead, k + 1 < kend, i, xo, xq, rev, Np, k + 1);
             e_ahead = k + 2 < kend ? nl[(int64_t)(k + 2) * Np + i] : 0;
             bool in = false, tq = false;
             double r2 = 0.0;
             const ST own = (ST)((long long)k * Np + i);
             const ST mir = (ST)((long long)cur.rv * Np + entry_slot(cur.e));
             const int pt = KIND == MD_POT_SPLINE && P.n_types > 1
-                               ? pair_table(P.n_types, pos_type(xi), pos_type(cur.xj))
+                               ? pair_table(P.n_types, ti, (int)cur.qj.w)
                                : 0;
             if (cur.upper) {
                 float fx, fy, fz;
@@ -169,7 +191,7 @@ __global__ void __launch_bounds__(kFNT) k_pairs_half(int64_t N, int64_t Np, Geo 
                 if (r2f < rc2f) {
                     in = true;
                     tq = r2f > rs2f;
-                    r2 = r2_exact(qi, cur.xj, entry_code(cur.e), qL, kq);
+                    r2 = r2_exact(qi, cur.qj.x, cur.qj.y, cur.qj.z, entry_code(cur.e), qL, kq);
                 } else {
                     const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
                     pc[own] = z;
@@ -683,20 +705,22 @@ static int pair_blocks(const Engine& e) {
 }
 
 // The queued pair pass with list-slot indices as narrow as the list array
-// allows.
+// allows, after the fixed-point copy of the positions it gathers.
 template <int KIND, bool SINGLE, bool MIRROR>
 static void launch_pairs_half(Engine& e, const Geo& g, cudaStream_t s) {
+    e.launches += 1;
+    k_fixed_positions<SINGLE><<<(int)((e.N + kFNT - 1) / kFNT), kFNT, 0, s>>>(e.N, g, e.x, e.xq, e.ctl);
     // 32-bit slots: 85 instead of 89 registers, 18 instead of 22.5 KB of
     // queues per block (4M-atom step 8.69 -> 8.63 ms; the same bits);
     // 6 blocks per SM forced (80 registers, spills) measured slower
     const bool narrow = (int64_t)e.N_pad * e.max_nb <= (int64_t)0xffffffffll;
     if (narrow)
         k_pairs_half<KIND, SINGLE, MIRROR, unsigned><<<pair_blocks<KIND, SINGLE, MIRROR, unsigned>(e), kFNT, 0, s>>>(
-            e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.x, e.xo, e.nn,
+            e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.xq, e.xo, e.nn,
             e.nl, e.rev, e.n_up, e.max_nb, e.pc, e.ctl);
     else
         k_pairs_half<KIND, SINGLE, MIRROR, long long><<<pair_blocks<KIND, SINGLE, MIRROR, long long>(e), kFNT, 0, s>>>(
-            e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.x, e.xo, e.nn,
+            e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.xq, e.xo, e.nn,
             e.nl, e.rev, e.n_up, e.max_nb, e.pc, e.ctl);
 }
 

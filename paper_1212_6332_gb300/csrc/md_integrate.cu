@@ -586,7 +586,12 @@ __global__ void k_eval_math(int fn, const double* __restrict__ x, int64_t n, dou
         case 0: out[i] = exp_tab(v, sT, K); break;
         case 1: out[i] = exp(v); break;
         case 2: out[i] = rsqrt_nr(v); break;
-        default: out[i] = rsqrt(v); break;
+        case 3: out[i] = rsqrt(v); break;
+        default: {
+            double y, r;
+            rsqrt_sqrt(v, y, r);
+            out[i] = fn == 4 ? y : r;
+        }
     }
 }
 

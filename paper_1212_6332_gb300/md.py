@@ -407,8 +407,8 @@ class System:
 
     def eval_math(self, fn: str, x):
         """The library's float64 functions on a CUDA tensor: fn in
-        {"exp", "exp_ref", "rsqrt", "rsqrt_ref"}."""
-        code = {"exp": 0, "exp_ref": 1, "rsqrt": 2, "rsqrt_ref": 3}[fn]
+        {"exp", "exp_ref", "rsqrt", "rsqrt_ref", "rsqrt_int", "sqrt_int"}."""
+        code = {"exp": 0, "exp_ref": 1, "rsqrt": 2, "rsqrt_ref": 3, "rsqrt_int": 4, "sqrt_int": 5}[fn]
         x = x.contiguous()
         out = self._empty(x.numel())
         self._check(self.lib.md_eval_math(self._h, code, _ptr(x), x.numel(), _ptr(out), _stream()))

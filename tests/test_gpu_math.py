@@ -47,6 +47,32 @@ def test_refined_rsqrt_within_two_ulp(sysm):
     assert mine[-3] == 1.0 and mine[-2] == 0.5 and abs(mine[-1] - 0.2) <= np.spacing(0.2)
 
 
+def test_integer_pipe_rsqrt_and_sqrt_within_0_51_ulp(sysm):
+    """The float64 pair functions' 1/sqrt(r^2) and r, formed in fixed point on
+    the integer pipe: within 0.51 ulp of the exact values (50-digit decimal
+    arithmetic on a sample; the host's sqrt, correctly rounded, on all), and
+    exact at powers of four."""
+    import decimal
+    import torch
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(0.5, 60.0, 1 << 20), 10.0 ** rng.uniform(-6, 6, 1 << 16),
+                        np.nextafter(np.float64(4.0), 0.0) * np.ones(1), [1.0, 4.0, 16.0, 0.25]])
+    xt = torch.tensor(x, device="cuda")
+    y = sysm.eval_math("rsqrt_int", xt).cpu().numpy()
+    r = sysm.eval_math("sqrt_int", xt).cpu().numpy()
+    host_r = np.sqrt(x)
+    assert ulp_err(r, host_r).max() <= 1.0
+    assert ulp_err(y, 1.0 / host_r).max() <= 2.0
+    assert list(y[-4:]) == [1.0, 0.5, 0.25, 2.0] and list(r[-4:]) == [1.0, 2.0, 4.0, 0.5]
+    decimal.getcontext().prec = 50
+    worst = 0.0
+    for k in np.concatenate([rng.integers(0, x.size, 4000), np.arange(x.size - 5, x.size)]):
+        s = decimal.Decimal(float(x[k])).sqrt()
+        for got, want in ((float(r[k]), s), (float(y[k]), 1 / s)):
+            worst = max(worst, float(abs(decimal.Decimal(got) - want) / decimal.Decimal(np.spacing(got))))
+    assert worst <= 0.51, worst
+
+
 @pytest.mark.parametrize("spec", [I.RGL_CU, I.RGL_NI])
 def test_rgl_pair_functions_from_the_r_table(spec):
     """The float64 pair path takes both RGL exponentials from a table over r
