@@ -258,7 +258,7 @@ void free_engine(Engine& e) {
     dfree(e.atom_box); dfree(e.cell_box); dfree(e.cell_rank); dfree(e.cell_xyz); dfree(e.cell_org); dfree(e.spline_coef); dfree(e.spline_coef_f);
     dfree(e.spline_work); dfree(e.spline_pair_rec); dfree(e.rx_tab); dfree(e.knots_dev); dfree(e.chunk_lo); dfree(e.chunk_hi); dfree(e.box_chunk_off);
     dfree(e.x); dfree(e.x_alt); dfree(e.xb); dfree(e.v); dfree(e.v_alt); dfree(e.f); dfree(e.rho); dfree(e.Fp);
-    dfree(e.xf); dfree(e.e_atom); dfree(e.xo); dfree(e.xq); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
+    dfree(e.xf); dfree(e.e_atom); dfree(e.xo); dfree(e.xq); dfree(e.sum_q); dfree(e.perm); dfree(e.perm_alt); dfree(e.iperm);
     dfree(e.cell_of); dfree(e.cell_t); dfree(e.cell_t_alt); dfree(e.src); dfree(e.cell_count);
     dfree(e.cell_start); dfree(e.scan_tmp); dfree(e.nn); dfree(e.nl); dfree(e.pc); dfree(e.rev); dfree(e.nl_lo); dfree(e.n_up); dfree(e.exp_T);
     dfree(e.box_order); dfree(e.box_done); dfree(e.box_state);
@@ -458,6 +458,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
     AL(e.e_atom, Np);
     AL(e.xo, Np);
     AL(e.xq, Np);
+    AL(e.sum_q, kSumWords * Np);
     AL(e.perm, Np);
     AL(e.perm_alt, Np);
     AL(e.iperm, Np);
@@ -545,6 +546,7 @@ int create_impl(const md_config* cfg, const md_potential* pot, int B, const int6
         if (ce == cudaSuccess) ce = cudaMemset(e.v, 0, 3 * Np * sizeof(double));
         if (ce == cudaSuccess) ce = cudaMemset(e.f, 0, 3 * Np * sizeof(double));
         if (ce == cudaSuccess) ce = cudaMemset(e.e_atom, 0, Np * sizeof(double));
+        if (ce == cudaSuccess) ce = cudaMemset(e.sum_q, 0, kSumWords * Np * sizeof(long long));
         if (ce == cudaSuccess) ce = cudaMemset(e.ctl, 0, sizeof(Ctl));
         if (ce == cudaSuccess) ce = cudaMemset(e.disp_box, 0, sizeof(unsigned long long) * B);
         if (ce != cudaSuccess) {

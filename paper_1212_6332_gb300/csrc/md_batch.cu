@@ -49,6 +49,7 @@ struct BoxArgs {
     int* n_up;  // float64 tile path's list layout data, kept valid across schedules
     int* rev;
     int* nl_lo;  // row-major lower parts for the reverse-index search
+    int sum_S;  // word split of the fixed-point density sums (sum_split)
     Ctl* ctl;
     int* box_done;
     int* box_state;
@@ -299,23 +300,25 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
             }
         }
         __syncthreads();
-        // density sums: round-to-nearest adds of the cached values in list
-        // order, as the tile schedule's sums
+        // density sums: the fixed-point totals of the cached values, which
+        // the tile schedule's pair pass forms by atomic adds of the same
+        // terms (integer sums: the same bits in any order)
         for (int t = tid; t < nb; t += NT) {
             const int64_t i = a0 + t;
             const int n = min(A.nn[i], A.max_nb);
-            double r_i = 0.0, ep = 0.0;
+            FixedSum qr, qv;
+            bool ok = true;
             for (int k = 0; k < n; ++k) {
                 const double2 w = cache_fv(A.pc, (int64_t)k * A.Np + i);
-                r_i = __dadd_rn(r_i, w.x);
-                ep = __dadd_rn(ep, w.y);
+                ok &= qr.add(w.x, A.sum_S) & qv.add(w.y, A.sum_S);
             }
-            double F, Fpi;
-            embed<KIND>(P, r_i, F, Fpi);
+            if (!ok) atomicOr(&A.ctl->status, kStNonFinite);
+            double r_i, Fpi, E;
+            embed_sums<KIND>(P, qr, qv, A.sum_S, 0, A.pc, A.Np, i, n, r_i, Fpi, E);
             A.rho[i] = r_i;
             A.Fp[i] = Fpi;
             sFp[t] = Fpi;
-            A.e_atom[i] = fma(0.5, ep, F);
+            A.e_atom[i] = E;
         }
         __syncthreads();
         // force pass and second half-kick
@@ -457,6 +460,7 @@ static void box_launch(Engine& e, int n_steps, cudaStream_t s) {
     A.n_up = e.n_up;
     A.rev = e.rev;
     A.nl_lo = e.nl_lo;
+    A.sum_S = sum_split(e.max_nb);
     A.ctl = e.ctl;
     A.box_done = e.box_done;
     A.box_state = e.box_state;

@@ -281,6 +281,119 @@ __device__ __forceinline__ longlong4_32a fixed_pos(const double4_32a& p, int kq)
     return q;
 }
 
+// ---------------------------------------------------------------- fixed-point sums
+//
+// The float64 density and pair-energy sums of Eq. (1)-(2) are taken in
+// fixed point: every term rounded once to the nearest multiple of 2^-kSumQ
+// (on the integer pipe, from its bit pattern), the terms added as integers,
+// the total rounded once to a double. Integer addition is exact and
+// associative, so the total does not depend on the order of the terms: the
+// pair pass adds each pair's rho(r) and V(r) to both of its atoms with
+// atomic adds and still gets the same bits on every run, and every kernel
+// that forms the sums in another order (small systems, the block-per-box
+// schedule, the Newton's-third-law variant) gets those bits too. Error: at
+// most K 2^-(kSumQ+1) = K 4.4e-16 for K terms, plus the final rounding
+// (a float64 sum rounds up to K times by half an ulp of its running total:
+// 4.4e-16 for totals in [4, 8), 1.8e-15 for the ~20 of a Cu density).
+//
+// Range: a term q = x 2^kSumQ is split as q = hi 2^S + lo with lo in
+// [-2^(S-1), 2^(S-1)) and a total keeps two 64-bit words, sum(lo) and
+// sum(hi). S = 62 - ceil(log2(list capacity)) keeps the low word of a full
+// list inside 64 bits; for the terms of ordinary configurations (|x| below
+// 2^(S-1-kSumQ), 16 eV for a capacity of 96) hi is 0 and only the low word
+// is touched. The total hi 2^S + lo is exact in 128 bits, so no term size
+// short of ~2^60 eV loses range.
+//
+// Small totals: the resolution is absolute, and F'(rho) = -1/(2 sqrt(rho))
+// turns an absolute error of rho into a relative one of 1/(2 rho) times
+// it. An atom whose fixed-point density is below kSumSmall (an atom with
+// almost no neighbours inside r_cut: a gas, a dimer near its cutoff; a
+// crystal's densities are ~10-100) therefore takes both of its sums again
+// in float64, over its cached pair values in list order (list_sums_f64),
+// in every kernel that finishes the density: the same rule on the same exact
+// total picks the same path everywhere.
+constexpr int kSumQ = 50;
+
+// S for lists of capacity cap (at most 2^20)
+__host__ __device__ inline int sum_split(int cap) {
+    int c = 0;
+    while (c < 20 && (1 << c) < cap) ++c;
+    return 62 - c;
+}
+
+// round(x 2^kSumQ) to the nearest integer (ties to even), split into
+// (hi, lo) at S; false for a non-finite x or |x| 2^kSumQ >= 2^(2S) (then
+// |hi| could reach 2^S, and a full list of such terms the 64-bit range)
+__device__ __forceinline__ bool split_fixed(double x, int S, long long& hi, long long& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = e - 1075 + kSumQ;  // |x| 2^kSumQ = m 2^sh
+    hi = 0;
+    lo = 0;
+    if (e == 0) return true;  // zero or subnormal: far below the resolution
+    if (sh >= 0) {
+        if (sh + 53 > 2 * S) return false;  // Inf, NaN or |x| >= 2^(2S - kSumQ) (~2^60 eV)
+        __int128 q = (__int128)m << sh;
+        if (b >> 63) q = -q;
+        const __int128 h = (q + ((__int128)1 << (S - 1))) >> S;
+        hi = (long long)h;
+        lo = (long long)(q - h * ((__int128)1 << S));
+        return true;
+    }
+    if (sh <= -54) return true;  // |x| 2^kSumQ < 1/2
+    const int r = -sh;
+    unsigned long long v = m >> r;
+    const unsigned long long rem = m & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (v & 1ull))) ++v;
+    // v < 2^53 <= 2^(S-1): the whole term is the low word
+    lo = (b >> 63) ? -(long long)v : (long long)v;
+    return true;
+}
+
+// (hi 2^S + lo) 2^-kSumQ rounded once to the nearest double
+__device__ __forceinline__ double sum_value(long long hi, long long lo, int S) {
+    const __int128 t = (__int128)hi * ((__int128)1 << S) + (__int128)lo;
+    const unsigned __int128 u = t < 0 ? (unsigned __int128)(-t) : (unsigned __int128)t;
+    const double a = round_u128((unsigned long long)(u >> 64), (unsigned long long)u, kSumQ);
+    return t < 0 ? -a : a;
+}
+
+// One fixed-point total.
+struct FixedSum {
+    long long lo = 0, hi = 0;
+    __device__ __forceinline__ bool add(double x, int S) {
+        long long h, l;
+        const bool ok = split_fixed(x, S, h, l);
+        lo += l;
+        hi += h;
+        return ok;
+    }
+    __device__ __forceinline__ double value(int S) const { return sum_value(hi, lo, S); }
+};
+
+// whether a density total is below kSumSmall = 2 (then its float64 list
+// sum serves instead)
+__device__ __forceinline__ bool sums_small(const FixedSum& qr) {
+    return qr.hi == 0 && qr.lo < (2ll << kSumQ);
+}
+
+// rho_i and sum_j V_ij in float64 from the cached pair values of atom i's
+// list, in list order (round-to-nearest adds)
+__device__ __forceinline__ void list_sums_f64(const double4_32a* __restrict__ pc, int64_t Np, int64_t i, int n,
+                                              double& r_i, double& ep) {
+    r_i = 0.0;
+    ep = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double2 w = reinterpret_cast<const double2*>(pc)[2 * ((int64_t)k * Np + i) + 1];
+        r_i = __dadd_rn(r_i, w.x);
+        ep = __dadd_rn(ep, w.y);
+    }
+}
+
+// The per-atom totals live in kSumWords = 4 words per atom, word w of atom
+// i at sq[w N_pad + i]: rho low, V low, rho high, V high.
+
 // r^2 < c^2 for non-negative, non-NaN doubles, as an integer compare
 __device__ __forceinline__ bool below(double r2, double c2) {
     return __double_as_longlong(r2) < __double_as_longlong(c2);
@@ -672,10 +785,49 @@ __device__ __forceinline__ void embed(const Pot& P, double rho, double& F, doubl
             Fp = 0.0;
             return;
         }
-        double s = sqrt(rho);
+        // sqrt(rho) and 1/sqrt(rho) on the integer pipe (rsqrt_sqrt, within
+        // 0.51 ulp each; float64 sqrt and division take ~20 float64
+        // instructions); rho below the normal range keeps the library forms
+        double y, s;
+        if (rho >= 0x1p-1022) {
+            rsqrt_sqrt(rho, y, s);
+        } else {
+            s = sqrt(rho);
+            y = 1.0 / s;
+        }
         F = -P.F_scale * s;
-        Fp = -0.5 * P.F_scale / s;
+        Fp = (-0.5 * P.F_scale) * y;
     }
+}
+
+// rho_i, F'(rho_i) and E_i = F(rho_i) + 1/2 sum_j V_ij from the fixed-point
+// totals of rho(r_ij) and V(r_ij) (type: the atom's species, splines)
+// For a total below kSumSmall, pc (the pair cache), Np and n (the list
+// length) give the float64 list sums instead (pc null: no such fallback,
+// for the Newton's-third-law variant, whose lower slots hold no values).
+template <int KIND>
+__device__ __forceinline__ void embed_sums(const Pot& P, const FixedSum& qr, const FixedSum& qv, int S, int type,
+                                           const double4_32a* __restrict__ pc, int64_t Np, int64_t i, int n,
+                                           double& rho, double& Fp, double& E) {
+    double ep;
+    if (pc && sums_small(qr)) {
+        list_sums_f64(pc, Np, i, n, rho, ep);
+    } else {
+        rho = qr.value(S);
+        ep = qv.value(S);
+    }
+    double F;
+    embed<KIND>(P, rho, F, Fp, type);
+    E = fma(0.5, ep, F);
+}
+
+// the totals of atom i from the four words of sq
+__device__ __forceinline__ void load_sums(const long long* __restrict__ sq, int64_t Np, int64_t i, FixedSum& qr,
+                                          FixedSum& qv) {
+    qr.lo = sq[i];
+    qv.lo = sq[Np + i];
+    qr.hi = sq[2 * Np + i];
+    qv.hi = sq[3 * Np + i];
 }
 
 // ---------------------------------------------------------------- float32

@@ -26,6 +26,7 @@ constexpr int kStOverflow = 1;
 constexpr int kStNonFinite = 2;
 constexpr int kStTimeout = 4;
 constexpr int kStCellSide = 8;  // a pressure-coupled box shrank below one list radius per cell
+constexpr int kSumWords = 4;  // fixed-point density totals: words per atom (rho, V; low and high)
 
 // Potential, passed by value to kernels.
 struct Pot {
@@ -201,6 +202,7 @@ struct Engine {
     double* e_atom = nullptr;
     float4* xo = nullptr;    // mixed: cell-local offsets, w = packed cell coords
     longlong4_32a* xq = nullptr;  // float64 pair pass: fixed-point positions (x 2^kq) and species
+    long long* sum_q = nullptr;   // float64 density sums: fixed-point totals of rho_i and sum_j V_ij, 4 words x N_pad
     int* perm = nullptr;     // sorted slot -> caller index
     int* perm_alt = nullptr;
     int* iperm = nullptr;    // caller index -> sorted slot

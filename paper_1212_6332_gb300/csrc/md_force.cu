@@ -1,9 +1,9 @@
 // Density pass (Sec. 3.3, Fig. 5) and force pass (Fig. 6, Eq. 3), float64.
 //
-// Both passes walk the full neighbour list of each atom (both i->j and j->i
-// are stored), so every atom's sums are private to one thread and no atomic
-// update is needed (the paper does the same on the GPU; its CPU code uses
-// Newton's third law instead, Sec. 4.3). The list is column-major, so a warp
+// The force pass walks the full neighbour list of each atom (both i->j and
+// j->i are stored), so every atom's force sum is private to one thread and
+// no atomic update is needed (the paper does the same on the GPU; its CPU
+// code uses Newton's third law instead, Sec. 4.3). The list is column-major, so a warp
 // of 32 consecutive atoms loads one 128-byte row of indices per neighbour
 // slot; neighbour positions are gathered from the Morton-sorted array,
 // mostly from L1/L2.
@@ -18,16 +18,19 @@
 //            both lists' slots (the partner's slot comes from the reverse
 //            index built with the list); all four are functions of r
 //            alone, so both slots get the same bits the partner would have
-//            computed;
-//   density: rho_i = sum rho, 1/2 sum V over i's slots in list order;
-//            F(rho_i), F'(rho_i);
+//            computed; the same pass adds rho(r) and V(r) to both atoms'
+//            64-bit fixed-point totals by atomic integer adds (exact and
+//            order-free, so every run gives the same bits: see sum_fixed);
+//   density: rho_i and 1/2 sum V from those totals; F(rho_i), F'(rho_i)
+//            (the pass no longer reads the cache entries);
 //   force:   F_i = sum_j s_ij x_j - x_i sum_j s_ij with
 //            s_ij = A + (F'_i + F'_j) B   [Eq. (3) regrouped]
 //            i.e. 6 float64 operations per entry and no separation,
 //            optionally followed by v_i += dt/2 F_i/m (second half-kick).
-// The sums run over each list in list order, as a full evaluation per atom
-// does (the block-per-box schedule evaluates every entry from its own
-// side), so both give identical results.
+// The force sums run over each list in list order, as a full evaluation per
+// atom does (the block-per-box schedule evaluates every entry from its own
+// side), and the density totals are integer sums of the same terms, so both
+// give identical results.
 #include "md_device.cuh"
 
 namespace mdk {
@@ -60,15 +63,53 @@ struct PairQueue {
     ST own[2][kQueue];       // slot of the entry in i's list
     ST mir[2][kQueue];       // slot of the mirror entry in j's list
     int pt[2][kQueue];       // type-pair table (several species)
+    int ai[2][kQueue];       // the pair's atoms (the fixed-point density sums)
+    int aj[2][kQueue];
 };
 
-template <int KIND, bool MIRROR, typename ST>
+// The fixed-point sums of a pair (DENS): rho(r) and V(r) added to both
+// atoms' totals by atomic integer adds (the high words only when a term
+// needs them).
+struct SumOut {
+    long long* sq;  // [kSumWords N_pad] fixed-point totals, zeroed before the pass
+    int64_t Np;
+    int S;          // sum_split(list capacity)
+    Ctl* ctl;
+};
+
+__device__ __forceinline__ void red_pair(unsigned long long* w, int i, int j, long long v) {
+    if (v) {
+        atomicAdd(w + i, (unsigned long long)v);
+        atomicAdd(w + j, (unsigned long long)v);
+    }
+}
+
+__device__ __forceinline__ void add_pair_sums(const SumOut& so, int i, int j, double fr, double V) {
+    long long hr, lr, hv, lv;
+    const bool ok = split_fixed(fr, so.S, hr, lr) & split_fixed(V, so.S, hv, lv);
+    if (!ok) {
+        atomicOr(&so.ctl->status, kStNonFinite);
+        return;
+    }
+    unsigned long long* u = reinterpret_cast<unsigned long long*>(so.sq);
+    red_pair(u, i, j, lr);
+    red_pair(u + so.Np, i, j, lv);
+    if (hr | hv) {
+        red_pair(u + 2 * so.Np, i, j, hr);
+        red_pair(u + 3 * so.Np, i, j, hv);
+    }
+}
+
+template <int KIND, bool MIRROR, bool DENS, typename ST>
 __device__ __forceinline__ void eval_queued(const Pot& P, const PairQueue<ST>& q, int r, int p,
-                                            double4_32a* __restrict__ pc) {
+                                            double4_32a* __restrict__ pc, const SumOut& so) {
     const double r2 = q.r2[r][p];
     double A = 0.0, B = 0.0, V = 0.0, fr = 0.0;
     const int pt = KIND == MD_POT_SPLINE ? q.pt[r][p] : 0;
-    if (below(r2, P.rc2)) pair_eval<KIND>(P, P.exp_T, r2, V, fr, A, B, pt);
+    if (below(r2, P.rc2)) {
+        pair_eval<KIND>(P, P.exp_T, r2, V, fr, A, B, pt);
+        if (DENS) add_pair_sums(so, q.ai[r][p], q.aj[r][p], fr, V);
+    }
     const double4_32a c = make_double4_32a(A, B, fr, V);
     pc[(int64_t)q.own[r][p]] = c;
     if (MIRROR) pc[(int64_t)q.mir[r][p]] = c;
@@ -77,12 +118,19 @@ __device__ __forceinline__ void eval_queued(const Pot& P, const PairQueue<ST>& q
 // The positions in fixed point (x 2^kq, kq of the atom's box) with the
 // species label, gathered by the pair pass for its exact r^2: one
 // conversion per atom and step instead of one per list entry.
+// With sq, also clears the fixed-point sums that the pair pass adds into.
 template <bool SINGLE>
-__global__ void __launch_bounds__(kFNT) k_fixed_positions(int64_t N, Geo g, const double4_32a* __restrict__ x,
-                                                          longlong4_32a* __restrict__ xq, const Ctl* ctl) {
+__global__ void __launch_bounds__(kFNT) k_fixed_positions(int64_t N, int64_t Np, Geo g,
+                                                          const double4_32a* __restrict__ x,
+                                                          longlong4_32a* __restrict__ xq, long long* __restrict__ sq,
+                                                          const Ctl* ctl) {
     if (load_status(ctl)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    if (sq) {
+#pragma unroll
+        for (int w = 0; w < kSumWords; ++w) sq[w * Np + i] = 0;
+    }
     const int b = SINGLE ? 0 : g.atom_box[i];
     const int kq = SINGLE ? box_kq(g.L0[0], g.L0[1], g.L0[2]) : box_kq(g.L[3 * b], g.L[3 * b + 1], g.L[3 * b + 2]);
     xq[i] = fixed_pos(x[i], kq);
@@ -125,13 +173,13 @@ __device__ __forceinline__ PairRow load_pair_row(int e, bool valid, int64_t i, c
 #else
 #define MD_PAIR_BOUNDS __launch_bounds__(kFNT)
 #endif
-template <int KIND, bool SINGLE, bool MIRROR, typename ST>
+template <int KIND, bool SINGLE, bool MIRROR, bool DENS, typename ST>
 __global__ void MD_PAIR_BOUNDS k_pairs_half(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P, float rc2f,
                                                      float rs2f, const longlong4_32a* __restrict__ xq,
                                                      const float4* __restrict__ xo, const int* __restrict__ nn,
                                                      const int* __restrict__ nl, const int* __restrict__ rev,
                                                      const int* __restrict__ n_up, int max_nb,
-                                                     double4_32a* __restrict__ pc, const Ctl* ctl) {
+                                                     double4_32a* __restrict__ pc, SumOut so, const Ctl* ctl) {
     if (load_status(ctl)) return;
     __shared__ PairQueue<ST> queues[kFNT / 32];
     const int lane = threadIdx.x & 31;
@@ -180,7 +228,8 @@ __global__ void MD_PAIR_BOUNDS k_pairs_half(int64_t N, int64_t Np, Geo g, CellSe
             bool in = false, tq = false;
             double r2 = 0.0;
             const ST own = (ST)((long long)k * Np + i);
-            const ST mir = (ST)((long long)cur.rv * Np + entry_slot(cur.e));
+            const int j_cur = entry_slot(cur.e);
+            const ST mir = (ST)((long long)cur.rv * Np + j_cur);
             const int pt = KIND == MD_POT_SPLINE && P.n_types > 1
                                ? pair_table(P.n_types, ti, (int)cur.qj.w)
                                : 0;
@@ -209,6 +258,10 @@ __global__ void MD_PAIR_BOUNDS k_pairs_half(int64_t N, int64_t Np, Geo g, CellSe
                     q.own[r][p] = own;
                     q.mir[r][p] = mir;
                     if (KIND == MD_POT_SPLINE) q.pt[r][p] = pt;
+                    if (DENS) {
+                        q.ai[r][p] = (int)i;
+                        q.aj[r][p] = j_cur;
+                    }
                 }
                 qn[r] += __popc(m);
             }
@@ -217,7 +270,7 @@ __global__ void MD_PAIR_BOUNDS k_pairs_half(int64_t N, int64_t Np, Geo g, CellSe
             for (int r = 0; r < 2; ++r) {
                 if (qn[r] >= 32) {
                     qn[r] -= 32;
-                    eval_queued<KIND, MIRROR, ST>(P, q, r, qn[r] + lane, pc);
+                    eval_queued<KIND, MIRROR, DENS, ST>(P, q, r, qn[r] + lane, pc, so);
                     __syncwarp();
                 }
             }
@@ -227,13 +280,13 @@ __global__ void MD_PAIR_BOUNDS k_pairs_half(int64_t N, int64_t Np, Geo g, CellSe
     // pair_eval, which still costs less than two part-empty batches)
     if (qn[0] + qn[1] <= 32) {
         if (lane < qn[0])
-            eval_queued<KIND, MIRROR, ST>(P, q, 0, lane, pc);
+            eval_queued<KIND, MIRROR, DENS, ST>(P, q, 0, lane, pc, so);
         else if (lane < qn[0] + qn[1])
-            eval_queued<KIND, MIRROR, ST>(P, q, 1, lane - qn[0], pc);
+            eval_queued<KIND, MIRROR, DENS, ST>(P, q, 1, lane - qn[0], pc, so);
     } else {
 #pragma unroll
         for (int r = 0; r < 2; ++r)
-            if (lane < qn[r]) eval_queued<KIND, MIRROR, ST>(P, q, r, lane, pc);
+            if (lane < qn[r]) eval_queued<KIND, MIRROR, DENS, ST>(P, q, r, lane, pc, so);
     }
 }
 
@@ -248,43 +301,26 @@ __device__ __forceinline__ bool is_zero2(double2 c) {
     return (__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0;
 }
 
+// rho_i and the pair energy from the fixed-point totals the pair pass added
+// (see sum_fixed), then F(rho_i), F'(rho_i) and E_i = F(rho_i) + 1/2 sum V.
 template <int KIND>
-__global__ void __launch_bounds__(kFNT) k_rho_sum(int64_t N, int64_t Np, Pot P, const int* __restrict__ nn,
-                                                  int max_nb, const double4_32a* __restrict__ pc,
-                                                  const double4_32a* __restrict__ x, double* __restrict__ rho,
-                                                  double* __restrict__ Fp, double* __restrict__ e_atom,
-                                                  const Ctl* ctl) {
+__global__ void __launch_bounds__(kFNT) k_embed_sums(int64_t N, int64_t Np, Pot P, const long long* __restrict__ sq,
+                                                     int S, const int* __restrict__ nn, int max_nb,
+                                                     const double4_32a* __restrict__ pc,
+                                                     const double4_32a* __restrict__ x,
+                                                     double* __restrict__ rho, double* __restrict__ Fp,
+                                                     double* __restrict__ e_atom, const Ctl* ctl) {
     if (load_status(ctl)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < N;
-    const int n = active ? min(nn[i], max_nb) : 0;
-    const double2 zero = make_double2(0.0, 0.0);
-    // explicit round-to-nearest adds: the block-per-box schedule sums the
-    // same values in the same order and must not fuse them differently
-    double r_i = 0.0, ep = 0.0;
-    int k = 0;
-    double2 w = n > 0 ? cache_fv(pc, i) : zero;
-    while (true) {
-        while (k < n && is_zero2(w)) {
-            ++k;
-            w = k < n ? cache_fv(pc, (int64_t)k * Np + i) : zero;
-        }
-        const bool has = k < n;
-        if (!__any_sync(0xffffffffu, has)) break;
-        if (has) {
-            const double2 wn = k + 1 < n ? cache_fv(pc, (int64_t)(k + 1) * Np + i) : zero;
-            r_i = __dadd_rn(r_i, w.x);
-            ep = __dadd_rn(ep, w.y);
-            ++k;
-            w = wn;
-        }
-    }
-    if (!active) return;
-    double F, Fpi;
-    embed<KIND>(P, r_i, F, Fpi, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0);
+    if (i >= N) return;
+    FixedSum qr, qv;
+    load_sums(sq, Np, i, qr, qv);
+    double r_i, Fpi, E;
+    embed_sums<KIND>(P, qr, qv, S, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0, pc, Np, i,
+                     min(nn[i], max_nb), r_i, Fpi, E);
     rho[i] = r_i;
     Fp[i] = Fpi;
-    e_atom[i] = fma(0.5, ep, F);
+    e_atom[i] = E;
 }
 
 // VIR: also the per-atom virial w_i = -1/2 sum_j s_ij r_ij^2 (the pair
@@ -378,9 +414,10 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
 //   k_rho_small / k_force_small: 128 threads per 32 atoms stage a chunk of
 //     32 list rows of their atoms in shared memory (all loads in flight, and
 //     for the force pass s_ij and the partner's image position formed at the
-//     same time), then one lane per atom adds them in list order with the
-//     operations of k_rho_sum / k_force. The per-atom sums therefore keep
-//     their order and the results are bit-identical to the passes above.
+//     same time), then one lane per atom adds them: the density terms in
+//     the fixed point of k_pairs_half's atomic adds (exact integer sums),
+//     the force terms in list order with the operations of k_force. The
+//     results are therefore bit-identical to the passes above.
 #ifndef MD_SMALL_ATOMS
 #define MD_SMALL_ATOMS 32768
 #endif
@@ -451,8 +488,8 @@ template <int KIND>
 __global__ void __launch_bounds__(kFNT) k_rho_small(int64_t N, int64_t Np, Pot P, const int* __restrict__ nn,
                                                     int max_nb, const double4_32a* __restrict__ pc,
                                                     const double4_32a* __restrict__ x, double* __restrict__ rho,
-                                                    double* __restrict__ Fp, double* __restrict__ e_atom,
-                                                    const Ctl* ctl) {
+                                                    double* __restrict__ Fp, double* __restrict__ e_atom, int S,
+                                                    Ctl* ctl) {
     if (load_status(ctl)) return;
     __shared__ double2 sw[kSmallRows][32];
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
@@ -460,7 +497,8 @@ __global__ void __launch_bounds__(kFNT) k_rho_small(int64_t N, int64_t Np, Pot P
     const bool active = i < N;
     const int n = active ? min(nn[i], max_nb) : 0;
     const int kmax = warp_max(n);  // the same 32 atoms in every warp of the block
-    double r_i = 0.0, ep = 0.0;
+    FixedSum qr, qv;
+    bool ok = true;
     for (int k0 = 0; k0 < kmax; k0 += kSmallRows) {
 #pragma unroll
         for (int r = wq; r < kSmallRows; r += kFNT / 32) {
@@ -469,23 +507,24 @@ __global__ void __launch_bounds__(kFNT) k_rho_small(int64_t N, int64_t Np, Pot P
         }
         __syncthreads();
         if (wq == 0) {
-            // round-to-nearest adds in list order, as k_rho_sum (whose
-            // skipped zero entries leave its sums unchanged)
+            // the fixed-point totals of the pair pass's atomic adds (the same
+            // terms, so the same bits in any order)
             const int kend = min(n - k0, kSmallRows);
             for (int r = 0; r < kend; ++r) {
                 const double2 w = sw[r][lane];
-                r_i = __dadd_rn(r_i, w.x);
-                ep = __dadd_rn(ep, w.y);
+                ok &= qr.add(w.x, S) & qv.add(w.y, S);
             }
         }
         __syncthreads();
     }
     if (wq != 0 || !active) return;
-    double F, Fpi;
-    embed<KIND>(P, r_i, F, Fpi, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0);
+    if (!ok) atomicOr(&ctl->status, kStNonFinite);
+    double r_i, Fpi, E;
+    embed_sums<KIND>(P, qr, qv, S, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0, pc, Np, i, n, r_i,
+                     Fpi, E);
     rho[i] = r_i;
     Fp[i] = Fpi;
-    e_atom[i] = fma(0.5, ep, F);
+    e_atom[i] = E;
 }
 
 template <bool SINGLE, bool VIR>
@@ -575,12 +614,16 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
 // Float64 variant in the style of the paper's CPU code (Sec. 4.3): the pair
 // pass writes only the upper slot of each pair, and the density and force
 // passes walk only the upper entries of each list, adding every pair's term
-// to both atoms, to the partner by a float64 atomic add (rho_j, V_ij, and
-// -s_ij d_ij for the force). That halves the cache bytes and the float64
-// work of both sums at the price of one atomic per pair and component; the
-// order in which the atomics land varies, so the last bits of rho, F and
-// e_atom vary from run to run (the full-list passes are reproducible).
-// rho, e_atom and f are zeroed before their passes.
+// to both atoms, to the partner by an atomic add (rho_j and V_ij into the
+// fixed-point totals, -s_ij d_ij into the float64 force). That halves the
+// cache bytes and the float64 work of both sums at the price of one atomic
+// per pair and component. The density totals are exact integer sums, the
+// same bits as the full-list path (but for densities below kSumSmall, which
+// the full-list path takes in float64 from its lower slots, that this
+// variant does not write); the order in which the float64 force
+// atomics land varies, so the last bits of F vary from run to run (the
+// full-list passes are reproducible). The totals and f are zeroed before
+// their passes.
 
 // Upper entries of a list: rows 0..n_up-1 of a rotated list, else (a list
 // kept ascending) the entries with j > i among all rows.
@@ -592,41 +635,58 @@ __device__ __forceinline__ int upper_rows(const int* __restrict__ nn, const int*
 
 __global__ void __launch_bounds__(kFNT) k_rho_n3(int64_t N, int64_t Np, const int* __restrict__ nn,
                                                  const int* __restrict__ nl, const int* __restrict__ n_up, int max_nb,
-                                                 const double4_32a* __restrict__ pc, double* __restrict__ rho,
-                                                 double* __restrict__ ep, const Ctl* ctl) {
+                                                 const double4_32a* __restrict__ pc, long long* __restrict__ sq,
+                                                 int S, Ctl* ctl) {
     if (load_status(ctl)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int n = upper_rows(nn, n_up, max_nb, i);
-    double r_i = 0.0, e_i = 0.0;
+    unsigned long long* u = reinterpret_cast<unsigned long long*>(sq);
+    FixedSum qr, qv;
+    bool ok = true;
     for (int k = 0; k < n; ++k) {
         const int64_t slot = (int64_t)k * Np + i;
         const double2 w = cache_fv(pc, slot);
         if (is_zero2(w)) continue;
         const int j = entry_slot(nl[slot]);
         if (j <= i) continue;
-        r_i += w.x;
-        e_i += w.y;
-        atomicAdd(&rho[j], w.x);
-        atomicAdd(&ep[j], w.y);
+        long long hr, lr, hv, lv;
+        ok &= split_fixed(w.x, S, hr, lr) & split_fixed(w.y, S, hv, lv);
+        qr.lo += lr;
+        qr.hi += hr;
+        qv.lo += lv;
+        qv.hi += hv;
+        atomicAdd(u + j, (unsigned long long)lr);
+        atomicAdd(u + Np + j, (unsigned long long)lv);
+        if (hr | hv) {
+            atomicAdd(u + 2 * Np + j, (unsigned long long)hr);
+            atomicAdd(u + 3 * Np + j, (unsigned long long)hv);
+        }
     }
-    atomicAdd(&rho[i], r_i);
-    atomicAdd(&ep[i], e_i);
+    if (!ok) atomicOr(&ctl->status, kStNonFinite);
+    atomicAdd(u + i, (unsigned long long)qr.lo);
+    atomicAdd(u + Np + i, (unsigned long long)qv.lo);
+    atomicAdd(u + 2 * Np + i, (unsigned long long)qr.hi);
+    atomicAdd(u + 3 * Np + i, (unsigned long long)qv.hi);
 }
 
-// F(rho_i), F'(rho_i); e_atom arrives holding sum_j V_ij and leaves holding
-// F(rho_i) + 1/2 sum_j V_ij.
+// rho_i, F(rho_i), F'(rho_i) and E_i from the fixed-point totals
 template <int KIND>
-__global__ void __launch_bounds__(kFNT) k_embed_n3(int64_t N, Pot P, const double4_32a* __restrict__ x,
-                                                   const double* __restrict__ rho, double* __restrict__ Fp,
-                                                   double* __restrict__ e_atom, const Ctl* ctl) {
+__global__ void __launch_bounds__(kFNT) k_embed_n3(int64_t N, int64_t Np, Pot P, const double4_32a* __restrict__ x,
+                                                   const long long* __restrict__ sq, int S, double* __restrict__ rho,
+                                                   double* __restrict__ Fp, double* __restrict__ e_atom,
+                                                   const Ctl* ctl) {
     if (load_status(ctl)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double F, Fpi;
-    embed<KIND>(P, rho[i], F, Fpi, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0);
+    FixedSum qr, qv;
+    load_sums(sq, Np, i, qr, qv);
+    double r_i, Fpi, E;
+    embed_sums<KIND>(P, qr, qv, S, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0, nullptr, Np, i, 0,
+                     r_i, Fpi, E);
+    rho[i] = r_i;
     Fp[i] = Fpi;
-    e_atom[i] = fma(0.5, e_atom[i], F);
+    e_atom[i] = E;
 }
 
 // VIR: w_atom[i] = -sum over i's upper pairs of s_ij r_ij^2 (each pair
@@ -693,11 +753,11 @@ static float screen_r2f(double rc2) { return nextafterf((float)(rc2 * (1.0 + kSc
 
 // persistent pair pass: all resident blocks of this instantiation on every
 // SM, at most one 32-atom group per warp
-template <int KIND, bool SINGLE, bool MIRROR, typename ST>
+template <int KIND, bool SINGLE, bool MIRROR, bool DENS, typename ST>
 static int pair_blocks(const Engine& e) {
     static int per_sm = 0;
     if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_half<KIND, SINGLE, MIRROR, ST>, kFNT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_half<KIND, SINGLE, MIRROR, DENS, ST>, kFNT, 0);
         per_sm = std::max(per_sm, 1);
     }
     const int64_t groups = (e.N + 31) / 32, per_block = kFNT / 32;
@@ -705,23 +765,29 @@ static int pair_blocks(const Engine& e) {
 }
 
 // The queued pair pass with list-slot indices as narrow as the list array
-// allows, after the fixed-point copy of the positions it gathers.
-template <int KIND, bool SINGLE, bool MIRROR>
+// allows, after the fixed-point copy of the positions it gathers. DENS: the
+// pass also adds rho(r) and V(r) of every pair into both atoms' fixed-point
+// totals (cleared by the position copy), which k_embed_sums turns into rho_i.
+template <int KIND, bool SINGLE, bool MIRROR, bool DENS>
 static void launch_pairs_half(Engine& e, const Geo& g, cudaStream_t s) {
     e.launches += 1;
-    k_fixed_positions<SINGLE><<<(int)((e.N + kFNT - 1) / kFNT), kFNT, 0, s>>>(e.N, g, e.x, e.xq, e.ctl);
+    k_fixed_positions<SINGLE><<<(int)((e.N + kFNT - 1) / kFNT), kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.xq,
+                                                                             DENS ? e.sum_q : nullptr, e.ctl);
+    const SumOut so{e.sum_q, e.N_pad, sum_split(e.max_nb), e.ctl};
     // 32-bit slots: 85 instead of 89 registers, 18 instead of 22.5 KB of
     // queues per block (4M-atom step 8.69 -> 8.63 ms; the same bits);
     // 6 blocks per SM forced (80 registers, spills) measured slower
     const bool narrow = (int64_t)e.N_pad * e.max_nb <= (int64_t)0xffffffffll;
     if (narrow)
-        k_pairs_half<KIND, SINGLE, MIRROR, unsigned><<<pair_blocks<KIND, SINGLE, MIRROR, unsigned>(e), kFNT, 0, s>>>(
-            e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.xq, e.xo, e.nn,
-            e.nl, e.rev, e.n_up, e.max_nb, e.pc, e.ctl);
+        k_pairs_half<KIND, SINGLE, MIRROR, DENS, unsigned>
+            <<<pair_blocks<KIND, SINGLE, MIRROR, DENS, unsigned>(e), kFNT, 0, s>>>(
+                e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.xq, e.xo,
+                e.nn, e.nl, e.rev, e.n_up, e.max_nb, e.pc, so, e.ctl);
     else
-        k_pairs_half<KIND, SINGLE, MIRROR, long long><<<pair_blocks<KIND, SINGLE, MIRROR, long long>(e), kFNT, 0, s>>>(
-            e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.xq, e.xo, e.nn,
-            e.nl, e.rev, e.n_up, e.max_nb, e.pc, e.ctl);
+        k_pairs_half<KIND, SINGLE, MIRROR, DENS, long long>
+            <<<pair_blocks<KIND, SINGLE, MIRROR, DENS, long long>(e), kFNT, 0, s>>>(
+                e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), (float)e.pot.rs2, e.xq, e.xo,
+                e.nn, e.nl, e.rev, e.n_up, e.max_nb, e.pc, so, e.ctl);
 }
 
 // The small-system kernels: same results, more parallelism (see above).
@@ -739,12 +805,12 @@ static void run_fp64_small(Engine& e, int kick, cudaStream_t s, bool virial) {
                 e.N, e.N_pad, g, single_cell_sep(e), e.pot, screen_r2f(e.pot.rc2), e.x, e.xo, e.nn, e.nl, e.rev,
                 e.n_up, e.max_nb, e.pc, e.ctl);
         else
-            launch_pairs_half<KIND, SINGLE, true>(e, g, s);
+            launch_pairs_half<KIND, SINGLE, true, false>(e, g, s);
     }
     {
         PhaseScope scope(e, MD_PHASE_DENSITY, s);
         k_rho_small<KIND><<<nb32, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.nn, e.max_nb, e.pc, e.x, e.rho, e.Fp,
-                                                e.e_atom, e.ctl);
+                                                e.e_atom, sum_split(e.max_nb), e.ctl);
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     if (virial)
@@ -767,12 +833,12 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s, bool virial) {
     e.launches += 3;
     {
         PhaseScope scope(e, MD_PHASE_PAIRS, s);
-        launch_pairs_half<KIND, SINGLE, true>(e, g, s);
+        launch_pairs_half<KIND, SINGLE, true, true>(e, g, s);
     }
     {
         PhaseScope scope(e, MD_PHASE_DENSITY, s);
-        k_rho_sum<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.nn, e.max_nb, e.pc, e.x, e.rho, e.Fp, e.e_atom,
-                                            e.ctl);
+        k_embed_sums<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.sum_q, sum_split(e.max_nb), e.nn, e.max_nb,
+                                               e.pc, e.x, e.rho, e.Fp, e.e_atom, e.ctl);
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     if (virial)
@@ -791,14 +857,15 @@ static void run_fp64_n3(Engine& e, int kick, cudaStream_t s, bool virial) {
     e.launches += 4 + (kick ? 1 : 0);
     {
         PhaseScope scope(e, MD_PHASE_PAIRS, s);
-        launch_pairs_half<KIND, SINGLE, false>(e, g, s);
+        launch_pairs_half<KIND, SINGLE, false, false>(e, g, s);
     }
     {
         PhaseScope scope(e, MD_PHASE_DENSITY, s);
-        cudaMemsetAsync(e.rho, 0, sizeof(double) * e.N, s);
-        cudaMemsetAsync(e.e_atom, 0, sizeof(double) * e.N, s);
-        k_rho_n3<<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.nn, e.nl, e.n_up, e.max_nb, e.pc, e.rho, e.e_atom, e.ctl);
-        k_embed_n3<KIND><<<nb, kFNT, 0, s>>>(e.N, e.pot, e.x, e.rho, e.Fp, e.e_atom, e.ctl);
+        cudaMemsetAsync(e.sum_q, 0, sizeof(long long) * kSumWords * e.N_pad, s);
+        k_rho_n3<<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.nn, e.nl, e.n_up, e.max_nb, e.pc, e.sum_q,
+                                     sum_split(e.max_nb), e.ctl);
+        k_embed_n3<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.x, e.sum_q, sum_split(e.max_nb), e.rho, e.Fp,
+                                             e.e_atom, e.ctl);
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     cudaMemsetAsync(e.f, 0, sizeof(double) * 3 * e.N_pad, s);
