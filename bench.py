@@ -62,9 +62,9 @@ ORACLE_CELLS = 50        # CPU sample: 500,000 atoms of the same lattice
 #   spline: separation 3, r^2 5, rsqrt 8, r 1, u 1, V, V', rho, rho' 20,
 #        A and B 2 -> 40
 #   bytes: list 4K, reverse index 2K, the 32-byte cache entry written to
-#   both slots 32K, x 32
-# float64 density sums (k_rho_sum): 2 per entry; count 4, (rho, V) reads
-#   16K, rho/F'/E_i writes 24
+#   both slots 32K, x 32, the fixed-point density totals (4 words) 32
+# float64 density finish (k_embed_sums): F, F' and E_i from the fixed-point
+#   totals, 6 per atom; totals 32, count 4, rho/F'/E_i writes 24
 # float64 force pass (k_force): s = A + (F'_i + F'_j) B 3 and F_i += s x_j
 #   6, +1 for the total -> 10 per entry inside r_cut; list 4K, (A, B) 16K,
 #   count 4, x_i 32, F'_i 8, F 24, v 48
@@ -90,9 +90,9 @@ def kernel_model(phase: str, precision: str, kind: str, K: float, Ki: float):
     if precision == "fp64":
         if phase == "pairs":
             return ("k_pairs_half (float64 pair functions)",
-                    Ki / 2 * PAIR64.get(kind, 40.0) + (K - Ki) / 2 * 8.0, 38.0 * K + 32.0, "fp64")
+                    Ki / 2 * PAIR64.get(kind, 40.0) + (K - Ki) / 2 * 8.0, 38.0 * K + 64.0, "fp64")
         if phase == "density":
-            return "k_rho_sum (float64 density sums)", 2.0 * K, 16.0 * K + 28.0, "fp64"
+            return "k_embed_sums (fixed-point density totals, F, F')", 6.0, 60.0, "fp64"
         if phase == "force":
             return "k_force (float64 force pass)", 10.0 * Ki, 20.0 * K + 116.0, "fp64"
         if phase == "grad":
@@ -116,9 +116,18 @@ FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 STEP_BYTES = lambda K: 2 * 4.0 * K + 2 * 24.0  # noqa: E731
 # DRAM bytes (read + write) per atom of one k_pairs_half launch, from an ncu
 # capture of 1,048,576 atoms of the same lattice, potential and temperature
-# (0.453 GB read + 1.777 GB written; profiles/k_pairs_half_rgl_cu_1m_fp64.md);
+# (0.484 GB read + 1.813 GB written; profiles/k_pairs_half_rgl_cu_1m_fp64.md);
 # traffic grows in proportion to the atom count.
-PAIRS_DRAM_BYTES_PER_ATOM = (0.452660224e9 + 1.777106e9) / 1048576
+PAIRS_DRAM_BYTES_PER_ATOM = (0.484499e9 + 1.813424e9) / 1048576
+# What the same capture counts per evaluated pair (22.03M pairs): executed
+# float64 instructions (DFMA + DMUL + DADD) and their flops (an FMA as 2),
+# and the share of issue slots in use. The pass takes r^2, 1/r, r, the
+# table index and the exponentials' high-order terms on the integer and
+# float32 pipes, so it executes fewer float64 flops than the algorithm
+# counts (59 per RGL pair).
+PAIRS_FP64_INST_PER_PAIR = 13.51
+PAIRS_FP64_FLOPS_PER_PAIR = 20.75
+PAIRS_ISSUE_ACTIVE = 0.671
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
            0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
@@ -801,6 +810,24 @@ def main():
                                     "after the timed ones",
                 "hbm": main_block.get("hbm"), "binding": main_block.get("binding"),
                 "peaks": peaks}
+    if dom == "pairs" and args.precision == "fp64" and args.spec == "rgl_cu" and alu.get("frac"):
+        # the algorithm's float64 flops per second exceed the float64 pipe's
+        # peak because part of the work runs exactly on other pipes: the
+        # executed float64 flops (ncu count per pair) against the same peak
+        # say how busy the float64 pipe is, the issue share what binds
+        pairs_n = N * K_in / 2.0
+        ex = pairs_n * PAIRS_FP64_FLOPS_PER_PAIR / (main_block["launch_ms"] * 1e-3) / 1e12
+        roofline["executed_fp64"] = {
+            "flops_per_pair": PAIRS_FP64_FLOPS_PER_PAIR, "inst_per_pair": PAIRS_FP64_INST_PER_PAIR,
+            "achieved": ex, "peak": alu.get("peak"), "unit": "TFLOP/s", "frac": ex / alu.get("peak"),
+            "source": "float64 instruction counts per evaluated pair from the ncu capture of 1,048,576 atoms "
+                      "(profiles/k_pairs_half_rgl_cu_1m_fp64.md) over this run's launch time"}
+        roofline["issue_active"] = PAIRS_ISSUE_ACTIVE
+        roofline["note"] = ("achieved/frac: the algorithm's float64 flops (59 per RGL pair, counted for a plain "
+                            "float64 evaluation) over the launch time; above 1 because r^2, 1/r, r, the table "
+                            "index and the exponentials' high-order terms run exactly on the integer and float32 "
+                            "pipes. The pass is bound by instruction issue (issue_active, ncu) with the float64 "
+                            "pipe at executed_fp64.frac")
     # the whole step against HBM by its algorithmic byte count (list and
     # positions read by both force passes)
     step_bytes = N * STEP_BYTES(K_list)
