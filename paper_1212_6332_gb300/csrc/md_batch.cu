@@ -330,23 +330,25 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
             // the tile schedule's regrouped sum, sum_j s_ij x_j - x_i sum_j s_ij,
             // in the same order: the same bits
             double fx = 0.0, fy = 0.0, fz = 0.0, ssum = 0.0;
+            ShiftSum shift;
             for (int k = 0; k < n; ++k) {
                 const int64_t slot = (int64_t)k * A.Np + i;
                 double2 c = A.ab[2 * slot];
                 if ((__double_as_longlong(c.x) | __double_as_longlong(c.y)) == 0) continue;
                 const int e = A.nl[slot];
                 const int jl = entry_slot(e) - (int)a0;
-                double px, py, pz;
-                image_pos(sx[jl], entry_code(e), L, px, py, pz);
+                const unsigned code = entry_code(e);
+                const double4_32a xj = sx[jl];
                 double s = fma(Fpi + sFp[jl], c.y, c.x);
+                if (code != kNoShift) shift.add(s, code);
                 ssum += s;
-                fx = fma(s, px, fx);
-                fy = fma(s, py, fy);
-                fz = fma(s, pz, fz);
+                fx = fma(s, xj.x, fx);
+                fy = fma(s, xj.y, fy);
+                fz = fma(s, xj.z, fz);
             }
-            fx = fma(-xi.x, ssum, fx);
-            fy = fma(-xi.y, ssum, fy);
-            fz = fma(-xi.z, ssum, fz);
+            fx = fma(L[0], shift.value(0), fma(-xi.x, ssum, fx));
+            fy = fma(L[1], shift.value(1), fma(-xi.y, ssum, fy));
+            fz = fma(L[2], shift.value(2), fma(-xi.z, ssum, fz));
             A.f[i] = fx;
             A.f[A.Np + i] = fy;
             A.f[2 * A.Np + i] = fz;

@@ -391,6 +391,46 @@ __device__ __forceinline__ void list_sums_f64(const double4_32a* __restrict__ pc
     }
 }
 
+// The periodic image of a list entry in the force sums. Eq. (3) regrouped,
+// F_i = sum_j s_ij (x_j + c_j L) - x_i sum_j s_ij with c_j in {-1, 0, 1}^3 the
+// entry's image, is taken as sum_j s_ij x_j - x_i sum_j s_ij + L sigma with
+// sigma = sum_j c_j s_ij per axis accumulated exactly in 128-bit fixed point
+// (s 2^60 rounded once, half away from zero) on the integer pipe, and L sigma
+// rounded once per atom. In small periodic boxes a quarter of the entries
+// carry an image; the three float64 adds that formed x_j + c L ran in a
+// branch nearly every warp step took, where the integer adds cost a few
+// integer instructions on the lanes that need them.
+struct ShiftSum {
+    __int128 a[3] = {0, 0, 0};
+    __device__ __forceinline__ void add(double s, unsigned code) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+        const int e = (int)((b >> 52) & 0x7ffu);
+        const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+        const int sh = e - 1075 + 60;  // |s| 2^60 = m 2^sh
+        __int128 q = 0;
+        if (e != 0) {
+            if (sh >= 0)
+                q = (__int128)m << (sh < 64 ? sh : 64);  // (|s| >= 2^17: beyond any force term)
+            else if (sh > -54)
+                q = (__int128)((m + (1ull << (-sh - 1))) >> -sh);
+        }
+        if (b >> 63) q = -q;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const unsigned c = (code >> (2 * ax)) & 3u;
+            if (c == 0u) a[ax] -= q;
+            if (c == 2u) a[ax] += q;
+        }
+    }
+    // sigma of axis ax rounded once to the nearest double
+    __device__ __forceinline__ double value(int ax) const {
+        const __int128 t = a[ax];
+        const unsigned __int128 u = t < 0 ? (unsigned __int128)(-t) : (unsigned __int128)t;
+        const double v = round_u128((unsigned long long)(u >> 64), (unsigned long long)u, 60);
+        return t < 0 ? -v : v;
+    }
+};
+
 // The per-atom totals live in kSumWords = 4 words per atom, word w of atom
 // i at sq[w N_pad + i]: rho low, V low, rho high, V high.
 

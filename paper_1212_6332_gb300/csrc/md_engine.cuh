@@ -261,6 +261,7 @@ struct Engine {
     // CUDA graph of one step (and of a chunk of steps)
     cudaGraphExec_t graph_step = nullptr;
     cudaGraphExec_t graph_chunk = nullptr;
+    cudaGraphExec_t graph_last = nullptr;  // one step that forms the pair-energy sums (the last of a run)
     int graph_chunk_len = 0;
     bool graph_hist = false;
     int sched_choice = 0;  // autotuner result for batches (0 = unknown)
@@ -270,7 +271,12 @@ struct Engine {
     int* box_done = nullptr;
     int* box_state = nullptr;
     std::vector<BoxClass> box_classes;
-    long long graph_chunk_kernels = 0, graph_step_kernels = 0;
+    long long graph_chunk_kernels = 0, graph_step_kernels = 0, graph_last_kernels = 0;
+    // whether the next float64 force evaluation adds V(r) into the
+    // fixed-point pair-energy totals: off for the steps of a run before its
+    // last when no step records its energy (dynamics needs rho_i, F and F'
+    // only; the energies are read after the last step)
+    bool pair_energy = true;
 
     // profiling: launch counter and phase events
     long long launches = 0;

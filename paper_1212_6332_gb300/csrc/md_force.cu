@@ -74,6 +74,7 @@ struct SumOut {
     long long* sq;  // [kSumWords N_pad] fixed-point totals, zeroed before the pass
     int64_t Np;
     int S;          // sum_split(list capacity)
+    bool with_v;    // also the pair-energy totals (Engine::pair_energy)
     Ctl* ctl;
 };
 
@@ -85,15 +86,15 @@ __device__ __forceinline__ void red_pair(unsigned long long* w, int i, int j, lo
 }
 
 __device__ __forceinline__ void add_pair_sums(const SumOut& so, int i, int j, double fr, double V) {
-    long long hr, lr, hv, lv;
-    const bool ok = split_fixed(fr, so.S, hr, lr) & split_fixed(V, so.S, hv, lv);
+    long long hr, lr, hv = 0, lv = 0;
+    const bool ok = split_fixed(fr, so.S, hr, lr) & (!so.with_v || split_fixed(V, so.S, hv, lv));
     if (!ok) {
         atomicOr(&so.ctl->status, kStNonFinite);
         return;
     }
     unsigned long long* u = reinterpret_cast<unsigned long long*>(so.sq);
     red_pair(u, i, j, lr);
-    red_pair(u + so.Np, i, j, lv);
+    if (so.with_v) red_pair(u + so.Np, i, j, lv);
     if (hr | hv) {
         red_pair(u + 2 * so.Np, i, j, hr);
         red_pair(u + 3 * so.Np, i, j, hv);
@@ -302,10 +303,12 @@ __device__ __forceinline__ bool is_zero2(double2 c) {
 }
 
 // rho_i and the pair energy from the fixed-point totals the pair pass added
-// (see sum_fixed), then F(rho_i), F'(rho_i) and E_i = F(rho_i) + 1/2 sum V.
+// (see split_fixed), then F(rho_i), F'(rho_i) and E_i = F(rho_i) + 1/2 sum V
+// (with_v false: the pair pass formed no pair-energy totals, E_i = F(rho_i)
+// until a later evaluation forms them).
 template <int KIND>
 __global__ void __launch_bounds__(kFNT) k_embed_sums(int64_t N, int64_t Np, Pot P, const long long* __restrict__ sq,
-                                                     int S, const int* __restrict__ nn, int max_nb,
+                                                     int S, bool with_v, const int* __restrict__ nn, int max_nb,
                                                      const double4_32a* __restrict__ pc,
                                                      const double4_32a* __restrict__ x,
                                                      double* __restrict__ rho, double* __restrict__ Fp,
@@ -315,6 +318,7 @@ __global__ void __launch_bounds__(kFNT) k_embed_sums(int64_t N, int64_t Np, Pot 
     if (i >= N) return;
     FixedSum qr, qv;
     load_sums(sq, Np, i, qr, qv);
+    if (!with_v) qv = FixedSum{};
     double r_i, Fpi, E;
     embed_sums<KIND>(P, qr, qv, S, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0, pc, Np, i,
                      min(nn[i], max_nb), r_i, Fpi, E);
@@ -347,11 +351,16 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
         n = min(nn[i], max_nb);
     }
     const double2 zero = make_double2(0.0, 0.0);
-    // the sum is taken as sum_j s_ij x_j - x_i sum_j s_ij (Eq. 3 regrouped):
-    // per entry F'_i + F'_j, s, the sum of s and three FMAs with x_j, no
-    // separation (the virial alone forms it). Cancellation against x_i costs
-    // about L/|d| (~100 for a 360 A box) ulps of the force, ~1e-14 relative.
+    // the sum is taken as sum_j s_ij x_j - x_i sum_j s_ij (Eq. 3 regrouped),
+    // x_j in the entry's image: per entry F'_i + F'_j, s, the sum of s and
+    // three FMAs with x_j, no separation (the virial alone forms it).
+    // Cancellation against x_i costs about L/|d| (~100 for a 360 A box)
+    // ulps of the force, ~1e-14 relative. Boxes of a batch take the image
+    // as L sigma (ShiftSum), as the small-system and block-per-box kernels
+    // do, so a box gives the same bits in every schedule; a single box of
+    // more than kSmallAtoms atoms adds the shift to x_j in float64.
     double fx = 0.0, fy = 0.0, fz = 0.0, w = 0.0, ssum = 0.0;
+    ShiftSum shift;
     int k = 0;
     double2 c = n > 0 ? cache_ab(pc, i) : zero;
     while (true) {
@@ -366,14 +375,26 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
             const double2 cn = k + 1 < n ? cache_ab(pc, slot + Np) : zero;
             const int e = nl[slot];
             const int j = entry_slot(e);
+            const unsigned code = entry_code(e);
             const double s = fma(Fpi + Fp[j], c.y, c.x);
             double px, py, pz;
-            image_pos(x[j], entry_code(e), L, px, py, pz);
+            if (SINGLE) {
+                // one large box: only the atoms next to its faces meet an
+                // image, so the float64 shift in a branch costs little
+                image_pos(x[j], code, L, px, py, pz);
+            } else {
+                const double4_32a xj = x[j];
+                px = xj.x;
+                py = xj.y;
+                pz = xj.z;
+                if (code != kNoShift) shift.add(s, code);
+            }
             ssum += s;
             fx = fma(s, px, fx);
             fy = fma(s, py, fy);
             fz = fma(s, pz, fz);
             if (VIR) {
+                if (!SINGLE) image_pos(make_double4_32a(px, py, pz, 0.0), code, L, px, py, pz);
                 const double4_32a xi = x[i];
                 w = fma(s, norm2(px - xi.x, py - xi.y, pz - xi.z), w);
             }
@@ -386,6 +407,11 @@ __global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, co
     fx = fma(-xi.x, ssum, fx);
     fy = fma(-xi.y, ssum, fy);
     fz = fma(-xi.z, ssum, fz);
+    if (!SINGLE) {
+        fx = fma(L[0], shift.value(0), fx);
+        fy = fma(L[1], shift.value(1), fy);
+        fz = fma(L[2], shift.value(2), fz);
+    }
     f[i] = fx;
     f[Np + i] = fy;
     f[2 * Np + i] = fz;
@@ -535,8 +561,8 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
                                                       double* __restrict__ v, double c_kick, Bath bath,
                                                       double* __restrict__ w_atom, const Ctl* ctl) {
     if (load_status(ctl)) return;
-    __shared__ double4_32a sv[kSmallRows][32];  // (s_ij, image position of j)
-    __shared__ unsigned char sok[kSmallRows][32];
+    __shared__ double4_32a sv[kSmallRows][32];  // (s_ij, position of j)
+    __shared__ unsigned char sok[kSmallRows][32];  // 0: no term; else 1 + the entry's image code
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * 32 + lane;
     const bool active = i < N;
@@ -552,6 +578,7 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
     }
     const int kmax = warp_max(n);
     double fx = 0.0, fy = 0.0, fz = 0.0, w = 0.0, ssum = 0.0;
+    ShiftSum shift;
     double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     if (VIR && active && wq == 0) xi = x[i];
     for (int k0 = 0; k0 < kmax; k0 += kSmallRows) {
@@ -565,11 +592,9 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
                 if (!is_zero2(c)) {
                     const int e = nl[slot];
                     const int j = entry_slot(e);
-                    double4_32a q;
-                    q.x = fma(Fpi + Fp[j], c.y, c.x);
-                    image_pos(x[j], entry_code(e), L, q.y, q.z, q.w);
-                    sv[r][lane] = q;
-                    ok = 1;
+                    const double4_32a xj = x[j];
+                    sv[r][lane] = make_double4_32a(fma(Fpi + Fp[j], c.y, c.x), xj.x, xj.y, xj.z);
+                    ok = (unsigned char)(1u + entry_code(e));
                 }
             }
             sok[r][lane] = ok;
@@ -579,23 +604,30 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
             // the operations and order of k_force
             const int kend = min(n - k0, kSmallRows);
             for (int r = 0; r < kend; ++r) {
-                if (!sok[r][lane]) continue;
+                const unsigned ok = sok[r][lane];
+                if (!ok) continue;
                 const double4_32a q = sv[r][lane];
+                const unsigned code = ok - 1u;
                 const double s = q.x;
+                if (code != kNoShift) shift.add(s, code);
                 ssum += s;
                 fx = fma(s, q.y, fx);
                 fy = fma(s, q.z, fy);
                 fz = fma(s, q.w, fz);
-                if (VIR) w = fma(s, norm2(q.y - xi.x, q.z - xi.y, q.w - xi.z), w);
+                if (VIR) {
+                    double px, py, pz;
+                    image_pos(make_double4_32a(q.y, q.z, q.w, 0.0), code, L, px, py, pz);
+                    w = fma(s, norm2(px - xi.x, py - xi.y, pz - xi.z), w);
+                }
             }
         }
         __syncthreads();
     }
     if (wq != 0 || !active) return;
     xi = x[i];
-    fx = fma(-xi.x, ssum, fx);
-    fy = fma(-xi.y, ssum, fy);
-    fz = fma(-xi.z, ssum, fz);
+    fx = fma(L[0], shift.value(0), fma(-xi.x, ssum, fx));
+    fy = fma(L[1], shift.value(1), fma(-xi.y, ssum, fy));
+    fz = fma(L[2], shift.value(2), fma(-xi.z, ssum, fz));
     f[i] = fx;
     f[Np + i] = fy;
     f[2 * Np + i] = fz;
@@ -773,7 +805,7 @@ static void launch_pairs_half(Engine& e, const Geo& g, cudaStream_t s) {
     e.launches += 1;
     k_fixed_positions<SINGLE><<<(int)((e.N + kFNT - 1) / kFNT), kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.xq,
                                                                              DENS ? e.sum_q : nullptr, e.ctl);
-    const SumOut so{e.sum_q, e.N_pad, sum_split(e.max_nb), e.ctl};
+    const SumOut so{e.sum_q, e.N_pad, sum_split(e.max_nb), e.pair_energy, e.ctl};
     // 32-bit slots: 85 instead of 89 registers, 18 instead of 22.5 KB of
     // queues per block (4M-atom step 8.69 -> 8.63 ms; the same bits);
     // 6 blocks per SM forced (80 registers, spills) measured slower
@@ -837,8 +869,8 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s, bool virial) {
     }
     {
         PhaseScope scope(e, MD_PHASE_DENSITY, s);
-        k_embed_sums<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.sum_q, sum_split(e.max_nb), e.nn, e.max_nb,
-                                               e.pc, e.x, e.rho, e.Fp, e.e_atom, e.ctl);
+        k_embed_sums<KIND><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, e.pot, e.sum_q, sum_split(e.max_nb), e.pair_energy,
+                                               e.nn, e.max_nb, e.pc, e.x, e.rho, e.Fp, e.e_atom, e.ctl);
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     if (virial)
