@@ -302,11 +302,12 @@ MD_API int md_set_thermostat(md_batch* b, double T_e, double tau_T);
 /* Float64 force evaluation with Newton's third law (the paper's CPU scheme,
  * Sec. 4.3) instead of full-list sums: the density and force passes walk
  * only the upper half of each neighbour list (j > i) and add every pair's
- * rho, V and force to both atoms, to the partner by float64 atomic adds.
- * Half the cached bytes and float64 operations of the two sums; the order
- * in which the atomics land varies, so results agree with the full-list
- * passes to rounding, not bit for bit, and repeated runs may differ in the
- * last bits (the full-list default is reproducible). Per-atom virials hold
+ * rho, V and force to both atoms, to the partner by atomic adds (rho and V
+ * into the exact fixed-point totals the default path uses, the force in
+ * float64). Half the cached bytes and float64 operations of the two sums;
+ * the order in which the float64 force atomics land varies, so forces agree
+ * with the full-list passes to rounding, not bit for bit, and repeated runs
+ * may differ in the last bits (the full-list default is reproducible). Per-atom virials hold
  * each pair once (box pressures are unchanged). on = 0 restores the
  * default. Applies to single-box and tile-schedule steps; the box schedule
  * keeps its own in-shared-memory sums. Errors: MD_ERR_ARG for a NULL
@@ -424,6 +425,29 @@ MD_API int md_eval_math(md_batch* h, int fn, const double* x, int64_t n, double*
  * output array of its own. Errors: MD_ERR_ARG (precision not 0 or 1,
  * iters < 1, a NULL output), MD_ERR_NOMEM, MD_ERR_CUDA. */
 MD_API int md_fma_probe(int precision, int64_t iters, double* flops, double* ms, int* n_sm, md_stream stream);
+
+/* ---------------------------------------------------------------- deferred device status */
+
+/* Deferred device status (no counterpart in the paper). With on != 0,
+ * md_get_forces, md_batch_thermo, md_batch_set_potential and md_param_grad
+ * return once their work is enqueued on `stream` instead of waiting for it
+ * to read the device status word: a loop of such calls (a fitting loop)
+ * keeps the GPU busy without a host round trip per call. Outputs are valid
+ * once the stream reaches the call (host destinations on return, as
+ * before). A device-side condition that their kernels raise (a non-finite
+ * value, a list overflow) is reported by the next call that waits: md_sync,
+ * md_step, md_get_state, md_set_state and every call not listed here, all
+ * of which keep waiting. Argument errors are returned at once either way.
+ * on = 0 (the default) restores per-call waiting. Errors: MD_ERR_ARG for a
+ * NULL handle. */
+MD_API int md_set_deferred_status(md_batch* b, int on);
+
+/* Waits for `stream` and reports the device status word: MD_OK, or the
+ * condition a deferred call raised (MD_ERR_NONFINITE, MD_ERR_NEIGH_OVERFLOW,
+ * MD_ERR_UNSUPPORTED for a pressure-coupled box below one list radius per
+ * cell). No counterpart in the paper. Errors: MD_ERR_ARG for a NULL handle,
+ * MD_ERR_CUDA. */
+MD_API int md_sync(md_batch* b, md_stream stream);
 
 /* ---------------------------------------------------------------- allocation-free variant */
 

@@ -1160,7 +1160,7 @@ int md_get_forces(md_ctx* h, double* f, double* e_atom, double* rho, md_stream s
     if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
     int rc = emit_outputs(h, f, e_atom, rho, s);
     if (rc) return rc;
-    return finish_sync(E, s);
+    return E->deferred_status ? MD_OK : finish_sync(E, s);
 }
 
 int md_batch_compute_forces(md_batch* b, const double* x, double* f, double* e_box, md_stream st) {
@@ -1268,6 +1268,12 @@ int md_batch_thermo(md_batch* b, double* thermo_box, md_stream st) {
     if (!E->have_state) return fail(E, MD_ERR_ARG, "no state");
     launch_thermo(*E, s);
     CK(cudaGetLastError());
+    if (E->deferred_status) {
+        // the per-box records only (a host destination is complete on return)
+        OutDst o = out_dst(*E, thermo_box, 4 * (size_t)E->B);
+        CK(cudaMemcpyAsync(o.dev, E->thermo_dev, 4 * E->B * sizeof(double), cudaMemcpyDefault, s));
+        return out_finish(E, o, s);
+    }
     int rc = thermo_impl(b, nullptr, thermo_box, s);
     if (rc) return rc;
     return finish_sync(E, s);
@@ -1433,11 +1439,22 @@ int md_batch_set_potential(md_batch* b, const md_potential* pot, md_stream st) {
         launch_thermo(*E, s);
         CK(cudaGetLastError());
     }
-    int rc2 = finish_sync(E, s);
+    int rc2 = E->deferred_status ? MD_OK : finish_sync(E, s);
     // the forces (and the pair cache) are those of the stored positions and
     // the new potential
     if (rc2 == MD_OK && E->have_state) E->forces_ok = true;
     return rc2;
+}
+
+int md_set_deferred_status(md_batch* b, int on) {
+    if (!b) return MD_ERR_ARG;
+    b->e.deferred_status = on != 0;
+    return MD_OK;
+}
+
+int md_sync(md_batch* b, md_stream st) {
+    if (!b) return MD_ERR_ARG;
+    return finish_sync(&b->e, (cudaStream_t)st);
 }
 
 int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* grad, md_stream st) {
@@ -1472,7 +1489,7 @@ int md_param_grad(md_batch* b, const double* g_f, const double* g_e, double* gra
     E->forces_ok = keep;
     if (rc) return fail(E, rc, "parameter gradient failed");
     CK(cudaGetLastError());
-    return finish_sync(E, s);
+    return E->deferred_status ? MD_OK : finish_sync(E, s);
 }
 
 int md_num_params(const md_batch* b) {

@@ -277,6 +277,9 @@ struct Engine {
     // last when no step records its energy (dynamics needs rho_i, F and F'
     // only; the energies are read after the last step)
     bool pair_energy = true;
+    // md_set_deferred_status: the calls that only wait to read the device
+    // status word return without waiting
+    bool deferred_status = false;
 
     // profiling: launch counter and phase events
     long long launches = 0;

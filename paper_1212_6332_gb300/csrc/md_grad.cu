@@ -292,6 +292,12 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_cached(int64_t N, int64
 // (i, j) and (j, i) add up to one term with the summed weights: w_i + w_j =
 // (g_i - g_j) . d / r, a_F,i + a_F,j; the cached values of both slots are
 // the same. Half the separations, square roots and parameter terms.
+// The five parameter terms are linear combinations of four sums per thread,
+// T1 = sum tV, T4 = sum tR, T23 = sum (r tV + w V), T56 = sum (r tR + a_F' rho)
+// (with u = r/r0 - 1 and c0 = r/r0^2 expanded), combined once at the end:
+// d/dA = T1/A, d/dxi = 2 T4/xi, d/dp = T1 - T23/r0, d/dq = 2 T4 - 2 T56/r0,
+// d/dr0 = (p T23 + 2q T56)/r0^2; 1/r and r come from the integer pipe
+// (rsqrt_sqrt). About 30 float64 instructions per pair instead of 53.
 __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_pairs(int64_t N, int64_t Np, Geo g, Pot P,
                                                                const double4_32a* __restrict__ x,
                                                                const int* __restrict__ nn,
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_pairs(int64_t N, int64_
     __shared__ double sh[kGNT / 32];
     const double inv_r0 = 1.0 / P.r0, inv_r02 = inv_r0 * inv_r0, pp = P.p, q2 = P.q2;
     const double2 zero = make_double2(0.0, 0.0);
-    double acc[kRglParams] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double t1 = 0.0, t4 = 0.0, t23 = 0.0, t56 = 0.0;
     // warp-uniform outer loop (all lanes take part in the vote below); each
     // lane steps to its own next non-zero upper entry, as k_grad_u_cached
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
@@ -352,24 +358,28 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_pairs(int64_t N, int64_
             double dx, dy, dz;
             sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
             const double r2 = norm2(dx, dy, dz);
-            const double rinv = rsqrt_nr(r2);
-            const double r = r2 * rinv;
+            double rinv, r;
+            rsqrt_sqrt(r2, rinv, r);
             const double W = ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * rinv;
             const double AFp = W * (Fpi + Fp[j]);
             const double AF = aFi + (u[j] * Fpp[j] + ge * Fp[j]);
             const double V = fv.y, rh = fv.x, Vp = c.x * r, rhp = c.y * r;
-            const double uu = fma(r, inv_r0, -1.0), c0 = r * inv_r02;
             const double tV = W * Vp + aV2 * V, tR = AFp * rhp + AF * rh;
-            acc[0] += tV * inv_A;
-            acc[1] += tR * two_inv_xi;
-            acc[2] += -uu * tV - W * V * inv_r0;
-            acc[3] += -2.0 * uu * tR - 2.0 * AFp * rh * inv_r0;
-            acc[4] += pp * (c0 * tV + W * V * inv_r02) + q2 * (c0 * tR + AFp * rh * inv_r02);
+            t1 += tV;
+            t4 += tR;
+            t23 = fma(r, tV, fma(W, V, t23));
+            t56 = fma(r, tR, fma(AFp, rh, t56));
             ++k;
             c = cn;
             }
         }
     }
+    double acc[kRglParams];
+    acc[0] = t1 * inv_A;
+    acc[1] = t4 * two_inv_xi;
+    acc[2] = t1 - inv_r0 * t23;
+    acc[3] = 2.0 * t4 - 2.0 * inv_r0 * t56;
+    acc[4] = inv_r02 * (pp * t23 + q2 * t56);
     for (int k = 0; k < kRglParams; ++k) {
         double t = block_sum<kGNT>(acc[k], sh);
         if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * kRglParams + k] = t;

@@ -92,10 +92,12 @@ def force_matching_loss(f, e_box, f_tgt, e_tgt, counts, w_e: float = 0.1, idx=No
 
 
 def make_batch(spec: dict, configs, skin: float = 0.0, precision: str = "fp64", mass: float = 63.546,
-               types=None) -> System:
+               types=None, deferred: bool = True) -> System:
     """A batch System holding fixed configurations (inputs.Box objects);
     types (one label per atom, configurations concatenated) for a potential
-    with several species."""
+    with several species. deferred: the forward and adjoint calls of a
+    fitting loop return without waiting for the device status word
+    (System.set_deferred_status); call System.sync() to check it."""
     offs = np.zeros(len(configs) + 1, dtype=np.int64)
     offs[1:] = np.cumsum([c.n for c in configs])
     s = System(spec, boxes=np.stack([c.box for c in configs]), atom_offsets=offs, skin=skin, mass=mass,
@@ -104,4 +106,6 @@ def make_batch(spec: dict, configs, skin: float = 0.0, precision: str = "fp64", 
         s.set_types(types)
     x = torch.tensor(np.concatenate([c.x for c in configs]), device="cuda")
     s.set_state(x)
+    if deferred:
+        s.set_deferred_status(True)
     return s

@@ -28,7 +28,7 @@ SYMBOLS = ("md_create", "md_destroy", "md_set_state", "md_get_state", "md_build_
            "md_batch_step", "md_batch_set_potential", "md_set_thermostat", "md_set_newton3", "md_set_types", "md_pressure", "md_set_barostat", "md_get_box", "md_param_grad", "md_num_params", "md_status_string",
            "md_last_error", "md_profile_start", "md_profile_read",
            "md_eval_math", "md_forces_noalloc", "md_batch_thermo",
-           "md_batch_schedule", "md_fma_probe")
+           "md_batch_schedule", "md_fma_probe", "md_set_deferred_status", "md_sync")
 NOALLOC_MAX_ATOMS = 16384
 PHASES = ("kick_drift", "rebuild", "pairs", "density", "force", "other", "grad")
 
@@ -99,6 +99,8 @@ def load(path: str | pathlib.Path | None = None) -> ctypes.CDLL:
         "md_batch_set_potential": [vp, P(Potential), vp],
         "md_set_thermostat": [vp, ctypes.c_double, ctypes.c_double],
         "md_set_newton3": [vp, ctypes.c_int],
+        "md_set_deferred_status": [vp, ctypes.c_int],
+        "md_sync": [vp, vp],
         "md_set_types": [vp, vp, vp],
         "md_pressure": [vp, vp, vp],
         "md_set_barostat": [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double],
@@ -385,6 +387,18 @@ class System:
         """Electron-phonon friction of Eq. (4) towards T_e (K) with time
         constant tau_T (fs) in the following steps; tau_T <= 0 turns it off."""
         self._check(self.lib.md_set_thermostat(self._h, float(T_e), float(tau_T)))
+
+    def set_deferred_status(self, on: bool = True):
+        """md_set_deferred_status: get_forces, batch_thermo, set_potential and
+        param_grad return without waiting for the device status word; a
+        condition their kernels raise is reported by the next call that
+        waits (sync(), step(), get_state(), ...)."""
+        self._check(self.lib.md_set_deferred_status(self._h, int(bool(on))))
+
+    def sync(self):
+        """md_sync: waits for the stream and raises MDError for a pending
+        device condition."""
+        self._check(self.lib.md_sync(self._h, _stream()))
 
     def set_newton3(self, on: bool = True):
         """Float64 density and force sums over the upper half of each list

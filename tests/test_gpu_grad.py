@@ -122,3 +122,44 @@ def test_adjoint_from_the_forward_cache_equals_the_recomputed_one(kind):
     scale = np.abs(ref).max()
     assert np.abs(cached - recomputed).max() <= 1e-12 * scale
     assert np.abs(recomputed - ref).max() <= 1e-10 * scale
+
+
+def test_deferred_status_gives_the_same_fit_and_reports_at_sync():
+    """A fitting loop with deferred device status (the calls return without
+    waiting for the status word) gives the bits of the waiting loop; sync()
+    reports a clean status; argument errors still come back at once."""
+    import torch
+    from paper_1212_6332_gb300.fit import ForceField, config_index, force_matching_loss, make_batch, theta_of
+    from paper_1212_6332_gb300.md import MDError
+    cfgs = configs((3, 4, 3), seed=33)
+    ref = make_batch(I.RGL_CU, cfgs, deferred=False)
+    f_tgt = ref.get_forces()["f"].clone()
+    e_tgt = ref.batch_thermo()[:, 1].clone()
+    ref.close()
+    counts = torch.tensor([c.n for c in cfgs], device="cuda", dtype=torch.float64)
+    idx = config_index(counts)
+    out = {}
+    for deferred in (False, True):
+        s = make_batch(MODEL, cfgs, deferred=deferred)
+        theta = theta_of(MODEL).cuda().requires_grad_(True)
+        hist = []
+        for _ in range(3):
+            f, e = ForceField.apply(theta, s, MODEL)
+            L = force_matching_loss(f, e, f_tgt, e_tgt, counts, idx=idx)
+            (g,) = torch.autograd.grad(L, theta)
+            hist.append((L.item(), g.cpu().numpy(), f.detach().cpu().numpy()))
+            with torch.no_grad():
+                theta -= 1e-3 * g
+        s.sync()
+        if deferred:
+            with pytest.raises(MDError):
+                s.param_grad(torch.zeros(s.n, 3, dtype=torch.float64, device="cuda"),
+                             torch.zeros(s.n_boxes, dtype=torch.float64, device="cuda"),
+                             grad=torch.zeros(s.n_params, dtype=torch.float64))  # host tensor: rejected
+        s.close()
+        out[deferred] = hist
+    # (the loss itself goes through torch's index_add_, whose float64 atomics
+    # land in any order: compared to rounding; forces and gradients by bits)
+    for (la, ga, fa), (lb, gb, fb) in zip(out[False], out[True]):
+        assert abs(la - lb) <= 1e-14 * abs(la)
+        assert np.array_equal(ga, gb) and np.array_equal(fa, fb)
