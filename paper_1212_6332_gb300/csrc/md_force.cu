@@ -517,34 +517,35 @@ __global__ void __launch_bounds__(kFNT) k_rho_small(int64_t N, int64_t Np, Pot P
                                                     double* __restrict__ Fp, double* __restrict__ e_atom, int S,
                                                     Ctl* ctl) {
     if (load_status(ctl)) return;
-    __shared__ double2 sw[kSmallRows][32];
+    // each warp adds the fixed-point terms of its rows (every fourth row of
+    // the 32 atoms' lists, all loads in flight), the warps' partial totals
+    // then meet in shared memory: integer sums, so the bits of the pair
+    // pass's atomic adds in any split
+    __shared__ long long part[kFNT / 32][4][32];
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * 32 + lane;
     const bool active = i < N;
     const int n = active ? min(nn[i], max_nb) : 0;
-    const int kmax = warp_max(n);  // the same 32 atoms in every warp of the block
     FixedSum qr, qv;
     bool ok = true;
-    for (int k0 = 0; k0 < kmax; k0 += kSmallRows) {
-#pragma unroll
-        for (int r = wq; r < kSmallRows; r += kFNT / 32) {
-            const int k = k0 + r;
-            sw[r][lane] = k < n ? cache_fv(pc, (int64_t)k * Np + i) : make_double2(0.0, 0.0);
-        }
-        __syncthreads();
-        if (wq == 0) {
-            // the fixed-point totals of the pair pass's atomic adds (the same
-            // terms, so the same bits in any order)
-            const int kend = min(n - k0, kSmallRows);
-            for (int r = 0; r < kend; ++r) {
-                const double2 w = sw[r][lane];
-                ok &= qr.add(w.x, S) & qv.add(w.y, S);
-            }
-        }
-        __syncthreads();
+    for (int k = wq; k < n; k += kFNT / 32) {
+        const double2 w = cache_fv(pc, (int64_t)k * Np + i);
+        ok &= qr.add(w.x, S) & qv.add(w.y, S);
     }
-    if (wq != 0 || !active) return;
+    part[wq][0][lane] = qr.lo;
+    part[wq][1][lane] = qr.hi;
+    part[wq][2][lane] = qv.lo;
+    part[wq][3][lane] = qv.hi;
     if (!ok) atomicOr(&ctl->status, kStNonFinite);
+    __syncthreads();
+    if (wq != 0 || !active) return;
+#pragma unroll
+    for (int w = 1; w < kFNT / 32; ++w) {
+        qr.lo += part[w][0][lane];
+        qr.hi += part[w][1][lane];
+        qv.lo += part[w][2][lane];
+        qv.hi += part[w][3][lane];
+    }
     double r_i, Fpi, E;
     embed_sums<KIND>(P, qr, qv, S, KIND == MD_POT_SPLINE && P.n_types > 1 ? pos_type(x[i]) : 0, pc, Np, i, n, r_i,
                      Fpi, E);
@@ -593,8 +594,13 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
                     const int e = nl[slot];
                     const int j = entry_slot(e);
                     const double4_32a xj = x[j];
-                    sv[r][lane] = make_double4_32a(fma(Fpi + Fp[j], c.y, c.x), xj.x, xj.y, xj.z);
-                    ok = (unsigned char)(1u + entry_code(e));
+                    const double sij = fma(Fpi + Fp[j], c.y, c.x);
+                    const unsigned code = entry_code(e);
+                    sv[r][lane] = make_double4_32a(sij, xj.x, xj.y, xj.z);
+                    ok = (unsigned char)(1u + code);
+                    // the image sums are integer: each warp takes its rows'
+                    // terms, the partial sums meet after the loop
+                    if (code != kNoShift) shift.add(sij, code);
                 }
             }
             sok[r][lane] = ok;
@@ -609,7 +615,6 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
                 const double4_32a q = sv[r][lane];
                 const unsigned code = ok - 1u;
                 const double s = q.x;
-                if (code != kNoShift) shift.add(s, code);
                 ssum += s;
                 fx = fma(s, q.y, fx);
                 fy = fma(s, q.z, fy);
@@ -623,7 +628,17 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
         }
         __syncthreads();
     }
+    __shared__ __int128 spart[kFNT / 32 - 1][3][32];
+    if (wq != 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) spart[wq - 1][a][lane] = shift.a[a];
+    }
+    __syncthreads();
     if (wq != 0 || !active) return;
+#pragma unroll
+    for (int w2 = 0; w2 < kFNT / 32 - 1; ++w2)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) shift.a[a] += spart[w2][a][lane];
     xi = x[i];
     fx = fma(L[0], shift.value(0), fma(-xi.x, ssum, fx));
     fy = fma(L[1], shift.value(1), fma(-xi.y, ssum, fy));
