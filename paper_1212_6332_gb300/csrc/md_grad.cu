@@ -522,7 +522,13 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline(int64_t N, int64_t Np,
                                                           const double* __restrict__ Fpp,
                                                           const double* __restrict__ u, int ncoef,
                                                           double* __restrict__ partial) {
-    extern __shared__ double sg[];  // [ncoef] coefficient gradients: V pieces, rho pieces, F pieces
+    // [ncoef] coefficient gradients of this block (V pieces, rho pieces, F
+    // pieces): its own slice of partial, added to by native float64 atomics
+    // in L2. (A shared-memory histogram made the float64 atomics retry under
+    // the contention of a shell's pairs meeting the same spline pieces,
+    // each retry a float64 add: the spline loss + gradient ran at 231 per
+    // second.)
+    double* sg = partial + (int64_t)blockIdx.x * ncoef;
     for (int k = threadIdx.x; k < ncoef; k += NT) sg[k] = 0.0;
     __syncthreads();
     // per table 4 (n - 1) coefficients: V pair tables, rho pair tables, F tables
@@ -554,8 +560,6 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline(int64_t N, int64_t Np,
         // embedding: u_i dF'/dtheta + gE dF/dtheta at rho_i
         spline_adj(P, 2, rho[i], ge, u[i], gF + atom_tab<MD_POT_SPLINE>(P, x, i) * cF);
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < ncoef; k += NT) partial[(int64_t)blockIdx.x * ncoef + k] = sg[k];
 }
 
 // Transpose of the knot-value -> coefficient map of one natural spline
@@ -760,7 +764,7 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline_mixed(int64_t N, int64
                                                                 const double* __restrict__ Fpp,
                                                                 const double* __restrict__ u, int ncoef,
                                                                 double* __restrict__ partial) {
-    extern __shared__ double sg[];  // [ncoef] as in k_grad_param_spline
+    double* sg = partial + (int64_t)blockIdx.x * ncoef;  // as in k_grad_param_spline
     for (int k = threadIdx.x; k < ncoef; k += NT) sg[k] = 0.0;
     __syncthreads();
     const int np_ = P.n_types * (P.n_types + 1) / 2;
@@ -794,8 +798,6 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline_mixed(int64_t N, int64
         }
         spline_adj(P, 2, rho[i], ge, u[i], gF + off_type(oi) * cF);
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < ncoef; k += NT) partial[(int64_t)blockIdx.x * ncoef + k] = sg[k];
 }
 
 // The same histogram with every pair visited once, from the atom of the
@@ -818,7 +820,7 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline_pairs(int64_t N, int64
                                                                 const double* __restrict__ Fpp,
                                                                 const double* __restrict__ u, int ncoef,
                                                                 double* __restrict__ partial) {
-    extern __shared__ double sg[];  // [ncoef], as in k_grad_param_spline
+    double* sg = partial + (int64_t)blockIdx.x * ncoef;  // as in k_grad_param_spline
     for (int k = threadIdx.x; k < ncoef; k += NT) sg[k] = 0.0;
     __syncthreads();
     const int np_ = P.n_types * (P.n_types + 1) / 2;
@@ -852,8 +854,6 @@ __global__ void __launch_bounds__(NT) k_grad_param_spline_pairs(int64_t N, int64
         // embedding: u_i dF'/dtheta + gE dF/dtheta at rho_i
         spline_adj(P, 2, rho[i], ge, u[i], gF + atom_tab<MD_POT_SPLINE>(P, x, i) * cF);
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < ncoef; k += NT) partial[(int64_t)blockIdx.x * ncoef + k] = sg[k];
 }
 
 // Spline coefficient count over all tables: P pair tables each for V and rho,
@@ -898,11 +898,7 @@ static int grad_mixed_impl(Engine& e, const double* g_f, const double* g_e, doub
         e.launches += 2;
     } else {
         int ncoef = spline_ncoef(e);
-        size_t smem = (size_t)ncoef * sizeof(double);
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_grad_param_spline_mixed<kGNT, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        k_grad_param_spline_mixed<kGNT, WIDE><<<e.grad_blocks, kGNT, smem, s>>>(
+        k_grad_param_spline_mixed<kGNT, WIDE><<<e.grad_blocks, kGNT, 0, s>>>(
             e.N, e.N_pad, g, e.pot, e.xo, e.nn, e.nl, e.max_nb, e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp, e.grad_u,
             ncoef, e.grad_partial);
         k_sum_partials<<<ncoef, 256, 0, s>>>(e.grad_blocks, ncoef, e.grad_partial, e.grad_coef);
@@ -947,13 +943,12 @@ static int grad_impl(Engine& e, const double* g_f, const double* g_e, double* gr
         e.launches += 2;
     } else {
         int ncoef = spline_ncoef(e);
-        size_t smem = (size_t)ncoef * sizeof(double);
         if (e.n_up)
-            k_grad_param_spline_pairs<kGNT><<<npb, kGNT, smem, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.n_up,
+            k_grad_param_spline_pairs<kGNT><<<npb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.n_up,
                                                                     e.max_nb, e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp,
                                                                     e.grad_u, ncoef, e.grad_partial);
         else
-            k_grad_param_spline<kGNT><<<npb, kGNT, smem, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb,
+            k_grad_param_spline<kGNT><<<npb, kGNT, 0, s>>>(e.N, e.N_pad, g, e.pot, e.x, e.nn, e.nl, e.max_nb,
                                                               e.grad_g, g_e, e.rho, e.Fp, e.grad_Fpp, e.grad_u, ncoef,
                                                               e.grad_partial);
         k_sum_partials<<<ncoef, 256, 0, s>>>(npb, ncoef, e.grad_partial, e.grad_coef);
