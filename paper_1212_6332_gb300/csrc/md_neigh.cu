@@ -252,6 +252,10 @@ __global__ void __launch_bounds__(kRotNT) k_rotate_tiles(int64_t N, int64_t Np, 
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t i = tile * 32 + lane;
         const bool due = i < N && box_due(disp, g.B == 1 ? 0 : g.atom_box[i], mode, thr);
+        // a tile none of whose atoms rebuilds is skipped by the whole block
+        // (every warp holds the same 32 atoms, so the vote agrees): between
+        // list builds of a batch most tiles are such tiles
+        if (!__any_sync(0xffffffffu, due)) continue;
         const int n = due ? min(nn[i], max_nb) : 0;
         const int kmax = warp_max(n);
         for (int k = wq; k < kmax; k += kRotNT / 32) s_tile[k * 32 + lane] = k < n ? raw[(int64_t)k * Np + i] : 0;
