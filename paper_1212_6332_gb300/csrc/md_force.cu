@@ -172,7 +172,9 @@ __device__ __forceinline__ PairRow load_pair_row(int e, bool valid, int64_t i, c
 #ifdef MD_PAIR_MIN_BLOCKS
 #define MD_PAIR_BOUNDS __launch_bounds__(kFNT, MD_PAIR_MIN_BLOCKS)
 #else
-#define MD_PAIR_BOUNDS __launch_bounds__(kFNT)
+// boxes of a batch (per-atom box geometry: 110 registers, 4 blocks per SM
+// unbounded) are held to 5 resident blocks
+#define MD_PAIR_BOUNDS __launch_bounds__(kFNT, SINGLE ? 1 : 5)
 #endif
 template <int KIND, bool SINGLE, bool MIRROR, bool DENS, typename ST>
 __global__ void MD_PAIR_BOUNDS k_pairs_half(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P, float rc2f,
