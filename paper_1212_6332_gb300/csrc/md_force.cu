@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kFNT) k_embed_sums(int64_t N, int64_t Np, Pot 
 // VIR: also the per-atom virial w_i = -1/2 sum_j s_ij r_ij^2 (the pair
 // virial of Eq. (6) split evenly between the two atoms of each pair).
 template <bool SINGLE, bool VIR>
-__global__ void __launch_bounds__(kFNT) k_force(int64_t N, int64_t Np, Geo g, const double4_32a* __restrict__ x,
+__global__ void __launch_bounds__(kFNT, SINGLE ? 1 : 10) k_force(int64_t N, int64_t Np, Geo g, const double4_32a* __restrict__ x,
                                                 const int* __restrict__ nn, const int* __restrict__ nl, int max_nb,
                                                 const double4_32a* __restrict__ pc, const double* __restrict__ Fp,
                                                 double* __restrict__ f, double* __restrict__ v, double c_kick,
