@@ -172,9 +172,11 @@ __device__ __forceinline__ PairRow load_pair_row(int e, bool valid, int64_t i, c
 #ifdef MD_PAIR_MIN_BLOCKS
 #define MD_PAIR_BOUNDS __launch_bounds__(kFNT, MD_PAIR_MIN_BLOCKS)
 #else
-// boxes of a batch (per-atom box geometry: 110 registers, 4 blocks per SM
-// unbounded) are held to 5 resident blocks
-#define MD_PAIR_BOUNDS __launch_bounds__(kFNT, SINGLE ? 1 : 5)
+// 5 resident blocks: the single-box pass fits them unbounded (92
+// registers); boxes of a batch (per-atom box geometry) would take 110
+// registers and 4 blocks. (An explicit minimum of one block lets the
+// compiler take 172 registers: 0.99 -> 1.64 ms per 1M atoms.)
+#define MD_PAIR_BOUNDS __launch_bounds__(kFNT, 5)
 #endif
 template <int KIND, bool SINGLE, bool MIRROR, bool DENS, typename ST>
 __global__ void MD_PAIR_BOUNDS k_pairs_half(int64_t N, int64_t Np, Geo g, CellSep cs0, Pot P, float rc2f,
@@ -331,8 +333,11 @@ __global__ void __launch_bounds__(kFNT) k_embed_sums(int64_t N, int64_t Np, Pot 
 
 // VIR: also the per-atom virial w_i = -1/2 sum_j s_ij r_ij^2 (the pair
 // virial of Eq. (6) split evenly between the two atoms of each pair).
+// Resident blocks: 12 for the single box (40 registers, as unbounded), 10
+// for batches (48 registers for the 128-bit image sums, 56 unbounded:
+// 4096-box force phase 3.85 -> 3.69 ms) and the virial variants.
 template <bool SINGLE, bool VIR>
-__global__ void __launch_bounds__(kFNT, SINGLE ? 1 : 10) k_force(int64_t N, int64_t Np, Geo g, const double4_32a* __restrict__ x,
+__global__ void __launch_bounds__(kFNT, VIR ? 10 : (SINGLE ? 12 : 10)) k_force(int64_t N, int64_t Np, Geo g, const double4_32a* __restrict__ x,
                                                 const int* __restrict__ nn, const int* __restrict__ nl, int max_nb,
                                                 const double4_32a* __restrict__ pc, const double* __restrict__ Fp,
                                                 double* __restrict__ f, double* __restrict__ v, double c_kick,
