@@ -116,9 +116,10 @@ FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 STEP_BYTES = lambda K: 2 * 4.0 * K + 2 * 24.0  # noqa: E731
 # DRAM bytes (read + write) per atom of one k_pairs_half launch, from an ncu
 # capture of 1,048,576 atoms of the same lattice, potential and temperature
-# (0.484 GB read + 1.813 GB written; profiles/k_pairs_half_rgl_cu_1m_fp64.md);
-# traffic grows in proportion to the atom count.
-PAIRS_DRAM_BYTES_PER_ATOM = (0.484499e9 + 1.813424e9) / 1048576
+# (0.464 GB read + 1.792 GB written, a step that forms no pair-energy
+# totals; profiles/k_pairs_half_rgl_cu_1m_fp64.md); traffic grows in
+# proportion to the atom count.
+PAIRS_DRAM_BYTES_PER_ATOM = (0.463907e9 + 1.791848e9) / 1048576
 # What the same capture counts per evaluated pair (22.03M pairs): executed
 # float64 instructions (DFMA + DMUL + DADD) and their flops (an FMA as 2),
 # and the share of issue slots in use. The pass takes r^2, 1/r, r, the
@@ -127,7 +128,7 @@ PAIRS_DRAM_BYTES_PER_ATOM = (0.484499e9 + 1.813424e9) / 1048576
 # counts (59 per RGL pair).
 PAIRS_FP64_INST_PER_PAIR = 13.51
 PAIRS_FP64_FLOPS_PER_PAIR = 20.75
-PAIRS_ISSUE_ACTIVE = 0.671
+PAIRS_ISSUE_ACTIVE = 0.676
 
 REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
            0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
