@@ -193,6 +193,7 @@ void fill_pot(Engine& e) {
         P.a = p.p[2];
         P.n = p.p[3];
         P.m = p.p[4];
+        P.sc96 = P.n == 9.0 && P.m == 6.0;
         P.F_scale = p.p[1] * p.p[0];
     }
     P.ek = e.exp_const;

@@ -764,7 +764,18 @@ __device__ __forceinline__ void pair_eval(const Pot& P, const double* __restrict
         }
     } else if (KIND == MD_POT_SC) {
         double ar = P.a * rinv;
-        double an = P.eps * powr(ar, P.n), am = powr(ar, P.m);
+        double an, am;
+        if (P.sc96) {
+            // the Sutton-Chen Cu exponents: a^2, a^3, a^6 = (a^3)^2, a^9 =
+            // a^6 a^3, four float64 multiplies where the two general
+            // integer-power loops take eleven
+            const double a2 = ar * ar, a3 = a2 * ar, a6 = a3 * a3;
+            am = a6;
+            an = P.eps * (a6 * a3);
+        } else {
+            an = P.eps * powr(ar, P.n);
+            am = powr(ar, P.m);
+        }
         if (tap) {
             double S, dS;
             taper(P, r, S, dS);

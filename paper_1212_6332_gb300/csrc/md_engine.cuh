@@ -41,6 +41,7 @@ struct Pot {
     double xi, r0;  // RGL xi and r0 (parameter derivatives)
     // SC: V = eps (a/r)^n S, rho = (a/r)^m S; F = -F_scale sqrt(rho)
     double eps, a, n, m;
+    int sc96;        // SC exponents n = 9, m = 6: (a/r)^9 and (a/r)^6 from one chain of products
     double F_scale;
     // spline: per-interval cubic coefficients (c0 + c1 u + c2 u^2 + c3 u^3,
     // u = t - t_k) for V, rho, F; n knots -> n - 1 intervals
