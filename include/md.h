@@ -223,7 +223,11 @@ MD_API int md_get_forces(md_ctx* ctx, double* f, double* e_atom, double* rho, md
  * per step). thermo_hist (optional, host or device) receives n_steps rows
  * of (ke, pe, etot, temperature); out (optional, host) the final state's
  * md_thermo. use_graph != 0 replays the steps from a captured CUDA graph
- * (faster for small systems; same results). */
+ * (faster for small systems; same results). Without thermo_hist the
+ * float64 path forms the pair energies (sum_j V_ij of Eq. 1) on the last
+ * step only: dynamics needs rho_i, F and F' alone, so trajectories are
+ * unchanged, and every energy this library reports after the call (out,
+ * md_get_thermo, md_get_forces) is that of the final positions. */
 MD_API int md_step(md_ctx* ctx, int n_steps, md_thermo* out, double* thermo_hist, int use_graph, md_stream stream);
 
 /* The current md_thermo (host): kinetic energy, E_T of Eq. (2) and the
