@@ -65,9 +65,10 @@ ORACLE_CELLS = 50        # CPU sample: 500,000 atoms of the same lattice
 #   both slots 32K, x 32, the fixed-point density totals (4 words) 32
 # float64 density finish (k_embed_sums): F, F' and E_i from the fixed-point
 #   totals, 6 per atom; totals 32, count 4, rho/F'/E_i writes 24
-# float64 force pass (k_force): s = A + (F'_i + F'_j) B 3 and F_i += s x_j
-#   6, +1 for the total -> 10 per entry inside r_cut; list 4K, (A, B) 16K,
-#   count 4, x_i 32, F'_i 8, F 24, v 48
+# float64 force pass (k_force): separation 3, s = A + (F'_i + F'_j) B 3 and
+#   F_i += s d 6 -> 12 per entry inside r_cut (the kernel executes s in
+#   float64 and the rest as float32 pieces); list 4K, (A, B) 16K, count 4,
+#   fixed-point x_i 32, F'_i 8, F 24, v 48
 # float32 density pass (k_density_mixed): separation 9, r^2 5, compare 1 per
 #   entry; rsqrt 4, r 1, exp argument 2, exp 5, f = xi^2 e S 2, sum 2 per
 #   pair inside r_cut (SC: (a/r)^6 6 instead of the exponential); list 4K,
@@ -94,7 +95,7 @@ def kernel_model(phase: str, precision: str, kind: str, K: float, Ki: float):
         if phase == "density":
             return "k_embed_sums (fixed-point density totals, F, F')", 6.0, 60.0, "fp64"
         if phase == "force":
-            return "k_force (float64 force pass)", 10.0 * Ki, 20.0 * K + 116.0, "fp64"
+            return "k_force (float64 force pass)", 12.0 * Ki, 20.0 * K + 116.0, "fp64"
         if phase == "grad":
             return "adjoint kernels (float64, cached pair values)", 42.0 * Ki, 72.0 * K + 64.0, "fp64"
     else:

@@ -70,7 +70,11 @@ enum md_status {
 };
 
 enum md_precision {
-    MD_FP64 = 0,  /* all arithmetic in float64 */
+    MD_FP64 = 0,  /* float64 accuracy: float64 state, pair functions and
+                     F'; r^2 and separations exact in fixed point, the
+                     density totals exact integer sums, the force sums of
+                     Eq. (3) in float32 pieces with float-float totals
+                     (about 2^-46 of a term) */
     MD_MIXED = 1  /* float32 pair math relative to cell-local origins;
                      compensated sums; float64 positions, velocities and
                      integration */

@@ -50,6 +50,7 @@ struct BoxArgs {
     int* rev;
     int* nl_lo;  // row-major lower parts for the reverse-index search
     int sum_S;  // word split of the fixed-point density sums (sum_split)
+    int cut_bits;  // 2^cut_bits > r_cut, for the force sums' separation split (DSplit)
     Ctl* ctl;
     int* box_done;
     int* box_state;
@@ -327,10 +328,12 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
             const double4_32a xi = sx[t];
             const double Fpi = sFp[t];
             const int n = min(A.nn[i], A.max_nb);
-            // the tile schedule's regrouped sum, sum_j s_ij x_j - x_i sum_j s_ij,
-            // in the same order: the same bits
-            double fx = 0.0, fy = 0.0, fz = 0.0, ssum = 0.0;
-            ShiftSum shift;
+            // the tile schedule's sum of s_ij (x_j - x_i), the separation in
+            // its fixed point, in float32 pieces in the same order: the same bits
+            const DSplit D = dsplit_init(kq, A.cut_bits);
+            const long long qi[3] = {to_fixed(xi.x, kq) - D.rnd, to_fixed(xi.y, kq) - D.rnd,
+                                     to_fixed(xi.z, kq) - D.rnd};
+            ForceSumF fs;
             for (int k = 0; k < n; ++k) {
                 const int64_t slot = (int64_t)k * A.Np + i;
                 double2 c = A.ab[2 * slot];
@@ -339,16 +342,17 @@ __global__ void k_box_steps(Geo g, Pot P, BoxArgs A, int n_steps) {
                 const int jl = entry_slot(e) - (int)a0;
                 const unsigned code = entry_code(e);
                 const double4_32a xj = sx[jl];
-                double s = fma(Fpi + sFp[jl], c.y, c.x);
-                if (code != kNoShift) shift.add(s, code);
-                ssum += s;
-                fx = fma(s, xj.x, fx);
-                fy = fma(s, xj.y, fy);
-                fz = fma(s, xj.z, fz);
+                const double s = fma(Fpi + sFp[jl], c.y, c.x);
+                long long rx = to_fixed(xj.x, kq) - qi[0], ry = to_fixed(xj.y, kq) - qi[1],
+                          rz = to_fixed(xj.z, kq) - qi[2];
+                if (code != kNoShift) {
+                    rx += qshift(code, 0, qL[0]);
+                    ry += qshift(code, 1, qL[1]);
+                    rz += qshift(code, 2, qL[2]);
+                }
+                fs.add(s, rx, ry, rz, D);
             }
-            fx = fma(L[0], shift.value(0), fma(-xi.x, ssum, fx));
-            fy = fma(L[1], shift.value(1), fma(-xi.y, ssum, fy));
-            fz = fma(L[2], shift.value(2), fma(-xi.z, ssum, fz));
+            const double fx = fs.value(0), fy = fs.value(1), fz = fs.value(2);
             A.f[i] = fx;
             A.f[A.Np + i] = fy;
             A.f[2 * A.Np + i] = fz;
@@ -463,6 +467,7 @@ static void box_launch(Engine& e, int n_steps, cudaStream_t s) {
     A.rev = e.rev;
     A.nl_lo = e.nl_lo;
     A.sum_S = sum_split(e.max_nb);
+    A.cut_bits = cut_bits(e.pot.rc);
     A.ctl = e.ctl;
     A.box_done = e.box_done;
     A.box_state = e.box_state;

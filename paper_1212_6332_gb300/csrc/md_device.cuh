@@ -2,6 +2,8 @@
 // embedding functions of Eq. (1) in float64 and float32.
 #pragma once
 
+#include <cmath>
+
 #include "md_engine.cuh"
 #include "md_math.cuh"
 
@@ -92,19 +94,6 @@ __device__ __forceinline__ void sep_entry(const double4_32a& xi, const double4_3
         dx += image_shift(code & 3u, L[0]);
         dy += image_shift((code >> 2) & 3u, L[1]);
         dz += image_shift((code >> 4) & 3u, L[2]);
-    }
-}
-
-// The partner's position in the image of a list entry: x_j plus the shift.
-__device__ __forceinline__ void image_pos(const double4_32a& xj, unsigned code, const double* L, double& px,
-                                          double& py, double& pz) {
-    px = xj.x;
-    py = xj.y;
-    pz = xj.z;
-    if (code != kNoShift) {
-        px += image_shift(code & 3u, L[0]);
-        py += image_shift((code >> 2) & 3u, L[1]);
-        pz += image_shift((code >> 4) & 3u, L[2]);
     }
 }
 
@@ -391,45 +380,136 @@ __device__ __forceinline__ void list_sums_f64(const double4_32a* __restrict__ pc
     }
 }
 
-// The periodic image of a list entry in the force sums. Eq. (3) regrouped,
-// F_i = sum_j s_ij (x_j + c_j L) - x_i sum_j s_ij with c_j in {-1, 0, 1}^3 the
-// entry's image, is taken as sum_j s_ij x_j - x_i sum_j s_ij + L sigma with
-// sigma = sum_j c_j s_ij per axis accumulated exactly in 128-bit fixed point
-// (s 2^60 rounded once, half away from zero) on the integer pipe, and L sigma
-// rounded once per atom. In small periodic boxes a quarter of the entries
-// carry an image; the three float64 adds that formed x_j + c L ran in a
-// branch nearly every warp step took, where the integer adds cost a few
-// integer instructions on the lanes that need them.
-struct ShiftSum {
-    __int128 a[3] = {0, 0, 0};
-    __device__ __forceinline__ void add(double s, unsigned code) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(s);
-        const int e = (int)((b >> 52) & 0x7ffu);
-        const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
-        const int sh = e - 1075 + 60;  // |s| 2^60 = m 2^sh
-        __int128 q = 0;
-        if (e != 0) {
-            if (sh >= 0)
-                q = (__int128)m << (sh < 64 ? sh : 64);  // (|s| >= 2^17: beyond any force term)
-            else if (sh > -54)
-                q = (__int128)((m + (1ull << (-sh - 1))) >> -sh);
-        }
-        if (b >> 63) q = -q;
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            const unsigned c = (code >> (2 * ax)) & 3u;
-            if (c == 0u) a[ax] -= q;
-            if (c == 2u) a[ax] += q;
-        }
-    }
-    // sigma of axis ax rounded once to the nearest double
-    __device__ __forceinline__ double value(int ax) const {
-        const __int128 t = a[ax];
-        const unsigned __int128 u = t < 0 ? (unsigned __int128)(-t) : (unsigned __int128)t;
-        const double v = round_u128((unsigned long long)(u >> 64), (unsigned long long)u, 60);
-        return t < 0 ? -v : v;
-    }
+// ---------------------------------------------------------------- force sums in float32 pieces
+//
+// The force of Eq. (3) as f_i = sum_j s_ij d_ij over the list, d_ij = x_j -
+// x_i from the fixed-point positions (exact, the entry's image shift added
+// as an integer), with float32 arithmetic only: float64 issues at about 1/64
+// of the float32 rate on this part, so four float64 instructions per entry
+// cost more than the ~100 float32 and integer ones below.
+//   d: the fixed-point difference (pre-shifted by sh bits with rounding
+//     where the box's scale would put more than 54 bits below r_cut) cut
+//     into three exact float32 values formed from the bits (an integer add
+//     or or with an exponent-scaled 1.5 2^23 or 2^23, then one exact
+//     subtraction): a = its high word (signed, below 2^22), b = the next
+//     23 bits, c = the last 9; then d_h = RN(a + b) with its exact
+//     remainder (Dekker's Fast2Sum), d_l = RN(remainder + c): d_h + d_l is
+//     d to about 2^-48 of |d|, whatever |d|;
+//   s: s_h = s truncated to 24 significant bits, s_l = the remaining 29
+//     bits rounded to 23 (both from the float64 bit pattern), relative
+//     error 2^-48;
+//   s d = p + e with p = s_h d_h rounded, e = its exact error (one FMA) +
+//     s_l d_h + s_h d_l (s_l d_l, 2^-47 of the term, is left out);
+//   the total is a float-float pair (A, c): A + p by Knuth's TwoSum (the
+//     rounding error of the addition exactly), that error and e added to c,
+//     then (A, c) renormalised by Fast2Sum so that |c| <= ulp(A)/2.
+// The error of a term is at most about 2^-46 of |s| |d| (the rounding of
+// its small parts e, up to 2^-22 of p); the total adds about 2^-48 of
+// itself per term. The result A + c is exact in float64. Every operation is one IEEE rounding in a fixed
+// order (no contraction) and every rounding is to nearest, so the bits
+// depend on the list order alone and the errors carry no bias.
+struct DSplit {
+    long long rnd;  // 2^(sh - 1) if sh > 0, else 0: the pre-shift rounds to nearest
+    int sh;
+    int mh, mm, ml;  // bit patterns of 1.5 2^23 2^(32 + sh - kq), 2^23 2^(9 + sh - kq), 2^23 2^(sh - kq)
+    float ch, cm, cl;  // the same as float32 values
 };
+
+// cb: 2^cb > r_cut (entries with nonzero cached terms lie within r_cut)
+__device__ __forceinline__ DSplit dsplit_init(int kq, int cb) {
+    DSplit D;
+    D.sh = max(0, kq + cb - 54);
+    D.rnd = D.sh > 0 ? 1ll << (D.sh - 1) : 0ll;
+    D.mh = 0x4b400000 + (32 + D.sh - kq) * (1 << 23);
+    D.mm = 0x4b000000 + (9 + D.sh - kq) * (1 << 23);
+    D.ml = 0x4b000000 + (D.sh - kq) * (1 << 23);
+    D.ch = __int_as_float(D.mh);
+    D.cm = __int_as_float(D.mm);
+    D.cl = __int_as_float(D.ml);
+    return D;
+}
+
+// d + rnd (d in units of 2^-kq, the rounding constant already added) ->
+// d_h + d_l
+__device__ __forceinline__ void dsplit(long long dr, const DSplit& D, float& dh, float& dl) {
+    const int hi = (int)(dr >> 32);
+    const unsigned lo = (unsigned)dr;
+    const int k = hi >> D.sh;                                                      // bits 32 + sh and up
+    const unsigned t = __funnelshift_r(lo, (unsigned)hi, 9 + D.sh) & 0x7fffffu;  // bits 9 + sh .. 31 + sh
+    const unsigned u = (lo >> D.sh) & 0x1ffu;                                     // bits sh .. 8 + sh
+    const float a = __fsub_rn(__int_as_float(D.mh + k), D.ch);
+    const float b = __fsub_rn(__uint_as_float((unsigned)D.mm | t), D.cm);  // 0 <= b < one unit of a
+    const float c = __fsub_rn(__uint_as_float((unsigned)D.ml | u), D.cl);  // 0 <= c < one unit of b
+    dh = __fadd_rn(a, b);
+    const float r = __fsub_rn(b, __fsub_rn(dh, a));  // a + b = dh + r exactly (a = 0 or |a| > b)
+    dl = __fadd_rn(r, c);
+}
+
+// s -> s_h + s_l from the float64 bits (2^-100 <= |s| < 2^128; zero, other
+// magnitudes and non-finite values go through the conversion, s_l = 0)
+__device__ __forceinline__ void ssplit(double s, float& sh, float& sl) {
+    const unsigned hi = (unsigned)__double2hiint(s), lo = (unsigned)__double2loint(s);
+    const unsigned ab = hi & 0x7fffffffu;
+    if (ab - (923u << 20) < ((1151u - 923u) << 20)) {
+        const unsigned sg = hi & 0x80000000u;
+        const unsigned fb = __funnelshift_l(lo, ab - (896u << 20), 3);  // |s| truncated to 24 bits
+        sh = __uint_as_float(fb | sg);
+        const unsigned F = ((fb & 0x7f800000u) - (23u << 23)) | sg;   // 2^23 at the residual's scale
+        // the residual's 29 bits rounded to 23 (a carry to 2^23 steps the
+        // exponent of the added pattern: still the exact value)
+        sl = __fsub_rn(__uint_as_float(F + (((lo & 0x1fffffffu) + 32u) >> 6)), __uint_as_float(F));
+    } else {
+        sh = __double2float_rn(s);
+        sl = 0.f;
+    }
+}
+
+struct ForceSumF {
+    float A[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+    // one component: A + c += s d with s = sh + sl, d = dh + dl
+    __device__ __forceinline__ void add(int ax, float sh, float sl, float dh, float dl) {
+        const float p = __fmul_rn(sh, dh);
+        float e = __fmaf_rn(sh, dh, -p);  // the product's rounding error, exactly
+        e = __fmaf_rn(sl, dh, e);
+        e = __fmaf_rn(sh, dl, e);
+        const float S = __fadd_rn(A[ax], p);  // TwoSum: S + err = A + p exactly
+        const float bp = __fsub_rn(S, A[ax]);
+        const float err = __fadd_rn(__fsub_rn(A[ax], __fsub_rn(S, bp)), __fsub_rn(p, bp));
+        const float t = __fadd_rn(c[ax], __fadd_rn(err, e));
+        // renormalised (Dekker's Fast2Sum), |c| <= ulp(A) / 2: the low part
+        // stays small, so its roundings stay ~2^-48 of the running total
+        A[ax] = __fadd_rn(S, t);
+        c[ax] = __fsub_rn(t, __fsub_rn(A[ax], S));
+    }
+    // one entry from its pieces (sh, sl; dh, dl per axis)
+    __device__ __forceinline__ void add(float sh, float sl, const float (&dh)[3], const float (&dl)[3]) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) add(ax, sh, sl, dh[ax], dl[ax]);
+    }
+    // one entry: s and the rounded difference (x, y, z)
+    __device__ __forceinline__ void add(double s, long long rx, long long ry, long long rz, const DSplit& D) {
+        float sh, sl, dh[3], dl[3];
+        ssplit(s, sh, sl);
+        dsplit(rx, D, dh[0], dl[0]);
+        dsplit(ry, D, dh[1], dl[1]);
+        dsplit(rz, D, dh[2], dl[2]);
+        add(sh, sl, dh, dl);
+    }
+    __device__ __forceinline__ double value(int ax) const { return (double)A[ax] + (double)c[ax]; }
+};
+
+// the fixed-point image shift of a list entry along one axis
+__device__ __forceinline__ long long qshift(unsigned code, int ax, long long qL) {
+    const unsigned c = (code >> (2 * ax)) & 3u;
+    return c == 0u ? -qL : (c == 2u ? qL : 0ll);
+}
+
+// 2^cb > rc, for dsplit_init (host side)
+inline int cut_bits(double rc) {
+    int ex = 0;
+    std::frexp(rc, &ex);  // rc = f 2^ex, f in [1/2, 1)
+    return ex;
+}
 
 // The per-atom totals live in kSumWords = 4 words per atom, word w of atom
 // i at sq[w N_pad + i]: rho low, V low, rho high, V high.

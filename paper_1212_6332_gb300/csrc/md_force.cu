@@ -332,42 +332,46 @@ __global__ void __launch_bounds__(kFNT) k_embed_sums(int64_t N, int64_t Np, Pot 
 }
 
 // VIR: also the per-atom virial w_i = -1/2 sum_j s_ij r_ij^2 (the pair
-// virial of Eq. (6) split evenly between the two atoms of each pair).
-// Resident blocks: 12 for the single box (40 registers, as unbounded), 10
-// for batches (48 registers for the 128-bit image sums, 56 unbounded:
-// 4096-box force phase 3.85 -> 3.69 ms) and the virial variants.
+// virial of Eq. (6) split evenly between the two atoms of each pair), r_ij^2
+// exact from the fixed-point difference as in the pair pass.
+// Resident blocks: 12 for the single box, 10 for batches and the virial
+// variants.
 template <bool SINGLE, bool VIR>
-__global__ void __launch_bounds__(kFNT, VIR ? 10 : (SINGLE ? 12 : 10)) k_force(int64_t N, int64_t Np, Geo g, const double4_32a* __restrict__ x,
+__global__ void __launch_bounds__(kFNT, VIR ? 10 : (SINGLE ? 12 : 10)) k_force(int64_t N, int64_t Np, Geo g, const longlong4_32a* __restrict__ xq,
                                                 const int* __restrict__ nn, const int* __restrict__ nl, int max_nb,
                                                 const double4_32a* __restrict__ pc, const double* __restrict__ Fp,
                                                 double* __restrict__ f, double* __restrict__ v, double c_kick,
-                                                Bath bath, double* __restrict__ w_atom, const Ctl* ctl) {
+                                                Bath bath, double* __restrict__ w_atom, int cb, const Ctl* ctl) {
     if (load_status(ctl)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < N;
-    // x_i is read again after the loop rather than held through it (39
-    // registers instead of 45: one more resident block per multiprocessor)
-    double L[3] = {0.0, 0.0, 0.0};
+    // the box's constants (for one box, the same in every thread)
+    const int b = SINGLE || !active ? 0 : g.atom_box[i];
+    double L[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+    const int kq = box_kq(L[0], L[1], L[2]);
+    const DSplit D = dsplit_init(kq, cb);
+    long long qL[3], qi[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) qL[a] = to_fixed(L[a], kq);
     double Fpi = 0.0;
     int n = 0;
     if (active) {
-        const int b = SINGLE ? 0 : g.atom_box[i];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+        const longlong4_32a q = xq[i];
+        // x_i less the pre-shift's rounding constant: x_j - that = d + rnd
+        qi[0] = q.x - D.rnd;
+        qi[1] = q.y - D.rnd;
+        qi[2] = q.z - D.rnd;
         Fpi = Fp[i];
         n = min(nn[i], max_nb);
     }
     const double2 zero = make_double2(0.0, 0.0);
-    // the sum is taken as sum_j s_ij x_j - x_i sum_j s_ij (Eq. 3 regrouped),
-    // x_j in the entry's image: per entry F'_i + F'_j, s, the sum of s and
-    // three FMAs with x_j, no separation (the virial alone forms it).
-    // Cancellation against x_i costs about L/|d| (~100 for a 360 A box)
-    // ulps of the force, ~1e-14 relative. Boxes of a batch take the image
-    // as L sigma (ShiftSum), as the small-system and block-per-box kernels
-    // do, so a box gives the same bits in every schedule; a single box of
-    // more than kSmallAtoms atoms adds the shift to x_j in float64.
-    double fx = 0.0, fy = 0.0, fz = 0.0, w = 0.0, ssum = 0.0;
-    ShiftSum shift;
+    // f_i = sum_j s_ij (x_j - x_i) (Eq. 3 with the separation exact in
+    // fixed point, the entry's image added as an integer): per entry F'_i +
+    // F'_j and s in float64, the rest in float32 pieces (ForceSumF)
+    ForceSumF fs;
+    double w = 0.0;
     int k = 0;
     double2 c = n > 0 ? cache_ab(pc, i) : zero;
     while (true) {
@@ -384,41 +388,21 @@ __global__ void __launch_bounds__(kFNT, VIR ? 10 : (SINGLE ? 12 : 10)) k_force(i
             const int j = entry_slot(e);
             const unsigned code = entry_code(e);
             const double s = fma(Fpi + Fp[j], c.y, c.x);
-            double px, py, pz;
-            if (SINGLE) {
-                // one large box: only the atoms next to its faces meet an
-                // image, so the float64 shift in a branch costs little
-                image_pos(x[j], code, L, px, py, pz);
-            } else {
-                const double4_32a xj = x[j];
-                px = xj.x;
-                py = xj.y;
-                pz = xj.z;
-                if (code != kNoShift) shift.add(s, code);
+            const longlong4_32a qj = xq[j];
+            long long rx = qj.x - qi[0], ry = qj.y - qi[1], rz = qj.z - qi[2];
+            if (code != kNoShift) {
+                rx += qshift(code, 0, qL[0]);
+                ry += qshift(code, 1, qL[1]);
+                rz += qshift(code, 2, qL[2]);
             }
-            ssum += s;
-            fx = fma(s, px, fx);
-            fy = fma(s, py, fy);
-            fz = fma(s, pz, fz);
-            if (VIR) {
-                if (!SINGLE) image_pos(make_double4_32a(px, py, pz, 0.0), code, L, px, py, pz);
-                const double4_32a xi = x[i];
-                w = fma(s, norm2(px - xi.x, py - xi.y, pz - xi.z), w);
-            }
+            fs.add(s, rx, ry, rz, D);
+            if (VIR) w = fma(s, r2_fixed(rx - D.rnd, ry - D.rnd, rz - D.rnd, 2 * kq), w);
             ++k;
             c = cn;
         }
     }
     if (!active) return;
-    const double4_32a xi = x[i];
-    fx = fma(-xi.x, ssum, fx);
-    fy = fma(-xi.y, ssum, fy);
-    fz = fma(-xi.z, ssum, fz);
-    if (!SINGLE) {
-        fx = fma(L[0], shift.value(0), fx);
-        fy = fma(L[1], shift.value(1), fy);
-        fz = fma(L[2], shift.value(2), fz);
-    }
+    const double fx = fs.value(0), fy = fs.value(1), fz = fs.value(2);
     f[i] = fx;
     f[Np + i] = fy;
     f[2 * Np + i] = fz;
@@ -567,28 +551,38 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
                                                       int max_nb, const double4_32a* __restrict__ pc,
                                                       const double* __restrict__ Fp, double* __restrict__ f,
                                                       double* __restrict__ v, double c_kick, Bath bath,
-                                                      double* __restrict__ w_atom, const Ctl* ctl) {
+                                                      double* __restrict__ w_atom, int cb, const Ctl* ctl) {
     if (load_status(ctl)) return;
-    __shared__ double4_32a sv[kSmallRows][32];  // (s_ij, position of j)
-    __shared__ unsigned char sok[kSmallRows][32];  // 0: no term; else 1 + the entry's image code
+    // the float32 pieces of each term: (s_h, s_l, d_h x, d_h y), (d_h z, d_l x, d_l y, d_l z)
+    __shared__ float4 sp[kSmallRows][2][32];
+    __shared__ double2 sw[VIR ? kSmallRows : 1][32];  // (s_ij, r_ij^2)
+    __shared__ unsigned char sok[kSmallRows][32];     // 1: a term
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * 32 + lane;
     const bool active = i < N;
-    double L[3] = {0.0, 0.0, 0.0};
+    const int b = SINGLE || !active ? 0 : g.atom_box[i];
+    double L[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+    const int kq = box_kq(L[0], L[1], L[2]);
+    const DSplit D = dsplit_init(kq, cb);
+    long long qL[3], qi[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) qL[a] = to_fixed(L[a], kq);
     double Fpi = 0.0;
     int n = 0;
     if (active) {
-        const int b = SINGLE ? 0 : g.atom_box[i];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) L[a] = SINGLE ? g.L0[a] : g.L[3 * b + a];
+        const double4_32a xi = x[i];
+        // the fixed point of k_fixed_positions, less the rounding constant
+        qi[0] = to_fixed(xi.x, kq) - D.rnd;
+        qi[1] = to_fixed(xi.y, kq) - D.rnd;
+        qi[2] = to_fixed(xi.z, kq) - D.rnd;
         Fpi = Fp[i];
         n = min(nn[i], max_nb);
     }
     const int kmax = warp_max(n);
-    double fx = 0.0, fy = 0.0, fz = 0.0, w = 0.0, ssum = 0.0;
-    ShiftSum shift;
-    double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    if (VIR && active && wq == 0) xi = x[i];
+    ForceSumF fs;
+    double w = 0.0;
     for (int k0 = 0; k0 < kmax; k0 += kSmallRows) {
 #pragma unroll 4
         for (int r = wq; r < kSmallRows; r += kFNT / 32) {
@@ -603,11 +597,22 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
                     const double4_32a xj = x[j];
                     const double sij = fma(Fpi + Fp[j], c.y, c.x);
                     const unsigned code = entry_code(e);
-                    sv[r][lane] = make_double4_32a(sij, xj.x, xj.y, xj.z);
-                    ok = (unsigned char)(1u + code);
-                    // the image sums are integer: each warp takes its rows'
-                    // terms, the partial sums meet after the loop
-                    if (code != kNoShift) shift.add(sij, code);
+                    long long rx = to_fixed(xj.x, kq) - qi[0], ry = to_fixed(xj.y, kq) - qi[1],
+                              rz = to_fixed(xj.z, kq) - qi[2];
+                    if (code != kNoShift) {
+                        rx += qshift(code, 0, qL[0]);
+                        ry += qshift(code, 1, qL[1]);
+                        rz += qshift(code, 2, qL[2]);
+                    }
+                    float sh, sl, dh[3], dl[3];
+                    ssplit(sij, sh, sl);
+                    dsplit(rx, D, dh[0], dl[0]);
+                    dsplit(ry, D, dh[1], dl[1]);
+                    dsplit(rz, D, dh[2], dl[2]);
+                    sp[r][0][lane] = make_float4(sh, sl, dh[0], dh[1]);
+                    sp[r][1][lane] = make_float4(dh[2], dl[0], dl[1], dl[2]);
+                    if (VIR) sw[r][lane] = make_double2(sij, r2_fixed(rx - D.rnd, ry - D.rnd, rz - D.rnd, 2 * kq));
+                    ok = 1;
                 }
             }
             sok[r][lane] = ok;
@@ -617,39 +622,19 @@ __global__ void __launch_bounds__(kFNT) k_force_small(int64_t N, int64_t Np, Geo
             // the operations and order of k_force
             const int kend = min(n - k0, kSmallRows);
             for (int r = 0; r < kend; ++r) {
-                const unsigned ok = sok[r][lane];
-                if (!ok) continue;
-                const double4_32a q = sv[r][lane];
-                const unsigned code = ok - 1u;
-                const double s = q.x;
-                ssum += s;
-                fx = fma(s, q.y, fx);
-                fy = fma(s, q.z, fy);
-                fz = fma(s, q.w, fz);
+                if (!sok[r][lane]) continue;
+                const float4 p0 = sp[r][0][lane], p1 = sp[r][1][lane];
+                fs.add(p0.x, p0.y, {p0.z, p0.w, p1.x}, {p1.y, p1.z, p1.w});
                 if (VIR) {
-                    double px, py, pz;
-                    image_pos(make_double4_32a(q.y, q.z, q.w, 0.0), code, L, px, py, pz);
-                    w = fma(s, norm2(px - xi.x, py - xi.y, pz - xi.z), w);
+                    const double2 q = sw[r][lane];
+                    w = fma(q.x, q.y, w);
                 }
             }
         }
         __syncthreads();
     }
-    __shared__ __int128 spart[kFNT / 32 - 1][3][32];
-    if (wq != 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) spart[wq - 1][a][lane] = shift.a[a];
-    }
-    __syncthreads();
     if (wq != 0 || !active) return;
-#pragma unroll
-    for (int w2 = 0; w2 < kFNT / 32 - 1; ++w2)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) shift.a[a] += spart[w2][a][lane];
-    xi = x[i];
-    fx = fma(L[0], shift.value(0), fma(-xi.x, ssum, fx));
-    fy = fma(L[1], shift.value(1), fma(-xi.y, ssum, fy));
-    fz = fma(L[2], shift.value(2), fma(-xi.z, ssum, fz));
+    const double fx = fs.value(0), fy = fs.value(1), fz = fs.value(2);
     f[i] = fx;
     f[Np + i] = fy;
     f[2 * Np + i] = fz;
@@ -869,10 +854,12 @@ static void run_fp64_small(Engine& e, int kick, cudaStream_t s, bool virial) {
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     if (virial)
         k_force_small<SINGLE, true><<<nb32, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.pc, e.Fp,
-                                                          e.f, kick ? e.v : nullptr, c_kick, e.bath, e.w_atom, e.ctl);
+                                                          e.f, kick ? e.v : nullptr, c_kick, e.bath, e.w_atom,
+                                                          cut_bits(e.pot.rc), e.ctl);
     else
         k_force_small<SINGLE, false><<<nb32, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.pc, e.Fp,
-                                                           e.f, kick ? e.v : nullptr, c_kick, e.bath, nullptr, e.ctl);
+                                                           e.f, kick ? e.v : nullptr, c_kick, e.bath, nullptr,
+                                                           cut_bits(e.pot.rc), e.ctl);
 }
 
 template <int KIND, bool SINGLE>
@@ -896,11 +883,13 @@ static void run_fp64(Engine& e, int kick, cudaStream_t s, bool virial) {
     }
     PhaseScope scope(e, MD_PHASE_FORCE, s);
     if (virial)
-        k_force<SINGLE, true><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.pc, e.Fp, e.f,
-                                                  kick ? e.v : nullptr, c_kick, e.bath, e.w_atom, e.ctl);
+        k_force<SINGLE, true><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.xq, e.nn, e.nl, e.max_nb, e.pc, e.Fp, e.f,
+                                                  kick ? e.v : nullptr, c_kick, e.bath, e.w_atom,
+                                                  cut_bits(e.pot.rc), e.ctl);
     else
-        k_force<SINGLE, false><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.x, e.nn, e.nl, e.max_nb, e.pc, e.Fp, e.f,
-                                                   kick ? e.v : nullptr, c_kick, e.bath, nullptr, e.ctl);
+        k_force<SINGLE, false><<<nb, kFNT, 0, s>>>(e.N, e.N_pad, g, e.xq, e.nn, e.nl, e.max_nb, e.pc, e.Fp, e.f,
+                                                   kick ? e.v : nullptr, c_kick, e.bath, nullptr,
+                                                   cut_bits(e.pot.rc), e.ctl);
 }
 
 template <int KIND, bool SINGLE>
