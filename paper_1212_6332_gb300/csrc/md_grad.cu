@@ -174,10 +174,11 @@ __device__ __forceinline__ bool zero_entry(double2 c) {
 }
 
 // u_i = sum_j (g_i - g_j) . d_ij rho'(r)/r with rho'/r from the cache and
-// d_ij from the entry's image (zero cache entries lie beyond r_cut). Each
-// lane steps to its own next non-zero entry, so the float64 work of an
-// iteration runs with nearly all lanes active (a branch over the zero
-// entries leaves them masked); the sum keeps its order.
+// d_ij from the entry's image (zero cache entries lie beyond r_cut). Every
+// entry in turn, the next cache value and list entry loaded ahead; zero
+// entries skip the arithmetic (stepping each lane to its next non-zero
+// entry kept the lanes converged at one dependent load per skipped
+// entry); the sum keeps its order.
 __global__ void __launch_bounds__(kGNT) k_grad_u_cached(int64_t N, int64_t Np, Geo g,
                                                         const double4_32a* __restrict__ x,
                                                         const int* __restrict__ nn, const int* __restrict__ nl,
@@ -201,26 +202,22 @@ __global__ void __launch_bounds__(kGNT) k_grad_u_cached(int64_t N, int64_t Np, G
     }
     const double2 zero = make_double2(0.0, 0.0);
     double acc = 0.0;
-    int k = 0;
     double2 c = n > 0 ? cache_ab(pc, i) : zero;
-    while (true) {
-        while (k < n && zero_entry(c)) {
-            ++k;
-            c = k < n ? cache_ab(pc, (int64_t)k * Np + i) : zero;
-        }
-        const bool has = k < n;
-        if (!__any_sync(0xffffffffu, has)) break;
-        if (has) {
-            const int64_t slot = (int64_t)k * Np + i;
-            const double2 cn = k + 1 < n ? cache_ab(pc, slot + Np) : zero;
-            const int e = nl[slot];
+    int e = n > 0 ? nl[i] : 0;
+    const int kmax = warp_max(n);
+    for (int k = 0; k < kmax; ++k) {
+        const int64_t slot = (int64_t)k * Np + i;
+        const bool more = k + 1 < n;
+        const double2 cn = more ? cache_ab(pc, slot + Np) : zero;
+        const int en = more ? nl[slot + Np] : 0;
+        if (k < n && !zero_entry(c)) {
             const int j = entry_slot(e);
             double dx, dy, dz;
             sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
             acc += ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * c.y;
-            ++k;
-            c = cn;
         }
+        c = cn;
+        e = en;
     }
     if (active) u[i] = acc;
 }
@@ -338,40 +335,37 @@ __global__ void __launch_bounds__(kGNT) k_grad_param_rgl_pairs(int64_t N, int64_
             aFi = u[i] * Fpp[i] + ge * Fpi;
         }
         const double aV2 = ge;  // 1/2 g_E from each side
-        int k = 0;
+        // every row in turn (the next cache value and list entry loaded
+        // ahead); zero entries and, in an unrotated list, entries j < i
+        // skip the arithmetic
         double2 c = n > 0 ? cache_ab(pc, i) : zero;
-        while (true) {
-            // next non-zero entry of an upper row (an unrotated list also
-            // holds entries j < i, skipped here)
-            while (k < n && (zero_entry(c) || entry_slot(nl[(int64_t)k * Np + i]) <= i)) {
-                ++k;
-                c = k < n ? cache_ab(pc, (int64_t)k * Np + i) : zero;
-            }
-            const bool has = k < n;
-            if (!__any_sync(0xffffffffu, has)) break;
-            if (has) {
+        int e = n > 0 ? nl[i] : 0;
+        const int kmax = warp_max(n);
+        for (int k = 0; k < kmax; ++k) {
             const int64_t slot = (int64_t)k * Np + i;
-            const double2 cn = k + 1 < n ? cache_ab(pc, slot + Np) : zero;
-            const int e = nl[slot];
+            const bool more = k + 1 < n;
+            const double2 cn = more ? cache_ab(pc, slot + Np) : zero;
+            const int en = more ? nl[slot + Np] : 0;
             const int j = entry_slot(e);
-            const double2 fv = cache_fv(pc, slot);
-            double dx, dy, dz;
-            sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
-            const double r2 = norm2(dx, dy, dz);
-            double rinv, r;
-            rsqrt_sqrt(r2, rinv, r);
-            const double W = ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * rinv;
-            const double AFp = W * (Fpi + Fp[j]);
-            const double AF = aFi + (u[j] * Fpp[j] + ge * Fp[j]);
-            const double V = fv.y, rh = fv.x, Vp = c.x * r, rhp = c.y * r;
-            const double tV = W * Vp + aV2 * V, tR = AFp * rhp + AF * rh;
-            t1 += tV;
-            t4 += tR;
-            t23 = fma(r, tV, fma(W, V, t23));
-            t56 = fma(r, tR, fma(AFp, rh, t56));
-            ++k;
-            c = cn;
+            if (k < n && !zero_entry(c) && j > i) {
+                const double2 fv = cache_fv(pc, slot);
+                double dx, dy, dz;
+                sep_entry(xi, x[j], entry_code(e), L, dx, dy, dz);
+                const double r2 = norm2(dx, dy, dz);
+                double rinv, r;
+                rsqrt_sqrt(r2, rinv, r);
+                const double W = ((gx - gs[j]) * dx + (gy - gs[Np + j]) * dy + (gz - gs[2 * Np + j]) * dz) * rinv;
+                const double AFp = W * (Fpi + Fp[j]);
+                const double AF = aFi + (u[j] * Fpp[j] + ge * Fp[j]);
+                const double V = fv.y, rh = fv.x, Vp = c.x * r, rhp = c.y * r;
+                const double tV = W * Vp + aV2 * V, tR = AFp * rhp + AF * rh;
+                t1 += tV;
+                t4 += tR;
+                t23 = fma(r, tV, fma(W, V, t23));
+                t56 = fma(r, tR, fma(AFp, rh, t56));
             }
+            c = cn;
+            e = en;
         }
     }
     double acc[kRglParams];
